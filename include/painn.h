@@ -1,0 +1,150 @@
+/*
+ * painn.h -- C ABI of the GB300 engine for a PaiNN-form semi-local potential
+ * (energy, forces, virial) over a periodic neighbour graph.
+ *
+ * Method: arXiv 2506.04055 ("chemtrain-deploy").  The total energy is a sum of semi-local
+ * per-atom energies over a cutoff graph (Methods, "(Semi-)Local Potential Models", energy-sum
+ * equation); forces are its negative gradient (Results, "Distributed potential computation",
+ * sum-rule equation); the MD code hands the library positions and a neighbour graph built
+ * with a skin, the library prunes edges longer than the cutoff every step, buffers data to
+ * fixed capacities that only grow, checks for overflow after a run and repeats it with larger
+ * buffers (Results, "Runtime optimizations and buffering").  The model is PaiNN (Methods,
+ * "Chosen Architectures"), with cutoff 5 A (Methods, "Training Details").
+ *
+ * Conventions (all entry points):
+ *   - Units: Angstrom, eV, amu, fs.  Arrays are row-major.  A cell is double[9] whose ROWS
+ *     are the lattice vectors a, b, c; every system is periodic in all three directions.
+ *   - Atom arrays are in the caller's order.  Positions/forces are [n][3] double.
+ *   - Pointers are host pointers unless CTD_DEVICE_PTRS is set in `flags`, in which case
+ *     species/positions/energy/forces/virial are device pointers valid on the context's
+ *     stream.  The caller owns every pointer it passes; the library copies what it keeps.
+ *   - The context owns its device buffers.  They grow (never shrink) up to the HBM budget
+ *     given at creation; a call that would exceed it fails with CTD_ERR_OUT_OF_BUDGET.
+ *   - Calls on one context are not thread-safe; distinct contexts are independent.
+ *   - Every call returns CTD_OK (0) or a negative CTD_ERR_* code; ctd_last_error() then
+ *     describes the failure.  Device kernels never trap: they raise status words that the
+ *     host reads after the launch.
+ */
+#ifndef CTD_PAINN_H
+#define CTD_PAINN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------------- */
+#define CTD_OK 0
+#define CTD_ERR_INVALID_ARG (-1)   /* bad pointer, size, flag, cell or parameter blob          */
+#define CTD_ERR_CAPACITY (-2)      /* an internal buffer overflowed and could not be regrown    */
+#define CTD_ERR_OUT_OF_BUDGET (-3) /* growing a buffer would exceed the HBM budget              */
+#define CTD_ERR_CELL_TOO_SMALL (-4) /* cell thinner than the search needs (image limit, 127)    */
+#define CTD_ERR_CUDA (-5)          /* a CUDA runtime call failed                                */
+#define CTD_ERR_TIMEOUT (-6)       /* a bounded device wait gave up                             */
+#define CTD_ERR_NONFINITE (-7)     /* NaN/Inf in positions or results                           */
+#define CTD_ERR_STATE (-8)         /* call out of order (no parameters, no neighbour list, ...) */
+
+/* ---- precision of the dense contractions ----------------------------------------------- */
+#define CTD_PREC_FP32 0   /* every product in FP32 on CUDA cores                              */
+#define CTD_PREC_BF16 1   /* filter / message / update MLPs in BF16 on tcgen05, FP32 accum    */
+
+/* ---- flags for ctd_compute ---------------------------------------------------------------- */
+#define CTD_NEED_FORCES 1      /* write forces[n][3]                                          */
+#define CTD_NEED_VIRIAL 2      /* write virial[9] = -sum_e r_e (x) dU/dr_e (row-major, eV)     */
+#define CTD_REBUILD 4          /* rebuild the neighbour list even if the skin still holds     */
+#define CTD_DEVICE_PTRS 8      /* I/O pointers are device pointers on the context's stream    */
+
+/* Model description.  F: feature width (even, multiple of 32, <= 256); K: radial basis size
+ * (<= 32); T: interaction layers (<= 8); n_species: embedding rows; rc: cutoff (A);
+ * precision: CTD_PREC_*.  Must equal the header of the parameter blob. */
+typedef struct {
+  int32_t F, K, T, n_species;
+  double rc;
+  int32_t precision;
+} ctd_model_desc;
+
+/* Per-call statistics (the library "returns statistics of the computation"). */
+typedef struct {
+  int64_t n_atoms;
+  int64_t n_verlet_edges;   /* directed edges within rc + skin                                */
+  int64_t n_active_edges;   /* directed edges within rc this step                             */
+  int32_t rebuilt;          /* 1 if this call rebuilt the neighbour list                      */
+  int32_t retries;          /* repeats after a capacity overflow                              */
+  double max_displacement;  /* largest displacement since the last rebuild (A)                */
+  int64_t bytes_allocated;  /* device bytes held by the context                               */
+  float ms_neighbors, ms_model;   /* device time of the neighbour and model stages (ms)      */
+} ctd_stats;
+
+typedef struct ctd_ctx ctd_ctx;
+
+/* Create a context on the current CUDA device.  `hbm_budget_bytes` caps the device memory
+ * the context may hold (0 = no cap).  `cuda_stream` is a cudaStream_t (NULL = a new stream
+ * owned by the context).  On success *out receives the context. */
+int ctd_create(ctd_ctx **out, const ctd_model_desc *desc, size_t hbm_budget_bytes,
+               void *cuda_stream);
+
+/* Copy model parameters from a host blob: 64-byte header (magic "CTDPAINN", int32 version=1,
+ * F, K, T, S, reserved; float64 rc, eps, e_scale; int64 n_values) followed by n_values
+ * float64 weights in this order (matrices [out][in]): emb[S][F]; per layer W1[F][F] b1[F]
+ * W2[3F][F] b2[3F] Wf[3F][K] bf[3F] U[F][F] V[F][F] A1[F][2F] c1[F] A2[3F][F] c2[3F];
+ * R1[F/2][F] d1[F/2] R2[F/2] d2[1].  The caller keeps the blob. */
+int ctd_load_params(ctd_ctx *ctx, const void *blob, size_t nbytes);
+
+/* Build the Verlet neighbour list of n atoms: every (i, j, n) with
+ * |x~_j - x~_i + n1 a + n2 b + n3 c| < cutoff + skin, i != j or n != 0, where x~ are the
+ * positions wrapped into the cell.  The test is evaluated in FP64 with every product and sum
+ * rounded separately in a fixed order (bit-reproducible).  Positions are host doubles [n][3]
+ * (device pointers if flags & CTD_DEVICE_PTRS).  *n_pairs_out receives the number of
+ * directed pairs.  The list is kept in the context and reused by ctd_compute until an atom
+ * moves more than skin/2. */
+int ctd_build_neighbors(ctd_ctx *ctx, int64_t n, const double *positions, const double cell[9],
+                        double cutoff, double skin, int32_t flags, int64_t *n_pairs_out);
+
+/* Copy the current Verlet list to host arrays ordered by (i, j, n1, n2, n3), caller's atom
+ * indices; shift holds n1, n2, n3 per pair relative to the wrapped positions.  cap = array
+ * length; returns CTD_ERR_CAPACITY if the list is longer (nothing written). */
+int ctd_get_pairs(ctd_ctx *ctx, int32_t *i, int32_t *j, int8_t *shift, int64_t cap);
+
+/* Energy (and forces, virial) of n atoms.  Rebuilds the neighbour list when none exists, when
+ * n or the cell changed, when an atom moved more than skin/2 since the last build, or when
+ * CTD_REBUILD is set (the skin defaults to 1 A if ctd_build_neighbors was never called).
+ * energy: double[1]; forces: double[n][3] (with CTD_NEED_FORCES); virial: double[9] (with
+ * CTD_NEED_VIRIAL); stats may be NULL. */
+int ctd_compute(ctd_ctx *ctx, int64_t n, const int32_t *species, const double *positions,
+                const double cell[9], int32_t flags, double *energy, double *forces,
+                double *virial, ctd_stats *stats);
+
+/* Optional per-atom energy output (double[n], same pointer kind as the compute call); NULL
+ * disables it. */
+int ctd_set_energy_out(ctd_ctx *ctx, double *energies);
+
+/* ---- molecular dynamics (NVE velocity Verlet, state resident on the device) --------------- */
+
+/* Load an MD state: n atoms, species, masses (amu), positions (A), velocities (A/fs), cell,
+ * neighbour skin (A).  Host arrays; copied to the device. */
+int ctd_md_set_state(ctd_ctx *ctx, int64_t n, const int32_t *species, const double *masses,
+                     const double *positions, const double *velocities, const double cell[9],
+                     double skin);
+
+/* Advance nsteps velocity-Verlet steps of dt fs entirely on the device, rebuilding the
+ * neighbour list whenever an atom moved more than skin/2.  epot/ekin (host, may be NULL)
+ * receive nsteps+1 potential / kinetic energies (eV).  n_rebuilds (may be NULL) receives the
+ * number of rebuilds. */
+int ctd_md_run(ctd_ctx *ctx, int32_t nsteps, double dt, double *epot, double *ekin,
+               int32_t *n_rebuilds);
+
+/* Copy the MD state back (host arrays [n][3], either may be NULL). */
+int ctd_md_get_state(ctd_ctx *ctx, double *positions, double *velocities);
+
+/* Text of the last failure on this context (never NULL). */
+const char *ctd_last_error(ctd_ctx *ctx);
+
+/* Release every device buffer and the context (and its stream if it created one). */
+void ctd_destroy(ctd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTD_PAINN_H */

@@ -1,0 +1,216 @@
+"""GB300 engine for a PaiNN-form semi-local potential (arXiv 2506.04055, chemtrain-deploy):
+energy, forces and virial over a periodic neighbour graph, plus a resident NVE loop.
+
+The compute path is the CUDA library ``libctd_painn.so`` (sm_103a) behind the C ABI in
+``include/painn.h``; this package only marshals arguments.  ``Potential`` wraps one context;
+``PaiNNEnergy`` is the ``torch.autograd.Function`` whose backward returns -grad_E * forces
+from the library's hand-written adjoint.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (CTD_DEVICE_PTRS, CTD_NEED_FORCES, CTD_NEED_VIRIAL, CTD_PREC_BF16,  # noqa: F401
+                   CTD_PREC_FP32, CTD_REBUILD, CtdError, ctd_model_desc, ctd_stats)
+
+__all__ = ["Potential", "PaiNNEnergy", "CtdError", "build", "load"]
+
+
+def build(force: bool = False) -> str:
+    from .buildlib import build as _build
+    return _build(force=force)
+
+
+def load():
+    return _lib.load()
+
+
+def _is_torch_cuda(a) -> bool:
+    try:
+        import torch
+    except ImportError:
+        return False
+    return isinstance(a, torch.Tensor) and a.is_cuda
+
+
+def _host(a, dtype, shape=None):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+class Potential:
+    """One engine context: model description, parameters, neighbour list, MD state.
+
+    precision: "fp32" (all products in FP32) or "bf16" (tensor-core MLPs, FP32 accumulation).
+    params: the blob of ``synthetic.params_blob`` (64-byte header + float64 weights).
+    stream: a CUDA stream handle (int) or None for a stream owned by the context.
+    """
+
+    def __init__(self, F: int, K: int = 20, T: int = 3, n_species: int = 2, rc: float = 5.0,
+                 precision: str = "fp32", params: bytes | None = None, hbm_budget_bytes: int = 0,
+                 stream: int | None = None):
+        prec = {"fp32": CTD_PREC_FP32, "bf16": CTD_PREC_BF16}[precision]
+        self.desc = ctd_model_desc(F, K, T, n_species, rc, prec)
+        self.F, self.K, self.T, self.S, self.rc, self.precision = F, K, T, n_species, rc, precision
+        self.ctx = _lib.ctd_create(self.desc, hbm_budget_bytes, stream)
+        if params is not None:
+            self.load_params(params)
+
+    # -- lifetime ------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            _lib.ctd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- parameters and neighbours ----------------------------------------------------------
+    def load_params(self, blob: bytes):
+        _lib.ctd_load_params(self.ctx, blob)
+
+    def build_neighbors(self, positions, cell, cutoff: float | None = None, skin: float = 1.0) -> int:
+        cutoff = self.rc if cutoff is None else cutoff
+        H = _host(cell, np.float64, (3, 3))
+        if _is_torch_cuda(positions):
+            x = positions.contiguous()
+            flags = CTD_DEVICE_PTRS
+        else:
+            x = _host(positions, np.float64, (-1, 3))
+            flags = 0
+        return _lib.ctd_build_neighbors(self.ctx, int(x.shape[0]), _ptr(x), _ptr(H), float(cutoff),
+                                        float(skin), flags)
+
+    def get_pairs(self, n_pairs: int):
+        i = np.empty(n_pairs, np.int32)
+        j = np.empty(n_pairs, np.int32)
+        s = np.empty((n_pairs, 3), np.int8)
+        _lib.ctd_get_pairs(self.ctx, _ptr(i), _ptr(j), _ptr(s), n_pairs)
+        return i, j, s
+
+    # -- energy / forces / virial ----------------------------------------------------------
+    def compute(self, species, positions, cell, forces: bool = True, virial: bool = True,
+                rebuild: bool = False, stats: bool = False, energies: bool = False):
+        """Energy (eV), forces [n,3] (eV/A), virial [3,3] (eV).  numpy inputs -> numpy outputs
+        (host pointers through the ABI); CUDA torch tensors -> CUDA torch tensors (device
+        pointers, the context's stream)."""
+        H = _host(cell, np.float64, (3, 3))
+        flags = (CTD_NEED_FORCES if forces else 0) | (CTD_NEED_VIRIAL if virial else 0)
+        flags |= CTD_REBUILD if rebuild else 0
+        st = ctd_stats() if stats else None
+        if _is_torch_cuda(positions):
+            import torch
+            dev = positions.device
+            x = positions.detach().to(torch.float64).contiguous()
+            z = species.to(device=dev, dtype=torch.int32).contiguous()
+            n = int(x.shape[0])
+            E = torch.zeros(1, dtype=torch.float64, device=dev)
+            Fo = torch.empty((n, 3), dtype=torch.float64, device=dev) if forces else None
+            W = torch.empty((3, 3), dtype=torch.float64, device=dev) if virial else None
+            Ea = torch.empty(n, dtype=torch.float64, device=dev) if energies else None
+            flags |= CTD_DEVICE_PTRS
+            # inputs were produced on torch's stream; the context runs on its own stream
+            torch.cuda.current_stream(dev).synchronize()
+        else:
+            x = _host(positions, np.float64, (-1, 3))
+            z = _host(species, np.int32)
+            n = int(x.shape[0])
+            E = np.zeros(1)
+            Fo = np.empty((n, 3)) if forces else None
+            W = np.empty((3, 3)) if virial else None
+            Ea = np.empty(n) if energies else None
+        _lib.ctd_set_energy_out(self.ctx, _ptr(Ea))
+        try:
+            _lib.ctd_compute(self.ctx, n, _ptr(z), _ptr(x), _ptr(H), flags, _ptr(E), _ptr(Fo),
+                             _ptr(W), st)
+        finally:
+            _lib.ctd_set_energy_out(self.ctx, None)
+        out = {"energy": E if flags & CTD_DEVICE_PTRS else float(E[0]), "forces": Fo, "virial": W}
+        if energies:
+            out["energies"] = Ea
+        if stats:
+            out["stats"] = {k: getattr(st, k) for k, _ in ctd_stats._fields_}
+        return out
+
+    # -- molecular dynamics ----------------------------------------------------------------
+    def md_set_state(self, species, masses, positions, velocities, cell, skin: float = 1.0):
+        z = _host(species, np.int32)
+        m = _host(masses, np.float64)
+        x = _host(positions, np.float64, (-1, 3))
+        v = _host(velocities, np.float64, (-1, 3))
+        H = _host(cell, np.float64, (3, 3))
+        self._md_n = x.shape[0]
+        _lib.ctd_md_set_state(self.ctx, x.shape[0], _ptr(z), _ptr(m), _ptr(x), _ptr(v), _ptr(H),
+                              float(skin))
+
+    def md_run(self, nsteps: int, dt: float):
+        """Run nsteps velocity-Verlet steps on the device.  Returns (epot, ekin, n_rebuilds)."""
+        ep = np.empty(nsteps + 1)
+        ek = np.empty(nsteps + 1)
+        nreb = _lib.ctd_md_run(self.ctx, nsteps, float(dt), _ptr(ep), _ptr(ek))
+        return ep, ek, nreb
+
+    def md_get_state(self):
+        x = np.empty((self._md_n, 3))
+        v = np.empty((self._md_n, 3))
+        _lib.ctd_md_get_state(self.ctx, _ptr(x), _ptr(v))
+        return x, v
+
+
+def _make_autograd():
+    import torch
+
+    class PaiNNEnergy(torch.autograd.Function):
+        """E = PaiNNEnergy.apply(positions, species, cell, potential) -> (energy, virial).
+
+        positions: CUDA float64 [n,3].  The forward call runs the library's energy, forces and
+        virial kernels; backward returns grad_E * (-forces) for the positions (the virial is a
+        non-differentiable second output)."""
+
+        @staticmethod
+        def forward(ctx, positions, species, cell, potential):
+            out = potential.compute(species, positions, cell, forces=True, virial=True)
+            ctx.save_for_backward(out["forces"])
+            ctx.mark_non_differentiable(out["virial"])
+            return out["energy"][0], out["virial"]
+
+        @staticmethod
+        def backward(ctx, grad_e, grad_w):
+            (forces,) = ctx.saved_tensors
+            return -grad_e * forces, None, None, None
+
+    return PaiNNEnergy
+
+
+class _Lazy:
+    _cls = None
+
+    def __getattr__(self, item):
+        if _Lazy._cls is None:
+            _Lazy._cls = _make_autograd()
+        return getattr(_Lazy._cls, item)
+
+
+PaiNNEnergy = _Lazy()

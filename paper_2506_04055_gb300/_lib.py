@@ -1,0 +1,163 @@
+"""ctypes binding of the C ABI in include/painn.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  No arithmetic of the method
+happens in Python: neighbour search, model, adjoint, reductions and integration all run in the
+CUDA kernels of ``libctd_painn.so``.  If the library cannot be loaded, ``load()`` raises; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libctd_painn.so")
+
+CTD_OK = 0
+CTD_ERR_INVALID_ARG = -1
+CTD_ERR_CAPACITY = -2
+CTD_ERR_OUT_OF_BUDGET = -3
+CTD_ERR_CELL_TOO_SMALL = -4
+CTD_ERR_CUDA = -5
+CTD_ERR_TIMEOUT = -6
+CTD_ERR_NONFINITE = -7
+CTD_ERR_STATE = -8
+CTD_PREC_FP32 = 0
+CTD_PREC_BF16 = 1
+CTD_NEED_FORCES = 1
+CTD_NEED_VIRIAL = 2
+CTD_REBUILD = 4
+CTD_DEVICE_PTRS = 8
+
+ERROR_NAMES = {
+    CTD_ERR_INVALID_ARG: "CTD_ERR_INVALID_ARG", CTD_ERR_CAPACITY: "CTD_ERR_CAPACITY",
+    CTD_ERR_OUT_OF_BUDGET: "CTD_ERR_OUT_OF_BUDGET", CTD_ERR_CELL_TOO_SMALL: "CTD_ERR_CELL_TOO_SMALL",
+    CTD_ERR_CUDA: "CTD_ERR_CUDA", CTD_ERR_TIMEOUT: "CTD_ERR_TIMEOUT",
+    CTD_ERR_NONFINITE: "CTD_ERR_NONFINITE", CTD_ERR_STATE: "CTD_ERR_STATE",
+}
+
+# Every symbol include/painn.h declares (checked by the CPU test suite).
+EXPORTS = [
+    "ctd_create", "ctd_load_params", "ctd_build_neighbors", "ctd_get_pairs", "ctd_compute",
+    "ctd_set_energy_out", "ctd_md_set_state", "ctd_md_run", "ctd_md_get_state",
+    "ctd_last_error", "ctd_destroy",
+]
+
+
+class ctd_model_desc(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_int32), ("K", ctypes.c_int32), ("T", ctypes.c_int32),
+                ("n_species", ctypes.c_int32), ("rc", ctypes.c_double), ("precision", ctypes.c_int32)]
+
+
+class ctd_stats(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("n_verlet_edges", ctypes.c_int64),
+                ("n_active_edges", ctypes.c_int64), ("rebuilt", ctypes.c_int32),
+                ("retries", ctypes.c_int32), ("max_displacement", ctypes.c_double),
+                ("bytes_allocated", ctypes.c_int64), ("ms_neighbors", ctypes.c_float),
+                ("ms_model", ctypes.c_float)]
+
+
+class CtdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libctd_painn.so (build it first with ``paper_2506_04055_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: run paper_2506_04055_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "ctd_create": ([P, P, ctypes.c_size_t, P], ctypes.c_int),
+        "ctd_load_params": ([P, P, ctypes.c_size_t], ctypes.c_int),
+        "ctd_build_neighbors": ([P, I64, P, P, D, D, I32, P], ctypes.c_int),
+        "ctd_get_pairs": ([P, P, P, P, I64], ctypes.c_int),
+        "ctd_compute": ([P, I64, P, P, P, I32, P, P, P, P], ctypes.c_int),
+        "ctd_set_energy_out": ([P, P], ctypes.c_int),
+        "ctd_md_set_state": ([P, I64, P, P, P, P, P, D], ctypes.c_int),
+        "ctd_md_run": ([P, I32, D, P, P, P], ctypes.c_int),
+        "ctd_md_get_state": ([P, P, P], ctypes.c_int),
+        "ctd_last_error": ([P], ctypes.c_char_p),
+        "ctd_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def check(ctx, code):
+    if code != CTD_OK:
+        msg = load().ctd_last_error(ctx)
+        raise CtdError(code, msg.decode() if msg else "")
+    return code
+
+
+# ---- same-name wrappers (pointers are ints or ctypes pointers) ---------------------------
+def ctd_create(desc: ctd_model_desc, hbm_budget_bytes: int = 0, cuda_stream: int | None = None):
+    ctx = ctypes.c_void_p()
+    code = load().ctd_create(ctypes.byref(ctx), ctypes.byref(desc), hbm_budget_bytes, cuda_stream)
+    if code != CTD_OK:
+        raise CtdError(code, "ctd_create failed (no CUDA device or invalid model description)")
+    return ctx
+
+
+def ctd_load_params(ctx, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    return check(ctx, load().ctd_load_params(ctx, buf, len(blob)))
+
+
+def ctd_build_neighbors(ctx, n, positions_ptr, cell_ptr, cutoff, skin, flags=0):
+    out = ctypes.c_int64()
+    check(ctx, load().ctd_build_neighbors(ctx, n, positions_ptr, cell_ptr, cutoff, skin, flags,
+                                          ctypes.byref(out)))
+    return out.value
+
+
+def ctd_get_pairs(ctx, i_ptr, j_ptr, shift_ptr, cap):
+    return check(ctx, load().ctd_get_pairs(ctx, i_ptr, j_ptr, shift_ptr, cap))
+
+
+def ctd_compute(ctx, n, species_ptr, positions_ptr, cell_ptr, flags, energy_ptr, forces_ptr,
+                virial_ptr, stats=None):
+    return check(ctx, load().ctd_compute(ctx, n, species_ptr, positions_ptr, cell_ptr, flags,
+                                         energy_ptr, forces_ptr, virial_ptr,
+                                         ctypes.byref(stats) if stats is not None else None))
+
+
+def ctd_set_energy_out(ctx, ptr):
+    return check(ctx, load().ctd_set_energy_out(ctx, ptr))
+
+
+def ctd_md_set_state(ctx, n, species_ptr, masses_ptr, positions_ptr, velocities_ptr, cell_ptr, skin):
+    return check(ctx, load().ctd_md_set_state(ctx, n, species_ptr, masses_ptr, positions_ptr,
+                                              velocities_ptr, cell_ptr, skin))
+
+
+def ctd_md_run(ctx, nsteps, dt, epot_ptr, ekin_ptr):
+    nreb = ctypes.c_int32()
+    check(ctx, load().ctd_md_run(ctx, nsteps, dt, epot_ptr, ekin_ptr, ctypes.byref(nreb)))
+    return nreb.value
+
+
+def ctd_md_get_state(ctx, positions_ptr, velocities_ptr):
+    return check(ctx, load().ctd_md_get_state(ctx, positions_ptr, velocities_ptr))
+
+
+def ctd_last_error(ctx) -> str:
+    msg = load().ctd_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def ctd_destroy(ctx):
+    load().ctd_destroy(ctx)

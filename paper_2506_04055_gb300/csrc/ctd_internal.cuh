@@ -1,0 +1,104 @@
+// ctd_internal.cuh -- internal declarations of the GB300 PaiNN engine (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace ctd {
+
+constexpr int kThreads = 256;
+constexpr int kMaxT = 8;
+constexpr int kMaxKP = 32;   // radial basis, padded to a multiple of 4
+
+// Cell geometry for the neighbour build.  H rows are lattice vectors; G = H^{-T}.
+struct CellGeom {
+  double H[9];
+  double G[9];
+  int nc[3];      // cells (slabs) per lattice direction
+  int M[3];       // neighbour slab half-range per direction
+  double R2;      // (cutoff + skin)^2, rounded once in FP64
+};
+
+// Device-side status word, raised by kernels instead of trapping.
+enum Status : int {
+  ST_OK = 0,
+  ST_REV_MISSING = 1,     // a reverse edge was not found
+  ST_VERLET_OVERFLOW = 2, // more Verlet edges than capacity
+  ST_NONFINITE = 4,
+};
+
+// FP32 weights of one interaction layer (device pointers).  "t" = transposed ([in][out]).
+struct LayerW {
+  const float *W1, *W1t, *b1;      // [F][F]
+  const float *W2, *W2t, *b2;      // [3F][F], [F][3F]
+  const float *Wf, *bf;            // [3F][KP] (zero padded), [3F]
+  const float *UV, *UVt;           // [2F][F] = [U;V], [F][2F] = [U^T | V^T]
+  const float *A1, *A1t, *c1;      // [F][2F], [2F][F]
+  const float *A2, *A2t, *c2;      // [3F][F], [F][3F]
+};
+
+struct ModelW {
+  int F, K, KP, T, S;
+  float rc, eps, e_scale;
+  const float* emb;                // [S][F]
+  LayerW L[kMaxT];
+  const float *R1, *R1t, *d1, *R2, *d2;   // [F/2][F], [F][F/2]
+};
+
+// ---------------------------------------------------------------- small device helpers
+__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + __expf(-x)); }
+__device__ __forceinline__ float dsilu_f(float x) {
+  float s = 1.0f / (1.0f + __expf(-x));
+  return s * (1.0f + x * (1.0f - s));
+}
+
+// ---------------------------------------------------------------- launchers (host side)
+// neighbors.cu
+void launch_wrap_bin(cudaStream_t st, int64_t n, const double* x_user, const CellGeom& g,
+                     double* xw, int32_t* wrapm, int32_t* cell, int32_t* cell_count);
+void launch_place(cudaStream_t st, int64_t n, const int32_t* cell, const int32_t* cell_start,
+                  int32_t* cursor, int32_t* tmp_idx);
+void launch_sort_cells(cudaStream_t st, int64_t ncell, const int32_t* cell_start,
+                       const int32_t* tmp_idx, int32_t* perm);
+void launch_gather_sorted(cudaStream_t st, int64_t n, const int32_t* perm, const double* xw,
+                          const double* x_user, const int32_t* species_user, double* xw_s,
+                          double* xref_s, int32_t* species_s, int32_t* inv_perm);
+void launch_pair_search(cudaStream_t st, bool fill, int64_t n, const double* xw_s,
+                        const int32_t* cell_start, const CellGeom& g, int32_t* count,
+                        const int32_t* row_ptr, int32_t* col, uint32_t* img, float4* base);
+void launch_reverse(cudaStream_t st, int64_t n, const int32_t* row_ptr, const int32_t* col,
+                    const uint32_t* img, int32_t* rev, int* status);
+void launch_delta(cudaStream_t st, int64_t n, const double* x_s, const double* xref_s,
+                  float4* delta, unsigned int* maxdisp2_bits);
+void launch_gather_positions(cudaStream_t st, int64_t n, const int32_t* perm, const double* x_user,
+                             double* x_s);
+void launch_prune(cudaStream_t st, bool fill, int64_t n, const int32_t* vrow, const int32_t* vcol,
+                  const float4* vbase, const float4* delta, float rc2, int32_t* acount,
+                  const int32_t* arow, int32_t* acol, float4* ar, int32_t* vidx, int32_t* v2a);
+void launch_prune_rev(cudaStream_t st, int64_t n, const int32_t* arow, const int32_t* vidx,
+                      const int32_t* vrev, const int32_t* v2a, int32_t* arev);
+// scan.cu
+size_t scan_temp_bytes(int64_t n);
+void launch_exclusive_scan(cudaStream_t st, int64_t n, const int32_t* in, int32_t* out,
+                           void* temp);   // out has n+1 entries; out[n] = total
+// md.cu
+void launch_kick_drift(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* x, double* v);
+void launch_kick(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* v);
+void launch_kinetic(cudaStream_t st, int64_t n, const double* m, const double* v, double* partials, int nb);
+void launch_sum_partials(cudaStream_t st, int nb, int width, const double* partials, double* out, double scale);
+void launch_scatter_rows(cudaStream_t st, int64_t n, int w, const int32_t* perm, const float* in, double* out);
+void launch_scatter_rows_d(cudaStream_t st, int64_t n, int w, const int32_t* perm, const double* in, double* out);
+void launch_gather_rows_d(cudaStream_t st, int64_t n, int w, const int32_t* perm, const double* in, double* out);
+void launch_gather_i32(cudaStream_t st, int64_t n, const int32_t* perm, const int32_t* in, int32_t* out);
+void launch_check_finite(cudaStream_t st, int64_t n, const double* a, int* status);
+// model_fp32.cu
+int model_buffer_count();
+int64_t model_buffer_floats_per_atom(int b, int F, int T);
+void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
+                                 const int32_t* arow, const int32_t* acol, const float4* ar,
+                                 const int32_t* arev, float* const* bufs, bool need_grad,
+                                 double* energy_partials, int n_energy_partials, float4* hedge,
+                                 float* force_s, double* virial_partials, int n_virial_partials,
+                                 float* e_atom, int* status);
+}  // namespace ctd

@@ -1,0 +1,140 @@
+// md.cu -- velocity-Verlet NVE kernels, output scatter to the caller's atom order and the
+// deterministic FP64 reductions of energy / virial partials.
+//
+// Forces drive every MD step (arXiv 2506.04055, Results "Distributed potential computation");
+// the integrator is velocity Verlet in FP64 on cell-sorted arrays.  Units: A, fs, amu, eV;
+// acceleration (A/fs^2) = 9.648533212331002e-3 * F (eV/A) / m (amu).
+#include "ctd_internal.cuh"
+
+namespace ctd {
+
+constexpr double kAcc = 9.648533212331002e-3;
+
+// v += dt/2 a(F);  x += dt v   (first half of velocity Verlet)
+__global__ void k_kick_drift(int64_t n, double dt, const float* __restrict__ force, const double* __restrict__ mass,
+                             double* __restrict__ x, double* __restrict__ v) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double s = 0.5 * dt * kAcc / mass[k];
+  for (int c = 0; c < 3; ++c) {
+    double vc = v[3 * k + c] + s * (double)force[3 * k + c];
+    v[3 * k + c] = vc;
+    x[3 * k + c] += dt * vc;
+  }
+}
+
+// v += dt/2 a(F)   (second half)
+__global__ void k_kick(int64_t n, double dt, const float* __restrict__ force, const double* __restrict__ mass,
+                       double* __restrict__ v) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double s = 0.5 * dt * kAcc / mass[k];
+  for (int c = 0; c < 3; ++c) v[3 * k + c] += s * (double)force[3 * k + c];
+}
+
+// per-block partial sums of m v^2 / 2 (eV)
+__global__ void k_kinetic(int64_t n, const double* __restrict__ mass, const double* __restrict__ v,
+                          double* __restrict__ partials) {
+  __shared__ double sb[kThreads / 32];
+  double acc = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    acc += 0.5 * mass[k] * (v[3 * k] * v[3 * k] + v[3 * k + 1] * v[3 * k + 1] + v[3 * k + 2] * v[3 * k + 2]) / kAcc;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += sb[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+// Sum `count` groups of `width` partials in a fixed order with Neumaier compensation:
+// out[c] = sum_b partials[b * width + c].  One warp, lane c handles column c (width <= 32).
+__global__ void k_sum_partials(int nb, int width, const double* __restrict__ partials, double* __restrict__ out,
+                               double scale) {
+  int c = threadIdx.x;
+  if (c >= width) return;
+  double s = 0.0, comp = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    double x = partials[(int64_t)b * width + c], t = s + x;
+    comp += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  out[c] = (s + comp) * scale;
+}
+
+// out[perm[k]] = (double) in[k]  for [n][w] rows
+__global__ void k_scatter_rows(int64_t n, int w, const int32_t* __restrict__ perm, const float* __restrict__ in,
+                               double* __restrict__ out) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * w) return;
+  int64_t k = idx / w;
+  int c = (int)(idx % w);
+  out[(int64_t)perm[k] * w + c] = (double)in[idx];
+}
+
+// out[perm[k]] = in[k]  (double rows) and the inverse gather
+__global__ void k_scatter_rows_d(int64_t n, int w, const int32_t* __restrict__ perm, const double* __restrict__ in,
+                                 double* __restrict__ out) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * w) return;
+  int64_t k = idx / w;
+  int c = (int)(idx % w);
+  out[(int64_t)perm[k] * w + c] = in[idx];
+}
+
+__global__ void k_gather_rows_d(int64_t n, int w, const int32_t* __restrict__ perm, const double* __restrict__ in,
+                                double* __restrict__ out) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * w) return;
+  int64_t k = idx / w;
+  int c = (int)(idx % w);
+  out[idx] = in[(int64_t)perm[k] * w + c];
+}
+
+__global__ void k_gather_i32(int64_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ in,
+                             int32_t* __restrict__ out) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  out[k] = in[perm[k]];
+}
+
+// flag non-finite entries of a double array
+__global__ void k_check_finite(int64_t n, const double* __restrict__ a, int* status) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  if (!isfinite(a[k])) atomicOr(status, (int)ST_NONFINITE);
+}
+
+static inline unsigned nblk(int64_t w) { return (unsigned)((w + kThreads - 1) / kThreads); }
+
+void launch_kick_drift(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* x, double* v) {
+  if (n) k_kick_drift<<<nblk(n), kThreads, 0, st>>>(n, dt, f, m, x, v);
+}
+void launch_kick(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* v) {
+  if (n) k_kick<<<nblk(n), kThreads, 0, st>>>(n, dt, f, m, v);
+}
+void launch_kinetic(cudaStream_t st, int64_t n, const double* m, const double* v, double* partials, int nb) {
+  k_kinetic<<<nb, kThreads, 0, st>>>(n, m, v, partials);
+}
+void launch_sum_partials(cudaStream_t st, int nb, int width, const double* partials, double* out, double scale) {
+  k_sum_partials<<<1, 32, 0, st>>>(nb, width, partials, out, scale);
+}
+void launch_scatter_rows(cudaStream_t st, int64_t n, int w, const int32_t* perm, const float* in, double* out) {
+  if (n) k_scatter_rows<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out);
+}
+void launch_scatter_rows_d(cudaStream_t st, int64_t n, int w, const int32_t* perm, const double* in, double* out) {
+  if (n) k_scatter_rows_d<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out);
+}
+void launch_gather_rows_d(cudaStream_t st, int64_t n, int w, const int32_t* perm, const double* in, double* out) {
+  if (n) k_gather_rows_d<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out);
+}
+void launch_gather_i32(cudaStream_t st, int64_t n, const int32_t* perm, const int32_t* in, int32_t* out) {
+  if (n) k_gather_i32<<<nblk(n), kThreads, 0, st>>>(n, perm, in, out);
+}
+void launch_check_finite(cudaStream_t st, int64_t n, const double* a, int* status) {
+  if (n) k_check_finite<<<nblk(n), kThreads, 0, st>>>(n, a, status);
+}
+
+}  // namespace ctd

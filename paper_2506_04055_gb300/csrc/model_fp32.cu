@@ -1,0 +1,722 @@
+// model_fp32.cu -- PaiNN-form energy and its hand-written adjoint, all products in FP32 on
+// CUDA cores (the FP32 reference precision of the engine).
+//
+// The potential is a sum of per-atom energies over a cutoff graph (arXiv 2506.04055, Methods,
+// semi-local energy equation) computed by T message-passing layers (Methods, "Graph Neural
+// Networks", message and update equations), instantiated as PaiNN (Methods, "Chosen
+// Architectures"); forces are the negative gradient (Results, "Distributed potential
+// computation", sum-rule equation).  Layer, with edge e = (i <- j), r_e = x_j - x_i + shift:
+//   phi_j  = W2 silu(W1 s_j + b1) + b2                       = [phi_s | phi_vv | phi_vs]
+//   W_e    = (Wf rbf(d_e) + bf) f_c(d_e)                      = [W_s | W_vv | W_vs]
+//   s_i   += sum_e phi_s,j W_s,e
+//   v_i   += sum_e (v_j phi_vv,j W_vv,e + u_e phi_vs,j W_vs,e)
+//   Uv, Vv = U v, V v;  a = A2 silu(A1 [s ; sqrt(|Vv|^2 + eps)] + c1) + c2 = [a_vv | a_sv | a_ss]
+//   v     += a_vv Uv;  s += a_ss + a_sv <Uv, Vv>
+//   U_i    = e_scale (R2 . silu(R1 s_i + d1) + d2)
+//
+// GB300 layout: atoms are cell-sorted so neighbour gathers hit L2; per atom the gathered
+// message table is PHI = [phi_s | psi_0 | psi_1 | psi_2 | phi_vs | phi_vv] with
+// psi_a = v_a * phi_vv pre-multiplied once per atom (5F gathered floats per edge instead of 6F).
+// Edge kernels run one group of F threads per receiver row (thread = feature channel), so the
+// segmented sum over a receiver's CSR row stays in registers: no atomics.  The adjoint of the
+// message step runs sender-side: the row of atom j visits every edge whose sender is j (the
+// list holds both directions and the filter depends only on |r|), gathering the receivers'
+// gradients; per-edge position gradients go to hedge[e] and the forces are assembled from
+// hedge and the reverse-edge index, again without atomics.
+#include "ctd_internal.cuh"
+
+namespace ctd {
+
+// ================================================================================ SIMT GEMM
+// out[m][n] = sum_k A[m][k] B[k][n], A [M][K] (lda), B [K][N] row-major; 64x128 tile,
+// 256 threads, each 8 rows x 4 columns, K staged 32 at a time (A transposed in smem).
+enum Epi { EPI_BIAS = 0, EPI_BIAS_SILU = 1, EPI_ADD = 2, EPI_DSILU = 3 };
+constexpr int GBM = 64, GBN = 128, GBK = 32;
+
+template <int EPI>
+__global__ __launch_bounds__(256) void k_gemm(int64_t M, int N, int K, const float* __restrict__ A, int lda,
+                                              const float* __restrict__ B, const float* __restrict__ bias,
+                                              const float* aux, int ldaux, float* out, int ldo,
+                                              float* __restrict__ out2, int ldo2) {
+  __shared__ __align__(16) float AsT[GBK][GBM + 4];
+  __shared__ __align__(16) float Bs[GBK][GBN];
+  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.y * GBM;
+  const int n0 = blockIdx.x * GBN;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+
+  for (int k0 = 0; k0 < K; k0 += GBK) {
+    // A tile: 64 rows x 32 k, two float4 per thread, stored transposed
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int idx = tid + q * 256;
+      int r = idx >> 3, c4 = (idx & 7) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m0 + r < M && k0 + c4 < K) v = *reinterpret_cast<const float4*>(&A[(m0 + r) * lda + k0 + c4]);
+      AsT[c4 + 0][r] = v.x;
+      AsT[c4 + 1][r] = v.y;
+      AsT[c4 + 2][r] = v.z;
+      AsT[c4 + 3][r] = v.w;
+    }
+    // B tile: 32 k x 128 n, four float4 per thread
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + q * 256;
+      int r = idx >> 5, c4 = (idx & 31) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k0 + r < K && n0 + c4 < N) v = *reinterpret_cast<const float4*>(&B[(int64_t)(k0 + r) * N + n0 + c4]);
+      *reinterpret_cast<float4*>(&Bs[r][c4]) = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < GBK; ++k) {
+      float4 a0 = *reinterpret_cast<const float4*>(&AsT[k][ty * 8]);
+      float4 a1 = *reinterpret_cast<const float4*>(&AsT[k][ty * 8 + 4]);
+      float4 b = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+      float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const int nb = n0 + tx * 4;
+  if (nb >= N) return;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int64_t m = m0 + ty * 8 + i;
+    if (m >= M) break;
+    float r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float x = acc[i][j];
+      if (EPI == EPI_BIAS || EPI == EPI_BIAS_SILU) x += bias ? bias[nb + j] : 0.0f;
+      if (EPI == EPI_ADD) x += aux[m * ldaux + nb + j];
+      if (EPI == EPI_DSILU) x *= dsilu_f(aux[m * ldaux + nb + j]);
+      r[j] = x;
+    }
+    *reinterpret_cast<float4*>(&out[m * ldo + nb]) = make_float4(r[0], r[1], r[2], r[3]);
+    if (EPI == EPI_BIAS_SILU)
+      *reinterpret_cast<float4*>(&out2[m * ldo2 + nb]) =
+          make_float4(silu_f(r[0]), silu_f(r[1]), silu_f(r[2]), silu_f(r[3]));
+  }
+}
+
+template <int EPI>
+static void gemm(cudaStream_t st, int64_t M, int N, int K, const float* A, int lda, const float* B,
+                 const float* bias, const float* aux, int ldaux, float* out, int ldo, float* out2 = nullptr,
+                 int ldo2 = 0) {
+  if (M == 0) return;
+  dim3 grid((N + GBN - 1) / GBN, (unsigned)((M + GBM - 1) / GBM));
+  k_gemm<EPI><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2);
+}
+
+// ================================================================================ node kernels
+__global__ void k_embed(int64_t n, int F, const int32_t* __restrict__ Z, const float* __restrict__ emb,
+                        float* __restrict__ S, float* __restrict__ V) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  S[idx] = emb[(int64_t)Z[i] * F + f];
+  V[i * 3 * F + f] = 0.0f;
+  V[i * 3 * F + F + f] = 0.0f;
+  V[i * 3 * F + 2 * F + f] = 0.0f;
+}
+
+// PHI[i] = [phi_s | v_0 phi_vv | v_1 phi_vv | v_2 phi_vv | phi_vs | phi_vv]
+__global__ void k_phi_pack(int64_t n, int F, const float* __restrict__ P3, const float* __restrict__ V,
+                           float* __restrict__ PHI) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  const float* p = P3 + i * 3 * F;
+  const float* v = V + i * 3 * F;
+  float* o = PHI + i * 6 * F;
+  float pvv = p[F + f];
+  o[f] = p[f];
+  o[F + f] = v[f] * pvv;
+  o[2 * F + f] = v[F + f] * pvv;
+  o[3 * F + f] = v[2 * F + f] * pvv;
+  o[4 * F + f] = p[2 * F + f];
+  o[5 * F + f] = pvv;
+}
+
+// Z = [s^m ; sqrt(sum_a Vv_a^2 + eps)], UV rows (i, a) = [Uv_a | Vv_a]
+__global__ void k_update_pre(int64_t n, int F, float eps, const float* __restrict__ SM,
+                             const float* __restrict__ UV, float* __restrict__ Z) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  const float* uv = UV + i * 3 * 2 * F;
+  float v0 = uv[F + f], v1 = uv[2 * F + F + f], v2 = uv[4 * F + F + f];
+  Z[i * 2 * F + f] = SM[idx];
+  Z[i * 2 * F + F + f] = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
+}
+
+// s' = s^m + a_ss + a_sv <Uv, Vv>,  v'_a = v^m_a + a_vv Uv_a
+__global__ void k_update_post(int64_t n, int F, const float* __restrict__ SM, const float* __restrict__ VM,
+                              const float* __restrict__ UV, const float* __restrict__ AV,
+                              float* __restrict__ Sn, float* __restrict__ Vn) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  const float* uv = UV + i * 6 * F;
+  const float* a = AV + i * 3 * F;
+  float sp = 0.0f;
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    float u = uv[al * 2 * F + f], v = uv[al * 2 * F + F + f];
+    sp += u * v;
+    Vn[i * 3 * F + al * F + f] = VM[i * 3 * F + al * F + f] + a[f] * u;
+  }
+  Sn[idx] = SM[idx] + a[2 * F + f] + a[F + f] * sp;
+}
+
+// Backward of the update elementwise part: given gs' (GS), gv' (GV):
+//   g_a = [sum_a gv'_a Uv_a | gs' <Uv,Vv> | gs'],  gUv_a = gv'_a a_vv + gs' a_sv Vv_a,
+//   gVv_a = gs' a_sv Uv_a (the |Vv| term is added after the A1 backward)
+__global__ void k_update_bwd_pre(int64_t n, int F, const float* __restrict__ GS, const float* __restrict__ GV,
+                                 const float* __restrict__ UV, const float* __restrict__ AV,
+                                 float* __restrict__ GA, float* __restrict__ GUV) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  const float* uv = UV + i * 6 * F;
+  const float* a = AV + i * 3 * F;
+  float gs = GS[idx], asv = a[F + f], avv = a[f];
+  float gsp = gs * asv, sp = 0.0f, gavv = 0.0f;
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    float u = uv[al * 2 * F + f], v = uv[al * 2 * F + F + f];
+    float gv = GV[i * 3 * F + al * F + f];
+    sp += u * v;
+    gavv += gv * u;
+    GUV[i * 6 * F + al * 2 * F + f] = gv * avv + gsp * v;
+    GUV[i * 6 * F + al * 2 * F + F + f] = gsp * u;
+  }
+  GA[i * 3 * F + f] = gavv;
+  GA[i * 3 * F + F + f] = gs * sp;
+  GA[i * 3 * F + 2 * F + f] = gs;
+}
+
+// gz = [gz_s | gz_n] (grad of [s^m ; |Vv|]):  gsm = gs' + gz_s;  gVv_a += gz_n Vv_a / |Vv|
+__global__ void k_update_bwd_mid(int64_t n, int F, float eps, const float* __restrict__ GS,
+                                 const float* __restrict__ GZ, const float* __restrict__ UV,
+                                 float* __restrict__ Gsm, float* __restrict__ GUV) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  const float* uv = UV + i * 6 * F;
+  float v0 = uv[F + f], v1 = uv[3 * F + f], v2 = uv[5 * F + f];
+  float nv = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
+  float g = GZ[i * 2 * F + F + f] / nv;
+  Gsm[idx] = GS[idx] + GZ[i * 2 * F + f];
+  GUV[i * 6 * F + F + f] += g * v0;
+  GUV[i * 6 * F + 3 * F + f] += g * v1;
+  GUV[i * 6 * F + 5 * F + f] += g * v2;
+}
+
+// Backward of PHI packing: gphi_vv = sum_a gpsi_a v_a, gv_a = gvm_a + gpsi_a phi_vv;
+// GP3 = [gphi_s | gphi_vv | gphi_vs]
+__global__ void k_phi_bwd_pre(int64_t n, int F, const float* __restrict__ GPHI, const float* __restrict__ PHI,
+                              const float* __restrict__ V, const float* __restrict__ Gvm,
+                              float* __restrict__ GP3, float* __restrict__ GVn) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  const float* g = GPHI + i * 5 * F;
+  float pvv = PHI[i * 6 * F + 5 * F + f];
+  float gpvv = 0.0f;
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    float gpsi = g[(1 + al) * F + f];
+    gpvv += gpsi * V[i * 3 * F + al * F + f];
+    GVn[i * 3 * F + al * F + f] = Gvm[i * 3 * F + al * F + f] + gpsi * pvv;
+  }
+  GP3[i * 3 * F + f] = g[f];
+  GP3[i * 3 * F + F + f] = gpvv;
+  GP3[i * 3 * F + 2 * F + f] = g[4 * F + f];
+}
+
+// ================================================================================ edge kernels
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Forward message: one group of F threads per receiver row.  Edges of the row are staged
+// F at a time (geometry, f_c, radial basis) in shared memory; thread f then accumulates
+// channel f of s and of the three components of v over the staged edges.
+template <int KP>
+__global__ __launch_bounds__(256) void k_edge_fwd(int64_t n, int F, int K, float rc,
+                                                  const int32_t* __restrict__ arow, const int32_t* __restrict__ acol,
+                                                  const float4* __restrict__ ar, const float* __restrict__ PHI,
+                                                  const float* __restrict__ S, const float* __restrict__ V,
+                                                  const float* __restrict__ Wf, const float* __restrict__ bf,
+                                                  float* __restrict__ SM, float* __restrict__ VM) {
+  extern __shared__ __align__(16) float sm[];
+  const int G = blockDim.x / F;                 // groups per block
+  const int g = threadIdx.x / F, f = threadIdx.x % F;
+  float* rbs = sm + (size_t)g * F * KP;                                          // [F edges][KP]
+  float4* geo = reinterpret_cast<float4*>(sm + (size_t)G * F * KP) + (size_t)g * F;  // (u, f_c)
+  int* js = reinterpret_cast<int*>(sm + (size_t)G * F * (KP + 4)) + (size_t)g * F;
+
+  float w_s[KP], w_vv[KP], w_vs[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    w_s[k] = Wf[(size_t)f * KP + k];
+    w_vv[k] = Wf[(size_t)(F + f) * KP + k];
+    w_vs[k] = Wf[(size_t)(2 * F + f) * KP + k];
+  }
+  const float b_s = bf[f], b_vv = bf[F + f], b_vs = bf[2 * F + f];
+  const float inv_rc = 1.0f / rc, sig = rc / (float)(K - 1), inv2s2 = 1.0f / (2.0f * sig * sig);
+  const int64_t ngroups = (int64_t)gridDim.x * G;
+
+  for (int64_t i = (int64_t)blockIdx.x * G + g; i < n; i += ngroups) {
+    const int a0 = arow[i], a1 = arow[i + 1];
+    float as = 0.f, av0 = 0.f, av1 = 0.f, av2 = 0.f;
+    for (int c0 = a0; c0 < a1; c0 += F) {
+      const int cnt = min(F, a1 - c0);
+      group_sync(1 + g, F);
+      if (f < cnt) {
+        float4 r = ar[c0 + f];
+        float d = r.w, id = 1.0f / d;
+        float fc = 0.5f * (cospif(d * inv_rc) + 1.0f);
+        geo[f] = make_float4(r.x * id, r.y * id, r.z * id, fc);
+        js[f] = acol[c0 + f];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+          float mu = (float)k * sig, t = d - mu;
+          rbs[f * KP + k] = k < K ? expf(-t * t * inv2s2) : 0.0f;
+        }
+      }
+      group_sync(1 + g, F);
+      for (int t = 0; t < cnt; ++t) {
+        const float4 ge = geo[t];
+        const float* rb = rbs + t * KP;
+        float ws = b_s, wvv = b_vv, wvs = b_vs;
+#pragma unroll
+        for (int k = 0; k < KP; k += 4) {
+          float4 q = *reinterpret_cast<const float4*>(rb + k);
+          ws = fmaf(w_s[k], q.x, ws); ws = fmaf(w_s[k + 1], q.y, ws);
+          ws = fmaf(w_s[k + 2], q.z, ws); ws = fmaf(w_s[k + 3], q.w, ws);
+          wvv = fmaf(w_vv[k], q.x, wvv); wvv = fmaf(w_vv[k + 1], q.y, wvv);
+          wvv = fmaf(w_vv[k + 2], q.z, wvv); wvv = fmaf(w_vv[k + 3], q.w, wvv);
+          wvs = fmaf(w_vs[k], q.x, wvs); wvs = fmaf(w_vs[k + 1], q.y, wvs);
+          wvs = fmaf(w_vs[k + 2], q.z, wvs); wvs = fmaf(w_vs[k + 3], q.w, wvs);
+        }
+        const float* p = PHI + (int64_t)js[t] * 6 * F;
+        const float ps = p[f], y0 = p[F + f], y1 = p[2 * F + f], y2 = p[3 * F + f], pvs = p[4 * F + f];
+        ws *= ge.w; wvv *= ge.w; wvs *= ge.w;
+        as = fmaf(ps, ws, as);
+        const float tvs = pvs * wvs;
+        av0 = fmaf(y0, wvv, fmaf(ge.x, tvs, av0));
+        av1 = fmaf(y1, wvv, fmaf(ge.y, tvs, av1));
+        av2 = fmaf(y2, wvv, fmaf(ge.z, tvs, av2));
+      }
+    }
+    SM[i * F + f] = S[i * F + f] + as;
+    VM[i * 3 * F + f] = V[i * 3 * F + f] + av0;
+    VM[i * 3 * F + F + f] = V[i * 3 * F + F + f] + av1;
+    VM[i * 3 * F + 2 * F + f] = V[i * 3 * F + 2 * F + f] + av2;
+  }
+}
+
+// Reduce four per-thread values over a warp; lane 8*q ends up with the sum of value q.
+__device__ __forceinline__ float warp_reduce4(float v0, float v1, float v2, float v3, int lane) {
+  // xor 16: lanes < 16 keep (v0, v1), lanes >= 16 keep (v2, v3)
+  bool hi = lane & 16;
+  float s0 = hi ? v0 : v2, s1 = hi ? v1 : v3;
+  float k0 = hi ? v2 : v0, k1 = hi ? v3 : v1;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  // xor 8: lanes with bit 3 clear keep k0, set keep k1
+  bool b8 = lane & 8;
+  float s = b8 ? k0 : k1, k = b8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, s, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;   // lane 0: v0, lane 8: v1, lane 16: v2, lane 24: v3
+}
+
+// Adjoint of the message step, sender-side.  Row j holds edges e' = (j <- i); its reverse
+// (i <- j) carried phi_j, v_j into receiver i with direction u_rev = -u_e'.  Thread f gathers
+// (gsm_i, gvm_i) and accumulates d/dphi_s,j, d/dpsi_j,a, d/dphi_vs,j over the row; per edge the
+// partial d/dd and d/du_rev are reduced over the F channels and turned into
+// hedge[e'] = dU/dr_(i<-j).
+template <int KP>
+__global__ __launch_bounds__(256) void k_edge_bwd(int64_t n, int F, int K, float rc, int accumulate,
+                                                  const int32_t* __restrict__ arow, const int32_t* __restrict__ acol,
+                                                  const float4* __restrict__ ar, const float* __restrict__ PHI,
+                                                  const float* __restrict__ Gsm, const float* __restrict__ Gvm,
+                                                  const float* __restrict__ Wf, const float* __restrict__ bf,
+                                                  float* __restrict__ GPHI, float4* __restrict__ hedge) {
+  extern __shared__ __align__(16) float sm[];
+  const int G = blockDim.x / F;
+  const int g = threadIdx.x / F, f = threadIdx.x % F, lane = threadIdx.x & 31, wig = f >> 5;
+  const int NW = F / 32;
+  float* rbs = sm + (size_t)g * F * (2 * KP + 8 + 4 * NW);     // [F][KP] rbf, [F][KP] drbf
+  float* drbs = rbs + F * KP;
+  float4* geo = reinterpret_cast<float4*>(drbs + F * KP);       // (u, d)
+  float4* gfc = geo + F;                                        // (f_c, f_c', -, -)
+  float* red = reinterpret_cast<float*>(gfc + F);               // [F edges][NW][4]
+  int* js = reinterpret_cast<int*>(sm + (size_t)G * F * (2 * KP + 8 + 4 * NW)) + (size_t)g * F;
+
+  float w_s[KP], w_vv[KP], w_vs[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    w_s[k] = Wf[(size_t)f * KP + k];
+    w_vv[k] = Wf[(size_t)(F + f) * KP + k];
+    w_vs[k] = Wf[(size_t)(2 * F + f) * KP + k];
+  }
+  const float b_s = bf[f], b_vv = bf[F + f], b_vs = bf[2 * F + f];
+  const float inv_rc = 1.0f / rc, sig = rc / (float)(K - 1), inv2s2 = 1.0f / (2.0f * sig * sig);
+  const float inv_s2 = 1.0f / (sig * sig);
+  const int64_t ngroups = (int64_t)gridDim.x * G;
+
+  for (int64_t j = (int64_t)blockIdx.x * G + g; j < n; j += ngroups) {
+    const float* pj = PHI + j * 6 * F;
+    const float ps = pj[f], y0 = pj[F + f], y1 = pj[2 * F + f], y2 = pj[3 * F + f], pvs = pj[4 * F + f];
+    float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
+    const int a0 = arow[j], a1 = arow[j + 1];
+    for (int c0 = a0; c0 < a1; c0 += F) {
+      const int cnt = min(F, a1 - c0);
+      group_sync(1 + g, F);
+      if (f < cnt) {
+        float4 r = ar[c0 + f];
+        float d = r.w, id = 1.0f / d;
+        float fc = 0.5f * (cospif(d * inv_rc) + 1.0f);
+        float dfc = -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc);
+        geo[f] = make_float4(r.x * id, r.y * id, r.z * id, d);
+        gfc[f] = make_float4(fc, dfc, 0.f, 0.f);
+        js[f] = acol[c0 + f];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+          float t = d - (float)k * sig;
+          float rb = k < K ? expf(-t * t * inv2s2) : 0.0f;
+          rbs[f * KP + k] = rb;
+          drbs[f * KP + k] = -rb * t * inv_s2;
+        }
+      }
+      group_sync(1 + g, F);
+      for (int t = 0; t < cnt; ++t) {
+        const float4 ge = geo[t];
+        const float4 fcv = gfc[t];
+        const float* rb = rbs + t * KP;
+        const float* drb = drbs + t * KP;
+        float ws = b_s, wvv = b_vv, wvs = b_vs, dws = 0.f, dwvv = 0.f, dwvs = 0.f;
+#pragma unroll
+        for (int k = 0; k < KP; k += 4) {
+          float4 q = *reinterpret_cast<const float4*>(rb + k);
+          float4 dq = *reinterpret_cast<const float4*>(drb + k);
+          float qa[4] = {q.x, q.y, q.z, q.w}, da[4] = {dq.x, dq.y, dq.z, dq.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            ws = fmaf(w_s[k + u], qa[u], ws);
+            wvv = fmaf(w_vv[k + u], qa[u], wvv);
+            wvs = fmaf(w_vs[k + u], qa[u], wvs);
+            dws = fmaf(w_s[k + u], da[u], dws);
+            dwvv = fmaf(w_vv[k + u], da[u], dwvv);
+            dwvs = fmaf(w_vs[k + u], da[u], dwvs);
+          }
+        }
+        const int64_t i = js[t];
+        const float gs = Gsm[i * F + f];
+        const float gv0 = Gvm[i * 3 * F + f], gv1 = Gvm[i * 3 * F + F + f], gv2 = Gvm[i * 3 * F + 2 * F + f];
+        const float fc = fcv.x, dfc = fcv.y;
+        const float Ws = ws * fc, Wvv = wvv * fc, Wvs = wvs * fc;
+        gps = fmaf(gs, Ws, gps);
+        gy0 = fmaf(gv0, Wvv, gy0);
+        gy1 = fmaf(gv1, Wvv, gy1);
+        gy2 = fmaf(gv2, Wvv, gy2);
+        // u_rev = -u
+        const float q = -(gv0 * ge.x + gv1 * ge.y + gv2 * ge.z);
+        gpvs = fmaf(q, Wvs, gpvs);
+        const float gWs = gs * ps, gWvv = gv0 * y0 + gv1 * y1 + gv2 * y2, gWvs = q * pvs;
+        float pd = fc * (gWs * dws + gWvv * dwvv + gWvs * dwvs) + dfc * (gWs * ws + gWvv * wvv + gWvs * wvs);
+        const float tv = pvs * Wvs;
+        float r = warp_reduce4(pd, gv0 * tv, gv1 * tv, gv2 * tv, lane);
+        if ((lane & 7) == 0) red[(t * NW + wig) * 4 + (lane >> 3)] = r;
+      }
+      group_sync(1 + g, F);
+      if (f < cnt) {
+        float pd = 0.f, gu0 = 0.f, gu1 = 0.f, gu2 = 0.f;
+        for (int w = 0; w < NW; ++w) {
+          const float* rr = red + (f * NW + w) * 4;
+          pd += rr[0]; gu0 += rr[1]; gu1 += rr[2]; gu2 += rr[3];
+        }
+        const float4 ge = geo[f];
+        const float ux = -ge.x, uy = -ge.y, uz = -ge.z, id = 1.0f / ge.w;
+        const float gdu = gu0 * ux + gu1 * uy + gu2 * uz;
+        float4 h = make_float4(pd * ux + (gu0 - gdu * ux) * id, pd * uy + (gu1 - gdu * uy) * id,
+                               pd * uz + (gu2 - gdu * uz) * id, 0.f);
+        if (accumulate) {
+          float4 o = hedge[c0 + f];
+          h.x += o.x; h.y += o.y; h.z += o.z;
+        }
+        hedge[c0 + f] = h;
+      }
+    }
+    float* o = GPHI + j * 5 * F;
+    o[f] = gps;
+    o[F + f] = gy0;
+    o[2 * F + f] = gy1;
+    o[3 * F + f] = gy2;
+    o[4 * F + f] = gpvs;
+  }
+}
+
+// ================================================================================ readout, forces
+// h3 = R1 s + d1 (done by the GEMM); U_i = e_scale (R2 . silu(h3) + d2);
+// G3 = e_scale R2 * silu'(h3) (seed of the backward pass); per-block FP64 energy partials.
+__global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restrict__ H3,
+                          const float* __restrict__ R2, const float* __restrict__ d2,
+                          float* __restrict__ G3, float* __restrict__ e_atom, double* __restrict__ partials) {
+  __shared__ double sbuf[kThreads / 32];
+  double acc = 0.0, comp = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float e = d2[0];
+    for (int k = 0; k < Fh; ++k) {
+      float h = H3[i * Fh + k];
+      e = fmaf(R2[k], silu_f(h), e);
+      if (G3) G3[i * Fh + k] = e_scale * R2[k] * dsilu_f(h);
+    }
+    e *= e_scale;
+    if (e_atom) e_atom[i] = e;
+    double x = (double)e, t = acc + x;   // Neumaier
+    comp += fabs(acc) >= fabs(x) ? (acc - t) + x : (x - t) + acc;
+    acc = t;
+  }
+  double v = acc + comp;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += sbuf[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+// F_i = sum_{e in row i} (hedge[rev e] - hedge[e]);  virial partials = sum_e r_e (x) hedge[e]
+// (= -sum_e r_e (x) dU/dr_e over all edges).  One warp per row, FP64 per-warp accumulation.
+__global__ void k_forces(int64_t n, const int32_t* __restrict__ arow, const float4* __restrict__ ar,
+                         const int32_t* __restrict__ arev, const float4* __restrict__ hedge,
+                         float* __restrict__ force, double* __restrict__ vpart, int* status) {
+  __shared__ double sv[kThreads / 32][9];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double vacc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
+  for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + w; i < n; i += nw) {
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int a = arow[i] + lane; a < arow[i + 1]; a += 32) {
+      const int ra = arev[a];
+      const float4 h = hedge[a], r = ar[a];
+      float4 hr = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ra >= 0) hr = hedge[ra];
+      else atomicOr(status, (int)ST_REV_MISSING);
+      fx += hr.x - h.x; fy += hr.y - h.y; fz += hr.z - h.z;
+      const float rr[3] = {r.x, r.y, r.z}, hh[3] = {h.x, h.y, h.z};
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[3 * p + q] = fmaf(rr[p], hh[q], v[3 * p + q]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      fx += __shfl_xor_sync(0xffffffffu, fx, o);
+      fy += __shfl_xor_sync(0xffffffffu, fy, o);
+      fz += __shfl_xor_sync(0xffffffffu, fz, o);
+#pragma unroll
+      for (int p = 0; p < 9; ++p) v[p] += __shfl_xor_sync(0xffffffffu, v[p], o);
+    }
+    if (lane == 0) {
+      force[3 * i] = fx; force[3 * i + 1] = fy; force[3 * i + 2] = fz;
+#pragma unroll
+      for (int p = 0; p < 9; ++p) vacc[p] += (double)v[p];
+    }
+  }
+  if (lane == 0)
+    for (int p = 0; p < 9; ++p) sv[w][p] = vacc[p];
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double s = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) s += sv[q][threadIdx.x];
+    vpart[(int64_t)blockIdx.x * 9 + threadIdx.x] = s;
+  }
+}
+
+// ================================================================================ driver
+static inline unsigned blocks_for(int64_t work) { return (unsigned)((work + kThreads - 1) / kThreads); }
+
+template <int KP>
+static void edge_fwd_kp(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow,
+                        const int32_t* acol, const float4* ar, const float* PHI, const float* S, const float* V,
+                        float* SM, float* VM) {
+  const int F = m.F, G = kThreads / F;
+  size_t smem = (size_t)G * F * (KP + 4) * sizeof(float) + (size_t)G * F * sizeof(int);
+  int64_t blocks = (n + G - 1) / G;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_edge_fwd<KP><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, arow, acol, ar, PHI, S, V,
+                                                           m.L[t].Wf, m.L[t].bf, SM, VM);
+}
+
+template <int KP>
+static void edge_bwd_kp(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
+                        const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm,
+                        const float* Gvm, float* GPHI, float4* hedge) {
+  const int F = m.F, G = kThreads / F, NW = F / 32;
+  size_t smem = (size_t)G * F * (2 * KP + 8 + 4 * NW) * sizeof(float) + (size_t)G * F * sizeof(int);
+  int64_t blocks = (n + G - 1) / G;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_edge_bwd<KP><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, accumulate, arow, acol, ar, PHI,
+                                                           Gsm, Gvm, m.L[t].Wf, m.L[t].bf, GPHI, hedge);
+}
+
+#define CTD_KP_DISPATCH(KPV, CALL) \
+  switch (KPV) {                   \
+    case 4: CALL(4); break;        \
+    case 8: CALL(8); break;        \
+    case 12: CALL(12); break;      \
+    case 16: CALL(16); break;      \
+    case 20: CALL(20); break;      \
+    case 24: CALL(24); break;      \
+    case 28: CALL(28); break;      \
+    default: CALL(32); break;      \
+  }
+
+void edge_smem_setup() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+#define CTD_SET_SMEM(K_)                                                                              \
+  cudaFuncSetAttribute(k_edge_fwd<K_>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);     \
+  cudaFuncSetAttribute(k_edge_bwd<K_>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  CTD_SET_SMEM(4) CTD_SET_SMEM(8) CTD_SET_SMEM(12) CTD_SET_SMEM(16) CTD_SET_SMEM(20) CTD_SET_SMEM(24)
+  CTD_SET_SMEM(28) CTD_SET_SMEM(32)
+#undef CTD_SET_SMEM
+}
+
+// Buffers (all float, sized by the caller; see api.cu for the list and shapes).
+enum BufId {
+  B_S0 = 0,                        // S[t] for t = 0..T  -> ids B_S0 + t
+  B_V0 = B_S0 + kMaxT + 1,         // V[t] for t = 0..T
+  B_PHI0 = B_V0 + kMaxT + 1,       // [n][6F] per layer
+  B_H10 = B_PHI0 + kMaxT,          // [n][F]
+  B_SM0 = B_H10 + kMaxT,           // [n][F]
+  B_VM0 = B_SM0 + kMaxT,           // [n][3F]
+  B_UV0 = B_VM0 + kMaxT,           // [3n][2F]
+  B_H20 = B_UV0 + kMaxT,           // [n][F]
+  B_AV0 = B_H20 + kMaxT,           // [n][3F]
+  B_T1 = B_AV0 + kMaxT,            // [n][3F] scratch
+  B_T2,                            // [n][3F] scratch
+  B_T3,                            // [3n][2F] scratch
+  B_GS, B_GV, B_GSM, B_GVM,        // [n][F], [n][3F], [n][F], [n][3F]
+  B_GPHI,                          // [n][5F]
+  B_H3, B_G3,                      // [n][F/2]
+  B_COUNT
+};
+
+int model_buffer_count() { return B_COUNT; }
+
+// floats per atom of buffer id b (0 if unused for this T)
+int64_t model_buffer_floats_per_atom(int b, int F, int T) {
+  auto layer = [&](int base, int cnt) { return b >= base && b < base + cnt; };
+  if (layer(B_S0, T + 1)) return F;
+  if (layer(B_V0, T + 1)) return 3 * F;
+  if (layer(B_PHI0, T)) return 6 * F;
+  if (layer(B_H10, T)) return F;
+  if (layer(B_SM0, T)) return F;
+  if (layer(B_VM0, T)) return 3 * F;
+  if (layer(B_UV0, T)) return 6 * F;
+  if (layer(B_H20, T)) return F;
+  if (layer(B_AV0, T)) return 3 * F;
+  switch (b) {
+    case B_T1: case B_T2: return 3 * F;
+    case B_T3: return 6 * F;
+    case B_GS: case B_GSM: return F;
+    case B_GV: case B_GVM: return 3 * F;
+    case B_GPHI: return 5 * F;
+    case B_H3: case B_G3: return F / 2;
+    default: return 0;
+  }
+}
+
+void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
+                                 const int32_t* arow, const int32_t* acol, const float4* ar,
+                                 const int32_t* arev, float* const* B, bool need_grad,
+                                 double* energy_partials, int n_energy_partials, float4* hedge,
+                                 float* force_s, double* virial_partials, int n_virial_partials,
+                                 float* e_atom, int* status) {
+  edge_smem_setup();
+  const int F = m.F, T = m.T, Fh = F / 2;
+  const unsigned nb = blocks_for(n * F);
+  if (n > 0) k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0]);
+  for (int t = 0; t < T; ++t) {
+    const LayerW& L = m.L[t];
+    float *S = B[B_S0 + t], *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
+    float *SM = B[B_SM0 + t], *VM = B[B_VM0 + t], *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
+    float *T1 = B[B_T1], *T2 = B[B_T2];
+    // phi = W2 silu(W1 s + b1) + b2
+    gemm<EPI_BIAS_SILU>(st, n, F, F, S, F, L.W1t, L.b1, nullptr, 0, H1, F, T1, F);
+    gemm<EPI_BIAS>(st, n, 3 * F, F, T1, F, L.W2t, L.b2, nullptr, 0, T2, 3 * F);
+    if (n > 0) k_phi_pack<<<nb, kThreads, 0, st>>>(n, F, T2, V, PHI);
+    // message
+#define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM)
+    if (n > 0) { CTD_KP_DISPATCH(m.KP, CTD_FWD) }
+#undef CTD_FWD
+    // update
+    gemm<EPI_BIAS>(st, 3 * n, 2 * F, F, VM, F, L.UVt, nullptr, nullptr, 0, UV, 2 * F);
+    if (n > 0) k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1);
+    gemm<EPI_BIAS_SILU>(st, n, F, 2 * F, T1, 2 * F, L.A1t, L.c1, nullptr, 0, H2, F, T2, F);
+    gemm<EPI_BIAS>(st, n, 3 * F, F, T2, F, L.A2t, L.c2, nullptr, 0, AV, 3 * F);
+    if (n > 0) k_update_post<<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1]);
+  }
+  // readout
+  gemm<EPI_BIAS>(st, n, Fh, F, B[B_S0 + T], F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
+  k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2,
+                                                    need_grad ? B[B_G3] : nullptr, e_atom, energy_partials);
+  if (!need_grad) return;
+  // dU/ds^T = G3 R1
+  gemm<EPI_BIAS>(st, n, F, Fh, B[B_G3], Fh, m.R1, nullptr, nullptr, 0, B[B_GS], F);
+  if (n > 0) cudaMemsetAsync(B[B_GV], 0, sizeof(float) * (size_t)n * 3 * F, st);
+  for (int t = T - 1; t >= 0; --t) {
+    const LayerW& L = m.L[t];
+    float *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
+    float *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
+    float *T1 = B[B_T1], *T2 = B[B_T2], *T3 = B[B_T3];
+    float *GS = B[B_GS], *GV = B[B_GV], *GSM = B[B_GSM], *GVM = B[B_GVM], *GPHI = B[B_GPHI];
+    // update backward
+    if (n > 0) k_update_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, T1, T3);
+    gemm<EPI_DSILU>(st, n, F, 3 * F, T1, 3 * F, L.A2, nullptr, H2, F, T2, F);          // gh2
+    gemm<EPI_BIAS>(st, n, 2 * F, F, T2, F, L.A1, nullptr, nullptr, 0, T1, 2 * F);       // gz
+    if (n > 0) k_update_bwd_mid<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, GSM, T3);
+    gemm<EPI_ADD>(st, 3 * n, F, 2 * F, T3, 2 * F, L.UV, nullptr, GV, F, GVM, F);         // gvm
+    // message backward
+#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge)
+    if (n > 0) { CTD_KP_DISPATCH(m.KP, CTD_BWD) }
+#undef CTD_BWD
+    // phi backward -> gradients w.r.t. the layer input (s_t, v_t)
+    if (n > 0) k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV);
+    gemm<EPI_DSILU>(st, n, F, 3 * F, T2, 3 * F, L.W2, nullptr, H1, F, T1, F);          // gh1
+    gemm<EPI_ADD>(st, n, F, F, T1, F, L.W1, nullptr, GSM, F, GS, F);                    // gs
+  }
+  k_forces<<<n_virial_partials, kThreads, 0, st>>>(n, arow, ar, arev, hedge, force_s, virial_partials, status);
+}
+
+}  // namespace ctd

@@ -1,0 +1,80 @@
+"""CPU checks of the C-ABI boundary: the library builds for sm_103a, loads, and exports every
+entry point include/painn.h declares; argument validation that needs no GPU; the parameter
+blob layout the header documents."""
+import os
+import re
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "painn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ctd_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2506_04055_gb300 as eng
+    eng.build()
+    return eng.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2506_04055_gb300 import _lib
+    declared = _declared()
+    assert declared == sorted(_lib.EXPORTS)
+    so = os.path.join(ROOT, "paper_2506_04055_gb300", "libctd_painn.so")
+    syms = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (ctd_[a-z_]+)\b", syms))
+    for name in declared:
+        assert name in exported, name
+        getattr(lib, name)
+
+
+def test_library_targets_sm103a():
+    so = os.path.join(ROOT, "paper_2506_04055_gb300", "libctd_painn.so")
+    out = subprocess.run(["cuobjdump", "--list-elf", so], capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_invalid_model_description_rejected(lib):
+    from paper_2506_04055_gb300 import _lib
+    for desc in (_lib.ctd_model_desc(48, 20, 3, 2, 5.0, 0), _lib.ctd_model_desc(64, 40, 3, 2, 5.0, 0),
+                 _lib.ctd_model_desc(64, 20, 3, 2, -1.0, 0), _lib.ctd_model_desc(64, 20, 3, 2, 5.0, 7)):
+        with pytest.raises(_lib.CtdError) as ei:
+            _lib.ctd_create(desc)
+        assert ei.value.code == _lib.CTD_ERR_INVALID_ARG
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2506_04055_gb300 import _lib
+    with pytest.raises(_lib.CtdError) as ei:
+        _lib.ctd_create(_lib.ctd_model_desc(64, 20, 3, 2, 5.0, 0))
+    assert ei.value.code == _lib.CTD_ERR_CUDA
+
+
+def test_param_blob_layout():
+    F, K, T, S = 64, 20, 3, 2
+    blob = syn.params_blob(F, K, T, S, rc=5.0, e_scale=2.0, seed=0)
+    assert blob[:8] == b"CTDPAINN"
+    ver, f, k, t, s, _ = struct.unpack("<iiiiii", blob[8:32])
+    rc, eps, esc, nval = struct.unpack("<dddq", blob[32:64])
+    assert (ver, f, k, t, s, rc, esc) == (1, F, K, T, S, 5.0, 2.0)
+    per = F * F + F + 3 * F * F + 3 * F + 3 * F * K + 3 * F + 2 * F * F + 2 * F * F + F + 3 * F * F + 3 * F
+    assert nval == S * F + T * per + (F // 2) * F + F // 2 + F // 2 + 1 == (len(blob) - 64) // 8
+    vals = np.frombuffer(blob[64:], np.float64)
+    P = syn.unpack_params(vals.copy(), F, K, T, S)
+    bound = np.sqrt(6.0 / (F + F))
+    assert np.abs(P["W1_0"]).max() <= bound and np.abs(P["W1_0"]).max() > 0.9 * bound
+    assert np.all(P["b1_0"] == 0)
