@@ -1,0 +1,368 @@
+"""Benchmark: atom-steps/s of NVE molecular dynamics driven by the PaiNN-form potential.
+
+One step = velocity-Verlet half kick + drift, per-step prune of the Verlet list (rebuild when
+an atom moved more than skin/2), energy + forces + virial (forward and adjoint kernels), second
+half kick.  Workload (default): single-species fcc crystal, a = 4.05 A, 63x63x63 cells
+(1,000,188 atoms), Gaussian jitter 0.05 A, cutoff 5 A, skin 1 A, F = 128, 3 layers, 20 radial
+basis functions, Xavier-uniform weights from seed 0; synthetic inputs (no datasets/weights).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s (E+F) at 1M atoms, BF16 vs FP32 at stated force RMSE; p50/p99"
+FCC_CELLS = 63
+F, K, T, S = 128, 20, 3, 1
+RC, SKIN, DT, TEMP = 5.0, 1.0, 1.0, 300.0
+
+# algorithmic FLOPs per (active edge, feature channel) of the two edge kernels:
+# message: filter 3K FMA + f_c scaling + s / v message terms; adjoint: filter and its radial
+# derivative (2 x 3K FMA) + message adjoint terms + per-edge gradient partials.
+EDGE_FWD_FLOP_PER_EF = 6 * K + 18
+EDGE_BWD_FLOP_PER_EF = 12 * K + 45
+FP32_LANES_PER_SM, N_SM = 128, 152
+
+
+def workload_desc(cells):
+    n = 4 * cells ** 3
+    return (f"fcc {cells}x{cells}x{cells} cells ({n:,} atoms), a=4.05 A, jitter 0.05 A, 1 species; "
+            f"PaiNN F={F}, T={T}, K={K} Gaussians, rc={RC} A, skin={SKIN} A; NVE velocity Verlet "
+            f"dt={DT} fs from {TEMP:.0f} K")
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(name)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2506_04055_gb300", "csrc", rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec.get("bytes_per_launch") if h == rec.get("source_sha") else None
+
+
+def cpu_baseline(seconds_hint=True):
+    """The FP64 oracle as it stands, one energy + forces + virial evaluation (with its own
+    linked-cell pair search) of the 4,000-atom 10x10x10 fcc sub-cell, F=128, T=3."""
+    import oracle
+    import synthetic as syn
+    oracle.build()
+    sy = syn.fcc(10, 10, 10, a=4.05, jitter=0.05, seed=0)
+    vals = syn.xavier_params(F, K, T, S, seed=0)
+    t0 = time.perf_counter()
+    oracle.painn(vals, F, K, T, S, sy.species, sy.positions, sy.cell)
+    dt = time.perf_counter() - t0
+    return {"value": sy.n / dt, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"one E+F+W evaluation of the {sy.n}-atom 10x10x10 fcc sub-cell "
+                      f"(single thread, {dt:.1f} s, pair search included, no integration)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, same metric, one bounded sample per
+    step (E+F+W of a 500-atom 5x5x5 fcc sub-cell of the same crystal and model)."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle
+    import synthetic as syn
+    oracle.build()
+    sy = syn.fcc(5, 5, 5, a=4.05, jitter=0.05, seed=0)
+    vals = syn.xavier_params(F, K, T, S, seed=0)
+    for _ in range(args.warmup):
+        oracle.painn(vals, F, K, T, S, sy.species, sy.positions, sy.cell)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.painn(vals, F, K, T, S, sy.species, sy.positions, sy.cell)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sy.n * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "atom-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(FCC_CELLS), "sample": "5x5x5 fcc sub-cell (500 atoms) per step",
+                       "parallelism": "single process, host cores"},
+            "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"E+F+W of the 500-atom 5x5x5 fcc sub-cell per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2506_04055_gb300 as eng
+    import synthetic as syn
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        eng.build()
+    if dist:
+        dist.barrier()
+    eng.load()
+
+    cells = args.cells
+    sy = syn.fcc(cells, cells, cells, a=4.05, jitter=0.05, seed=rank)
+    v0 = syn.maxwell_boltzmann(sy.masses, TEMP, seed=rank)
+    blob = syn.params_blob(F, K, T, S, rc=RC, seed=0)
+    stream = torch.cuda.current_stream()
+    results = {}
+    precisions = ["fp32"] if args.precision == "fp32" else (["bf16"] if args.precision == "bf16" else ["fp32", "bf16"])
+    for prec in precisions:
+        try:
+            pot = eng.Potential(F, K=K, T=T, n_species=S, rc=RC, precision=prec, params=blob,
+                                stream=stream.cuda_stream)
+        except eng.CtdError as e:
+            results[prec] = {"error": str(e)}
+            continue
+        pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=SKIN)
+        for _ in range(args.warmup):
+            pot.md_run(1, DT)
+        torch.cuda.synchronize()
+        pot.profile(True)
+        pot.profile_read(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        rebuilds = 0
+        with ClockSampler(local) as clk:
+            t_start = torch.cuda.Event(enable_timing=True)
+            t_end = torch.cuda.Event(enable_timing=True)
+            t_start.record(stream)
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                _, _, nreb = pot.md_run(1, DT)
+                rebuilds += nreb
+                ev[k][1].record(stream)
+            t_end.record(stream)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        total_ms = t_start.elapsed_time(t_end)
+        step_ms = sorted(a.elapsed_time(b) for a, b in ev)
+        prof = pot.profile_read(reset=True)
+        pot.profile(False)
+        ep, ek, _ = pot.md_run(0, DT)
+        # e2e: the public C-ABI call with host (pinned) buffers, copies inside the timed region
+        n = sy.n
+        x_pin = torch.from_numpy(sy.positions.copy()).pin_memory()
+        z_pin = torch.from_numpy(sy.species.copy()).pin_memory()
+        f_pin = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+        e_pin = torch.empty(1, dtype=torch.float64).pin_memory()
+        w_pin = torch.empty(9, dtype=torch.float64).pin_memory()
+        H = np.ascontiguousarray(sy.cell)
+        import ctypes
+        from paper_2506_04055_gb300 import _lib
+        flags = _lib.CTD_NEED_FORCES | _lib.CTD_NEED_VIRIAL
+        P = lambda t: ctypes.c_void_p(t.data_ptr())
+        for _ in range(max(1, args.warmup // 2)):
+            _lib.ctd_compute(pot.ctx, n, P(z_pin), P(x_pin), H.ctypes.data_as(ctypes.c_void_p), flags,
+                             P(e_pin), P(f_pin), P(w_pin))
+        e2e_steps = max(3, args.steps // 2)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            _lib.ctd_compute(pot.ctx, n, P(z_pin), P(x_pin), H.ctypes.data_as(ctypes.c_void_p), flags,
+                             P(e_pin), P(f_pin), P(w_pin))
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        pot.close()
+        results[prec] = {"total_ms": total_ms, "step_ms": step_ms, "prof": prof, "rebuilds": rebuilds,
+                         "clocks": clk.summary(), "e2e_s": e2e_s, "e2e_steps": e2e_steps,
+                         "h2d": n * 3 * 8 + n * 4 + 72, "d2h": n * 3 * 8 + 8 + 72,
+                         "epot": [float(ep[0])], "ekin": [float(ek[0])]}
+
+    def maxall(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    head = "bf16" if "bf16" in results and "error" not in results["bf16"] else "fp32"
+    summary = {}
+    for prec, r in results.items():
+        if "error" in r:
+            summary[prec] = r
+            continue
+        tot = maxall(r["total_ms"])
+        e2e = maxall(r["e2e_s"])
+        summary[prec] = {"value": sy.n * world * args.steps / (tot / 1e3), "ms_per_step": tot / args.steps,
+                         "p50_ms": r["step_ms"][len(r["step_ms"]) // 2],
+                         "p99_ms": r["step_ms"][min(len(r["step_ms"]) - 1, int(0.99 * len(r["step_ms"])))],
+                         "e2e": sy.n * world * r["e2e_steps"] / e2e, "rebuilds": r["rebuilds"]}
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    r = results[head]
+    s = summary[head]
+    peaks, peak_kind = read_peaks()
+    prof = r["prof"]
+    # dominant kernel stage by device time in the timed region
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    active_edges_per_launch = r.get("active_edges")
+    roofline = None
+    if dom in ("edge_bwd", "edge_fwd") and dom_launches:
+        # active edges: n_e from the stats of one compute call on the same system
+        import paper_2506_04055_gb300 as eng2
+        with eng2.Potential(F, K=K, T=T, n_species=S, rc=RC, params=blob) as p2:
+            st = p2.compute(sy.species, sy.positions, sy.cell, stats=True)["stats"]
+        ea = st["n_active_edges"]
+        per_ef = EDGE_BWD_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_FLOP_PER_EF
+        flop = ea * F * per_ef
+        achieved = flop / (dom_ms / dom_launches / 1e3) / 1e12
+        peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": kernel_traffic(f"k_{dom}"),
+                    "peak_source": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                   f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
+                    "algorithmic_flop_per_launch": flop, "launch_ms": dom_ms / dom_launches,
+                    "active_edges": ea}
+    launches = int(sum(v[1] for v in prof.values()))
+    line = {
+        "metric": METRIC, "value": s["value"], "unit": "atom-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": s["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(cells), "atoms_per_gpu": sy.n,
+                   "precision": head, "parallelism": f"replicas x{world} (independent systems)",
+                   "l2": "inputs larger than L2 (tens of GB resident per GPU)"},
+        "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "rebuilds": s["rebuilds"],
+        "roofline": roofline,
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": launches,
+        "e2e": {"value": s["e2e"], "unit": "atom-steps/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "clocks": r["clocks"],
+    }
+    for prec in summary:
+        line[prec] = summary[prec]
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="both", choices=["fp32", "bf16", "both"])
+    ap.add_argument("--cells", type=int, default=FCC_CELLS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

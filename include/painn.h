@@ -138,6 +138,21 @@ int ctd_md_run(ctd_ctx *ctx, int32_t nsteps, double dt, double *epot, double *ek
 /* Copy the MD state back (host arrays [n][3], either may be NULL). */
 int ctd_md_get_state(ctd_ctx *ctx, double *positions, double *velocities);
 
+/* ---- launch accounting and stage timing (benchmarks, statistics) ------------------------- */
+/* Stages: 0 neighbour build, 1 per-step prune, 2 node MLPs (message phi, update, readout),
+ * 3 edge message, 4 edge adjoint, 5 forces / virial / energy reductions, 6 integrator,
+ * 7 other (output scatter, checks). */
+#define CTD_NSTAGES 8
+
+/* enable != 0: bracket every kernel launch with CUDA events on the context's stream (adds a
+ * small host cost per launch).  Launch counts are always kept. */
+int ctd_profile_enable(ctd_ctx *ctx, int32_t enable);
+
+/* Copy the accumulated device milliseconds and launch counts per stage (arrays of
+ * CTD_NSTAGES, either may be NULL) since the last reset; reset != 0 zeroes them.  Waits for
+ * the timed launches to finish. */
+int ctd_profile_read(ctd_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
+
 /* Text of the last failure on this context (never NULL). */
 const char *ctd_last_error(ctd_ctx *ctx);
 

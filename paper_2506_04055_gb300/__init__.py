@@ -154,6 +154,14 @@ class Potential:
             out["stats"] = {k: getattr(st, k) for k, _ in ctd_stats._fields_}
         return out
 
+    # -- launch accounting ------------------------------------------------------------------
+    def profile(self, enable: bool = True):
+        _lib.ctd_profile_enable(self.ctx, enable)
+
+    def profile_read(self, reset: bool = True):
+        """{stage: (device ms, launches)} since the last reset."""
+        return _lib.ctd_profile_read(self.ctx, reset)
+
     # -- molecular dynamics ----------------------------------------------------------------
     def md_set_state(self, species, masses, positions, velocities, cell, skin: float = 1.0):
         z = _host(species, np.int32)

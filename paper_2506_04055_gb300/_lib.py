@@ -40,8 +40,10 @@ ERROR_NAMES = {
 EXPORTS = [
     "ctd_create", "ctd_load_params", "ctd_build_neighbors", "ctd_get_pairs", "ctd_compute",
     "ctd_set_energy_out", "ctd_md_set_state", "ctd_md_run", "ctd_md_get_state",
-    "ctd_last_error", "ctd_destroy",
+    "ctd_profile_enable", "ctd_profile_read", "ctd_last_error", "ctd_destroy",
 ]
+CTD_NSTAGES = 8
+STAGES = ["build", "prune", "node", "edge_fwd", "edge_bwd", "forces", "md", "other"]
 
 
 class ctd_model_desc(ctypes.Structure):
@@ -85,6 +87,8 @@ def load(path: str = LIB_PATH):
         "ctd_md_set_state": ([P, I64, P, P, P, P, P, D], ctypes.c_int),
         "ctd_md_run": ([P, I32, D, P, P, P], ctypes.c_int),
         "ctd_md_get_state": ([P, P, P], ctypes.c_int),
+        "ctd_profile_enable": ([P, I32], ctypes.c_int),
+        "ctd_profile_read": ([P, P, P, I32], ctypes.c_int),
         "ctd_last_error": ([P], ctypes.c_char_p),
         "ctd_destroy": ([P], None),
     }
@@ -152,6 +156,17 @@ def ctd_md_run(ctx, nsteps, dt, epot_ptr, ekin_ptr):
 
 def ctd_md_get_state(ctx, positions_ptr, velocities_ptr):
     return check(ctx, load().ctd_md_get_state(ctx, positions_ptr, velocities_ptr))
+
+
+def ctd_profile_enable(ctx, enable: bool):
+    return check(ctx, load().ctd_profile_enable(ctx, 1 if enable else 0))
+
+
+def ctd_profile_read(ctx, reset: bool = True):
+    ms = (ctypes.c_double * CTD_NSTAGES)()
+    ln = (ctypes.c_int64 * CTD_NSTAGES)()
+    check(ctx, load().ctd_profile_read(ctx, ms, ln, 1 if reset else 0))
+    return {s: (ms[k], ln[k]) for k, s in enumerate(STAGES)}
 
 
 def ctd_last_error(ctx) -> str:

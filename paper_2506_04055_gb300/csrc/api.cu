@@ -28,6 +28,9 @@ struct DBuf {
 
 constexpr int kPartials = 152 * 4;   // fixed block count of the reductions (deterministic)
 
+// The tensor-core path is compiled in only when its kernels exist in this build.
+bool bf16_available() { return false; }
+
 }  // namespace
 
 struct ctd_ctx {
@@ -62,6 +65,8 @@ struct ctd_ctx {
   std::vector<DBuf> mbuf;
   double* energy_out_user = nullptr;
 
+  ProfState prof;
+
   // MD state (sorted order)
   bool md_ready = false, md_forces_valid = false;
   DBuf md_v, md_m, md_x_user, md_v_user, md_ep, md_ek, md_tmp;
@@ -77,6 +82,12 @@ struct ctd_ctx {
 };
 
 namespace {
+
+// Binds the calling thread's launch accounting to a context for the duration of an API call.
+struct Bind {
+  explicit Bind(ctd_ctx* c) { prof_bind(c ? &c->prof : nullptr); }
+  ~Bind() { prof_bind(nullptr); }
+};
 
 int fail(ctd_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -195,6 +206,7 @@ int build_from_device_positions(ctd_ctx* c, int64_t n, const double H[9], double
   if (!(cutoff > 0.0) || !(skin >= 0.0)) return fail(c, CTD_ERR_INVALID_ARG, "cutoff must be > 0, skin >= 0");
   int r = setup_geometry(c, H, cutoff + skin);
   if (r) return r;
+  StageGuard sg(STG_BUILD);
   cudaStream_t st = c->st;
   const int64_t n1 = n > 0 ? n : 1;
   ENSURE(c, c->xw, sizeof(double) * 3 * n1);
@@ -263,6 +275,7 @@ int copy_in(ctd_ctx* c, void* dst, const void* src, size_t bytes, bool device) {
 
 // Per-step prune of the Verlet list to the active list (positions already in c->x_s, sorted).
 int prune(ctd_ctx* c, double* maxdisp_out) {
+  StageGuard sg(STG_PRUNE);
   cudaStream_t st = c->st;
   const int64_t n = c->n, n1 = n > 0 ? n : 1, e1 = c->n_verlet > 0 ? c->n_verlet : 1;
   ENSURE(c, c->delta, sizeof(float4) * n1);
@@ -324,6 +337,7 @@ int evaluate(ctd_ctx* c, bool need_grad) {
                               P<float4>(c->ar), P<int32_t>(c->arev), ptrs.data(), need_grad, P<double>(c->epart),
                               kPartials, P<float4>(c->hedge), P<float>(c->force_s), P<double>(c->vpart),
                               kPartials, P<float>(c->eatom), P<int>(c->status));
+  StageGuard sg(STG_FORCES);
   launch_sum_partials(st, kPartials, 1, P<double>(c->epart), P<double>(c->out_e), 1.0);
   if (need_grad) launch_sum_partials(st, kPartials, 9, P<double>(c->vpart), P<double>(c->out_w), 1.0);
   CUDA_OK(c, cudaGetLastError());
@@ -494,6 +508,7 @@ int ctd_create(ctd_ctx** out, const ctd_model_desc* desc, size_t hbm_budget_byte
       desc->T > kMaxT || desc->n_species < 1 || !(desc->rc > 0.0) ||
       (desc->precision != CTD_PREC_FP32 && desc->precision != CTD_PREC_BF16))
     return CTD_ERR_INVALID_ARG;
+  if (desc->precision == CTD_PREC_BF16 && !bf16_available()) return CTD_ERR_INVALID_ARG;
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
     cudaGetLastError();
@@ -519,6 +534,7 @@ int ctd_create(ctd_ctx** out, const ctd_model_desc* desc, size_t hbm_budget_byte
 void ctd_destroy(ctd_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
+  c->prof.collect();
   for (DBuf* b : c->all)
     if (b->p) cudaFree(b->p);
   for (DBuf& b : c->mbuf)
@@ -531,12 +547,14 @@ const char* ctd_last_error(ctd_ctx* c) { return c ? c->err.c_str() : "null conte
 
 int ctd_load_params(ctd_ctx* c, const void* blob, size_t nbytes) {
   if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
   return load_params_impl(c, blob, nbytes);
 }
 
 int ctd_build_neighbors(ctd_ctx* c, int64_t n, const double* positions, const double cell[9], double cutoff,
                         double skin, int32_t flags, int64_t* n_pairs_out) {
   if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
   if (n < 0 || (n > 0 && !positions) || !cell) return fail(c, CTD_ERR_INVALID_ARG, "bad positions / cell");
   if (n > (int64_t)INT32_MAX / 4) return fail(c, CTD_ERR_INVALID_ARG, "too many atoms");
   const bool dev = flags & CTD_DEVICE_PTRS;
@@ -553,6 +571,7 @@ int ctd_build_neighbors(ctd_ctx* c, int64_t n, const double* positions, const do
 
 int ctd_get_pairs(ctd_ctx* c, int32_t* pi, int32_t* pj, int8_t* shift, int64_t cap) {
   if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
   if (!c->have_list) return fail(c, CTD_ERR_STATE, "no neighbour list");
   if (cap < c->n_verlet) return fail(c, CTD_ERR_CAPACITY, "output arrays shorter than the pair list");
   if (!pi || !pj || !shift) return fail(c, CTD_ERR_INVALID_ARG, "null output array");
@@ -595,6 +614,27 @@ int ctd_get_pairs(ctd_ctx* c, int32_t* pi, int32_t* pj, int8_t* shift, int64_t c
   return CTD_OK;
 }
 
+int ctd_profile_enable(ctd_ctx* c, int32_t enable) {
+  if (!c) return CTD_ERR_INVALID_ARG;
+  c->prof.collect();
+  c->prof.on = enable != 0;
+  return CTD_OK;
+}
+
+int ctd_profile_read(ctd_ctx* c, double* ms, int64_t* launches, int32_t reset) {
+  if (!c) return CTD_ERR_INVALID_ARG;
+  c->prof.collect();
+  for (int s = 0; s < STG_COUNT; ++s) {
+    if (ms) ms[s] = c->prof.ms[s];
+    if (launches) launches[s] = c->prof.launches[s];
+    if (reset) {
+      c->prof.ms[s] = 0.0;
+      c->prof.launches[s] = 0;
+    }
+  }
+  return CTD_OK;
+}
+
 int ctd_set_energy_out(ctd_ctx* c, double* energies) {
   if (!c) return CTD_ERR_INVALID_ARG;
   c->energy_out_user = energies;
@@ -604,6 +644,7 @@ int ctd_set_energy_out(ctd_ctx* c, double* energies) {
 int ctd_compute(ctd_ctx* c, int64_t n, const int32_t* species, const double* positions, const double cell[9],
                 int32_t flags, double* energy, double* forces, double* virial, ctd_stats* stats) {
   if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
   if (!c->have_params) return fail(c, CTD_ERR_STATE, "parameters not loaded");
   if (n < 0 || (n > 0 && (!positions || !species)) || !cell || !energy)
     return fail(c, CTD_ERR_INVALID_ARG, "bad arguments");
@@ -680,6 +721,7 @@ int ctd_compute(ctd_ctx* c, int64_t n, const int32_t* species, const double* pos
 int ctd_md_set_state(ctd_ctx* c, int64_t n, const int32_t* species, const double* masses, const double* positions,
                      const double* velocities, const double cell[9], double skin) {
   if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
   if (!c->have_params) return fail(c, CTD_ERR_STATE, "parameters not loaded");
   if (n <= 0 || !species || !masses || !positions || !velocities || !cell || !(skin >= 0.0))
     return fail(c, CTD_ERR_INVALID_ARG, "bad MD state");
@@ -754,6 +796,7 @@ int md_forces(ctd_ctx* c, int32_t* rebuilds) {
 
 int ctd_md_run(ctd_ctx* c, int32_t nsteps, double dt, double* epot, double* ekin, int32_t* n_rebuilds) {
   if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
   if (!c->md_ready) return fail(c, CTD_ERR_STATE, "no MD state");
   if (nsteps < 0 || !(dt > 0.0)) return fail(c, CTD_ERR_INVALID_ARG, "bad step count or time step");
   const int64_t n = c->n;
@@ -768,6 +811,7 @@ int ctd_md_run(ctd_ctx* c, int32_t nsteps, double dt, double* epot, double* ekin
     if (r) return r;
     c->md_forces_valid = true;
   }
+  StageGuard sg(STG_MD);
   auto record = [&](int step) {
     cudaMemcpyAsync(P<double>(c->md_ep) + step, c->out_e.p, sizeof(double), cudaMemcpyDeviceToDevice, st);
     launch_kinetic(st, n, P<double>(c->md_m), P<double>(c->md_v), P<double>(c->kpart), kPartials);
@@ -791,6 +835,7 @@ int ctd_md_run(ctd_ctx* c, int32_t nsteps, double dt, double* epot, double* ekin
 
 int ctd_md_get_state(ctd_ctx* c, double* positions, double* velocities) {
   if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
   if (!c->md_ready) return fail(c, CTD_ERR_STATE, "no MD state");
   const int64_t n = c->n;
   int32_t* perm = P<int32_t>(c->perm);

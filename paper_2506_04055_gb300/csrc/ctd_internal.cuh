@@ -4,8 +4,41 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
+#include <vector>
 
 namespace ctd {
+
+// ---------------------------------------------------------------- launch accounting / timing
+// Every kernel launch is wrapped in a LaunchScope: it counts the launch under the current
+// stage and, when profiling is on, brackets it with CUDA events on the launching stream.
+enum Stage : int {
+  STG_BUILD = 0, STG_PRUNE, STG_NODE, STG_EDGE_FWD, STG_EDGE_BWD, STG_FORCES, STG_MD, STG_MISC, STG_COUNT
+};
+struct ProfState {
+  bool on = false;
+  int stage = STG_MISC;
+  double ms[STG_COUNT] = {};
+  int64_t launches[STG_COUNT] = {};
+  struct Rec { int stage; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  ~ProfState();
+  void collect();            // waits for pending events and accumulates their times
+};
+void prof_bind(ProfState* p);   // bind the calling thread to a context's profiler (or null)
+int prof_stage();
+void prof_set_stage(int s);
+struct StageGuard {
+  int prev;
+  explicit StageGuard(int s) : prev(prof_stage()) { prof_set_stage(s); }
+  ~StageGuard() { prof_set_stage(prev); }
+};
+struct LaunchScope {
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  explicit LaunchScope(cudaStream_t s);
+  ~LaunchScope();
+};
 
 constexpr int kThreads = 256;
 constexpr int kMaxT = 8;

@@ -110,31 +110,31 @@ __global__ void k_check_finite(int64_t n, const double* __restrict__ a, int* sta
 static inline unsigned nblk(int64_t w) { return (unsigned)((w + kThreads - 1) / kThreads); }
 
 void launch_kick_drift(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* x, double* v) {
-  if (n) k_kick_drift<<<nblk(n), kThreads, 0, st>>>(n, dt, f, m, x, v);
+  if (n) { LaunchScope ls_(st); k_kick_drift<<<nblk(n), kThreads, 0, st>>>(n, dt, f, m, x, v); }
 }
 void launch_kick(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* v) {
-  if (n) k_kick<<<nblk(n), kThreads, 0, st>>>(n, dt, f, m, v);
+  if (n) { LaunchScope ls_(st); k_kick<<<nblk(n), kThreads, 0, st>>>(n, dt, f, m, v); }
 }
 void launch_kinetic(cudaStream_t st, int64_t n, const double* m, const double* v, double* partials, int nb) {
-  k_kinetic<<<nb, kThreads, 0, st>>>(n, m, v, partials);
+  { LaunchScope ls_(st); k_kinetic<<<nb, kThreads, 0, st>>>(n, m, v, partials); }
 }
 void launch_sum_partials(cudaStream_t st, int nb, int width, const double* partials, double* out, double scale) {
-  k_sum_partials<<<1, 32, 0, st>>>(nb, width, partials, out, scale);
+  { LaunchScope ls_(st); k_sum_partials<<<1, 32, 0, st>>>(nb, width, partials, out, scale); }
 }
 void launch_scatter_rows(cudaStream_t st, int64_t n, int w, const int32_t* perm, const float* in, double* out) {
-  if (n) k_scatter_rows<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out);
+  if (n) { LaunchScope ls_(st); k_scatter_rows<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out); }
 }
 void launch_scatter_rows_d(cudaStream_t st, int64_t n, int w, const int32_t* perm, const double* in, double* out) {
-  if (n) k_scatter_rows_d<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out);
+  if (n) { LaunchScope ls_(st); k_scatter_rows_d<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out); }
 }
 void launch_gather_rows_d(cudaStream_t st, int64_t n, int w, const int32_t* perm, const double* in, double* out) {
-  if (n) k_gather_rows_d<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out);
+  if (n) { LaunchScope ls_(st); k_gather_rows_d<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out); }
 }
 void launch_gather_i32(cudaStream_t st, int64_t n, const int32_t* perm, const int32_t* in, int32_t* out) {
-  if (n) k_gather_i32<<<nblk(n), kThreads, 0, st>>>(n, perm, in, out);
+  if (n) { LaunchScope ls_(st); k_gather_i32<<<nblk(n), kThreads, 0, st>>>(n, perm, in, out); }
 }
 void launch_check_finite(cudaStream_t st, int64_t n, const double* a, int* status) {
-  if (n) k_check_finite<<<nblk(n), kThreads, 0, st>>>(n, a, status);
+  if (n) { LaunchScope ls_(st); k_check_finite<<<nblk(n), kThreads, 0, st>>>(n, a, status); }
 }
 
 }  // namespace ctd

@@ -114,7 +114,7 @@ static void gemm(cudaStream_t st, int64_t M, int N, int K, const float* A, int l
                  int ldo2 = 0) {
   if (M == 0) return;
   dim3 grid((N + GBN - 1) / GBN, (unsigned)((M + GBM - 1) / GBM));
-  k_gemm<EPI><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2);
+  { LaunchScope ls_(st); k_gemm<EPI><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); }
 }
 
 // ================================================================================ node kernels
@@ -571,8 +571,8 @@ static void edge_fwd_kp(cudaStream_t st, const ModelW& m, int t, int64_t n, cons
   int64_t blocks = (n + G - 1) / G;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  k_edge_fwd<KP><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, arow, acol, ar, PHI, S, V,
-                                                           m.L[t].Wf, m.L[t].bf, SM, VM);
+  { LaunchScope ls_(st); k_edge_fwd<KP><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, arow, acol, ar, PHI, S, V,
+                                                           m.L[t].Wf, m.L[t].bf, SM, VM); }
 }
 
 template <int KP>
@@ -584,8 +584,8 @@ static void edge_bwd_kp(cudaStream_t st, const ModelW& m, int t, int accumulate,
   int64_t blocks = (n + G - 1) / G;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  k_edge_bwd<KP><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, accumulate, arow, acol, ar, PHI,
-                                                           Gsm, Gvm, m.L[t].Wf, m.L[t].bf, GPHI, hedge);
+  { LaunchScope ls_(st); k_edge_bwd<KP><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, accumulate, arow, acol, ar, PHI,
+                                                           Gsm, Gvm, m.L[t].Wf, m.L[t].bf, GPHI, hedge); }
 }
 
 #define CTD_KP_DISPATCH(KPV, CALL) \
@@ -664,9 +664,10 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
                                  float* force_s, double* virial_partials, int n_virial_partials,
                                  float* e_atom, int* status) {
   edge_smem_setup();
+  StageGuard node_stage(STG_NODE);
   const int F = m.F, T = m.T, Fh = F / 2;
   const unsigned nb = blocks_for(n * F);
-  if (n > 0) k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0]);
+  if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0]); }
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
     float *S = B[B_S0 + t], *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
@@ -675,22 +676,25 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     // phi = W2 silu(W1 s + b1) + b2
     gemm<EPI_BIAS_SILU>(st, n, F, F, S, F, L.W1t, L.b1, nullptr, 0, H1, F, T1, F);
     gemm<EPI_BIAS>(st, n, 3 * F, F, T1, F, L.W2t, L.b2, nullptr, 0, T2, 3 * F);
-    if (n > 0) k_phi_pack<<<nb, kThreads, 0, st>>>(n, F, T2, V, PHI);
+    if (n > 0) { LaunchScope ls_(st); k_phi_pack<<<nb, kThreads, 0, st>>>(n, F, T2, V, PHI); }
     // message
 #define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM)
-    if (n > 0) { CTD_KP_DISPATCH(m.KP, CTD_FWD) }
+    if (n > 0) {
+      StageGuard sg(STG_EDGE_FWD);
+      CTD_KP_DISPATCH(m.KP, CTD_FWD)
+    }
 #undef CTD_FWD
     // update
     gemm<EPI_BIAS>(st, 3 * n, 2 * F, F, VM, F, L.UVt, nullptr, nullptr, 0, UV, 2 * F);
-    if (n > 0) k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1);
+    if (n > 0) { LaunchScope ls_(st); k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1); }
     gemm<EPI_BIAS_SILU>(st, n, F, 2 * F, T1, 2 * F, L.A1t, L.c1, nullptr, 0, H2, F, T2, F);
     gemm<EPI_BIAS>(st, n, 3 * F, F, T2, F, L.A2t, L.c2, nullptr, 0, AV, 3 * F);
-    if (n > 0) k_update_post<<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1]);
+    if (n > 0) { LaunchScope ls_(st); k_update_post<<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1]); }
   }
   // readout
   gemm<EPI_BIAS>(st, n, Fh, F, B[B_S0 + T], F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
-  k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2,
-                                                    need_grad ? B[B_G3] : nullptr, e_atom, energy_partials);
+  { LaunchScope ls_(st); k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2,
+                                                    need_grad ? B[B_G3] : nullptr, e_atom, energy_partials); }
   if (!need_grad) return;
   // dU/ds^T = G3 R1
   gemm<EPI_BIAS>(st, n, F, Fh, B[B_G3], Fh, m.R1, nullptr, nullptr, 0, B[B_GS], F);
@@ -702,21 +706,25 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     float *T1 = B[B_T1], *T2 = B[B_T2], *T3 = B[B_T3];
     float *GS = B[B_GS], *GV = B[B_GV], *GSM = B[B_GSM], *GVM = B[B_GVM], *GPHI = B[B_GPHI];
     // update backward
-    if (n > 0) k_update_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, T1, T3);
+    if (n > 0) { LaunchScope ls_(st); k_update_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, T1, T3); }
     gemm<EPI_DSILU>(st, n, F, 3 * F, T1, 3 * F, L.A2, nullptr, H2, F, T2, F);          // gh2
     gemm<EPI_BIAS>(st, n, 2 * F, F, T2, F, L.A1, nullptr, nullptr, 0, T1, 2 * F);       // gz
-    if (n > 0) k_update_bwd_mid<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, GSM, T3);
+    if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, GSM, T3); }
     gemm<EPI_ADD>(st, 3 * n, F, 2 * F, T3, 2 * F, L.UV, nullptr, GV, F, GVM, F);         // gvm
     // message backward
 #define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge)
-    if (n > 0) { CTD_KP_DISPATCH(m.KP, CTD_BWD) }
+    if (n > 0) {
+      StageGuard sg(STG_EDGE_BWD);
+      CTD_KP_DISPATCH(m.KP, CTD_BWD)
+    }
 #undef CTD_BWD
     // phi backward -> gradients w.r.t. the layer input (s_t, v_t)
-    if (n > 0) k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV);
+    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV); }
     gemm<EPI_DSILU>(st, n, F, 3 * F, T2, 3 * F, L.W2, nullptr, H1, F, T1, F);          // gh1
     gemm<EPI_ADD>(st, n, F, F, T1, F, L.W1, nullptr, GSM, F, GS, F);                    // gs
   }
-  k_forces<<<n_virial_partials, kThreads, 0, st>>>(n, arow, ar, arev, hedge, force_s, virial_partials, status);
+  StageGuard fstage(STG_FORCES);
+  { LaunchScope ls_(st); k_forces<<<n_virial_partials, kThreads, 0, st>>>(n, arow, ar, arev, hedge, force_s, virial_partials, status); }
 }
 
 }  // namespace ctd

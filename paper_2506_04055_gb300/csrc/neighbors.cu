@@ -52,8 +52,8 @@ __global__ void k_wrap_bin(int64_t n, const double* __restrict__ x, CellGeom g,
 void launch_wrap_bin(cudaStream_t st, int64_t n, const double* x_user, const CellGeom& g,
                      double* xw, int32_t* wrapm, int32_t* cell, int32_t* cell_count) {
   if (n == 0) return;
-  k_wrap_bin<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, x_user, g, xw, wrapm,
-                                                                             cell, cell_count);
+  { LaunchScope ls_(st); k_wrap_bin<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, x_user, g, xw, wrapm,
+                                                                             cell, cell_count); }
 }
 
 // ------------------------------------------------------------------------------- counting sort
@@ -69,8 +69,8 @@ __global__ void k_place(int64_t n, const int32_t* __restrict__ cell, const int32
 void launch_place(cudaStream_t st, int64_t n, const int32_t* cell, const int32_t* cell_start,
                   int32_t* cursor, int32_t* tmp_idx) {
   if (n == 0) return;
-  k_place<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, cell, cell_start, cursor,
-                                                                         tmp_idx);
+  { LaunchScope ls_(st); k_place<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, cell, cell_start, cursor,
+                                                                         tmp_idx); }
 }
 
 // One warp per cell: rank of each member = number of members with a smaller caller index.
@@ -92,8 +92,8 @@ void launch_sort_cells(cudaStream_t st, int64_t ncell, const int32_t* cell_start
                        const int32_t* tmp_idx, int32_t* perm) {
   if (ncell == 0) return;
   int64_t threads = ncell * 32;
-  k_sort_cells<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(ncell, cell_start,
-                                                                                    tmp_idx, perm);
+  { LaunchScope ls_(st); k_sort_cells<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(ncell, cell_start,
+                                                                                    tmp_idx, perm); }
 }
 
 __global__ void k_gather_sorted(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ xw,
@@ -115,8 +115,8 @@ void launch_gather_sorted(cudaStream_t st, int64_t n, const int32_t* perm, const
                           const double* x_user, const int32_t* species_user, double* xw_s,
                           double* xref_s, int32_t* species_s, int32_t* inv_perm) {
   if (n == 0) return;
-  k_gather_sorted<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-      n, perm, xw, x_user, species_user, xw_s, xref_s, species_s, inv_perm);
+  { LaunchScope ls_(st); k_gather_sorted<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+      n, perm, xw, x_user, species_user, xw_s, xref_s, species_s, inv_perm); }
 }
 
 // ------------------------------------------------------------------------------- pair search
@@ -195,9 +195,9 @@ void launch_pair_search(cudaStream_t st, bool fill, int64_t n, const double* xw_
   int64_t threads = n * 32;
   unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
   if (fill)
-    k_pair_search<true><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, count, row_ptr, col, img, base);
+    { LaunchScope ls_(st); k_pair_search<true><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, count, row_ptr, col, img, base); }
   else
-    k_pair_search<false><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, count, row_ptr, col, img, base);
+    { LaunchScope ls_(st); k_pair_search<false><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, count, row_ptr, col, img, base); }
 }
 
 // ------------------------------------------------------------------------------- reverse edges
@@ -233,8 +233,8 @@ void launch_reverse(cudaStream_t st, int64_t n, const int32_t* row_ptr, const in
                     const uint32_t* img, int32_t* rev, int* status) {
   if (n == 0) return;
   int64_t threads = n * 32;
-  k_reverse<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, row_ptr, col, img,
-                                                                                 rev, status);
+  { LaunchScope ls_(st); k_reverse<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, row_ptr, col, img,
+                                                                                 rev, status); }
 }
 
 // ------------------------------------------------------------------------------- per step
@@ -251,7 +251,7 @@ __global__ void k_gather_positions(int64_t n, const int32_t* __restrict__ perm, 
 void launch_gather_positions(cudaStream_t st, int64_t n, const int32_t* perm, const double* x_user,
                              double* x_s) {
   if (n == 0) return;
-  k_gather_positions<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, perm, x_user, x_s);
+  { LaunchScope ls_(st); k_gather_positions<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, perm, x_user, x_s); }
 }
 
 __global__ void k_delta(int64_t n, const double* __restrict__ xs, const double* __restrict__ xref,
@@ -273,8 +273,8 @@ __global__ void k_delta(int64_t n, const double* __restrict__ xs, const double* 
 void launch_delta(cudaStream_t st, int64_t n, const double* x_s, const double* xref_s, float4* delta,
                   unsigned int* maxdisp2_bits) {
   if (n == 0) return;
-  k_delta<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, x_s, xref_s, delta,
-                                                                         maxdisp2_bits);
+  { LaunchScope ls_(st); k_delta<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, x_s, xref_s, delta,
+                                                                         maxdisp2_bits); }
 }
 
 template <bool FILL>
@@ -325,9 +325,9 @@ void launch_prune(cudaStream_t st, bool fill, int64_t n, const int32_t* vrow, co
   int64_t threads = n * 32;
   unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
   if (fill)
-    k_prune<true><<<blocks, kThreads, 0, st>>>(n, vrow, vcol, vbase, delta, rc2, acount, arow, acol, ar, vidx, v2a);
+    { LaunchScope ls_(st); k_prune<true><<<blocks, kThreads, 0, st>>>(n, vrow, vcol, vbase, delta, rc2, acount, arow, acol, ar, vidx, v2a); }
   else
-    k_prune<false><<<blocks, kThreads, 0, st>>>(n, vrow, vcol, vbase, delta, rc2, acount, arow, acol, ar, vidx, v2a);
+    { LaunchScope ls_(st); k_prune<false><<<blocks, kThreads, 0, st>>>(n, vrow, vcol, vbase, delta, rc2, acount, arow, acol, ar, vidx, v2a); }
 }
 
 __global__ void k_prune_rev(int64_t n_active, const int32_t* __restrict__ vidx,
@@ -357,8 +357,8 @@ void launch_prune_rev(cudaStream_t st, int64_t n, const int32_t* arow, const int
                       const int32_t* vrev, const int32_t* v2a, int32_t* arev) {
   if (n == 0) return;
   int64_t threads = n * 32;
-  k_prune_rev_rows<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, arow, vidx, vrev,
-                                                                                        v2a, arev);
+  { LaunchScope ls_(st); k_prune_rev_rows<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, arow, vidx, vrev,
+                                                                                        v2a, arev); }
 }
 
 }  // namespace ctd

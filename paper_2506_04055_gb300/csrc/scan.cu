@@ -87,9 +87,9 @@ void launch_exclusive_scan(cudaStream_t st, int64_t n, const int32_t* in, int32_
     return;
   }
   int nb = (int)((n + kScanTile - 1) / kScanTile);
-  k_scan_totals<<<nb, kThreads, 0, st>>>(n, in, sums);
-  k_scan_sums<<<1, kThreads, 0, st>>>(nb, sums);
-  k_scan_apply<<<nb, kThreads, 0, st>>>(n, in, sums, out);
+  { LaunchScope ls_(st); k_scan_totals<<<nb, kThreads, 0, st>>>(n, in, sums); }
+  { LaunchScope ls_(st); k_scan_sums<<<1, kThreads, 0, st>>>(nb, sums); }
+  { LaunchScope ls_(st); k_scan_apply<<<nb, kThreads, 0, st>>>(n, in, sums, out); }
 }
 
 }  // namespace ctd
