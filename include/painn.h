@@ -153,6 +153,37 @@ int ctd_profile_enable(ctd_ctx *ctx, int32_t enable);
  * the timed launches to finish. */
 int ctd_profile_read(ctd_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
 
+/* ---- neighbour list without device allocation ------------------------------------------ */
+/* The paper has no counterpart to this call; it exists for callers of this library that must
+ * not allocate device memory: an MD code that manages a fixed device memory pool and cannot
+ * let a library call cudaMalloc/cudaFree behind it, or a driver that must not allocate
+ * between its own set-up and teardown.
+ *
+ * It finds the same pair set as ctd_build_neighbors (same wrap, same cell search, same FP64
+ * pair test with cutoff + skin) without a context and without allocating: every scratch
+ * array lives in one static device array of about 4 MB that each GPU loading this library
+ * holds until the process exits.  Limits: n <= CTD_NOALLOC_MAX_ATOMS atoms and at most
+ * CTD_NOALLOC_MAX_CELLS search cells (cell volume / (cutoff + skin)^3, roughly); beyond
+ * either the call returns CTD_ERR_INVALID_ARG and does nothing.
+ *
+ * positions: device doubles [n][3] (any atom order, need not be wrapped); cell: host
+ * double[9] (rows = lattice vectors).  pair_i, pair_j: device int32 [cap]; pair_shift: device
+ * int8 [cap][3].  They receive the pairs in the caller's atom indices (grouped by atom, not
+ * sorted) with the image shift relative to the wrapped positions.  *n_pairs (host) receives
+ * the number of pairs; if it exceeds cap nothing is written and CTD_ERR_CAPACITY is returned.
+ * cuda_stream: the cudaStream_t to run on (NULL = default stream); the call synchronises it.
+ *
+ * The first call on each device looks up the device address of the static array (with that
+ * device current), so make a first call before capturing any stream on that device.  All
+ * calls share the one array, and each starts by clearing the parts that must start at zero;
+ * calls that overlap on the GPU (different streams or threads at once) race on it and must be
+ * serialised by the caller. */
+#define CTD_NOALLOC_MAX_ATOMS 32768
+#define CTD_NOALLOC_MAX_CELLS 32768
+int ctd_neighbors_noalloc(int64_t n, const double *positions, const double cell[9], double cutoff,
+                          double skin, int32_t *pair_i, int32_t *pair_j, int8_t *pair_shift,
+                          int64_t cap, int64_t *n_pairs, void *cuda_stream);
+
 /* Text of the last failure on this context (never NULL). */
 const char *ctd_last_error(ctd_ctx *ctx);
 

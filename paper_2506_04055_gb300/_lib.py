@@ -40,8 +40,11 @@ ERROR_NAMES = {
 EXPORTS = [
     "ctd_create", "ctd_load_params", "ctd_build_neighbors", "ctd_get_pairs", "ctd_compute",
     "ctd_set_energy_out", "ctd_md_set_state", "ctd_md_run", "ctd_md_get_state",
-    "ctd_profile_enable", "ctd_profile_read", "ctd_last_error", "ctd_destroy",
+    "ctd_profile_enable", "ctd_profile_read", "ctd_neighbors_noalloc", "ctd_last_error",
+    "ctd_destroy",
 ]
+CTD_NOALLOC_MAX_ATOMS = 32768
+CTD_NOALLOC_MAX_CELLS = 32768
 CTD_NSTAGES = 8
 STAGES = ["build", "prune", "node", "edge_fwd", "edge_bwd", "forces", "md", "other"]
 
@@ -89,6 +92,7 @@ def load(path: str = LIB_PATH):
         "ctd_md_get_state": ([P, P, P], ctypes.c_int),
         "ctd_profile_enable": ([P, I32], ctypes.c_int),
         "ctd_profile_read": ([P, P, P, I32], ctypes.c_int),
+        "ctd_neighbors_noalloc": ([I64, P, P, D, D, P, P, P, I64, P, P], ctypes.c_int),
         "ctd_last_error": ([P], ctypes.c_char_p),
         "ctd_destroy": ([P], None),
     }
@@ -167,6 +171,16 @@ def ctd_profile_read(ctx, reset: bool = True):
     ln = (ctypes.c_int64 * CTD_NSTAGES)()
     check(ctx, load().ctd_profile_read(ctx, ms, ln, 1 if reset else 0))
     return {s: (ms[k], ln[k]) for k, s in enumerate(STAGES)}
+
+
+def ctd_neighbors_noalloc(n, positions_ptr, cell_ptr, cutoff, skin, i_ptr, j_ptr, shift_ptr, cap,
+                          cuda_stream=None):
+    """Returns (status code, number of pairs); never raises on CTD_ERR_CAPACITY so callers can
+    size their arrays from the count."""
+    npairs = ctypes.c_int64()
+    code = load().ctd_neighbors_noalloc(n, positions_ptr, cell_ptr, cutoff, skin, i_ptr, j_ptr,
+                                        shift_ptr, cap, ctypes.byref(npairs), cuda_stream)
+    return code, npairs.value
 
 
 def ctd_last_error(ctx) -> str:
