@@ -153,6 +153,16 @@ int ctd_profile_enable(ctd_ctx *ctx, int32_t enable);
  * the timed launches to finish. */
 int ctd_profile_read(ctd_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
 
+/* ---- tensor-core building block ---------------------------------------------------------- */
+/* C[M][N] = A[M][K] . B[N][K]^T with BF16 operands and FP32 accumulation on the tcgen05
+ * tensor cores, operand tiles staged by TMA -- the contraction every MLP of the BF16 path
+ * runs on.  Device pointers on the context's stream: A bf16 row-major with leading dimension
+ * lda (elements, lda*2 a multiple of 16 bytes), B bf16 [N][K] row-major, C float row-major
+ * with leading dimension ldc.  K: multiple of 64; N: multiple of 32, <= 512.  Synchronises
+ * the stream; CTD_ERR_TIMEOUT if a bounded device wait gave up. */
+int ctd_gemm_bf16(ctd_ctx *ctx, int64_t M, int32_t N, int32_t K, const void *A, int64_t lda,
+                  const void *B, float *C, int64_t ldc);
+
 /* ---- neighbour list without device allocation ------------------------------------------ */
 /* The paper has no counterpart to this call; it exists for callers of this library that must
  * not allocate device memory: an MD code that manages a fixed device memory pool and cannot

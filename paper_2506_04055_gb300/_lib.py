@@ -40,7 +40,8 @@ ERROR_NAMES = {
 EXPORTS = [
     "ctd_create", "ctd_load_params", "ctd_build_neighbors", "ctd_get_pairs", "ctd_compute",
     "ctd_set_energy_out", "ctd_md_set_state", "ctd_md_run", "ctd_md_get_state",
-    "ctd_profile_enable", "ctd_profile_read", "ctd_neighbors_noalloc", "ctd_last_error",
+    "ctd_profile_enable", "ctd_profile_read", "ctd_gemm_bf16", "ctd_neighbors_noalloc",
+    "ctd_last_error",
     "ctd_destroy",
 ]
 CTD_NOALLOC_MAX_ATOMS = 32768
@@ -72,12 +73,12 @@ _lib = None
 
 
 def load(path: str = LIB_PATH):
-    """Load libctd_painn.so (build it first with ``paper_2506_04055_gb300.build.build()``)."""
+    """Load libctd_painn.so (build it first with ``paper_2506_04055_gb300.build()``)."""
     global _lib
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise OSError(f"{path} is missing: run paper_2506_04055_gb300.build.build() first")
+        raise OSError(f"{path} is missing: run paper_2506_04055_gb300.build() first")
     lib = ctypes.CDLL(path)
     P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     sig = {
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
         "ctd_md_get_state": ([P, P, P], ctypes.c_int),
         "ctd_profile_enable": ([P, I32], ctypes.c_int),
         "ctd_profile_read": ([P, P, P, I32], ctypes.c_int),
+        "ctd_gemm_bf16": ([P, I64, I32, I32, P, I64, P, P, I64], ctypes.c_int),
         "ctd_neighbors_noalloc": ([I64, P, P, D, D, P, P, P, I64, P, P], ctypes.c_int),
         "ctd_last_error": ([P], ctypes.c_char_p),
         "ctd_destroy": ([P], None),
@@ -171,6 +173,10 @@ def ctd_profile_read(ctx, reset: bool = True):
     ln = (ctypes.c_int64 * CTD_NSTAGES)()
     check(ctx, load().ctd_profile_read(ctx, ms, ln, 1 if reset else 0))
     return {s: (ms[k], ln[k]) for k, s in enumerate(STAGES)}
+
+
+def ctd_gemm_bf16(ctx, M, N, K, a_ptr, lda, b_ptr, c_ptr, ldc):
+    return check(ctx, load().ctd_gemm_bf16(ctx, M, N, K, a_ptr, lda, b_ptr, c_ptr, ldc))
 
 
 def ctd_neighbors_noalloc(n, positions_ptr, cell_ptr, cutoff, skin, i_ptr, j_ptr, shift_ptr, cap,

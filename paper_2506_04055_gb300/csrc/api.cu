@@ -635,6 +635,26 @@ int ctd_profile_read(ctd_ctx* c, double* ms, int64_t* launches, int32_t reset) {
   return CTD_OK;
 }
 
+int ctd_gemm_bf16(ctd_ctx* c, int64_t M, int32_t N, int32_t K, const void* A, int64_t lda, const void* B,
+                  float* C, int64_t ldc) {
+  if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
+  if (M < 0 || !gemm_bf16_supported(N, K) || (M > 0 && (!A || !B || !C)) || lda < K || ldc < N || ldc % 4)
+    return fail(c, CTD_ERR_INVALID_ARG, "gemm: K must be a multiple of 64, N of 32 (<= 512)");
+  ENSURE(c, c->status, sizeof(int32_t) * 4);
+  CUDA_OK(c, cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), c->st));
+  int r = gemm_bf16<0>(c->st, M, N, K, static_cast<const __nv_bfloat16*>(A), lda,
+                       static_cast<const __nv_bfloat16*>(B), nullptr, nullptr, 0, C, (int)ldc, nullptr, 0,
+                       P<int>(c->status));
+  if (r) return fail(c, CTD_ERR_INVALID_ARG, "gemm: unsupported shape or alignment");
+  CUDA_OK(c, cudaGetLastError());
+  int st = 0;
+  CUDA_OK(c, cudaMemcpyAsync(&st, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  if (st & ST_TIMEOUT) return fail(c, CTD_ERR_TIMEOUT, "gemm: a bounded device wait gave up");
+  return CTD_OK;
+}
+
 int ctd_set_energy_out(ctd_ctx* c, double* energies) {
   if (!c) return CTD_ERR_INVALID_ARG;
   c->energy_out_user = energies;

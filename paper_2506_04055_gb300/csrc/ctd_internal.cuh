@@ -59,6 +59,7 @@ enum Status : int {
   ST_REV_MISSING = 1,     // a reverse edge was not found
   ST_VERLET_OVERFLOW = 2, // more Verlet edges than capacity
   ST_NONFINITE = 4,
+  ST_TIMEOUT = 8,         // a bounded device wait gave up
 };
 
 // FP32 weights of one interaction layer (device pointers).  "t" = transposed ([in][out]).
@@ -125,6 +126,13 @@ void launch_scatter_rows_d(cudaStream_t st, int64_t n, int w, const int32_t* per
 void launch_gather_rows_d(cudaStream_t st, int64_t n, int w, const int32_t* perm, const double* in, double* out);
 void launch_gather_i32(cudaStream_t st, int64_t n, const int32_t* perm, const int32_t* in, int32_t* out);
 void launch_check_finite(cudaStream_t st, int64_t n, const double* a, int* status);
+// gemm_bf16.cu: C[M][N] = A[M][K] . W[N][K]^T on tcgen05 (BF16 in, FP32 accumulate), epilogue
+// EPI 0 bias, 1 bias + SiLU (bf16 copy gets the SiLU), 2 + aux, 3 * SiLU'(aux).
+bool gemm_bf16_supported(int N, int K);
+template <int EPI>
+int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, int64_t lda,
+              const __nv_bfloat16* W, const float* bias, const float* aux, int ldaux, float* out, int ldo,
+              __nv_bfloat16* outb, int ldob, int* status);
 // model_fp32.cu
 int model_buffer_count();
 int64_t model_buffer_floats_per_atom(int b, int F, int T);
