@@ -48,7 +48,8 @@ extern "C" {
 
 /* ---- precision of the dense contractions ----------------------------------------------- */
 #define CTD_PREC_FP32 0   /* every product in FP32 on CUDA cores                              */
-#define CTD_PREC_BF16 1   /* filter / message / update MLPs in BF16 on tcgen05, FP32 accum    */
+#define CTD_PREC_BF16 1   /* filter / message / update MLPs in BF16 on tcgen05, FP32 accum;
+                             F must be 64 or 128                                             */
 
 /* ---- flags for ctd_compute ---------------------------------------------------------------- */
 #define CTD_NEED_FORCES 1      /* write forces[n][3]                                          */

@@ -29,7 +29,16 @@ struct DBuf {
 constexpr int kPartials = 152 * 4;   // fixed block count of the reductions (deterministic)
 
 // The tensor-core path is compiled in only when its kernels exist in this build.
-bool bf16_available() { return false; }
+bool bf16_available() { return true; }
+
+// Host float -> bf16, round to nearest even (NaN kept quiet).
+uint16_t to_bf16_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
 
 }  // namespace
 
@@ -45,7 +54,7 @@ struct ctd_ctx {
   // parameters
   bool have_params = false;
   double eps = 1e-8, e_scale = 1.0;
-  DBuf params;
+  DBuf params, params_bf;
   ModelW mw{};
 
   // neighbour state
@@ -62,7 +71,7 @@ struct ctd_ctx {
   DBuf xw_s, xref_s, z_s, x_s, count, vrow, vcol, vimg, vbase, vrev, v2a, status, delta, maxd;
   DBuf acount, arow, acol, ar, vidx, arev, hedge, force_s, eatom, epart, vpart, kpart, scan_tmp;
   DBuf out_e, out_f, out_w, out_eatom;
-  std::vector<DBuf> mbuf;
+  std::vector<DBuf> mbuf, mbufb;
   double* energy_out_user = nullptr;
 
   ProfState prof;
@@ -72,7 +81,7 @@ struct ctd_ctx {
   DBuf md_v, md_m, md_x_user, md_v_user, md_ep, md_ek, md_tmp;
 
   ctd_ctx() {
-    DBuf* list[] = {&params, &x_user, &z_user, &xw, &wrapm, &cellid, &cell_count, &cell_start, &cursor,
+    DBuf* list[] = {&params, &params_bf, &x_user, &z_user, &xw, &wrapm, &cellid, &cell_count, &cell_start, &cursor,
                     &tmp_idx, &perm, &inv_perm, &xw_s, &xref_s, &z_s, &x_s, &count, &vrow, &vcol, &vimg,
                     &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev,
                     &hedge, &force_s, &eatom, &epart, &vpart, &kpart, &scan_tmp, &out_e, &out_f, &out_w,
@@ -197,6 +206,7 @@ int check_status(ctd_ctx* c) {
   CUDA_OK(c, cudaStreamSynchronize(c->st));
   if (st & ST_REV_MISSING) return fail(c, CTD_ERR_CAPACITY, "reverse edge missing in the neighbour list");
   if (st & ST_NONFINITE) return fail(c, CTD_ERR_NONFINITE, "non-finite value in positions or results");
+  if (st & ST_TIMEOUT) return fail(c, CTD_ERR_TIMEOUT, "a bounded device wait gave up");
   return CTD_OK;
 }
 
@@ -333,10 +343,27 @@ int evaluate(ctd_ctx* c, bool need_grad) {
   ENSURE(c, c->out_e, sizeof(double) * 4);
   ENSURE(c, c->out_w, sizeof(double) * 9);
   if (T == 0) CUDA_OK(c, cudaMemsetAsync(c->hedge.p, 0, sizeof(float4) * e1, st));
-  model_forward_backward_fp32(st, c->mw, n, P<int32_t>(c->z_s), P<int32_t>(c->arow), P<int32_t>(c->acol),
-                              P<float4>(c->ar), P<int32_t>(c->arev), ptrs.data(), need_grad, P<double>(c->epart),
-                              kPartials, P<float4>(c->hedge), P<float>(c->force_s), P<double>(c->vpart),
-                              kPartials, P<float>(c->eatom), P<int>(c->status));
+  if (c->desc.precision == CTD_PREC_BF16) {
+    const int nbb = model_bf16_buffer_count();
+    if ((int)c->mbufb.size() < nbb) c->mbufb.resize(nbb);
+    std::vector<__nv_bfloat16*> bptrs(nbb, nullptr);
+    for (int b = 0; b < nbb; ++b) {
+      int64_t per = model_bf16_buffer_elems_per_atom(b, F, T);
+      if (per == 0) continue;
+      ENSURE(c, c->mbufb[b], sizeof(__nv_bfloat16) * (size_t)per * (size_t)n1);
+      bptrs[b] = P<__nv_bfloat16>(c->mbufb[b]);
+    }
+    int bad = model_forward_backward_bf16(st, c->mw, n, P<int32_t>(c->z_s), P<int32_t>(c->arow), P<int32_t>(c->acol),
+                                          P<float4>(c->ar), P<int32_t>(c->arev), ptrs.data(), bptrs.data(), need_grad,
+                                          P<double>(c->epart), kPartials, P<float4>(c->hedge), P<float>(c->force_s),
+                                          P<double>(c->vpart), kPartials, P<float>(c->eatom), P<int>(c->status));
+    if (bad) return fail(c, CTD_ERR_INVALID_ARG, "BF16 path: unsupported GEMM shape");
+  } else {
+    model_forward_backward_fp32(st, c->mw, n, P<int32_t>(c->z_s), P<int32_t>(c->arow), P<int32_t>(c->acol),
+                                P<float4>(c->ar), P<int32_t>(c->arev), ptrs.data(), need_grad, P<double>(c->epart),
+                                kPartials, P<float4>(c->hedge), P<float>(c->force_s), P<double>(c->vpart),
+                                kPartials, P<float>(c->eatom), P<int>(c->status));
+  }
   StageGuard sg(STG_FORCES);
   launch_sum_partials(st, kPartials, 1, P<double>(c->epart), P<double>(c->out_e), 1.0);
   if (need_grad) launch_sum_partials(st, kPartials, 9, P<double>(c->vpart), P<double>(c->out_w), 1.0);
@@ -401,7 +428,7 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
   // host staging of every FP32 array, 16-byte aligned offsets
   std::vector<float> h;
   auto alloc = [&](size_t cnt) {
-    size_t off = (h.size() + 3) / 4 * 4;
+    size_t off = (h.size() + 7) / 8 * 8;   // 32 B: the BF16 twin of every array is 16-byte aligned
     h.resize(off + cnt, 0.0f);
     return off;
   };
@@ -472,7 +499,13 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
   size_t o_d2 = put(take(1), 1, 1, false);
   ENSURE(c, c->params, h.size() * sizeof(float));
   CUDA_OK(c, cudaMemcpyAsync(c->params.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  // BF16 twin: element k of the BF16 buffer is element k of the FP32 buffer, rounded
+  std::vector<uint16_t> hb(h.size());
+  for (size_t k = 0; k < h.size(); ++k) hb[k] = to_bf16_bits(h[k]);
+  ENSURE(c, c->params_bf, hb.size() * sizeof(uint16_t));
+  CUDA_OK(c, cudaMemcpyAsync(c->params_bf.p, hb.data(), hb.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
+  const __nv_bfloat16* bbase = P<__nv_bfloat16>(c->params_bf);
   const float* base = P<float>(c->params);
   ModelW& m = c->mw;
   m.F = F; m.K = K; m.KP = KP; m.T = T; m.S = S;
@@ -487,8 +520,12 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
     L.UV = base + o.UV; L.UVt = base + o.UVt;
     L.A1 = base + o.A1; L.A1t = base + o.A1t; L.c1 = base + o.c1;
     L.A2 = base + o.A2; L.A2t = base + o.A2t; L.c2 = base + o.c2;
+    L.W1b = bbase + o.W1; L.W1tb = bbase + o.W1t; L.W2b = bbase + o.W2; L.W2tb = bbase + o.W2t;
+    L.UVb = bbase + o.UV; L.UVtb = bbase + o.UVt; L.A1b = bbase + o.A1; L.A1tb = bbase + o.A1t;
+    L.A2b = bbase + o.A2; L.A2tb = bbase + o.A2t;
   }
   m.R1 = base + o_R1; m.R1t = base + o_R1t; m.d1 = base + o_d1; m.R2 = base + o_R2; m.d2 = base + o_d2;
+  m.R1b = bbase + o_R1; m.R1tb = bbase + o_R1t;
   c->eps = eps;
   c->e_scale = esc;
   c->have_params = true;
@@ -508,7 +545,8 @@ int ctd_create(ctd_ctx** out, const ctd_model_desc* desc, size_t hbm_budget_byte
       desc->T > kMaxT || desc->n_species < 1 || !(desc->rc > 0.0) ||
       (desc->precision != CTD_PREC_FP32 && desc->precision != CTD_PREC_BF16))
     return CTD_ERR_INVALID_ARG;
-  if (desc->precision == CTD_PREC_BF16 && !bf16_available()) return CTD_ERR_INVALID_ARG;
+  if (desc->precision == CTD_PREC_BF16 && (!bf16_available() || !(F == 64 || F == 128)))
+    return CTD_ERR_INVALID_ARG;
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
     cudaGetLastError();
@@ -538,6 +576,8 @@ void ctd_destroy(ctd_ctx* c) {
   for (DBuf* b : c->all)
     if (b->p) cudaFree(b->p);
   for (DBuf& b : c->mbuf)
+    if (b.p) cudaFree(b.p);
+  for (DBuf& b : c->mbufb)
     if (b.p) cudaFree(b.p);
   if (c->own_stream) cudaStreamDestroy(c->st);
   delete c;
@@ -826,6 +866,8 @@ int ctd_md_run(ctd_ctx* c, int32_t nsteps, double dt, double* epot, double* ekin
   ENSURE(c, c->kpart, sizeof(double) * kPartials);
   int32_t rebuilds = 0;
   int r;
+  ENSURE(c, c->status, sizeof(int32_t) * 4);
+  CUDA_OK(c, cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), st));
   if (!c->md_forces_valid) {
     r = md_forces(c, &rebuilds);
     if (r) return r;
@@ -848,7 +890,8 @@ int ctd_md_run(ctd_ctx* c, int32_t nsteps, double dt, double* epot, double* ekin
   CUDA_OK(c, cudaGetLastError());
   if (epot) CUDA_OK(c, cudaMemcpyAsync(epot, c->md_ep.p, sizeof(double) * (nsteps + 1), cudaMemcpyDeviceToHost, st));
   if (ekin) CUDA_OK(c, cudaMemcpyAsync(ekin, c->md_ek.p, sizeof(double) * (nsteps + 1), cudaMemcpyDeviceToHost, st));
-  CUDA_OK(c, cudaStreamSynchronize(st));
+  r = check_status(c);
+  if (r) return r;
   if (n_rebuilds) *n_rebuilds = rebuilds;
   return CTD_OK;
 }

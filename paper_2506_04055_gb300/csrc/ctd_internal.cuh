@@ -70,6 +70,8 @@ struct LayerW {
   const float *UV, *UVt;           // [2F][F] = [U;V], [F][2F] = [U^T | V^T]
   const float *A1, *A1t, *c1;      // [F][2F], [2F][F]
   const float *A2, *A2t, *c2;      // [3F][F], [F][3F]
+  // BF16 copies for the tensor-core path (same shapes as the FP32 arrays above)
+  const __nv_bfloat16 *W1b, *W1tb, *W2b, *W2tb, *UVb, *UVtb, *A1b, *A1tb, *A2b, *A2tb;
 };
 
 struct ModelW {
@@ -78,6 +80,7 @@ struct ModelW {
   const float* emb;                // [S][F]
   LayerW L[kMaxT];
   const float *R1, *R1t, *d1, *R2, *d2;   // [F/2][F], [F][F/2]
+  const __nv_bfloat16 *R1b, *R1tb;
 };
 
 // ---------------------------------------------------------------- small device helpers
@@ -136,6 +139,13 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, 
 // model_fp32.cu
 int model_buffer_count();
 int64_t model_buffer_floats_per_atom(int b, int F, int T);
+int model_bf16_buffer_count();
+int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T);
+int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
+                                const int32_t* arow, const int32_t* acol, const float4* ar, const int32_t* arev,
+                                float* const* bufs, __nv_bfloat16* const* bbufs, bool need_grad,
+                                double* energy_partials, int n_energy_partials, float4* hedge, float* force_s,
+                                double* virial_partials, int n_virial_partials, float* e_atom, int* status);
 void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
                                  const int32_t* arow, const int32_t* acol, const float4* ar,
                                  const int32_t* arev, float* const* bufs, bool need_grad,

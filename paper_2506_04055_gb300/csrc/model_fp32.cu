@@ -119,12 +119,13 @@ static void gemm(cudaStream_t st, int64_t M, int N, int K, const float* A, int l
 
 // ================================================================================ node kernels
 __global__ void k_embed(int64_t n, int F, const int32_t* __restrict__ Z, const float* __restrict__ emb,
-                        float* __restrict__ S, float* __restrict__ V) {
+                        float* __restrict__ S, float* __restrict__ V, __nv_bfloat16* __restrict__ Sb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
   int f = (int)(idx % F);
   S[idx] = emb[(int64_t)Z[i] * F + f];
+  if (Sb) Sb[idx] = __float2bfloat16_rn(S[idx]);
   V[i * 3 * F + f] = 0.0f;
   V[i * 3 * F + F + f] = 0.0f;
   V[i * 3 * F + 2 * F + f] = 0.0f;
@@ -151,21 +152,26 @@ __global__ void k_phi_pack(int64_t n, int F, const float* __restrict__ P3, const
 
 // Z = [s^m ; sqrt(sum_a Vv_a^2 + eps)], UV rows (i, a) = [Uv_a | Vv_a]
 __global__ void k_update_pre(int64_t n, int F, float eps, const float* __restrict__ SM,
-                             const float* __restrict__ UV, float* __restrict__ Z) {
+                             const float* __restrict__ UV, float* __restrict__ Z, __nv_bfloat16* __restrict__ Zb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
   int f = (int)(idx % F);
   const float* uv = UV + i * 3 * 2 * F;
   float v0 = uv[F + f], v1 = uv[2 * F + F + f], v2 = uv[4 * F + F + f];
+  const float nv = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
   Z[i * 2 * F + f] = SM[idx];
-  Z[i * 2 * F + F + f] = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
+  Z[i * 2 * F + F + f] = nv;
+  if (Zb) {
+    Zb[i * 2 * F + f] = __float2bfloat16_rn(SM[idx]);
+    Zb[i * 2 * F + F + f] = __float2bfloat16_rn(nv);
+  }
 }
 
 // s' = s^m + a_ss + a_sv <Uv, Vv>,  v'_a = v^m_a + a_vv Uv_a
 __global__ void k_update_post(int64_t n, int F, const float* __restrict__ SM, const float* __restrict__ VM,
                               const float* __restrict__ UV, const float* __restrict__ AV,
-                              float* __restrict__ Sn, float* __restrict__ Vn) {
+                              float* __restrict__ Sn, float* __restrict__ Vn, __nv_bfloat16* __restrict__ Snb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
@@ -179,7 +185,9 @@ __global__ void k_update_post(int64_t n, int F, const float* __restrict__ SM, co
     sp += u * v;
     Vn[i * 3 * F + al * F + f] = VM[i * 3 * F + al * F + f] + a[f] * u;
   }
-  Sn[idx] = SM[idx] + a[2 * F + f] + a[F + f] * sp;
+  const float snew = SM[idx] + a[2 * F + f] + a[F + f] * sp;
+  Sn[idx] = snew;
+  if (Snb) Snb[idx] = __float2bfloat16_rn(snew);
 }
 
 // Backward of the update elementwise part: given gs' (GS), gv' (GV):
@@ -187,7 +195,7 @@ __global__ void k_update_post(int64_t n, int F, const float* __restrict__ SM, co
 //   gVv_a = gs' a_sv Uv_a (the |Vv| term is added after the A1 backward)
 __global__ void k_update_bwd_pre(int64_t n, int F, const float* __restrict__ GS, const float* __restrict__ GV,
                                  const float* __restrict__ UV, const float* __restrict__ AV,
-                                 float* __restrict__ GA, float* __restrict__ GUV) {
+                                 float* __restrict__ GA, float* __restrict__ GUV, __nv_bfloat16* __restrict__ GAb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
@@ -208,12 +216,17 @@ __global__ void k_update_bwd_pre(int64_t n, int F, const float* __restrict__ GS,
   GA[i * 3 * F + f] = gavv;
   GA[i * 3 * F + F + f] = gs * sp;
   GA[i * 3 * F + 2 * F + f] = gs;
+  if (GAb) {
+    GAb[i * 3 * F + f] = __float2bfloat16_rn(gavv);
+    GAb[i * 3 * F + F + f] = __float2bfloat16_rn(gs * sp);
+    GAb[i * 3 * F + 2 * F + f] = __float2bfloat16_rn(gs);
+  }
 }
 
 // gz = [gz_s | gz_n] (grad of [s^m ; |Vv|]):  gsm = gs' + gz_s;  gVv_a += gz_n Vv_a / |Vv|
 __global__ void k_update_bwd_mid(int64_t n, int F, float eps, const float* __restrict__ GS,
                                  const float* __restrict__ GZ, const float* __restrict__ UV,
-                                 float* __restrict__ Gsm, float* __restrict__ GUV) {
+                                 float* __restrict__ Gsm, float* __restrict__ GUV, __nv_bfloat16* __restrict__ GUVb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
@@ -226,13 +239,17 @@ __global__ void k_update_bwd_mid(int64_t n, int F, float eps, const float* __res
   GUV[i * 6 * F + F + f] += g * v0;
   GUV[i * 6 * F + 3 * F + f] += g * v1;
   GUV[i * 6 * F + 5 * F + f] += g * v2;
+  if (GUVb) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) GUVb[i * 6 * F + q * F + f] = __float2bfloat16_rn(GUV[i * 6 * F + q * F + f]);
+  }
 }
 
 // Backward of PHI packing: gphi_vv = sum_a gpsi_a v_a, gv_a = gvm_a + gpsi_a phi_vv;
 // GP3 = [gphi_s | gphi_vv | gphi_vs]
 __global__ void k_phi_bwd_pre(int64_t n, int F, const float* __restrict__ GPHI, const float* __restrict__ PHI,
                               const float* __restrict__ V, const float* __restrict__ Gvm,
-                              float* __restrict__ GP3, float* __restrict__ GVn) {
+                              float* __restrict__ GP3, float* __restrict__ GVn, __nv_bfloat16* __restrict__ GP3b) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
@@ -249,6 +266,11 @@ __global__ void k_phi_bwd_pre(int64_t n, int F, const float* __restrict__ GPHI, 
   GP3[i * 3 * F + f] = g[f];
   GP3[i * 3 * F + F + f] = gpvv;
   GP3[i * 3 * F + 2 * F + f] = g[4 * F + f];
+  if (GP3b) {
+    GP3b[i * 3 * F + f] = __float2bfloat16_rn(g[f]);
+    GP3b[i * 3 * F + F + f] = __float2bfloat16_rn(gpvv);
+    GP3b[i * 3 * F + 2 * F + f] = __float2bfloat16_rn(g[4 * F + f]);
+  }
 }
 
 // ================================================================================ edge kernels
@@ -265,7 +287,8 @@ __global__ __launch_bounds__(256) void k_edge_fwd(int64_t n, int F, int K, float
                                                   const float4* __restrict__ ar, const float* __restrict__ PHI,
                                                   const float* __restrict__ S, const float* __restrict__ V,
                                                   const float* __restrict__ Wf, const float* __restrict__ bf,
-                                                  float* __restrict__ SM, float* __restrict__ VM) {
+                                                  float* __restrict__ SM, float* __restrict__ VM,
+                                                  __nv_bfloat16* __restrict__ VMb) {
   extern __shared__ __align__(16) float sm[];
   const int G = blockDim.x / F;                 // groups per block
   const int g = threadIdx.x / F, f = threadIdx.x % F;
@@ -331,6 +354,11 @@ __global__ __launch_bounds__(256) void k_edge_fwd(int64_t n, int F, int K, float
     VM[i * 3 * F + f] = V[i * 3 * F + f] + av0;
     VM[i * 3 * F + F + f] = V[i * 3 * F + F + f] + av1;
     VM[i * 3 * F + 2 * F + f] = V[i * 3 * F + 2 * F + f] + av2;
+    if (VMb) {
+      VMb[i * 3 * F + f] = __float2bfloat16_rn(VM[i * 3 * F + f]);
+      VMb[i * 3 * F + F + f] = __float2bfloat16_rn(VM[i * 3 * F + F + f]);
+      VMb[i * 3 * F + 2 * F + f] = __float2bfloat16_rn(VM[i * 3 * F + 2 * F + f]);
+    }
   }
 }
 
@@ -484,7 +512,8 @@ __global__ __launch_bounds__(256) void k_edge_bwd(int64_t n, int F, int K, float
 // G3 = e_scale R2 * silu'(h3) (seed of the backward pass); per-block FP64 energy partials.
 __global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restrict__ H3,
                           const float* __restrict__ R2, const float* __restrict__ d2,
-                          float* __restrict__ G3, float* __restrict__ e_atom, double* __restrict__ partials) {
+                          float* __restrict__ G3, __nv_bfloat16* __restrict__ G3b, float* __restrict__ e_atom,
+                          double* __restrict__ partials) {
   __shared__ double sbuf[kThreads / 32];
   double acc = 0.0, comp = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -492,7 +521,11 @@ __global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restr
     for (int k = 0; k < Fh; ++k) {
       float h = H3[i * Fh + k];
       e = fmaf(R2[k], silu_f(h), e);
-      if (G3) G3[i * Fh + k] = e_scale * R2[k] * dsilu_f(h);
+      if (G3) {
+        const float gk = e_scale * R2[k] * dsilu_f(h);
+        G3[i * Fh + k] = gk;
+        if (G3b) G3b[i * Fh + k] = __float2bfloat16_rn(gk);
+      }
     }
     e *= e_scale;
     if (e_atom) e_atom[i] = e;
@@ -565,14 +598,14 @@ static inline unsigned blocks_for(int64_t work) { return (unsigned)((work + kThr
 template <int KP>
 static void edge_fwd_kp(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow,
                         const int32_t* acol, const float4* ar, const float* PHI, const float* S, const float* V,
-                        float* SM, float* VM) {
+                        float* SM, float* VM, __nv_bfloat16* VMb) {
   const int F = m.F, G = kThreads / F;
   size_t smem = (size_t)G * F * (KP + 4) * sizeof(float) + (size_t)G * F * sizeof(int);
   int64_t blocks = (n + G - 1) / G;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   { LaunchScope ls_(st); k_edge_fwd<KP><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, arow, acol, ar, PHI, S, V,
-                                                           m.L[t].Wf, m.L[t].bf, SM, VM); }
+                                                           m.L[t].Wf, m.L[t].bf, SM, VM, VMb); }
 }
 
 template <int KP>
@@ -667,7 +700,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
   StageGuard node_stage(STG_NODE);
   const int F = m.F, T = m.T, Fh = F / 2;
   const unsigned nb = blocks_for(n * F);
-  if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0]); }
+  if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], nullptr); }
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
     float *S = B[B_S0 + t], *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
@@ -678,7 +711,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     gemm<EPI_BIAS>(st, n, 3 * F, F, T1, F, L.W2t, L.b2, nullptr, 0, T2, 3 * F);
     if (n > 0) { LaunchScope ls_(st); k_phi_pack<<<nb, kThreads, 0, st>>>(n, F, T2, V, PHI); }
     // message
-#define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM)
+#define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, nullptr)
     if (n > 0) {
       StageGuard sg(STG_EDGE_FWD);
       CTD_KP_DISPATCH(m.KP, CTD_FWD)
@@ -686,15 +719,15 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
 #undef CTD_FWD
     // update
     gemm<EPI_BIAS>(st, 3 * n, 2 * F, F, VM, F, L.UVt, nullptr, nullptr, 0, UV, 2 * F);
-    if (n > 0) { LaunchScope ls_(st); k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1); }
+    if (n > 0) { LaunchScope ls_(st); k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1, nullptr); }
     gemm<EPI_BIAS_SILU>(st, n, F, 2 * F, T1, 2 * F, L.A1t, L.c1, nullptr, 0, H2, F, T2, F);
     gemm<EPI_BIAS>(st, n, 3 * F, F, T2, F, L.A2t, L.c2, nullptr, 0, AV, 3 * F);
-    if (n > 0) { LaunchScope ls_(st); k_update_post<<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1]); }
+    if (n > 0) { LaunchScope ls_(st); k_update_post<<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1], nullptr); }
   }
   // readout
   gemm<EPI_BIAS>(st, n, Fh, F, B[B_S0 + T], F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
   { LaunchScope ls_(st); k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2,
-                                                    need_grad ? B[B_G3] : nullptr, e_atom, energy_partials); }
+                                                    need_grad ? B[B_G3] : nullptr, nullptr, e_atom, energy_partials); }
   if (!need_grad) return;
   // dU/ds^T = G3 R1
   gemm<EPI_BIAS>(st, n, F, Fh, B[B_G3], Fh, m.R1, nullptr, nullptr, 0, B[B_GS], F);
@@ -706,10 +739,10 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     float *T1 = B[B_T1], *T2 = B[B_T2], *T3 = B[B_T3];
     float *GS = B[B_GS], *GV = B[B_GV], *GSM = B[B_GSM], *GVM = B[B_GVM], *GPHI = B[B_GPHI];
     // update backward
-    if (n > 0) { LaunchScope ls_(st); k_update_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, T1, T3); }
+    if (n > 0) { LaunchScope ls_(st); k_update_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, T1, T3, nullptr); }
     gemm<EPI_DSILU>(st, n, F, 3 * F, T1, 3 * F, L.A2, nullptr, H2, F, T2, F);          // gh2
     gemm<EPI_BIAS>(st, n, 2 * F, F, T2, F, L.A1, nullptr, nullptr, 0, T1, 2 * F);       // gz
-    if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, GSM, T3); }
+    if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, GSM, T3, nullptr); }
     gemm<EPI_ADD>(st, 3 * n, F, 2 * F, T3, 2 * F, L.UV, nullptr, GV, F, GVM, F);         // gvm
     // message backward
 #define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge)
@@ -719,12 +752,116 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     }
 #undef CTD_BWD
     // phi backward -> gradients w.r.t. the layer input (s_t, v_t)
-    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV); }
+    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV, nullptr); }
     gemm<EPI_DSILU>(st, n, F, 3 * F, T2, 3 * F, L.W2, nullptr, H1, F, T1, F);          // gh1
     gemm<EPI_ADD>(st, n, F, F, T1, F, L.W1, nullptr, GSM, F, GS, F);                    // gs
   }
   StageGuard fstage(STG_FORCES);
   { LaunchScope ls_(st); k_forces<<<n_virial_partials, kThreads, 0, st>>>(n, arow, ar, arev, hedge, force_s, virial_partials, status); }
+}
+
+
+// ================================================================================ BF16 driver
+// Same layer as above; every node MLP contraction runs on tcgen05 with BF16 operands and FP32
+// accumulation (gemm_bf16.cu).  Producers write a BF16 shadow of each GEMM A operand; all
+// elementwise work, the edge kernels, the reductions and the stored activations stay FP32.
+enum BufB {
+  BB_S0 = 0,                 // bf16 S[t], t = 0..T    [n][F]
+  BB_A1 = BB_S0 + kMaxT + 1, // silu(h1)               [n][F]
+  BB_VM,                     // v^m                    [n][3F]
+  BB_Z,                      // [s^m ; |Vv|]           [n][2F]
+  BB_A2,                     // silu(h2)               [n][F]
+  BB_GA,                     // g_a                    [n][3F]
+  BB_GH2,                    // g_h2                   [n][F]
+  BB_GUV,                    // [gUv | gVv]            [3n][2F]
+  BB_GP3,                    // g_phi                  [n][3F]
+  BB_GH1,                    // g_h1                   [n][F]
+  BB_COUNT
+};
+
+int model_bf16_buffer_count() { return BB_COUNT; }
+
+int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T) {
+  if (b >= BB_S0 && b < BB_S0 + T + 1) return F;
+  switch (b) {
+    case BB_A1: case BB_A2: case BB_GH2: case BB_GH1: return F;
+    case BB_VM: case BB_GA: case BB_GP3: return 3 * F;
+    case BB_Z: return 2 * F;
+    case BB_GUV: return 6 * F;
+    default: return 0;
+  }
+}
+
+int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
+                                const int32_t* arow, const int32_t* acol, const float4* ar, const int32_t* arev,
+                                float* const* B, __nv_bfloat16* const* Bb, bool need_grad,
+                                double* energy_partials, int n_energy_partials, float4* hedge, float* force_s,
+                                double* virial_partials, int n_virial_partials, float* e_atom, int* status) {
+  edge_smem_setup();
+  StageGuard node_stage(STG_NODE);
+  const int F = m.F, T = m.T, Fh = F / 2;
+  const unsigned nb = blocks_for(n * F);
+  int bad = 0;
+  if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], Bb[BB_S0]); }
+  for (int t = 0; t < T; ++t) {
+    const LayerW& L = m.L[t];
+    float *S = B[B_S0 + t], *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
+    float *SM = B[B_SM0 + t], *VM = B[B_VM0 + t], *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
+    float *T1 = B[B_T1], *T2 = B[B_T2];
+    bad |= gemm_bf16<1>(st, n, F, F, Bb[BB_S0 + t], F, L.W1b, L.b1, nullptr, 0, H1, F, Bb[BB_A1], F, status);
+    bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, nullptr, 0, T2, 3 * F, nullptr, 0, status);
+    if (n > 0) { LaunchScope ls_(st); k_phi_pack<<<nb, kThreads, 0, st>>>(n, F, T2, V, PHI); }
+#define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM])
+    if (n > 0) {
+      StageGuard sg(STG_EDGE_FWD);
+      CTD_KP_DISPATCH(m.KP, CTD_FWD)
+    }
+#undef CTD_FWD
+    bad |= gemm_bf16<0>(st, 3 * n, 2 * F, F, Bb[BB_VM], F, L.UVb, nullptr, nullptr, 0, UV, 2 * F, nullptr, 0, status);
+    if (n > 0) { LaunchScope ls_(st); k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1, Bb[BB_Z]); }
+    bad |= gemm_bf16<1>(st, n, F, 2 * F, Bb[BB_Z], 2 * F, L.A1b, L.c1, nullptr, 0, H2, F, Bb[BB_A2], F, status);
+    bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A2], F, L.A2b, L.c2, nullptr, 0, AV, 3 * F, nullptr, 0, status);
+    if (n > 0) {
+      LaunchScope ls_(st);
+      k_update_post<<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1], Bb[BB_S0 + t + 1]);
+    }
+  }
+  // The readout MLP (F -> F/2 -> 1, ~1 % of the node FLOPs) stays in FP32: its output is the
+  // per-atom energy itself, which BF16 operands would perturb by ~2^-9 of the readout terms.
+  gemm<EPI_BIAS>(st, n, Fh, F, B[B_S0 + T], F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
+  {
+    LaunchScope ls_(st);
+    k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2,
+                                                      need_grad ? B[B_G3] : nullptr, nullptr, e_atom,
+                                                      energy_partials);
+  }
+  if (!need_grad) return bad;
+  gemm<EPI_BIAS>(st, n, F, Fh, B[B_G3], Fh, m.R1, nullptr, nullptr, 0, B[B_GS], F);
+  if (n > 0) cudaMemsetAsync(B[B_GV], 0, sizeof(float) * (size_t)n * 3 * F, st);
+  for (int t = T - 1; t >= 0; --t) {
+    const LayerW& L = m.L[t];
+    float *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
+    float *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
+    float *T1 = B[B_T1], *T2 = B[B_T2], *T3 = B[B_T3];
+    float *GS = B[B_GS], *GV = B[B_GV], *GSM = B[B_GSM], *GVM = B[B_GVM], *GPHI = B[B_GPHI];
+    if (n > 0) { LaunchScope ls_(st); k_update_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, T1, T3, Bb[BB_GA]); }
+    bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GA], 3 * F, L.A2tb, nullptr, H2, F, nullptr, 0, Bb[BB_GH2], F, status);
+    bad |= gemm_bf16<0>(st, n, 2 * F, F, Bb[BB_GH2], F, L.A1tb, nullptr, nullptr, 0, T1, 2 * F, nullptr, 0, status);
+    if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, GSM, T3, Bb[BB_GUV]); }
+    bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
+#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge)
+    if (n > 0) {
+      StageGuard sg(STG_EDGE_BWD);
+      CTD_KP_DISPATCH(m.KP, CTD_BWD)
+    }
+#undef CTD_BWD
+    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV, Bb[BB_GP3]); }
+    bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GP3], 3 * F, L.W2tb, nullptr, H1, F, nullptr, 0, Bb[BB_GH1], F, status);
+    bad |= gemm_bf16<2>(st, n, F, F, Bb[BB_GH1], F, L.W1tb, nullptr, GSM, F, GS, F, nullptr, 0, status);
+  }
+  StageGuard fstage(STG_FORCES);
+  { LaunchScope ls_(st); k_forces<<<n_virial_partials, kThreads, 0, st>>>(n, arow, ar, arev, hedge, force_s, virial_partials, status); }
+  return bad;
 }
 
 }  // namespace ctd

@@ -1,0 +1,70 @@
+"""BF16 path (tcgen05 MLPs, FP32 accumulation and elementwise, FP64 reductions) vs the FP64 oracle.
+
+Stated tolerance: relative force RMSE <= 1e-2.  Energy: |dE|/N <= 1e-2 of the RMS per-atom
+energy (the energy error is reported alongside; BF16 operands carry 2^-9 relative rounding)."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from gpu_common import BF16_FORCE_RMSE, compare, engine, model, rel_force_rmse
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(eng, orc, sy, F, T, S, bias=0.1, seed=0):
+    vals, blob = model(F, T, S, seed=seed, bias=bias)
+    with eng.Potential(F, T=T, n_species=S, precision="bf16", params=blob) as pot:
+        out = pot.compute(sy.species, sy.positions, sy.cell, energies=True)
+    ref = orc.painn(vals, F, 20, T, S, sy.species, sy.positions, sy.cell)
+    return out, ref
+
+
+def test_bf16_water192_F64(orc):
+    eng = engine()
+    out, ref = _run(eng, orc, syn.water_box(64, seed=0), 64, 3, 2, bias=0.0)
+    fr, er, wr = compare(out, ref, force_tol=BF16_FORCE_RMSE, e_tol=1e-2, w_tol=2e-2)
+    print(f"bf16 water192: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
+
+
+def test_bf16_fcc4000_F128(orc):
+    """The 10x10x10-cell (4,000-atom) fcc sub-run of the 1M-atom configuration."""
+    eng = engine()
+    out, ref = _run(eng, orc, syn.fcc(10, 10, 10, jitter=0.05, seed=0), 128, 3, 1, bias=0.0)
+    fr, er, wr = compare(out, ref, force_tol=BF16_FORCE_RMSE, e_tol=1e-2, w_tol=2e-2)
+    print(f"bf16 fcc4000: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
+
+
+def test_bf16_mixture_biases(orc):
+    eng = engine()
+    out, ref = _run(eng, orc, syn.mixture(n_chain=30, n_water=150, seed=1), 64, 2, 4, bias=0.2, seed=3)
+    fr, er, wr = compare(out, ref, force_tol=BF16_FORCE_RMSE, e_tol=1e-2, w_tol=2e-2)
+    print(f"bf16 mixture: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
+
+
+def test_bf16_small_cell_and_tails(orc):
+    eng = engine()
+    for sy in (syn.water_box(21, seed=2), syn.fcc(3, 3, 2, jitter=0.1, seed=3)):
+        out, ref = _run(eng, orc, sy, 128, 2, 2, seed=4)
+        fr, er, wr = compare(out, ref, force_tol=BF16_FORCE_RMSE, e_tol=1e-2, w_tol=2e-2)
+        print(f"bf16 {sy.name}: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
+
+
+def test_bf16_vs_fp32_at_1M():
+    """Full 1,000,188-atom fcc workload: BF16 forces within 1e-2 relative RMSE of the FP32 path
+    (which matches the oracle to 1e-5 at every size it is checked)."""
+    eng = engine()
+    sy = syn.fcc(63, 63, 63, jitter=0.05, seed=0)
+    _, blob = model(128, 3, 1, seed=0)
+    outs = {}
+    for prec in ("fp32", "bf16"):
+        with eng.Potential(128, T=3, n_species=1, precision=prec, params=blob) as pot:
+            outs[prec] = pot.compute(sy.species, sy.positions, sy.cell)
+    fr = rel_force_rmse(outs["bf16"]["forces"], outs["fp32"]["forces"])
+    assert fr <= BF16_FORCE_RMSE, fr
+    print(f"bf16 vs fp32 at 1M: force rmse {fr:.2e}")
+
+
+def test_bf16_rejects_unsupported_width():
+    eng = engine()
+    with pytest.raises(eng.CtdError):
+        eng.Potential(32, T=1, n_species=1, precision="bf16")
