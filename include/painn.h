@@ -139,6 +139,13 @@ int ctd_md_run(ctd_ctx *ctx, int32_t nsteps, double dt, double *epot, double *ek
 /* Copy the MD state back (host arrays [n][3], either may be NULL). */
 int ctd_md_get_state(ctd_ctx *ctx, double *positions, double *velocities);
 
+/* ---- options -------------------------------------------------------------------------- */
+/* CTD_OPT_TC_ADJOINT (value 0/1, default 0): on the BF16 path with F = 128, run the edge
+ * adjoint with the radial filter on tcgen05 as well (the message kernel always does).  The
+ * CUDA-core adjoint is the default because it is faster on the 1M-atom fcc workload. */
+#define CTD_OPT_TC_ADJOINT 1
+int ctd_set_option(ctd_ctx *ctx, int32_t option, int64_t value);
+
 /* ---- launch accounting and stage timing (benchmarks, statistics) ------------------------- */
 /* Stages: 0 neighbour build, 1 per-step prune, 2 node MLPs (message phi, update, readout),
  * 3 edge message, 4 edge adjoint, 5 forces / virial / energy reductions, 6 integrator,

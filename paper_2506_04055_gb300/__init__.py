@@ -91,6 +91,9 @@ class Potential:
     def load_params(self, blob: bytes):
         _lib.ctd_load_params(self.ctx, blob)
 
+    def set_option(self, option: int, value: int):
+        _lib.ctd_set_option(self.ctx, option, value)
+
     def build_neighbors(self, positions, cell, cutoff: float | None = None, skin: float = 1.0) -> int:
         cutoff = self.rc if cutoff is None else cutoff
         H = _host(cell, np.float64, (3, 3))

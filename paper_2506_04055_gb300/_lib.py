@@ -40,7 +40,7 @@ ERROR_NAMES = {
 EXPORTS = [
     "ctd_create", "ctd_load_params", "ctd_build_neighbors", "ctd_get_pairs", "ctd_compute",
     "ctd_set_energy_out", "ctd_md_set_state", "ctd_md_run", "ctd_md_get_state",
-    "ctd_profile_enable", "ctd_profile_read", "ctd_gemm_bf16", "ctd_neighbors_noalloc",
+    "ctd_set_option", "ctd_profile_enable", "ctd_profile_read", "ctd_gemm_bf16", "ctd_neighbors_noalloc",
     "ctd_last_error",
     "ctd_destroy",
 ]
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
         "ctd_md_set_state": ([P, I64, P, P, P, P, P, D], ctypes.c_int),
         "ctd_md_run": ([P, I32, D, P, P, P], ctypes.c_int),
         "ctd_md_get_state": ([P, P, P], ctypes.c_int),
+        "ctd_set_option": ([P, I32, I64], ctypes.c_int),
         "ctd_profile_enable": ([P, I32], ctypes.c_int),
         "ctd_profile_read": ([P, P, P, I32], ctypes.c_int),
         "ctd_gemm_bf16": ([P, I64, I32, I32, P, I64, P, P, I64], ctypes.c_int),
@@ -162,6 +163,13 @@ def ctd_md_run(ctx, nsteps, dt, epot_ptr, ekin_ptr):
 
 def ctd_md_get_state(ctx, positions_ptr, velocities_ptr):
     return check(ctx, load().ctd_md_get_state(ctx, positions_ptr, velocities_ptr))
+
+
+CTD_OPT_TC_ADJOINT = 1
+
+
+def ctd_set_option(ctx, option, value):
+    return check(ctx, load().ctd_set_option(ctx, option, value))
 
 
 def ctd_profile_enable(ctx, enable: bool):

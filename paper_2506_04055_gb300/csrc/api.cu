@@ -196,6 +196,16 @@ int setup_geometry(ctd_ctx* c, const double H[9], double R) {
     ncell *= nc;
   }
   g.R2 = R * R;
+  // Morton numbering when the padded 2^b grid stays within 8x the cell count
+  int mx = std::max(g.nc[0], std::max(g.nc[1], g.nc[2]));
+  int bits = 0;
+  while ((1 << bits) < mx) ++bits;
+  const int64_t mcells = (int64_t)1 << (3 * bits);
+  g.morton_bits = 0;
+  if (bits > 0 && bits <= 9 && mcells <= std::max<int64_t>(8 * ncell, 4096)) {
+    g.morton_bits = bits;
+    ncell = mcells;
+  }
   c->ncell = ncell;
   return CTD_OK;
 }
@@ -449,7 +459,7 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
     return off;
   };
   struct Off {
-    size_t W1, W1t, b1, W2, W2t, b2, Wf, bf, UV, UVt, A1, A1t, c1, A2, A2t, c2;
+    size_t W1, W1t, b1, W2, W2t, b2, Wf, Wf64, bf, UV, UVt, A1, A1t, c1, A2, A2t, c2;
   } lo[kMaxT];
   size_t o_emb = put(take((size_t)S * F), S, F, false);
   for (int t = 0; t < T; ++t) {
@@ -475,6 +485,10 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
     o.Wf = alloc((size_t)3 * F * KP);
     for (int r = 0; r < 3 * F; ++r)
       for (int k = 0; k < K; ++k) h[o.Wf + (size_t)r * KP + k] = (float)Wf[(size_t)r * K + k];
+    // [3F][64] zero-padded copy whose BF16 twin is the tensor-core filter operand
+    o.Wf64 = alloc((size_t)3 * F * 64);
+    for (int r = 0; r < 3 * F; ++r)
+      for (int k = 0; k < K && k < 64; ++k) h[o.Wf64 + (size_t)r * 64 + k] = (float)Wf[(size_t)r * K + k];
     o.bf = put(bf, 1, 3 * F, false);
     o.UV = alloc((size_t)2 * F * F);
     o.UVt = alloc((size_t)2 * F * F);
@@ -523,6 +537,7 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
     L.W1b = bbase + o.W1; L.W1tb = bbase + o.W1t; L.W2b = bbase + o.W2; L.W2tb = bbase + o.W2t;
     L.UVb = bbase + o.UV; L.UVtb = bbase + o.UVt; L.A1b = bbase + o.A1; L.A1tb = bbase + o.A1t;
     L.A2b = bbase + o.A2; L.A2tb = bbase + o.A2t;
+    L.Wfb = bbase + o.Wf64;
   }
   m.R1 = base + o_R1; m.R1t = base + o_R1t; m.d1 = base + o_d1; m.R2 = base + o_R2; m.d2 = base + o_d2;
   m.R1b = bbase + o_R1; m.R1tb = bbase + o_R1t;
@@ -652,6 +667,17 @@ int ctd_get_pairs(ctd_ctx* c, int32_t* pi, int32_t* pj, int8_t* shift, int64_t c
     for (int k = 0; k < 3; ++k) shift[3 * e + k] = rec[(size_t)e].s[k];
   }
   return CTD_OK;
+}
+
+int ctd_set_option(ctd_ctx* c, int32_t option, int64_t value) {
+  if (!c) return CTD_ERR_INVALID_ARG;
+  switch (option) {
+    case CTD_OPT_TC_ADJOINT:
+      c->mw.tc_adjoint = value != 0;
+      return CTD_OK;
+    default:
+      return fail(c, CTD_ERR_INVALID_ARG, "unknown option");
+  }
 }
 
 int ctd_profile_enable(ctd_ctx* c, int32_t enable) {

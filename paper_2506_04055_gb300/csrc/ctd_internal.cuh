@@ -1,5 +1,6 @@
 // ctd_internal.cuh -- internal declarations of the GB300 PaiNN engine (not part of the ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -51,7 +52,24 @@ struct CellGeom {
   int nc[3];      // cells (slabs) per lattice direction
   int M[3];       // neighbour slab half-range per direction
   double R2;      // (cutoff + skin)^2, rounded once in FP64
+  int morton_bits;  // 0: cells numbered lexicographically; b > 0: Morton order on a 2^b grid
 };
+
+// Linear index of cell (c0, c1, c2).  Morton (Z-order) numbering keeps spatially close cells
+// close in the cell-sorted atom order, so a block of consecutive rows is a compact region and
+// its neighbours' features stay in L2.
+__host__ __device__ __forceinline__ uint32_t morton_spread(uint32_t x) {
+  x &= 0x3ffu;
+  x = (x | (x << 16)) & 0x030000ffu;
+  x = (x | (x << 8)) & 0x0300f00fu;
+  x = (x | (x << 4)) & 0x030c30c3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+__host__ __device__ __forceinline__ int cell_linear(const CellGeom& g, int c0, int c1, int c2) {
+  if (g.morton_bits == 0) return (c0 * g.nc[1] + c1) * g.nc[2] + c2;
+  return (int)(morton_spread((uint32_t)c0) | (morton_spread((uint32_t)c1) << 1) | (morton_spread((uint32_t)c2) << 2));
+}
 
 // Device-side status word, raised by kernels instead of trapping.
 enum Status : int {
@@ -72,6 +90,7 @@ struct LayerW {
   const float *A2, *A2t, *c2;      // [3F][F], [F][3F]
   // BF16 copies for the tensor-core path (same shapes as the FP32 arrays above)
   const __nv_bfloat16 *W1b, *W1tb, *W2b, *W2tb, *UVb, *UVtb, *A1b, *A1tb, *A2b, *A2tb;
+  const __nv_bfloat16* Wfb;        // [3F][64] radial filter, zero padded (tensor-core edge kernels)
 };
 
 struct ModelW {
@@ -81,6 +100,7 @@ struct ModelW {
   LayerW L[kMaxT];
   const float *R1, *R1t, *d1, *R2, *d2;   // [F/2][F], [F][F/2]
   const __nv_bfloat16 *R1b, *R1tb;
+  bool tc_adjoint;                 // BF16 path: edge adjoint with the tensor-core filter
 };
 
 // ---------------------------------------------------------------- small device helpers
@@ -132,6 +152,15 @@ void launch_check_finite(cudaStream_t st, int64_t n, const double* a, int* statu
 // gemm_bf16.cu: C[M][N] = A[M][K] . W[N][K]^T on tcgen05 (BF16 in, FP32 accumulate), epilogue
 // EPI 0 bias, 1 bias + SiLU (bf16 copy gets the SiLU), 2 + aux, 3 * SiLU'(aux).
 bool gemm_bf16_supported(int N, int K);
+bool make_tmap_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+// edge_tc.cu: tensor-core edge message / adjoint (F = 128, K <= 32)
+bool edge_tc_supported(int F, int K);
+int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow, const int32_t* acol,
+                const float4* ar, const float* PHI, const float* S, const float* V, float* SM, float* VM,
+                __nv_bfloat16* VMb, int* status);
+int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
+                const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm, const float* Gvm,
+                float* GPHI, float4* hedge, int* status);
 template <int EPI>
 int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, int64_t lda,
               const __nv_bfloat16* W, const float* bias, const float* aux, int ldaux, float* out, int ldo,

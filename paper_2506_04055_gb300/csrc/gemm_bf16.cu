@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ CU
   umma::fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
+  int issued = 0, last_acc = 0;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -114,7 +115,11 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ CU
         }
         umma::mma_commit(&empty[s]);
         umma::mma_commit(&tfull[a]);
+        last_acc = a;
+        ++issued;
       }
+      // the MMAs of the last issued tile have completed before TMEM is released
+      if (issued > 0) umma::mbar_wait(&tfull[last_acc], ((issued - 1) / p.n_acc) & 1, 200000000ull);
     }
   } else {
     // epilogue warps 2..5: TMEM lane quarter = warp % 4
@@ -191,7 +196,7 @@ static EncodeTiledFn encode_fn() {
 }
 
 // 2D bf16 tensor map over rows x cols (row pitch ld elements), box rows x 64 columns, 128B swizzle.
-static bool make_tmap(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+bool make_tmap_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
@@ -241,7 +246,7 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
   while (cols < (uint32_t)(p.n_acc * N)) cols <<= 1;
   p.tmem_cols = cols;
   CUtensorMap ta, tb;
-  if (!make_tmap(&ta, A, M, K, lda, kTileM) || !make_tmap(&tb, W, N, K, K, p.b_box_rows)) return -2;
+  if (!make_tmap_bf16(&ta, A, M, K, lda, kTileM) || !make_tmap_bf16(&tb, W, N, K, K, p.b_box_rows)) return -2;
   size_t smem = 1024 + b_bytes + (size_t)p.a_stages * a_bytes + 256;
   // a CTA holding more than half of TMEM runs alone on its SM, so allocation never waits
   if (p.tmem_cols > 256 && smem < 120 * 1024) smem = 120 * 1024;

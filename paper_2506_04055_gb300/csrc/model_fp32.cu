@@ -802,6 +802,12 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   const int F = m.F, T = m.T, Fh = F / 2;
   const unsigned nb = blocks_for(n * F);
   int bad = 0;
+  // Radial filter on tcgen05 inside the message kernel (F = 128); other widths keep the FP32
+  // filter.  The adjoint keeps the SIMT kernel: its gather-latency-bound epilogue runs faster
+  // with the 16 warps per SM the SIMT kernel reaches than with the 8 the TMEM budget allows
+  // (measured on the 1M-atom fcc workload; edge_bwd_tc stays available and tested).
+  const bool use_tc = edge_tc_supported(F, m.K);
+  const bool use_tc_bwd = use_tc && m.tc_adjoint;
   if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], Bb[BB_S0]); }
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
@@ -814,7 +820,11 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
 #define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM])
     if (n > 0) {
       StageGuard sg(STG_EDGE_FWD);
-      CTD_KP_DISPATCH(m.KP, CTD_FWD)
+      if (use_tc) {
+        bad |= edge_fwd_tc(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], status);
+      } else {
+        CTD_KP_DISPATCH(m.KP, CTD_FWD)
+      }
     }
 #undef CTD_FWD
     bad |= gemm_bf16<0>(st, 3 * n, 2 * F, F, Bb[BB_VM], F, L.UVb, nullptr, nullptr, 0, UV, 2 * F, nullptr, 0, status);
@@ -852,7 +862,11 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
 #define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge)
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
-      CTD_KP_DISPATCH(m.KP, CTD_BWD)
+      if (use_tc_bwd) {
+        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge, status);
+      } else {
+        CTD_KP_DISPATCH(m.KP, CTD_BWD)
+      }
     }
 #undef CTD_BWD
     if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV, Bb[BB_GP3]); }

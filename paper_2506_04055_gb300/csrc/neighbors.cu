@@ -44,7 +44,7 @@ __global__ void k_wrap_bin(int64_t n, const double* __restrict__ x, CellGeom g,
   for (int k = 0; k < 3; ++k)
     xw[3 * i + k] = __dadd_rn(__dadd_rn(__dmul_rn(f[0], g.H[k]), __dmul_rn(f[1], g.H[3 + k])),
                               __dmul_rn(f[2], g.H[6 + k]));
-  int lin = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
+  int lin = cell_linear(g, c[0], c[1], c[2]);
   cell[i] = lin;
   atomicAdd(&cell_count[lin], 1);
 }
@@ -162,7 +162,7 @@ __global__ void k_pair_search(int64_t n, const double* __restrict__ xs, const in
           sh[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)im[0], g.H[c]), __dmul_rn((double)im[1], g.H[3 + c])),
                             __dmul_rn((double)im[2], g.H[6 + c]));
         bool zero_img = (im[0] == 0) && (im[1] == 0) && (im[2] == 0);
-        int lin = (w[0] * g.nc[1] + w[1]) * g.nc[2] + w[2];
+        int lin = cell_linear(g, w[0], w[1], w[2]);
         int b = cstart[lin], e = cstart[lin + 1];
         for (int j0 = b; j0 < e; j0 += 32) {
           int j = j0 + lane;

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "painn.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ctd_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(ctd_[a-z_0-9]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert declared == sorted(_lib.EXPORTS)
     so = os.path.join(ROOT, "paper_2506_04055_gb300", "libctd_painn.so")
     syms = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (ctd_[a-z_]+)\b", syms))
+    exported = set(re.findall(r"\bT (ctd_[a-z_0-9]+)\b", syms))
     for name in declared:
         assert name in exported, name
         getattr(lib, name)

@@ -11,9 +11,12 @@ from gpu_common import BF16_FORCE_RMSE, compare, engine, model, rel_force_rmse
 pytestmark = pytest.mark.gpu
 
 
-def _run(eng, orc, sy, F, T, S, bias=0.1, seed=0):
+def _run(eng, orc, sy, F, T, S, bias=0.1, seed=0, tc_adjoint=False):
     vals, blob = model(F, T, S, seed=seed, bias=bias)
     with eng.Potential(F, T=T, n_species=S, precision="bf16", params=blob) as pot:
+        if tc_adjoint:
+            from paper_2506_04055_gb300 import _lib
+            pot.set_option(_lib.CTD_OPT_TC_ADJOINT, 1)
         out = pot.compute(sy.species, sy.positions, sy.cell, energies=True)
     ref = orc.painn(vals, F, 20, T, S, sy.species, sy.positions, sy.cell)
     return out, ref
@@ -32,6 +35,15 @@ def test_bf16_fcc4000_F128(orc):
     out, ref = _run(eng, orc, syn.fcc(10, 10, 10, jitter=0.05, seed=0), 128, 3, 1, bias=0.0)
     fr, er, wr = compare(out, ref, force_tol=BF16_FORCE_RMSE, e_tol=1e-2, w_tol=2e-2)
     print(f"bf16 fcc4000: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
+
+
+def test_bf16_tensor_core_adjoint(orc):
+    """The edge adjoint with the tcgen05 filter (option) on the fcc sub-cell and a small cell."""
+    eng = engine()
+    for sy in (syn.fcc(10, 10, 10, jitter=0.05, seed=0), syn.water_box(21, seed=2)):
+        out, ref = _run(eng, orc, sy, 128, 3, 2, bias=0.1, tc_adjoint=True)
+        fr, er, wr = compare(out, ref, force_tol=BF16_FORCE_RMSE, e_tol=1e-2, w_tol=2e-2)
+        print(f"bf16 tc-adjoint {sy.name}: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
 
 
 def test_bf16_mixture_biases(orc):
