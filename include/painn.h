@@ -171,6 +171,39 @@ int ctd_profile_read(ctd_ctx *ctx, double *ms, int64_t *launches, int32_t reset)
 int ctd_gemm_bf16(ctd_ctx *ctx, int64_t M, int32_t N, int32_t K, const void *A, int64_t lda,
                   const void *B, float *C, int64_t ldc);
 
+/* ---- serving: continuous batching of independent MD replicas --------------------------------- */
+/* A server keeps many independent replicas (own atoms, cell, neighbour list) resident on one
+ * GPU and advances all of them together: each ctd_serve_step is one velocity-Verlet step in
+ * which every stage (integrator, prune, model, adjoint, force assembly) is one launch over the
+ * concatenation of the resident replicas.  Requests queue FIFO and are admitted between steps
+ * while the HBM budget (hbm_budget_bytes of ctd_serve_create; 0 = none) and max_replicas allow;
+ * a replica leaves after its nsteps steps and its final state stays available to
+ * ctd_serve_poll.  A replica's trajectory does not depend on which other replicas share the
+ * batch (per-replica reductions run in a fixed order of its own atoms).  dt: time step (fs),
+ * shared by all replicas.  The params blob is the one ctd_load_params takes. */
+typedef struct ctd_server ctd_server;
+int ctd_serve_create(ctd_server **out, const ctd_model_desc *desc, const void *params, size_t nbytes,
+                     size_t hbm_budget_bytes, int32_t max_replicas, double dt, void *cuda_stream);
+/* Queue one replica (host arrays, copied): n atoms, species, masses (amu), positions (A),
+ * velocities (A/fs), cell, neighbour skin (A), number of steps.  *request_id identifies it. */
+int ctd_serve_submit(ctd_server *s, int64_t n, const int32_t *species, const double *masses,
+                     const double *positions, const double *velocities, const double cell[9],
+                     double skin, int32_t nsteps, int64_t *request_id);
+/* Retire finished replicas, admit queued ones, run one step of all resident replicas (a newly
+ * admitted replica's first step evaluates its initial forces without moving it).  Outputs
+ * (may be NULL): replicas resident during the step, admitted and retired by this call. */
+int ctd_serve_step(ctd_server *s, int32_t *n_resident, int32_t *n_admitted, int32_t *n_finished);
+/* State of a request: 0 queued, 1 resident, 2 finished; steps done.  When finished, positions
+ * and velocities ([n][3], caller's atom order) receive the final state.  epot / ekin receive the
+ * energies recorded so far (one per step, the first at the initial positions: up to nsteps+1
+ * values); virial[9] the latest virial.  Any output pointer may be NULL. */
+int ctd_serve_poll(ctd_server *s, int64_t request_id, int32_t *state, int32_t *steps_done,
+                   double *positions, double *velocities, double *epot, double *ekin, double *virial);
+int ctd_serve_stats(ctd_server *s, int64_t *resident_atoms, int32_t *resident_replicas,
+                    int32_t *queued, int64_t *bytes_held);
+const char *ctd_serve_last_error(ctd_server *s);
+void ctd_serve_destroy(ctd_server *s);
+
 /* ---- neighbour list without device allocation ------------------------------------------ */
 /* The paper has no counterpart to this call; it exists for callers of this library that must
  * not allocate device memory: an MD code that manages a fixed device memory pool and cannot

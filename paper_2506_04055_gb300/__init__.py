@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (CTD_DEVICE_PTRS, CTD_NEED_FORCES, CTD_NEED_VIRIAL, CTD_PREC_BF16,  # noqa: F401
                    CTD_PREC_FP32, CTD_REBUILD, CtdError, ctd_model_desc, ctd_stats)
 
-__all__ = ["Potential", "PaiNNEnergy", "CtdError", "build", "load"]
+__all__ = ["Potential", "Server", "PaiNNEnergy", "CtdError", "build", "load"]
 
 
 def build(force: bool = False) -> str:
@@ -188,6 +188,71 @@ class Potential:
         v = np.empty((self._md_n, 3))
         _lib.ctd_md_get_state(self.ctx, _ptr(x), _ptr(v))
         return x, v
+
+
+class Server:
+    """Continuous-batching MD server (see ctd_serve_* in include/painn.h).
+
+    submit() queues a replica, step() advances every resident replica by one velocity-Verlet
+    step (admitting and retiring between steps), poll() returns a request's state and results."""
+
+    def __init__(self, F: int, params: bytes, K: int = 20, T: int = 3, n_species: int = 2, rc: float = 5.0,
+                 precision: str = "fp32", hbm_budget_bytes: int = 0, max_replicas: int = 1024, dt: float = 1.0,
+                 stream: int | None = None):
+        prec = {"fp32": CTD_PREC_FP32, "bf16": CTD_PREC_BF16}[precision]
+        self.desc = ctd_model_desc(F, K, T, n_species, rc, prec)
+        self.srv = _lib.ctd_serve_create(self.desc, params, hbm_budget_bytes, max_replicas, dt, stream)
+        self._n = {}
+        self._steps = {}
+
+    def close(self):
+        if getattr(self, "srv", None):
+            _lib.ctd_serve_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, species, masses, positions, velocities, cell, nsteps: int, skin: float = 1.0) -> int:
+        z = _host(species, np.int32)
+        m = _host(masses, np.float64)
+        x = _host(positions, np.float64, (-1, 3))
+        v = _host(velocities, np.float64, (-1, 3))
+        H = _host(cell, np.float64, (3, 3))
+        rid = _lib.ctd_serve_submit(self.srv, x.shape[0], _ptr(z), _ptr(m), _ptr(x), _ptr(v), _ptr(H),
+                                    float(skin), int(nsteps))
+        self._n[rid] = x.shape[0]
+        self._steps[rid] = int(nsteps)
+        return rid
+
+    def step(self):
+        """Returns (resident replicas, admitted, finished)."""
+        return _lib.ctd_serve_step(self.srv)
+
+    def poll(self, rid: int):
+        n, ns = self._n[rid], self._steps[rid]
+        x = np.empty((n, 3))
+        v = np.empty((n, 3))
+        ep = np.full(ns + 1, np.nan)
+        ek = np.full(ns + 1, np.nan)
+        w = np.empty((3, 3))
+        state, done = _lib.ctd_serve_poll(self.srv, rid, _ptr(x), _ptr(v), _ptr(ep), _ptr(ek), _ptr(w))
+        out = {"state": state, "steps_done": done, "epot": ep, "ekin": ek, "virial": w}
+        if state == 2:
+            out["positions"], out["velocities"] = x, v
+        return out
+
+    def stats(self):
+        return _lib.ctd_serve_stats(self.srv)
 
 
 def _make_autograd():

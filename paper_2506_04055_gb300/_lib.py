@@ -40,7 +40,9 @@ ERROR_NAMES = {
 EXPORTS = [
     "ctd_create", "ctd_load_params", "ctd_build_neighbors", "ctd_get_pairs", "ctd_compute",
     "ctd_set_energy_out", "ctd_md_set_state", "ctd_md_run", "ctd_md_get_state",
-    "ctd_set_option", "ctd_profile_enable", "ctd_profile_read", "ctd_gemm_bf16", "ctd_neighbors_noalloc",
+    "ctd_set_option", "ctd_profile_enable", "ctd_profile_read", "ctd_gemm_bf16",
+    "ctd_serve_create", "ctd_serve_submit", "ctd_serve_step", "ctd_serve_poll", "ctd_serve_stats",
+    "ctd_serve_last_error", "ctd_serve_destroy", "ctd_neighbors_noalloc",
     "ctd_last_error",
     "ctd_destroy",
 ]
@@ -96,6 +98,13 @@ def load(path: str = LIB_PATH):
         "ctd_profile_read": ([P, P, P, I32], ctypes.c_int),
         "ctd_gemm_bf16": ([P, I64, I32, I32, P, I64, P, P, I64], ctypes.c_int),
         "ctd_neighbors_noalloc": ([I64, P, P, D, D, P, P, P, I64, P, P], ctypes.c_int),
+        "ctd_serve_create": ([P, P, P, ctypes.c_size_t, ctypes.c_size_t, I32, D, P], ctypes.c_int),
+        "ctd_serve_submit": ([P, I64, P, P, P, P, P, D, I32, P], ctypes.c_int),
+        "ctd_serve_step": ([P, P, P, P], ctypes.c_int),
+        "ctd_serve_poll": ([P, I64, P, P, P, P, P, P, P], ctypes.c_int),
+        "ctd_serve_stats": ([P, P, P, P, P], ctypes.c_int),
+        "ctd_serve_last_error": ([P], ctypes.c_char_p),
+        "ctd_serve_destroy": ([P], None),
         "ctd_last_error": ([P], ctypes.c_char_p),
         "ctd_destroy": ([P], None),
     }
@@ -195,6 +204,56 @@ def ctd_neighbors_noalloc(n, positions_ptr, cell_ptr, cutoff, skin, i_ptr, j_ptr
     code = load().ctd_neighbors_noalloc(n, positions_ptr, cell_ptr, cutoff, skin, i_ptr, j_ptr,
                                         shift_ptr, cap, ctypes.byref(npairs), cuda_stream)
     return code, npairs.value
+
+
+def serve_check(srv, code):
+    if code != CTD_OK:
+        msg = load().ctd_serve_last_error(srv)
+        raise CtdError(code, msg.decode() if msg else "")
+    return code
+
+
+def ctd_serve_create(desc, blob, hbm_budget_bytes=0, max_replicas=1024, dt=1.0, cuda_stream=None):
+    srv = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    code = load().ctd_serve_create(ctypes.byref(srv), ctypes.byref(desc), buf, len(blob), hbm_budget_bytes,
+                                   max_replicas, dt, cuda_stream)
+    if code != CTD_OK:
+        raise CtdError(code, "ctd_serve_create failed")
+    return srv
+
+
+def ctd_serve_submit(srv, n, species_ptr, masses_ptr, positions_ptr, velocities_ptr, cell_ptr, skin, nsteps):
+    rid = ctypes.c_int64()
+    serve_check(srv, load().ctd_serve_submit(srv, n, species_ptr, masses_ptr, positions_ptr, velocities_ptr,
+                                             cell_ptr, skin, nsteps, ctypes.byref(rid)))
+    return rid.value
+
+
+def ctd_serve_step(srv):
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    serve_check(srv, load().ctd_serve_step(srv, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def ctd_serve_poll(srv, rid, positions_ptr=None, velocities_ptr=None, epot_ptr=None, ekin_ptr=None,
+                   virial_ptr=None):
+    st, done = ctypes.c_int32(), ctypes.c_int32()
+    serve_check(srv, load().ctd_serve_poll(srv, rid, ctypes.byref(st), ctypes.byref(done), positions_ptr,
+                                           velocities_ptr, epot_ptr, ekin_ptr, virial_ptr))
+    return st.value, done.value
+
+
+def ctd_serve_stats(srv):
+    atoms, reps, q, held = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    serve_check(srv, load().ctd_serve_stats(srv, ctypes.byref(atoms), ctypes.byref(reps), ctypes.byref(q),
+                                            ctypes.byref(held)))
+    return {"resident_atoms": atoms.value, "resident_replicas": reps.value, "queued": q.value,
+            "bytes_held": held.value}
+
+
+def ctd_serve_destroy(srv):
+    load().ctd_serve_destroy(srv)
 
 
 def ctd_last_error(ctx) -> str:

@@ -14,19 +14,11 @@
 #include <string>
 #include <vector>
 
-#include "ctd_internal.cuh"
-#include "../../include/painn.h"
+#include "ctx.cuh"
 
 using namespace ctd;
 
-namespace {
-
-struct DBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
-constexpr int kPartials = 152 * 4;   // fixed block count of the reductions (deterministic)
+namespace ctd {
 
 // The tensor-core path is compiled in only when its kernels exist in this build.
 bool bf16_available() { return true; }
@@ -40,75 +32,16 @@ uint16_t to_bf16_bits(float f) {
   return (uint16_t)(u >> 16);
 }
 
-}  // namespace
+}  // namespace ctd
 
-struct ctd_ctx {
-  ctd_model_desc desc{};
-  int device = 0;
-  cudaStream_t st = nullptr;
-  bool own_stream = false;
-  size_t budget = 0, held = 0;
-  std::string err;
-  std::vector<DBuf*> all;
-
-  // parameters
-  bool have_params = false;
-  double eps = 1e-8, e_scale = 1.0;
-  DBuf params, params_bf;
-  ModelW mw{};
-
-  // neighbour state
-  bool have_list = false;
-  int64_t n = 0, n_verlet = 0;
-  double H[9] = {0};
-  double cutoff = 0.0, skin = 1.0;
-  bool skin_set = false;
-  CellGeom geom{};
-  int64_t ncell = 0;
-  double last_maxdisp = 0.0;
-
-  DBuf x_user, z_user, xw, wrapm, cellid, cell_count, cell_start, cursor, tmp_idx, perm, inv_perm;
-  DBuf xw_s, xref_s, z_s, x_s, count, vrow, vcol, vimg, vbase, vrev, v2a, status, delta, maxd;
-  DBuf acount, arow, acol, ar, vidx, arev, hedge, force_s, eatom, epart, vpart, kpart, scan_tmp;
-  DBuf out_e, out_f, out_w, out_eatom;
-  std::vector<DBuf> mbuf, mbufb;
-  double* energy_out_user = nullptr;
-
-  ProfState prof;
-
-  // MD state (sorted order)
-  bool md_ready = false, md_forces_valid = false;
-  DBuf md_v, md_m, md_x_user, md_v_user, md_ep, md_ek, md_tmp;
-
-  ctd_ctx() {
-    DBuf* list[] = {&params, &params_bf, &x_user, &z_user, &xw, &wrapm, &cellid, &cell_count, &cell_start, &cursor,
-                    &tmp_idx, &perm, &inv_perm, &xw_s, &xref_s, &z_s, &x_s, &count, &vrow, &vcol, &vimg,
-                    &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev,
-                    &hedge, &force_s, &eatom, &epart, &vpart, &kpart, &scan_tmp, &out_e, &out_f, &out_w,
-                    &out_eatom, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp};
-    for (DBuf* b : list) all.push_back(b);
-  }
-};
-
-namespace {
-
-// Binds the calling thread's launch accounting to a context for the duration of an API call.
-struct Bind {
-  explicit Bind(ctd_ctx* c) { prof_bind(c ? &c->prof : nullptr); }
-  ~Bind() { prof_bind(nullptr); }
-};
+namespace ctd {
 
 int fail(ctd_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
 }
 
-#define CUDA_OK(ctx, call)                                                                     \
-  do {                                                                                         \
-    cudaError_t e_ = (call);                                                                   \
-    if (e_ != cudaSuccess)                                                                     \
-      return fail(ctx, CTD_ERR_CUDA, std::string(#call " -> ") + cudaGetErrorString(e_));      \
-  } while (0)
+
 
 // Grow-only allocation with 25 % headroom, charged against the budget.
 int ensure(ctd_ctx* c, DBuf& b, size_t bytes) {
@@ -142,16 +75,8 @@ int ensure(ctd_ctx* c, DBuf& b, size_t bytes) {
   return CTD_OK;
 }
 
-#define ENSURE(c, b, bytes)                \
-  do {                                     \
-    int r_ = ensure((c), (b), (bytes));    \
-    if (r_ != CTD_OK) return r_;           \
-  } while (0)
 
-template <class T>
-T* P(DBuf& b) {
-  return static_cast<T*>(b.p);
-}
+
 
 // G = H^{-T} by cofactors, the expression order of the canonical pair test (every product and
 // difference rounded on its own; this file is compiled without floating-point contraction).
@@ -178,8 +103,7 @@ bool finite_cell(const double H[9]) {
   return std::fabs(det) > 1e-9;
 }
 
-int setup_geometry(ctd_ctx* c, const double H[9], double R) {
-  CellGeom& g = c->geom;
+int setup_geometry_into(ctd_ctx* c, CellGeom& g, int64_t* ncell_out, const double H[9], double R) {
   memcpy(g.H, H, sizeof(double) * 9);
   inv_transpose(H, g.G);
   int64_t ncell = 1;
@@ -206,8 +130,12 @@ int setup_geometry(ctd_ctx* c, const double H[9], double R) {
     g.morton_bits = bits;
     ncell = mcells;
   }
-  c->ncell = ncell;
+  *ncell_out = ncell;
   return CTD_OK;
+}
+
+int setup_geometry(ctd_ctx* c, const double H[9], double R) {
+  return setup_geometry_into(c, c->geom, &c->ncell, H, R);
 }
 
 int check_status(ctd_ctx* c) {
@@ -547,7 +475,7 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
   return CTD_OK;
 }
 
-}  // namespace
+}  // namespace ctd
 
 // ============================================================================== C ABI
 extern "C" {

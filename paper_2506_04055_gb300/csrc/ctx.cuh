@@ -1,0 +1,111 @@
+// ctx.cuh -- the engine context behind the C ABI (internal): grow-only device buffers, model
+// weights, the neighbour-list and MD state, and the host-side stages shared by the single-system
+// calls (api.cu) and the multi-replica serving loop (serve.cu).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "ctd_internal.cuh"
+#include "../../include/painn.h"
+
+namespace ctd {
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+constexpr int kPartials = 152 * 4;   // fixed block count of the reductions (deterministic)
+
+bool bf16_available();
+uint16_t to_bf16_bits(float f);
+
+}  // namespace ctd
+
+struct ctd_ctx {
+  using DBuf = ctd::DBuf;
+  using ProfState = ctd::ProfState;
+  using ModelW = ctd::ModelW;
+  using CellGeom = ctd::CellGeom;
+  ctd_model_desc desc{};
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  size_t budget = 0, held = 0;
+  std::string err;
+  std::vector<DBuf*> all;
+
+  // parameters
+  bool have_params = false;
+  double eps = 1e-8, e_scale = 1.0;
+  DBuf params, params_bf;
+  ModelW mw{};
+
+  // neighbour state
+  bool have_list = false;
+  int64_t n = 0, n_verlet = 0;
+  double H[9] = {0};
+  double cutoff = 0.0, skin = 1.0;
+  bool skin_set = false;
+  CellGeom geom{};
+  int64_t ncell = 0;
+  double last_maxdisp = 0.0;
+
+  DBuf x_user, z_user, xw, wrapm, cellid, cell_count, cell_start, cursor, tmp_idx, perm, inv_perm;
+  DBuf xw_s, xref_s, z_s, x_s, count, vrow, vcol, vimg, vbase, vrev, v2a, status, delta, maxd;
+  DBuf acount, arow, acol, ar, vidx, arev, hedge, force_s, eatom, epart, vpart, kpart, scan_tmp;
+  DBuf out_e, out_f, out_w, out_eatom;
+  std::vector<DBuf> mbuf, mbufb;
+  double* energy_out_user = nullptr;
+
+  ProfState prof;
+
+  // MD state (sorted order)
+  bool md_ready = false, md_forces_valid = false;
+  DBuf md_v, md_m, md_x_user, md_v_user, md_ep, md_ek, md_tmp;
+
+  ctd_ctx() {
+    DBuf* list[] = {&params, &params_bf, &x_user, &z_user, &xw, &wrapm, &cellid, &cell_count, &cell_start, &cursor,
+                    &tmp_idx, &perm, &inv_perm, &xw_s, &xref_s, &z_s, &x_s, &count, &vrow, &vcol, &vimg,
+                    &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev,
+                    &hedge, &force_s, &eatom, &epart, &vpart, &kpart, &scan_tmp, &out_e, &out_f, &out_w,
+                    &out_eatom, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp};
+    for (DBuf* b : list) all.push_back(b);
+  }
+};
+
+namespace ctd {
+
+// Binds the calling thread's launch accounting to a context for the duration of an API call.
+struct Bind {
+  explicit Bind(ctd_ctx* c) { prof_bind(c ? &c->prof : nullptr); }
+  ~Bind() { prof_bind(nullptr); }
+};
+
+int fail(ctd_ctx* c, int code, const std::string& msg);
+int ensure(ctd_ctx* c, DBuf& b, size_t bytes);
+template <class T>
+T* P(DBuf& b) {
+  return static_cast<T*>(b.p);
+}
+void inv_transpose(const double H[9], double G[9]);
+bool finite_cell(const double H[9]);
+int setup_geometry_into(ctd_ctx* c, CellGeom& g, int64_t* ncell, const double H[9], double R);
+int check_status(ctd_ctx* c);
+int copy_in(ctd_ctx* c, void* dst, const void* src, size_t bytes, bool device);
+int prune(ctd_ctx* c, double* maxdisp_out);
+int evaluate(ctd_ctx* c, bool need_grad);
+
+}  // namespace ctd
+
+#define CUDA_OK(ctx, call)                                                                     \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return ctd::fail(ctx, CTD_ERR_CUDA, std::string(#call " -> ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define ENSURE(c, b, bytes)                \
+  do {                                     \
+    int r_ = ctd::ensure((c), (b), (bytes)); \
+    if (r_ != CTD_OK) return r_;           \
+  } while (0)

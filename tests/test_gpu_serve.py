@@ -1,0 +1,96 @@
+"""Serving loop: continuous batching of independent MD replicas (ctd_serve_*).
+
+Checks: a replica's trajectory is bit-identical alone and in a mix of other replicas admitted
+at other times; it agrees with the single-system resident MD loop (ctd_md_run); admission
+respects the HBM budget; finished replicas return their final state in the caller's order."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from gpu_common import engine, model
+
+pytestmark = pytest.mark.gpu
+
+F, T, S = 64, 2, 3
+DT = 0.5
+
+
+def _replicas():
+    w = syn.water_box(64, seed=0)
+    f = syn.fcc(3, 3, 3, jitter=0.05, seed=1)
+    f.species[:] = 2
+    small = syn.water_box(21, seed=2)
+    g = syn.fcc(2, 2, 2, jitter=0.05, seed=3)
+    g.species[:] = 2
+    out = []
+    for k, sy in enumerate((w, f, small, g)):
+        v = syn.maxwell_boltzmann(sy.masses, 300.0, seed=10 + k)
+        out.append((sy, v))
+    return out
+
+
+def _run_server(eng, blob, items, nsteps, precision, stagger=0, budget=0, max_replicas=64):
+    srv = eng.Server(F, blob, T=T, n_species=S, precision=precision, dt=DT, hbm_budget_bytes=budget,
+                     max_replicas=max_replicas)
+    ids = []
+    late = items[:stagger] if stagger else []
+    first = items[stagger:] if stagger else items
+    for sy, v in first:
+        ids.append(srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, nsteps, skin=1.0))
+    steps = 0
+    max_res = 0
+    while True:
+        if stagger and steps == 3:
+            for sy, v in late:
+                ids.append(srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, nsteps, skin=1.0))
+        res, adm, fin = srv.step()
+        max_res = max(max_res, res)
+        steps += 1
+        if all(srv.poll(i)["state"] == 2 for i in ids) and (not stagger or steps > 3):
+            break
+        assert steps < 10 * nsteps + 50
+    results = {i: srv.poll(i) for i in ids}
+    srv.close()
+    return ids, results, max_res
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_alone_equals_mixed(precision):
+    eng = engine()
+    _, blob = model(F, T, S, seed=4, bias=0.1)
+    items = _replicas()
+    a = items[0]
+    ids1, r1, _ = _run_server(eng, blob, [a], 12, precision)
+    # the same replica submitted late, into a batch that already runs three others
+    ids2, r2, _ = _run_server(eng, blob, [a] + items[1:], 12, precision, stagger=1)
+    alone, mixed = r1[ids1[0]], r2[ids2[-1]]
+    np.testing.assert_array_equal(alone["epot"], mixed["epot"])
+    np.testing.assert_array_equal(alone["positions"], mixed["positions"])
+    np.testing.assert_array_equal(alone["velocities"], mixed["velocities"])
+    assert np.isfinite(alone["epot"]).all() and alone["steps_done"] == 12
+
+
+def test_matches_single_system_md():
+    eng = engine()
+    _, blob = model(F, T, S, seed=5, bias=0.1)
+    sy, v = _replicas()[1]
+    ids, res, _ = _run_server(eng, blob, [(sy, v)], 15, "fp32")
+    r = res[ids[0]]
+    with eng.Potential(F, T=T, n_species=S, params=blob) as pot:
+        pot.md_set_state(sy.species, sy.masses, sy.positions, v, sy.cell, skin=1.0)
+        ep, ek, _ = pot.md_run(15, DT)
+        x, vv = pot.md_get_state()
+    np.testing.assert_allclose(r["positions"], x, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(r["velocities"], vv, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(r["epot"], ep, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(r["ekin"], ek, rtol=1e-9, atol=1e-12)
+
+
+def test_budget_limits_residency():
+    eng = engine()
+    _, blob = model(F, T, S, seed=6)
+    items = _replicas() * 3
+    # budget for roughly two of the larger replicas at a time
+    ids, res, max_res = _run_server(eng, blob, items, 4, "fp32", budget=200 * 1024 * 1024, max_replicas=3)
+    assert max_res <= 3
+    assert all(res[i]["state"] == 2 and res[i]["steps_done"] == 4 for i in ids)
