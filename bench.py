@@ -213,6 +213,9 @@ def run_ours(args):
         except eng.CtdError as e:
             results[prec] = {"error": str(e)}
             continue
+        if args.tc_adjoint and prec == "bf16":
+            from paper_2506_04055_gb300 import _lib as L
+            pot.set_option(L.CTD_OPT_TC_ADJOINT, 1)
         pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=SKIN)
         for _ in range(args.warmup):
             pot.md_run(1, DT)
@@ -357,6 +360,7 @@ def main():
     ap.add_argument("--precision", default="both", choices=["fp32", "bf16", "both"])
     ap.add_argument("--cells", type=int, default=FCC_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tc-adjoint", action="store_true", help="BF16: edge adjoint with the tcgen05 filter")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

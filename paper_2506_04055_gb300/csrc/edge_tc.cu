@@ -78,7 +78,7 @@ struct EdgeTcArgs {
 // ------------------------------------------------------------------------------ message
 // Row bookkeeping shared by both kernels: the producer marks, for each edge slot of a tile,
 // how many rows end at that edge (the row itself plus any empty rows right after it); rows
-// without edges at the start of the CTA's range are flushed before the first tile.
+// without edges at the start of a stream's range are flushed before its first tile.
 __device__ __forceinline__ void mark_row_ends(int lane, int* sfl, int NE, int64_t tb, int64_t r1,
                                               const int32_t* __restrict__ arow, int64_t& rp) {
   for (int s = lane; s < NE; s += 32) sfl[s] = 0;
@@ -94,113 +94,163 @@ __device__ __forceinline__ void mark_row_ends(int lane, int* sfl, int NE, int64_
   __syncwarp();
 }
 
-template <int NE>
-__global__ void __launch_bounds__(192, 2) k_edge_fwd_tc(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
+// Streams: a CTA splits its rows into NS contiguous sub-ranges ("streams"), each with its own
+// tiles, TMEM region and barriers and its own epilogue warpgroup, so one SM keeps 4 * NS
+// epilogue warps busy on independent rows while sharing one copy of Wf.
+struct StreamRange {
+  int64_t r0, r1, e0, e1;
+  int ntiles;
+};
+template <int NE, int NS>
+__device__ __forceinline__ StreamRange stream_range(const EdgeTcArgs& p, int s) {
+  StreamRange R;
+  const int64_t c0 = (int64_t)blockIdx.x * p.rows_per_cta;
+  const int64_t c1 = (c0 + p.rows_per_cta < p.n) ? c0 + p.rows_per_cta : p.n;
+  const int64_t q = (c1 - c0 + NS - 1) / NS;
+  R.r0 = c0 + s * q < c1 ? c0 + s * q : c1;
+  R.r1 = R.r0 + q < c1 ? R.r0 + q : c1;
+  R.e0 = p.arow[R.r0];
+  R.e1 = p.arow[R.r1];
+  R.ntiles = (int)((R.e1 - R.e0 + NE - 1) / NE);
+  return R;
+}
+
+// warps 0..1 producers, warp 2 MMA / TMEM owner, warps 3 .. 3 + 4 NS - 1 epilogue
+template <int NE, int NS>
+__global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = align1024(smem_raw);
-  unsigned char* sA = smem;                                  // Wf tiles
-  unsigned char* sB = sA + kWfBytes;                         // [2][NE x 128 B] basis tiles
-  int* sj = reinterpret_cast<int*>(sB + 2 * NE * 128);       // [2][NE] sender index
-  int* sfl = sj + 2 * NE;                                    // [2][NE] rows ending at the slot
-  float4* sgeo = reinterpret_cast<float4*>(sfl + 2 * NE);    // [2][NE] (u, f_c)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sgeo + 2 * NE);
-  uint64_t* wbar = bars;
-  uint64_t* bready = bars + 1;   // [2]
-  uint64_t* bfree = bars + 3;    // [2]
-  uint64_t* tfull = bars + 5;
-  uint64_t* tempty = bars + 6;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7);
+  unsigned char* sA = smem;                                        // Wf tiles
+  unsigned char* sB = sA + kWfBytes;                               // [NS][2][NE x 128 B] basis tiles
+  int* sj = reinterpret_cast<int*>(sB + NS * 2 * NE * 128);        // [NS][2][NE] sender index
+  int* sfl = sj + NS * 2 * NE;                                     // [NS][2][NE] rows ending at the slot
+  float4* sgeo = reinterpret_cast<float4*>(sfl + NS * 2 * NE);     // [NS][2][NE] (u, f_c)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sgeo + NS * 2 * NE);
+  uint64_t* wbar = bars;                 // Wf loaded
+  uint64_t* sbar = bars + 1;             // per stream: bready[2], bfree[2], tfull, tempty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + 6 * NS);
 
-  const int64_t r0 = (int64_t)blockIdx.x * p.rows_per_cta;
-  if (r0 >= p.n) return;
-  const int64_t r1 = (r0 + p.rows_per_cta < p.n) ? r0 + p.rows_per_cta : p.n;
-  const int64_t e0 = p.arow[r0], e1 = p.arow[r1];
-  const int ntiles = (int)((e1 - e0 + NE - 1) / NE);
+  if ((int64_t)blockIdx.x * p.rows_per_cta >= p.n) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     umma::mbar_init(wbar, 1);
-    for (int i = 0; i < 2; ++i) {
-      umma::mbar_init(&bready[i], 1);
-      umma::mbar_init(&bfree[i], 4);
+    for (int s = 0; s < NS; ++s) {
+      uint64_t* b = sbar + 6 * s;
+      umma::mbar_init(&b[0], 1);
+      umma::mbar_init(&b[1], 1);
+      umma::mbar_init(&b[2], 4);
+      umma::mbar_init(&b[3], 4);
+      umma::mbar_init(&b[4], 1);
+      umma::mbar_init(&b[5], 4);
     }
-    umma::mbar_init(tfull, 1);
-    umma::mbar_init(tempty, 4);
     umma::mbar_fence_init();
   }
-  if (warp == 1) umma::tmem_alloc(tmem_slot, 256);
+  if (warp == 2) umma::tmem_alloc(tmem_slot, 512);
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
-  int issued = 0;
+  int issued[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) issued[s] = 0;
 
-  if (warp == 0) {
-    if (lane == 0) {
+  if (warp < 2) {
+    if (warp == 0 && lane == 0) {
       umma::mbar_expect_tx(wbar, kWfBytes);
       for (int m = 0; m < 3; ++m) umma::tma_load_2d(sA + m * kWfTileBytes, &tmWf, 0, m * 128, wbar);
     }
     const float sig = p.rc / (float)(p.K - 1), inv2s2 = 1.0f / (2.0f * sig * sig), inv_rc = 1.0f / p.rc;
-    int64_t rp = r0;
-    while (rp < r1 && p.arow[rp + 1] == e0) ++rp;   // leading empty rows: flushed by the epilogue
-    for (int it = 0; it < ntiles; ++it) {
-      const int b = it & 1;
-      if (it >= 2 && !umma::mbar_wait(&bfree[b], ((it >> 1) - 1) & 1)) { ok = false; break; }
-      unsigned char* tile = sB + b * NE * 128;
-      const int64_t tb = e0 + (int64_t)it * NE;
-      for (int s = lane; s < NE; s += 32) {
-        const int64_t e = tb + s;
-        float rb[kKPad];
-        int j = 0;
-        float4 geo = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (e < e1) {
-          const float4 r = p.ar[e];
-          const float d = r.w, id = 1.0f / d;
-          geo = make_float4(r.x * id, r.y * id, r.z * id, 0.5f * (cospif(d * inv_rc) + 1.0f));
-          j = p.acol[e];
+    // producer warp w serves streams w, w + 2, ...; tiles are produced round-robin
+    StreamRange R[NS];
+    int64_t rp[NS];
+    int maxt = 0;
 #pragma unroll
-          for (int k = 0; k < kKPad; ++k) {
-            const float t = d - (float)k * sig;
-            rb[k] = k < p.K ? expf(-t * t * inv2s2) : 0.0f;
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < kKPad; ++k) rb[k] = 0.0f;
-        }
-        store_basis_row(tile, s, rb);
-        sj[b * NE + s] = j;
-        sgeo[b * NE + s] = geo;
-      }
-      mark_row_ends(lane, sfl + b * NE, NE, tb, r1, p.arow, rp);
-      umma::fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&bready[b]);
+    for (int s = 0; s < NS; ++s) {
+      R[s] = stream_range<NE, NS>(p, s);
+      rp[s] = R[s].r0;
+      while (rp[s] < R[s].r1 && p.arow[rp[s] + 1] == R[s].e0) ++rp[s];
+      maxt = R[s].ntiles > maxt ? R[s].ntiles : maxt;
     }
-  } else if (warp == 1) {
+    for (int it = 0; ok && it < maxt; ++it) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if ((s & 1) != warp || it >= R[s].ntiles) continue;
+        uint64_t* b = sbar + 6 * s;
+        const int bb = it & 1;
+        if (it >= 2 && !umma::mbar_wait(&b[2 + bb], ((it >> 1) - 1) & 1)) { ok = false; break; }
+        unsigned char* tile = sB + (s * 2 + bb) * NE * 128;
+        const int64_t tb = R[s].e0 + (int64_t)it * NE;
+        const int so = (s * 2 + bb) * NE;
+        for (int k0 = lane; k0 < NE; k0 += 32) {
+          const int64_t e = tb + k0;
+          float rb[kKPad];
+          int j = 0;
+          float4 geo = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (e < R[s].e1) {
+            const float4 r = p.ar[e];
+            const float d = r.w, id = 1.0f / d;
+            geo = make_float4(r.x * id, r.y * id, r.z * id, 0.5f * (cospif(d * inv_rc) + 1.0f));
+            j = p.acol[e];
+#pragma unroll
+            for (int k = 0; k < kKPad; ++k) {
+              const float t = d - (float)k * sig;
+              rb[k] = k < p.K ? expf(-t * t * inv2s2) : 0.0f;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < kKPad; ++k) rb[k] = 0.0f;
+          }
+          store_basis_row(tile, k0, rb);
+          sj[so + k0] = j;
+          sgeo[so + k0] = geo;
+        }
+        mark_row_ends(lane, sfl + so, NE, tb, R[s].r1, p.arow, rp[s]);
+        umma::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&b[bb]);
+      }
+    }
+  } else if (warp == 2) {
     if (lane == 0) {
       if (!umma::mbar_wait(wbar, 0)) ok = false;
       const uint32_t idesc = umma::idesc_bf16_m128(NE);
-      for (int it = 0; ok && it < ntiles; ++it) {
-        const int b = it & 1;
-        if (!umma::mbar_wait(&bready[b], (it >> 1) & 1)) { ok = false; break; }
-        if (it >= 1 && !umma::mbar_wait(tempty, (it - 1) & 1)) { ok = false; break; }
-        umma::fence_after();
-        const uint32_t bbase = umma::smem_u32(sB + b * NE * 128);
+      int nt[NS], maxt = 0;
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
+      for (int s = 0; s < NS; ++s) {
+        nt[s] = stream_range<NE, NS>(p, s).ntiles;
+        maxt = nt[s] > maxt ? nt[s] : maxt;
+      }
+      for (int it = 0; ok && it < maxt; ++it) {
 #pragma unroll
-          for (int k = 0; k < 2; ++k)
-            umma::mma_bf16(tmem + (uint32_t)(m * NE), umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * k),
-                           umma::desc_sw128(bbase + 32u * k), idesc, k > 0);
-        umma::mma_commit(tfull);
-        ++issued;
+        for (int s = 0; s < NS; ++s) {
+          if (it >= nt[s]) continue;
+          uint64_t* b = sbar + 6 * s;
+          const int bb = it & 1;
+          if (!umma::mbar_wait(&b[bb], (it >> 1) & 1)) { ok = false; break; }
+          if (it >= 1 && !umma::mbar_wait(&b[5], (it - 1) & 1)) { ok = false; break; }
+          umma::fence_after();
+          const uint32_t bbase = umma::smem_u32(sB + (s * 2 + bb) * NE * 128);
+#pragma unroll
+          for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+              umma::mma_bf16(tmem + (uint32_t)(s * 3 * NE + m * NE),
+                             umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * k),
+                             umma::desc_sw128(bbase + 32u * k), idesc, k > 0);
+          umma::mma_commit(&b[4]);
+          ++issued[s];
+        }
       }
     }
   } else {
+    const int s = (warp - 3) >> 2;         // stream of this epilogue warpgroup
     const int q = warp & 3, f = q * 32 + lane;
+    const StreamRange R = stream_range<NE, NS>(p, s);
+    uint64_t* b = sbar + 6 * s;
     const float bs = p.bf[f], bvv = p.bf[kF + f], bvs = p.bf[2 * kF + f];
-    int64_t r = r0;
+    int64_t r = R.r0;
     float as = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f;
     auto flush = [&]() {
       const int64_t i = r;
@@ -219,209 +269,229 @@ __global__ void __launch_bounds__(192, 2) k_edge_fwd_tc(const __grid_constant__ 
       as = a0 = a1 = a2 = 0.f;
       ++r;
     };
-    while (r < r1 && p.arow[r + 1] == e0) flush();
-    for (int it = 0; it < ntiles; ++it) {
-      const int b = it & 1;
-      if (!umma::mbar_wait(tfull, it & 1)) { ok = false; break; }
+    while (r < R.r1 && p.arow[r + 1] == R.e0) flush();
+    for (int it = 0; it < R.ntiles; ++it) {
+      const int bb = it & 1;
+      if (!umma::mbar_wait(&b[4], it & 1)) { ok = false; break; }
       umma::fence_after();
-      const int64_t tb = e0 + (int64_t)it * NE;
-      const int nlive = (int)((e1 - tb) < NE ? (e1 - tb) : NE);
-      const int* tj = sj + b * NE;
-      const int* tf = sfl + b * NE;
-      const float4* tg = sgeo + b * NE;
-      float ga[8][5], gb[8][5];
-      // neighbour messages of 8 edges: phi_s, psi_0..2, phi_vs of sender j, channel f
-      auto gather8 = [&](float (&G)[8][5], int s0) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const bool live = s0 + u < nlive;
-          const float* pj = p.PHI + (int64_t)(live ? tj[s0 + u] : 0) * 6 * kF + f;
-#pragma unroll
-          for (int k = 0; k < 5; ++k) G[u][k] = live ? __ldg(pj + k * kF) : 0.f;
-        }
-      };
-      auto compute8 = [&](const float (&G)[8][5], int s0, const float* ds, const float* dv, const float* dw) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (s0 + u < nlive) {
-            const float4 geo = tg[s0 + u];
-            const float fc = geo.w;
-            const float ws = (ds[u] + bs) * fc, wvv = (dv[u] + bvv) * fc, wvs = (dw[u] + bvs) * fc;
-            as = fmaf(G[u][0], ws, as);
-            const float tvs = G[u][4] * wvs;
-            a0 = fmaf(G[u][1], wvv, fmaf(geo.x, tvs, a0));
-            a1 = fmaf(G[u][2], wvv, fmaf(geo.y, tvs, a1));
-            a2 = fmaf(G[u][3], wvv, fmaf(geo.z, tvs, a2));
-            for (int nf = tf[s0 + u]; nf > 0; --nf) flush();
-          }
-        }
-      };
-      gather8(ga, 0);
-#pragma unroll
-      for (int c = 0; c < NE / 16; ++c) {
-        float ds[16], dv[16], dw[16];
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 16);
-        umma::tmem_ld16(ta, ds);
-        umma::tmem_ld16(ta + NE, dv);
-        umma::tmem_ld16(ta + 2 * NE, dw);
-        if (c == NE / 16 - 1) {
+      const int64_t tb = R.e0 + (int64_t)it * NE;
+      const int nlive = (int)((R.e1 - tb) < NE ? (R.e1 - tb) : NE);
+      const int so = (s * 2 + bb) * NE;
+      const int* tj = sj + so;
+      const int* tf = sfl + so;
+      const float4* tg = sgeo + so;
+#pragma unroll 1
+      for (int c = 0; c < NE / 8; ++c) {
+        float ds[8], dv[8], dw[8];
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * 3 * NE + c * 8);
+        umma::tmem_ld8(ta, ds);
+        umma::tmem_ld8(ta + NE, dv);
+        umma::tmem_ld8(ta + 2 * NE, dw);
+        if (c == NE / 8 - 1) {
           umma::fence_before();
           __syncwarp();
-          if (lane == 0) umma::mbar_arrive(tempty);
+          if (lane == 0) umma::mbar_arrive(&b[5]);
         }
-        gather8(gb, c * 16 + 8);
-        compute8(ga, c * 16, ds, dv, dw);
-        if (c + 1 < NE / 16) gather8(ga, (c + 1) * 16);
-        compute8(gb, c * 16 + 8, ds + 8, dv + 8, dw + 8);
+        float g[8][5];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool live = c * 8 + u < nlive;
+          const float* pj = p.PHI + (int64_t)(live ? tj[c * 8 + u] : 0) * 6 * kF + f;
+#pragma unroll
+          for (int k = 0; k < 5; ++k) g[u][k] = live ? __ldg(pj + k * kF) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int slot = c * 8 + u;
+          if (slot < nlive) {
+            const float4 geo = tg[slot];
+            const float fc = geo.w;
+            const float ws = (ds[u] + bs) * fc, wvv = (dv[u] + bvv) * fc, wvs = (dw[u] + bvs) * fc;
+            as = fmaf(g[u][0], ws, as);
+            const float tvs = g[u][4] * wvs;
+            a0 = fmaf(g[u][1], wvv, fmaf(geo.x, tvs, a0));
+            a1 = fmaf(g[u][2], wvv, fmaf(geo.y, tvs, a1));
+            a2 = fmaf(g[u][3], wvv, fmaf(geo.z, tvs, a2));
+            for (int nf = tf[slot]; nf > 0; --nf) flush();
+          }
+        }
       }
       __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&bfree[b]);
+      if (lane == 0) umma::mbar_arrive(&b[2 + bb]);
     }
     if (ok)
-      while (r < r1) flush();
+      while (r < R.r1) flush();
   }
   if (!ok) atomicOr(p.status, (int)ST_TIMEOUT);
-  // the MMAs of the last issued tile have completed before TMEM is released
-  if (warp == 1 && lane == 0 && issued > 0) umma::mbar_wait(tfull, (issued - 1) & 1, 200000000ull);
+  // the MMAs of every stream's last issued tile have completed before TMEM is released
+  if (warp == 2 && lane == 0)
+    for (int s = 0; s < NS; ++s)
+      if (issued[s] > 0) umma::mbar_wait(&sbar[6 * s + 4], (issued[s] - 1) & 1, 200000000ull);
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
-  if (warp == 1) umma::tmem_dealloc(tmem, 256);
+  if (warp == 2) umma::tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------------------------ adjoint
 // Sender-side: row j walks edges e' = (j <- i); the reverse edge (i <- j) carried phi_j, v_j
 // into receiver i with direction -u_e'.  Per tile the MMA gives both the filter W~ (basis)
 // and its radial derivative W~' (derivative basis).  Per edge the channel partials of dU/dd
-// and dU/du_rev are reduced over the four epilogue warps and turned into hedge[e'].
-template <int NE>
-__global__ void __launch_bounds__(192, 2) k_edge_bwd_tc(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
+// and dU/du_rev are reduced over the four warps of the stream's epilogue warpgroup and turned
+// into hedge[e'].
+template <int NE, int NS>
+__global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tc(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = align1024(smem_raw);
-  unsigned char* sA = smem;                                    // Wf tiles
-  unsigned char* sB = sA + kWfBytes;                           // [2][2][NE x 128 B] basis, derivative
-  int* sj = reinterpret_cast<int*>(sB + 4 * NE * 128);         // [2][NE]
-  int* sfl = sj + 2 * NE;                                      // [2][NE]
-  float4* sgeo = reinterpret_cast<float4*>(sfl + 2 * NE);      // [2][NE] (u, d)
-  float2* sfc = reinterpret_cast<float2*>(sgeo + 2 * NE);      // [2][NE] (f_c, f_c')
-  float* red = reinterpret_cast<float*>(sfc + 2 * NE);         // [NE][4 warps][4]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(red + NE * 16);
+  unsigned char* sA = smem;                                          // Wf tiles
+  unsigned char* sB = sA + kWfBytes;                                 // [NS][2][2][NE x 128 B]
+  int* sj = reinterpret_cast<int*>(sB + NS * 4 * NE * 128);          // [NS][2][NE]
+  int* sfl = sj + NS * 2 * NE;                                       // [NS][2][NE]
+  float4* sgeo = reinterpret_cast<float4*>(sfl + NS * 2 * NE);       // [NS][2][NE] (u, d)
+  float2* sfc = reinterpret_cast<float2*>(sgeo + NS * 2 * NE);       // [NS][2][NE] (f_c, f_c')
+  float* red = reinterpret_cast<float*>(sfc + NS * 2 * NE);          // [NS][NE][4 warps][4]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(red + NS * NE * 16);
   uint64_t* wbar = bars;
-  uint64_t* bready = bars + 1;   // [2]
-  uint64_t* bfree = bars + 3;    // [2]
-  uint64_t* tfull = bars + 5;
-  uint64_t* tempty = bars + 6;
-  uint64_t* esync = bars + 7;    // [2] epilogue warps: partials written / edge gradients written
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+  uint64_t* sbar = bars + 1;    // per stream: bready[2], bfree[2], tfull, tempty, esync[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + 8 * NS);
 
-  const int64_t r0 = (int64_t)blockIdx.x * p.rows_per_cta;
-  if (r0 >= p.n) return;
-  const int64_t r1 = (r0 + p.rows_per_cta < p.n) ? r0 + p.rows_per_cta : p.n;
-  const int64_t e0 = p.arow[r0], e1 = p.arow[r1];
-  const int ntiles = (int)((e1 - e0 + NE - 1) / NE);
+  if ((int64_t)blockIdx.x * p.rows_per_cta >= p.n) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     umma::mbar_init(wbar, 1);
-    for (int i = 0; i < 2; ++i) {
-      umma::mbar_init(&bready[i], 1);
-      umma::mbar_init(&bfree[i], 4);
+    for (int s = 0; s < NS; ++s) {
+      uint64_t* b = sbar + 8 * s;
+      umma::mbar_init(&b[0], 1);
+      umma::mbar_init(&b[1], 1);
+      umma::mbar_init(&b[2], 4);
+      umma::mbar_init(&b[3], 4);
+      umma::mbar_init(&b[4], 1);
+      umma::mbar_init(&b[5], 4);
+      umma::mbar_init(&b[6], 4);
+      umma::mbar_init(&b[7], 4);
     }
-    umma::mbar_init(tfull, 1);
-    umma::mbar_init(tempty, 4);
-    umma::mbar_init(&esync[0], 4);
-    umma::mbar_init(&esync[1], 4);
     umma::mbar_fence_init();
   }
-  if (warp == 1) umma::tmem_alloc(tmem_slot, 256);
+  if (warp == 2) umma::tmem_alloc(tmem_slot, 512);
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
-  int issued = 0;
+  int issued[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) issued[s] = 0;
 
-  if (warp == 0) {
-    if (lane == 0) {
+  if (warp < 2) {
+    if (warp == 0 && lane == 0) {
       umma::mbar_expect_tx(wbar, kWfBytes);
       for (int m = 0; m < 3; ++m) umma::tma_load_2d(sA + m * kWfTileBytes, &tmWf, 0, m * 128, wbar);
     }
     const float sig = p.rc / (float)(p.K - 1), inv2s2 = 1.0f / (2.0f * sig * sig), inv_s2 = 1.0f / (sig * sig);
     const float inv_rc = 1.0f / p.rc;
-    int64_t rp = r0;
-    while (rp < r1 && p.arow[rp + 1] == e0) ++rp;
-    for (int it = 0; it < ntiles; ++it) {
-      const int b = it & 1;
-      if (it >= 2 && !umma::mbar_wait(&bfree[b], ((it >> 1) - 1) & 1)) { ok = false; break; }
-      unsigned char* tile = sB + (2 * b) * NE * 128;
-      unsigned char* dtile = sB + (2 * b + 1) * NE * 128;
-      const int64_t tb = e0 + (int64_t)it * NE;
-      for (int s = lane; s < NE; s += 32) {
-        const int64_t e = tb + s;
-        float rb[kKPad], drb[kKPad];
-        int i = 0;
-        float4 geo = make_float4(0.f, 0.f, 0.f, 1.f);
-        float2 fcv = make_float2(0.f, 0.f);
-        if (e < e1) {
-          const float4 r = p.ar[e];
-          const float d = r.w, id = 1.0f / d;
-          geo = make_float4(r.x * id, r.y * id, r.z * id, d);
-          fcv = make_float2(0.5f * (cospif(d * inv_rc) + 1.0f), -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc));
-          i = p.acol[e];
+    StreamRange R[NS];
+    int64_t rp[NS];
+    int maxt = 0;
 #pragma unroll
-          for (int k = 0; k < kKPad; ++k) {
-            const float t = d - (float)k * sig;
-            const float v = k < p.K ? expf(-t * t * inv2s2) : 0.0f;
-            rb[k] = v;
-            drb[k] = -v * t * inv_s2;
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < kKPad; ++k) rb[k] = drb[k] = 0.0f;
-        }
-        store_basis_row(tile, s, rb);
-        store_basis_row(dtile, s, drb);
-        sj[b * NE + s] = i;
-        sgeo[b * NE + s] = geo;
-        sfc[b * NE + s] = fcv;
-      }
-      mark_row_ends(lane, sfl + b * NE, NE, tb, r1, p.arow, rp);
-      umma::fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&bready[b]);
+    for (int s = 0; s < NS; ++s) {
+      R[s] = stream_range<NE, NS>(p, s);
+      rp[s] = R[s].r0;
+      while (rp[s] < R[s].r1 && p.arow[rp[s] + 1] == R[s].e0) ++rp[s];
+      maxt = R[s].ntiles > maxt ? R[s].ntiles : maxt;
     }
-  } else if (warp == 1) {
+    for (int it = 0; ok && it < maxt; ++it) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if ((s & 1) != warp || it >= R[s].ntiles) continue;
+        uint64_t* b = sbar + 8 * s;
+        const int bb = it & 1;
+        if (it >= 2 && !umma::mbar_wait(&b[2 + bb], ((it >> 1) - 1) & 1)) { ok = false; break; }
+        unsigned char* tile = sB + ((s * 2 + bb) * 2) * NE * 128;
+        unsigned char* dtile = tile + NE * 128;
+        const int64_t tb = R[s].e0 + (int64_t)it * NE;
+        const int so = (s * 2 + bb) * NE;
+        for (int k0 = lane; k0 < NE; k0 += 32) {
+          const int64_t e = tb + k0;
+          float rb[kKPad], drb[kKPad];
+          int i = 0;
+          float4 geo = make_float4(0.f, 0.f, 0.f, 1.f);
+          float2 fcv = make_float2(0.f, 0.f);
+          if (e < R[s].e1) {
+            const float4 r = p.ar[e];
+            const float d = r.w, id = 1.0f / d;
+            geo = make_float4(r.x * id, r.y * id, r.z * id, d);
+            fcv = make_float2(0.5f * (cospif(d * inv_rc) + 1.0f), -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc));
+            i = p.acol[e];
+#pragma unroll
+            for (int k = 0; k < kKPad; ++k) {
+              const float t = d - (float)k * sig;
+              const float v = k < p.K ? expf(-t * t * inv2s2) : 0.0f;
+              rb[k] = v;
+              drb[k] = -v * t * inv_s2;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < kKPad; ++k) rb[k] = drb[k] = 0.0f;
+          }
+          store_basis_row(tile, k0, rb);
+          store_basis_row(dtile, k0, drb);
+          sj[so + k0] = i;
+          sgeo[so + k0] = geo;
+          sfc[so + k0] = fcv;
+        }
+        mark_row_ends(lane, sfl + so, NE, tb, R[s].r1, p.arow, rp[s]);
+        umma::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&b[bb]);
+      }
+    }
+  } else if (warp == 2) {
     if (lane == 0) {
       if (!umma::mbar_wait(wbar, 0)) ok = false;
       const uint32_t idesc = umma::idesc_bf16_m128(NE);
-      for (int it = 0; ok && it < ntiles; ++it) {
-        const int b = it & 1;
-        if (!umma::mbar_wait(&bready[b], (it >> 1) & 1)) { ok = false; break; }
-        if (it >= 1 && !umma::mbar_wait(tempty, (it - 1) & 1)) { ok = false; break; }
-        umma::fence_after();
+      int nt[NS], maxt = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {          // h = 0: basis -> W~, h = 1: derivative -> W~'
-          const uint32_t bbase = umma::smem_u32(sB + (2 * b + h) * NE * 128);
+      for (int s = 0; s < NS; ++s) {
+        nt[s] = stream_range<NE, NS>(p, s).ntiles;
+        maxt = nt[s] > maxt ? nt[s] : maxt;
+      }
+      for (int it = 0; ok && it < maxt; ++it) {
 #pragma unroll
-          for (int m = 0; m < 3; ++m)
+        for (int s = 0; s < NS; ++s) {
+          if (it >= nt[s]) continue;
+          uint64_t* b = sbar + 8 * s;
+          const int bb = it & 1;
+          if (!umma::mbar_wait(&b[bb], (it >> 1) & 1)) { ok = false; break; }
+          if (it >= 1 && !umma::mbar_wait(&b[5], (it - 1) & 1)) { ok = false; break; }
+          umma::fence_after();
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
-              umma::mma_bf16(tmem + (uint32_t)((3 * h + m) * NE),
-                             umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * k),
-                             umma::desc_sw128(bbase + 32u * k), idesc, k > 0);
+          for (int h = 0; h < 2; ++h) {          // h = 0: basis -> W~, h = 1: derivative -> W~'
+            const uint32_t bbase = umma::smem_u32(sB + ((s * 2 + bb) * 2 + h) * NE * 128);
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+              for (int k = 0; k < 2; ++k)
+                umma::mma_bf16(tmem + (uint32_t)(s * 6 * NE + (3 * h + m) * NE),
+                               umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * k),
+                               umma::desc_sw128(bbase + 32u * k), idesc, k > 0);
+          }
+          umma::mma_commit(&b[4]);
+          ++issued[s];
         }
-        umma::mma_commit(tfull);
-        ++issued;
       }
     }
   } else {
+    const int s = (warp - 3) >> 2;
     const int q = warp & 3, f = q * 32 + lane;
+    const StreamRange R = stream_range<NE, NS>(p, s);
+    uint64_t* b = sbar + 8 * s;
+    float* sred = red + s * NE * 16;
     const float bs = p.bf[f], bvv = p.bf[kF + f], bvs = p.bf[2 * kF + f];
-    int64_t r = r0;
-    // this row's own messages phi_s, psi_0..2, phi_vs (channel f), and the next row's, prefetched
+    int64_t r = R.r0;
     float cur[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, nxt[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     auto fetch = [&](int64_t row, float (&o)[5]) {
-      if (row < r1) {
+      if (row < R.r1) {
         const float* pj = p.PHI + row * 6 * kF + f;
 #pragma unroll
         for (int k = 0; k < 5; ++k) o[k] = __ldg(pj + k * kF);
@@ -439,34 +509,42 @@ __global__ void __launch_bounds__(192, 2) k_edge_bwd_tc(const __grid_constant__ 
     };
     fetch(r, cur);
     fetch(r + 1, nxt);
-    while (r < r1 && p.arow[r + 1] == e0) flush();
-    for (int it = 0; it < ntiles; ++it) {
-      const int b = it & 1;
-      if (!umma::mbar_wait(tfull, it & 1)) { ok = false; break; }
+    while (r < R.r1 && p.arow[r + 1] == R.e0) flush();
+    for (int it = 0; it < R.ntiles; ++it) {
+      const int bb = it & 1;
+      if (!umma::mbar_wait(&b[4], it & 1)) { ok = false; break; }
       umma::fence_after();
-      const int64_t tb = e0 + (int64_t)it * NE;
-      const int nlive = (int)((e1 - tb) < NE ? (e1 - tb) : NE);
-      const int* ti = sj + b * NE;
-      const int* tf = sfl + b * NE;
-      const float4* tg = sgeo + b * NE;
-      const float2* tc = sfc + b * NE;
-      float ga[8][4], gb[8][4];
-      // receivers' gradients (gsm_i, gvm_i) of 8 edges, channel f
-      auto gather8 = [&](float (&G)[8][4], int s0) {
+      const int64_t tb = R.e0 + (int64_t)it * NE;
+      const int nlive = (int)((R.e1 - tb) < NE ? (R.e1 - tb) : NE);
+      const int so = (s * 2 + bb) * NE;
+      const int* ti = sj + so;
+      const int* tf = sfl + so;
+      const float4* tg = sgeo + so;
+      const float2* tc = sfc + so;
+#pragma unroll 1
+      for (int c = 0; c < NE / 8; ++c) {
+        float W[6][8];
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * 6 * NE + c * 8);
+#pragma unroll
+        for (int h = 0; h < 6; ++h) umma::tmem_ld8(ta + h * NE, W[h]);
+        if (c == NE / 8 - 1) {
+          umma::fence_before();
+          __syncwarp();
+          if (lane == 0) umma::mbar_arrive(&b[5]);
+        }
+        float G[8][4];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const bool live = s0 + u < nlive;
-          const int64_t i = live ? ti[s0 + u] : 0;
+          const bool live = c * 8 + u < nlive;
+          const int64_t i = live ? ti[c * 8 + u] : 0;
           G[u][0] = live ? __ldg(p.Gsm + i * kF + f) : 0.f;
           G[u][1] = live ? __ldg(p.Gvm + i * 3 * kF + f) : 0.f;
           G[u][2] = live ? __ldg(p.Gvm + i * 3 * kF + kF + f) : 0.f;
           G[u][3] = live ? __ldg(p.Gvm + i * 3 * kF + 2 * kF + f) : 0.f;
         }
-      };
-      auto compute8 = [&](const float (&G)[8][4], int s0, const float (&W)[6][8]) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const int slot = s0 + u;
+          const int slot = c * 8 + u;
           float pd = 0.f, pu0 = 0.f, pu1 = 0.f, pu2 = 0.f;
           const bool live = slot < nlive;
           if (live) {
@@ -499,41 +577,21 @@ __global__ void __launch_bounds__(192, 2) k_edge_bwd_tc(const __grid_constant__ 
           kk += __shfl_xor_sync(0xffffffffu, kk, 4);
           kk += __shfl_xor_sync(0xffffffffu, kk, 2);
           kk += __shfl_xor_sync(0xffffffffu, kk, 1);
-          if ((lane & 7) == 0) red[(slot * 4 + q) * 4 + (lane >> 3)] = kk;
+          if ((lane & 7) == 0) sred[(slot * 4 + q) * 4 + (lane >> 3)] = kk;
           if (live)
             for (int nf = tf[slot]; nf > 0; --nf) flush();
         }
-      };
-      gather8(ga, 0);
-#pragma unroll
-      for (int c = 0; c < NE / 8; ++c) {
-        float W[6][8];
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 8);
-#pragma unroll
-        for (int h = 0; h < 6; ++h) umma::tmem_ld8(ta + h * NE, W[h]);
-        if (c == NE / 8 - 1) {
-          umma::fence_before();
-          __syncwarp();
-          if (lane == 0) umma::mbar_arrive(tempty);
-        }
-        if (c % 2 == 0) {
-          if (c + 1 < NE / 8) gather8(gb, (c + 1) * 8);
-          compute8(ga, c * 8, W);
-        } else {
-          if (c + 1 < NE / 8) gather8(ga, (c + 1) * 8);
-          compute8(gb, c * 8, W);
-        }
       }
-      // all four epilogue warps have written their partials for this tile
+      // the four warps of this stream have written their partials for the tile
       __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&esync[0]);
-      if (!umma::mbar_wait(&esync[0], it & 1)) { ok = false; break; }
-      const int t = f;   // 128 threads, NE <= 128 slots
+      if (lane == 0) umma::mbar_arrive(&b[6]);
+      if (!umma::mbar_wait(&b[6], it & 1)) { ok = false; break; }
+      const int t = f;
       if (t < nlive) {
         float pd = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-          const float* rr = red + (t * 4 + w) * 4;
+          const float* rr = sred + (t * 4 + w) * 4;
           pd += rr[0]; g0 += rr[1]; g1 += rr[2]; g2 += rr[3];
         }
         const float4 geo = tg[t];
@@ -549,42 +607,44 @@ __global__ void __launch_bounds__(192, 2) k_edge_bwd_tc(const __grid_constant__ 
         p.hedge[e] = h;
       }
       __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&esync[1]);
-      if (!umma::mbar_wait(&esync[1], it & 1)) { ok = false; break; }
-      if (lane == 0) umma::mbar_arrive(&bfree[b]);
+      if (lane == 0) umma::mbar_arrive(&b[7]);
+      if (!umma::mbar_wait(&b[7], it & 1)) { ok = false; break; }
+      if (lane == 0) umma::mbar_arrive(&b[2 + bb]);
     }
     if (ok)
-      while (r < r1) flush();
+      while (r < R.r1) flush();
   }
   if (!ok) atomicOr(p.status, (int)ST_TIMEOUT);
-  // the MMAs of the last issued tile have completed before TMEM is released
-  if (warp == 1 && lane == 0 && issued > 0) umma::mbar_wait(tfull, (issued - 1) & 1, 200000000ull);
+  if (warp == 2 && lane == 0)
+    for (int s = 0; s < NS; ++s)
+      if (issued[s] > 0) umma::mbar_wait(&sbar[8 * s + 4], (issued[s] - 1) & 1, 200000000ull);
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
-  if (warp == 1) umma::tmem_dealloc(tmem, 256);
+  if (warp == 2) umma::tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------------------------ host side
-constexpr int kFwdNE = 64, kBwdNE = 32;
+constexpr int kFwdNE = 32, kFwdNS = 4;   // 4 streams x 3 x 32 TMEM columns, 16 epilogue warps
+constexpr int kBwdNE = 16, kBwdNS = 3;   // 3 streams x 6 x 16 TMEM columns, 12 epilogue warps
 
 static size_t fwd_smem() {
-  size_t s = 1024 + kWfBytes + 2 * kFwdNE * 128 + 4 * kFwdNE * 4 + 2 * kFwdNE * 16 + 128;
-  return s < 80 * 1024 ? 80 * 1024 : s;   // at most two CTAs per SM: 2 x 256 TMEM columns
+  return 1024 + kWfBytes + (size_t)kFwdNS * 2 * kFwdNE * 128 + (size_t)kFwdNS * 2 * kFwdNE * (4 + 4 + 16) +
+         8 * (1 + 6 * kFwdNS) + 64;
 }
 static size_t bwd_smem() {
-  size_t s = 1024 + kWfBytes + 4 * kBwdNE * 128 + 4 * kBwdNE * 4 + 2 * kBwdNE * 16 + 2 * kBwdNE * 8 +
-             kBwdNE * 16 * 4 + 256;
-  return s < 80 * 1024 ? 80 * 1024 : s;
+  return 1024 + kWfBytes + (size_t)kBwdNS * 4 * kBwdNE * 128 + (size_t)kBwdNS * 2 * kBwdNE * (4 + 4 + 16 + 8) +
+         (size_t)kBwdNS * kBwdNE * 16 * 4 + 8 * (1 + 8 * kBwdNS) + 64;
 }
 
 bool edge_tc_supported(int F, int K) { return F == kF && K <= kKPad && K >= 2; }
 
+// One CTA per SM (512 TMEM columns each), rows split evenly over the CTAs.
 static int grid_for(int64_t n, int64_t* rows_per_cta) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t ctas = 2LL * sms;
+  int64_t ctas = sms;
   int64_t rpc = (n + ctas - 1) / ctas;
   if (rpc < 1) rpc = 1;
   *rows_per_cta = rpc;
@@ -603,11 +663,11 @@ int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_
   const int grid = grid_for(n, &a.rows_per_cta);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
+    cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     attr = true;
   }
   LaunchScope ls_(st);
-  k_edge_fwd_tc<kFwdNE><<<grid, 192, fwd_smem(), st>>>(tm, a);
+  k_edge_fwd_tc<kFwdNE, kFwdNS><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
   return 0;
 }
 
@@ -623,11 +683,11 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
   const int grid = grid_for(n, &a.rows_per_cta);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_edge_bwd_tc<kBwdNE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tc<kBwdNE, kBwdNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
     attr = true;
   }
   LaunchScope ls_(st);
-  k_edge_bwd_tc<kBwdNE><<<grid, 192, bwd_smem(), st>>>(tm, a);
+  k_edge_bwd_tc<kBwdNE, kBwdNS><<<grid, 32 * (3 + 4 * kBwdNS), bwd_smem(), st>>>(tm, a);
   return 0;
 }
 
