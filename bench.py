@@ -215,7 +215,7 @@ def run_ours(args):
             continue
         if args.tc_adjoint and prec == "bf16":
             from paper_2506_04055_gb300 import _lib as L
-            pot.set_option(L.CTD_OPT_TC_ADJOINT, 1)
+            pot.set_option(L.CTD_OPT_TC_ADJOINT, args.tc_adjoint)
         pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=SKIN)
         for _ in range(args.warmup):
             pot.md_run(1, DT)
@@ -360,7 +360,8 @@ def main():
     ap.add_argument("--precision", default="both", choices=["fp32", "bf16", "both"])
     ap.add_argument("--cells", type=int, default=FCC_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tc-adjoint", action="store_true", help="BF16: edge adjoint with the tcgen05 filter")
+    ap.add_argument("--tc-adjoint", type=int, default=0,
+                    help="BF16: edge adjoint with the tcgen05 filter (1 register gathers, 2 bulk-copy gathers)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

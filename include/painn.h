@@ -140,9 +140,10 @@ int ctd_md_run(ctd_ctx *ctx, int32_t nsteps, double dt, double *epot, double *ek
 int ctd_md_get_state(ctd_ctx *ctx, double *positions, double *velocities);
 
 /* ---- options -------------------------------------------------------------------------- */
-/* CTD_OPT_TC_ADJOINT (value 0/1, default 0): on the BF16 path with F = 128, run the edge
- * adjoint with the radial filter on tcgen05 as well (the message kernel always does).  The
- * CUDA-core adjoint is the default because it is faster on the 1M-atom fcc workload. */
+/* CTD_OPT_TC_ADJOINT (value 0, 1 or 2; default 0): on the BF16 path with F = 128, run the
+ * edge adjoint with the radial filter on tcgen05 as well (the message kernel always does):
+ * 1 = neighbour gradients gathered into registers, 2 = gathered into shared memory by bulk
+ * asynchronous copies.  0 keeps the CUDA-core adjoint. */
 #define CTD_OPT_TC_ADJOINT 1
 int ctd_set_option(ctd_ctx *ctx, int32_t option, int64_t value);
 

@@ -601,7 +601,9 @@ int ctd_set_option(ctd_ctx* c, int32_t option, int64_t value) {
   if (!c) return CTD_ERR_INVALID_ARG;
   switch (option) {
     case CTD_OPT_TC_ADJOINT:
+      if (value < 0 || value > 2) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0, 1 or 2");
       c->mw.tc_adjoint = value != 0;
+      c->mw.tc_adjoint_variant = (int)value;
       return CTD_OK;
     default:
       return fail(c, CTD_ERR_INVALID_ARG, "unknown option");

@@ -101,6 +101,7 @@ struct ModelW {
   const float *R1, *R1t, *d1, *R2, *d2;   // [F/2][F], [F][F/2]
   const __nv_bfloat16 *R1b, *R1tb;
   bool tc_adjoint;                 // BF16 path: edge adjoint with the tensor-core filter
+  int tc_adjoint_variant;          // 1: register gathers, 2: bulk-copy gathers into shared memory
 };
 
 // ---------------------------------------------------------------- small device helpers

@@ -624,9 +624,312 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tc(const __gr
   if (warp == 2) umma::tmem_dealloc(tmem, 512);
 }
 
+// ------------------------------------------------------------------------------ adjoint, bulk-gathered
+// Same arithmetic as k_edge_bwd_tc; the receivers' gradient rows (gsm_i: F floats, gvm_i: 3F
+// floats) of a tile's edges are brought into shared memory by cp.async.bulk copies issued by
+// the producer and completed on the tile's mbarrier, so the epilogue reads only shared memory
+// and TMEM.  Two row streams, tiles of NE edges, basis and gather buffers double-buffered.
+template <int NE, int NS>
+__global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
+  static_assert(NS <= 2, "one producer warp per stream");
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = align1024(smem_raw);
+  unsigned char* sA = smem;                                          // Wf tiles
+  unsigned char* sB = sA + kWfBytes;                                 // [NS][2][2][NE x 128 B]
+  float* sG = reinterpret_cast<float*>(sB + NS * 4 * NE * 128);      // [NS][2][NE][4F]
+  int* sj = reinterpret_cast<int*>(sG + (size_t)NS * 2 * NE * 4 * kF);   // [NS][2][NE]
+  int* sfl = sj + NS * 2 * NE;                                       // [NS][2][NE]
+  float4* sgeo = reinterpret_cast<float4*>(sfl + NS * 2 * NE);       // [NS][2][NE] (u, d)
+  float2* sfc = reinterpret_cast<float2*>(sgeo + NS * 2 * NE);       // [NS][2][NE] (f_c, f_c')
+  float* red = reinterpret_cast<float*>(sfc + NS * 2 * NE);          // [NS][NE][4 warps][4]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(red + NS * NE * 16);
+  uint64_t* wbar = bars;
+  uint64_t* sbar = bars + 1;    // per stream: bready[2], bfree[2], tfull, tempty, esync[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + 8 * NS);
+
+  if ((int64_t)blockIdx.x * p.rows_per_cta >= p.n) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    umma::mbar_init(wbar, 1);
+    for (int s = 0; s < NS; ++s) {
+      uint64_t* b = sbar + 8 * s;
+      umma::mbar_init(&b[0], 1);
+      umma::mbar_init(&b[1], 1);
+      umma::mbar_init(&b[2], 4);
+      umma::mbar_init(&b[3], 4);
+      umma::mbar_init(&b[4], 1);
+      umma::mbar_init(&b[5], 4);
+      umma::mbar_init(&b[6], 4);
+      umma::mbar_init(&b[7], 4);
+    }
+    umma::mbar_fence_init();
+  }
+  if (warp == 2) umma::tmem_alloc(tmem_slot, 256);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  int issued[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) issued[s] = 0;
+  int gathered = 0;   // producer: tiles whose bulk copies were issued
+
+  if (warp < 2) {
+    if (warp == 0 && lane == 0) {
+      umma::mbar_expect_tx(wbar, kWfBytes);
+      for (int m = 0; m < 3; ++m) umma::tma_load_2d(sA + m * kWfTileBytes, &tmWf, 0, m * 128, wbar);
+    }
+    if (warp < NS) {
+      const int s = warp;
+      const float sig = p.rc / (float)(p.K - 1), inv2s2 = 1.0f / (2.0f * sig * sig), inv_s2 = 1.0f / (sig * sig);
+      const float inv_rc = 1.0f / p.rc;
+      const StreamRange R = stream_range<NE, NS>(p, s);
+      int64_t rp = R.r0;
+      while (rp < R.r1 && p.arow[rp + 1] == R.e0) ++rp;
+      uint64_t* b = sbar + 8 * s;
+      for (int it = 0; it < R.ntiles; ++it) {
+        const int bb = it & 1;
+        if (it >= 2 && !umma::mbar_wait(&b[2 + bb], ((it >> 1) - 1) & 1)) { ok = false; break; }
+        const int64_t tb = R.e0 + (int64_t)it * NE;
+        const int nlive = (int)((R.e1 - tb) < NE ? (R.e1 - tb) : NE);
+        const int so = (s * 2 + bb) * NE;
+        float* g = sG + (size_t)so * 4 * kF;
+        if (lane == 0) umma::mbar_expect_tx_only(&b[bb], (uint32_t)(nlive * 4 * kF * 4));
+        __syncwarp();
+        unsigned char* tile = sB + ((s * 2 + bb) * 2) * NE * 128;
+        unsigned char* dtile = tile + NE * 128;
+        for (int k0 = lane; k0 < NE; k0 += 32) {
+          const int64_t e = tb + k0;
+          float rb[kKPad], drb[kKPad];
+          int i = 0;
+          float4 geo = make_float4(0.f, 0.f, 0.f, 1.f);
+          float2 fcv = make_float2(0.f, 0.f);
+          if (k0 < nlive) {
+            const float4 r = p.ar[e];
+            const float d = r.w, id = 1.0f / d;
+            geo = make_float4(r.x * id, r.y * id, r.z * id, d);
+            fcv = make_float2(0.5f * (cospif(d * inv_rc) + 1.0f), -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc));
+            i = p.acol[e];
+            umma::bulk_copy_g2s(g + (size_t)k0 * 4 * kF, p.Gsm + (int64_t)i * kF, kF * 4, &b[bb]);
+            umma::bulk_copy_g2s(g + (size_t)k0 * 4 * kF + kF, p.Gvm + (int64_t)i * 3 * kF, 3 * kF * 4, &b[bb]);
+#pragma unroll
+            for (int k = 0; k < kKPad; ++k) {
+              const float t = d - (float)k * sig;
+              const float v = k < p.K ? expf(-t * t * inv2s2) : 0.0f;
+              rb[k] = v;
+              drb[k] = -v * t * inv_s2;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < kKPad; ++k) rb[k] = drb[k] = 0.0f;
+          }
+          store_basis_row(tile, k0, rb);
+          store_basis_row(dtile, k0, drb);
+          sj[so + k0] = i;
+          sgeo[so + k0] = geo;
+          sfc[so + k0] = fcv;
+        }
+        gathered = it + 1;
+        mark_row_ends(lane, sfl + so, NE, tb, R.r1, p.arow, rp);
+        umma::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&b[bb]);
+      }
+    }
+  } else if (warp == 2) {
+    if (lane == 0) {
+      if (!umma::mbar_wait(wbar, 0)) ok = false;
+      const uint32_t idesc = umma::idesc_bf16_m128(NE);
+      int nt[NS], maxt = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        nt[s] = stream_range<NE, NS>(p, s).ntiles;
+        maxt = nt[s] > maxt ? nt[s] : maxt;
+      }
+      for (int it = 0; ok && it < maxt; ++it) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          if (it >= nt[s]) continue;
+          uint64_t* b = sbar + 8 * s;
+          const int bb = it & 1;
+          if (!umma::mbar_wait(&b[bb], (it >> 1) & 1)) { ok = false; break; }
+          if (it >= 1 && !umma::mbar_wait(&b[5], (it - 1) & 1)) { ok = false; break; }
+          umma::fence_after();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t bbase = umma::smem_u32(sB + ((s * 2 + bb) * 2 + h) * NE * 128);
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+              for (int k = 0; k < 2; ++k)
+                umma::mma_bf16(tmem + (uint32_t)(s * 6 * NE + (3 * h + m) * NE),
+                               umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * k),
+                               umma::desc_sw128(bbase + 32u * k), idesc, k > 0);
+          }
+          umma::mma_commit(&b[4]);
+          ++issued[s];
+        }
+      }
+    }
+  } else {
+    const int s = (warp - 3) >> 2;
+    const int q = warp & 3, f = q * 32 + lane;
+    const StreamRange R = stream_range<NE, NS>(p, s);
+    uint64_t* b = sbar + 8 * s;
+    const float bs = p.bf[f], bvv = p.bf[kF + f], bvs = p.bf[2 * kF + f];
+    int64_t r = R.r0;
+    float cur[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, nxt[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    auto fetch = [&](int64_t row, float (&o)[5]) {
+      if (row < R.r1) {
+        const float* pj = p.PHI + row * 6 * kF + f;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) o[k] = __ldg(pj + k * kF);
+      }
+    };
+    float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
+    auto flush = [&]() {
+      float* o = p.GPHI + r * 5 * kF;
+      o[f] = gps; o[kF + f] = gy0; o[2 * kF + f] = gy1; o[3 * kF + f] = gy2; o[4 * kF + f] = gpvs;
+      gps = gy0 = gy1 = gy2 = gpvs = 0.f;
+      ++r;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) cur[k] = nxt[k];
+      fetch(r + 1, nxt);
+    };
+    fetch(r, cur);
+    fetch(r + 1, nxt);
+    while (r < R.r1 && p.arow[r + 1] == R.e0) flush();
+    for (int it = 0; it < R.ntiles; ++it) {
+      const int bb = it & 1;
+      if (!umma::mbar_wait(&b[4], it & 1)) { ok = false; break; }
+      // the tile's gather phase completed before the MMA thread issued it; waiting on it here
+      // returns at once and makes the bulk-copied rows visible to this thread
+      if (!umma::mbar_wait(&b[bb], (it >> 1) & 1)) { ok = false; break; }
+      umma::fence_after();
+      const int64_t tb = R.e0 + (int64_t)it * NE;
+      const int nlive = (int)((R.e1 - tb) < NE ? (R.e1 - tb) : NE);
+      const int so = (s * 2 + bb) * NE;
+      const int* tf = sfl + so;
+      const float4* tg = sgeo + so;
+      const float2* tc = sfc + so;
+      float* tG = sG + (size_t)so * 4 * kF + f;   // this thread's feature in each gathered row
+#pragma unroll 1
+      for (int c = 0; c < NE / 8; ++c) {
+        float W[6][8];
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * 6 * NE + c * 8);
+#pragma unroll
+        for (int h = 0; h < 6; ++h) umma::tmem_ld8(ta + h * NE, W[h]);
+        if (c == NE / 8 - 1) {
+          umma::fence_before();
+          __syncwarp();
+          if (lane == 0) umma::mbar_arrive(&b[5]);
+        }
+        // Per edge: accumulate the row's phi gradients, and overwrite this thread's gathered
+        // gradients in place with its partials of (dU/dd, dU/du) for the reduction over features.
+        auto edge = [&](int u, int slot) {
+          float* gg = tG + (size_t)slot * 4 * kF;
+          const float gs = gg[0], gv0 = gg[kF], gv1 = gg[2 * kF], gv2 = gg[3 * kF];
+          const float4 geo = tg[slot];
+          const float2 fcv = tc[slot];
+          const float ws = W[0][u] + bs, wvv = W[1][u] + bvv, wvs = W[2][u] + bvs;
+          const float fc = fcv.x, dfc = fcv.y;
+          const float Ws = ws * fc, Wvv = wvv * fc, Wvs = wvs * fc;
+          gps = fmaf(gs, Ws, gps);
+          gy0 = fmaf(gv0, Wvv, gy0);
+          gy1 = fmaf(gv1, Wvv, gy1);
+          gy2 = fmaf(gv2, Wvv, gy2);
+          const float qv = -(gv0 * geo.x + gv1 * geo.y + gv2 * geo.z);
+          gpvs = fmaf(qv, Wvs, gpvs);
+          const float gWs = gs * cur[0], gWvv = gv0 * cur[1] + gv1 * cur[2] + gv2 * cur[3], gWvs = qv * cur[4];
+          const float tv = cur[4] * Wvs;
+          gg[0] = fc * (gWs * W[3][u] + gWvv * W[4][u] + gWvs * W[5][u]) + dfc * (gWs * ws + gWvv * wvv + gWvs * wvs);
+          gg[kF] = gv0 * tv;
+          gg[2 * kF] = gv1 * tv;
+          gg[3 * kF] = gv2 * tv;
+        };
+        const int4 fa = *reinterpret_cast<const int4*>(tf + c * 8), fb = *reinterpret_cast<const int4*>(tf + c * 8 + 4);
+        if ((fa.x | fa.y | fa.z | fa.w | fb.x | fb.y | fb.z | fb.w) == 0 && c * 8 + 8 <= nlive) {
+          // no row ends in these eight edges: straight-line code the compiler can interleave
+#pragma unroll
+          for (int u = 0; u < 8; ++u) edge(u, c * 8 + u);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int slot = c * 8 + u;
+            if (slot < nlive) {
+              edge(u, slot);
+              for (int nf = tf[slot]; nf > 0; --nf) flush();
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&b[6]);
+      if (!umma::mbar_wait(&b[6], it & 1)) { ok = false; break; }
+      {
+        // Reduction over the F features: thread f sums half (h) of component `comp` of edge
+        // `slot`, starting at a lane-dependent rotation so that a quarter-warp's 16-byte reads
+        // fall in distinct banks; the two halves combine across lanes 2k, 2k+1, and lane 8k then
+        // holds the four components of edge 4q + k.
+        const int o = f >> 1, slot = o >> 2, comp = o & 3, h = f & 1;
+        float acc = 0.f;
+        if (slot < nlive) {
+          const float* base = sG + (size_t)so * 4 * kF + (size_t)slot * 4 * kF + comp * kF + h * 64;
+          float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float4 v = *reinterpret_cast<const float4*>(base + ((4 * i + 4 * lane) & 63));
+            a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
+          }
+          acc = (a0 + a1) + (a2 + a3);
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        const float g0 = __shfl_down_sync(0xffffffffu, acc, 2);
+        const float g1 = __shfl_down_sync(0xffffffffu, acc, 4);
+        const float g2 = __shfl_down_sync(0xffffffffu, acc, 6);
+        if ((lane & 7) == 0 && slot < nlive) {
+          const float pd = acc;
+          const float4 geo = tg[slot];
+          const float ux = -geo.x, uy = -geo.y, uz = -geo.z, id = 1.0f / geo.w;
+          const float gdu = g0 * ux + g1 * uy + g2 * uz;
+          float4 hv = make_float4(pd * ux + (g0 - gdu * ux) * id, pd * uy + (g1 - gdu * uy) * id,
+                                  pd * uz + (g2 - gdu * uz) * id, 0.f);
+          const int64_t e = tb + slot;
+          if (p.accumulate) {
+            const float4 ov = p.hedge[e];
+            hv.x += ov.x; hv.y += ov.y; hv.z += ov.z;
+          }
+          p.hedge[e] = hv;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&b[2 + bb]);
+    }
+    if (ok)
+      while (r < R.r1) flush();
+  }
+  if (!ok) atomicOr(p.status, (int)ST_TIMEOUT);
+  if (warp < NS && lane == 0) {
+    // the bulk copies of the last two tiles this producer issued have landed before the CTA
+    // exits (in a normal run both phases completed long ago and the waits return at once)
+    for (int t = gathered - 2; t < gathered; ++t)
+      if (t >= 0) umma::mbar_wait(&sbar[8 * warp + (t & 1)], (t >> 1) & 1, 200000000ull);
+  }
+  if (warp == 2 && lane == 0)
+    for (int s = 0; s < NS; ++s)
+      if (issued[s] > 0) umma::mbar_wait(&sbar[8 * s + 4], (issued[s] - 1) & 1, 200000000ull);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  if (warp == 2) umma::tmem_dealloc(tmem, 256);
+}
+
 // ------------------------------------------------------------------------------ host side
 constexpr int kFwdNE = 32, kFwdNS = 4;   // 4 streams x 3 x 32 TMEM columns, 16 epilogue warps
 constexpr int kBwdNE = 16, kBwdNS = 3;   // 3 streams x 6 x 16 TMEM columns, 12 epilogue warps
+constexpr int kBwgNE = 16, kBwgNS = 2;   // bulk-gathered adjoint: 2 streams, double-buffered tiles
 
 static size_t fwd_smem() {
   return 1024 + kWfBytes + (size_t)kFwdNS * 2 * kFwdNE * 128 + (size_t)kFwdNS * 2 * kFwdNE * (4 + 4 + 16) +
@@ -635,6 +938,11 @@ static size_t fwd_smem() {
 static size_t bwd_smem() {
   return 1024 + kWfBytes + (size_t)kBwdNS * 4 * kBwdNE * 128 + (size_t)kBwdNS * 2 * kBwdNE * (4 + 4 + 16 + 8) +
          (size_t)kBwdNS * kBwdNE * 16 * 4 + 8 * (1 + 8 * kBwdNS) + 64;
+}
+
+static size_t bwg_smem() {
+  return 1024 + kWfBytes + (size_t)kBwgNS * 4 * kBwgNE * 128 + (size_t)kBwgNS * 2 * kBwgNE * 4 * kF * 4 +
+         (size_t)kBwgNS * 2 * kBwgNE * (4 + 4 + 16 + 8) + (size_t)kBwgNS * kBwgNE * 16 * 4 + 8 * (1 + 8 * kBwgNS) + 64;
 }
 
 bool edge_tc_supported(int F, int K) { return F == kF && K <= kKPad && K >= 2; }
@@ -684,10 +992,14 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_edge_bwd_tc<kBwdNE, kBwdNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     attr = true;
   }
   LaunchScope ls_(st);
-  k_edge_bwd_tc<kBwdNE, kBwdNS><<<grid, 32 * (3 + 4 * kBwdNS), bwd_smem(), st>>>(tm, a);
+  if (m.tc_adjoint_variant == 2)
+    k_edge_bwd_tcg<kBwgNE, kBwgNS><<<grid, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
+  else
+    k_edge_bwd_tc<kBwdNE, kBwdNS><<<grid, 32 * (3 + 4 * kBwdNS), bwd_smem(), st>>>(tm, a);
   return 0;
 }
 
