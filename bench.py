@@ -213,7 +213,7 @@ def run_ours(args):
         except eng.CtdError as e:
             results[prec] = {"error": str(e)}
             continue
-        if args.tc_adjoint and prec == "bf16":
+        if args.tc_adjoint is not None and prec == "bf16":
             from paper_2506_04055_gb300 import _lib as L
             pot.set_option(L.CTD_OPT_TC_ADJOINT, args.tc_adjoint)
         pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=SKIN)
@@ -351,6 +351,286 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ supplementary workloads
+# The default run above is the 1M-atom fcc line.  --workload selects one of the other
+# configurations of the method's evaluation (each prints its own JSON line):
+#   water192   192-atom water, F=64, T=3: E+F+W call latency, 100-step NVE drift vs the oracle
+#   water96k   96,000-atom water, F=64, T=3, skin 1 A: 1,000 NVE steps, p50/p99, drift
+#   mixture90k 90,300-atom triclinic 4-species mixture, F=64, T=2: stored vs recomputed edge filters
+#   serve      512 replicas (log-uniform 64..20,000 atoms, water / fcc), Poisson arrivals swept
+#              around the saturation rate; p50/p99 latency vs serial per-system FP32 launches
+
+
+def _init_engine():
+    import torch
+
+    import paper_2506_04055_gb300 as eng
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    eng.build()
+    eng.load()
+    return eng, torch
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))] if xs else None
+
+
+def _timed_md(pot, torch, steps, warmup, dt):
+    """steps x md_run(1) with CUDA events per step on the context's (torch's) stream; returns
+    per-step ms, total ms, energy series (steps + 1), rebuilds, stage profile, clocks."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        pot.md_run(1, dt)
+    torch.cuda.synchronize()
+    pot.profile(True)
+    pot.profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ep_s, ek_s, reb = [], [], 0
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(steps):
+            ev[k][0].record(stream)
+            ep, ek, nreb = pot.md_run(1, dt)
+            ev[k][1].record(stream)
+            if k == 0:
+                ep_s.append(ep[0]); ek_s.append(ek[0])
+            ep_s.append(ep[1]); ek_s.append(ek[1])
+            reb += nreb
+        t1.record(stream)
+        torch.cuda.synchronize()
+    prof = pot.profile_read(reset=True)
+    pot.profile(False)
+    return {"step_ms": [a.elapsed_time(b) for a, b in ev], "total_ms": t0.elapsed_time(t1),
+            "ep": np.array(ep_s), "ek": np.array(ek_s), "rebuilds": reb,
+            "stage_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
+            "launches": int(sum(v[1] for v in prof.values())), "clocks": clk.summary()}
+
+
+def _md_line(metric, n, steps, warmup, r, dtype, config, extra):
+    e = r["ep"] + r["ek"]
+    line = {"metric": metric, "value": n * steps / (r["total_ms"] / 1e3), "unit": "atom-steps/s", "n_gpus": 1,
+            "steps": steps, "warmup": warmup, "ms_per_step": r["total_ms"] / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config,
+            "p50_ms": _pct(r["step_ms"], 0.5), "p99_ms": _pct(r["step_ms"], 0.99), "rebuilds": r["rebuilds"],
+            "drift_ev_per_atom": float((e[-1] - e[0]) / n), "max_abs_dE_ev_per_atom": float(np.abs(e - e[0]).max() / n),
+            "stage_ms_per_step": r["stage_ms_per_step"], "gpu_launches": r["launches"], "clocks": r["clocks"]}
+    line.update(extra)
+    return line
+
+
+def run_water192(args):
+    """192-atom water (64 H2O, L = 12.42 A), F=64, T=3, 2 species, Xavier weights (seed 0):
+    E+F+W call latency through the C ABI with host buffers, and 100 NVE steps at dt 0.5 fs from
+    300 K compared with the FP64 oracle's own trajectory."""
+    import oracle
+    import synthetic as syn
+    eng, torch = _init_engine()
+    Fw, Tw, Sw, dtw = 64, 3, 2, 0.5
+    sy = syn.water_box(64, seed=0)
+    v0 = syn.maxwell_boltzmann(sy.masses, 300.0, seed=0)
+    vals = syn.xavier_params(Fw, K, Tw, Sw, seed=0)
+    blob = syn.params_blob(Fw, K, Tw, Sw, rc=RC, values=vals)
+    oracle.build()
+    t0 = time.perf_counter()
+    ref = oracle.painn(vals, Fw, K, Tw, Sw, sy.species, sy.positions, sy.cell)
+    t_orc = time.perf_counter() - t0
+    _, _, ep_o, ek_o = oracle.nve(vals, Fw, K, Tw, Sw, sy.species, sy.masses, sy.positions, v0, sy.cell, dtw, 100)
+    eo = ep_o + ek_o
+    out = {}
+    for prec in ("fp32", "bf16"):
+        with eng.Potential(Fw, K=K, T=Tw, n_species=Sw, rc=RC, precision=prec, params=blob,
+                           stream=torch.cuda.current_stream().cuda_stream) as pot:
+            for _ in range(max(3, args.warmup)):
+                pot.compute(sy.species, sy.positions, sy.cell)
+            lat = []
+            for _ in range(max(args.steps, 200)):
+                t0 = time.perf_counter()
+                o = pot.compute(sy.species, sy.positions, sy.cell)
+                lat.append((time.perf_counter() - t0) * 1e3)
+            fr = float(np.sqrt(((o["forces"] - ref["forces"]) ** 2).sum() / (ref["forces"] ** 2).sum()))
+            pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=1.0)
+            r = _timed_md(pot, torch, 100, 0, dtw)
+            e = r["ep"] + r["ek"]
+            out[prec] = {"call_ms_p50": _pct(lat, 0.5), "call_ms_p99": _pct(lat, 0.99),
+                         "calls_per_s": 1e3 / statistics.mean(lat), "rel_force_rmse_vs_oracle": fr,
+                         "abs_dE_per_atom_vs_oracle": abs(float(o["energy"]) - ref["energy"]) / sy.n,
+                         "nve_100x0.5fs_drift_ev_per_atom": float((e[-1] - e[0]) / sy.n),
+                         "nve_max_dev_from_oracle_etot_ev_per_atom": float(np.abs(e - eo).max() / sy.n),
+                         "md_ms_per_step": r["total_ms"] / 100}
+    line = {"metric": "E+F+W call latency (host buffers) and 100-step NVE drift, 192-atom water",
+            "value": out["fp32"]["call_ms_p50"], "unit": "ms/call (p50, FP32)", "n_gpus": 1,
+            "steps": max(args.steps, 200), "warmup": max(3, args.warmup), "higher_is_better": False,
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "water 64 H2O (192 atoms), L=12.42 A; PaiNN F=64, T=3, K=20, rc=5 A; "
+                                   "NVE dt=0.5 fs, 300 K"},
+            "fp32": out["fp32"], "bf16": out["bf16"],
+            "oracle_nve_100x0.5fs_drift_ev_per_atom": float((eo[-1] - eo[0]) / sy.n),
+            "cpu_baseline": {"value": t_orc * 1e3, "unit": "ms/call", "cores": 1, "kind": "oracle",
+                             "sample": "one E+F+W evaluation of the same 192 atoms (single thread)"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_water96k(args):
+    """96,000-atom water (32,000 H2O, L = 98.6 A), F=64, T=3, skin 1 A, rebuild at skin/2,
+    1,000 velocity-Verlet steps at dt 0.5 fs from 300 K (FP32, then BF16)."""
+    import synthetic as syn
+    eng, torch = _init_engine()
+    Fw, Tw, Sw, dtw = 64, 3, 2, 0.5
+    steps = args.steps if args.steps_given else 1000
+    sy = syn.water_box(32000, seed=0)
+    v0 = syn.maxwell_boltzmann(sy.masses, 300.0, seed=0)
+    blob = syn.params_blob(Fw, K, Tw, Sw, rc=RC, seed=0)
+    res = {}
+    for prec in ("fp32", "bf16"):
+        with eng.Potential(Fw, K=K, T=Tw, n_species=Sw, rc=RC, precision=prec, params=blob,
+                           stream=torch.cuda.current_stream().cuda_stream) as pot:
+            pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=1.0)
+            res[prec] = _timed_md(pot, torch, steps, max(3, args.warmup), dtw)
+    cfg = {"workload": f"water 32,000 H2O ({sy.n:,} atoms), L={sy.cell[0, 0]:.2f} A; PaiNN F=64, T=3, K=20, "
+                       f"rc=5 A, skin=1 A; NVE dt=0.5 fs, 300 K", "precision": "fp32",
+           "l2": "inputs larger than L2"}
+    line = _md_line("atom-steps/s, 96k-atom water NVE (FP32), p50/p99, energy drift", sy.n, steps, max(3, args.warmup),
+                    res["fp32"], "f32", cfg, {})
+    b = res["bf16"]
+    eb = b["ep"] + b["ek"]
+    line["bf16"] = {"value": sy.n * steps / (b["total_ms"] / 1e3), "ms_per_step": b["total_ms"] / steps,
+                    "p50_ms": _pct(b["step_ms"], 0.5), "p99_ms": _pct(b["step_ms"], 0.99),
+                    "drift_ev_per_atom": float((eb[-1] - eb[0]) / sy.n), "rebuilds": b["rebuilds"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_mixture90k(args):
+    """Triclinic 4-species mixture (300-atom chain in 30,000 triatomics, 90,300 atoms), F=64,
+    T=2: NVE steps with the adjoint recomputing the edge filters versus reading them stored."""
+    import synthetic as syn
+    eng, torch = _init_engine()
+    from paper_2506_04055_gb300 import _lib as L
+    Fm, Tm, Sm = 64, 2, 4
+    steps = args.steps if args.steps_given else 100
+    sy = syn.mixture(n_chain=300, n_water=30000, seed=0)
+    v0 = syn.maxwell_boltzmann(sy.masses, 300.0, seed=0)
+    blob = syn.params_blob(Fm, K, Tm, Sm, rc=RC, seed=0)
+    res, held, stored = {}, {}, {}
+    for mode in ("recompute", "store"):
+        with eng.Potential(Fm, K=K, T=Tm, n_species=Sm, rc=RC, precision="fp32", params=blob,
+                           stream=torch.cuda.current_stream().cuda_stream) as pot:
+            pot.set_option(L.CTD_OPT_EDGE_STORE, 1 if mode == "store" else 0)
+            st = pot.compute(sy.species, sy.positions, sy.cell, stats=True)["stats"]
+            held[mode], stored[mode] = st["bytes_allocated"], st["edges_stored"]
+            pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=1.0)
+            res[mode] = _timed_md(pot, torch, steps, max(3, args.warmup), 0.5)
+    cfg = {"workload": f"mixture: 300-atom chain in 30,000 triatomics ({sy.n:,} atoms), triclinic tilts <= 10%, "
+                       f"4 species; PaiNN F=64, T=2, K=20, rc=5 A, skin=1 A; NVE dt=0.5 fs, 300 K",
+           "precision": "fp32", "l2": "inputs larger than L2"}
+    r = res["recompute"]
+    line = _md_line("atom-steps/s, 90k-atom mixture, recomputed vs stored edge filters", sy.n, steps,
+                    max(3, args.warmup), r, "f32", cfg, {})
+    s_ = res["store"]
+    line["store"] = {"value": sy.n * steps / (s_["total_ms"] / 1e3), "ms_per_step": s_["total_ms"] / steps,
+                     "p50_ms": _pct(s_["step_ms"], 0.5), "p99_ms": _pct(s_["step_ms"], 0.99),
+                     "stage_ms_per_step": s_["stage_ms_per_step"], "bytes_held": held["store"],
+                     "edges_stored": stored["store"]}
+    line["recompute"] = {"bytes_held": held["recompute"], "edges_stored": stored["recompute"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Continuous-batching server: R replicas (atom counts log-uniform in [64, 20,000], water and
+    fcc alternating), each S steps; closed loop (all at t=0) to find the saturation rate, then
+    Poisson arrivals at 0.1, 0.5, 1 and 2 times it.  Baseline: the same replicas one after
+    another through the single-system FP32 MD loop (a subset, scaled)."""
+    import synthetic as syn
+    eng, torch = _init_engine()
+    Fs, Ts, Ss = 64, 3, 2
+    R, S_ = args.replicas, args.serve_steps
+    dts = 0.5
+    sizes = syn.request_sizes(R, seed=0)
+    reps = []
+    for k, nt in enumerate(sizes):
+        sy = syn.system_near(int(nt), "water" if k % 2 == 0 else "fcc", seed=k)
+        reps.append((sy, syn.maxwell_boltzmann(sy.masses, 300.0, seed=1000 + k)))
+    natoms = np.array([sy.n for sy, _ in reps])
+    blob = syn.params_blob(Fs, K, Ts, Ss, rc=RC, seed=0)
+    stream = torch.cuda.current_stream()
+    budget = int(args.serve_budget_gib * (1 << 30))
+
+    def session(rate, precision):
+        srv = eng.Server(Fs, blob, K=K, T=Ts, n_species=Ss, rc=RC, precision=precision, dt=dts,
+                         hbm_budget_bytes=budget, max_replicas=R, stream=stream.cuda_stream)
+        rng = np.random.Generator(np.random.PCG64(7))
+        arrive = np.zeros(R) if rate is None else np.cumsum(rng.exponential(1.0 / rate, size=R))
+        sub_t, fin_t, lat, res_atoms = [], [], [], []
+        nsub = nfin = 0
+        t0 = time.perf_counter()
+        while nfin < R:
+            now = time.perf_counter() - t0
+            while nsub < R and arrive[nsub] <= now:
+                sy, v = reps[nsub]
+                srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, S_, skin=1.0)
+                sub_t.append(now)
+                nsub += 1
+            st = srv.stats()
+            if st["resident_replicas"] == 0 and st["queued"] == 0 and nsub < R:
+                time.sleep(max(0.0, min(0.01, arrive[nsub] - now)))
+                continue
+            a = time.perf_counter()
+            _, _, nf = srv.step()
+            stream.synchronize()
+            b = time.perf_counter()
+            lat.append((b - a) * 1e3)
+            res_atoms.append(st["resident_atoms"])
+            for _ in range(nf):
+                fin_t.append(b - t0)
+            nfin += nf
+        wall = time.perf_counter() - t0
+        srv.close()
+        req = np.array(fin_t) - np.array(sub_t)
+        busy = sum(lat) / 1e3
+        return {"rate_per_s": rate, "wall_s": wall, "atom_steps_per_s": float(natoms.sum()) * S_ / wall,
+                "atom_steps_per_busy_s": float(natoms.sum()) * S_ / busy,
+                "step_ms_p50": _pct(lat, 0.5), "step_ms_p99": _pct(lat, 0.99), "server_steps": len(lat),
+                "request_s_p50": float(np.percentile(req, 50)), "request_s_p99": float(np.percentile(req, 99)),
+                "mean_resident_atoms": float(np.mean(res_atoms))}
+
+    # warm-up session (kernels, allocations)
+    session(None, args.serve_precision)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        sat = session(None, args.serve_precision)
+        rate_sat = R / sat["wall_s"]
+        sweep = [session(f * rate_sat, args.serve_precision) for f in (0.1, 0.5, 1.0, 2.0)]
+    # serial baseline: single-system FP32 MD loop, replicas one after another (first few)
+    nser = min(R, args.serial_replicas)
+    with eng.Potential(Fs, K=K, T=Ts, n_species=Ss, rc=RC, precision="fp32", params=blob,
+                       stream=stream.cuda_stream) as pot:
+        sy, v = reps[0]
+        pot.md_set_state(sy.species, sy.masses, sy.positions, v, sy.cell, skin=1.0)
+        pot.md_run(S_, dts)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(nser):
+            sy, v = reps[k]
+            pot.md_set_state(sy.species, sy.masses, sy.positions, v, sy.cell, skin=1.0)
+            pot.md_run(S_, dts)
+        torch.cuda.synchronize()
+        ser_s = time.perf_counter() - t0
+    serial = float(natoms[:nser].sum()) * S_ / ser_s
+    line = {"metric": "serving: aggregate atom-steps/s at saturation, p50/p99 step and request latency vs arrival rate",
+            "value": sat["atom_steps_per_s"], "unit": "atom-steps/s", "n_gpus": 1, "steps": S_, "warmup": 1,
+            "ms_per_step": sat["step_ms_p50"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if args.serve_precision == "bf16" else "f32", "data": "synthetic",
+            "config": {"workload": f"{R} MD replicas, atoms log-uniform in [64, 20000] (water / fcc alternating, "
+                                   f"{int(natoms.sum()):,} atoms in all, mean {natoms.mean():.0f}); PaiNN F=64, "
+                                   f"T=3, K=20, rc=5 A, skin 1 A; {S_} NVE steps each at dt 0.5 fs; HBM budget "
+                                   f"{args.serve_budget_gib} GiB", "precision": args.serve_precision},
+            "saturation": sat, "saturation_rate_per_s": rate_sat, "sweep": sweep,
+            "serial_fp32": {"value": serial, "unit": "atom-steps/s", "replicas": nser,
+                            "sample": f"first {nser} replicas, set_state + {S_} steps each, one after another"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,13 +640,25 @@ def main():
     ap.add_argument("--precision", default="both", choices=["fp32", "bf16", "both"])
     ap.add_argument("--cells", type=int, default=FCC_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tc-adjoint", type=int, default=0,
-                    help="BF16: edge adjoint with the tcgen05 filter (1 register gathers, 2 bulk-copy gathers)")
+    ap.add_argument("--tc-adjoint", type=int, default=None,
+                    help="BF16 edge adjoint: 0 CUDA cores, 1 tcgen05 filter with register gathers, "
+                         "2 tcgen05 filter with bulk-copy gathers (the library's default)")
+    ap.add_argument("--workload", default="fcc1m",
+                    choices=["fcc1m", "water192", "water96k", "mixture90k", "serve"])
+    ap.add_argument("--replicas", type=int, default=512)
+    ap.add_argument("--serve-steps", type=int, default=20)
+    ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--serve-budget-gib", type=float, default=16.0)
+    ap.add_argument("--serial-replicas", type=int, default=64)
     args = ap.parse_args()
+    args.steps_given = any(a == "--steps" or a.startswith("--steps=") for a in sys.argv[1:])
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "fcc1m":
         run_ours(args)
+    else:
+        {"water192": run_water192, "water96k": run_water96k, "mixture90k": run_mixture90k,
+         "serve": run_serve}[args.workload](args)
 
 
 if __name__ == "__main__":

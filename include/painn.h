@@ -76,6 +76,8 @@ typedef struct {
   double max_displacement;  /* largest displacement since the last rebuild (A)                */
   int64_t bytes_allocated;  /* device bytes held by the context                               */
   float ms_neighbors, ms_model;   /* device time of the neighbour and model stages (ms)      */
+  int32_t edges_stored;     /* 1 if the adjoint read per-edge filters stored by the forward   */
+  int32_t reserved;
 } ctd_stats;
 
 typedef struct ctd_ctx ctd_ctx;
@@ -140,11 +142,18 @@ int ctd_md_run(ctd_ctx *ctx, int32_t nsteps, double dt, double *epot, double *ek
 int ctd_md_get_state(ctd_ctx *ctx, double *positions, double *velocities);
 
 /* ---- options -------------------------------------------------------------------------- */
-/* CTD_OPT_TC_ADJOINT (value 0, 1 or 2; default 0): on the BF16 path with F = 128, run the
+/* CTD_OPT_TC_ADJOINT (value 0, 1 or 2; default 2): on the BF16 path with F = 128, run the
  * edge adjoint with the radial filter on tcgen05 as well (the message kernel always does):
  * 1 = neighbour gradients gathered into registers, 2 = gathered into shared memory by bulk
- * asynchronous copies.  0 keeps the CUDA-core adjoint. */
+ * asynchronous copies.  0 selects the CUDA-core adjoint. */
 #define CTD_OPT_TC_ADJOINT 1
+/* CTD_OPT_EDGE_STORE (value 0 or 1; default 0): the forward message kernel stores, per active
+ * edge and layer, the cutoff-scaled radial filter and its distance derivative (6F floats), and
+ * the adjoint reads them instead of recomputing basis and filter (the default).  Storage costs
+ * T x E x 6F x 4 bytes; it is used only when that fits the HBM budget (if one is set) and 80 %
+ * of the device's free memory, and otherwise the call recomputes (ctd_stats.edges_stored says
+ * which).  It applies to the CUDA-core edge kernels: the FP32 path and BF16 with F != 128. */
+#define CTD_OPT_EDGE_STORE 2
 int ctd_set_option(ctd_ctx *ctx, int32_t option, int64_t value);
 
 /* ---- launch accounting and stage timing (benchmarks, statistics) ------------------------- */

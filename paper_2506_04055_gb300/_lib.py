@@ -62,7 +62,8 @@ class ctd_stats(ctypes.Structure):
                 ("n_active_edges", ctypes.c_int64), ("rebuilt", ctypes.c_int32),
                 ("retries", ctypes.c_int32), ("max_displacement", ctypes.c_double),
                 ("bytes_allocated", ctypes.c_int64), ("ms_neighbors", ctypes.c_float),
-                ("ms_model", ctypes.c_float)]
+                ("ms_model", ctypes.c_float), ("edges_stored", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class CtdError(RuntimeError):
@@ -175,6 +176,7 @@ def ctd_md_get_state(ctx, positions_ptr, velocities_ptr):
 
 
 CTD_OPT_TC_ADJOINT = 1
+CTD_OPT_EDGE_STORE = 2
 
 
 def ctd_set_option(ctx, option, value):

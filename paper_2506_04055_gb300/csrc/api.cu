@@ -281,6 +281,23 @@ int evaluate(ctd_ctx* c, bool need_grad) {
   ENSURE(c, c->out_e, sizeof(double) * 4);
   ENSURE(c, c->out_w, sizeof(double) * 9);
   if (T == 0) CUDA_OK(c, cudaMemsetAsync(c->hedge.p, 0, sizeof(float4) * e1, st));
+  // Edge filters stored for the adjoint when asked for and when they fit: within the HBM
+  // budget if one is set, and within 80 % of the device's free memory; recomputed otherwise.
+  float* wst = nullptr;
+  const int64_t wlayer = e1 * 6 * (int64_t)F;
+  c->last_stored = false;
+  if (c->mw.edge_store && need_grad && T > 0) {
+    const size_t want = sizeof(float) * (size_t)wlayer * (size_t)T;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const bool fits_budget = !c->budget || c->held - c->wstore.bytes + want <= c->budget;
+    const bool fits_device = want <= c->wstore.bytes || (double)want <= 0.8 * (double)(free_b + c->wstore.bytes);
+    if (fits_budget && fits_device) {
+      ENSURE(c, c->wstore, want);
+      wst = P<float>(c->wstore);
+      c->last_stored = true;
+    }
+  }
   if (c->desc.precision == CTD_PREC_BF16) {
     const int nbb = model_bf16_buffer_count();
     if ((int)c->mbufb.size() < nbb) c->mbufb.resize(nbb);
@@ -294,13 +311,14 @@ int evaluate(ctd_ctx* c, bool need_grad) {
     int bad = model_forward_backward_bf16(st, c->mw, n, P<int32_t>(c->z_s), P<int32_t>(c->arow), P<int32_t>(c->acol),
                                           P<float4>(c->ar), P<int32_t>(c->arev), ptrs.data(), bptrs.data(), need_grad,
                                           P<double>(c->epart), kPartials, P<float4>(c->hedge), P<float>(c->force_s),
-                                          P<double>(c->vpart), kPartials, P<float>(c->eatom), P<int>(c->status));
+                                          P<double>(c->vpart), kPartials, P<float>(c->eatom), P<int>(c->status),
+                                          wst, wlayer);
     if (bad) return fail(c, CTD_ERR_INVALID_ARG, "BF16 path: unsupported GEMM shape");
   } else {
     model_forward_backward_fp32(st, c->mw, n, P<int32_t>(c->z_s), P<int32_t>(c->arow), P<int32_t>(c->acol),
                                 P<float4>(c->ar), P<int32_t>(c->arev), ptrs.data(), need_grad, P<double>(c->epart),
                                 kPartials, P<float4>(c->hedge), P<float>(c->force_s), P<double>(c->vpart),
-                                kPartials, P<float>(c->eatom), P<int>(c->status));
+                                kPartials, P<float>(c->eatom), P<int>(c->status), wst, wlayer);
   }
   StageGuard sg(STG_FORCES);
   launch_sum_partials(st, kPartials, 1, P<double>(c->epart), P<double>(c->out_e), 1.0);
@@ -498,6 +516,8 @@ int ctd_create(ctd_ctx** out, const ctd_model_desc* desc, size_t hbm_budget_byte
   ctd_ctx* c = new ctd_ctx();
   c->desc = *desc;
   c->budget = hbm_budget_bytes;
+  c->mw.tc_adjoint = true;   // BF16 path, F = 128: bulk-gathered tensor-core adjoint
+  c->mw.tc_adjoint_variant = 2;
   cudaGetDevice(&c->device);
   if (cuda_stream) {
     c->st = static_cast<cudaStream_t>(cuda_stream);
@@ -600,6 +620,10 @@ int ctd_get_pairs(ctd_ctx* c, int32_t* pi, int32_t* pj, int8_t* shift, int64_t c
 int ctd_set_option(ctd_ctx* c, int32_t option, int64_t value) {
   if (!c) return CTD_ERR_INVALID_ARG;
   switch (option) {
+    case CTD_OPT_EDGE_STORE:
+      if (value < 0 || value > 1) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_EDGE_STORE takes 0 or 1");
+      c->mw.edge_store = value != 0;
+      return CTD_OK;
     case CTD_OPT_TC_ADJOINT:
       if (value < 0 || value > 2) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0, 1 or 2");
       c->mw.tc_adjoint = value != 0;
@@ -726,6 +750,7 @@ int ctd_compute(ctd_ctx* c, int64_t n, const int32_t* species, const double* pos
     stats->retries = 0;
     stats->max_displacement = md;
     stats->bytes_allocated = (int64_t)c->held;
+    stats->edges_stored = c->last_stored ? 1 : 0;
     cudaEventElapsedTime(&stats->ms_neighbors, ev[0], ev[1]);
     cudaEventElapsedTime(&stats->ms_model, ev[1], ev[2]);
     for (auto& e : ev) cudaEventDestroy(e);

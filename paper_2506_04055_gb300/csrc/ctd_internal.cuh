@@ -102,6 +102,7 @@ struct ModelW {
   const __nv_bfloat16 *R1b, *R1tb;
   bool tc_adjoint;                 // BF16 path: edge adjoint with the tensor-core filter
   int tc_adjoint_variant;          // 1: register gathers, 2: bulk-copy gathers into shared memory
+  bool edge_store;                 // store per-edge filters in the forward pass for the adjoint
 };
 
 // ---------------------------------------------------------------- small device helpers
@@ -175,11 +176,12 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
                                 const int32_t* arow, const int32_t* acol, const float4* ar, const int32_t* arev,
                                 float* const* bufs, __nv_bfloat16* const* bbufs, bool need_grad,
                                 double* energy_partials, int n_energy_partials, float4* hedge, float* force_s,
-                                double* virial_partials, int n_virial_partials, float* e_atom, int* status);
+                                double* virial_partials, int n_virial_partials, float* e_atom, int* status,
+                                float* wstore, int64_t wstore_layer_floats);
 void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
                                  const int32_t* arow, const int32_t* acol, const float4* ar,
                                  const int32_t* arev, float* const* bufs, bool need_grad,
                                  double* energy_partials, int n_energy_partials, float4* hedge,
                                  float* force_s, double* virial_partials, int n_virial_partials,
-                                 float* e_atom, int* status);
+                                 float* e_atom, int* status, float* wstore, int64_t wstore_layer_floats);
 }  // namespace ctd

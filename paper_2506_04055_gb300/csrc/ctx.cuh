@@ -54,6 +54,8 @@ struct ctd_ctx {
   DBuf xw_s, xref_s, z_s, x_s, count, vrow, vcol, vimg, vbase, vrev, v2a, status, delta, maxd;
   DBuf acount, arow, acol, ar, vidx, arev, hedge, force_s, eatom, epart, vpart, kpart, scan_tmp;
   DBuf out_e, out_f, out_w, out_eatom;
+  DBuf wstore;              // per-edge filters [T][E][6F] when edge storage is on
+  bool last_stored = false;  // the last evaluation stored edge filters
   std::vector<DBuf> mbuf, mbufb;
   double* energy_out_user = nullptr;
 
@@ -68,7 +70,7 @@ struct ctd_ctx {
                     &tmp_idx, &perm, &inv_perm, &xw_s, &xref_s, &z_s, &x_s, &count, &vrow, &vcol, &vimg,
                     &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev,
                     &hedge, &force_s, &eatom, &epart, &vpart, &kpart, &scan_tmp, &out_e, &out_f, &out_w,
-                    &out_eatom, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp};
+                    &out_eatom, &wstore, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp};
     for (DBuf* b : list) all.push_back(b);
   }
 };

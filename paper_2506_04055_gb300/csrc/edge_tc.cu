@@ -94,6 +94,25 @@ __device__ __forceinline__ void mark_row_ends(int lane, int* sfl, int NE, int64_
   __syncwarp();
 }
 
+// Same flags as mark_row_ends, with the warp reading 32 row ends per step: row ends are
+// non-decreasing, so the ends inside the tile are a prefix of the lanes.
+__device__ __forceinline__ void mark_row_ends_warp(int lane, int* sfl, int NE, int64_t tb, int64_t r1,
+                                                   const int32_t* __restrict__ arow, int64_t& rp) {
+  for (int s = lane; s < NE; s += 32) sfl[s] = 0;
+  __syncwarp();
+  for (;;) {
+    const int64_t row = rp + lane;
+    const int64_t v = row < r1 ? (int64_t)arow[row + 1] : INT64_MAX;
+    const bool in = v <= tb + NE;
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) atomicAdd(&sfl[v - 1 - tb], 1);
+    const int cnt = __popc(m);
+    rp += cnt;
+    if (cnt < 32) break;
+  }
+  __syncwarp();
+}
+
 // Streams: a CTA splits its rows into NS contiguous sub-ranges ("streams"), each with its own
 // tiles, TMEM region and barriers and its own epilogue warpgroup, so one SM keeps 4 * NS
 // epilogue warps busy on independent rows while sharing one copy of Wf.
@@ -691,48 +710,50 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
       uint64_t* b = sbar + 8 * s;
       for (int it = 0; it < R.ntiles; ++it) {
         const int bb = it & 1;
-        if (it >= 2 && !umma::mbar_wait(&b[2 + bb], ((it >> 1) - 1) & 1)) { ok = false; break; }
         const int64_t tb = R.e0 + (int64_t)it * NE;
         const int nlive = (int)((R.e1 - tb) < NE ? (R.e1 - tb) : NE);
+        // geometry and basis first: they need no buffer, so their loads overlap the wait
+        const int k0 = lane;
+        float rb[kKPad], drb[kKPad];
+        int i = 0;
+        float4 geo = make_float4(0.f, 0.f, 0.f, 1.f);
+        float2 fcv = make_float2(0.f, 0.f);
+        if (k0 < nlive) {
+          const int64_t e = tb + k0;
+          const float4 r = p.ar[e];
+          i = p.acol[e];
+          const float d = r.w, id = 1.0f / d;
+          geo = make_float4(r.x * id, r.y * id, r.z * id, d);
+          fcv = make_float2(0.5f * (cospif(d * inv_rc) + 1.0f), -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc));
+#pragma unroll
+          for (int k = 0; k < kKPad; ++k) {
+            const float t = d - (float)k * sig;
+            const float v = k < p.K ? expf(-t * t * inv2s2) : 0.0f;
+            rb[k] = v;
+            drb[k] = -v * t * inv_s2;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < kKPad; ++k) rb[k] = drb[k] = 0.0f;
+        }
+        if (it >= 2 && !umma::mbar_wait(&b[2 + bb], ((it >> 1) - 1) & 1)) { ok = false; break; }
         const int so = (s * 2 + bb) * NE;
         float* g = sG + (size_t)so * 4 * kF;
         if (lane == 0) umma::mbar_expect_tx_only(&b[bb], (uint32_t)(nlive * 4 * kF * 4));
         __syncwarp();
         unsigned char* tile = sB + ((s * 2 + bb) * 2) * NE * 128;
-        unsigned char* dtile = tile + NE * 128;
-        for (int k0 = lane; k0 < NE; k0 += 32) {
-          const int64_t e = tb + k0;
-          float rb[kKPad], drb[kKPad];
-          int i = 0;
-          float4 geo = make_float4(0.f, 0.f, 0.f, 1.f);
-          float2 fcv = make_float2(0.f, 0.f);
+        if (k0 < NE) {
           if (k0 < nlive) {
-            const float4 r = p.ar[e];
-            const float d = r.w, id = 1.0f / d;
-            geo = make_float4(r.x * id, r.y * id, r.z * id, d);
-            fcv = make_float2(0.5f * (cospif(d * inv_rc) + 1.0f), -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc));
-            i = p.acol[e];
             umma::bulk_copy_g2s(g + (size_t)k0 * 4 * kF, p.Gsm + (int64_t)i * kF, kF * 4, &b[bb]);
             umma::bulk_copy_g2s(g + (size_t)k0 * 4 * kF + kF, p.Gvm + (int64_t)i * 3 * kF, 3 * kF * 4, &b[bb]);
-#pragma unroll
-            for (int k = 0; k < kKPad; ++k) {
-              const float t = d - (float)k * sig;
-              const float v = k < p.K ? expf(-t * t * inv2s2) : 0.0f;
-              rb[k] = v;
-              drb[k] = -v * t * inv_s2;
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < kKPad; ++k) rb[k] = drb[k] = 0.0f;
           }
           store_basis_row(tile, k0, rb);
-          store_basis_row(dtile, k0, drb);
-          sj[so + k0] = i;
+          store_basis_row(tile + NE * 128, k0, drb);
           sgeo[so + k0] = geo;
           sfc[so + k0] = fcv;
         }
         gathered = it + 1;
-        mark_row_ends(lane, sfl + so, NE, tb, R.r1, p.arow, rp);
+        mark_row_ends_warp(lane, sfl + so, NE, tb, R.r1, p.arow, rp);
         umma::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&b[bb]);
@@ -815,12 +836,14 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
       const float4* tg = sgeo + so;
       const float2* tc = sfc + so;
       float* tG = sG + (size_t)so * 4 * kF + f;   // this thread's feature in each gathered row
+      // lane 8k of warp q writes edge 4q + k of the tile; its previous value is read now
+      const int hslot = f >> 3;
+      float4 hold = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p.accumulate && (lane & 7) == 0 && hslot < nlive) hold = p.hedge[tb + hslot];
 #pragma unroll 1
       for (int c = 0; c < NE / 8; ++c) {
         float W[6][8];
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * 6 * NE + c * 8);
-#pragma unroll
-        for (int h = 0; h < 6; ++h) umma::tmem_ld8(ta + h * NE, W[h]);
+        umma::tmem_ld8x6(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * 6 * NE + c * 8), NE, W);
         if (c == NE / 8 - 1) {
           umma::fence_before();
           __syncwarp();
@@ -896,12 +919,8 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
           const float gdu = g0 * ux + g1 * uy + g2 * uz;
           float4 hv = make_float4(pd * ux + (g0 - gdu * ux) * id, pd * uy + (g1 - gdu * uy) * id,
                                   pd * uz + (g2 - gdu * uz) * id, 0.f);
-          const int64_t e = tb + slot;
-          if (p.accumulate) {
-            const float4 ov = p.hedge[e];
-            hv.x += ov.x; hv.y += ov.y; hv.z += ov.z;
-          }
-          p.hedge[e] = hv;
+          hv.x += hold.x; hv.y += hold.y; hv.z += hold.z;
+          p.hedge[tb + slot] = hv;
         }
       }
       __syncwarp();

@@ -281,20 +281,28 @@ __device__ __forceinline__ void group_sync(int id, int nthreads) {
 // Forward message: one group of F threads per receiver row.  Edges of the row are staged
 // F at a time (geometry, f_c, radial basis) in shared memory; thread f then accumulates
 // channel f of s and of the three components of v over the staged edges.
-template <int KP>
+//
+// STORE: the kernel also writes, per edge e and channel c in (s, vv, vs), the cutoff-scaled
+// filter W_c,e = f_c (Wf rbf + bf) and its distance derivative dW_c,e/dd, as
+// wst[e][6F] = [W_s | W_vv | W_vs | dW_s | dW_vv | dW_vs], so that the adjoint reads them
+// instead of recomputing the basis and the filter.
+template <int KP, bool STORE>
 __global__ __launch_bounds__(256) void k_edge_fwd(int64_t n, int F, int K, float rc,
                                                   const int32_t* __restrict__ arow, const int32_t* __restrict__ acol,
                                                   const float4* __restrict__ ar, const float* __restrict__ PHI,
                                                   const float* __restrict__ S, const float* __restrict__ V,
                                                   const float* __restrict__ Wf, const float* __restrict__ bf,
                                                   float* __restrict__ SM, float* __restrict__ VM,
-                                                  __nv_bfloat16* __restrict__ VMb) {
+                                                  __nv_bfloat16* __restrict__ VMb, float* __restrict__ wst) {
   extern __shared__ __align__(16) float sm[];
+  constexpr int KD = STORE ? KP : 0;            // derivative basis staged only when storing
   const int G = blockDim.x / F;                 // groups per block
   const int g = threadIdx.x / F, f = threadIdx.x % F;
-  float* rbs = sm + (size_t)g * F * KP;                                          // [F edges][KP]
-  float4* geo = reinterpret_cast<float4*>(sm + (size_t)G * F * KP) + (size_t)g * F;  // (u, f_c)
-  int* js = reinterpret_cast<int*>(sm + (size_t)G * F * (KP + 4)) + (size_t)g * F;
+  float* rbs = sm + (size_t)g * F * (KP + KD);                                   // [F edges][KP]
+  float* drbs = rbs + (size_t)F * KP;                                            // [F edges][KD]
+  float4* geo = reinterpret_cast<float4*>(sm + (size_t)G * F * (KP + KD)) + (size_t)g * F;  // (u, f_c)
+  float* dfcs = reinterpret_cast<float*>(sm + (size_t)G * F * (KP + KD + 4)) + (size_t)g * F;
+  int* js = reinterpret_cast<int*>(sm + (size_t)G * F * (KP + KD + 4 + (STORE ? 1 : 0))) + (size_t)g * F;
 
   float w_s[KP], w_vv[KP], w_vs[KP];
 #pragma unroll
@@ -305,6 +313,7 @@ __global__ __launch_bounds__(256) void k_edge_fwd(int64_t n, int F, int K, float
   }
   const float b_s = bf[f], b_vv = bf[F + f], b_vs = bf[2 * F + f];
   const float inv_rc = 1.0f / rc, sig = rc / (float)(K - 1), inv2s2 = 1.0f / (2.0f * sig * sig);
+  const float inv_s2 = 1.0f / (sig * sig);
   const int64_t ngroups = (int64_t)gridDim.x * G;
 
   for (int64_t i = (int64_t)blockIdx.x * G + g; i < n; i += ngroups) {
@@ -318,11 +327,14 @@ __global__ __launch_bounds__(256) void k_edge_fwd(int64_t n, int F, int K, float
         float d = r.w, id = 1.0f / d;
         float fc = 0.5f * (cospif(d * inv_rc) + 1.0f);
         geo[f] = make_float4(r.x * id, r.y * id, r.z * id, fc);
+        if (STORE) dfcs[f] = -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc);
         js[f] = acol[c0 + f];
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
           float mu = (float)k * sig, t = d - mu;
-          rbs[f * KP + k] = k < K ? expf(-t * t * inv2s2) : 0.0f;
+          const float v = k < K ? expf(-t * t * inv2s2) : 0.0f;
+          rbs[f * KP + k] = v;
+          if (STORE) drbs[f * KP + k] = -v * t * inv_s2;
         }
       }
       group_sync(1 + g, F);
@@ -342,6 +354,24 @@ __global__ __launch_bounds__(256) void k_edge_fwd(int64_t n, int F, int K, float
         }
         const float* p = PHI + (int64_t)js[t] * 6 * F;
         const float ps = p[f], y0 = p[F + f], y1 = p[2 * F + f], y2 = p[3 * F + f], pvs = p[4 * F + f];
+        if (STORE) {
+          const float* drb = drbs + t * KP;
+          float dws = 0.f, dwvv = 0.f, dwvs = 0.f;
+#pragma unroll
+          for (int k = 0; k < KP; ++k) {
+            dws = fmaf(w_s[k], drb[k], dws);
+            dwvv = fmaf(w_vv[k], drb[k], dwvv);
+            dwvs = fmaf(w_vs[k], drb[k], dwvs);
+          }
+          const float fc = ge.w, dfc = dfcs[t];
+          float* o = wst + (int64_t)(c0 + t) * 6 * F + f;
+          o[0] = ws * fc;
+          o[F] = wvv * fc;
+          o[2 * F] = wvs * fc;
+          o[3 * F] = fc * dws + dfc * ws;
+          o[4 * F] = fc * dwvv + dfc * wvv;
+          o[5 * F] = fc * dwvs + dfc * wvs;
+        }
         ws *= ge.w; wvv *= ge.w; wvs *= ge.w;
         as = fmaf(ps, ws, as);
         const float tvs = pvs * wvs;
@@ -385,27 +415,32 @@ __device__ __forceinline__ float warp_reduce4(float v0, float v1, float v2, floa
 // (gsm_i, gvm_i) and accumulates d/dphi_s,j, d/dpsi_j,a, d/dphi_vs,j over the row; per edge the
 // partial d/dd and d/du_rev are reduced over the F channels and turned into
 // hedge[e'] = dU/dr_(i<-j).
-template <int KP>
+//
+// STORED: the filter and its distance derivative come from wst (written by k_edge_fwd<.., true>
+// for the same edge, whose distance equals its reverse's) instead of being recomputed.
+template <int KP, bool STORED>
 __global__ __launch_bounds__(256) void k_edge_bwd(int64_t n, int F, int K, float rc, int accumulate,
                                                   const int32_t* __restrict__ arow, const int32_t* __restrict__ acol,
                                                   const float4* __restrict__ ar, const float* __restrict__ PHI,
                                                   const float* __restrict__ Gsm, const float* __restrict__ Gvm,
                                                   const float* __restrict__ Wf, const float* __restrict__ bf,
-                                                  float* __restrict__ GPHI, float4* __restrict__ hedge) {
+                                                  float* __restrict__ GPHI, float4* __restrict__ hedge,
+                                                  const float* __restrict__ wst) {
   extern __shared__ __align__(16) float sm[];
+  constexpr int KB = STORED ? 0 : KP;   // basis staged only when recomputing
   const int G = blockDim.x / F;
   const int g = threadIdx.x / F, f = threadIdx.x % F, lane = threadIdx.x & 31, wig = f >> 5;
   const int NW = F / 32;
-  float* rbs = sm + (size_t)g * F * (2 * KP + 8 + 4 * NW);     // [F][KP] rbf, [F][KP] drbf
-  float* drbs = rbs + F * KP;
-  float4* geo = reinterpret_cast<float4*>(drbs + F * KP);       // (u, d)
+  float* rbs = sm + (size_t)g * F * (2 * KB + 8 + 4 * NW);     // [F][KB] rbf, [F][KB] drbf
+  float* drbs = rbs + F * KB;
+  float4* geo = reinterpret_cast<float4*>(drbs + F * KB);       // (u, d)
   float4* gfc = geo + F;                                        // (f_c, f_c', -, -)
   float* red = reinterpret_cast<float*>(gfc + F);               // [F edges][NW][4]
-  int* js = reinterpret_cast<int*>(sm + (size_t)G * F * (2 * KP + 8 + 4 * NW)) + (size_t)g * F;
+  int* js = reinterpret_cast<int*>(sm + (size_t)G * F * (2 * KB + 8 + 4 * NW)) + (size_t)g * F;
 
-  float w_s[KP], w_vv[KP], w_vs[KP];
+  float w_s[KB > 0 ? KB : 1], w_vv[KB > 0 ? KB : 1], w_vs[KB > 0 ? KB : 1];
 #pragma unroll
-  for (int k = 0; k < KP; ++k) {
+  for (int k = 0; k < KB; ++k) {
     w_s[k] = Wf[(size_t)f * KP + k];
     w_vv[k] = Wf[(size_t)(F + f) * KP + k];
     w_vs[k] = Wf[(size_t)(2 * F + f) * KP + k];
@@ -432,7 +467,7 @@ __global__ __launch_bounds__(256) void k_edge_bwd(int64_t n, int F, int K, float
         gfc[f] = make_float4(fc, dfc, 0.f, 0.f);
         js[f] = acol[c0 + f];
 #pragma unroll
-        for (int k = 0; k < KP; ++k) {
+        for (int k = 0; k < KB; ++k) {
           float t = d - (float)k * sig;
           float rb = k < K ? expf(-t * t * inv2s2) : 0.0f;
           rbs[f * KP + k] = rb;
@@ -442,30 +477,38 @@ __global__ __launch_bounds__(256) void k_edge_bwd(int64_t n, int F, int K, float
       group_sync(1 + g, F);
       for (int t = 0; t < cnt; ++t) {
         const float4 ge = geo[t];
-        const float4 fcv = gfc[t];
-        const float* rb = rbs + t * KP;
-        const float* drb = drbs + t * KP;
-        float ws = b_s, wvv = b_vv, wvs = b_vs, dws = 0.f, dwvv = 0.f, dwvs = 0.f;
+        float Ws, Wvv, Wvs, pd_s, pd_vv, pd_vs;   // filter and dW/dd per channel (f_c folded in)
+        if (STORED) {
+          const float* w = wst + (int64_t)(c0 + t) * 6 * F + f;
+          Ws = w[0]; Wvv = w[F]; Wvs = w[2 * F];
+          pd_s = w[3 * F]; pd_vv = w[4 * F]; pd_vs = w[5 * F];
+        } else {
+          const float4 fcv = gfc[t];
+          const float* rb = rbs + t * KP;
+          const float* drb = drbs + t * KP;
+          float ws = b_s, wvv = b_vv, wvs = b_vs, dws = 0.f, dwvv = 0.f, dwvs = 0.f;
 #pragma unroll
-        for (int k = 0; k < KP; k += 4) {
-          float4 q = *reinterpret_cast<const float4*>(rb + k);
-          float4 dq = *reinterpret_cast<const float4*>(drb + k);
-          float qa[4] = {q.x, q.y, q.z, q.w}, da[4] = {dq.x, dq.y, dq.z, dq.w};
+          for (int k = 0; k < KB; k += 4) {
+            float4 q = *reinterpret_cast<const float4*>(rb + k);
+            float4 dq = *reinterpret_cast<const float4*>(drb + k);
+            float qa[4] = {q.x, q.y, q.z, q.w}, da[4] = {dq.x, dq.y, dq.z, dq.w};
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            ws = fmaf(w_s[k + u], qa[u], ws);
-            wvv = fmaf(w_vv[k + u], qa[u], wvv);
-            wvs = fmaf(w_vs[k + u], qa[u], wvs);
-            dws = fmaf(w_s[k + u], da[u], dws);
-            dwvv = fmaf(w_vv[k + u], da[u], dwvv);
-            dwvs = fmaf(w_vs[k + u], da[u], dwvs);
+            for (int u = 0; u < 4; ++u) {
+              ws = fmaf(w_s[k + u], qa[u], ws);
+              wvv = fmaf(w_vv[k + u], qa[u], wvv);
+              wvs = fmaf(w_vs[k + u], qa[u], wvs);
+              dws = fmaf(w_s[k + u], da[u], dws);
+              dwvv = fmaf(w_vv[k + u], da[u], dwvv);
+              dwvs = fmaf(w_vs[k + u], da[u], dwvs);
+            }
           }
+          const float fc = fcv.x, dfc = fcv.y;
+          Ws = ws * fc; Wvv = wvv * fc; Wvs = wvs * fc;
+          pd_s = fc * dws + dfc * ws; pd_vv = fc * dwvv + dfc * wvv; pd_vs = fc * dwvs + dfc * wvs;
         }
         const int64_t i = js[t];
         const float gs = Gsm[i * F + f];
         const float gv0 = Gvm[i * 3 * F + f], gv1 = Gvm[i * 3 * F + F + f], gv2 = Gvm[i * 3 * F + 2 * F + f];
-        const float fc = fcv.x, dfc = fcv.y;
-        const float Ws = ws * fc, Wvv = wvv * fc, Wvs = wvs * fc;
         gps = fmaf(gs, Ws, gps);
         gy0 = fmaf(gv0, Wvv, gy0);
         gy1 = fmaf(gv1, Wvv, gy1);
@@ -474,7 +517,7 @@ __global__ __launch_bounds__(256) void k_edge_bwd(int64_t n, int F, int K, float
         const float q = -(gv0 * ge.x + gv1 * ge.y + gv2 * ge.z);
         gpvs = fmaf(q, Wvs, gpvs);
         const float gWs = gs * ps, gWvv = gv0 * y0 + gv1 * y1 + gv2 * y2, gWvs = q * pvs;
-        float pd = fc * (gWs * dws + gWvv * dwvv + gWvs * dwvs) + dfc * (gWs * ws + gWvv * wvv + gWvs * wvs);
+        float pd = gWs * pd_s + gWvv * pd_vv + gWvs * pd_vs;
         const float tv = pvs * Wvs;
         float r = warp_reduce4(pd, gv0 * tv, gv1 * tv, gv2 * tv, lane);
         if ((lane & 7) == 0) red[(t * NW + wig) * 4 + (lane >> 3)] = r;
@@ -598,27 +641,39 @@ static inline unsigned blocks_for(int64_t work) { return (unsigned)((work + kThr
 template <int KP>
 static void edge_fwd_kp(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow,
                         const int32_t* acol, const float4* ar, const float* PHI, const float* S, const float* V,
-                        float* SM, float* VM, __nv_bfloat16* VMb) {
+                        float* SM, float* VM, __nv_bfloat16* VMb, float* wst) {
   const int F = m.F, G = kThreads / F;
-  size_t smem = (size_t)G * F * (KP + 4) * sizeof(float) + (size_t)G * F * sizeof(int);
+  const int KD = wst ? KP : 0;
+  size_t smem = (size_t)G * F * (KP + KD + 4 + (wst ? 1 : 0)) * sizeof(float) + (size_t)G * F * sizeof(int);
   int64_t blocks = (n + G - 1) / G;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  { LaunchScope ls_(st); k_edge_fwd<KP><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, arow, acol, ar, PHI, S, V,
-                                                           m.L[t].Wf, m.L[t].bf, SM, VM, VMb); }
+  LaunchScope ls_(st);
+  if (wst)
+    k_edge_fwd<KP, true><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, arow, acol, ar, PHI, S, V,
+                                                                   m.L[t].Wf, m.L[t].bf, SM, VM, VMb, wst);
+  else
+    k_edge_fwd<KP, false><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, arow, acol, ar, PHI, S, V,
+                                                                    m.L[t].Wf, m.L[t].bf, SM, VM, VMb, nullptr);
 }
 
 template <int KP>
 static void edge_bwd_kp(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
                         const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm,
-                        const float* Gvm, float* GPHI, float4* hedge) {
+                        const float* Gvm, float* GPHI, float4* hedge, const float* wst) {
   const int F = m.F, G = kThreads / F, NW = F / 32;
-  size_t smem = (size_t)G * F * (2 * KP + 8 + 4 * NW) * sizeof(float) + (size_t)G * F * sizeof(int);
+  const int KB = wst ? 0 : KP;
+  size_t smem = (size_t)G * F * (2 * KB + 8 + 4 * NW) * sizeof(float) + (size_t)G * F * sizeof(int);
   int64_t blocks = (n + G - 1) / G;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  { LaunchScope ls_(st); k_edge_bwd<KP><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, accumulate, arow, acol, ar, PHI,
-                                                           Gsm, Gvm, m.L[t].Wf, m.L[t].bf, GPHI, hedge); }
+  LaunchScope ls_(st);
+  if (wst)
+    k_edge_bwd<KP, true><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, accumulate, arow, acol, ar, PHI,
+                                                                   Gsm, Gvm, m.L[t].Wf, m.L[t].bf, GPHI, hedge, wst);
+  else
+    k_edge_bwd<KP, false><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, accumulate, arow, acol, ar, PHI,
+                                                                    Gsm, Gvm, m.L[t].Wf, m.L[t].bf, GPHI, hedge, nullptr);
 }
 
 #define CTD_KP_DISPATCH(KPV, CALL) \
@@ -638,8 +693,10 @@ void edge_smem_setup() {
   if (done) return;
   done = true;
 #define CTD_SET_SMEM(K_)                                                                              \
-  cudaFuncSetAttribute(k_edge_fwd<K_>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);     \
-  cudaFuncSetAttribute(k_edge_bwd<K_>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_edge_fwd<K_, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+  cudaFuncSetAttribute(k_edge_fwd<K_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);  \
+  cudaFuncSetAttribute(k_edge_bwd<K_, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+  cudaFuncSetAttribute(k_edge_bwd<K_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   CTD_SET_SMEM(4) CTD_SET_SMEM(8) CTD_SET_SMEM(12) CTD_SET_SMEM(16) CTD_SET_SMEM(20) CTD_SET_SMEM(24)
   CTD_SET_SMEM(28) CTD_SET_SMEM(32)
 #undef CTD_SET_SMEM
@@ -695,7 +752,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
                                  const int32_t* arev, float* const* B, bool need_grad,
                                  double* energy_partials, int n_energy_partials, float4* hedge,
                                  float* force_s, double* virial_partials, int n_virial_partials,
-                                 float* e_atom, int* status) {
+                                 float* e_atom, int* status, float* wstore, int64_t wstore_layer_floats) {
   edge_smem_setup();
   StageGuard node_stage(STG_NODE);
   const int F = m.F, T = m.T, Fh = F / 2;
@@ -711,7 +768,8 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     gemm<EPI_BIAS>(st, n, 3 * F, F, T1, F, L.W2t, L.b2, nullptr, 0, T2, 3 * F);
     if (n > 0) { LaunchScope ls_(st); k_phi_pack<<<nb, kThreads, 0, st>>>(n, F, T2, V, PHI); }
     // message
-#define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, nullptr)
+    float* wst = (wstore && need_grad) ? wstore + t * wstore_layer_floats : nullptr;
+#define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, nullptr, wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_FWD);
       CTD_KP_DISPATCH(m.KP, CTD_FWD)
@@ -745,7 +803,8 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, GSM, T3, nullptr); }
     gemm<EPI_ADD>(st, 3 * n, F, 2 * F, T3, 2 * F, L.UV, nullptr, GV, F, GVM, F);         // gvm
     // message backward
-#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge)
+    const float* wst = wstore ? wstore + t * wstore_layer_floats : nullptr;
+#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge, wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
       CTD_KP_DISPATCH(m.KP, CTD_BWD)
@@ -796,16 +855,17 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
                                 const int32_t* arow, const int32_t* acol, const float4* ar, const int32_t* arev,
                                 float* const* B, __nv_bfloat16* const* Bb, bool need_grad,
                                 double* energy_partials, int n_energy_partials, float4* hedge, float* force_s,
-                                double* virial_partials, int n_virial_partials, float* e_atom, int* status) {
+                                double* virial_partials, int n_virial_partials, float* e_atom, int* status,
+                                float* wstore, int64_t wstore_layer_floats) {
   edge_smem_setup();
   StageGuard node_stage(STG_NODE);
   const int F = m.F, T = m.T, Fh = F / 2;
   const unsigned nb = blocks_for(n * F);
   int bad = 0;
   // Radial filter on tcgen05 inside the message kernel (F = 128); other widths keep the FP32
-  // filter.  The adjoint keeps the SIMT kernel: its gather-latency-bound epilogue runs faster
-  // with the 16 warps per SM the SIMT kernel reaches than with the 8 the TMEM budget allows
-  // (measured on the 1M-atom fcc workload; edge_bwd_tc stays available and tested).
+  // filter.  The adjoint takes the tcgen05 filter too unless the CUDA-core kernel is selected
+  // (m.tc_adjoint).  The tensor-core kernels recompute the filter, so storing edge filters
+  // applies to the CUDA-core edge kernels only.
   const bool use_tc = edge_tc_supported(F, m.K);
   const bool use_tc_bwd = use_tc && m.tc_adjoint;
   if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], Bb[BB_S0]); }
@@ -817,7 +877,8 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     bad |= gemm_bf16<1>(st, n, F, F, Bb[BB_S0 + t], F, L.W1b, L.b1, nullptr, 0, H1, F, Bb[BB_A1], F, status);
     bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, nullptr, 0, T2, 3 * F, nullptr, 0, status);
     if (n > 0) { LaunchScope ls_(st); k_phi_pack<<<nb, kThreads, 0, st>>>(n, F, T2, V, PHI); }
-#define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM])
+    float* wst = (wstore && need_grad && !use_tc) ? wstore + t * wstore_layer_floats : nullptr;
+#define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_FWD);
       if (use_tc) {
@@ -859,7 +920,8 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     bad |= gemm_bf16<0>(st, n, 2 * F, F, Bb[BB_GH2], F, L.A1tb, nullptr, nullptr, 0, T1, 2 * F, nullptr, 0, status);
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, GSM, T3, Bb[BB_GUV]); }
     bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
-#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge)
+    const float* wst = (wstore && !use_tc) ? wstore + t * wstore_layer_floats : nullptr;
+#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge, wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
       if (use_tc_bwd) {

@@ -11,10 +11,10 @@ from gpu_common import BF16_FORCE_RMSE, compare, engine, model, rel_force_rmse
 pytestmark = pytest.mark.gpu
 
 
-def _run(eng, orc, sy, F, T, S, bias=0.1, seed=0, tc_adjoint=0):
+def _run(eng, orc, sy, F, T, S, bias=0.1, seed=0, tc_adjoint=None):
     vals, blob = model(F, T, S, seed=seed, bias=bias)
     with eng.Potential(F, T=T, n_species=S, precision="bf16", params=blob) as pot:
-        if tc_adjoint:
+        if tc_adjoint is not None:
             from paper_2506_04055_gb300 import _lib
             pot.set_option(_lib.CTD_OPT_TC_ADJOINT, tc_adjoint)
         out = pot.compute(sy.species, sy.positions, sy.cell, energies=True)
@@ -37,9 +37,10 @@ def test_bf16_fcc4000_F128(orc):
     print(f"bf16 fcc4000: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_bf16_tensor_core_adjoint(orc, variant):
-    """The edge adjoint with the tcgen05 filter (option) on the fcc sub-cell and a small cell."""
+    """Each edge-adjoint variant (CUDA cores; tcgen05 filter with register or bulk-copy gathers)
+    on the fcc sub-cell and a small cell."""
     eng = engine()
     for sy in (syn.fcc(10, 10, 10, jitter=0.05, seed=0), syn.water_box(21, seed=2)):
         out, ref = _run(eng, orc, sy, 128, 3, 2, bias=0.1, tc_adjoint=variant)
