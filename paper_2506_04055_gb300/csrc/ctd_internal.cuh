@@ -111,6 +111,14 @@ __device__ __forceinline__ float dsilu_f(float x) {
   float s = 1.0f / (1.0f + __expf(-x));
   return s * (1.0f + x * (1.0f - s));
 }
+// Approximate-division forms for epilogues whose result is rounded to BF16 (relative error of
+// the division ~2 ulp of FP32, far below BF16's 2^-9; both tend to the right limits for large
+// |x|: __fdividef returns 0 once the denominator exceeds 2^126).
+__device__ __forceinline__ float silu_fast(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
+__device__ __forceinline__ float dsilu_fast(float x) {
+  const float s = __fdividef(1.0f, 1.0f + __expf(-x));
+  return s * (1.0f + x * (1.0f - s));
+}
 
 // ---------------------------------------------------------------- launchers (host side)
 // neighbors.cu

@@ -5,11 +5,12 @@
 // stored [out][in], i.e. K-major, so both operands are K-major 128B-swizzled tiles.
 //
 // One CTA per SM (persistent over 128-row tiles).  Warp 0: TMA producer (the weight tile W is
-// loaded once per CTA and stays in shared memory; A tiles stream through one or two stages).
-// Warp 1: TMEM allocation and the single-thread MMA issue (M = 128, N up to 256 per
-// instruction, K = 16 per instruction).  Warps 2-5: epilogue, one thread per tile row
-// (TMEM lane), 32 columns per tcgen05.ld.  Every wait is bounded; on a timeout the kernel
-// records ST_TIMEOUT in the status word and winds down.
+// loaded once per CTA and stays in shared memory; A streams through a ring of 64-column
+// k-blocks, 16 KB each, as many stages as shared memory holds).  Warp 1: TMEM allocation and
+// the single-thread MMA issue (M = 128, N up to 256 per instruction, K = 16 per instruction).
+// Warps 2-9: epilogue, two warps per TMEM lane quarter taking alternate 32-column chunks.
+// Every wait is bounded; on a timeout the kernel records ST_TIMEOUT in the status word and
+// winds down.
 #include <cstdio>
 
 #include "ctd_internal.cuh"
@@ -30,40 +31,46 @@ struct GemmBf16Args {
   bf16* outb;
   int ldob;
   int* status;
-  int a_stages, n_acc, b_box_rows, n_chunk;
+  int a_stages, n_acc, b_box_rows, n_chunk;   // a_stages: k-block stages of the A ring
   uint32_t tmem_cols;
 };
 
 constexpr int kTileM = 128;
 constexpr int kBlockK = 64;
 constexpr int kATileBytes = kTileM * kBlockK * 2;   // 16 KB per 64-column block
+constexpr int kTP = 36;                              // row pitch (floats) of an epilogue transpose tile
+constexpr int kEpiWarps = 8;
+constexpr int kMaxAStages = 8;
 
 template <int EPI>
-__global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, GemmBf16Args p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int KB = p.K / kBlockK;
   const int N = p.N;
   unsigned char* sB = smem;                                        // KB x N x 128 B
-  unsigned char* sA = sB + (size_t)KB * N * 128;                   // a_stages x KB x 16 KB
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)p.a_stages * KB * kATileBytes);
-  uint64_t* full = bars;          // [2]
-  uint64_t* empty = bars + 2;     // [2]
-  uint64_t* tfull = bars + 4;     // [2]
-  uint64_t* tempty = bars + 6;    // [2]
-  uint64_t* bbar = bars + 8;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+  unsigned char* sA = sB + (size_t)KB * N * 128;                   // a_stages x 16 KB
+  float* sT = reinterpret_cast<float*>(sA + (size_t)p.a_stages * kATileBytes);   // kEpiWarps x 32 x kTP
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sT + kEpiWarps * 32 * kTP);
+  uint64_t* full = bars;                    // [kMaxAStages]
+  uint64_t* empty = bars + kMaxAStages;     // [kMaxAStages]
+  uint64_t* tfull = bars + 2 * kMaxAStages; // [2]
+  uint64_t* tempty = tfull + 2;             // [2]
+  uint64_t* bbar = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bbar + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (p.M + kTileM - 1) / kTileM;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < p.a_stages; ++i) {
       umma::mbar_init(&full[i], 1);
       umma::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       umma::mbar_init(&tfull[i], 1);
-      umma::mbar_init(&tempty[i], 4);
+      umma::mbar_init(&tempty[i], kEpiWarps);
     }
     umma::mbar_init(bbar, 1);
     umma::mbar_fence_init();
@@ -74,7 +81,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ CU
   umma::fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
-  int issued = 0, last_acc = 0;
+  int64_t issued = 0;   // MMA thread: k-blocks issued
 
   if (warp == 0) {
     if (lane == 0) {
@@ -82,28 +89,31 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ CU
       for (int kb = 0; kb < KB; ++kb)
         for (int r0 = 0; r0 < N; r0 += p.b_box_rows)
           umma::tma_load_2d(sB + (size_t)kb * N * 128 + (size_t)r0 * 128, &tmB, kb * kBlockK, r0, bbar);
-      int it = 0;
-      for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int s = it % p.a_stages, u = it / p.a_stages;
-        if (it >= p.a_stages && !umma::mbar_wait(&empty[s], (u - 1) & 1)) { ok = false; break; }
-        umma::mbar_expect_tx(&full[s], (uint32_t)(KB * kATileBytes));
-        for (int kb = 0; kb < KB; ++kb)
-          umma::tma_load_2d(sA + ((size_t)s * KB + kb) * kATileBytes, &tmA, kb * kBlockK, (int)(tile * kTileM),
-                            &full[s]);
+      int64_t g = 0;   // k-blocks loaded so far
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = (int)(g % p.a_stages);
+          const int64_t u = g / p.a_stages;
+          if (g >= p.a_stages && !umma::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) { ok = false; break; }
+          umma::mbar_expect_tx(&full[s], (uint32_t)kATileBytes);
+          umma::tma_load_2d(sA + (size_t)s * kATileBytes, &tmA, kb * kBlockK, (int)(tile * kTileM), &full[s]);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       if (!umma::mbar_wait(bbar, 0)) ok = false;
       int it = 0;
+      int64_t g = 0;   // k-blocks consumed so far
+      const uint32_t idesc = umma::idesc_bf16_m128(p.n_chunk);
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++it) {
-        const int s = it % p.a_stages, a = it % p.n_acc;
-        if (!umma::mbar_wait(&full[s], (it / p.a_stages) & 1)) { ok = false; break; }
+        const int a = it % p.n_acc;
         if (it >= p.n_acc && !umma::mbar_wait(&tempty[a], ((it / p.n_acc) - 1) & 1)) { ok = false; break; }
-        umma::fence_after();
-        const uint32_t idesc = umma::idesc_bf16_m128(p.n_chunk);
-        for (int kb = 0; kb < KB; ++kb) {
-          const uint32_t a_base = umma::smem_u32(sA + ((size_t)s * KB + kb) * kATileBytes);
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = (int)(g % p.a_stages);
+          if (!umma::mbar_wait(&full[s], (uint32_t)((g / p.a_stages) & 1))) { ok = false; break; }
+          umma::fence_after();
+          const uint32_t a_base = umma::smem_u32(sA + (size_t)s * kATileBytes);
           const uint32_t b_base = umma::smem_u32(sB + (size_t)kb * N * 128);
           for (int j = 0; j < kBlockK / 16; ++j) {
             const uint64_t ad = umma::desc_sw128(a_base + 32u * j);
@@ -112,63 +122,87 @@ __global__ void __launch_bounds__(192, 1) k_gemm_bf16(const __grid_constant__ CU
               umma::mma_bf16(tmem + (uint32_t)(a * N + nc), ad, bd, idesc, (kb | j) != 0);
             }
           }
+          umma::mma_commit(&empty[s]);
+          ++issued;
         }
-        umma::mma_commit(&empty[s]);
+        if (!ok) break;
         umma::mma_commit(&tfull[a]);
-        last_acc = a;
-        ++issued;
       }
-      // the MMAs of the last issued tile have completed before TMEM is released
-      if (issued > 0) umma::mbar_wait(&tfull[last_acc], ((issued - 1) / p.n_acc) & 1, 200000000ull);
+      // every MMA issued has completed before TMEM is released (the commits of a thread
+      // complete in order, so the last k-block's empty barrier covers all of them)
+      if (issued > 0) {
+        const int64_t last = issued - 1;
+        umma::mbar_wait(&empty[last % p.a_stages], (uint32_t)((last / p.a_stages) & 1), 200000000ull);
+      }
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4
-    const int q = warp & 3;
-    const int row = q * 32 + lane;
+    // epilogue warps 2..5: TMEM lane quarter = warp % 4.  Each 32-row x 32-column chunk goes
+    // TMEM -> registers (thread = row) -> padded shared tile -> registers (8 lanes per row,
+    // 16 bytes each), so that global loads and stores move whole 128-byte row segments.
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    float* T = sT + (warp - 2) * 32 * kTP;
+    const int cr = lane >> 3, cc = 4 * (lane & 7);   // row within a group of 4, column quad
+    const int nchunks = N / 32;
     int it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       const int a = it % p.n_acc;
       if (!umma::mbar_wait(&tfull[a], (it / p.n_acc) & 1)) { ok = false; break; }
       umma::fence_after();
-      const int64_t m = tile * kTileM + row;
-      for (int c0 = 0; c0 < N; c0 += 32) {
+      const int64_t m0 = tile * kTileM + q * 32;   // first row of this warp's quarter
+      if (half >= nchunks) {
+        umma::fence_before();
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&tempty[a]);
+      }
+      for (int ch = half; ch < nchunks; ch += 2) {
+        const int c0 = 32 * ch;
         float v[32];
         umma::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * N + c0), v);
-        if (m < p.M) {
-          float o[32];
+        if (ch + 2 >= nchunks) {
+          // the accumulator has been read: the MMA of a later tile may reuse it
+          umma::fence_before();
+          __syncwarp();
+          if (lane == 0) umma::mbar_arrive(&tempty[a]);
+        }
+        __syncwarp();
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            float x = v[i];
-            if (EPI == 0 || EPI == 1) x += p.bias ? p.bias[c0 + i] : 0.0f;
-            if (EPI == 2) x += p.aux[m * p.ldaux + c0 + i];
-            if (EPI == 3) x *= dsilu_f(p.aux[m * p.ldaux + c0 + i]);
-            o[i] = x;
+        for (int i = 0; i < 8; ++i)
+          *reinterpret_cast<float4*>(T + lane * kTP + 4 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        __syncwarp();
+        float4 bq = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((EPI == 0 || EPI == 1) && p.bias) bq = *reinterpret_cast<const float4*>(p.bias + c0 + cc);
+        // the chunk's aux values, all loads in flight before any store
+        float4 g[8];
+        if (EPI == 2 || EPI == 3) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int64_t m = m0 + cr + 4 * j;
+            g[j] = m < p.M ? __ldg(reinterpret_cast<const float4*>(p.aux + m * p.ldaux + c0 + cc))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          if (p.out) {
-            float4* dst = reinterpret_cast<float4*>(p.out + m * p.ldo + c0);
+        }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) dst[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
-          }
-          if (p.outb) {
-            uint4* dst = reinterpret_cast<uint4*>(p.outb + m * p.ldob + c0);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              uint32_t w[4];
-#pragma unroll
-              for (int h = 0; h < 4; ++h) {
-                float x0 = o[8 * i + 2 * h], x1 = o[8 * i + 2 * h + 1];
-                if (EPI == 1) { x0 = silu_f(x0); x1 = silu_f(x1); }
-                __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
-                w[h] = *reinterpret_cast<uint32_t*>(&b2);
-              }
-              dst[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        for (int j = 0; j < 8; ++j) {
+          const int r = cr + 4 * j;
+          const int64_t m = m0 + r;
+          float4 x = *reinterpret_cast<const float4*>(T + r * kTP + cc);
+          if (m < p.M) {
+            if (EPI == 0 || EPI == 1) { x.x += bq.x; x.y += bq.y; x.z += bq.z; x.w += bq.w; }
+            if (EPI == 2) { x.x += g[j].x; x.y += g[j].y; x.z += g[j].z; x.w += g[j].w; }
+            if (EPI == 3) {
+              x.x *= dsilu_fast(g[j].x); x.y *= dsilu_fast(g[j].y); x.z *= dsilu_fast(g[j].z); x.w *= dsilu_fast(g[j].w);
+            }
+            if (p.out) *reinterpret_cast<float4*>(p.out + m * p.ldo + c0 + cc) = x;
+            if (p.outb) {
+              float y0 = x.x, y1 = x.y, y2 = x.z, y3 = x.w;
+              if (EPI == 1) { y0 = silu_fast(y0); y1 = silu_fast(y1); y2 = silu_fast(y2); y3 = silu_fast(y3); }
+              __nv_bfloat162 b01 = __floats2bfloat162_rn(y0, y1), b23 = __floats2bfloat162_rn(y2, y3);
+              *reinterpret_cast<uint2*>(p.outb + m * p.ldob + c0 + cc) =
+                  make_uint2(*reinterpret_cast<uint32_t*>(&b01), *reinterpret_cast<uint32_t*>(&b23));
             }
           }
         }
       }
-      umma::fence_before();
-      __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&tempty[a]);
     }
   }
   if (!ok) atomicOr(p.status, (int)ST_TIMEOUT);
@@ -227,8 +261,11 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
               const float* bias, const float* aux, int ldaux, float* out, int ldo, bf16* outb, int ldob,
               int* status) {
   if (M == 0) return 0;
+  // the epilogue moves 16-byte quads of FP32 (8-byte quads of BF16) per row
   if (!gemm_bf16_supported(N, K) || (lda * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) ||
-      (reinterpret_cast<uintptr_t>(W) & 15))
+      (reinterpret_cast<uintptr_t>(W) & 15) || (out && (ldo % 4 || (reinterpret_cast<uintptr_t>(out) & 15))) ||
+      (outb && (ldob % 4 || (reinterpret_cast<uintptr_t>(outb) & 7))) ||
+      (aux && (ldaux % 4 || (reinterpret_cast<uintptr_t>(aux) & 15))) || (bias && (reinterpret_cast<uintptr_t>(bias) & 15)))
     return -1;
   GemmBf16Args p{};
   p.M = M; p.N = N; p.K = K; p.bias = bias; p.aux = aux; p.ldaux = ldaux; p.out = out; p.ldo = ldo;
@@ -237,17 +274,19 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
   p.n_chunk = N <= 256 ? N : N / 2;
   if (p.n_chunk > 256 || p.n_chunk % 16) return -1;
   const int KB = K / kBlockK;
-  const size_t b_bytes = (size_t)KB * N * 128, a_bytes = (size_t)KB * kATileBytes;
-  const size_t limit = 227 * 1024 - 1024 - 256;
-  p.a_stages = (b_bytes + 2 * a_bytes <= limit) ? 2 : 1;
-  if (b_bytes + a_bytes > limit) return -1;
+  const size_t b_bytes = (size_t)KB * N * 128;
+  const size_t t_bytes = (size_t)kEpiWarps * 32 * kTP * sizeof(float);
+  const size_t limit = 227 * 1024 - 1024 - 256 - t_bytes;
+  if (b_bytes + 2 * (size_t)kATileBytes > limit) return -1;
+  p.a_stages = (int)((limit - b_bytes) / kATileBytes);
+  if (p.a_stages > kMaxAStages) p.a_stages = kMaxAStages;
   p.n_acc = 2 * N <= 512 ? 2 : 1;
   uint32_t cols = 32;
   while (cols < (uint32_t)(p.n_acc * N)) cols <<= 1;
   p.tmem_cols = cols;
   CUtensorMap ta, tb;
   if (!make_tmap_bf16(&ta, A, M, K, lda, kTileM) || !make_tmap_bf16(&tb, W, N, K, K, p.b_box_rows)) return -2;
-  size_t smem = 1024 + b_bytes + (size_t)p.a_stages * a_bytes + 256;
+  size_t smem = 1024 + b_bytes + (size_t)p.a_stages * kATileBytes + t_bytes + 256;
   // a CTA holding more than half of TMEM runs alone on its SM, so allocation never waits
   if (p.tmem_cols > 256 && smem < 120 * 1024) smem = 120 * 1024;
   static bool attr_set[4] = {false, false, false, false};
@@ -259,7 +298,7 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
   const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
   {
     LaunchScope ls_(st);
-    k_gemm_bf16<EPI><<<grid, 192, smem, st>>>(ta, tb, p);
+    k_gemm_bf16<EPI><<<grid, 64 + 32 * kEpiWarps, smem, st>>>(ta, tb, p);
   }
   return 0;
 }
