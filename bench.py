@@ -213,9 +213,13 @@ def run_ours(args):
         except eng.CtdError as e:
             results[prec] = {"error": str(e)}
             continue
+        from paper_2506_04055_gb300 import _lib as L
         if args.tc_adjoint is not None and prec == "bf16":
-            from paper_2506_04055_gb300 import _lib as L
             pot.set_option(L.CTD_OPT_TC_ADJOINT, args.tc_adjoint)
+        if args.tc_message is not None and prec == "bf16":
+            pot.set_option(L.CTD_OPT_TC_MESSAGE, args.tc_message)
+        if args.chunk_rows is not None:
+            pot.set_option(L.CTD_OPT_EDGE_CHUNK_ROWS, args.chunk_rows)
         pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=SKIN)
         for _ in range(args.warmup):
             pot.md_run(1, DT)
@@ -642,7 +646,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tc-adjoint", type=int, default=None,
                     help="BF16 edge adjoint: 0 CUDA cores, 1 tcgen05 filter with register gathers, "
-                         "2 tcgen05 filter with bulk-copy gathers (the library's default)")
+                         "2 tcgen05 filter with bulk-copy gathers (the library's default), 3 as 2 with "
+                         "the folded basis")
+    ap.add_argument("--tc-message", type=int, default=None,
+                    help="BF16 message kernel: 1 register gathers (the library's default), 2 bulk-copy gathers")
+    ap.add_argument("--chunk-rows", type=int, default=None,
+                    help="rows per block-cyclic chunk of the bulk-gathered edge kernels (0: contiguous)")
     ap.add_argument("--workload", default="fcc1m",
                     choices=["fcc1m", "water192", "water96k", "mixture90k", "serve"])
     ap.add_argument("--replicas", type=int, default=512)

@@ -142,10 +142,12 @@ int ctd_md_run(ctd_ctx *ctx, int32_t nsteps, double dt, double *epot, double *ek
 int ctd_md_get_state(ctd_ctx *ctx, double *positions, double *velocities);
 
 /* ---- options -------------------------------------------------------------------------- */
-/* CTD_OPT_TC_ADJOINT (value 0, 1 or 2; default 2): on the BF16 path with F = 128, run the
- * edge adjoint with the radial filter on tcgen05 as well (the message kernel always does):
+/* CTD_OPT_TC_ADJOINT (value 0..4; default 2): on the BF16 path with F = 128, run the edge
+ * adjoint with the radial filter on tcgen05 as well (the message kernel always does):
  * 1 = neighbour gradients gathered into registers, 2 = gathered into shared memory by bulk
- * asynchronous copies.  0 selects the CUDA-core adjoint. */
+ * asynchronous copies, 3 = as 2 with the cutoff and bias folded into the tensor-core basis,
+ * 4 = as 2 with each basis value entered as a BF16 pair (hi + lo, two MMAs).  0 selects the
+ * CUDA-core adjoint. */
 #define CTD_OPT_TC_ADJOINT 1
 /* CTD_OPT_EDGE_STORE (value 0 or 1; default 0): the forward message kernel stores, per active
  * edge and layer, the cutoff-scaled radial filter and its distance derivative (6F floats), and
@@ -154,6 +156,15 @@ int ctd_md_get_state(ctd_ctx *ctx, double *positions, double *velocities);
  * of the device's free memory, and otherwise the call recomputes (ctd_stats.edges_stored says
  * which).  It applies to the CUDA-core edge kernels: the FP32 path and BF16 with F != 128. */
 #define CTD_OPT_EDGE_STORE 2
+/* CTD_OPT_TC_MESSAGE (value 1..3; default 1): BF16 path with F = 128, message kernel with the
+ * senders' rows gathered into registers (1), into shared memory by bulk asynchronous copies
+ * with the filter's cutoff and bias folded into the tensor-core basis (2), or as 1 with each
+ * basis value entered as a BF16 pair (hi + lo, two MMAs) (3). */
+#define CTD_OPT_TC_MESSAGE 3
+/* CTD_OPT_EDGE_CHUNK_ROWS (value >= 0; default 32): the bulk-gathered edge kernels hand out the
+ * sorted rows in chunks of this many rows, block-cyclically over all row streams of the GPU;
+ * 0 gives each stream one contiguous range. */
+#define CTD_OPT_EDGE_CHUNK_ROWS 4
 int ctd_set_option(ctd_ctx *ctx, int32_t option, int64_t value);
 
 /* ---- launch accounting and stage timing (benchmarks, statistics) ------------------------- */

@@ -177,6 +177,8 @@ def ctd_md_get_state(ctx, positions_ptr, velocities_ptr):
 
 CTD_OPT_TC_ADJOINT = 1
 CTD_OPT_EDGE_STORE = 2
+CTD_OPT_TC_MESSAGE = 3
+CTD_OPT_EDGE_CHUNK_ROWS = 4
 
 
 def ctd_set_option(ctx, option, value):

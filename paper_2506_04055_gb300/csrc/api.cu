@@ -234,6 +234,7 @@ int prune(ctd_ctx* c, double* maxdisp_out) {
   ENSURE(c, c->ar, sizeof(float4) * e1);
   ENSURE(c, c->vidx, sizeof(int32_t) * e1);
   ENSURE(c, c->arev, sizeof(int32_t) * e1);
+  ENSURE(c, c->aend, sizeof(int32_t) * e1);
   CUDA_OK(c, cudaMemsetAsync(c->maxd.p, 0, sizeof(unsigned int), st));
   launch_delta(st, n, P<double>(c->x_s), P<double>(c->xref_s), P<float4>(c->delta), P<unsigned int>(c->maxd));
   if (maxdisp_out) {
@@ -252,7 +253,7 @@ int prune(ctd_ctx* c, double* maxdisp_out) {
                rc2, P<int32_t>(c->acount), P<int32_t>(c->arow), P<int32_t>(c->acol), P<float4>(c->ar),
                P<int32_t>(c->vidx), P<int32_t>(c->v2a));
   launch_prune_rev(st, n, P<int32_t>(c->arow), P<int32_t>(c->vidx), P<int32_t>(c->vrev), P<int32_t>(c->v2a),
-                   P<int32_t>(c->arev));
+                   P<int32_t>(c->arev), P<int32_t>(c->aend));
   CUDA_OK(c, cudaGetLastError());
   return CTD_OK;
 }
@@ -312,7 +313,7 @@ int evaluate(ctd_ctx* c, bool need_grad) {
                                           P<float4>(c->ar), P<int32_t>(c->arev), ptrs.data(), bptrs.data(), need_grad,
                                           P<double>(c->epart), kPartials, P<float4>(c->hedge), P<float>(c->force_s),
                                           P<double>(c->vpart), kPartials, P<float>(c->eatom), P<int>(c->status),
-                                          wst, wlayer);
+                                          wst, wlayer, P<int32_t>(c->aend));
     if (bad) return fail(c, CTD_ERR_INVALID_ARG, "BF16 path: unsupported GEMM shape");
   } else {
     model_forward_backward_fp32(st, c->mw, n, P<int32_t>(c->z_s), P<int32_t>(c->arow), P<int32_t>(c->acol),
@@ -435,6 +436,9 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
     o.Wf64 = alloc((size_t)3 * F * 64);
     for (int r = 0; r < 3 * F; ++r)
       for (int k = 0; k < K && k < 64; ++k) h[o.Wf64 + (size_t)r * 64 + k] = (float)Wf[(size_t)r * K + k];
+    // the filter bias in column K: kernels that fold it put f_c at basis index K, the others 0
+    if (K < 32)
+      for (int r = 0; r < 3 * F; ++r) h[o.Wf64 + (size_t)r * 64 + K] = (float)bf[r];
     o.bf = put(bf, 1, 3 * F, false);
     o.UV = alloc((size_t)2 * F * F);
     o.UVt = alloc((size_t)2 * F * F);
@@ -518,6 +522,8 @@ int ctd_create(ctd_ctx** out, const ctd_model_desc* desc, size_t hbm_budget_byte
   c->budget = hbm_budget_bytes;
   c->mw.tc_adjoint = true;   // BF16 path, F = 128: bulk-gathered tensor-core adjoint
   c->mw.tc_adjoint_variant = 2;
+  c->mw.tc_message_variant = 1;
+  c->mw.edge_chunk_rows = 32;
   cudaGetDevice(&c->device);
   if (cuda_stream) {
     c->st = static_cast<cudaStream_t>(cuda_stream);
@@ -620,12 +626,20 @@ int ctd_get_pairs(ctd_ctx* c, int32_t* pi, int32_t* pj, int8_t* shift, int64_t c
 int ctd_set_option(ctd_ctx* c, int32_t option, int64_t value) {
   if (!c) return CTD_ERR_INVALID_ARG;
   switch (option) {
+    case CTD_OPT_EDGE_CHUNK_ROWS:
+      if (value < 0 || value > (1 << 30)) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_EDGE_CHUNK_ROWS out of range");
+      c->mw.edge_chunk_rows = value;
+      return CTD_OK;
+    case CTD_OPT_TC_MESSAGE:
+      if (value < 1 || value > 3) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_MESSAGE takes 1, 2 or 3");
+      c->mw.tc_message_variant = (int)value;
+      return CTD_OK;
     case CTD_OPT_EDGE_STORE:
       if (value < 0 || value > 1) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_EDGE_STORE takes 0 or 1");
       c->mw.edge_store = value != 0;
       return CTD_OK;
     case CTD_OPT_TC_ADJOINT:
-      if (value < 0 || value > 2) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0, 1 or 2");
+      if (value < 0 || value > 6) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0 .. 6");
       c->mw.tc_adjoint = value != 0;
       c->mw.tc_adjoint_variant = (int)value;
       return CTD_OK;

@@ -101,8 +101,10 @@ struct ModelW {
   const float *R1, *R1t, *d1, *R2, *d2;   // [F/2][F], [F][F/2]
   const __nv_bfloat16 *R1b, *R1tb;
   bool tc_adjoint;                 // BF16 path: edge adjoint with the tensor-core filter
-  int tc_adjoint_variant;          // 1: register gathers, 2: bulk-copy gathers into shared memory
+  int tc_adjoint_variant;          // 1 register gathers, 2 bulk-copy gathers, 3 + folded basis, 4 + split basis
   bool edge_store;                 // store per-edge filters in the forward pass for the adjoint
+  int tc_message_variant;          // BF16 message kernel: 1 register gathers, 2 bulk-copy gathers, 3 = 1 + split basis
+  int64_t edge_chunk_rows;         // bulk-gathered kernels: rows per chunk (0: one range per stream)
 };
 
 // ---------------------------------------------------------------- small device helpers
@@ -144,7 +146,8 @@ void launch_prune(cudaStream_t st, bool fill, int64_t n, const int32_t* vrow, co
                   const float4* vbase, const float4* delta, float rc2, int32_t* acount,
                   const int32_t* arow, int32_t* acol, float4* ar, int32_t* vidx, int32_t* v2a);
 void launch_prune_rev(cudaStream_t st, int64_t n, const int32_t* arow, const int32_t* vidx,
-                      const int32_t* vrev, const int32_t* v2a, int32_t* arev);
+                      const int32_t* vrev, const int32_t* v2a, int32_t* arev,
+                      int32_t* aend);
 // scan.cu
 size_t scan_temp_bytes(int64_t n);
 void launch_exclusive_scan(cudaStream_t st, int64_t n, const int32_t* in, int32_t* out,
@@ -167,10 +170,12 @@ bool make_tmap_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols
 bool edge_tc_supported(int F, int K);
 int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow, const int32_t* acol,
                 const float4* ar, const float* PHI, const float* S, const float* V, float* SM, float* VM,
-                __nv_bfloat16* VMb, int* status);
+                __nv_bfloat16* VMb, int* status,
+                const int32_t* aend);
 int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
                 const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm, const float* Gvm,
-                float* GPHI, float4* hedge, int* status);
+                float* GPHI, float4* hedge, int* status,
+                const int32_t* aend);
 template <int EPI>
 int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, int64_t lda,
               const __nv_bfloat16* W, const float* bias, const float* aux, int ldaux, float* out, int ldo,
@@ -185,7 +190,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
                                 float* const* bufs, __nv_bfloat16* const* bbufs, bool need_grad,
                                 double* energy_partials, int n_energy_partials, float4* hedge, float* force_s,
                                 double* virial_partials, int n_virial_partials, float* e_atom, int* status,
-                                float* wstore, int64_t wstore_layer_floats);
+                                float* wstore, int64_t wstore_layer_floats, const int32_t* aend);
 void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
                                  const int32_t* arow, const int32_t* acol, const float4* ar,
                                  const int32_t* arev, float* const* bufs, bool need_grad,

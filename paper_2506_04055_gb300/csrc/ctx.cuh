@@ -52,7 +52,7 @@ struct ctd_ctx {
 
   DBuf x_user, z_user, xw, wrapm, cellid, cell_count, cell_start, cursor, tmp_idx, perm, inv_perm;
   DBuf xw_s, xref_s, z_s, x_s, count, vrow, vcol, vimg, vbase, vrev, v2a, status, delta, maxd;
-  DBuf acount, arow, acol, ar, vidx, arev, hedge, force_s, eatom, epart, vpart, kpart, scan_tmp;
+  DBuf acount, arow, acol, ar, vidx, arev, aend, hedge, force_s, eatom, epart, vpart, kpart, scan_tmp;
   DBuf out_e, out_f, out_w, out_eatom;
   DBuf wstore;              // per-edge filters [T][E][6F] when edge storage is on
   bool last_stored = false;  // the last evaluation stored edge filters
@@ -68,7 +68,7 @@ struct ctd_ctx {
   ctd_ctx() {
     DBuf* list[] = {&params, &params_bf, &x_user, &z_user, &xw, &wrapm, &cellid, &cell_count, &cell_start, &cursor,
                     &tmp_idx, &perm, &inv_perm, &xw_s, &xref_s, &z_s, &x_s, &count, &vrow, &vcol, &vimg,
-                    &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev,
+                    &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev, &aend,
                     &hedge, &force_s, &eatom, &epart, &vpart, &kpart, &scan_tmp, &out_e, &out_f, &out_w,
                     &out_eatom, &wstore, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp};
     for (DBuf* b : list) all.push_back(b);

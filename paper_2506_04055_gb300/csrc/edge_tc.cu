@@ -50,14 +50,31 @@ __device__ __forceinline__ void store_basis_row(unsigned char* tile, int r, cons
   }
 }
 
+// Row r of a hi and a lo tile: hi = bf16(v), lo = bf16(v - hi).  The MMA adds Wf . hi and
+// Wf . lo in FP32, so the basis enters with about 16 significant bits instead of 8 (the
+// tensor pipe has ample headroom for the second product).
+__device__ __forceinline__ void store_basis_row_split(unsigned char* hi, unsigned char* lo, int r,
+                                                      const float (&v)[kKPad]) {
+  float h[kKPad], l[kKPad];
+#pragma unroll
+  for (int k = 0; k < kKPad; ++k) {
+    h[k] = __bfloat162float(__float2bfloat16_rn(v[k]));
+    l[k] = v[k] - h[k];
+  }
+  store_basis_row(hi, r, h);
+  store_basis_row(lo, r, l);
+}
+
 struct EdgeTcArgs {
   int64_t n;
   int64_t rows_per_cta;
+  int64_t chunk_rows;              // block-cyclic kernels: rows per chunk
   int K;
   float rc;
   int accumulate;
   const int32_t* __restrict__ arow;
   const int32_t* __restrict__ acol;
+  const int32_t* __restrict__ aend;  // rows completed at each edge (1 + following empty rows; 0 inside a row)
   const float4* __restrict__ ar;
   const float* __restrict__ PHI;   // [n][6F]
   const float* __restrict__ S;     // [n][F]
@@ -134,20 +151,59 @@ __device__ __forceinline__ StreamRange stream_range(const EdgeTcArgs& p, int s) 
   return R;
 }
 
+// Block-cyclic work for the bulk-gathered kernels: the sorted rows are cut into chunks of
+// p.chunk_rows rows, and chunk k goes to stream k mod (gridDim.x * NS), the stream id being
+// blockIdx.x * NS + s.  All streams of the GPU then sweep the (cell-ordered) atoms together,
+// so the neighbour rows they gather at any moment stay within a window that fits in L2.
+struct Chunk {
+  int64_t r0, r1, e0, e1;
+  int ntiles;
+};
+template <int NE>
+__device__ __forceinline__ bool chunk_at(const EdgeTcArgs& p, int64_t k, Chunk& c) {
+  const int64_t r0 = k * p.chunk_rows;
+  if (r0 >= p.n) return false;
+  c.r0 = r0;
+  c.r1 = r0 + p.chunk_rows < p.n ? r0 + p.chunk_rows : p.n;
+  c.e0 = p.arow[c.r0];
+  c.e1 = p.arow[c.r1];
+  c.ntiles = (int)((c.e1 - c.e0 + NE - 1) / NE);
+  return true;
+}
+
+// Folded radial basis (k < K): b_k = f_c rbf_k, b_K = f_c, so that the filter's bias sits in
+// column K of the BF16 filter matrix and the MMA yields W = f_c (Wf rbf + bf) itself; with
+// DERIV also the distance derivative db_k = f_c rbf'_k + f_c' rbf_k, db_K = f_c'.
+template <bool DERIV>
+__device__ __forceinline__ void folded_basis(float d, int K, float sig, float inv2s2, float inv_s2, float inv_rc,
+                                             float (&b)[kKPad], float (&db)[kKPad]) {
+  const float fc = 0.5f * (cospif(d * inv_rc) + 1.0f);
+  const float dfc = -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc);
+#pragma unroll
+  for (int k = 0; k < kKPad; ++k) {
+    const float t = d - (float)k * sig;
+    const float v = k < K ? expf(-t * t * inv2s2) : 0.0f;
+    b[k] = k < K ? fc * v : (k == K ? fc : 0.0f);
+    if (DERIV) db[k] = k < K ? fc * (-v * t * inv_s2) + dfc * v : (k == K ? dfc : 0.0f);
+  }
+}
+
 // warps 0..1 producers, warp 2 MMA / TMEM owner, warps 3 .. 3 + 4 NS - 1 epilogue
-template <int NE, int NS>
+template <int NE, int NS, bool SPLIT, int TB, bool AEND = false>
 __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = align1024(smem_raw);
   unsigned char* sA = smem;                                        // Wf tiles
-  unsigned char* sB = sA + kWfBytes;                               // [NS][2][NE x 128 B] basis tiles
-  int* sj = reinterpret_cast<int*>(sB + NS * 2 * NE * 128);        // [NS][2][NE] sender index
+  constexpr int NB = SPLIT ? 2 : 1;                                // basis tiles per buffer (hi[, lo])
+  static_assert(NS * TB * 3 * NE <= 512, "TMEM columns");
+  unsigned char* sB = sA + kWfBytes;                               // [NS][2][NB][NE x 128 B] basis
+  int* sj = reinterpret_cast<int*>(sB + NS * 2 * NB * NE * 128);   // [NS][2][NE] sender index
   int* sfl = sj + NS * 2 * NE;                                     // [NS][2][NE] rows ending at the slot
   float4* sgeo = reinterpret_cast<float4*>(sfl + NS * 2 * NE);     // [NS][2][NE] (u, f_c)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sgeo + NS * 2 * NE);
   uint64_t* wbar = bars;                 // Wf loaded
-  uint64_t* sbar = bars + 1;             // per stream: bready[2], bfree[2], tfull, tempty
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + 6 * NS);
+  uint64_t* sbar = bars + 1;             // per stream: bready[2], bfree[2], tfull[2], tempty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + 8 * NS);
 
   if ((int64_t)blockIdx.x * p.rows_per_cta >= p.n) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -155,13 +211,15 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
   if (threadIdx.x == 0) {
     umma::mbar_init(wbar, 1);
     for (int s = 0; s < NS; ++s) {
-      uint64_t* b = sbar + 6 * s;
+      uint64_t* b = sbar + 8 * s;
       umma::mbar_init(&b[0], 1);
       umma::mbar_init(&b[1], 1);
       umma::mbar_init(&b[2], 4);
       umma::mbar_init(&b[3], 4);
       umma::mbar_init(&b[4], 1);
-      umma::mbar_init(&b[5], 4);
+      umma::mbar_init(&b[5], 1);
+      umma::mbar_init(&b[6], 4);
+      umma::mbar_init(&b[7], 4);
     }
     umma::mbar_fence_init();
   }
@@ -189,26 +247,28 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
     for (int s = 0; s < NS; ++s) {
       R[s] = stream_range<NE, NS>(p, s);
       rp[s] = R[s].r0;
-      while (rp[s] < R[s].r1 && p.arow[rp[s] + 1] == R[s].e0) ++rp[s];
+      if (!AEND)
+        while (rp[s] < R[s].r1 && p.arow[rp[s] + 1] == R[s].e0) ++rp[s];
       maxt = R[s].ntiles > maxt ? R[s].ntiles : maxt;
     }
     for (int it = 0; ok && it < maxt; ++it) {
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         if ((s & 1) != warp || it >= R[s].ntiles) continue;
-        uint64_t* b = sbar + 6 * s;
+        uint64_t* b = sbar + 8 * s;
         const int bb = it & 1;
         if (it >= 2 && !umma::mbar_wait(&b[2 + bb], ((it >> 1) - 1) & 1)) { ok = false; break; }
-        unsigned char* tile = sB + (s * 2 + bb) * NE * 128;
+        unsigned char* tile = sB + (s * 2 + bb) * NB * NE * 128;
         const int64_t tb = R[s].e0 + (int64_t)it * NE;
         const int so = (s * 2 + bb) * NE;
         for (int k0 = lane; k0 < NE; k0 += 32) {
           const int64_t e = tb + k0;
           float rb[kKPad];
-          int j = 0;
+          int j = 0, ecnt = 0;
           float4 geo = make_float4(0.f, 0.f, 0.f, 0.f);
           if (e < R[s].e1) {
             const float4 r = p.ar[e];
+            if (AEND) ecnt = p.aend[e];
             const float d = r.w, id = 1.0f / d;
             geo = make_float4(r.x * id, r.y * id, r.z * id, 0.5f * (cospif(d * inv_rc) + 1.0f));
             j = p.acol[e];
@@ -221,11 +281,15 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
 #pragma unroll
             for (int k = 0; k < kKPad; ++k) rb[k] = 0.0f;
           }
-          store_basis_row(tile, k0, rb);
+          if (SPLIT)
+            store_basis_row_split(tile, tile + NE * 128, k0, rb);
+          else
+            store_basis_row(tile, k0, rb);
           sj[so + k0] = j;
           sgeo[so + k0] = geo;
+          if (AEND) sfl[so + k0] = ecnt;
         }
-        mark_row_ends(lane, sfl + so, NE, tb, R[s].r1, p.arow, rp[s]);
+        if (!AEND) mark_row_ends(lane, sfl + so, NE, tb, R[s].r1, p.arow, rp[s]);
         umma::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&b[bb]);
@@ -245,20 +309,22 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
           if (it >= nt[s]) continue;
-          uint64_t* b = sbar + 6 * s;
+          uint64_t* b = sbar + 8 * s;
           const int bb = it & 1;
           if (!umma::mbar_wait(&b[bb], (it >> 1) & 1)) { ok = false; break; }
-          if (it >= 1 && !umma::mbar_wait(&b[5], (it - 1) & 1)) { ok = false; break; }
+          // TMEM buffer a was last read by the epilogue for tile it - TB
+          const int a = it % TB;
+          if (it >= TB && !umma::mbar_wait(&b[6 + a], ((it / TB) - 1) & 1)) { ok = false; break; }
           umma::fence_after();
-          const uint32_t bbase = umma::smem_u32(sB + (s * 2 + bb) * NE * 128);
+          const uint32_t bbase = umma::smem_u32(sB + (s * 2 + bb) * NB * NE * 128);
 #pragma unroll
           for (int m = 0; m < 3; ++m)
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
-              umma::mma_bf16(tmem + (uint32_t)(s * 3 * NE + m * NE),
-                             umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * k),
-                             umma::desc_sw128(bbase + 32u * k), idesc, k > 0);
-          umma::mma_commit(&b[4]);
+            for (int k = 0; k < 2 * NB; ++k)   // k-halves of the hi tile[, then of the lo tile]
+              umma::mma_bf16(tmem + (uint32_t)((s * TB + a) * 3 * NE + m * NE),
+                             umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * (k & 1)),
+                             umma::desc_sw128(bbase + (uint32_t)(k >> 1) * NE * 128 + 32u * (k & 1)), idesc, k > 0);
+          umma::mma_commit(&b[4 + a]);
           ++issued[s];
         }
       }
@@ -267,7 +333,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
     const int s = (warp - 3) >> 2;         // stream of this epilogue warpgroup
     const int q = warp & 3, f = q * 32 + lane;
     const StreamRange R = stream_range<NE, NS>(p, s);
-    uint64_t* b = sbar + 6 * s;
+    uint64_t* b = sbar + 8 * s;
     const float bs = p.bf[f], bvv = p.bf[kF + f], bvs = p.bf[2 * kF + f];
     int64_t r = R.r0;
     float as = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f;
@@ -290,8 +356,8 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
     };
     while (r < R.r1 && p.arow[r + 1] == R.e0) flush();
     for (int it = 0; it < R.ntiles; ++it) {
-      const int bb = it & 1;
-      if (!umma::mbar_wait(&b[4], it & 1)) { ok = false; break; }
+      const int bb = it & 1, a = it % TB;
+      if (!umma::mbar_wait(&b[4 + a], (it / TB) & 1)) { ok = false; break; }
       umma::fence_after();
       const int64_t tb = R.e0 + (int64_t)it * NE;
       const int nlive = (int)((R.e1 - tb) < NE ? (R.e1 - tb) : NE);
@@ -302,14 +368,14 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
 #pragma unroll 1
       for (int c = 0; c < NE / 8; ++c) {
         float ds[8], dv[8], dw[8];
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * 3 * NE + c * 8);
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((s * TB + a) * 3 * NE + c * 8);
         umma::tmem_ld8(ta, ds);
         umma::tmem_ld8(ta + NE, dv);
         umma::tmem_ld8(ta + 2 * NE, dw);
         if (c == NE / 8 - 1) {
           umma::fence_before();
           __syncwarp();
-          if (lane == 0) umma::mbar_arrive(&b[5]);
+          if (lane == 0) umma::mbar_arrive(&b[6 + a]);
         }
         float g[8][5];
 #pragma unroll
@@ -331,7 +397,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
             a0 = fmaf(g[u][1], wvv, fmaf(geo.x, tvs, a0));
             a1 = fmaf(g[u][2], wvv, fmaf(geo.y, tvs, a1));
             a2 = fmaf(g[u][3], wvv, fmaf(geo.z, tvs, a2));
-            for (int nf = tf[slot]; nf > 0; --nf) flush();
+            for (int nf = tf[slot]; nf > 0 && r < R.r1; --nf) flush();
           }
         }
       }
@@ -345,7 +411,8 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
   // the MMAs of every stream's last issued tile have completed before TMEM is released
   if (warp == 2 && lane == 0)
     for (int s = 0; s < NS; ++s)
-      if (issued[s] > 0) umma::mbar_wait(&sbar[6 * s + 4], (issued[s] - 1) & 1, 200000000ull);
+      if (issued[s] > 0)
+        umma::mbar_wait(&sbar[8 * s + 4 + ((issued[s] - 1) % TB)], ((issued[s] - 1) / TB) & 1, 200000000ull);
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
@@ -643,31 +710,34 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tc(const __gr
   if (warp == 2) umma::tmem_dealloc(tmem, 512);
 }
 
-// ------------------------------------------------------------------------------ adjoint, bulk-gathered
-// Same arithmetic as k_edge_bwd_tc; the receivers' gradient rows (gsm_i: F floats, gvm_i: 3F
-// floats) of a tile's edges are brought into shared memory by cp.async.bulk copies issued by
-// the producer and completed on the tile's mbarrier, so the epilogue reads only shared memory
-// and TMEM.  Two row streams, tiles of NE edges, basis and gather buffers double-buffered.
+// ------------------------------------------------------------------------------ bulk-gathered kernels
+// Both kernels below: warps 0..NS-1 produce (one per stream: folded basis tiles, geometry,
+// row-end flags, and cp.async.bulk copies of the gathered neighbour rows into shared memory,
+// completing on the tile's mbarrier); warp 2 owns TMEM and issues the MMAs; 4 epilogue warps
+// per stream, thread f of the stream handling feature f.  Tiles of NE edges, two buffers per
+// stream, chunks of rows handed out block-cyclically (chunk_at).
+
+// Message: W = f_c (Wf rbf + bf) for the tile's edges straight from the MMA (folded basis);
+// per edge, thread f reads [phi_s | v_0 phi_vv | v_1 phi_vv | v_2 phi_vv | phi_vs] of the
+// sender (gathered rows of PHI) and accumulates the receiver's messages over its row.
 template <int NE, int NS>
-__global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
+__global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tcg(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   static_assert(NS <= 2, "one producer warp per stream");
+  constexpr int kRow = 5 * kF;   // gathered floats per edge
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = align1024(smem_raw);
-  unsigned char* sA = smem;                                          // Wf tiles
-  unsigned char* sB = sA + kWfBytes;                                 // [NS][2][2][NE x 128 B]
-  float* sG = reinterpret_cast<float*>(sB + NS * 4 * NE * 128);      // [NS][2][NE][4F]
-  int* sj = reinterpret_cast<int*>(sG + (size_t)NS * 2 * NE * 4 * kF);   // [NS][2][NE]
-  int* sfl = sj + NS * 2 * NE;                                       // [NS][2][NE]
+  unsigned char* sA = smem;                                          // Wf tiles (bias in column K)
+  unsigned char* sB = sA + kWfBytes;                                 // [NS][2][hi, lo][NE x 128 B]
+  float* sG = reinterpret_cast<float*>(sB + NS * 4 * NE * 128);      // [NS][2][NE][5F]
+  int* sfl = reinterpret_cast<int*>(sG + (size_t)NS * 2 * NE * kRow);   // [NS][2][NE]
   float4* sgeo = reinterpret_cast<float4*>(sfl + NS * 2 * NE);       // [NS][2][NE] (u, d)
-  float2* sfc = reinterpret_cast<float2*>(sgeo + NS * 2 * NE);       // [NS][2][NE] (f_c, f_c')
-  float* red = reinterpret_cast<float*>(sfc + NS * 2 * NE);          // [NS][NE][4 warps][4]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(red + NS * NE * 16);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sgeo + NS * 2 * NE);
   uint64_t* wbar = bars;
-  uint64_t* sbar = bars + 1;    // per stream: bready[2], bfree[2], tfull, tempty, esync[2]
+  uint64_t* sbar = bars + 1;    // per stream: bready[2], bfree[2], tfull[2], tempty[2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + 8 * NS);
 
-  if ((int64_t)blockIdx.x * p.rows_per_cta >= p.n) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nstreams = (int64_t)gridDim.x * NS;
 
   if (threadIdx.x == 0) {
     umma::mbar_init(wbar, 1);
@@ -678,7 +748,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
       umma::mbar_init(&b[2], 4);
       umma::mbar_init(&b[3], 4);
       umma::mbar_init(&b[4], 1);
-      umma::mbar_init(&b[5], 4);
+      umma::mbar_init(&b[5], 1);
       umma::mbar_init(&b[6], 4);
       umma::mbar_init(&b[7], 4);
     }
@@ -693,7 +763,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
   int issued[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) issued[s] = 0;
-  int gathered = 0;   // producer: tiles whose bulk copies were issued
+  int gathered = 0;
 
   if (warp < 2) {
     if (warp == 0 && lane == 0) {
@@ -704,56 +774,66 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
       const int s = warp;
       const float sig = p.rc / (float)(p.K - 1), inv2s2 = 1.0f / (2.0f * sig * sig), inv_s2 = 1.0f / (sig * sig);
       const float inv_rc = 1.0f / p.rc;
-      const StreamRange R = stream_range<NE, NS>(p, s);
-      int64_t rp = R.r0;
-      while (rp < R.r1 && p.arow[rp + 1] == R.e0) ++rp;
       uint64_t* b = sbar + 8 * s;
-      for (int it = 0; it < R.ntiles; ++it) {
+      // this stream's tiles in order: chunk k, tile t; the next tile's edge data is loaded one
+      // tile ahead so that its latency overlaps the current tile
+      int64_t k = (int64_t)blockIdx.x * NS + s;
+      Chunk C;
+      bool have = chunk_at<NE>(p, k, C);
+      int t = 0;
+      auto normalize = [&]() {
+        while (have && t >= C.ntiles) {
+          k += nstreams;
+          t = 0;
+          have = chunk_at<NE>(p, k, C);
+        }
+      };
+      float4 rn = make_float4(0.f, 0.f, 0.f, 1.f);
+      int jn = 0, en = 0, nln = 0;
+      int64_t tbn = 0;
+      auto fetch = [&]() {
+        tbn = C.e0 + (int64_t)t * NE;
+        nln = (int)((C.e1 - tbn) < NE ? (C.e1 - tbn) : NE);
+        if (lane < nln) {
+          rn = p.ar[tbn + lane];
+          jn = p.acol[tbn + lane];
+          en = p.aend[tbn + lane];
+        }
+      };
+      normalize();
+      bool cur = have;
+      if (cur) fetch();
+      for (int it = 0; cur && ok; ++it) {
+        const float4 r = rn;
+        const int jj = jn, ecnt = en, nlive = nln;
+        const int64_t tb = tbn;
+        ++t;
+        normalize();
+        cur = have;
+        if (cur) fetch();
         const int bb = it & 1;
-        const int64_t tb = R.e0 + (int64_t)it * NE;
-        const int nlive = (int)((R.e1 - tb) < NE ? (R.e1 - tb) : NE);
-        // geometry and basis first: they need no buffer, so their loads overlap the wait
-        const int k0 = lane;
-        float rb[kKPad], drb[kKPad];
-        int i = 0;
+        float bv[kKPad], dummy[kKPad];
         float4 geo = make_float4(0.f, 0.f, 0.f, 1.f);
-        float2 fcv = make_float2(0.f, 0.f);
-        if (k0 < nlive) {
-          const int64_t e = tb + k0;
-          const float4 r = p.ar[e];
-          i = p.acol[e];
+        if (lane < nlive) {
           const float d = r.w, id = 1.0f / d;
           geo = make_float4(r.x * id, r.y * id, r.z * id, d);
-          fcv = make_float2(0.5f * (cospif(d * inv_rc) + 1.0f), -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc));
-#pragma unroll
-          for (int k = 0; k < kKPad; ++k) {
-            const float t = d - (float)k * sig;
-            const float v = k < p.K ? expf(-t * t * inv2s2) : 0.0f;
-            rb[k] = v;
-            drb[k] = -v * t * inv_s2;
-          }
+          folded_basis<false>(d, p.K, sig, inv2s2, inv_s2, inv_rc, bv, dummy);
         } else {
 #pragma unroll
-          for (int k = 0; k < kKPad; ++k) rb[k] = drb[k] = 0.0f;
+          for (int q = 0; q < kKPad; ++q) bv[q] = 0.0f;
         }
         if (it >= 2 && !umma::mbar_wait(&b[2 + bb], ((it >> 1) - 1) & 1)) { ok = false; break; }
         const int so = (s * 2 + bb) * NE;
-        float* g = sG + (size_t)so * 4 * kF;
-        if (lane == 0) umma::mbar_expect_tx_only(&b[bb], (uint32_t)(nlive * 4 * kF * 4));
+        if (lane == 0) umma::mbar_expect_tx_only(&b[bb], (uint32_t)(nlive * kRow * 4));
         __syncwarp();
-        unsigned char* tile = sB + ((s * 2 + bb) * 2) * NE * 128;
-        if (k0 < NE) {
-          if (k0 < nlive) {
-            umma::bulk_copy_g2s(g + (size_t)k0 * 4 * kF, p.Gsm + (int64_t)i * kF, kF * 4, &b[bb]);
-            umma::bulk_copy_g2s(g + (size_t)k0 * 4 * kF + kF, p.Gvm + (int64_t)i * 3 * kF, 3 * kF * 4, &b[bb]);
-          }
-          store_basis_row(tile, k0, rb);
-          store_basis_row(tile + NE * 128, k0, drb);
-          sgeo[so + k0] = geo;
-          sfc[so + k0] = fcv;
+        if (lane < NE) {
+          if (lane < nlive)
+            umma::bulk_copy_g2s(sG + (size_t)(so + lane) * kRow, p.PHI + (int64_t)jj * 6 * kF, kRow * 4, &b[bb]);
+          store_basis_row_split(sB + (s * 2 + bb) * 2 * NE * 128, sB + ((s * 2 + bb) * 2 + 1) * NE * 128, lane, bv);
+          sgeo[so + lane] = geo;
+          sfl[so + lane] = lane < nlive ? ecnt : 0;
         }
         gathered = it + 1;
-        mark_row_ends_warp(lane, sfl + so, NE, tb, R.r1, p.arow, rp);
         umma::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&b[bb]);
@@ -763,208 +843,583 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
     if (lane == 0) {
       if (!umma::mbar_wait(wbar, 0)) ok = false;
       const uint32_t idesc = umma::idesc_bf16_m128(NE);
-      int nt[NS], maxt = 0;
+      int64_t k[NS];
+      int t[NS], it[NS];
+      bool have[NS];
+      Chunk C[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        nt[s] = stream_range<NE, NS>(p, s).ntiles;
-        maxt = nt[s] > maxt ? nt[s] : maxt;
+        k[s] = (int64_t)blockIdx.x * NS + s;
+        t[s] = 0;
+        it[s] = 0;
+        have[s] = chunk_at<NE>(p, k[s], C[s]);
       }
-      for (int it = 0; ok && it < maxt; ++it) {
+      // issue for whichever stream has its next tile ready (non-blocking probes), so that a
+      // late tile of one stream does not hold back the other; a stall of more than 2 s without
+      // progress gives up with a timeout
+      bool any = true;
+      uint32_t idle = 0;
+      uint64_t t_idle = 0;
+      while (ok && any) {
+        any = false;
+        bool progressed = false;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-          if (it >= nt[s]) continue;
-          uint64_t* b = sbar + 8 * s;
-          const int bb = it & 1;
-          if (!umma::mbar_wait(&b[bb], (it >> 1) & 1)) { ok = false; break; }
-          if (it >= 1 && !umma::mbar_wait(&b[5], (it - 1) & 1)) { ok = false; break; }
-          umma::fence_after();
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t bbase = umma::smem_u32(sB + ((s * 2 + bb) * 2 + h) * NE * 128);
-#pragma unroll
-            for (int m = 0; m < 3; ++m)
-#pragma unroll
-              for (int k = 0; k < 2; ++k)
-                umma::mma_bf16(tmem + (uint32_t)(s * 6 * NE + (3 * h + m) * NE),
-                               umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * k),
-                               umma::desc_sw128(bbase + 32u * k), idesc, k > 0);
+          while (have[s] && t[s] >= C[s].ntiles) {
+            k[s] += nstreams;
+            t[s] = 0;
+            have[s] = chunk_at<NE>(p, k[s], C[s]);
           }
-          umma::mma_commit(&b[4]);
-          ++issued[s];
+          if (!have[s]) continue;
+          any = true;
+          uint64_t* b = sbar + 8 * s;
+          const int bb = it[s] & 1;
+          if (!umma::mbar_test(&b[bb], (it[s] / 2) & 1)) continue;
+          if (it[s] >= 2 && !umma::mbar_test(&b[6 + bb], ((it[s] >> 1) - 1) & 1)) continue;
+          progressed = true;
+          umma::fence_after();
+          const uint32_t bbase = umma::smem_u32(sB + (s * 2 + bb) * 2 * NE * 128);
+#pragma unroll
+          for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)   // k-halves of the hi tile, then of the lo tile
+              umma::mma_bf16(tmem + (uint32_t)((s * 2 + bb) * 3 * NE + m * NE),
+                             umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * (kk & 1)),
+                             umma::desc_sw128(bbase + (uint32_t)(kk >> 1) * NE * 128 + 32u * (kk & 1)), idesc, kk > 0);
+          umma::mma_commit(&b[4 + bb]);
+          issued[s] = ++it[s];
+          ++t[s];
+        }
+        if (any && !progressed) {
+          if (idle++ == 0) t_idle = umma::globaltimer();
+          else if ((idle & 255) == 0 && umma::globaltimer() - t_idle > 2000000000ull) ok = false;
+        } else {
+          idle = 0;
         }
       }
     }
   } else {
     const int s = (warp - 3) >> 2;
     const int q = warp & 3, f = q * 32 + lane;
-    const StreamRange R = stream_range<NE, NS>(p, s);
     uint64_t* b = sbar + 8 * s;
-    const float bs = p.bf[f], bvv = p.bf[kF + f], bvs = p.bf[2 * kF + f];
-    int64_t r = R.r0;
-    float cur[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, nxt[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    auto fetch = [&](int64_t row, float (&o)[5]) {
-      if (row < R.r1) {
-        const float* pj = p.PHI + row * 6 * kF + f;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) o[k] = __ldg(pj + k * kF);
-      }
-    };
-    float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
-    auto flush = [&]() {
-      float* o = p.GPHI + r * 5 * kF;
-      o[f] = gps; o[kF + f] = gy0; o[2 * kF + f] = gy1; o[3 * kF + f] = gy2; o[4 * kF + f] = gpvs;
-      gps = gy0 = gy1 = gy2 = gpvs = 0.f;
-      ++r;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) cur[k] = nxt[k];
-      fetch(r + 1, nxt);
-    };
-    fetch(r, cur);
-    fetch(r + 1, nxt);
-    while (r < R.r1 && p.arow[r + 1] == R.e0) flush();
-    for (int it = 0; it < R.ntiles; ++it) {
-      const int bb = it & 1;
-      if (!umma::mbar_wait(&b[4], it & 1)) { ok = false; break; }
-      // the tile's gather phase completed before the MMA thread issued it; waiting on it here
-      // returns at once and makes the bulk-copied rows visible to this thread
-      if (!umma::mbar_wait(&b[bb], (it >> 1) & 1)) { ok = false; break; }
-      umma::fence_after();
-      const int64_t tb = R.e0 + (int64_t)it * NE;
-      const int nlive = (int)((R.e1 - tb) < NE ? (R.e1 - tb) : NE);
-      const int so = (s * 2 + bb) * NE;
-      const int* tf = sfl + so;
-      const float4* tg = sgeo + so;
-      const float2* tc = sfc + so;
-      float* tG = sG + (size_t)so * 4 * kF + f;   // this thread's feature in each gathered row
-      // lane 8k of warp q writes edge 4q + k of the tile; its previous value is read now
-      const int hslot = f >> 3;
-      float4 hold = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (p.accumulate && (lane & 7) == 0 && hslot < nlive) hold = p.hedge[tb + hslot];
-#pragma unroll 1
-      for (int c = 0; c < NE / 8; ++c) {
-        float W[6][8];
-        umma::tmem_ld8x6(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * 6 * NE + c * 8), NE, W);
-        if (c == NE / 8 - 1) {
-          umma::fence_before();
-          __syncwarp();
-          if (lane == 0) umma::mbar_arrive(&b[5]);
+    int it = 0;
+    Chunk C;
+    for (int64_t k = (int64_t)blockIdx.x * NS + s; ok && chunk_at<NE>(p, k, C); k += nstreams) {
+      int64_t r = C.r0;
+      float as = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      // residual stream of the current row, loaded one row ahead
+      float rs = 0.f, rv0 = 0.f, rv1 = 0.f, rv2 = 0.f;
+      auto fetch = [&](int64_t row) {
+        if (row < C.r1) {
+          rs = __ldg(p.S + row * kF + f);
+          const float* v = p.V + row * 3 * kF + f;
+          rv0 = __ldg(v); rv1 = __ldg(v + kF); rv2 = __ldg(v + 2 * kF);
         }
-        // Per edge: accumulate the row's phi gradients, and overwrite this thread's gathered
-        // gradients in place with its partials of (dU/dd, dU/du) for the reduction over features.
-        auto edge = [&](int u, int slot) {
-          float* gg = tG + (size_t)slot * 4 * kF;
-          const float gs = gg[0], gv0 = gg[kF], gv1 = gg[2 * kF], gv2 = gg[3 * kF];
-          const float4 geo = tg[slot];
-          const float2 fcv = tc[slot];
-          const float ws = W[0][u] + bs, wvv = W[1][u] + bvv, wvs = W[2][u] + bvs;
-          const float fc = fcv.x, dfc = fcv.y;
-          const float Ws = ws * fc, Wvv = wvv * fc, Wvs = wvs * fc;
-          gps = fmaf(gs, Ws, gps);
-          gy0 = fmaf(gv0, Wvv, gy0);
-          gy1 = fmaf(gv1, Wvv, gy1);
-          gy2 = fmaf(gv2, Wvv, gy2);
-          const float qv = -(gv0 * geo.x + gv1 * geo.y + gv2 * geo.z);
-          gpvs = fmaf(qv, Wvs, gpvs);
-          const float gWs = gs * cur[0], gWvv = gv0 * cur[1] + gv1 * cur[2] + gv2 * cur[3], gWvs = qv * cur[4];
-          const float tv = cur[4] * Wvs;
-          gg[0] = fc * (gWs * W[3][u] + gWvv * W[4][u] + gWvs * W[5][u]) + dfc * (gWs * ws + gWvv * wvv + gWvs * wvs);
-          gg[kF] = gv0 * tv;
-          gg[2 * kF] = gv1 * tv;
-          gg[3 * kF] = gv2 * tv;
-        };
-        const int4 fa = *reinterpret_cast<const int4*>(tf + c * 8), fb = *reinterpret_cast<const int4*>(tf + c * 8 + 4);
-        if ((fa.x | fa.y | fa.z | fa.w | fb.x | fb.y | fb.z | fb.w) == 0 && c * 8 + 8 <= nlive) {
-          // no row ends in these eight edges: straight-line code the compiler can interleave
+      };
+      auto flush = [&]() {
+        const int64_t i = r;
+        const float v0 = rv0 + a0, v1 = rv1 + a1, v2 = rv2 + a2;
+        p.SM[i * kF + f] = rs + as;
+        float* vm = p.VM + i * 3 * kF + f;
+        vm[0] = v0; vm[kF] = v1; vm[2 * kF] = v2;
+        if (p.VMb) {
+          bf16* vb = p.VMb + i * 3 * kF + f;
+          vb[0] = __float2bfloat16_rn(v0); vb[kF] = __float2bfloat16_rn(v1); vb[2 * kF] = __float2bfloat16_rn(v2);
+        }
+        as = a0 = a1 = a2 = 0.f;
+        ++r;
+        fetch(r);
+      };
+      fetch(r);
+      while (r < C.r1 && p.arow[r + 1] == C.e0) flush();
+      for (int t = 0; t < C.ntiles; ++t, ++it) {
+        const int bb = it & 1;
+        if (!umma::mbar_wait(&b[4 + bb], (it >> 1) & 1)) { ok = false; break; }
+        if (!umma::mbar_wait(&b[bb], (it >> 1) & 1)) { ok = false; break; }   // gathered rows visible
+        umma::fence_after();
+        const int64_t tb = C.e0 + (int64_t)t * NE;
+        const int nlive = (int)((C.e1 - tb) < NE ? (C.e1 - tb) : NE);
+        const int so = (s * 2 + bb) * NE;
+        const int* tf = sfl + so;
+        const float4* tg = sgeo + so;
+        const float* tG = sG + (size_t)so * kRow + f;
+#pragma unroll 1
+        for (int c = 0; c < NE / 8; ++c) {
+          float W[3][8];
+          const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((s * 2 + bb) * 3 * NE + c * 8);
+          umma::tmem_ld8(ta, W[0]);
+          umma::tmem_ld8(ta + NE, W[1]);
+          umma::tmem_ld8(ta + 2 * NE, W[2]);
+          if (c == NE / 8 - 1) {
+            umma::fence_before();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&b[6 + bb]);
+          }
+          auto edge = [&](int u, int slot) {
+            const float* gg = tG + (size_t)slot * kRow;
+            const float4 geo = tg[slot];
+            as = fmaf(gg[0], W[0][u], as);
+            const float tvs = gg[4 * kF] * W[2][u];
+            a0 = fmaf(gg[kF], W[1][u], fmaf(geo.x, tvs, a0));
+            a1 = fmaf(gg[2 * kF], W[1][u], fmaf(geo.y, tvs, a1));
+            a2 = fmaf(gg[3 * kF], W[1][u], fmaf(geo.z, tvs, a2));
+          };
+          const int4 fa = *reinterpret_cast<const int4*>(tf + c * 8), fb = *reinterpret_cast<const int4*>(tf + c * 8 + 4);
+          if ((fa.x | fa.y | fa.z | fa.w | fb.x | fb.y | fb.z | fb.w) == 0 && c * 8 + 8 <= nlive) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) edge(u, c * 8 + u);
-        } else {
+            for (int u = 0; u < 8; ++u) edge(u, c * 8 + u);
+          } else {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int slot = c * 8 + u;
-            if (slot < nlive) {
-              edge(u, slot);
-              for (int nf = tf[slot]; nf > 0; --nf) flush();
+            for (int u = 0; u < 8; ++u) {
+              const int slot = c * 8 + u;
+              if (slot < nlive) {
+                edge(u, slot);
+                for (int nf = tf[slot]; nf > 0 && r < C.r1; --nf) flush();
+              }
             }
           }
         }
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&b[2 + bb]);
       }
-      __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&b[6]);
-      if (!umma::mbar_wait(&b[6], it & 1)) { ok = false; break; }
-      {
-        // Reduction over the F features: thread f sums half (h) of component `comp` of edge
-        // `slot`, starting at a lane-dependent rotation so that a quarter-warp's 16-byte reads
-        // fall in distinct banks; the two halves combine across lanes 2k, 2k+1, and lane 8k then
-        // holds the four components of edge 4q + k.
-        const int o = f >> 1, slot = o >> 2, comp = o & 3, h = f & 1;
-        float acc = 0.f;
-        if (slot < nlive) {
-          const float* base = sG + (size_t)so * 4 * kF + (size_t)slot * 4 * kF + comp * kF + h * 64;
-          float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float4 v = *reinterpret_cast<const float4*>(base + ((4 * i + 4 * lane) & 63));
-            a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
-          }
-          acc = (a0 + a1) + (a2 + a3);
-        }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        const float g0 = __shfl_down_sync(0xffffffffu, acc, 2);
-        const float g1 = __shfl_down_sync(0xffffffffu, acc, 4);
-        const float g2 = __shfl_down_sync(0xffffffffu, acc, 6);
-        if ((lane & 7) == 0 && slot < nlive) {
-          const float pd = acc;
-          const float4 geo = tg[slot];
-          const float ux = -geo.x, uy = -geo.y, uz = -geo.z, id = 1.0f / geo.w;
-          const float gdu = g0 * ux + g1 * uy + g2 * uz;
-          float4 hv = make_float4(pd * ux + (g0 - gdu * ux) * id, pd * uy + (g1 - gdu * uy) * id,
-                                  pd * uz + (g2 - gdu * uz) * id, 0.f);
-          hv.x += hold.x; hv.y += hold.y; hv.z += hold.z;
-          p.hedge[tb + slot] = hv;
-        }
-      }
-      __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&b[2 + bb]);
+      if (!ok) break;
+      while (r < C.r1) flush();
     }
-    if (ok)
-      while (r < R.r1) flush();
   }
   if (!ok) atomicOr(p.status, (int)ST_TIMEOUT);
   if (warp < NS && lane == 0) {
-    // the bulk copies of the last two tiles this producer issued have landed before the CTA
-    // exits (in a normal run both phases completed long ago and the waits return at once)
+    // the bulk copies of the last two tiles this producer issued have landed before exit
     for (int t = gathered - 2; t < gathered; ++t)
       if (t >= 0) umma::mbar_wait(&sbar[8 * warp + (t & 1)], (t >> 1) & 1, 200000000ull);
   }
   if (warp == 2 && lane == 0)
     for (int s = 0; s < NS; ++s)
-      if (issued[s] > 0) umma::mbar_wait(&sbar[8 * s + 4], (issued[s] - 1) & 1, 200000000ull);
+      if (issued[s] > 0)
+        umma::mbar_wait(&sbar[8 * s + 4 + ((issued[s] - 1) & 1)], ((issued[s] - 1) >> 1) & 1, 200000000ull);
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
   if (warp == 2) umma::tmem_dealloc(tmem, 256);
 }
 
+// Adjoint: the MMA yields the filter and its distance derivative per edge (FOLD: with f_c and
+// the bias folded into the basis, W and dW/dd themselves; otherwise Wf rbf and Wf rbf', the
+// bias and f_c applied in FP32 by the epilogue); the receivers' gradient rows (gsm_i: F floats, gvm_i: 3F floats) are gathered by bulk copies.
+// Thread f accumulates the row's phi gradients and overwrites its own feature of the gathered
+// row with its partials of (dU/dd, dU/du); after a stream barrier the partials are reduced over
+// the F features from shared memory and turned into hedge[e].
+template <int NE, int NS, bool FOLD, bool SPLIT, int NBUF = 2>
+__global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
+  static_assert(NS <= 2, "one producer warp per stream");
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = align1024(smem_raw);
+  unsigned char* sA = smem;                                          // Wf tiles (bias in column K)
+  // per buffer one (or, SPLIT, a hi and a lo) operand of 2 NE rows: the basis of the tile's
+  // edges in rows 0..NE-1 and their derivative basis in rows NE..2NE-1, so that one MMA per
+  // channel block yields [W | dW/dd] as 2 NE columns
+  constexpr int NB = SPLIT ? 2 : 1;
+  static_assert(NS * 2 * 6 * NE <= 512, "TMEM columns");
+  static_assert(NE % 8 == 0 && NBUF >= 2 && NBUF <= 4, "tile shape");
+  unsigned char* sB = sA + kWfBytes;                                 // [NS][NBUF][NB][2 NE x 128 B]
+  float* sG = reinterpret_cast<float*>(sB + NS * NBUF * NB * 2 * NE * 128);   // [NS][NBUF][NE][4F]
+  int* sfl = reinterpret_cast<int*>(sG + (size_t)NS * NBUF * NE * 4 * kF);   // [NS][NBUF][NE]
+  float4* sgeo = reinterpret_cast<float4*>(sfl + NS * NBUF * NE);    // [NS][NBUF][NE] (u, d)
+  float2* sfc = reinterpret_cast<float2*>(sgeo + NS * NBUF * NE);    // [NS][NBUF][NE] (f_c, f_c'), !FOLD
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sfc + NS * NBUF * NE);
+  uint64_t* wbar = bars;
+  // per stream: bready[4], bfree[4] (NBUF used), tfull[2], tempty[2], esync
+  constexpr int kBars = 13;
+  uint64_t* sbar = bars + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + kBars * NS);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nstreams = (int64_t)gridDim.x * NS;
+
+  if (threadIdx.x == 0) {
+    umma::mbar_init(wbar, 1);
+    for (int s = 0; s < NS; ++s) {
+      uint64_t* b = sbar + kBars * s;
+      for (int x = 0; x < 4; ++x) {
+        umma::mbar_init(&b[x], 1);       // bready
+        umma::mbar_init(&b[4 + x], 4);   // bfree
+      }
+      umma::mbar_init(&b[8], 1);         // tfull
+      umma::mbar_init(&b[9], 1);
+      umma::mbar_init(&b[10], 4);        // tempty
+      umma::mbar_init(&b[11], 4);
+      umma::mbar_init(&b[12], 4);        // esync
+    }
+    umma::mbar_fence_init();
+  }
+  if (warp == 2) umma::tmem_alloc(tmem_slot, 512);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  int issued[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) issued[s] = 0;
+  int gathered = 0;
+
+  if (warp < 2) {
+    if (warp == 0 && lane == 0) {
+      umma::mbar_expect_tx(wbar, kWfBytes);
+      for (int m = 0; m < 3; ++m) umma::tma_load_2d(sA + m * kWfTileBytes, &tmWf, 0, m * 128, wbar);
+    }
+    if (warp < NS) {
+      const int s = warp;
+      const float sig = p.rc / (float)(p.K - 1), inv2s2 = 1.0f / (2.0f * sig * sig), inv_s2 = 1.0f / (sig * sig);
+      const float inv_rc = 1.0f / p.rc;
+      uint64_t* b = sbar + kBars * s;
+      // this stream's tiles in order: chunk k, tile t; the next tile's edge data is loaded one
+      // tile ahead so that its latency overlaps the current tile
+      int64_t k = (int64_t)blockIdx.x * NS + s;
+      Chunk C;
+      bool have = chunk_at<NE>(p, k, C);
+      int t = 0;
+      auto normalize = [&]() {
+        while (have && t >= C.ntiles) {
+          k += nstreams;
+          t = 0;
+          have = chunk_at<NE>(p, k, C);
+        }
+      };
+      float4 rn = make_float4(0.f, 0.f, 0.f, 1.f);
+      int jn = 0, en = 0, nln = 0;
+      int64_t tbn = 0;
+      auto fetch = [&]() {
+        tbn = C.e0 + (int64_t)t * NE;
+        nln = (int)((C.e1 - tbn) < NE ? (C.e1 - tbn) : NE);
+        if (lane < nln) {
+          rn = p.ar[tbn + lane];
+          jn = p.acol[tbn + lane];
+          en = p.aend[tbn + lane];
+        }
+      };
+      normalize();
+      bool cur = have;
+      if (cur) fetch();
+      for (int it = 0; cur && ok; ++it) {
+        const float4 r = rn;
+        const int jj = jn, ecnt = en, nlive = nln;
+        const int64_t tb = tbn;
+        ++t;
+        normalize();
+        cur = have;
+        if (cur) fetch();
+        const int bb = it % NBUF;
+        float bv[kKPad], dbv[kKPad];
+        float4 geo = make_float4(0.f, 0.f, 0.f, 1.f);
+        float2 fcv = make_float2(0.f, 0.f);
+        if (lane < nlive) {
+          const float d = r.w, id = 1.0f / d;
+          geo = make_float4(r.x * id, r.y * id, r.z * id, d);
+          if (FOLD) {
+            folded_basis<true>(d, p.K, sig, inv2s2, inv_s2, inv_rc, bv, dbv);
+          } else {
+            fcv = make_float2(0.5f * (cospif(d * inv_rc) + 1.0f), -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc));
+#pragma unroll
+            for (int q = 0; q < kKPad; ++q) {
+              const float tq = d - (float)q * sig;
+              const float v = q < p.K ? expf(-tq * tq * inv2s2) : 0.0f;
+              bv[q] = v;
+              dbv[q] = -v * tq * inv_s2;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < kKPad; ++q) bv[q] = dbv[q] = 0.0f;
+        }
+        if (it >= NBUF && !umma::mbar_wait(&b[4 + bb], ((it / NBUF) - 1) & 1)) { ok = false; break; }
+        const int so = (s * NBUF + bb) * NE;
+        float* g = sG + (size_t)so * 4 * kF;
+        if (lane == 0) umma::mbar_expect_tx_only(&b[bb], (uint32_t)(nlive * 4 * kF * 4));
+        __syncwarp();
+        unsigned char* tile = sB + (s * NBUF + bb) * NB * 2 * NE * 128;
+        if (lane < NE) {
+          if (lane < nlive) {
+            umma::bulk_copy_g2s(g + (size_t)lane * 4 * kF, p.Gsm + (int64_t)jj * kF, kF * 4, &b[bb]);
+            umma::bulk_copy_g2s(g + (size_t)lane * 4 * kF + kF, p.Gvm + (int64_t)jj * 3 * kF, 3 * kF * 4, &b[bb]);
+          }
+          if (SPLIT) {
+            store_basis_row_split(tile, tile + 2 * NE * 128, lane, bv);
+            store_basis_row_split(tile, tile + 2 * NE * 128, NE + lane, dbv);
+          } else {
+            store_basis_row(tile, lane, bv);
+            store_basis_row(tile, NE + lane, dbv);
+          }
+          sgeo[so + lane] = geo;
+          if (!FOLD) sfc[so + lane] = fcv;
+          sfl[so + lane] = lane < nlive ? ecnt : 0;
+        }
+        gathered = it + 1;
+        umma::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&b[bb]);
+      }
+    }
+  } else if (warp == 2) {
+    if (lane == 0) {
+      if (!umma::mbar_wait(wbar, 0)) ok = false;
+      const uint32_t idesc = umma::idesc_bf16_m128(2 * NE);
+      int64_t k[NS];
+      int t[NS], it[NS];
+      bool have[NS];
+      Chunk C[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        k[s] = (int64_t)blockIdx.x * NS + s;
+        t[s] = 0;
+        it[s] = 0;
+        have[s] = chunk_at<NE>(p, k[s], C[s]);
+      }
+      // issue for whichever stream has its next tile ready (non-blocking probes), so that a
+      // late tile of one stream does not hold back the other; a stall of more than 2 s without
+      // progress gives up with a timeout
+      bool any = true;
+      uint32_t idle = 0;
+      uint64_t t_idle = 0;
+      while (ok && any) {
+        any = false;
+        bool progressed = false;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          while (have[s] && t[s] >= C[s].ntiles) {
+            k[s] += nstreams;
+            t[s] = 0;
+            have[s] = chunk_at<NE>(p, k[s], C[s]);
+          }
+          if (!have[s]) continue;
+          any = true;
+          uint64_t* b = sbar + kBars * s;
+          const int bb = it[s] % NBUF, a = it[s] & 1;
+          if (!umma::mbar_test(&b[bb], (it[s] / NBUF) & 1)) continue;
+          if (it[s] >= 2 && !umma::mbar_test(&b[10 + a], ((it[s] >> 1) - 1) & 1)) continue;
+          progressed = true;
+          umma::fence_after();
+          const uint32_t bbase = umma::smem_u32(sB + (s * NBUF + bb) * NB * 2 * NE * 128);
+#pragma unroll
+          for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int kk = 0; kk < 2 * NB; ++kk)   // k-halves of the hi operand[, then of the lo one]
+              umma::mma_bf16(tmem + (uint32_t)((s * 2 + a) * 6 * NE + m * 2 * NE),
+                             umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * (kk & 1)),
+                             umma::desc_sw128(bbase + (uint32_t)(kk >> 1) * 2 * NE * 128 + 32u * (kk & 1)), idesc, kk > 0);
+          umma::mma_commit(&b[8 + a]);
+          issued[s] = ++it[s];
+          ++t[s];
+        }
+        if (any && !progressed) {
+          if (idle++ == 0) t_idle = umma::globaltimer();
+          else if ((idle & 255) == 0 && umma::globaltimer() - t_idle > 2000000000ull) ok = false;
+        } else {
+          idle = 0;
+        }
+      }
+    }
+  } else {
+    const int s = (warp - 3) >> 2;
+    const int q = warp & 3, f = q * 32 + lane;
+    uint64_t* b = sbar + kBars * s;
+    const float bs = FOLD ? 0.f : p.bf[f], bvv = FOLD ? 0.f : p.bf[kF + f], bvs = FOLD ? 0.f : p.bf[2 * kF + f];
+    int it = 0;
+    Chunk C;
+    for (int64_t k = (int64_t)blockIdx.x * NS + s; ok && chunk_at<NE>(p, k, C); k += nstreams) {
+      int64_t r = C.r0;
+      float cur[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, nxt[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      auto fetch = [&](int64_t row, float (&o)[5]) {
+        if (row < C.r1) {
+          const float* pj = p.PHI + row * 6 * kF + f;
+#pragma unroll
+          for (int kk = 0; kk < 5; ++kk) o[kk] = __ldg(pj + kk * kF);
+        }
+      };
+      float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
+      auto flush = [&]() {
+        float* o = p.GPHI + r * 5 * kF;
+        o[f] = gps; o[kF + f] = gy0; o[2 * kF + f] = gy1; o[3 * kF + f] = gy2; o[4 * kF + f] = gpvs;
+        gps = gy0 = gy1 = gy2 = gpvs = 0.f;
+        ++r;
+#pragma unroll
+        for (int kk = 0; kk < 5; ++kk) cur[kk] = nxt[kk];
+        fetch(r + 1, nxt);
+      };
+      fetch(r, cur);
+      fetch(r + 1, nxt);
+      while (r < C.r1 && p.arow[r + 1] == C.e0) flush();
+      for (int t = 0; t < C.ntiles; ++t, ++it) {
+        const int bb = it % NBUF, a = it & 1;
+        if (!umma::mbar_wait(&b[8 + a], (it >> 1) & 1)) { ok = false; break; }
+        if (!umma::mbar_wait(&b[bb], (it / NBUF) & 1)) { ok = false; break; }   // gathered rows visible
+        umma::fence_after();
+        const int64_t tb = C.e0 + (int64_t)t * NE;
+        const int nlive = (int)((C.e1 - tb) < NE ? (C.e1 - tb) : NE);
+        const int so = (s * NBUF + bb) * NE;
+        const int* tf = sfl + so;
+        const float4* tg = sgeo + so;
+        const float2* tc = sfc + so;
+        float* tG = sG + (size_t)so * 4 * kF + f;   // this thread's feature in each gathered row
+        // lane 8k of warp q writes edge 4q + k of the tile; its previous value is read now
+        const int hslot = f >> 3;
+        float4 hold = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p.accumulate && (lane & 7) == 0 && hslot < nlive) hold = p.hedge[tb + hslot];
+#pragma unroll 1
+        for (int c = 0; c < NE / 8; ++c) {
+          // column groups at stride NE: W_s, dW_s, W_vv, dW_vv, W_vs, dW_vs
+          float W[6][8];
+          umma::tmem_ld8x6(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((s * 2 + a) * 6 * NE + c * 8), NE, W);
+          if (c == NE / 8 - 1) {
+            umma::fence_before();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&b[10 + a]);
+          }
+          // per edge: accumulate the row's phi gradients; overwrite this thread's gathered
+          // gradients in place with its partials of (dU/dd, dU/du)
+          auto edge = [&](int u, int slot) {
+            float* gg = tG + (size_t)slot * 4 * kF;
+            const float gs = gg[0], gv0 = gg[kF], gv1 = gg[2 * kF], gv2 = gg[3 * kF];
+            const float4 geo = tg[slot];
+            float Ws, Wvv, Wvs, dWs, dWvv, dWvs;   // filter and its distance derivative, f_c included
+            if (FOLD) {
+              Ws = W[0][u]; Wvv = W[2][u]; Wvs = W[4][u];
+              dWs = W[1][u]; dWvv = W[3][u]; dWvs = W[5][u];
+            } else {
+              const float2 fcv = tc[slot];
+              const float ws = W[0][u] + bs, wvv = W[2][u] + bvv, wvs = W[4][u] + bvs;
+              Ws = ws * fcv.x; Wvv = wvv * fcv.x; Wvs = wvs * fcv.x;
+              dWs = fcv.x * W[1][u] + fcv.y * ws;
+              dWvv = fcv.x * W[3][u] + fcv.y * wvv;
+              dWvs = fcv.x * W[5][u] + fcv.y * wvs;
+            }
+            gps = fmaf(gs, Ws, gps);
+            gy0 = fmaf(gv0, Wvv, gy0);
+            gy1 = fmaf(gv1, Wvv, gy1);
+            gy2 = fmaf(gv2, Wvv, gy2);
+            const float qv = -(gv0 * geo.x + gv1 * geo.y + gv2 * geo.z);
+            gpvs = fmaf(qv, Wvs, gpvs);
+            const float gWs = gs * cur[0], gWvv = gv0 * cur[1] + gv1 * cur[2] + gv2 * cur[3], gWvs = qv * cur[4];
+            const float tv = cur[4] * Wvs;
+            gg[0] = gWs * dWs + gWvv * dWvv + gWvs * dWvs;
+            gg[kF] = gv0 * tv;
+            gg[2 * kF] = gv1 * tv;
+            gg[3 * kF] = gv2 * tv;
+          };
+          const int4 fa = *reinterpret_cast<const int4*>(tf + c * 8), fb = *reinterpret_cast<const int4*>(tf + c * 8 + 4);
+          if ((fa.x | fa.y | fa.z | fa.w | fb.x | fb.y | fb.z | fb.w) == 0 && c * 8 + 8 <= nlive) {
+            // no row ends in these eight edges: straight-line code the compiler can interleave
+#pragma unroll
+            for (int u = 0; u < 8; ++u) edge(u, c * 8 + u);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int slot = c * 8 + u;
+              if (slot < nlive) {
+                edge(u, slot);
+                for (int nf = tf[slot]; nf > 0 && r < C.r1; --nf) flush();
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&b[12]);
+        if (!umma::mbar_wait(&b[12], it & 1)) { ok = false; break; }
+        {
+          // Reduction over the F features: thread f sums half (h) of component `comp` of edge
+          // `slot`, starting at a lane-dependent rotation so that a quarter-warp's 16-byte reads
+          // fall in distinct banks; the two halves combine across lanes 2k, 2k+1, and lane 8k
+          // then holds the four components of edge 4q + k.
+          const int o = f >> 1, slot = o >> 2, comp = o & 3, h = f & 1;
+          float acc = 0.f;
+          if (slot < nlive) {
+            const float* base = sG + (size_t)so * 4 * kF + (size_t)slot * 4 * kF + comp * kF + h * 64;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+            for (int ii = 0; ii < 16; ++ii) {
+              const float4 v = *reinterpret_cast<const float4*>(base + ((4 * ii + 4 * lane) & 63));
+              a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
+            }
+            acc = (a0 + a1) + (a2 + a3);
+          }
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          const float g0 = __shfl_down_sync(0xffffffffu, acc, 2);
+          const float g1 = __shfl_down_sync(0xffffffffu, acc, 4);
+          const float g2 = __shfl_down_sync(0xffffffffu, acc, 6);
+          if ((lane & 7) == 0 && slot < nlive) {
+            const float pd = acc;
+            const float4 geo = tg[slot];
+            const float ux = -geo.x, uy = -geo.y, uz = -geo.z, id = 1.0f / geo.w;
+            const float gdu = g0 * ux + g1 * uy + g2 * uz;
+            float4 hv = make_float4(pd * ux + (g0 - gdu * ux) * id, pd * uy + (g1 - gdu * uy) * id,
+                                    pd * uz + (g2 - gdu * uz) * id, 0.f);
+            hv.x += hold.x; hv.y += hold.y; hv.z += hold.z;
+            p.hedge[tb + slot] = hv;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&b[4 + bb]);
+      }
+      if (!ok) break;
+      while (r < C.r1) flush();
+    }
+  }
+  if (!ok) atomicOr(p.status, (int)ST_TIMEOUT);
+  if (warp < NS && lane == 0) {
+    // the bulk copies of the last two tiles this producer issued have landed before exit
+    for (int t = gathered - NBUF; t < gathered; ++t)
+      if (t >= 0) umma::mbar_wait(&sbar[kBars * warp + (t % NBUF)], (t / NBUF) & 1, 200000000ull);
+  }
+  if (warp == 2 && lane == 0)
+    for (int s = 0; s < NS; ++s)
+      if (issued[s] > 0)
+        umma::mbar_wait(&sbar[kBars * s + 8 + ((issued[s] - 1) & 1)], ((issued[s] - 1) >> 1) & 1, 200000000ull);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  if (warp == 2) umma::tmem_dealloc(tmem, 512);
+}
+
 // ------------------------------------------------------------------------------ host side
 constexpr int kFwdNE = 32, kFwdNS = 4;   // 4 streams x 3 x 32 TMEM columns, 16 epilogue warps
+constexpr bool kFwdSplit = false;        // basis as BF16 hi + lo (two MMAs) in the message kernel
+constexpr int kFwdTB = 1;                // TMEM accumulator buffers per stream
+constexpr bool kBwgSplit = false;        // basis as BF16 hi + lo in the bulk-gathered adjoint
 constexpr int kBwdNE = 16, kBwdNS = 3;   // 3 streams x 6 x 16 TMEM columns, 12 epilogue warps
 constexpr int kBwgNE = 16, kBwgNS = 2;   // bulk-gathered adjoint: 2 streams, double-buffered tiles
+constexpr int kFwgNE = 16, kFwgNS = 2;   // bulk-gathered message kernel
+constexpr int64_t kChunkRows = 32;       // default rows per block-cyclic chunk
 
-static size_t fwd_smem() {
-  return 1024 + kWfBytes + (size_t)kFwdNS * 2 * kFwdNE * 128 + (size_t)kFwdNS * 2 * kFwdNE * (4 + 4 + 16) +
-         8 * (1 + 6 * kFwdNS) + 64;
+static size_t fwd_smem(bool split = kFwdSplit) {
+  return 1024 + kWfBytes + (size_t)kFwdNS * 2 * (split ? 2 : 1) * kFwdNE * 128 + (size_t)kFwdNS * 2 * kFwdNE * (4 + 4 + 16) +
+         8 * (1 + 8 * kFwdNS) + 64;
 }
 static size_t bwd_smem() {
   return 1024 + kWfBytes + (size_t)kBwdNS * 4 * kBwdNE * 128 + (size_t)kBwdNS * 2 * kBwdNE * (4 + 4 + 16 + 8) +
          (size_t)kBwdNS * kBwdNE * 16 * 4 + 8 * (1 + 8 * kBwdNS) + 64;
 }
 
-static size_t bwg_smem() {
-  return 1024 + kWfBytes + (size_t)kBwgNS * 4 * kBwgNE * 128 + (size_t)kBwgNS * 2 * kBwgNE * 4 * kF * 4 +
-         (size_t)kBwgNS * 2 * kBwgNE * (4 + 4 + 16 + 8) + (size_t)kBwgNS * kBwgNE * 16 * 4 + 8 * (1 + 8 * kBwgNS) + 64;
+static size_t bwg_smem(bool split = kBwgSplit, int ne = kBwgNE, int nbuf = 2) {
+  return 1024 + kWfBytes + (size_t)kBwgNS * nbuf * (split ? 2 : 1) * 2 * ne * 128 + (size_t)kBwgNS * nbuf * ne * 4 * kF * 4 +
+         (size_t)kBwgNS * nbuf * ne * (4 + 16 + 8) + 8 * (1 + 13 * kBwgNS) + 64;
+}
+static size_t fwg_smem() {
+  return 1024 + kWfBytes + (size_t)kFwgNS * 4 * kFwgNE * 128 + (size_t)kFwgNS * 2 * kFwgNE * 5 * kF * 4 +
+         (size_t)kFwgNS * 2 * kFwgNE * (4 + 16) + 8 * (1 + 8 * kFwgNS) + 64;
 }
 
-bool edge_tc_supported(int F, int K) { return F == kF && K <= kKPad && K >= 2; }
+// K < kKPad leaves basis column K free for the folded filter bias
+bool edge_tc_supported(int F, int K) { return F == kF && K < kKPad && K >= 2; }
+
+// Rows per block-cyclic chunk: the context's setting, or one contiguous range per stream (0).
+static int64_t chunk_rows_for(const ModelW& m, int64_t n, int ns) {
+  if (m.edge_chunk_rows > 0) return m.edge_chunk_rows;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t streams = (int64_t)sms * ns;
+  const int64_t r = (n + streams - 1) / streams;
+  return r > 0 ? r : 1;
+}
 
 // One CTA per SM (512 TMEM columns each), rows split evenly over the CTAs.
 static int grid_for(int64_t n, int64_t* rows_per_cta) {
@@ -980,44 +1435,74 @@ static int grid_for(int64_t n, int64_t* rows_per_cta) {
 
 int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow, const int32_t* acol,
                 const float4* ar, const float* PHI, const float* S, const float* V, float* SM, float* VM,
-                bf16* VMb, int* status) {
+                bf16* VMb, int* status, const int32_t* aend) {
   if (n == 0) return 0;
   CUtensorMap tm;
   if (!make_tmap_bf16(&tm, m.L[t].Wfb, 3 * kF, 64, 64, 128)) return -2;
   EdgeTcArgs a{};
   a.n = n; a.K = m.K; a.rc = m.rc; a.arow = arow; a.acol = acol; a.ar = ar; a.PHI = PHI; a.S = S; a.V = V;
-  a.bf = m.L[t].bf; a.SM = SM; a.VM = VM; a.VMb = VMb; a.status = status;
+  a.bf = m.L[t].bf; a.SM = SM; a.VM = VM; a.VMb = VMb; a.status = status; a.aend = aend;
   const int grid = grid_for(n, &a.rows_per_cta);
+  a.chunk_rows = chunk_rows_for(m, n, kFwgNS);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
+    cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
+    cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, true, kFwdTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(true));
+    cudaFuncSetAttribute(k_edge_fwd_tcg<kFwgNE, kFwgNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwg_smem());
     attr = true;
   }
   LaunchScope ls_(st);
-  k_edge_fwd_tc<kFwdNE, kFwdNS><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
+  if (m.tc_message_variant == 1) {
+    k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
+  } else if (m.tc_message_variant == 3) {
+    k_edge_fwd_tc<kFwdNE, kFwdNS, true, kFwdTB><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(true), st>>>(tm, a);
+  } else {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_edge_fwd_tcg<kFwgNE, kFwgNS><<<sms, 32 * (3 + 4 * kFwgNS), fwg_smem(), st>>>(tm, a);
+  }
   return 0;
 }
 
 int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
                 const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm, const float* Gvm,
-                float* GPHI, float4* hedge, int* status) {
+                float* GPHI, float4* hedge, int* status, const int32_t* aend) {
   if (n == 0) return 0;
   CUtensorMap tm;
   if (!make_tmap_bf16(&tm, m.L[t].Wfb, 3 * kF, 64, 64, 128)) return -2;
   EdgeTcArgs a{};
   a.n = n; a.K = m.K; a.rc = m.rc; a.accumulate = accumulate; a.arow = arow; a.acol = acol; a.ar = ar;
   a.PHI = PHI; a.Gsm = Gsm; a.Gvm = Gvm; a.bf = m.L[t].bf; a.GPHI = GPHI; a.hedge = hedge; a.status = status;
+  a.aend = aend;
   const int grid = grid_for(n, &a.rows_per_cta);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_edge_bwd_tc<kBwdNE, kBwdNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
-    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, true, kBwgSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(true));
+    cudaFuncSetAttribute(k_edge_bwd_tcg<8, kBwgNS, false, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(false, 8, 4));
+    cudaFuncSetAttribute(k_edge_bwd_tcg<8, kBwgNS, false, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(true, 8, 4));
     attr = true;
   }
+  a.chunk_rows = chunk_rows_for(m, n, kBwgNS);
   LaunchScope ls_(st);
-  if (m.tc_adjoint_variant == 2)
-    k_edge_bwd_tcg<kBwgNE, kBwgNS><<<grid, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
-  else
+  if (m.tc_adjoint_variant >= 2) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (m.tc_adjoint_variant == 3)
+      k_edge_bwd_tcg<kBwgNE, kBwgNS, true, kBwgSplit><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
+    else if (m.tc_adjoint_variant == 5)
+      k_edge_bwd_tcg<8, kBwgNS, false, false, 4><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(false, 8, 4), st>>>(tm, a);
+    else if (m.tc_adjoint_variant == 6)
+      k_edge_bwd_tcg<8, kBwgNS, false, true, 4><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(true, 8, 4), st>>>(tm, a);
+    else if (m.tc_adjoint_variant == 4)
+      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(true), st>>>(tm, a);
+    else
+      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
+  } else
     k_edge_bwd_tc<kBwdNE, kBwdNS><<<grid, 32 * (3 + 4 * kBwdNS), bwd_smem(), st>>>(tm, a);
   return 0;
 }

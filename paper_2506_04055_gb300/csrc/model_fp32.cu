@@ -856,7 +856,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
                                 float* const* B, __nv_bfloat16* const* Bb, bool need_grad,
                                 double* energy_partials, int n_energy_partials, float4* hedge, float* force_s,
                                 double* virial_partials, int n_virial_partials, float* e_atom, int* status,
-                                float* wstore, int64_t wstore_layer_floats) {
+                                float* wstore, int64_t wstore_layer_floats, const int32_t* aend) {
   edge_smem_setup();
   StageGuard node_stage(STG_NODE);
   const int F = m.F, T = m.T, Fh = F / 2;
@@ -882,7 +882,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     if (n > 0) {
       StageGuard sg(STG_EDGE_FWD);
       if (use_tc) {
-        bad |= edge_fwd_tc(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], status);
+        bad |= edge_fwd_tc(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], status, aend);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_FWD)
       }
@@ -925,7 +925,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
       if (use_tc_bwd) {
-        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge, status);
+        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge, status, aend);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_BWD)
       }

@@ -341,24 +341,35 @@ __global__ void k_prune_rev(int64_t n_active, const int32_t* __restrict__ vidx,
 // The active edge count lives on the device (arow[n]); launch over the Verlet capacity bound
 // given by the caller through arow's last entry is not known on the host, so the kernel is
 // launched per row instead: one warp per row walks its active edges.
+// Also writes aend[a]: 0 except on the last active edge of a non-empty row, where it is 1 plus
+// the number of empty rows that follow (the rows an edge walker completes at that edge).
 __global__ void k_prune_rev_rows(int64_t n, const int32_t* __restrict__ arow, const int32_t* __restrict__ vidx,
                                  const int32_t* __restrict__ vrev, const int32_t* __restrict__ v2a,
-                                 int32_t* __restrict__ arev) {
+                                 int32_t* __restrict__ arev, int32_t* __restrict__ aend) {
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (i >= n) return;
-  for (int a = arow[i] + lane; a < arow[i + 1]; a += 32) {
+  const int a1 = arow[i + 1];
+  for (int a = arow[i] + lane; a < a1; a += 32) {
     const int rv = vrev[vidx[a]];
     arev[a] = rv >= 0 ? v2a[rv] : -1;   // -1 is flagged by the force kernel
+    if (aend) {
+      int cnt = 0;
+      if (a == a1 - 1) {
+        cnt = 1;
+        for (int64_t r = i + 1; r < n && arow[r + 1] == a1; ++r) ++cnt;
+      }
+      aend[a] = cnt;
+    }
   }
 }
 
 void launch_prune_rev(cudaStream_t st, int64_t n, const int32_t* arow, const int32_t* vidx,
-                      const int32_t* vrev, const int32_t* v2a, int32_t* arev) {
+                      const int32_t* vrev, const int32_t* v2a, int32_t* arev, int32_t* aend) {
   if (n == 0) return;
   int64_t threads = n * 32;
   { LaunchScope ls_(st); k_prune_rev_rows<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(n, arow, vidx, vrev,
-                                                                                        v2a, arev); }
+                                                                                        v2a, arev, aend); }
 }
 
 }  // namespace ctd

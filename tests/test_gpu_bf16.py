@@ -37,7 +37,7 @@ def test_bf16_fcc4000_F128(orc):
     print(f"bf16 fcc4000: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_bf16_tensor_core_adjoint(orc, variant):
     """Each edge-adjoint variant (CUDA cores; tcgen05 filter with register or bulk-copy gathers)
     on the fcc sub-cell and a small cell."""
@@ -82,3 +82,21 @@ def test_bf16_rejects_unsupported_width():
     eng = engine()
     with pytest.raises(eng.CtdError):
         eng.Potential(32, T=1, n_species=1, precision="bf16")
+
+
+@pytest.mark.parametrize("message", [1, 2, 3])
+def test_bf16_message_variants(orc, message):
+    """Message kernel with register gathers (1) or bulk-copy gathers and the folded basis (2),
+    on the fcc sub-cell, a small water cell and a 4-species mixture with filter biases."""
+    from paper_2506_04055_gb300 import _lib
+    eng = engine()
+    cases = ((syn.fcc(10, 10, 10, jitter=0.05, seed=0), 1, 0.1), (syn.water_box(21, seed=2), 2, 0.1),
+             (syn.mixture(n_chain=30, n_water=150, seed=1), 4, 0.2))
+    for sy, S, bias in cases:
+        vals, blob = model(128, 2, S, seed=5, bias=bias)
+        with eng.Potential(128, T=2, n_species=S, precision="bf16", params=blob) as pot:
+            pot.set_option(_lib.CTD_OPT_TC_MESSAGE, message)
+            out = pot.compute(sy.species, sy.positions, sy.cell, energies=True)
+        ref = orc.painn(vals, 128, 20, 2, S, sy.species, sy.positions, sy.cell)
+        fr, er, wr = compare(out, ref, force_tol=BF16_FORCE_RMSE, e_tol=1e-2, w_tol=2e-2)
+        print(f"bf16 message{message} {sy.name}: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
