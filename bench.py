@@ -34,6 +34,12 @@ RC, SKIN, DT, TEMP = 5.0, 1.0, 1.0, 300.0
 # derivative (2 x 3K FMA) + message adjoint terms + per-edge gradient partials.
 EDGE_FWD_FLOP_PER_EF = 6 * K + 18
 EDGE_BWD_FLOP_PER_EF = 12 * K + 45
+# On the BF16 path (F = 128) the filter contractions run on the tensor pipe; the FMA pipes keep
+# the elementwise part: message 21 FLOP (bias, f_c, four message terms), adjoint 50 FLOP (bias,
+# f_c and f_c' terms, phi-gradient sums, u-projection, dU/dd and dU/du partials and their
+# reduction over the features).
+EDGE_FWD_TC_ALU_FLOP_PER_EF = 21
+EDGE_BWD_TC_ALU_FLOP_PER_EF = 50
 FP32_LANES_PER_SM, N_SM = 128, 152
 
 
@@ -320,17 +326,34 @@ def run_ours(args):
         with eng2.Potential(F, K=K, T=T, n_species=S, rc=RC, params=blob) as p2:
             st = p2.compute(sy.species, sy.positions, sy.cell, stats=True)["stats"]
         ea = st["n_active_edges"]
-        per_ef = EDGE_BWD_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_FLOP_PER_EF
-        flop = ea * F * per_ef
-        achieved = flop / (dom_ms / dom_launches / 1e3) / 1e12
+        launch_s = dom_ms / dom_launches / 1e3
         peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+        tc = head == "bf16" and F == 128 and (dom == "edge_fwd" or args.tc_adjoint != 0)
+        if tc:
+            # FMA-pipe FLOPs of the tensor-core kernel; the filter contractions (2K FLOP per
+            # edge, feature and channel, and as many again for the derivative in the adjoint)
+            # are on the tensor pipe and reported beside it against the BF16 peak
+            alu_ef = EDGE_BWD_TC_ALU_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_TC_ALU_FLOP_PER_EF
+            tensor = ea * 3 * F * 2 * K * (2 if dom == "edge_bwd" else 1)
+            kname = ("k_edge_bwd_tc" if args.tc_adjoint == 1 else "k_edge_bwd_tcg") if dom == "edge_bwd" else "k_edge_fwd_tc"
+        else:
+            alu_ef = EDGE_BWD_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_FLOP_PER_EF
+            tensor = 0
+            kname = f"k_{dom}"
+        flop = ea * F * alu_ef
+        achieved = flop / launch_s / 1e12
+        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": kernel_traffic(f"k_{dom}"),
+                    "traffic": kernel_traffic(kname),
                     "peak_source": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                    f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
                     "algorithmic_flop_per_launch": flop, "launch_ms": dom_ms / dom_launches,
                     "active_edges": ea}
+        if tensor:
+            tpk = peaks.get("bf16_tflops_sustained", 1700.0)
+            roofline["tensor_flop_per_launch"] = tensor
+            roofline["tensor_tflops"] = tensor / launch_s / 1e12
+            roofline["tensor_frac_of_bf16_sustained"] = tensor / launch_s / 1e12 / tpk
     launches = int(sum(v[1] for v in prof.values()))
     line = {
         "metric": METRIC, "value": s["value"], "unit": "atom-steps/s", "n_gpus": world,

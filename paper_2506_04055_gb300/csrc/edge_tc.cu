@@ -891,6 +891,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tcg(const __g
           ++t[s];
         }
         if (any && !progressed) {
+          __nanosleep(64);
           if (idle++ == 0) t_idle = umma::globaltimer();
           else if ((idle & 255) == 0 && umma::globaltimer() - t_idle > 2000000000ull) ok = false;
         } else {
@@ -1211,6 +1212,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
           ++t[s];
         }
         if (any && !progressed) {
+          __nanosleep(64);
           if (idle++ == 0) t_idle = umma::globaltimer();
           else if ((idle & 255) == 0 && umma::globaltimer() - t_idle > 2000000000ull) ok = false;
         } else {
