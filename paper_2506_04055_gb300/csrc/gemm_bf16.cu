@@ -1,7 +1,7 @@
 // gemm_bf16.cu -- persistent tcgen05 GEMM for the node MLPs of the BF16 path:
 //   C[M][N] = A[M][K] . W[N][K]^T   (BF16 operands, FP32 accumulation in TMEM)
 // with the same fused epilogues as the FP32 SIMT GEMM (bias, bias + SiLU, residual add,
-// multiply by SiLU').  A rows are atoms (or atom x spatial component), W is a weight matrix
+// multiply by SiLU') and one that packs the phi-MLP output into the message kernel's PHI rows.  A rows are atoms (or atom x spatial component), W is a weight matrix
 // stored [out][in], i.e. K-major, so both operands are K-major 128B-swizzled tiles.
 //
 // One CTA per SM (persistent over 128-row tiles).  Warp 0: TMA producer (the weight tile W is
@@ -170,7 +170,21 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __gr
           *reinterpret_cast<float4*>(T + lane * kTP + 4 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         __syncwarp();
         float4 bq = make_float4(0.f, 0.f, 0.f, 0.f);
-        if ((EPI == 0 || EPI == 1) && p.bias) bq = *reinterpret_cast<const float4*>(p.bias + c0 + cc);
+        if ((EPI == 0 || EPI == 1 || EPI == 4) && p.bias) bq = *reinterpret_cast<const float4*>(p.bias + c0 + cc);
+        // EPI 4 (phi packing, N = 3F): columns [phi_s | phi_vv | phi_vs]; row m of PHI (6F) gets
+        // [phi_s | v_0 phi_vv | v_1 phi_vv | v_2 phi_vv | phi_vs | phi_vv], v from aux ([n][3F])
+        const int Fb = N / 3, blk = EPI == 4 ? c0 / Fb : 0, f0 = c0 - blk * Fb + cc;
+        float4 gv[EPI == 4 ? 8 : 1][3];
+        if (EPI == 4 && blk == 1) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int64_t m = m0 + cr + 4 * j;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              gv[j][c] = m < p.M ? __ldg(reinterpret_cast<const float4*>(p.aux + m * p.ldaux + c * Fb + f0))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
         // the chunk's aux values, all loads in flight before any store
         float4 g[8];
         if (EPI == 2 || EPI == 3) {
@@ -187,7 +201,22 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __gr
           const int64_t m = m0 + r;
           float4 x = *reinterpret_cast<const float4*>(T + r * kTP + cc);
           if (m < p.M) {
-            if (EPI == 0 || EPI == 1) { x.x += bq.x; x.y += bq.y; x.z += bq.z; x.w += bq.w; }
+            if (EPI == 0 || EPI == 1 || EPI == 4) { x.x += bq.x; x.y += bq.y; x.z += bq.z; x.w += bq.w; }
+            if (EPI == 4) {
+              float* o = p.out + m * p.ldo;
+              if (blk == 0) {
+                *reinterpret_cast<float4*>(o + f0) = x;
+              } else if (blk == 2) {
+                *reinterpret_cast<float4*>(o + 4 * Fb + f0) = x;
+              } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                  *reinterpret_cast<float4*>(o + (1 + c) * Fb + f0) =
+                      make_float4(gv[j][c].x * x.x, gv[j][c].y * x.y, gv[j][c].z * x.z, gv[j][c].w * x.w);
+                *reinterpret_cast<float4*>(o + 5 * Fb + f0) = x;
+              }
+              continue;
+            }
             if (EPI == 2) { x.x += g[j].x; x.y += g[j].y; x.z += g[j].z; x.w += g[j].w; }
             if (EPI == 3) {
               x.x *= dsilu_fast(g[j].x); x.y *= dsilu_fast(g[j].y); x.z *= dsilu_fast(g[j].z); x.w *= dsilu_fast(g[j].w);
@@ -289,7 +318,7 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
   size_t smem = 1024 + b_bytes + (size_t)p.a_stages * kATileBytes + t_bytes + 256;
   // a CTA holding more than half of TMEM runs alone on its SM, so allocation never waits
   if (p.tmem_cols > 256 && smem < 120 * 1024) smem = 120 * 1024;
-  static bool attr_set[4] = {false, false, false, false};
+  static bool attr_set[5] = {false, false, false, false, false};
   if (!attr_set[EPI]) {
     cudaFuncSetAttribute(k_gemm_bf16<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set[EPI] = true;
@@ -310,6 +339,8 @@ template int gemm_bf16<1>(cudaStream_t, int64_t, int, int, const bf16*, int64_t,
 template int gemm_bf16<2>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
                           const float*, int, float*, int, bf16*, int, int*);
 template int gemm_bf16<3>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
+                          const float*, int, float*, int, bf16*, int, int*);
+template int gemm_bf16<4>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
                           const float*, int, float*, int, bf16*, int, int*);
 
 }  // namespace ctd

@@ -160,8 +160,10 @@ __global__ void k_update_pre(int64_t n, int F, float eps, const float* __restric
   const float* uv = UV + i * 3 * 2 * F;
   float v0 = uv[F + f], v1 = uv[2 * F + F + f], v2 = uv[4 * F + F + f];
   const float nv = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
-  Z[i * 2 * F + f] = SM[idx];
-  Z[i * 2 * F + F + f] = nv;
+  if (Z) {
+    Z[i * 2 * F + f] = SM[idx];
+    Z[i * 2 * F + F + f] = nv;
+  }
   if (Zb) {
     Zb[i * 2 * F + f] = __float2bfloat16_rn(SM[idx]);
     Zb[i * 2 * F + F + f] = __float2bfloat16_rn(nv);
@@ -213,9 +215,11 @@ __global__ void k_update_bwd_pre(int64_t n, int F, const float* __restrict__ GS,
     GUV[i * 6 * F + al * 2 * F + f] = gv * avv + gsp * v;
     GUV[i * 6 * F + al * 2 * F + F + f] = gsp * u;
   }
-  GA[i * 3 * F + f] = gavv;
-  GA[i * 3 * F + F + f] = gs * sp;
-  GA[i * 3 * F + 2 * F + f] = gs;
+  if (GA) {
+    GA[i * 3 * F + f] = gavv;
+    GA[i * 3 * F + F + f] = gs * sp;
+    GA[i * 3 * F + 2 * F + f] = gs;
+  }
   if (GAb) {
     GAb[i * 3 * F + f] = __float2bfloat16_rn(gavv);
     GAb[i * 3 * F + F + f] = __float2bfloat16_rn(gs * sp);
@@ -245,6 +249,54 @@ __global__ void k_update_bwd_mid(int64_t n, int F, float eps, const float* __res
   }
 }
 
+// BF16 path: the same two steps writing the BF16 operand of the U/V backward GEMM directly.
+//   pre: g_a (BF16) and the Uv half of each GUV row, gUv_a = gv'_a a_vv + gs' a_sv Vv_a;
+//   mid: gsm = gs' + gz_s and the Vv half, gVv_a = gs' a_sv Uv_a + gz_n Vv_a / |Vv|.
+__global__ void k_update_bwd_pre_bf16(int64_t n, int F, const float* __restrict__ GS, const float* __restrict__ GV,
+                                      const float* __restrict__ UV, const float* __restrict__ AV,
+                                      __nv_bfloat16* __restrict__ GAb, __nv_bfloat16* __restrict__ GUVb) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  const float* uv = UV + i * 6 * F;
+  const float* a = AV + i * 3 * F;
+  const float gs = GS[idx], asv = a[F + f], avv = a[f];
+  const float gsp = gs * asv;
+  float sp = 0.0f, gavv = 0.0f;
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    const float u = uv[al * 2 * F + f], v = uv[al * 2 * F + F + f];
+    const float gv = GV[i * 3 * F + al * F + f];
+    sp += u * v;
+    gavv += gv * u;
+    GUVb[i * 6 * F + al * 2 * F + f] = __float2bfloat16_rn(gv * avv + gsp * v);
+  }
+  GAb[i * 3 * F + f] = __float2bfloat16_rn(gavv);
+  GAb[i * 3 * F + F + f] = __float2bfloat16_rn(gs * sp);
+  GAb[i * 3 * F + 2 * F + f] = __float2bfloat16_rn(gs);
+}
+
+__global__ void k_update_bwd_mid_bf16(int64_t n, int F, float eps, const float* __restrict__ GS,
+                                      const float* __restrict__ GZ, const float* __restrict__ UV,
+                                      const float* __restrict__ AV, float* __restrict__ Gsm,
+                                      __nv_bfloat16* __restrict__ GUVb) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  const float* uv = UV + i * 6 * F;
+  const float v0 = uv[F + f], v1 = uv[3 * F + f], v2 = uv[5 * F + f];
+  const float nv = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
+  const float g = GZ[i * 2 * F + F + f] / nv;
+  const float gs = GS[idx];
+  const float gsp = gs * AV[i * 3 * F + F + f];
+  Gsm[idx] = gs + GZ[i * 2 * F + f];
+  GUVb[i * 6 * F + F + f] = __float2bfloat16_rn(gsp * uv[f] + g * v0);
+  GUVb[i * 6 * F + 3 * F + f] = __float2bfloat16_rn(gsp * uv[2 * F + f] + g * v1);
+  GUVb[i * 6 * F + 5 * F + f] = __float2bfloat16_rn(gsp * uv[4 * F + f] + g * v2);
+}
+
 // Backward of PHI packing: gphi_vv = sum_a gpsi_a v_a, gv_a = gvm_a + gpsi_a phi_vv;
 // GP3 = [gphi_s | gphi_vv | gphi_vs]
 __global__ void k_phi_bwd_pre(int64_t n, int F, const float* __restrict__ GPHI, const float* __restrict__ PHI,
@@ -263,9 +315,11 @@ __global__ void k_phi_bwd_pre(int64_t n, int F, const float* __restrict__ GPHI, 
     gpvv += gpsi * V[i * 3 * F + al * F + f];
     GVn[i * 3 * F + al * F + f] = Gvm[i * 3 * F + al * F + f] + gpsi * pvv;
   }
-  GP3[i * 3 * F + f] = g[f];
-  GP3[i * 3 * F + F + f] = gpvv;
-  GP3[i * 3 * F + 2 * F + f] = g[4 * F + f];
+  if (GP3) {
+    GP3[i * 3 * F + f] = g[f];
+    GP3[i * 3 * F + F + f] = gpvv;
+    GP3[i * 3 * F + 2 * F + f] = g[4 * F + f];
+  }
   if (GP3b) {
     GP3b[i * 3 * F + f] = __float2bfloat16_rn(g[f]);
     GP3b[i * 3 * F + F + f] = __float2bfloat16_rn(gpvv);
@@ -875,8 +929,8 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     float *SM = B[B_SM0 + t], *VM = B[B_VM0 + t], *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
     float *T1 = B[B_T1], *T2 = B[B_T2];
     bad |= gemm_bf16<1>(st, n, F, F, Bb[BB_S0 + t], F, L.W1b, L.b1, nullptr, 0, H1, F, Bb[BB_A1], F, status);
-    bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, nullptr, 0, T2, 3 * F, nullptr, 0, status);
-    if (n > 0) { LaunchScope ls_(st); k_phi_pack<<<nb, kThreads, 0, st>>>(n, F, T2, V, PHI); }
+    // phi = W2 silu(.) + b2, packed into PHI by the GEMM epilogue
+    bad |= gemm_bf16<4>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, V, 3 * F, PHI, 6 * F, nullptr, 0, status);
     float* wst = (wstore && need_grad && !use_tc) ? wstore + t * wstore_layer_floats : nullptr;
 #define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], wst)
     if (n > 0) {
@@ -889,7 +943,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     }
 #undef CTD_FWD
     bad |= gemm_bf16<0>(st, 3 * n, 2 * F, F, Bb[BB_VM], F, L.UVb, nullptr, nullptr, 0, UV, 2 * F, nullptr, 0, status);
-    if (n > 0) { LaunchScope ls_(st); k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1, Bb[BB_Z]); }
+    if (n > 0) { LaunchScope ls_(st); k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, nullptr, Bb[BB_Z]); }
     bad |= gemm_bf16<1>(st, n, F, 2 * F, Bb[BB_Z], 2 * F, L.A1b, L.c1, nullptr, 0, H2, F, Bb[BB_A2], F, status);
     bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A2], F, L.A2b, L.c2, nullptr, 0, AV, 3 * F, nullptr, 0, status);
     if (n > 0) {
@@ -915,10 +969,10 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     float *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
     float *T1 = B[B_T1], *T2 = B[B_T2], *T3 = B[B_T3];
     float *GS = B[B_GS], *GV = B[B_GV], *GSM = B[B_GSM], *GVM = B[B_GVM], *GPHI = B[B_GPHI];
-    if (n > 0) { LaunchScope ls_(st); k_update_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, T1, T3, Bb[BB_GA]); }
+    if (n > 0) { LaunchScope ls_(st); k_update_bwd_pre_bf16<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, Bb[BB_GA], Bb[BB_GUV]); }
     bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GA], 3 * F, L.A2tb, nullptr, H2, F, nullptr, 0, Bb[BB_GH2], F, status);
     bad |= gemm_bf16<0>(st, n, 2 * F, F, Bb[BB_GH2], F, L.A1tb, nullptr, nullptr, 0, T1, 2 * F, nullptr, 0, status);
-    if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, GSM, T3, Bb[BB_GUV]); }
+    if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid_bf16<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, AV, GSM, Bb[BB_GUV]); }
     bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
     const float* wst = (wstore && !use_tc) ? wstore + t * wstore_layer_floats : nullptr;
 #define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge, wst)
@@ -931,7 +985,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
       }
     }
 #undef CTD_BWD
-    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV, Bb[BB_GP3]); }
+    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, nullptr, GV, Bb[BB_GP3]); }
     bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GP3], 3 * F, L.W2tb, nullptr, H1, F, nullptr, 0, Bb[BB_GH1], F, status);
     bad |= gemm_bf16<2>(st, n, F, F, Bb[BB_GH1], F, L.W1tb, nullptr, GSM, F, GS, F, nullptr, 0, status);
   }
