@@ -631,7 +631,7 @@ int ctd_set_option(ctd_ctx* c, int32_t option, int64_t value) {
       c->mw.edge_chunk_rows = value;
       return CTD_OK;
     case CTD_OPT_TC_MESSAGE:
-      if (value < 1 || value > 3) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_MESSAGE takes 1, 2 or 3");
+      if (value < 1 || value > 4) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_MESSAGE takes 1 .. 4");
       c->mw.tc_message_variant = (int)value;
       return CTD_OK;
     case CTD_OPT_EDGE_STORE:

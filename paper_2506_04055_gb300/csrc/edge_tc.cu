@@ -189,7 +189,7 @@ __device__ __forceinline__ void folded_basis(float d, int K, float sig, float in
 }
 
 // warps 0..1 producers, warp 2 MMA / TMEM owner, warps 3 .. 3 + 4 NS - 1 epilogue
-template <int NE, int NS, bool SPLIT, int TB, bool AEND = false>
+template <int NE, int NS, bool SPLIT, int TB, bool AEND = false, bool CHUNKED = false>
 __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = align1024(smem_raw);
@@ -205,8 +205,9 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
   uint64_t* sbar = bars + 1;             // per stream: bready[2], bfree[2], tfull[2], tempty[2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + 8 * NS);
 
-  if ((int64_t)blockIdx.x * p.rows_per_cta >= p.n) return;
+  if (!CHUNKED && (int64_t)blockIdx.x * p.rows_per_cta >= p.n) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nstreams = (int64_t)gridDim.x * NS;
 
   if (threadIdx.x == 0) {
     umma::mbar_init(wbar, 1);
@@ -239,47 +240,82 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
       for (int m = 0; m < 3; ++m) umma::tma_load_2d(sA + m * kWfTileBytes, &tmWf, 0, m * 128, wbar);
     }
     const float sig = p.rc / (float)(p.K - 1), inv2s2 = 1.0f / (2.0f * sig * sig), inv_rc = 1.0f / p.rc;
-    // producer warp w serves streams w, w + 2, ...; tiles are produced round-robin
-    StreamRange R[NS];
-    int64_t rp[NS];
-    int maxt = 0;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      R[s] = stream_range<NE, NS>(p, s);
-      rp[s] = R[s].r0;
+    // producer warp w serves streams w, w + 2, ...; tiles are produced round-robin.  Each stream
+    // walks either one contiguous row range or (CHUNKED) its block-cyclic row chunks.
+    constexpr int NO = (NS + 1) / 2;
+    int64_t ck[NO], rp[NO];
+    Chunk C[NO];
+    bool have[NO];
+    int t[NO], it[NO];
+    auto first = [&](int o, int s) -> bool {
+      if (CHUNKED) {
+        ck[o] = (int64_t)blockIdx.x * NS + s;
+        return chunk_at<NE>(p, ck[o], C[o]);
+      }
+      const StreamRange R = stream_range<NE, NS>(p, s);
+      C[o].r0 = R.r0; C[o].r1 = R.r1; C[o].e0 = R.e0; C[o].e1 = R.e1; C[o].ntiles = R.ntiles;
+      return true;
+    };
+    auto enter = [&](int o) {   // at a range's first tile: skip its leading empty rows
+      rp[o] = C[o].r0;
       if (!AEND)
-        while (rp[s] < R[s].r1 && p.arow[rp[s] + 1] == R[s].e0) ++rp[s];
-      maxt = R[s].ntiles > maxt ? R[s].ntiles : maxt;
-    }
-    for (int it = 0; ok && it < maxt; ++it) {
+        while (rp[o] < C[o].r1 && p.arow[rp[o] + 1] == C[o].e0) ++rp[o];
+    };
+    auto norm = [&](int o) {
+      while (have[o] && t[o] >= C[o].ntiles) {
+        t[o] = 0;
+        if (CHUNKED) {
+          ck[o] += nstreams;
+          have[o] = chunk_at<NE>(p, ck[o], C[o]);
+        } else {
+          have[o] = false;
+        }
+        if (have[o]) enter(o);
+      }
+    };
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        if ((s & 1) != warp || it >= R[s].ntiles) continue;
+    for (int o = 0; o < NO; ++o) {
+      const int s = warp + 2 * o;
+      have[o] = s < NS && first(o, s);
+      t[o] = 0;
+      it[o] = 0;
+      if (have[o]) enter(o);
+    }
+    bool any = true;
+    while (ok && any) {
+      any = false;
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        const int s = warp + 2 * o;
+        if (s >= NS) continue;
+        norm(o);
+        if (!have[o]) continue;
+        any = true;
         uint64_t* b = sbar + 8 * s;
-        const int bb = it & 1;
-        if (it >= 2 && !umma::mbar_wait(&b[2 + bb], ((it >> 1) - 1) & 1)) { ok = false; break; }
+        const int bb = it[o] & 1;
+        if (it[o] >= 2 && !umma::mbar_wait(&b[2 + bb], ((it[o] >> 1) - 1) & 1)) { ok = false; break; }
         unsigned char* tile = sB + (s * 2 + bb) * NB * NE * 128;
-        const int64_t tb = R[s].e0 + (int64_t)it * NE;
+        const int64_t tb = C[o].e0 + (int64_t)t[o] * NE;
         const int so = (s * 2 + bb) * NE;
         for (int k0 = lane; k0 < NE; k0 += 32) {
           const int64_t e = tb + k0;
           float rb[kKPad];
           int j = 0, ecnt = 0;
           float4 geo = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (e < R[s].e1) {
+          if (e < C[o].e1) {
             const float4 r = p.ar[e];
             if (AEND) ecnt = p.aend[e];
             const float d = r.w, id = 1.0f / d;
             geo = make_float4(r.x * id, r.y * id, r.z * id, 0.5f * (cospif(d * inv_rc) + 1.0f));
             j = p.acol[e];
 #pragma unroll
-            for (int k = 0; k < kKPad; ++k) {
-              const float t = d - (float)k * sig;
-              rb[k] = k < p.K ? expf(-t * t * inv2s2) : 0.0f;
+            for (int kk = 0; kk < kKPad; ++kk) {
+              const float tq = d - (float)kk * sig;
+              rb[kk] = kk < p.K ? expf(-tq * tq * inv2s2) : 0.0f;
             }
           } else {
 #pragma unroll
-            for (int k = 0; k < kKPad; ++k) rb[k] = 0.0f;
+            for (int kk = 0; kk < kKPad; ++kk) rb[kk] = 0.0f;
           }
           if (SPLIT)
             store_basis_row_split(tile, tile + NE * 128, k0, rb);
@@ -289,53 +325,91 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
           sgeo[so + k0] = geo;
           if (AEND) sfl[so + k0] = ecnt;
         }
-        if (!AEND) mark_row_ends(lane, sfl + so, NE, tb, R[s].r1, p.arow, rp[s]);
+        if (!AEND) mark_row_ends(lane, sfl + so, NE, tb, C[o].r1, p.arow, rp[o]);
         umma::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&b[bb]);
+        ++t[o];
+        ++it[o];
       }
     }
   } else if (warp == 2) {
     if (lane == 0) {
       if (!umma::mbar_wait(wbar, 0)) ok = false;
       const uint32_t idesc = umma::idesc_bf16_m128(NE);
-      int nt[NS], maxt = 0;
+      int64_t kc[NS];
+      int t[NS], it[NS];
+      bool have[NS];
+      Chunk C[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        nt[s] = stream_range<NE, NS>(p, s).ntiles;
-        maxt = nt[s] > maxt ? nt[s] : maxt;
+        t[s] = 0;
+        it[s] = 0;
+        if (CHUNKED) {
+          kc[s] = (int64_t)blockIdx.x * NS + s;
+          have[s] = chunk_at<NE>(p, kc[s], C[s]);
+        } else {
+          const StreamRange R = stream_range<NE, NS>(p, s);
+          C[s].r0 = R.r0; C[s].r1 = R.r1; C[s].e0 = R.e0; C[s].e1 = R.e1; C[s].ntiles = R.ntiles;
+          have[s] = true;
+        }
       }
-      for (int it = 0; ok && it < maxt; ++it) {
+      // one tile per stream in turn, blocking on each stream's barriers
+      bool any = true;
+      while (ok && any) {
+        any = false;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-          if (it >= nt[s]) continue;
+          while (have[s] && t[s] >= C[s].ntiles) {
+            t[s] = 0;
+            if (CHUNKED) {
+              kc[s] += nstreams;
+              have[s] = chunk_at<NE>(p, kc[s], C[s]);
+            } else {
+              have[s] = false;
+            }
+          }
+          if (!have[s]) continue;
+          any = true;
           uint64_t* b = sbar + 8 * s;
-          const int bb = it & 1;
-          if (!umma::mbar_wait(&b[bb], (it >> 1) & 1)) { ok = false; break; }
+          const int bb = it[s] & 1;
+          if (!umma::mbar_wait(&b[bb], (it[s] >> 1) & 1)) { ok = false; break; }
           // TMEM buffer a was last read by the epilogue for tile it - TB
-          const int a = it % TB;
-          if (it >= TB && !umma::mbar_wait(&b[6 + a], ((it / TB) - 1) & 1)) { ok = false; break; }
+          const int a = it[s] % TB;
+          if (it[s] >= TB && !umma::mbar_wait(&b[6 + a], ((it[s] / TB) - 1) & 1)) { ok = false; break; }
           umma::fence_after();
           const uint32_t bbase = umma::smem_u32(sB + (s * 2 + bb) * NB * NE * 128);
 #pragma unroll
           for (int m = 0; m < 3; ++m)
 #pragma unroll
-            for (int k = 0; k < 2 * NB; ++k)   // k-halves of the hi tile[, then of the lo tile]
+            for (int kk = 0; kk < 2 * NB; ++kk)   // k-halves of the hi tile[, then of the lo tile]
               umma::mma_bf16(tmem + (uint32_t)((s * TB + a) * 3 * NE + m * NE),
-                             umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * (k & 1)),
-                             umma::desc_sw128(bbase + (uint32_t)(k >> 1) * NE * 128 + 32u * (k & 1)), idesc, k > 0);
+                             umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * (kk & 1)),
+                             umma::desc_sw128(bbase + (uint32_t)(kk >> 1) * NE * 128 + 32u * (kk & 1)), idesc, kk > 0);
           umma::mma_commit(&b[4 + a]);
-          ++issued[s];
+          issued[s] = ++it[s];
+          ++t[s];
         }
       }
     }
   } else {
     const int s = (warp - 3) >> 2;         // stream of this epilogue warpgroup
     const int q = warp & 3, f = q * 32 + lane;
-    const StreamRange R = stream_range<NE, NS>(p, s);
     uint64_t* b = sbar + 8 * s;
     const float bs = p.bf[f], bvv = p.bf[kF + f], bvs = p.bf[2 * kF + f];
-    int64_t r = R.r0;
+    int it = 0;
+    Chunk C;
+    int64_t kc = (int64_t)blockIdx.x * NS + s;
+    bool have;
+    if (CHUNKED) {
+      have = chunk_at<NE>(p, kc, C);
+    } else {
+      const StreamRange R = stream_range<NE, NS>(p, s);
+      C.r0 = R.r0; C.r1 = R.r1; C.e0 = R.e0; C.e1 = R.e1; C.ntiles = R.ntiles;
+      have = true;
+    }
+    for (; ok && have; kc += nstreams, have = CHUNKED && chunk_at<NE>(p, kc, C)) {
+    int64_t r = C.r0;
     float as = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f;
     auto flush = [&]() {
       const int64_t i = r;
@@ -354,13 +428,13 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
       as = a0 = a1 = a2 = 0.f;
       ++r;
     };
-    while (r < R.r1 && p.arow[r + 1] == R.e0) flush();
-    for (int it = 0; it < R.ntiles; ++it) {
+    while (r < C.r1 && p.arow[r + 1] == C.e0) flush();
+    for (int t = 0; t < C.ntiles; ++t, ++it) {
       const int bb = it & 1, a = it % TB;
       if (!umma::mbar_wait(&b[4 + a], (it / TB) & 1)) { ok = false; break; }
       umma::fence_after();
-      const int64_t tb = R.e0 + (int64_t)it * NE;
-      const int nlive = (int)((R.e1 - tb) < NE ? (R.e1 - tb) : NE);
+      const int64_t tb = C.e0 + (int64_t)t * NE;
+      const int nlive = (int)((C.e1 - tb) < NE ? (C.e1 - tb) : NE);
       const int so = (s * 2 + bb) * NE;
       const int* tj = sj + so;
       const int* tf = sfl + so;
@@ -397,15 +471,16 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
             a0 = fmaf(g[u][1], wvv, fmaf(geo.x, tvs, a0));
             a1 = fmaf(g[u][2], wvv, fmaf(geo.y, tvs, a1));
             a2 = fmaf(g[u][3], wvv, fmaf(geo.z, tvs, a2));
-            for (int nf = tf[slot]; nf > 0 && r < R.r1; --nf) flush();
+            for (int nf = tf[slot]; nf > 0 && r < C.r1; --nf) flush();
           }
         }
       }
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&b[2 + bb]);
     }
-    if (ok)
-      while (r < R.r1) flush();
+    if (!ok) break;
+    while (r < C.r1) flush();
+    }
   }
   if (!ok) atomicOr(p.status, (int)ST_TIMEOUT);
   // the MMAs of every stream's last issued tile have completed before TMEM is released
@@ -1328,9 +1403,11 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         if (!umma::mbar_wait(&b[12], it & 1)) { ok = false; break; }
         {
           // Reduction over the F features: thread f sums half (h) of component `comp` of edge
-          // `slot`, starting at a lane-dependent rotation so that a quarter-warp's 16-byte reads
-          // fall in distinct banks; the two halves combine across lanes 2k, 2k+1, and lane 8k
-          // then holds the four components of edge 4q + k.
+          // `slot`, starting at a rotation 4 (2 comp + h) so that a quarter-warp's 16-byte reads
+          // fall in distinct banks and the summation order depends on (comp, h) alone, not on
+          // the edge's slot in the tile (results do not depend on where tiles start); the two
+          // halves combine across lanes 2k, 2k+1, and lane 8k then holds the four components of
+          // edge 4q + k.
           const int o = f >> 1, slot = o >> 2, comp = o & 3, h = f & 1;
           float acc = 0.f;
           if (slot < nlive) {
@@ -1338,7 +1415,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
             for (int ii = 0; ii < 16; ++ii) {
-              const float4 v = *reinterpret_cast<const float4*>(base + ((4 * ii + 4 * lane) & 63));
+              const float4 v = *reinterpret_cast<const float4*>(base + ((4 * ii + 4 * (lane & 7)) & 63));
               a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
             }
             acc = (a0 + a1) + (a2 + a3);
@@ -1445,17 +1522,20 @@ int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_
   a.n = n; a.K = m.K; a.rc = m.rc; a.arow = arow; a.acol = acol; a.ar = ar; a.PHI = PHI; a.S = S; a.V = V;
   a.bf = m.L[t].bf; a.SM = SM; a.VM = VM; a.VMb = VMb; a.status = status; a.aend = aend;
   const int grid = grid_for(n, &a.rows_per_cta);
-  a.chunk_rows = chunk_rows_for(m, n, kFwgNS);
+  a.chunk_rows = chunk_rows_for(m, n, m.tc_message_variant == 4 ? kFwdNS : kFwgNS);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, true, kFwdTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(true));
+    cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     cudaFuncSetAttribute(k_edge_fwd_tcg<kFwgNE, kFwgNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwg_smem());
     attr = true;
   }
   LaunchScope ls_(st);
   if (m.tc_message_variant == 1) {
     k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
+  } else if (m.tc_message_variant == 4) {
+    k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, true><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
   } else if (m.tc_message_variant == 3) {
     k_edge_fwd_tc<kFwdNE, kFwdNS, true, kFwdTB><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(true), st>>>(tm, a);
   } else {

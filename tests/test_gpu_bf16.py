@@ -84,7 +84,7 @@ def test_bf16_rejects_unsupported_width():
         eng.Potential(32, T=1, n_species=1, precision="bf16")
 
 
-@pytest.mark.parametrize("message", [1, 2, 3])
+@pytest.mark.parametrize("message", [1, 2, 3, 4])
 def test_bf16_message_variants(orc, message):
     """Message kernel with register gathers (1) or bulk-copy gathers and the folded basis (2),
     on the fcc sub-cell, a small water cell and a 4-species mixture with filter biases."""

@@ -94,3 +94,37 @@ def test_budget_limits_residency():
     ids, res, max_res = _run_server(eng, blob, items, 4, "fp32", budget=200 * 1024 * 1024, max_replicas=3)
     assert max_res <= 3
     assert all(res[i]["state"] == 2 and res[i]["steps_done"] == 4 for i in ids)
+
+
+def test_alone_equals_mixed_tensor_core_F128():
+    """F = 128 on the BF16 path runs the tensor-core edge kernels, whose row chunks span replica
+    boundaries in the batched system: a replica's trajectory must still not depend on its
+    neighbours in the batch."""
+    eng = engine()
+    Fw, Tw, Sw = 128, 2, 3
+    vals = syn.xavier_params(Fw, 20, Tw, Sw, seed=7, bias_scale=0.1)
+    blob = syn.params_blob(Fw, 20, Tw, Sw, values=vals)
+    items = _replicas()
+
+    def run(subset, stagger):
+        srv = eng.Server(Fw, blob, T=Tw, n_species=Sw, precision="bf16", dt=DT)
+        ids = []
+        for k, (sy, v) in enumerate(subset):
+            if k < len(subset) - stagger:
+                ids.append(srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, 6, skin=1.0))
+        for step in range(40):
+            if stagger and step == 2:
+                sy, v = subset[-1]
+                ids.append(srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, 6, skin=1.0))
+            srv.step()
+            if all(srv.poll(i)["state"] == 2 for i in ids) and (not stagger or step >= 2):
+                break
+        out = srv.poll(ids[-1])
+        srv.close()
+        return out
+
+    alone = run([items[0]], 0)
+    mixed = run(items[1:] + [items[0]], 1)
+    assert alone["state"] == 2 and mixed["state"] == 2
+    np.testing.assert_array_equal(alone["epot"], mixed["epot"])
+    np.testing.assert_array_equal(alone["positions"], mixed["positions"])
