@@ -189,7 +189,7 @@ __device__ __forceinline__ void folded_basis(float d, int K, float sig, float in
 }
 
 // warps 0..1 producers, warp 2 MMA / TMEM owner, warps 3 .. 3 + 4 NS - 1 epilogue
-template <int NE, int NS, bool SPLIT, int TB, bool AEND = false, bool CHUNKED = false>
+template <int NE, int NS, bool SPLIT, int TB, bool AEND = false, bool CHUNKED = false, bool V0 = false>
 __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = align1024(smem_raw);
@@ -451,13 +451,14 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
           __syncwarp();
           if (lane == 0) umma::mbar_arrive(&b[6 + a]);
         }
+        // V0 (first layer, v = 0): the psi channels v_a phi_vv are zero and not gathered
         float g[8][5];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const bool live = c * 8 + u < nlive;
           const float* pj = p.PHI + (int64_t)(live ? tj[c * 8 + u] : 0) * 6 * kF + f;
 #pragma unroll
-          for (int k = 0; k < 5; ++k) g[u][k] = live ? __ldg(pj + k * kF) : 0.f;
+          for (int k = 0; k < 5; ++k) g[u][k] = live && (!V0 || k == 0 || k == 4) ? __ldg(pj + k * kF) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -468,9 +469,15 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
             const float ws = (ds[u] + bs) * fc, wvv = (dv[u] + bvv) * fc, wvs = (dw[u] + bvs) * fc;
             as = fmaf(g[u][0], ws, as);
             const float tvs = g[u][4] * wvs;
-            a0 = fmaf(g[u][1], wvv, fmaf(geo.x, tvs, a0));
-            a1 = fmaf(g[u][2], wvv, fmaf(geo.y, tvs, a1));
-            a2 = fmaf(g[u][3], wvv, fmaf(geo.z, tvs, a2));
+            if (V0) {
+              a0 = fmaf(geo.x, tvs, a0);
+              a1 = fmaf(geo.y, tvs, a1);
+              a2 = fmaf(geo.z, tvs, a2);
+            } else {
+              a0 = fmaf(g[u][1], wvv, fmaf(geo.x, tvs, a0));
+              a1 = fmaf(g[u][2], wvv, fmaf(geo.y, tvs, a1));
+              a2 = fmaf(g[u][3], wvv, fmaf(geo.z, tvs, a2));
+            }
             for (int nf = tf[slot]; nf > 0 && r < C.r1; --nf) flush();
           }
         }
@@ -1526,6 +1533,8 @@ int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
+    cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, true, kFwdTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(true));
     cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     cudaFuncSetAttribute(k_edge_fwd_tcg<kFwgNE, kFwgNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwg_smem());
@@ -1533,7 +1542,11 @@ int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_
   }
   LaunchScope ls_(st);
   if (m.tc_message_variant == 1) {
-    k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
+    // the first layer's v = 0 (embedding): its message kernel skips the psi channels
+    if (t == 0)
+      k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, false, true><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
+    else
+      k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
   } else if (m.tc_message_variant == 4) {
     k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, true><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
   } else if (m.tc_message_variant == 3) {

@@ -347,7 +347,8 @@ __global__ __launch_bounds__(256) void k_edge_fwd(int64_t n, int F, int K, float
                                                   const float* __restrict__ S, const float* __restrict__ V,
                                                   const float* __restrict__ Wf, const float* __restrict__ bf,
                                                   float* __restrict__ SM, float* __restrict__ VM,
-                                                  __nv_bfloat16* __restrict__ VMb, float* __restrict__ wst) {
+                                                  __nv_bfloat16* __restrict__ VMb, float* __restrict__ wst,
+                                                  int v_zero) {
   extern __shared__ __align__(16) float sm[];
   constexpr int KD = STORE ? KP : 0;            // derivative basis staged only when storing
   const int G = blockDim.x / F;                 // groups per block
@@ -406,8 +407,10 @@ __global__ __launch_bounds__(256) void k_edge_fwd(int64_t n, int F, int K, float
           wvs = fmaf(w_vs[k], q.x, wvs); wvs = fmaf(w_vs[k + 1], q.y, wvs);
           wvs = fmaf(w_vs[k + 2], q.z, wvs); wvs = fmaf(w_vs[k + 3], q.w, wvs);
         }
+        // v_zero (first layer, v = 0): the psi channels v_a phi_vv are zero and not gathered
         const float* p = PHI + (int64_t)js[t] * 6 * F;
-        const float ps = p[f], y0 = p[F + f], y1 = p[2 * F + f], y2 = p[3 * F + f], pvs = p[4 * F + f];
+        const float ps = p[f], pvs = p[4 * F + f];
+        const float y0 = v_zero ? 0.f : p[F + f], y1 = v_zero ? 0.f : p[2 * F + f], y2 = v_zero ? 0.f : p[3 * F + f];
         if (STORE) {
           const float* drb = drbs + t * KP;
           float dws = 0.f, dwvv = 0.f, dwvs = 0.f;
@@ -696,6 +699,7 @@ template <int KP>
 static void edge_fwd_kp(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow,
                         const int32_t* acol, const float4* ar, const float* PHI, const float* S, const float* V,
                         float* SM, float* VM, __nv_bfloat16* VMb, float* wst) {
+  const int v_zero = t == 0;   // the first layer's v is the embedding's zero
   const int F = m.F, G = kThreads / F;
   const int KD = wst ? KP : 0;
   size_t smem = (size_t)G * F * (KP + KD + 4 + (wst ? 1 : 0)) * sizeof(float) + (size_t)G * F * sizeof(int);
@@ -705,10 +709,10 @@ static void edge_fwd_kp(cudaStream_t st, const ModelW& m, int t, int64_t n, cons
   LaunchScope ls_(st);
   if (wst)
     k_edge_fwd<KP, true><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, arow, acol, ar, PHI, S, V,
-                                                                   m.L[t].Wf, m.L[t].bf, SM, VM, VMb, wst);
+                                                                   m.L[t].Wf, m.L[t].bf, SM, VM, VMb, wst, v_zero);
   else
     k_edge_fwd<KP, false><<<(unsigned)blocks, kThreads, smem, st>>>(n, F, m.K, m.rc, arow, acol, ar, PHI, S, V,
-                                                                    m.L[t].Wf, m.L[t].bf, SM, VM, VMb, nullptr);
+                                                                    m.L[t].Wf, m.L[t].bf, SM, VM, VMb, nullptr, v_zero);
 }
 
 template <int KP>
