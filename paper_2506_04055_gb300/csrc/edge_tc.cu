@@ -667,8 +667,10 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tc(const __gr
     };
     float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
     auto flush = [&]() {
-      float* o = p.GPHI + r * 5 * kF;
-      o[f] = gps; o[kF + f] = gy0; o[2 * kF + f] = gy1; o[3 * kF + f] = gy2; o[4 * kF + f] = gpvs;
+      if (p.GPHI) {
+        float* o = p.GPHI + r * 5 * kF;
+        o[f] = gps; o[kF + f] = gy0; o[2 * kF + f] = gy1; o[3 * kF + f] = gy2; o[4 * kF + f] = gpvs;
+      }
       gps = gy0 = gy1 = gy2 = gpvs = 0.f;
       ++r;
 #pragma unroll
@@ -1321,8 +1323,10 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
       };
       float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
       auto flush = [&]() {
-        float* o = p.GPHI + r * 5 * kF;
-        o[f] = gps; o[kF + f] = gy0; o[2 * kF + f] = gy1; o[3 * kF + f] = gy2; o[4 * kF + f] = gpvs;
+        if (p.GPHI) {
+          float* o = p.GPHI + r * 5 * kF;
+          o[f] = gps; o[kF + f] = gy0; o[2 * kF + f] = gy1; o[3 * kF + f] = gy2; o[4 * kF + f] = gpvs;
+        }
         gps = gy0 = gy1 = gy2 = gpvs = 0.f;
         ++r;
 #pragma unroll

@@ -598,12 +598,14 @@ __global__ __launch_bounds__(256) void k_edge_bwd(int64_t n, int F, int K, float
         hedge[c0 + f] = h;
       }
     }
-    float* o = GPHI + j * 5 * F;
-    o[f] = gps;
-    o[F + f] = gy0;
-    o[2 * F + f] = gy1;
-    o[3 * F + f] = gy2;
-    o[4 * F + f] = gpvs;
+    if (GPHI) {
+      float* o = GPHI + j * 5 * F;
+      o[f] = gps;
+      o[F + f] = gy0;
+      o[2 * F + f] = gy1;
+      o[3 * F + f] = gy2;
+      o[4 * F + f] = gpvs;
+    }
   }
 }
 
@@ -862,12 +864,16 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     gemm<EPI_ADD>(st, 3 * n, F, 2 * F, T3, 2 * F, L.UV, nullptr, GV, F, GVM, F);         // gvm
     // message backward
     const float* wst = wstore ? wstore + t * wstore_layer_floats : nullptr;
-#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge, wst)
+    // the first layer's inputs (embedding, v = 0) do not depend on positions: its edge adjoint
+    // writes no phi gradients and the phi backward below it is skipped
+    float* gphi = t > 0 ? GPHI : nullptr;
+#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, gphi, hedge, wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
       CTD_KP_DISPATCH(m.KP, CTD_BWD)
     }
 #undef CTD_BWD
+    if (t == 0) break;
     // phi backward -> gradients w.r.t. the layer input (s_t, v_t)
     if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV, nullptr); }
     gemm<EPI_DSILU>(st, n, F, 3 * F, T2, 3 * F, L.W2, nullptr, H1, F, T1, F);          // gh1
@@ -979,16 +985,19 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid_bf16<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, AV, GSM, Bb[BB_GUV]); }
     bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
     const float* wst = (wstore && !use_tc) ? wstore + t * wstore_layer_floats : nullptr;
-#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge, wst)
+    // first layer: no phi gradients, no phi backward (its inputs do not depend on positions)
+    float* gphi = t > 0 ? GPHI : nullptr;
+#define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, gphi, hedge, wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
       if (use_tc_bwd) {
-        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, GPHI, hedge, status, aend);
+        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, gphi, hedge, status, aend);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_BWD)
       }
     }
 #undef CTD_BWD
+    if (t == 0) break;
     if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, nullptr, GV, Bb[BB_GP3]); }
     bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GP3], 3 * F, L.W2tb, nullptr, H1, F, nullptr, 0, Bb[BB_GH1], F, status);
     bad |= gemm_bf16<2>(st, n, F, F, Bb[BB_GH1], F, L.W1tb, nullptr, GSM, F, GS, F, nullptr, 0, status);
