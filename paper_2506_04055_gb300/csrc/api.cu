@@ -639,7 +639,7 @@ int ctd_set_option(ctd_ctx* c, int32_t option, int64_t value) {
       c->mw.edge_store = value != 0;
       return CTD_OK;
     case CTD_OPT_TC_ADJOINT:
-      if (value < 0 || value > 6) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0 .. 6");
+      if (value < 0 || value > 4) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0 .. 4");
       c->mw.tc_adjoint = value != 0;
       c->mw.tc_adjoint_variant = (int)value;
       return CTD_OK;

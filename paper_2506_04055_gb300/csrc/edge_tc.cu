@@ -65,6 +65,31 @@ __device__ __forceinline__ void store_basis_row_split(unsigned char* hi, unsigne
   store_basis_row(lo, r, l);
 }
 
+// Columns 16h .. 16h+15 of row r of a 128B-swizzled BF16 tile (two 16-byte chunks).
+__device__ __forceinline__ void store_basis_half(unsigned char* tile, int r, int h, const float (&v)[16]) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    uint32_t w[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * c + 2 * x], v[8 * c + 2 * x + 1]);
+      w[x] = *reinterpret_cast<uint32_t*>(&b2);
+    }
+    *reinterpret_cast<uint4*>(tile + umma::sw128_offset(r, 16 * h + 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+__device__ __forceinline__ void store_basis_half_split(unsigned char* hi, unsigned char* lo, int r, int h,
+                                                       const float (&v)[16]) {
+  float a[16], b[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    a[k] = __bfloat162float(__float2bfloat16_rn(v[k]));
+    b[k] = v[k] - a[k];
+  }
+  store_basis_half(hi, r, h, a);
+  store_basis_half(lo, r, h, b);
+}
+
 struct EdgeTcArgs {
   int64_t n;
   int64_t rows_per_cta;
@@ -1093,7 +1118,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tcg(const __g
 // Thread f accumulates the row's phi gradients and overwrites its own feature of the gathered
 // row with its partials of (dU/dd, dU/du); after a stream barrier the partials are reduced over
 // the F features from shared memory and turned into hedge[e].
-template <int NE, int NS, bool FOLD, bool SPLIT, int NBUF = 2>
+template <int NE, int NS, bool FOLD, bool SPLIT, int NBUF = 2, int KC = 0>
 __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   static_assert(NS <= 2, "one producer warp per stream");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -1104,7 +1129,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
   // channel block yields [W | dW/dd] as 2 NE columns
   constexpr int NB = SPLIT ? 2 : 1;
   static_assert(NS * 2 * 6 * NE <= 512, "TMEM columns");
-  static_assert(NE % 8 == 0 && NBUF >= 2 && NBUF <= 4, "tile shape");
+  static_assert(NE == 16 && NBUF >= 2 && NBUF <= 4, "tile shape: one lane pair per edge");
   unsigned char* sB = sA + kWfBytes;                                 // [NS][NBUF][NB][2 NE x 128 B]
   float* sG = reinterpret_cast<float*>(sB + NS * NBUF * NB * 2 * NE * 128);   // [NS][NBUF][NE][4F]
   int* sfl = reinterpret_cast<int*>(sG + (size_t)NS * NBUF * NE * 4 * kF);   // [NS][NBUF][NE]
@@ -1170,16 +1195,21 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
           have = chunk_at<NE>(p, k, C);
         }
       };
+      // lane pair (slot, h): slot = lane & 15 handles edge `slot` of the tile; its halves
+      // h = lane >> 4 compute basis entries k = 2q + h and swap the ones the other half stores,
+      // so that each lane writes 16 contiguous columns and issues one bulk copy
+      const int slot = lane & (NE - 1), h = lane >> 4;
+      const int KK = KC > 0 ? KC : p.K;
       float4 rn = make_float4(0.f, 0.f, 0.f, 1.f);
       int jn = 0, en = 0, nln = 0;
       int64_t tbn = 0;
       auto fetch = [&]() {
         tbn = C.e0 + (int64_t)t * NE;
         nln = (int)((C.e1 - tbn) < NE ? (C.e1 - tbn) : NE);
-        if (lane < nln) {
-          rn = p.ar[tbn + lane];
-          jn = p.acol[tbn + lane];
-          en = p.aend[tbn + lane];
+        if (slot < nln) {
+          rn = p.ar[tbn + slot];
+          jn = p.acol[tbn + slot];
+          en = p.aend[tbn + slot];
         }
       };
       normalize();
@@ -1194,27 +1224,46 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         cur = have;
         if (cur) fetch();
         const int bb = it % NBUF;
-        float bv[kKPad], dbv[kKPad];
+        float bq[16], dq[16];
         float4 geo = make_float4(0.f, 0.f, 0.f, 1.f);
         float2 fcv = make_float2(0.f, 0.f);
-        if (lane < nlive) {
+        const bool live = slot < nlive;
+        if (live) {
           const float d = r.w, id = 1.0f / d;
           geo = make_float4(r.x * id, r.y * id, r.z * id, d);
-          if (FOLD) {
-            folded_basis<true>(d, p.K, sig, inv2s2, inv_s2, inv_rc, bv, dbv);
-          } else {
-            fcv = make_float2(0.5f * (cospif(d * inv_rc) + 1.0f), -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc));
+          const float fc = 0.5f * (cospif(d * inv_rc) + 1.0f);
+          const float dfc = -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc);
+          fcv = make_float2(fc, dfc);
 #pragma unroll
-            for (int q = 0; q < kKPad; ++q) {
-              const float tq = d - (float)q * sig;
-              const float v = q < p.K ? expf(-tq * tq * inv2s2) : 0.0f;
-              bv[q] = v;
-              dbv[q] = -v * tq * inv_s2;
+          for (int q = 0; q < 16; ++q) {
+            const int kk = 2 * q + h;
+            const float tq = d - (float)kk * sig;
+            const bool in = kk < KK;
+            const float v = in ? expf(-tq * tq * inv2s2) : 0.0f;
+            const float dv = -v * tq * inv_s2;
+            if (FOLD) {
+              // f_c and the bias column K folded in (see folded_basis)
+              bq[q] = in ? fc * v : (kk == KK ? fc : 0.0f);
+              dq[q] = in ? fc * dv + dfc * v : (kk == KK ? dfc : 0.0f);
+            } else {
+              bq[q] = v;
+              dq[q] = dv;
             }
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < kKPad; ++q) bv[q] = dbv[q] = 0.0f;
+          for (int q = 0; q < 16; ++q) bq[q] = dq[q] = 0.0f;
+        }
+        // this lane's columns 16h .. 16h+15: its own parity and the partner's
+        float bs[16], ds[16];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float yb = __shfl_xor_sync(0xffffffffu, h == 0 ? bq[8 + i] : bq[i], 16);
+          const float yd = __shfl_xor_sync(0xffffffffu, h == 0 ? dq[8 + i] : dq[i], 16);
+          bs[2 * i] = h == 0 ? bq[i] : yb;
+          bs[2 * i + 1] = h == 0 ? yb : bq[8 + i];
+          ds[2 * i] = h == 0 ? dq[i] : yd;
+          ds[2 * i + 1] = h == 0 ? yd : dq[8 + i];
         }
         if (it >= NBUF && !umma::mbar_wait(&b[4 + bb], ((it / NBUF) - 1) & 1)) { ok = false; break; }
         const int so = (s * NBUF + bb) * NE;
@@ -1222,21 +1271,23 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         if (lane == 0) umma::mbar_expect_tx_only(&b[bb], (uint32_t)(nlive * 4 * kF * 4));
         __syncwarp();
         unsigned char* tile = sB + (s * NBUF + bb) * NB * 2 * NE * 128;
-        if (lane < NE) {
-          if (lane < nlive) {
-            umma::bulk_copy_g2s(g + (size_t)lane * 4 * kF, p.Gsm + (int64_t)jj * kF, kF * 4, &b[bb]);
-            umma::bulk_copy_g2s(g + (size_t)lane * 4 * kF + kF, p.Gvm + (int64_t)jj * 3 * kF, 3 * kF * 4, &b[bb]);
-          }
-          if (SPLIT) {
-            store_basis_row_split(tile, tile + 2 * NE * 128, lane, bv);
-            store_basis_row_split(tile, tile + 2 * NE * 128, NE + lane, dbv);
-          } else {
-            store_basis_row(tile, lane, bv);
-            store_basis_row(tile, NE + lane, dbv);
-          }
-          sgeo[so + lane] = geo;
-          if (!FOLD) sfc[so + lane] = fcv;
-          sfl[so + lane] = lane < nlive ? ecnt : 0;
+        if (live) {
+          if (h == 0)
+            umma::bulk_copy_g2s(g + (size_t)slot * 4 * kF, p.Gsm + (int64_t)jj * kF, kF * 4, &b[bb]);
+          else
+            umma::bulk_copy_g2s(g + (size_t)slot * 4 * kF + kF, p.Gvm + (int64_t)jj * 3 * kF, 3 * kF * 4, &b[bb]);
+        }
+        if (SPLIT) {
+          store_basis_half_split(tile, tile + 2 * NE * 128, slot, h, bs);
+          store_basis_half_split(tile, tile + 2 * NE * 128, NE + slot, h, ds);
+        } else {
+          store_basis_half(tile, slot, h, bs);
+          store_basis_half(tile, NE + slot, h, ds);
+        }
+        if (h == 0) {
+          sgeo[so + slot] = geo;
+          if (!FOLD) sfc[so + slot] = fcv;
+          sfl[so + slot] = live ? ecnt : 0;
         }
         gathered = it + 1;
         umma::fence_proxy_async_smem();
@@ -1581,8 +1632,7 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, true, kBwgSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(true));
-    cudaFuncSetAttribute(k_edge_bwd_tcg<8, kBwgNS, false, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(false, 8, 4));
-    cudaFuncSetAttribute(k_edge_bwd_tcg<8, kBwgNS, false, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(true, 8, 4));
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     attr = true;
   }
   a.chunk_rows = chunk_rows_for(m, n, kBwgNS);
@@ -1593,12 +1643,10 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (m.tc_adjoint_variant == 3)
       k_edge_bwd_tcg<kBwgNE, kBwgNS, true, kBwgSplit><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
-    else if (m.tc_adjoint_variant == 5)
-      k_edge_bwd_tcg<8, kBwgNS, false, false, 4><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(false, 8, 4), st>>>(tm, a);
-    else if (m.tc_adjoint_variant == 6)
-      k_edge_bwd_tcg<8, kBwgNS, false, true, 4><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(true, 8, 4), st>>>(tm, a);
     else if (m.tc_adjoint_variant == 4)
       k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(true), st>>>(tm, a);
+    else if (m.K == 20)   // the usual basis size: compile-time loop bound
+      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
     else
       k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
   } else
