@@ -214,7 +214,7 @@ __device__ __forceinline__ void folded_basis(float d, int K, float sig, float in
 }
 
 // warps 0..1 producers, warp 2 MMA / TMEM owner, warps 3 .. 3 + 4 NS - 1 epilogue
-template <int NE, int NS, bool SPLIT, int TB, bool AEND = false, bool CHUNKED = false, bool V0 = false>
+template <int NE, int NS, bool SPLIT, int TB, bool AEND = false, bool CHUNKED = false, bool V0 = false, int KC = 0>
 __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = align1024(smem_raw);
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
 #pragma unroll
             for (int kk = 0; kk < kKPad; ++kk) {
               const float tq = d - (float)kk * sig;
-              rb[kk] = kk < p.K ? expf(-tq * tq * inv2s2) : 0.0f;
+              rb[kk] = kk < (KC > 0 ? KC : p.K) ? expf(-tq * tq * inv2s2) : 0.0f;
             }
           } else {
 #pragma unroll
@@ -1590,6 +1590,10 @@ int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_
     cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, false, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
+    cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, false, true, 20>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
+    cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, false, false, 20>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, true, kFwdTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(true));
     cudaFuncSetAttribute(k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     cudaFuncSetAttribute(k_edge_fwd_tcg<kFwgNE, kFwgNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwg_smem());
@@ -1598,8 +1602,13 @@ int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_
   LaunchScope ls_(st);
   if (m.tc_message_variant == 1) {
     // the first layer's v = 0 (embedding): its message kernel skips the psi channels
-    if (t == 0)
+    // K = 20 (the usual basis) with a compile-time loop bound
+    if (t == 0 && m.K == 20)
+      k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, false, true, 20><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
+    else if (t == 0)
       k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, false, true><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
+    else if (m.K == 20)
+      k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB, false, false, false, 20><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
     else
       k_edge_fwd_tc<kFwdNE, kFwdNS, kFwdSplit, kFwdTB><<<grid, 32 * (3 + 4 * kFwdNS), fwd_smem(), st>>>(tm, a);
   } else if (m.tc_message_variant == 4) {
