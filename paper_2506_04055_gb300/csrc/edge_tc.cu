@@ -1415,9 +1415,8 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
           }
           // per edge: accumulate the row's phi gradients; overwrite this thread's gathered
           // gradients in place with its partials of (dU/dd, dU/du)
-          auto edge = [&](int u, int slot) {
+          auto edge = [&](int u, int slot, float gs, float gv0, float gv1, float gv2) {
             float* gg = tG + (size_t)slot * 4 * kF;
-            const float gs = gg[0], gv0 = gg[kF], gv1 = gg[2 * kF], gv2 = gg[3 * kF];
             const float4 geo = tg[slot];
             float Ws, Wvv, Wvs, dWs, dWvv, dWvs;   // filter and its distance derivative, f_c included
             if (FOLD) {
@@ -1446,15 +1445,23 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
           };
           const int4 fa = *reinterpret_cast<const int4*>(tf + c * 8), fb = *reinterpret_cast<const int4*>(tf + c * 8 + 4);
           if ((fa.x | fa.y | fa.z | fa.w | fb.x | fb.y | fb.z | fb.w) == 0 && c * 8 + 8 <= nlive) {
-            // no row ends in these eight edges: straight-line code the compiler can interleave
+            // no row ends in these eight edges: all their gathered values are read first, so
+            // the 32 shared-memory loads overlap, then straight-line arithmetic
+            float G[8][4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) edge(u, c * 8 + u);
+            for (int u = 0; u < 8; ++u) {
+              const float* gg = tG + (size_t)(c * 8 + u) * 4 * kF;
+              G[u][0] = gg[0]; G[u][1] = gg[kF]; G[u][2] = gg[2 * kF]; G[u][3] = gg[3 * kF];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) edge(u, c * 8 + u, G[u][0], G[u][1], G[u][2], G[u][3]);
           } else {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int slot = c * 8 + u;
               if (slot < nlive) {
-                edge(u, slot);
+                const float* gg = tG + (size_t)slot * 4 * kF;
+                edge(u, slot, gg[0], gg[kF], gg[2 * kF], gg[3 * kF]);
                 for (int nf = tf[slot]; nf > 0 && r < C.r1; --nf) flush();
               }
             }
