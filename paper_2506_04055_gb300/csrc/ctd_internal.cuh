@@ -175,7 +175,7 @@ int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_
 int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
                 const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm, const float* Gvm,
                 float* GPHI, float4* hedge, int* status,
-                const int32_t* aend);
+                const int32_t* aend, const float* G4);
 template <int EPI>
 int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, int64_t lda,
               const __nv_bfloat16* W, const float* bias, const float* aux, int ldaux, float* out, int ldo,

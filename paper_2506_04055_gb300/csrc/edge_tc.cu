@@ -112,6 +112,7 @@ struct EdgeTcArgs {
   bf16* __restrict__ VMb;
   float* __restrict__ GPHI;        // [n][5F]  (adjoint)
   float4* __restrict__ hedge;      // [E]      (adjoint)
+  const float* __restrict__ G4;    // [n][F][4] = (gsm, gvm_0..2) per feature (adjoint, interleaved)
   int* status;
 };
 
@@ -1118,7 +1119,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tcg(const __g
 // Thread f accumulates the row's phi gradients and overwrites its own feature of the gathered
 // row with its partials of (dU/dd, dU/du); after a stream barrier the partials are reduced over
 // the F features from shared memory and turned into hedge[e].
-template <int NE, int NS, bool FOLD, bool SPLIT, int NBUF = 2, int KC = 0>
+template <int NE, int NS, bool FOLD, bool SPLIT, int NBUF = 2, int KC = 0, bool G4L = false>
 __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   static_assert(NS <= 2, "one producer warp per stream");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -1272,10 +1273,14 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         __syncwarp();
         unsigned char* tile = sB + (s * NBUF + bb) * NB * 2 * NE * 128;
         if (live) {
-          if (h == 0)
+          if (G4L) {
+            // G4L: the receiver's (gsm, gvm) interleaved per feature, one 2 KB row
+            if (h == 0) umma::bulk_copy_g2s(g + (size_t)slot * 4 * kF, p.G4 + (int64_t)jj * 4 * kF, 4 * kF * 4, &b[bb]);
+          } else if (h == 0) {
             umma::bulk_copy_g2s(g + (size_t)slot * 4 * kF, p.Gsm + (int64_t)jj * kF, kF * 4, &b[bb]);
-          else
+          } else {
             umma::bulk_copy_g2s(g + (size_t)slot * 4 * kF + kF, p.Gvm + (int64_t)jj * 3 * kF, 3 * kF * 4, &b[bb]);
+          }
         }
         if (SPLIT) {
           store_basis_half_split(tile, tile + 2 * NE * 128, slot, h, bs);
@@ -1415,6 +1420,12 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
           }
           // per edge: accumulate the row's phi gradients; overwrite this thread's gathered
           // gradients in place with its partials of (dU/dd, dU/du)
+          // this thread's gathered values of edge `slot` and where its partials go back
+          auto gat = [&](int slot) -> float4 {
+            if (G4L) return *reinterpret_cast<const float4*>(sG + ((size_t)(so + slot) * kF + f) * 4);
+            const float* gg = tG + (size_t)slot * 4 * kF;
+            return make_float4(gg[0], gg[kF], gg[2 * kF], gg[3 * kF]);
+          };
           auto edge = [&](int u, int slot, float gs, float gv0, float gv1, float gv2) {
             float* gg = tG + (size_t)slot * 4 * kF;
             const float4 geo = tg[slot];
@@ -1438,30 +1449,32 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
             gpvs = fmaf(qv, Wvs, gpvs);
             const float gWs = gs * cur[0], gWvv = gv0 * cur[1] + gv1 * cur[2] + gv2 * cur[3], gWvs = qv * cur[4];
             const float tv = cur[4] * Wvs;
-            gg[0] = gWs * dWs + gWvv * dWvv + gWvs * dWvs;
-            gg[kF] = gv0 * tv;
-            gg[2 * kF] = gv1 * tv;
-            gg[3 * kF] = gv2 * tv;
+            const float pd = gWs * dWs + gWvv * dWvv + gWvs * dWvs;
+            if (G4L) {
+              *reinterpret_cast<float4*>(sG + ((size_t)(so + slot) * kF + f) * 4) = make_float4(pd, gv0 * tv, gv1 * tv, gv2 * tv);
+            } else {
+              gg[0] = pd;
+              gg[kF] = gv0 * tv;
+              gg[2 * kF] = gv1 * tv;
+              gg[3 * kF] = gv2 * tv;
+            }
           };
           const int4 fa = *reinterpret_cast<const int4*>(tf + c * 8), fb = *reinterpret_cast<const int4*>(tf + c * 8 + 4);
           if ((fa.x | fa.y | fa.z | fa.w | fb.x | fb.y | fb.z | fb.w) == 0 && c * 8 + 8 <= nlive) {
             // no row ends in these eight edges: all their gathered values are read first, so
             // the 32 shared-memory loads overlap, then straight-line arithmetic
-            float G[8][4];
+            float4 G[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const float* gg = tG + (size_t)(c * 8 + u) * 4 * kF;
-              G[u][0] = gg[0]; G[u][1] = gg[kF]; G[u][2] = gg[2 * kF]; G[u][3] = gg[3 * kF];
-            }
+            for (int u = 0; u < 8; ++u) G[u] = gat(c * 8 + u);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) edge(u, c * 8 + u, G[u][0], G[u][1], G[u][2], G[u][3]);
+            for (int u = 0; u < 8; ++u) edge(u, c * 8 + u, G[u].x, G[u].y, G[u].z, G[u].w);
           } else {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int slot = c * 8 + u;
               if (slot < nlive) {
-                const float* gg = tG + (size_t)slot * 4 * kF;
-                edge(u, slot, gg[0], gg[kF], gg[2 * kF], gg[3 * kF]);
+                const float4 gq = gat(slot);
+                edge(u, slot, gq.x, gq.y, gq.z, gq.w);
                 for (int nf = tf[slot]; nf > 0 && r < C.r1; --nf) flush();
               }
             }
@@ -1477,8 +1490,31 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
           // the edge's slot in the tile (results do not depend on where tiles start); the two
           // halves combine across lanes 2k, 2k+1, and lane 8k then holds the four components of
           // edge 4q + k.
-          const int o = f >> 1, slot = o >> 2, comp = o & 3, h = f & 1;
-          float acc = 0.f;
+          // G4L: thread f sums all four components of edge f >> 3 over 16 features
+          // (part = f & 7, rotated by the part so that a quarter-warp's 16-byte reads fall in
+          // distinct banks), then the eight parts combine across lanes 8k .. 8k+7
+          const int o = f >> 1, slot = G4L ? (f >> 3) : (o >> 2), comp = o & 3, h = f & 1;
+          float acc = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+          if (G4L) {
+            const int part = f & 7;
+            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (slot < nlive) {
+              const float4* base = reinterpret_cast<const float4*>(sG) + (size_t)(so + slot) * kF + part * 16;
+#pragma unroll
+              for (int ii = 0; ii < 16; ++ii) {
+                const float4 v = base[(ii + part) & 15];
+                sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+              }
+            }
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1) {
+              sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+              sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+              sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
+              sum.w += __shfl_xor_sync(0xffffffffu, sum.w, off);
+            }
+            acc = sum.x; g0 = sum.y; g1 = sum.z; g2 = sum.w;
+          } else {
           if (slot < nlive) {
             const float* base = sG + (size_t)so * 4 * kF + (size_t)slot * 4 * kF + comp * kF + h * 64;
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -1490,9 +1526,10 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
             acc = (a0 + a1) + (a2 + a3);
           }
           acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-          const float g0 = __shfl_down_sync(0xffffffffu, acc, 2);
-          const float g1 = __shfl_down_sync(0xffffffffu, acc, 4);
-          const float g2 = __shfl_down_sync(0xffffffffu, acc, 6);
+          g0 = __shfl_down_sync(0xffffffffu, acc, 2);
+          g1 = __shfl_down_sync(0xffffffffu, acc, 4);
+          g2 = __shfl_down_sync(0xffffffffu, acc, 6);
+          }
           if ((lane & 7) == 0 && slot < nlive) {
             const float pd = acc;
             const float4 geo = tg[slot];
@@ -1633,7 +1670,7 @@ int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_
 
 int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
                 const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm, const float* Gvm,
-                float* GPHI, float4* hedge, int* status, const int32_t* aend) {
+                float* GPHI, float4* hedge, int* status, const int32_t* aend, const float* G4) {
   if (n == 0) return 0;
   CUtensorMap tm;
   if (!make_tmap_bf16(&tm, m.L[t].Wfb, 3 * kF, 64, 64, 128)) return -2;
@@ -1641,6 +1678,7 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
   a.n = n; a.K = m.K; a.rc = m.rc; a.accumulate = accumulate; a.arow = arow; a.acol = acol; a.ar = ar;
   a.PHI = PHI; a.Gsm = Gsm; a.Gvm = Gvm; a.bf = m.L[t].bf; a.GPHI = GPHI; a.hedge = hedge; a.status = status;
   a.aend = aend;
+  a.G4 = G4;
   const int grid = grid_for(n, &a.rows_per_cta);
   static bool attr = false;
   if (!attr) {
@@ -1649,6 +1687,8 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, true, kBwgSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(true));
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     attr = true;
   }
   a.chunk_rows = chunk_rows_for(m, n, kBwgNS);
@@ -1661,7 +1701,12 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
       k_edge_bwd_tcg<kBwgNE, kBwgNS, true, kBwgSplit><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
     else if (m.tc_adjoint_variant == 4)
       k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(true), st>>>(tm, a);
-    else if (m.K == 20)   // the usual basis size: compile-time loop bound
+    // the usual basis size (K = 20) with a compile-time loop bound; G4: gradients interleaved
+    else if (m.K == 20 && G4)
+      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
+    else if (G4)
+      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 0, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
+    else if (m.K == 20)
       k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
     else
       k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);

@@ -297,6 +297,18 @@ __global__ void k_update_bwd_mid_bf16(int64_t n, int F, float eps, const float* 
   GUVb[i * 6 * F + 5 * F + f] = __float2bfloat16_rn(gsp * uv[4 * F + f] + g * v2);
 }
 
+// G4[i][f] = (gsm_i,f, gvm_i,0,f, gvm_i,1,f, gvm_i,2,f): the receivers' gradients interleaved per
+// feature for the bulk-gathered tensor-core adjoint (one 2 KB row per gathered receiver).
+__global__ void k_interleave_g4(int64_t n, int F, const float* __restrict__ Gsm, const float* __restrict__ Gvm,
+                                float4* __restrict__ G4) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  int64_t i = idx / F;
+  int f = (int)(idx % F);
+  const float* gv = Gvm + i * 3 * F + f;
+  G4[idx] = make_float4(Gsm[idx], gv[0], gv[F], gv[2 * F]);
+}
+
 // Backward of PHI packing: gphi_vv = sum_a gpsi_a v_a, gv_a = gvm_a + gpsi_a phi_vv;
 // GP3 = [gphi_s | gphi_vv | gphi_vs]
 __global__ void k_phi_bwd_pre(int64_t n, int F, const float* __restrict__ GPHI, const float* __restrict__ PHI,
@@ -778,6 +790,7 @@ enum BufId {
   B_T3,                            // [3n][2F] scratch
   B_GS, B_GV, B_GSM, B_GVM,        // [n][F], [n][3F], [n][F], [n][3F]
   B_GPHI,                          // [n][5F]
+  B_G4,                            // [n][F][4] = (gsm, gvm_0..2) per feature (tensor-core adjoint)
   B_H3, B_G3,                      // [n][F/2]
   B_COUNT
 };
@@ -802,6 +815,7 @@ int64_t model_buffer_floats_per_atom(int b, int F, int T) {
     case B_GS: case B_GSM: return F;
     case B_GV: case B_GVM: return 3 * F;
     case B_GPHI: return 5 * F;
+    case B_G4: return 4 * F;
     case B_H3: case B_G3: return F / 2;
     default: return 0;
   }
@@ -982,8 +996,11 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_pre_bf16<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, Bb[BB_GA], Bb[BB_GUV]); }
     bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GA], 3 * F, L.A2tb, nullptr, H2, F, nullptr, 0, Bb[BB_GH2], F, status);
     bad |= gemm_bf16<0>(st, n, 2 * F, F, Bb[BB_GH2], F, L.A1tb, nullptr, nullptr, 0, T1, 2 * F, nullptr, 0, status);
+    // the bulk-gathered tensor-core adjoint reads gsm and gvm interleaved per feature (G4)
+    float* G4 = (use_tc_bwd && m.tc_adjoint_variant == 2) ? B[B_G4] : nullptr;
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid_bf16<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, AV, GSM, Bb[BB_GUV]); }
     bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
+    if (G4 && n > 0) { LaunchScope ls_(st); k_interleave_g4<<<nb, kThreads, 0, st>>>(n, F, GSM, GVM, reinterpret_cast<float4*>(G4)); }
     const float* wst = (wstore && !use_tc) ? wstore + t * wstore_layer_floats : nullptr;
     // first layer: no phi gradients, no phi backward (its inputs do not depend on positions)
     float* gphi = t > 0 ? GPHI : nullptr;
@@ -991,7 +1008,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
       if (use_tc_bwd) {
-        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, gphi, hedge, status, aend);
+        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, gphi, hedge, status, aend, G4);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_BWD)
       }
