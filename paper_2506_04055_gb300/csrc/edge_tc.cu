@@ -1119,7 +1119,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tcg(const __g
 // Thread f accumulates the row's phi gradients and overwrites its own feature of the gathered
 // row with its partials of (dU/dd, dU/du); after a stream barrier the partials are reduced over
 // the F features from shared memory and turned into hedge[e].
-template <int NE, int NS, bool FOLD, bool SPLIT, int NBUF = 2, int KC = 0, bool G4L = false>
+template <int NE, int NS, bool FOLD, bool SPLIT, int NBUF = 2, int KC = 0, bool G4L = false, bool L0 = false>
 __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   static_assert(NS <= 2, "one producer warp per stream");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -1374,7 +1374,8 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         if (row < C.r1) {
           const float* pj = p.PHI + row * 6 * kF + f;
 #pragma unroll
-          for (int kk = 0; kk < 5; ++kk) o[kk] = __ldg(pj + kk * kF);
+          for (int kk = 0; kk < 5; ++kk)
+            if (!L0 || kk == 0 || kk == 4) o[kk] = __ldg(pj + kk * kF);
         }
       };
       float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
@@ -1441,13 +1442,18 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
               dWvv = fcv.x * W[3][u] + fcv.y * wvv;
               dWvs = fcv.x * W[5][u] + fcv.y * wvs;
             }
-            gps = fmaf(gs, Ws, gps);
-            gy0 = fmaf(gv0, Wvv, gy0);
-            gy1 = fmaf(gv1, Wvv, gy1);
-            gy2 = fmaf(gv2, Wvv, gy2);
+            // L0 (first layer): v = 0 so psi = 0, and no phi gradients are written, so only the
+            // per-edge partials are formed
+            if (!L0) {
+              gps = fmaf(gs, Ws, gps);
+              gy0 = fmaf(gv0, Wvv, gy0);
+              gy1 = fmaf(gv1, Wvv, gy1);
+              gy2 = fmaf(gv2, Wvv, gy2);
+            }
             const float qv = -(gv0 * geo.x + gv1 * geo.y + gv2 * geo.z);
-            gpvs = fmaf(qv, Wvs, gpvs);
-            const float gWs = gs * cur[0], gWvv = gv0 * cur[1] + gv1 * cur[2] + gv2 * cur[3], gWvs = qv * cur[4];
+            if (!L0) gpvs = fmaf(qv, Wvs, gpvs);
+            const float gWs = gs * cur[0], gWvs = qv * cur[4];
+            const float gWvv = L0 ? 0.0f : gv0 * cur[1] + gv1 * cur[2] + gv2 * cur[3];
             const float tv = cur[4] * Wvs;
             const float pd = gWs * dWs + gWvv * dWvv + gWvs * dWvs;
             if (G4L) {
@@ -1688,6 +1694,7 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(true));
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     attr = true;
   }
@@ -1702,6 +1709,8 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
     else if (m.tc_adjoint_variant == 4)
       k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(true), st>>>(tm, a);
     // the usual basis size (K = 20) with a compile-time loop bound; G4: gradients interleaved
+    else if (m.K == 20 && G4 && t == 0 && !GPHI)   // first layer: v = 0, no phi gradients
+      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
     else if (m.K == 20 && G4)
       k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
     else if (G4)
