@@ -60,7 +60,8 @@ def _load():
                 f.restype = ctypes.c_int64
             lib.orc_param_count.argtypes = [ctypes.c_int32] * 4
             lib.orc_param_count.restype = ctypes.c_int64
-            lib.orc_painn.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, P, P, P, P, P, P, P]
+            lib.orc_painn.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, P, P, P, P, P, P,
+                                      P, P]
             lib.orc_painn.restype = ctypes.c_int
             lib.orc_nve.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, ctypes.c_double,
                                     ctypes.c_int32, P, P]
@@ -134,12 +135,14 @@ def param_count(F, K, T, S) -> int:
 
 
 def painn(params, F, K, T, S, species, positions, cell, pairs=None, rc=5.0, eps=1e-8,
-          e_scale=1.0, forces=True, virial=True):
+          e_scale=1.0, forces=True, virial=True, weights=None):
     """Energy, per-atom energies, forces and virial in FP64.
 
     ``pairs`` = (i, j, n) over the given positions (edges beyond rc are ignored); when None
-    they are found with the oracle's own cell search on wrapped positions.
-    Returns dict(energy, energies, forces [n,3] or None, virial [3,3] or None).
+    they are found with the oracle's own cell search on wrapped positions.  ``weights`` [n]
+    (default all ones): the energy is sum_i w_i U_i and forces / virial are its derivatives
+    (one processor's share of a spatial decomposition when w marks the owned atoms).
+    Returns dict(energy, energies (unweighted U_i), forces [n,3] or None, virial [3,3] or None).
     """
     lib = _load()
     params = _f64(params)
@@ -159,8 +162,11 @@ def painn(params, F, K, T, S, species, positions, cell, pairs=None, rc=5.0, eps=
     Ei = np.empty(n)
     Fo = np.empty((n, 3)) if forces else None
     Wv = np.empty((3, 3)) if virial else None
+    w = None if weights is None else _f64(weights)
+    if w is not None and w.shape != (n,):
+        raise ValueError("weights must have one entry per atom")
     rcode = lib.orc_painn(ctypes.byref(md), _p(params), n, _p(Z), _p(x), _p(H), pi.size, _p(pi),
-                          _p(pj), _p(pn), _p(E), _p(Ei), _p(Fo), _p(Wv))
+                          _p(pj), _p(pn), _p(w), _p(E), _p(Ei), _p(Fo), _p(Wv))
     if rcode != 0:
         raise RuntimeError(f"orc_painn failed with {rcode}")
     return {"energy": float(E[0]), "energies": Ei, "forces": Fo, "virial": Wv}

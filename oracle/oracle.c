@@ -276,10 +276,16 @@ static void radial(const orc_model *md, const orc_layer *L, double d, double fc,
 
 /* Energy, per-atom energies, forces and virial for the pair list (i <- j, n).  The list may
  * contain edges longer than rc (a Verlet list); they contribute nothing.
- * E: scalar; Ei[n] (may be NULL); Fo[n][3] (may be NULL); Wv[9] row-major (may be NULL). */
+ * w[n] (may be NULL = all ones): per-atom weights of the energy, E = sum_i w_i U_i, and the
+ * forces and virial are those of that weighted sum.  With w = 1 on the atoms a processor owns
+ * and 0 on its copied atoms this is one processor's share of the spatial decomposition (Results,
+ * "Distributed potential computation": the total energy is the sum of the owned atoms' U_i, the
+ * total force on an atom the sum of its copies' partial forces).
+ * E: scalar; Ei[n] (unweighted U_i, may be NULL); Fo[n][3] (may be NULL); Wv[9] row-major
+ * (may be NULL). */
 int orc_painn(const orc_model *md, const double *params, int64_t n, const int32_t *Z,
               const double *x, const double H[9], int64_t ne, const int32_t *pi, const int32_t *pj,
-              const int8_t *pn, double *E, double *Ei, double *Fo, double *Wv) {
+              const int8_t *pn, const double *w, double *E, double *Ei, double *Fo, double *Wv) {
   const int F = md->F, K = md->K, T = md->T, F3 = 3 * F, Fh = F / 2;
   if (T < 0 || T > ORC_MAXT || F < 2 || F > 512 || (F % 2) || K < 2 || K > 256) return ORC_EINVAL;
   orc_params P;
@@ -357,7 +363,7 @@ int orc_painn(const orc_model *md, const double *params, int64_t n, const int32_
     }
   }
 
-  /* readout: U_i = e_scale (R2 . silu(R1 s_i + d1) + d2), U = sum_i U_i */
+  /* readout: U_i = e_scale (R2 . silu(R1 s_i + d1) + d2), U = sum_i w_i U_i */
   double *sT = s_in + (int64_t)T * nF;
   double Etot = 0.0;
   for (int64_t i = 0; i < n; ++i) {
@@ -366,7 +372,7 @@ int orc_painn(const orc_model *md, const double *params, int64_t n, const int32_
     for (int k = 0; k < Fh; ++k) ei += P.R2[k] * silu(h3[i * Fh + k]);
     ei *= md->e_scale;
     if (Ei) Ei[i] = ei;
-    Etot += ei;
+    Etot += w ? w[i] * ei : ei;
   }
   *E = Etot;
 
@@ -376,10 +382,11 @@ int orc_painn(const orc_model *md, const double *params, int64_t n, const int32_
     double *gph = calloc((size_t)3 * nF, sizeof(double));
     double Wacc[9] = {0};
     if (Fo) memset(Fo, 0, sizeof(double) * 3 * n);
-    /* dU/ds^T */
+    /* dU/ds^T, seeded with dU/dU_i = w_i */
     for (int64_t i = 0; i < n; ++i) {
       double g3[512];
-      for (int k = 0; k < Fh; ++k) g3[k] = md->e_scale * P.R2[k] * dsilu(h3[i * Fh + k]);
+      const double wi = w ? w[i] : 1.0;
+      for (int k = 0; k < Fh; ++k) g3[k] = wi * md->e_scale * P.R2[k] * dsilu(h3[i * Fh + k]);
       matvec_T_add(P.R1, g3, Fh, F, &gs[i * F]);
     }
     for (int t = T - 1; t >= 0; --t) {
@@ -521,7 +528,7 @@ static int forces_at(const orc_model *md, const double *params, int64_t n, const
   int8_t *pn = malloc(3 * (np + 1));
   if (!pi || !pj || !pn) { free(xw); free(m); free(pi); free(pj); free(pn); return ORC_ENOMEM; }
   orc_pairs_cells(n, xw, H, md->rc, pi, pj, pn, np);
-  int rc = orc_painn(md, params, n, Z, xw, H, np, pi, pj, pn, E, NULL, Fo, NULL);
+  int rc = orc_painn(md, params, n, Z, xw, H, np, pi, pj, pn, NULL, E, NULL, Fo, NULL);
   free(xw); free(m); free(pi); free(pj); free(pn);
   return rc;
 }
