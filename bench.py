@@ -421,6 +421,9 @@ def run_ours(args):
 #   mixture90k 90,300-atom triclinic 4-species mixture, F=64, T=2: stored vs recomputed edge filters
 #   serve      512 replicas (log-uniform 64..20,000 atoms, water / fcc), Poisson arrivals swept
 #              around the saturation rate; p50/p99 latency vs serial per-system FP32 launches
+#   domains    the 1M-atom fcc system evaluated through a spatial domain decomposition with copied
+#              atoms (grids 1x1x1 ... 2x2x2, T-hop pruning on and off) against the periodic system:
+#              copies, edges, time, and the parallel efficiency of Results "Parallelization cost"
 
 
 def _init_engine():
@@ -693,6 +696,91 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_domains(args):
+    """E+F+W of the 1M-atom fcc system through ctd_domains_compute for several domain grids,
+    next to the periodic single-system call on the same positions (no neighbour rebuild inside
+    the timed calls).  For each grid: owned atoms + copies, copies before T-hop pruning, active
+    edges, ms per call, and the parallel efficiency eps = S / P with
+    S = prod_a (L_a + 2 T R) / (L_a / p_a + 2 T R) (the paper's speed-up estimate for P domains,
+    R = rc) beside the measured eps = t(1x1x1 with copies) / t(grid) (all domains of a grid run
+    on this one GPU, so the grid's time is the work P processors would share)."""
+    import synthetic as syn
+    eng, torch = _init_engine()
+    prec = "fp32" if args.precision == "fp32" else "bf16"
+    n_cells = args.cells
+    sy = syn.fcc(n_cells, n_cells, n_cells, seed=0)
+    n = sy.n
+    blob = syn.params_blob(F, K, T, 1, rc=RC, seed=0)
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    x = torch.tensor(sy.positions, device=dev)
+    z = torch.tensor(sy.species, device=dev, dtype=torch.int32)
+    reps = args.steps if args.steps_given else 5
+    warm = max(3, args.warmup)
+
+    def timed(obj):
+        for _ in range(warm):
+            out = obj.compute(z, x, sy.cell, stats=True)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = obj.compute(z, x, sy.cell, stats=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        assert out["stats"]["rebuilt"] == 0
+        return out, float(np.median(ms))
+
+    L = [float(np.linalg.norm(sy.cell[a])) for a in range(3)]
+    TR = T * RC
+    rows = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        with eng.Potential(F, K=K, T=T, n_species=1, rc=RC, precision=prec, params=blob,
+                           stream=stream.cuda_stream) as pot:
+            ref, t_ref = timed(pot)
+            f_ref = ref["forces"].double()
+            e_ref = float(ref["energy"].cpu()[0])
+            ref_edges = ref["stats"]["n_active_edges"]
+        for grid in [(1, 1, 1), (2, 1, 1), (2, 2, 1), (2, 2, 2)]:
+            for hop in ([True, False] if grid == (2, 2, 2) else [True]):
+                with eng.Domains(F, blob, grid=grid, K=K, T=T, n_species=1, rc=RC, precision=prec, hop_prune=hop,
+                                 skin=1.0, stream=stream.cuda_stream) as dom:
+                    out, t = timed(dom)
+                    info = dom.info()
+                    held = out["stats"]["bytes_allocated"]
+                P = grid[0] * grid[1] * grid[2]
+                S = float(np.prod([(L[a] + 2 * TR) / (L[a] / grid[a] + 2 * TR) for a in range(3)]))
+                df = (out["forces"].double() - f_ref)
+                rows.append({
+                    "grid": list(grid), "hop_prune": hop, "ms": t,
+                    "owned_plus_copies": int(sum(d["n_owned"] + d["n_copies"] for d in info)),
+                    "copies": int(sum(d["n_copies"] for d in info)),
+                    "copies_before_pruning": int(sum(d["n_candidates"] for d in info)),
+                    "active_edges": int(sum(d["n_active_edges"] for d in info)),
+                    "max_domain_atoms": int(max(d["n_owned"] + d["n_copies"] for d in info)),
+                    "bytes_held": int(held),
+                    "rel_dE_vs_periodic": abs(float(out["energy"].cpu()[0]) - e_ref) / abs(e_ref),
+                    "rel_force_rmse_vs_periodic": float(torch.sqrt((df ** 2).sum() / (f_ref ** 2).sum())),
+                    "paper_S": S, "paper_eps": S / P})
+    t1 = next(r["ms"] for r in rows if r["grid"] == [1, 1, 1])
+    for r in rows:
+        r["measured_eps"] = t1 / r["ms"]
+        r["work_vs_periodic"] = r["ms"] / t_ref
+    best = next(r for r in rows if r["grid"] == [2, 2, 2] and r["hop_prune"])
+    line = {"metric": "atom-steps/s of E+F+W through a 2x2x2 domain decomposition (1M fcc), grids and parallel "
+                      "efficiency", "value": n / (best["ms"] / 1e3), "unit": "atom-steps/s", "n_gpus": 1,
+            "steps": reps, "warmup": warm, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(n_cells) + "; E+F+W calls at fixed positions",
+                       "precision": prec, "halo": f"R_comm = T rc + skin = {T * RC + 1.0:g} A",
+                       "l2": "inputs larger than L2"},
+            "periodic": {"ms": t_ref, "atoms": n, "active_edges": int(ref_edges)},
+            "grids": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -711,7 +799,7 @@ def main():
     ap.add_argument("--chunk-rows", type=int, default=None,
                     help="rows per block-cyclic chunk of the bulk-gathered edge kernels (0: contiguous)")
     ap.add_argument("--workload", default="fcc1m",
-                    choices=["fcc1m", "water192", "water96k", "mixture90k", "serve"])
+                    choices=["fcc1m", "water192", "water96k", "mixture90k", "serve", "domains"])
     ap.add_argument("--replicas", type=int, default=512)
     ap.add_argument("--serve-steps", type=int, default=20)
     ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "bf16"])
@@ -725,7 +813,7 @@ def main():
         run_ours(args)
     else:
         {"water192": run_water192, "water96k": run_water96k, "mixture90k": run_mixture90k,
-         "serve": run_serve}[args.workload](args)
+         "serve": run_serve, "domains": run_domains}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -225,6 +225,56 @@ int ctd_serve_stats(ctd_server *s, int64_t *resident_atoms, int32_t *resident_re
 const char *ctd_serve_last_error(ctd_server *s);
 void ctd_serve_destroy(ctd_server *s);
 
+/* ---- spatial domain decomposition with copied atoms ---------------------------------------- */
+/* Results, "Distributed potential computation" (energy-sum and sum-rule equations) and
+ * "Parallelization cost": the periodic system is split into grid[0] x grid[1] x grid[2]
+ * domains over its fractional coordinates; each atom is owned by the domain whose box holds its
+ * wrapped position, and each domain also holds copies of every atom and periodic image within
+ * R_comm = T rc + skin of its box (measured perpendicular to the box faces).  A domain's energy
+ * is the sum of its owned atoms' U_i; the total energy is the sum over domains, and the force
+ * on an atom the sum of the partial forces on its copies.  With hop_prune != 0, copies more
+ * than T hops (over the neighbour graph with cutoff rc + skin) from every owned atom are
+ * dropped, and edges with neither atom within T - 1 hops are not evaluated; the results do not
+ * change (up to FP32 summation order).
+ *
+ * All domains run on this GPU as one batched system: this is the decomposition a run on
+ * grid[0] grid[1] grid[2] processors would compute, with its two exchanges (copy positions
+ * before the model, copy forces after it) as kernels.  ctd_domains_info reports the work the
+ * copies add.  desc / params / nbytes / hbm_budget_bytes / cuda_stream: as ctd_create and
+ * ctd_load_params.  grid[a] in 1..64 with at most 4096 domains; skin >= 0 (A).  Options
+ * (ctd_set_option) and profiling go through the context ctd_domains_context returns. */
+typedef struct ctd_domains ctd_domains;
+typedef struct {
+  int64_t n_owned;         /* atoms the domain owns                                           */
+  int64_t n_copies;        /* copies of other atoms (and periodic images) it evaluates         */
+  int64_t n_candidates;    /* copies within R_comm before hop pruning                          */
+  int64_t n_verlet_edges;  /* its neighbour pairs (cutoff rc + skin)                            */
+  int64_t n_active_edges;  /* its edges in the last evaluation (r < rc, hop test)               */
+  int32_t grid_index[3];   /* the domain's position in the grid                                 */
+  int32_t reserved;
+} ctd_domain_info;
+int ctd_domains_create(ctd_domains **out, const ctd_model_desc *desc, const void *params, size_t nbytes,
+                       size_t hbm_budget_bytes, const int32_t grid[3], int32_t hop_prune, double skin,
+                       void *cuda_stream);
+/* Energy, forces and virial of the periodic system by the decomposition, with the conventions
+ * and flags of ctd_compute (CTD_REBUILD forces a new decomposition).  The decomposition and
+ * the domains' neighbour lists are reused while no atom has moved more than skin / 2 since
+ * they were built; n or cell changing also rebuilds them.  forces[n][3] in the caller's order
+ * are the summed partial forces of each atom's copies (FP64 sums in a fixed order); per-atom
+ * energies (ctd_set_energy_out on the context) come from each atom's owned copy.  stats:
+ * n_atoms counts owned atoms plus copies, the edge counts are summed over the domains. */
+int ctd_domains_compute(ctd_domains *d, int64_t n, const int32_t *species, const double *positions,
+                        const double cell[9], int32_t flags, double *energy, double *forces,
+                        double *virial, ctd_stats *stats);
+/* Counts of domain index `domain` (0 <= domain < grid[0] grid[1] grid[2], row-major over the
+ * grid) from the last ctd_domains_compute; CTD_ERR_STATE before the first. */
+int ctd_domains_info(ctd_domains *d, int32_t domain, ctd_domain_info *info);
+/* The batched context behind the decomposition (model options, profiling, per-atom energies);
+ * owned by the decomposition, do not destroy it. */
+ctd_ctx *ctd_domains_context(ctd_domains *d);
+const char *ctd_domains_last_error(ctd_domains *d);
+void ctd_domains_destroy(ctd_domains *d);
+
 /* ---- neighbour list without device allocation ------------------------------------------ */
 /* The paper has no counterpart to this call; it exists for callers of this library that must
  * not allocate device memory: an MD code that manages a fixed device memory pool and cannot

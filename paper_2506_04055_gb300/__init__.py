@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (CTD_DEVICE_PTRS, CTD_NEED_FORCES, CTD_NEED_VIRIAL, CTD_PREC_BF16,  # noqa: F401
                    CTD_PREC_FP32, CTD_REBUILD, CtdError, ctd_model_desc, ctd_stats)
 
-__all__ = ["Potential", "Server", "PaiNNEnergy", "CtdError", "build", "load"]
+__all__ = ["Potential", "Server", "Domains", "PaiNNEnergy", "CtdError", "build", "load"]
 
 
 def build(force: bool = False) -> str:
@@ -49,6 +49,48 @@ def _ptr(a):
     if isinstance(a, np.ndarray):
         return a.ctypes.data_as(ctypes.c_void_p)
     return ctypes.c_void_p(a.data_ptr())
+
+
+def _compute(call, ctx, species, positions, cell, forces, virial, rebuild, stats, energies):
+    """Marshal one energy / forces / virial call: numpy -> host pointers, CUDA torch tensors ->
+    device pointers; ``call(n, z, x, H, flags, E, F, W, stats)`` runs the C entry point and
+    ``ctx`` is the context whose per-atom energy output is set around it."""
+    H = _host(cell, np.float64, (3, 3))
+    flags = (CTD_NEED_FORCES if forces else 0) | (CTD_NEED_VIRIAL if virial else 0)
+    flags |= CTD_REBUILD if rebuild else 0
+    st = ctd_stats() if stats else None
+    if _is_torch_cuda(positions):
+        import torch
+        dev = positions.device
+        x = positions.detach().to(torch.float64).contiguous()
+        z = species.to(device=dev, dtype=torch.int32).contiguous()
+        n = int(x.shape[0])
+        E = torch.zeros(1, dtype=torch.float64, device=dev)
+        Fo = torch.empty((n, 3), dtype=torch.float64, device=dev) if forces else None
+        W = torch.empty((3, 3), dtype=torch.float64, device=dev) if virial else None
+        Ea = torch.empty(n, dtype=torch.float64, device=dev) if energies else None
+        flags |= CTD_DEVICE_PTRS
+        # inputs were produced on torch's stream; the context runs on its own stream
+        torch.cuda.current_stream(dev).synchronize()
+    else:
+        x = _host(positions, np.float64, (-1, 3))
+        z = _host(species, np.int32)
+        n = int(x.shape[0])
+        E = np.zeros(1)
+        Fo = np.empty((n, 3)) if forces else None
+        W = np.empty((3, 3)) if virial else None
+        Ea = np.empty(n) if energies else None
+    _lib.ctd_set_energy_out(ctx, _ptr(Ea))
+    try:
+        call(n, _ptr(z), _ptr(x), _ptr(H), flags, _ptr(E), _ptr(Fo), _ptr(W), st)
+    finally:
+        _lib.ctd_set_energy_out(ctx, None)
+    out = {"energy": E if flags & CTD_DEVICE_PTRS else float(E[0]), "forces": Fo, "virial": W}
+    if energies:
+        out["energies"] = Ea
+    if stats:
+        out["stats"] = {k: getattr(st, k) for k, _ in ctd_stats._fields_}
+    return out
 
 
 class Potential:
@@ -119,43 +161,9 @@ class Potential:
         """Energy (eV), forces [n,3] (eV/A), virial [3,3] (eV).  numpy inputs -> numpy outputs
         (host pointers through the ABI); CUDA torch tensors -> CUDA torch tensors (device
         pointers, the context's stream)."""
-        H = _host(cell, np.float64, (3, 3))
-        flags = (CTD_NEED_FORCES if forces else 0) | (CTD_NEED_VIRIAL if virial else 0)
-        flags |= CTD_REBUILD if rebuild else 0
-        st = ctd_stats() if stats else None
-        if _is_torch_cuda(positions):
-            import torch
-            dev = positions.device
-            x = positions.detach().to(torch.float64).contiguous()
-            z = species.to(device=dev, dtype=torch.int32).contiguous()
-            n = int(x.shape[0])
-            E = torch.zeros(1, dtype=torch.float64, device=dev)
-            Fo = torch.empty((n, 3), dtype=torch.float64, device=dev) if forces else None
-            W = torch.empty((3, 3), dtype=torch.float64, device=dev) if virial else None
-            Ea = torch.empty(n, dtype=torch.float64, device=dev) if energies else None
-            flags |= CTD_DEVICE_PTRS
-            # inputs were produced on torch's stream; the context runs on its own stream
-            torch.cuda.current_stream(dev).synchronize()
-        else:
-            x = _host(positions, np.float64, (-1, 3))
-            z = _host(species, np.int32)
-            n = int(x.shape[0])
-            E = np.zeros(1)
-            Fo = np.empty((n, 3)) if forces else None
-            W = np.empty((3, 3)) if virial else None
-            Ea = np.empty(n) if energies else None
-        _lib.ctd_set_energy_out(self.ctx, _ptr(Ea))
-        try:
-            _lib.ctd_compute(self.ctx, n, _ptr(z), _ptr(x), _ptr(H), flags, _ptr(E), _ptr(Fo),
-                             _ptr(W), st)
-        finally:
-            _lib.ctd_set_energy_out(self.ctx, None)
-        out = {"energy": E if flags & CTD_DEVICE_PTRS else float(E[0]), "forces": Fo, "virial": W}
-        if energies:
-            out["energies"] = Ea
-        if stats:
-            out["stats"] = {k: getattr(st, k) for k, _ in ctd_stats._fields_}
-        return out
+        def call(n, z, x, H, flags, E, Fo, W, st):
+            _lib.ctd_compute(self.ctx, n, z, x, H, flags, E, Fo, W, st)
+        return _compute(call, self.ctx, species, positions, cell, forces, virial, rebuild, stats, energies)
 
     # -- launch accounting ------------------------------------------------------------------
     def profile(self, enable: bool = True):
@@ -253,6 +261,61 @@ class Server:
 
     def stats(self):
         return _lib.ctd_serve_stats(self.srv)
+
+
+class Domains:
+    """Spatial domain decomposition of one periodic system (see ctd_domains_* in
+    include/painn.h): grid = (p0, p1, p2) domains, each with copies of the atoms within
+    T rc + skin of its box; copies more than T hops from the domain's own atoms are dropped when
+    hop_prune is set.  compute() returns what Potential.compute returns, from the summed domain
+    energies and the summed partial forces of each atom's copies; info() the per-domain counts."""
+
+    def __init__(self, F: int, params: bytes, grid=(2, 2, 2), K: int = 20, T: int = 3, n_species: int = 2,
+                 rc: float = 5.0, precision: str = "fp32", hop_prune: bool = True, skin: float = 1.0,
+                 hbm_budget_bytes: int = 0, stream: int | None = None):
+        prec = {"fp32": CTD_PREC_FP32, "bf16": CTD_PREC_BF16}[precision]
+        self.desc = ctd_model_desc(F, K, T, n_species, rc, prec)
+        self.grid = tuple(int(g) for g in grid)
+        self.dom = _lib.ctd_domains_create(self.desc, params, self.grid, hop_prune, skin, hbm_budget_bytes, stream)
+        self.ctx = _lib.ctd_domains_context(self.dom)
+
+    def close(self):
+        if getattr(self, "dom", None):
+            _lib.ctd_domains_destroy(self.dom)
+            self.dom = None
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, option: int, value: int):
+        _lib.ctd_set_option(self.ctx, option, value)
+
+    def compute(self, species, positions, cell, forces: bool = True, virial: bool = True,
+                rebuild: bool = False, stats: bool = False, energies: bool = False):
+        def call(n, z, x, H, flags, E, Fo, W, st):
+            _lib.ctd_domains_compute(self.dom, n, z, x, H, flags, E, Fo, W, st)
+        return _compute(call, self.ctx, species, positions, cell, forces, virial, rebuild, stats, energies)
+
+    def info(self):
+        """Per-domain counts (owned atoms, copies kept, copies before pruning, edges)."""
+        n = self.grid[0] * self.grid[1] * self.grid[2]
+        return [_lib.ctd_domains_info(self.dom, d) for d in range(n)]
+
+    def profile(self, enable: bool = True):
+        _lib.ctd_profile_enable(self.ctx, enable)
+
+    def profile_read(self, reset: bool = True):
+        return _lib.ctd_profile_read(self.ctx, reset)
 
 
 def _make_autograd():

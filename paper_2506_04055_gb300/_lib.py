@@ -42,7 +42,9 @@ EXPORTS = [
     "ctd_set_energy_out", "ctd_md_set_state", "ctd_md_run", "ctd_md_get_state",
     "ctd_set_option", "ctd_profile_enable", "ctd_profile_read", "ctd_gemm_bf16",
     "ctd_serve_create", "ctd_serve_submit", "ctd_serve_step", "ctd_serve_poll", "ctd_serve_stats",
-    "ctd_serve_last_error", "ctd_serve_destroy", "ctd_neighbors_noalloc",
+    "ctd_serve_last_error", "ctd_serve_destroy", "ctd_domains_create", "ctd_domains_compute",
+    "ctd_domains_info", "ctd_domains_context", "ctd_domains_last_error", "ctd_domains_destroy",
+    "ctd_neighbors_noalloc",
     "ctd_last_error",
     "ctd_destroy",
 ]
@@ -64,6 +66,12 @@ class ctd_stats(ctypes.Structure):
                 ("bytes_allocated", ctypes.c_int64), ("ms_neighbors", ctypes.c_float),
                 ("ms_model", ctypes.c_float), ("edges_stored", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class ctd_domain_info(ctypes.Structure):
+    _fields_ = [("n_owned", ctypes.c_int64), ("n_copies", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+                ("n_verlet_edges", ctypes.c_int64), ("n_active_edges", ctypes.c_int64),
+                ("grid_index", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32)]
 
 
 class CtdError(RuntimeError):
@@ -106,6 +114,12 @@ def load(path: str = LIB_PATH):
         "ctd_serve_stats": ([P, P, P, P, P], ctypes.c_int),
         "ctd_serve_last_error": ([P], ctypes.c_char_p),
         "ctd_serve_destroy": ([P], None),
+        "ctd_domains_create": ([P, P, P, ctypes.c_size_t, ctypes.c_size_t, P, I32, D, P], ctypes.c_int),
+        "ctd_domains_compute": ([P, I64, P, P, P, I32, P, P, P, P], ctypes.c_int),
+        "ctd_domains_info": ([P, I32, P], ctypes.c_int),
+        "ctd_domains_context": ([P], P),
+        "ctd_domains_last_error": ([P], ctypes.c_char_p),
+        "ctd_domains_destroy": ([P], None),
         "ctd_last_error": ([P], ctypes.c_char_p),
         "ctd_destroy": ([P], None),
     }
@@ -258,6 +272,47 @@ def ctd_serve_stats(srv):
 
 def ctd_serve_destroy(srv):
     load().ctd_serve_destroy(srv)
+
+
+def domains_check(dom, code):
+    if code != CTD_OK:
+        msg = load().ctd_domains_last_error(dom)
+        raise CtdError(code, msg.decode() if msg else "")
+    return code
+
+
+def ctd_domains_create(desc, blob, grid, hop_prune=True, skin=1.0, hbm_budget_bytes=0, cuda_stream=None):
+    dom = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid])
+    code = load().ctd_domains_create(ctypes.byref(dom), ctypes.byref(desc), buf, len(blob), hbm_budget_bytes,
+                                     g, 1 if hop_prune else 0, float(skin), cuda_stream)
+    if code != CTD_OK:
+        raise CtdError(code, "ctd_domains_create failed")
+    return dom
+
+
+def ctd_domains_compute(dom, n, species_ptr, positions_ptr, cell_ptr, flags, energy_ptr, forces_ptr,
+                        virial_ptr, stats=None):
+    return domains_check(dom, load().ctd_domains_compute(dom, n, species_ptr, positions_ptr, cell_ptr, flags,
+                                                         energy_ptr, forces_ptr, virial_ptr,
+                                                         ctypes.byref(stats) if stats is not None else None))
+
+
+def ctd_domains_info(dom, domain):
+    info = ctd_domain_info()
+    domains_check(dom, load().ctd_domains_info(dom, domain, ctypes.byref(info)))
+    out = {k: getattr(info, k) for k, _ in ctd_domain_info._fields_ if k not in ("grid_index", "reserved")}
+    out["grid_index"] = tuple(info.grid_index)
+    return out
+
+
+def ctd_domains_context(dom):
+    return ctypes.c_void_p(load().ctd_domains_context(dom))
+
+
+def ctd_domains_destroy(dom):
+    load().ctd_domains_destroy(dom)
 
 
 def ctd_last_error(ctx) -> str:

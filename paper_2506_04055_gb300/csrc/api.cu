@@ -145,6 +145,7 @@ int check_status(ctd_ctx* c) {
   if (st & ST_REV_MISSING) return fail(c, CTD_ERR_CAPACITY, "reverse edge missing in the neighbour list");
   if (st & ST_NONFINITE) return fail(c, CTD_ERR_NONFINITE, "non-finite value in positions or results");
   if (st & ST_TIMEOUT) return fail(c, CTD_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (st & ST_OWNERSHIP) return fail(c, CTD_ERR_STATE, "domain decomposition: an atom is not owned exactly once");
   return CTD_OK;
 }
 
@@ -246,16 +247,30 @@ int prune(ctd_ctx* c, double* maxdisp_out) {
     *maxdisp_out = std::sqrt((double)d2);
   }
   const float rc2 = (float)(c->desc.rc * c->desc.rc);
+  const uint8_t* near = c->use_near ? P<uint8_t>(c->near) : nullptr;
   launch_prune(st, false, n, P<int32_t>(c->vrow), P<int32_t>(c->vcol), P<float4>(c->vbase), P<float4>(c->delta),
-               rc2, P<int32_t>(c->acount), nullptr, nullptr, nullptr, nullptr, nullptr);
+               rc2, near, P<int32_t>(c->acount), nullptr, nullptr, nullptr, nullptr, nullptr);
   launch_exclusive_scan(st, n, P<int32_t>(c->acount), P<int32_t>(c->arow), c->scan_tmp.p);
   launch_prune(st, true, n, P<int32_t>(c->vrow), P<int32_t>(c->vcol), P<float4>(c->vbase), P<float4>(c->delta),
-               rc2, P<int32_t>(c->acount), P<int32_t>(c->arow), P<int32_t>(c->acol), P<float4>(c->ar),
+               rc2, near, P<int32_t>(c->acount), P<int32_t>(c->arow), P<int32_t>(c->acol), P<float4>(c->ar),
                P<int32_t>(c->vidx), P<int32_t>(c->v2a));
   launch_prune_rev(st, n, P<int32_t>(c->arow), P<int32_t>(c->vidx), P<int32_t>(c->vrev), P<int32_t>(c->v2a),
                    P<int32_t>(c->arev), P<int32_t>(c->aend));
   CUDA_OK(c, cudaGetLastError());
   return CTD_OK;
+}
+
+// Device bytes per atom of the model's activation buffers (FP32 and, on the BF16 path, the
+// BF16 operand copies), as evaluate() allocates them.
+size_t model_bytes_per_atom(const ctd_ctx* c) {
+  const int F = c->desc.F, T = c->desc.T;
+  const bool g4 = model_uses_g4(c->mw, c->desc.precision);
+  size_t bytes = 0;
+  for (int b = 0; b < model_buffer_count(); ++b) bytes += sizeof(float) * (size_t)model_buffer_floats_per_atom(b, F, T, g4);
+  if (c->desc.precision == CTD_PREC_BF16)
+    for (int b = 0; b < model_bf16_buffer_count(); ++b)
+      bytes += sizeof(__nv_bfloat16) * (size_t)model_bf16_buffer_elems_per_atom(b, F, T);
+  return bytes;
 }
 
 // Model evaluation on the current active list; forces (sorted, FP32) in c->force_s,
@@ -267,8 +282,9 @@ int evaluate(ctd_ctx* c, bool need_grad) {
   const int nb = model_buffer_count();
   if ((int)c->mbuf.size() < nb) c->mbuf.resize(nb);
   std::vector<float*> ptrs(nb, nullptr);
+  const bool g4 = model_uses_g4(c->mw, c->desc.precision);
   for (int b = 0; b < nb; ++b) {
-    int64_t per = model_buffer_floats_per_atom(b, F, T);
+    int64_t per = model_buffer_floats_per_atom(b, F, T, g4);
     if (per == 0) continue;
     size_t bytes = sizeof(float) * (size_t)per * (size_t)n1;
     ENSURE(c, c->mbuf[b], bytes);
@@ -282,6 +298,7 @@ int evaluate(ctd_ctx* c, bool need_grad) {
   ENSURE(c, c->out_e, sizeof(double) * 4);
   ENSURE(c, c->out_w, sizeof(double) * 9);
   if (T == 0) CUDA_OK(c, cudaMemsetAsync(c->hedge.p, 0, sizeof(float4) * e1, st));
+  const float* ew = c->use_ew ? P<float>(c->ew) : nullptr;
   // Edge filters stored for the adjoint when asked for and when they fit: within the HBM
   // budget if one is set, and within 80 % of the device's free memory; recomputed otherwise.
   float* wst = nullptr;
@@ -313,13 +330,13 @@ int evaluate(ctd_ctx* c, bool need_grad) {
                                           P<float4>(c->ar), P<int32_t>(c->arev), ptrs.data(), bptrs.data(), need_grad,
                                           P<double>(c->epart), kPartials, P<float4>(c->hedge), P<float>(c->force_s),
                                           P<double>(c->vpart), kPartials, P<float>(c->eatom), P<int>(c->status),
-                                          wst, wlayer, P<int32_t>(c->aend));
+                                          wst, wlayer, P<int32_t>(c->aend), ew);
     if (bad) return fail(c, CTD_ERR_INVALID_ARG, "BF16 path: unsupported GEMM shape");
   } else {
     model_forward_backward_fp32(st, c->mw, n, P<int32_t>(c->z_s), P<int32_t>(c->arow), P<int32_t>(c->acol),
                                 P<float4>(c->ar), P<int32_t>(c->arev), ptrs.data(), need_grad, P<double>(c->epart),
                                 kPartials, P<float4>(c->hedge), P<float>(c->force_s), P<double>(c->vpart),
-                                kPartials, P<float>(c->eatom), P<int>(c->status), wst, wlayer);
+                                kPartials, P<float>(c->eatom), P<int>(c->status), wst, wlayer, ew);
   }
   StageGuard sg(STG_FORCES);
   launch_sum_partials(st, kPartials, 1, P<double>(c->epart), P<double>(c->out_e), 1.0);

@@ -78,6 +78,7 @@ enum Status : int {
   ST_VERLET_OVERFLOW = 2, // more Verlet edges than capacity
   ST_NONFINITE = 4,
   ST_TIMEOUT = 8,         // a bounded device wait gave up
+  ST_OWNERSHIP = 16,      // a spatial decomposition left an atom without exactly one owned copy
 };
 
 // FP32 weights of one interaction layer (device pointers).  "t" = transposed ([in][out]).
@@ -143,7 +144,7 @@ void launch_delta(cudaStream_t st, int64_t n, const double* x_s, const double* x
 void launch_gather_positions(cudaStream_t st, int64_t n, const int32_t* perm, const double* x_user,
                              double* x_s);
 void launch_prune(cudaStream_t st, bool fill, int64_t n, const int32_t* vrow, const int32_t* vcol,
-                  const float4* vbase, const float4* delta, float rc2, int32_t* acount,
+                  const float4* vbase, const float4* delta, float rc2, const uint8_t* near, int32_t* acount,
                   const int32_t* arow, int32_t* acol, float4* ar, int32_t* vidx, int32_t* v2a);
 void launch_prune_rev(cudaStream_t st, int64_t n, const int32_t* arow, const int32_t* vidx,
                       const int32_t* vrev, const int32_t* v2a, int32_t* arev,
@@ -182,7 +183,8 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, 
               __nv_bfloat16* outb, int ldob, int* status);
 // model_fp32.cu
 int model_buffer_count();
-int64_t model_buffer_floats_per_atom(int b, int F, int T);
+bool model_uses_g4(const ModelW& m, int precision);
+int64_t model_buffer_floats_per_atom(int b, int F, int T, bool g4);
 int model_bf16_buffer_count();
 int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T);
 int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
@@ -190,11 +192,13 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
                                 float* const* bufs, __nv_bfloat16* const* bbufs, bool need_grad,
                                 double* energy_partials, int n_energy_partials, float4* hedge, float* force_s,
                                 double* virial_partials, int n_virial_partials, float* e_atom, int* status,
-                                float* wstore, int64_t wstore_layer_floats, const int32_t* aend);
+                                float* wstore, int64_t wstore_layer_floats, const int32_t* aend,
+                                const float* ew);
 void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
                                  const int32_t* arow, const int32_t* acol, const float4* ar,
                                  const int32_t* arev, float* const* bufs, bool need_grad,
                                  double* energy_partials, int n_energy_partials, float4* hedge,
                                  float* force_s, double* virial_partials, int n_virial_partials,
-                                 float* e_atom, int* status, float* wstore, int64_t wstore_layer_floats);
+                                 float* e_atom, int* status, float* wstore, int64_t wstore_layer_floats,
+                                 const float* ew);
 }  // namespace ctd

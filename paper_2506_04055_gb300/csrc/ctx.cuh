@@ -55,6 +55,8 @@ struct ctd_ctx {
   DBuf acount, arow, acol, ar, vidx, arev, aend, hedge, force_s, eatom, epart, vpart, kpart, scan_tmp;
   DBuf out_e, out_f, out_w, out_eatom;
   DBuf wstore;              // per-edge filters [T][E][6F] when edge storage is on
+  DBuf ew, near;            // per-atom energy weights and hop flags of a spatial decomposition
+  bool use_ew = false, use_near = false;
   bool last_stored = false;  // the last evaluation stored edge filters
   std::vector<DBuf> mbuf, mbufb;
   double* energy_out_user = nullptr;
@@ -70,7 +72,7 @@ struct ctd_ctx {
                     &tmp_idx, &perm, &inv_perm, &xw_s, &xref_s, &z_s, &x_s, &count, &vrow, &vcol, &vimg,
                     &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev, &aend,
                     &hedge, &force_s, &eatom, &epart, &vpart, &kpart, &scan_tmp, &out_e, &out_f, &out_w,
-                    &out_eatom, &wstore, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp};
+                    &out_eatom, &wstore, &ew, &near, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp};
     for (DBuf* b : list) all.push_back(b);
   }
 };
@@ -96,6 +98,7 @@ int check_status(ctd_ctx* c);
 int copy_in(ctd_ctx* c, void* dst, const void* src, size_t bytes, bool device);
 int prune(ctd_ctx* c, double* maxdisp_out);
 int evaluate(ctd_ctx* c, bool need_grad);
+size_t model_bytes_per_atom(const ctd_ctx* c);
 
 }  // namespace ctd
 

@@ -24,6 +24,7 @@
 // gradients; per-edge position gradients go to hedge[e] and the forces are assembled from
 // hedge and the reverse-edge index, again without atomics.
 #include "ctd_internal.cuh"
+#include "../../include/painn.h"
 
 namespace ctd {
 
@@ -623,25 +624,30 @@ __global__ __launch_bounds__(256) void k_edge_bwd(int64_t n, int F, int K, float
 
 // ================================================================================ readout, forces
 // h3 = R1 s + d1 (done by the GEMM); U_i = e_scale (R2 . silu(h3) + d2);
-// G3 = e_scale R2 * silu'(h3) (seed of the backward pass); per-block FP64 energy partials.
+// G3 = w_i e_scale R2 * silu'(h3) (seed of the backward pass); per-block FP64 partials of
+// sum_i w_i U_i.  ew (null: all ones) weights each atom's energy: 1 for the atoms a domain owns,
+// 0 for its copies of other domains' atoms (Results, "Distributed potential computation").
+// e_atom receives w_i U_i.
 __global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restrict__ H3,
                           const float* __restrict__ R2, const float* __restrict__ d2,
-                          float* __restrict__ G3, __nv_bfloat16* __restrict__ G3b, float* __restrict__ e_atom,
-                          double* __restrict__ partials) {
+                          const float* __restrict__ ew, float* __restrict__ G3, __nv_bfloat16* __restrict__ G3b,
+                          float* __restrict__ e_atom, double* __restrict__ partials) {
   __shared__ double sbuf[kThreads / 32];
   double acc = 0.0, comp = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float wi = ew ? ew[i] : 1.0f;
     float e = d2[0];
     for (int k = 0; k < Fh; ++k) {
       float h = H3[i * Fh + k];
       e = fmaf(R2[k], silu_f(h), e);
       if (G3) {
-        const float gk = e_scale * R2[k] * dsilu_f(h);
+        const float gk = wi * (e_scale * R2[k] * dsilu_f(h));
         G3[i * Fh + k] = gk;
         if (G3b) G3b[i * Fh + k] = __float2bfloat16_rn(gk);
       }
     }
     e *= e_scale;
+    e *= wi;
     if (e_atom) e_atom[i] = e;
     double x = (double)e, t = acc + x;   // Neumaier
     comp += fabs(acc) >= fabs(x) ? (acc - t) + x : (x - t) + acc;
@@ -798,7 +804,13 @@ enum BufId {
 int model_buffer_count() { return B_COUNT; }
 
 // floats per atom of buffer id b (0 if unused for this T)
-int64_t model_buffer_floats_per_atom(int b, int F, int T) {
+// The interleaved receiver gradients (G4) are read only by the bulk-gathered tensor-core
+// adjoint of the BF16 path; no other path allocates them.
+bool model_uses_g4(const ModelW& m, int precision) {
+  return precision == CTD_PREC_BF16 && edge_tc_supported(m.F, m.K) && m.tc_adjoint && m.tc_adjoint_variant == 2;
+}
+
+int64_t model_buffer_floats_per_atom(int b, int F, int T, bool g4) {
   auto layer = [&](int base, int cnt) { return b >= base && b < base + cnt; };
   if (layer(B_S0, T + 1)) return F;
   if (layer(B_V0, T + 1)) return 3 * F;
@@ -815,7 +827,7 @@ int64_t model_buffer_floats_per_atom(int b, int F, int T) {
     case B_GS: case B_GSM: return F;
     case B_GV: case B_GVM: return 3 * F;
     case B_GPHI: return 5 * F;
-    case B_G4: return 4 * F;
+    case B_G4: return g4 ? 4 * F : 0;
     case B_H3: case B_G3: return F / 2;
     default: return 0;
   }
@@ -826,7 +838,8 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
                                  const int32_t* arev, float* const* B, bool need_grad,
                                  double* energy_partials, int n_energy_partials, float4* hedge,
                                  float* force_s, double* virial_partials, int n_virial_partials,
-                                 float* e_atom, int* status, float* wstore, int64_t wstore_layer_floats) {
+                                 float* e_atom, int* status, float* wstore, int64_t wstore_layer_floats,
+                                 const float* ew) {
   edge_smem_setup();
   StageGuard node_stage(STG_NODE);
   const int F = m.F, T = m.T, Fh = F / 2;
@@ -858,7 +871,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
   }
   // readout
   gemm<EPI_BIAS>(st, n, Fh, F, B[B_S0 + T], F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
-  { LaunchScope ls_(st); k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2,
+  { LaunchScope ls_(st); k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2, ew,
                                                     need_grad ? B[B_G3] : nullptr, nullptr, e_atom, energy_partials); }
   if (!need_grad) return;
   // dU/ds^T = G3 R1
@@ -934,7 +947,8 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
                                 float* const* B, __nv_bfloat16* const* Bb, bool need_grad,
                                 double* energy_partials, int n_energy_partials, float4* hedge, float* force_s,
                                 double* virial_partials, int n_virial_partials, float* e_atom, int* status,
-                                float* wstore, int64_t wstore_layer_floats, const int32_t* aend) {
+                                float* wstore, int64_t wstore_layer_floats, const int32_t* aend,
+                                const float* ew) {
   edge_smem_setup();
   StageGuard node_stage(STG_NODE);
   const int F = m.F, T = m.T, Fh = F / 2;
@@ -946,6 +960,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   // applies to the CUDA-core edge kernels only.
   const bool use_tc = edge_tc_supported(F, m.K);
   const bool use_tc_bwd = use_tc && m.tc_adjoint;
+  const bool g4 = model_uses_g4(m, CTD_PREC_BF16);
   if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], Bb[BB_S0]); }
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
@@ -980,7 +995,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   gemm<EPI_BIAS>(st, n, Fh, F, B[B_S0 + T], F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
   {
     LaunchScope ls_(st);
-    k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2,
+    k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2, ew,
                                                       need_grad ? B[B_G3] : nullptr, nullptr, e_atom,
                                                       energy_partials);
   }
@@ -997,7 +1012,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GA], 3 * F, L.A2tb, nullptr, H2, F, nullptr, 0, Bb[BB_GH2], F, status);
     bad |= gemm_bf16<0>(st, n, 2 * F, F, Bb[BB_GH2], F, L.A1tb, nullptr, nullptr, 0, T1, 2 * F, nullptr, 0, status);
     // the bulk-gathered tensor-core adjoint reads gsm and gvm interleaved per feature (G4)
-    float* G4 = (use_tc_bwd && m.tc_adjoint_variant == 2) ? B[B_G4] : nullptr;
+    float* G4 = g4 ? B[B_G4] : nullptr;
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid_bf16<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, AV, GSM, Bb[BB_GUV]); }
     bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
     if (G4 && n > 0) { LaunchScope ls_(st); k_interleave_g4<<<nb, kThreads, 0, st>>>(n, F, GSM, GVM, reinterpret_cast<float4*>(G4)); }

@@ -280,13 +280,16 @@ void launch_delta(cudaStream_t st, int64_t n, const double* x_s, const double* x
 template <bool FILL>
 __global__ void k_prune(int64_t n, const int32_t* __restrict__ vrow, const int32_t* __restrict__ vcol,
                         const float4* __restrict__ vbase, const float4* __restrict__ delta, float rc2,
-                        int32_t* __restrict__ acount, const int32_t* __restrict__ arow,
-                        int32_t* __restrict__ acol, float4* __restrict__ ar, int32_t* __restrict__ vidx,
-                        int32_t* __restrict__ v2a) {
+                        const uint8_t* __restrict__ near, int32_t* __restrict__ acount,
+                        const int32_t* __restrict__ arow, int32_t* __restrict__ acol, float4* __restrict__ ar,
+                        int32_t* __restrict__ vidx, int32_t* __restrict__ v2a) {
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (i >= n) return;
   const float4 di = delta[i];
+  // near (null: keep all): an edge is kept only if one of its atoms is within T - 1 hops of an
+  // owned atom of its domain; the test is symmetric, so every kept edge keeps its reverse.
+  const bool near_i = near == nullptr || near[i] != 0;
   int out = FILL ? arow[i] : 0, cnt = 0;
   const int b = vrow[i], e = vrow[i + 1];
   for (int e0 = b; e0 < e; e0 += 32) {
@@ -301,7 +304,7 @@ __global__ void k_prune(int64_t n, const int32_t* __restrict__ vrow, const int32
       ry = bb.y + (dj.y - di.y);
       rz = bb.z + (dj.z - di.z);
       r2 = rx * rx + ry * ry + rz * rz;
-      keep = r2 < rc2;
+      keep = r2 < rc2 && (near_i || near[j] != 0);
     }
     unsigned m = __ballot_sync(0xffffffffu, keep);
     if (FILL) {
@@ -319,15 +322,15 @@ __global__ void k_prune(int64_t n, const int32_t* __restrict__ vrow, const int32
 }
 
 void launch_prune(cudaStream_t st, bool fill, int64_t n, const int32_t* vrow, const int32_t* vcol,
-                  const float4* vbase, const float4* delta, float rc2, int32_t* acount,
+                  const float4* vbase, const float4* delta, float rc2, const uint8_t* near, int32_t* acount,
                   const int32_t* arow, int32_t* acol, float4* ar, int32_t* vidx, int32_t* v2a) {
   if (n == 0) return;
   int64_t threads = n * 32;
   unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
   if (fill)
-    { LaunchScope ls_(st); k_prune<true><<<blocks, kThreads, 0, st>>>(n, vrow, vcol, vbase, delta, rc2, acount, arow, acol, ar, vidx, v2a); }
+    { LaunchScope ls_(st); k_prune<true><<<blocks, kThreads, 0, st>>>(n, vrow, vcol, vbase, delta, rc2, near, acount, arow, acol, ar, vidx, v2a); }
   else
-    { LaunchScope ls_(st); k_prune<false><<<blocks, kThreads, 0, st>>>(n, vrow, vcol, vbase, delta, rc2, acount, arow, acol, ar, vidx, v2a); }
+    { LaunchScope ls_(st); k_prune<false><<<blocks, kThreads, 0, st>>>(n, vrow, vcol, vbase, delta, rc2, near, acount, arow, acol, ar, vidx, v2a); }
 }
 
 __global__ void k_prune_rev(int64_t n_active, const int32_t* __restrict__ vidx,

@@ -195,11 +195,17 @@ void free_buf(ctd_ctx* c, DBuf& b) {
   }
 }
 
-// Device bytes a replica is expected to need (model buffers, edge lists, state), for admission.
-size_t estimate_bytes(const ctd_model_desc& d, int64_t n) {
-  const int64_t per_atom_model = 110LL * d.F * 4 + 64LL * d.F;   // FP32 activations + BF16 shadows
-  const int64_t edges = 120 * n;                                 // Verlet edges per atom, upper estimate
-  return (size_t)(n * (per_atom_model + 200) + edges * 80);
+// Device bytes a replica is expected to need (model buffers as evaluate() sizes them, edge
+// lists, state), for admission.  Per Verlet edge: the replica's own list and the batch copy
+// (vcol, vbase, vrev: 24 B each), the Verlet -> active map (4 B) and the active list (acol,
+// ar, vidx, arev, aend, hedge: 48 B); 120 Verlet edges per atom bound the water and fcc
+// densities at rc + skin = 6 A.  The batch buffers only grow and take 25 % headroom when they
+// do (ensure()), so the estimate carries that factor too.
+size_t estimate_bytes(const ctd_ctx* c, int64_t n) {
+  const int64_t per_atom_state = 256;   // positions, references, velocities, masses, forces, ...
+  const int64_t edges = 120 * n;
+  const size_t raw = (size_t)n * (model_bytes_per_atom(c) + per_atom_state) + (size_t)edges * 100;
+  return raw + raw / 4;
 }
 
 // Build the Verlet list of one resident replica from its current positions (segment of the
@@ -468,7 +474,7 @@ int ctd_serve_submit(ctd_server* s, int64_t n, const int32_t* species, const dou
   R->v.assign(velocities, velocities + 3 * n);
   memcpy(R->H, cell, sizeof(R->H));
   R->skin = skin;
-  R->est_bytes = estimate_bytes(s->c->desc, n);
+  R->est_bytes = estimate_bytes(s->c, n);
   if (s->c->budget && R->est_bytes > s->c->budget) {
     delete R;
     return sfail(s, CTD_ERR_OUT_OF_BUDGET, "request can never fit the HBM budget");
