@@ -12,6 +12,8 @@ What pins each function (tests/test_oracle_*.py):
   * painn                     -- pinned (closed forms, invariances, finite differences,
                                  strain finite differences, supercell extensivity)
   * nve                       -- pinned (time reversibility, dt^2 energy-error scaling)
+  * nvt                       -- pinned (NVE limit, conserved extended energy and its dt^2
+                                 scaling, time reversibility, mean temperature of free particles)
 """
 from __future__ import annotations
 
@@ -65,6 +67,10 @@ def _load():
             lib.orc_painn.restype = ctypes.c_int
             lib.orc_nve.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, ctypes.c_double,
                                     ctypes.c_int32, P, P]
+            lib.orc_nvt.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, ctypes.c_double,
+                                    ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                    P, P, P, P, P]
+            lib.orc_nvt.restype = ctypes.c_int
             lib.orc_nve.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -189,3 +195,27 @@ def nve(params, F, K, T, S, species, masses, positions, velocities, cell, dt, ns
     if rcode != 0:
         raise RuntimeError(f"orc_nve failed with {rcode}")
     return x, v, ep, ek
+
+
+def nvt(params, F, K, T, S, species, masses, positions, velocities, cell, dt, nsteps, temperature, tau,
+        chain=3, xi=None, vxi=None, rc=5.0, eps=1e-8, e_scale=1.0):
+    """Nose-Hoover chain NVT trajectory (temperature in K, tau and dt in fs).  Returns
+    (x, v, epot, ekin, ethermo, xi, vxi): ethermo is the chain's energy, epot + ekin + ethermo
+    the conserved quantity; xi / vxi the chain state after the run (pass them back to continue)."""
+    lib = _load()
+    x = _f64(positions, (-1, 3)).copy()
+    v = _f64(velocities, (-1, 3)).copy()
+    H = _f64(cell, (3, 3))
+    Z = np.ascontiguousarray(species, np.int32)
+    m = _f64(masses)
+    xi = np.zeros(chain) if xi is None else _f64(xi).copy()
+    vxi = np.zeros(chain) if vxi is None else _f64(vxi).copy()
+    ep, ek, eth = np.empty(nsteps + 1), np.empty(nsteps + 1), np.empty(nsteps + 1)
+    md = Model(F, K, T, S, rc, eps, e_scale)
+    rcode = lib.orc_nvt(ctypes.byref(md), _p(_f64(params)), x.shape[0], _p(Z), _p(m), _p(H), _p(x), _p(v),
+                        float(dt), int(nsteps), float(temperature), float(tau), int(chain), _p(xi), _p(vxi),
+                        _p(ep), _p(ek), _p(eth))
+    if rcode != 0:
+        raise RuntimeError(f"orc_nvt failed with {rcode}")
+    return x, v, ep, ek, eth, xi, vxi
+

@@ -559,3 +559,97 @@ int orc_nve(const orc_model *md, const double *params, int64_t n, const int32_t 
   free(Fo);
   return rc;
 }
+
+/* ------------------------------------------------------------------------------------------
+ * NVT with a Nose-Hoover chain thermostat (Methods, "MD simulations": NVT ensemble, Nose-Hoover
+ * thermostat with a temperature damping parameter tau).  The paper names neither the chain
+ * length nor the integrator; this follows the Martyna-Tuckerman-Klein (1996) equations of a
+ * chain of M thermostats,
+ *   dv_i/dt   = F_i/m_i - vxi_1 v_i
+ *   dvxi_1/dt = (2 K - Nf kT)/Q_1 - vxi_2 vxi_1
+ *   dvxi_j/dt = (Q_{j-1} vxi_{j-1}^2 - kT)/Q_j - vxi_{j+1} vxi_j      (vxi_{M+1} = 0)
+ *   dxi_j/dt  = vxi_j
+ * with Q_1 = Nf kT tau^2, Q_j = kT tau^2, Nf = 3n - 3 (centre of mass at rest), integrated by
+ * the symmetric Trotter splitting: a chain half step over dt/2, velocity Verlet, a chain half
+ * step.  The chain half step of length h updates vxi_M, then vxi_{M-1} .. vxi_1 (each between two
+ * factors exp(-h vxi_{j+1}/4)), scales the velocities by exp(-h vxi_1), advances every xi_j by
+ * h vxi_j, and sweeps the chain back up in the mirrored order.  Conserved quantity:
+ *   H = K + U + sum_j Q_j vxi_j^2 / 2 + Nf kT xi_1 + kT sum_{j>1} xi_j.
+ * ---------------------------------------------------------------------------------------- */
+#define ORC_KB 8.617333262e-5   /* eV / K */
+
+static double chain_force(int j, double KE, double Nf, double kT, const double *Q, const double *vxi) {
+  if (j == 0) return (2.0 * KE - Nf * kT) / Q[0];
+  return (Q[j - 1] * vxi[j - 1] * vxi[j - 1] - kT) / Q[j];
+}
+
+/* One chain half step of length h; returns the factor that scales every velocity. */
+static double chain_half(int M, double h, double KE, double Nf, double kT, const double *Q, double *xi,
+                         double *vxi) {
+  vxi[M - 1] += 0.5 * h * chain_force(M - 1, KE, Nf, kT, Q, vxi);
+  for (int j = M - 2; j >= 0; --j) {
+    double e = exp(-0.25 * h * vxi[j + 1]);
+    vxi[j] *= e;
+    vxi[j] += 0.5 * h * chain_force(j, KE, Nf, kT, Q, vxi);
+    vxi[j] *= e;
+  }
+  double scale = exp(-h * vxi[0]);
+  KE *= scale * scale;
+  for (int j = 0; j < M; ++j) xi[j] += h * vxi[j];
+  for (int j = 0; j < M - 1; ++j) {
+    double e = exp(-0.25 * h * vxi[j + 1]);
+    vxi[j] *= e;
+    vxi[j] += 0.5 * h * chain_force(j, KE, Nf, kT, Q, vxi);
+    vxi[j] *= e;
+  }
+  vxi[M - 1] += 0.5 * h * chain_force(M - 1, KE, Nf, kT, Q, vxi);
+  return scale;
+}
+
+static double kinetic(int64_t n, const double *mass, const double *vel) {
+  double ke = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < 3; ++c) ke += 0.5 * mass[i] * vel[3 * i + c] * vel[3 * i + c];
+  return ke / ORC_ACC;
+}
+
+static double chain_energy(int M, double Nf, double kT, const double *Q, const double *xi, const double *vxi) {
+  double e = 0.0;
+  for (int j = 0; j < M; ++j) e += 0.5 * Q[j] * vxi[j] * vxi[j] + (j == 0 ? Nf * kT : kT) * xi[j];
+  return e;
+}
+
+/* temperature (K), tau (fs), chain length M (1..16).  xi, vxi: [M] chain state, updated in place
+ * (start from zeros for a fresh chain).  epot / ekin / eth: [nsteps+1] (eth = chain energy). */
+int orc_nvt(const orc_model *md, const double *params, int64_t n, const int32_t *Z, const double *mass,
+            const double H[9], double *x, double *vel, double dt, int32_t nsteps, double temperature,
+            double tau, int32_t M, double *xi, double *vxi, double *epot, double *ekin, double *eth) {
+  if (M < 1 || M > 16 || n < 2 || !(tau > 0.0) || !(temperature > 0.0)) return ORC_EINVAL;
+  const double kT = ORC_KB * temperature, Nf = 3.0 * (double)n - 3.0;
+  double Q[16];
+  for (int j = 0; j < M; ++j) Q[j] = (j == 0 ? Nf : 1.0) * kT * tau * tau;
+  double *Fo = malloc(sizeof(double) * 3 * n);
+  if (!Fo) return ORC_ENOMEM;
+  double E;
+  int rc = forces_at(md, params, n, Z, x, H, &E, Fo);
+  for (int32_t step = 0; step <= nsteps && rc == ORC_OK; ++step) {
+    if (epot) epot[step] = E;
+    if (ekin) ekin[step] = kinetic(n, mass, vel);
+    if (eth) eth[step] = chain_energy(M, Nf, kT, Q, xi, vxi);
+    if (step == nsteps) break;
+    double s = chain_half(M, 0.5 * dt, kinetic(n, mass, vel), Nf, kT, Q, xi, vxi);
+    for (int64_t i = 0; i < n; ++i)
+      for (int c = 0; c < 3; ++c) {
+        vel[3 * i + c] = s * vel[3 * i + c] + 0.5 * dt * ORC_ACC * Fo[3 * i + c] / mass[i];
+        x[3 * i + c] += dt * vel[3 * i + c];
+      }
+    rc = forces_at(md, params, n, Z, x, H, &E, Fo);
+    for (int64_t i = 0; i < n; ++i)
+      for (int c = 0; c < 3; ++c) vel[3 * i + c] += 0.5 * dt * ORC_ACC * Fo[3 * i + c] / mass[i];
+    s = chain_half(M, 0.5 * dt, kinetic(n, mass, vel), Nf, kT, Q, xi, vxi);
+    for (int64_t i = 0; i < 3 * n; ++i) vel[i] *= s;
+  }
+  free(Fo);
+  return rc;
+}
+
