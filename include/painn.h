@@ -141,6 +141,25 @@ int ctd_md_run(ctd_ctx *ctx, int32_t nsteps, double dt, double *epot, double *ek
 /* Copy the MD state back (host arrays [n][3], either may be NULL). */
 int ctd_md_get_state(ctd_ctx *ctx, double *positions, double *velocities);
 
+/* Nose-Hoover chain thermostat for ctd_md_run (NVT; Methods, "MD simulations": Nose-Hoover
+ * thermostat with a temperature damping parameter).  chain = number of thermostats M (1..16;
+ * 0 switches back to NVE); temperature in K; tau in fs.  Equations (Martyna, Tuckerman, Klein):
+ * dv_i/dt = F_i/m_i - vxi_1 v_i, dvxi_1/dt = (2K - Nf kB T)/Q_1 - vxi_2 vxi_1,
+ * dvxi_j/dt = (Q_{j-1} vxi_{j-1}^2 - kB T)/Q_j - vxi_{j+1} vxi_j, dxi_j/dt = vxi_j, with
+ * Q_1 = Nf kB T tau^2, Q_j = kB T tau^2 and Nf = 3n - 3; each step is a chain half step, velocity
+ * Verlet, a chain half step (symmetric Trotter splitting).  The chain starts at rest; this call
+ * and ctd_md_set_state reset it.  The conserved quantity is epot + ekin + the chain energy that
+ * ctd_md_get_thermostat returns. */
+int ctd_md_set_thermostat(ctd_ctx *ctx, double temperature, double tau, int32_t chain);
+/* Chain state (xi[M], vxi[M], host, may be NULL) and the chain energy after every step of the
+ * last ctd_md_run (ethermo[nsteps+1], may be NULL): sum_j Q_j vxi_j^2/2 + Nf kB T xi_1
+ * + kB T sum_{j>1} xi_j (eV).  CTD_ERR_STATE without a thermostat. */
+int ctd_md_get_thermostat(ctd_ctx *ctx, double *xi, double *vxi, double *ethermo);
+/* Restore a chain state (xi[M], vxi[M], host) saved by ctd_md_get_thermostat, after
+ * ctd_md_set_state and ctd_md_set_thermostat, to continue a checkpointed NVT trajectory.
+ * CTD_ERR_STATE without a thermostat; CTD_ERR_INVALID_ARG for non-finite values. */
+int ctd_md_set_thermostat_state(ctd_ctx *ctx, const double *xi, const double *vxi);
+
 /* ---- options -------------------------------------------------------------------------- */
 /* CTD_OPT_TC_ADJOINT (value 0..4; default 2): on the BF16 path with F = 128, run the edge
  * adjoint with the radial filter on tcgen05 as well (the message kernel always does):
@@ -201,7 +220,8 @@ int ctd_gemm_bf16(ctd_ctx *ctx, int64_t M, int32_t N, int32_t K, const void *A, 
  * a replica leaves after its nsteps steps and its final state stays available to
  * ctd_serve_poll.  A replica's trajectory does not depend on which other replicas share the
  * batch (per-replica reductions run in a fixed order of its own atoms).  dt: time step (fs),
- * shared by all replicas.  The params blob is the one ctd_load_params takes. */
+ * shared by all replicas; max_replicas 1..65535.  The params blob is the one ctd_load_params
+ * takes. */
 typedef struct ctd_server ctd_server;
 int ctd_serve_create(ctd_server **out, const ctd_model_desc *desc, const void *params, size_t nbytes,
                      size_t hbm_budget_bytes, int32_t max_replicas, double dt, void *cuda_stream);
@@ -220,6 +240,12 @@ int ctd_serve_step(ctd_server *s, int32_t *n_resident, int32_t *n_admitted, int3
  * values); virial[9] the latest virial.  Any output pointer may be NULL. */
 int ctd_serve_poll(ctd_server *s, int64_t request_id, int32_t *state, int32_t *steps_done,
                    double *positions, double *velocities, double *epot, double *ekin, double *virial);
+/* Checkpoint of a resident replica: its current positions and velocities ([n][3], caller's atom
+ * order, host) and the steps it has done; the replica stays resident.  Submitting the snapshot
+ * with the remaining step count continues the trajectory (on this or another server).
+ * CTD_ERR_STATE if the request is queued or finished (poll returns the final state). */
+int ctd_serve_snapshot(ctd_server *s, int64_t request_id, double *positions, double *velocities,
+                       int32_t *steps_done);
 int ctd_serve_stats(ctd_server *s, int64_t *resident_atoms, int32_t *resident_replicas,
                     int32_t *queued, int64_t *bytes_held);
 const char *ctd_serve_last_error(ctd_server *s);

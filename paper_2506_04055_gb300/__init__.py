@@ -197,6 +197,24 @@ class Potential:
         _lib.ctd_md_get_state(self.ctx, _ptr(x), _ptr(v))
         return x, v
 
+    def md_set_thermostat(self, temperature: float, tau: float, chain: int = 3):
+        """Nose-Hoover chain NVT for md_run (temperature in K, tau in fs; chain=0: NVE)."""
+        _lib.ctd_md_set_thermostat(self.ctx, temperature, tau, chain)
+        self._chain = int(chain)
+
+    def md_set_thermostat_state(self, xi, vxi):
+        """Restore a chain state saved with md_get_thermostat (after md_set_state and
+        md_set_thermostat), to continue a checkpointed NVT trajectory."""
+        _lib.ctd_md_set_thermostat_state(self.ctx, _ptr(_host(xi, np.float64)), _ptr(_host(vxi, np.float64)))
+
+    def md_get_thermostat(self, nsteps: int | None = None):
+        """(xi, vxi, chain energy after each step of the last md_run of nsteps steps)."""
+        M = getattr(self, "_chain", 0)
+        xi, vxi = np.empty(M), np.empty(M)
+        eth = np.empty(nsteps + 1) if nsteps is not None else None
+        _lib.ctd_md_get_thermostat(self.ctx, _ptr(xi), _ptr(vxi), _ptr(eth))
+        return xi, vxi, eth
+
 
 class Server:
     """Continuous-batching MD server (see ctd_serve_* in include/painn.h).
@@ -258,6 +276,15 @@ class Server:
         if state == 2:
             out["positions"], out["velocities"] = x, v
         return out
+
+    def snapshot(self, rid: int):
+        """Current positions, velocities and steps done of a resident replica (a checkpoint);
+        submitting them with the remaining steps continues its trajectory."""
+        n = self._n[rid]
+        x = np.empty((n, 3))
+        v = np.empty((n, 3))
+        done = _lib.ctd_serve_snapshot(self.srv, rid, _ptr(x), _ptr(v))
+        return {"positions": x, "velocities": v, "steps_done": done}
 
     def stats(self):
         return _lib.ctd_serve_stats(self.srv)

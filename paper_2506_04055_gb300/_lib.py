@@ -40,6 +40,7 @@ ERROR_NAMES = {
 EXPORTS = [
     "ctd_create", "ctd_load_params", "ctd_build_neighbors", "ctd_get_pairs", "ctd_compute",
     "ctd_set_energy_out", "ctd_md_set_state", "ctd_md_run", "ctd_md_get_state",
+    "ctd_md_set_thermostat", "ctd_md_get_thermostat", "ctd_md_set_thermostat_state", "ctd_serve_snapshot",
     "ctd_set_option", "ctd_profile_enable", "ctd_profile_read", "ctd_gemm_bf16",
     "ctd_serve_create", "ctd_serve_submit", "ctd_serve_step", "ctd_serve_poll", "ctd_serve_stats",
     "ctd_serve_last_error", "ctd_serve_destroy", "ctd_domains_create", "ctd_domains_compute",
@@ -102,6 +103,10 @@ def load(path: str = LIB_PATH):
         "ctd_md_set_state": ([P, I64, P, P, P, P, P, D], ctypes.c_int),
         "ctd_md_run": ([P, I32, D, P, P, P], ctypes.c_int),
         "ctd_md_get_state": ([P, P, P], ctypes.c_int),
+        "ctd_md_set_thermostat": ([P, D, D, I32], ctypes.c_int),
+        "ctd_md_get_thermostat": ([P, P, P, P], ctypes.c_int),
+        "ctd_md_set_thermostat_state": ([P, P, P], ctypes.c_int),
+        "ctd_serve_snapshot": ([P, I64, P, P, P], ctypes.c_int),
         "ctd_set_option": ([P, I32, I64], ctypes.c_int),
         "ctd_profile_enable": ([P, I32], ctypes.c_int),
         "ctd_profile_read": ([P, P, P, I32], ctypes.c_int),
@@ -189,6 +194,18 @@ def ctd_md_get_state(ctx, positions_ptr, velocities_ptr):
     return check(ctx, load().ctd_md_get_state(ctx, positions_ptr, velocities_ptr))
 
 
+def ctd_md_set_thermostat(ctx, temperature, tau, chain):
+    return check(ctx, load().ctd_md_set_thermostat(ctx, float(temperature), float(tau), int(chain)))
+
+
+def ctd_md_get_thermostat(ctx, xi_ptr, vxi_ptr, ethermo_ptr):
+    return check(ctx, load().ctd_md_get_thermostat(ctx, xi_ptr, vxi_ptr, ethermo_ptr))
+
+
+def ctd_md_set_thermostat_state(ctx, xi_ptr, vxi_ptr):
+    return check(ctx, load().ctd_md_set_thermostat_state(ctx, xi_ptr, vxi_ptr))
+
+
 CTD_OPT_TC_ADJOINT = 1
 CTD_OPT_EDGE_STORE = 2
 CTD_OPT_TC_MESSAGE = 3
@@ -260,6 +277,12 @@ def ctd_serve_poll(srv, rid, positions_ptr=None, velocities_ptr=None, epot_ptr=N
     serve_check(srv, load().ctd_serve_poll(srv, rid, ctypes.byref(st), ctypes.byref(done), positions_ptr,
                                            velocities_ptr, epot_ptr, ekin_ptr, virial_ptr))
     return st.value, done.value
+
+
+def ctd_serve_snapshot(srv, rid, positions_ptr, velocities_ptr):
+    done = ctypes.c_int32()
+    serve_check(srv, load().ctd_serve_snapshot(srv, rid, positions_ptr, velocities_ptr, ctypes.byref(done)))
+    return done.value
 
 
 def ctd_serve_stats(srv):

@@ -825,6 +825,51 @@ int ctd_md_set_state(ctd_ctx* c, int64_t n, const int32_t* species, const double
   CUDA_OK(c, cudaGetLastError());
   c->md_ready = true;
   c->md_forces_valid = false;
+  if (c->nhc_state.p) CUDA_OK(c, cudaMemsetAsync(c->nhc_state.p, 0, c->nhc_state.bytes, c->st));   // new trajectory
+  return CTD_OK;
+}
+
+int ctd_md_set_thermostat(ctd_ctx* c, double temperature, double tau, int32_t chain) {
+  if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
+  if (chain < 0 || chain > 16) return fail(c, CTD_ERR_INVALID_ARG, "chain length must be 0..16");
+  if (chain > 0 && !(temperature > 0.0 && std::isfinite(temperature) && tau > 0.0 && std::isfinite(tau)))
+    return fail(c, CTD_ERR_INVALID_ARG, "temperature and tau must be positive and finite");
+  ENSURE(c, c->nhc_state, sizeof(double) * 40);
+  CUDA_OK(c, cudaMemsetAsync(c->nhc_state.p, 0, c->nhc_state.bytes, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  c->nhc_M = chain;
+  c->nhc_T = temperature;
+  c->nhc_tau = tau;
+  return CTD_OK;
+}
+
+int ctd_md_set_thermostat_state(ctd_ctx* c, const double* xi, const double* vxi) {
+  if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
+  if (c->nhc_M == 0) return fail(c, CTD_ERR_STATE, "no thermostat set");
+  if (!xi || !vxi) return fail(c, CTD_ERR_INVALID_ARG, "xi and vxi are required");
+  const int M = c->nhc_M;
+  for (int j = 0; j < M; ++j)
+    if (!std::isfinite(xi[j]) || !std::isfinite(vxi[j])) return fail(c, CTD_ERR_INVALID_ARG, "non-finite chain state");
+  CUDA_OK(c, cudaMemcpyAsync(c->nhc_state.p, xi, sizeof(double) * M, cudaMemcpyHostToDevice, c->st));
+  CUDA_OK(c, cudaMemcpyAsync(P<double>(c->nhc_state) + M, vxi, sizeof(double) * M, cudaMemcpyHostToDevice, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return CTD_OK;
+}
+
+int ctd_md_get_thermostat(ctd_ctx* c, double* xi, double* vxi, double* ethermo) {
+  if (!c) return CTD_ERR_INVALID_ARG;
+  Bind bind_(c);
+  if (c->nhc_M == 0) return fail(c, CTD_ERR_STATE, "no thermostat set");
+  const int M = c->nhc_M;
+  if (xi) CUDA_OK(c, cudaMemcpyAsync(xi, c->nhc_state.p, sizeof(double) * M, cudaMemcpyDeviceToHost, c->st));
+  if (vxi)
+    CUDA_OK(c, cudaMemcpyAsync(vxi, P<double>(c->nhc_state) + M, sizeof(double) * M, cudaMemcpyDeviceToHost, c->st));
+  if (ethermo && c->md_last_steps >= 0)
+    CUDA_OK(c, cudaMemcpyAsync(ethermo, c->md_eth.p, sizeof(double) * (c->md_last_steps + 1), cudaMemcpyDeviceToHost,
+                               c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
   return CTD_OK;
 }
 
@@ -886,19 +931,42 @@ int ctd_md_run(ctd_ctx* c, int32_t nsteps, double dt, double* epot, double* ekin
     c->md_forces_valid = true;
   }
   StageGuard sg(STG_MD);
+  // NVT: Nose-Hoover chain half steps around velocity Verlet (Nf = 3n - 3: centre of mass at rest)
+  const bool nvt = c->nhc_M > 0;
+  NhcParams np{};
+  if (nvt) {
+    if (n < 2) return fail(c, CTD_ERR_INVALID_ARG, "a thermostat needs at least two atoms");
+    np.M = c->nhc_M;
+    np.kT = 8.617333262e-5 * c->nhc_T;
+    np.Nf = 3.0 * (double)n - 3.0;
+    for (int j = 0; j < np.M; ++j) np.Q[j] = (j == 0 ? np.Nf : 1.0) * np.kT * c->nhc_tau * c->nhc_tau;
+    ENSURE(c, c->nhc_ke, sizeof(double) * 4);
+    ENSURE(c, c->md_eth, sizeof(double) * ((size_t)nsteps + 1));
+  }
+  double* gscale = nvt ? P<double>(c->nhc_state) + np.M * 2 : nullptr;
   auto record = [&](int step) {
     cudaMemcpyAsync(P<double>(c->md_ep) + step, c->out_e.p, sizeof(double), cudaMemcpyDeviceToDevice, st);
     launch_kinetic(st, n, P<double>(c->md_m), P<double>(c->md_v), P<double>(c->kpart), kPartials);
     launch_sum_partials(st, kPartials, 1, P<double>(c->kpart), P<double>(c->md_ek) + step, 1.0);
+    if (nvt) launch_nhc_energy(st, np, P<double>(c->nhc_state), P<double>(c->md_eth) + step);
   };
   record(0);
   for (int32_t s = 0; s < nsteps; ++s) {
-    launch_kick_drift(st, n, dt, P<float>(c->force_s), P<double>(c->md_m), P<double>(c->x_s), P<double>(c->md_v));
+    if (nvt) launch_nhc_half(st, np, 0.5 * dt, P<double>(c->md_ek) + s, P<double>(c->nhc_state));
+    launch_kick_drift(st, n, dt, P<float>(c->force_s), P<double>(c->md_m), gscale, P<double>(c->x_s),
+                      P<double>(c->md_v));
     r = md_forces(c, &rebuilds);
     if (r) return r;
     launch_kick(st, n, dt, P<float>(c->force_s), P<double>(c->md_m), P<double>(c->md_v));
+    if (nvt) {
+      launch_kinetic(st, n, P<double>(c->md_m), P<double>(c->md_v), P<double>(c->kpart), kPartials);
+      launch_sum_partials(st, kPartials, 1, P<double>(c->kpart), P<double>(c->nhc_ke), 1.0);
+      launch_nhc_half(st, np, 0.5 * dt, P<double>(c->nhc_ke), P<double>(c->nhc_state));
+      launch_scale_v(st, n, gscale, P<double>(c->md_v));
+    }
     record(s + 1);
   }
+  c->md_last_steps = nvt ? nsteps : -1;
   CUDA_OK(c, cudaGetLastError());
   if (epot) CUDA_OK(c, cudaMemcpyAsync(epot, c->md_ep.p, sizeof(double) * (nsteps + 1), cudaMemcpyDeviceToHost, st));
   if (ekin) CUDA_OK(c, cudaMemcpyAsync(ekin, c->md_ek.p, sizeof(double) * (nsteps + 1), cudaMemcpyDeviceToHost, st));

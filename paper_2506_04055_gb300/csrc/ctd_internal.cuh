@@ -154,7 +154,17 @@ size_t scan_temp_bytes(int64_t n);
 void launch_exclusive_scan(cudaStream_t st, int64_t n, const int32_t* in, int32_t* out,
                            void* temp);   // out has n+1 entries; out[n] = total
 // md.cu
-void launch_kick_drift(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* x, double* v);
+void launch_kick_drift(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, const double* vscale,
+                       double* x, double* v);
+// Nose-Hoover chain thermostat (md.cu)
+struct NhcParams {
+  int M;          // chain length (1..16)
+  double kT, Nf;  // target kB T (eV), degrees of freedom
+  double Q[16];   // thermostat masses (eV fs^2)
+};
+void launch_nhc_half(cudaStream_t st, const NhcParams& p, double h, const double* ke, double* state);
+void launch_nhc_energy(cudaStream_t st, const NhcParams& p, const double* state, double* out);
+void launch_scale_v(cudaStream_t st, int64_t n, const double* g, double* v);
 void launch_kick(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* v);
 void launch_kinetic(cudaStream_t st, int64_t n, const double* m, const double* v, double* partials, int nb);
 void launch_sum_partials(cudaStream_t st, int nb, int width, const double* partials, double* out, double scale);
@@ -171,8 +181,7 @@ bool make_tmap_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols
 bool edge_tc_supported(int F, int K);
 int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow, const int32_t* acol,
                 const float4* ar, const float* PHI, const float* S, const float* V, float* SM, float* VM,
-                __nv_bfloat16* VMb, int* status,
-                const int32_t* aend);
+                __nv_bfloat16* VMb, int* status, const int32_t* aend);
 int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
                 const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm, const float* Gvm,
                 float* GPHI, float4* hedge, int* status,

@@ -66,13 +66,19 @@ struct ctd_ctx {
   // MD state (sorted order)
   bool md_ready = false, md_forces_valid = false;
   DBuf md_v, md_m, md_x_user, md_v_user, md_ep, md_ek, md_tmp;
+  // Nose-Hoover chain (chain length 0: NVE)
+  int nhc_M = 0;
+  double nhc_T = 0.0, nhc_tau = 0.0;
+  int32_t md_last_steps = -1;
+  DBuf nhc_state, nhc_ke, md_eth;
 
   ctd_ctx() {
     DBuf* list[] = {&params, &params_bf, &x_user, &z_user, &xw, &wrapm, &cellid, &cell_count, &cell_start, &cursor,
                     &tmp_idx, &perm, &inv_perm, &xw_s, &xref_s, &z_s, &x_s, &count, &vrow, &vcol, &vimg,
                     &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev, &aend,
                     &hedge, &force_s, &eatom, &epart, &vpart, &kpart, &scan_tmp, &out_e, &out_f, &out_w,
-                    &out_eatom, &wstore, &ew, &near, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp};
+                    &out_eatom, &wstore, &ew, &near, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp,
+                    &nhc_state, &nhc_ke, &md_eth};
     for (DBuf* b : list) all.push_back(b);
   }
 };

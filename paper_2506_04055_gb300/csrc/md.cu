@@ -10,17 +10,72 @@ namespace ctd {
 
 constexpr double kAcc = 9.648533212331002e-3;
 
-// v += dt/2 a(F);  x += dt v   (first half of velocity Verlet)
+// v = g v + dt/2 a(F);  x += dt v   (first half of velocity Verlet; g = *vscale, the thermostat's
+// velocity factor of the preceding chain half step, or 1 without a thermostat)
 __global__ void k_kick_drift(int64_t n, double dt, const float* __restrict__ force, const double* __restrict__ mass,
-                             double* __restrict__ x, double* __restrict__ v) {
+                             const double* __restrict__ vscale, double* __restrict__ x, double* __restrict__ v) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
+  const double g = vscale ? *vscale : 1.0;
   double s = 0.5 * dt * kAcc / mass[k];
   for (int c = 0; c < 3; ++c) {
-    double vc = v[3 * k + c] + s * (double)force[3 * k + c];
+    double vc = g * v[3 * k + c] + s * (double)force[3 * k + c];
     v[3 * k + c] = vc;
     x[3 * k + c] += dt * vc;
   }
+}
+
+// ---- Nose-Hoover chain (NVT; Methods "MD simulations": Nose-Hoover thermostat, damping tau) ----
+// Chain of M thermostats (Martyna, Tuckerman, Klein 1996): dv_i/dt = F_i/m_i - vxi_1 v_i,
+// dvxi_1/dt = (2K - Nf kT)/Q_1 - vxi_2 vxi_1, dvxi_j/dt = (Q_{j-1} vxi_{j-1}^2 - kT)/Q_j
+// - vxi_{j+1} vxi_j, dxi_j/dt = vxi_j; Q_1 = Nf kT tau^2, Q_j = kT tau^2.  A chain half step of
+// length h: vxi_M, then vxi_{M-1} .. vxi_1 each between two factors exp(-h vxi_{j+1} / 4), the
+// velocity factor exp(-h vxi_1), xi_j += h vxi_j, and the mirrored sweep back up.  The chain is
+// a handful of scalars: one thread advances it; the velocity factor is applied by the next kick.
+// state: xi [M], vxi [M], the factor of the last half step [1].
+__device__ double nhc_force(int j, double ke, const NhcParams& p, const double* vxi) {
+  if (j == 0) return (2.0 * ke - p.Nf * p.kT) / p.Q[0];
+  return (p.Q[j - 1] * vxi[j - 1] * vxi[j - 1] - p.kT) / p.Q[j];
+}
+
+__global__ void k_nhc_half(NhcParams p, double h, const double* __restrict__ ke_in, double* __restrict__ state) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int M = p.M;
+  double* xi = state;
+  double* vxi = state + M;
+  double ke = *ke_in;
+  vxi[M - 1] += 0.5 * h * nhc_force(M - 1, ke, p, vxi);
+  for (int j = M - 2; j >= 0; --j) {
+    const double e = exp(-0.25 * h * vxi[j + 1]);
+    vxi[j] *= e;
+    vxi[j] += 0.5 * h * nhc_force(j, ke, p, vxi);
+    vxi[j] *= e;
+  }
+  const double g = exp(-h * vxi[0]);
+  ke *= g * g;
+  for (int j = 0; j < M; ++j) xi[j] += h * vxi[j];
+  for (int j = 0; j < M - 1; ++j) {
+    const double e = exp(-0.25 * h * vxi[j + 1]);
+    vxi[j] *= e;
+    vxi[j] += 0.5 * h * nhc_force(j, ke, p, vxi);
+    vxi[j] *= e;
+  }
+  vxi[M - 1] += 0.5 * h * nhc_force(M - 1, ke, p, vxi);
+  state[2 * M] = g;
+}
+
+// Energy of the chain: sum_j Q_j vxi_j^2 / 2 + Nf kT xi_1 + kT sum_{j>1} xi_j.
+__global__ void k_nhc_energy(NhcParams p, const double* __restrict__ state, double* __restrict__ out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double e = 0.0;
+  for (int j = 0; j < p.M; ++j)
+    e += 0.5 * p.Q[j] * state[p.M + j] * state[p.M + j] + (j == 0 ? p.Nf * p.kT : p.kT) * state[j];
+  *out = e;
+}
+
+__global__ void k_scale_v(int64_t n3, const double* __restrict__ g, double* __restrict__ v) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n3) v[k] *= *g;
 }
 
 // v += dt/2 a(F)   (second half)
@@ -109,8 +164,20 @@ __global__ void k_check_finite(int64_t n, const double* __restrict__ a, int* sta
 
 static inline unsigned nblk(int64_t w) { return (unsigned)((w + kThreads - 1) / kThreads); }
 
-void launch_kick_drift(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* x, double* v) {
-  if (n) { LaunchScope ls_(st); k_kick_drift<<<nblk(n), kThreads, 0, st>>>(n, dt, f, m, x, v); }
+void launch_kick_drift(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, const double* vscale,
+                       double* x, double* v) {
+  if (n) { LaunchScope ls_(st); k_kick_drift<<<nblk(n), kThreads, 0, st>>>(n, dt, f, m, vscale, x, v); }
+}
+void launch_nhc_half(cudaStream_t st, const NhcParams& p, double h, const double* ke, double* state) {
+  LaunchScope ls_(st);
+  k_nhc_half<<<1, 32, 0, st>>>(p, h, ke, state);
+}
+void launch_nhc_energy(cudaStream_t st, const NhcParams& p, const double* state, double* out) {
+  LaunchScope ls_(st);
+  k_nhc_energy<<<1, 32, 0, st>>>(p, state, out);
+}
+void launch_scale_v(cudaStream_t st, int64_t n, const double* g, double* v) {
+  if (n) { LaunchScope ls_(st); k_scale_v<<<nblk(3 * n), kThreads, 0, st>>>(3 * n, g, v); }
 }
 void launch_kick(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* v) {
   if (n) { LaunchScope ls_(st); k_kick<<<nblk(n), kThreads, 0, st>>>(n, dt, f, m, v); }

@@ -42,8 +42,12 @@ __global__ __launch_bounds__(256) void k_gemm(int64_t M, int N, int K, const flo
   __shared__ __align__(16) float AsT[GBK][GBM + 4];
   __shared__ __align__(16) float Bs[GBK][GBN];
   const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
-  const int64_t m0 = (int64_t)blockIdx.y * GBM;
-  const int n0 = blockIdx.x * GBN;
+  // 1-D grid, column tile fastest: consecutive blocks share their A rows (L2 reuse), and the row
+  // tile count is not limited to the 65,535 of a grid's y dimension (M = 3n rows exceed it
+  // beyond 1.4M atoms)
+  const int ncol = (N + GBN - 1) / GBN;
+  const int64_t m0 = (int64_t)(blockIdx.x / ncol) * GBM;
+  const int n0 = (int)(blockIdx.x % ncol) * GBN;
   float acc[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -114,8 +118,8 @@ static void gemm(cudaStream_t st, int64_t M, int N, int K, const float* A, int l
                  const float* bias, const float* aux, int ldaux, float* out, int ldo, float* out2 = nullptr,
                  int ldo2 = 0) {
   if (M == 0) return;
-  dim3 grid((N + GBN - 1) / GBN, (unsigned)((M + GBM - 1) / GBM));
-  { LaunchScope ls_(st); k_gemm<EPI><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); }
+  const int64_t blocks = (int64_t)((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
+  { LaunchScope ls_(st); k_gemm<EPI><<<(unsigned)blocks, 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); }
 }
 
 // ================================================================================ node kernels

@@ -419,7 +419,8 @@ extern "C" {
 
 int ctd_serve_create(ctd_server** out, const ctd_model_desc* desc, const void* params, size_t nbytes,
                      size_t hbm_budget_bytes, int32_t max_replicas, double dt, void* cuda_stream) {
-  if (!out || !desc || !(dt > 0.0) || max_replicas < 1) return CTD_ERR_INVALID_ARG;
+  // replicas index the y dimension of the list concatenation grid (at most 65,535)
+  if (!out || !desc || !(dt > 0.0) || max_replicas < 1 || max_replicas > 65535) return CTD_ERR_INVALID_ARG;
   *out = nullptr;
   ctd_ctx* c = nullptr;
   int r = ctd_create(&c, desc, hbm_budget_bytes, cuda_stream);
@@ -630,6 +631,21 @@ int ctd_serve_poll(ctd_server* s, int64_t request_id, int32_t* state, int32_t* s
   if (epot && ne) memcpy(epot, R->epot.data(), sizeof(double) * ne);
   if (ekin && ne) memcpy(ekin, R->ekin.data(), sizeof(double) * ne);
   if (virial) memcpy(virial, R->virial, sizeof(double) * 9);
+  return CTD_OK;
+}
+
+int ctd_serve_snapshot(ctd_server* s, int64_t request_id, double* positions, double* velocities, int32_t* steps_done) {
+  if (!s) return CTD_ERR_INVALID_ARG;
+  Bind bind_(s->c);
+  auto it = s->reps.find(request_id);
+  if (it == s->reps.end()) return sfail(s, CTD_ERR_INVALID_ARG, "unknown request");
+  Replica* R = it->second;
+  if (R->state != 1) return sfail(s, CTD_ERR_STATE, "request is not resident");
+  int r = collect(s, *R);   // current state in the caller's order, the replica stays resident
+  if (r) return r;
+  if (positions) memcpy(positions, R->out_x.data(), sizeof(double) * R->out_x.size());
+  if (velocities) memcpy(velocities, R->out_v.data(), sizeof(double) * R->out_v.size());
+  if (steps_done) *steps_done = R->done;
   return CTD_OK;
 }
 

@@ -128,3 +128,40 @@ def test_alone_equals_mixed_tensor_core_F128():
     assert alone["state"] == 2 and mixed["state"] == 2
     np.testing.assert_array_equal(alone["epot"], mixed["epot"])
     np.testing.assert_array_equal(alone["positions"], mixed["positions"])
+
+
+def test_snapshot_restart_continues_trajectory():
+    """A checkpoint of a resident replica, resubmitted with the remaining steps to a new server,
+    continues the trajectory (the new server builds its own neighbour list, so agreement is to
+    FP32 summation order, not bit for bit)."""
+    eng = engine()
+    _, blob = model(F, T, S, seed=8, bias=0.1)
+    sy, v = _replicas()[0]
+    N, K = 20, 8
+    ids, res, _ = _run_server(eng, blob, [(sy, v)], N, "fp32")
+    ref = res[ids[0]]
+    srv = eng.Server(F, blob, T=T, n_species=S, precision="fp32", dt=DT)
+    rid = srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, N, skin=1.0)
+    with pytest.raises(eng.CtdError):
+        srv.snapshot(rid)   # still queued
+    for _ in range(K + 1):  # the first step evaluates the initial forces without moving
+        srv.step()
+    snap = srv.snapshot(rid)
+    assert snap["steps_done"] == K
+    srv.step()              # the replica keeps running after a snapshot
+    assert srv.poll(rid)["steps_done"] == K + 1
+    srv.close()
+    srv2 = eng.Server(F, blob, T=T, n_species=S, precision="fp32", dt=DT)
+    rid2 = srv2.submit(sy.species, sy.masses, snap["positions"], snap["velocities"], sy.cell, N - K, skin=1.0)
+    for _ in range(N - K + 5):
+        if srv2.poll(rid2)["state"] == 2:
+            break
+        srv2.step()
+    out = srv2.poll(rid2)
+    assert out["state"] == 2
+    with pytest.raises(eng.CtdError):
+        srv2.snapshot(rid2)  # finished: poll has the final state
+    srv2.close()
+    np.testing.assert_allclose(out["positions"], ref["positions"], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(out["velocities"], ref["velocities"], rtol=0, atol=1e-7)
+    np.testing.assert_allclose(out["epot"][: N - K + 1], ref["epot"][K : N + 1], rtol=0, atol=1e-5)
