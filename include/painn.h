@@ -332,6 +332,14 @@ int ctd_neighbors_noalloc(int64_t n, const double *positions, const double cell[
                           double skin, int32_t *pair_i, int32_t *pair_j, int8_t *pair_shift,
                           int64_t cap, int64_t *n_pairs, void *cuda_stream);
 
+/* ---- failure detection self-test ------------------------------------------------------------ */
+/* Runs, on the context's stream, the path a tensor-core kernel takes when a bounded device wait
+ * gives up: one CTA allocates tensor memory, waits on an mbarrier that nothing arrives on for
+ * limit_ms (0 < limit_ms <= 2000), records the timeout, frees the tensor memory and returns.
+ * Returns CTD_ERR_TIMEOUT (the expected outcome; the context stays usable) and, in *waited_ms
+ * (may be NULL), how long the wait lasted.  Nothing faults or hangs. */
+int ctd_selftest_wait(ctd_ctx *ctx, double limit_ms, double *waited_ms);
+
 /* Text of the last failure on this context (never NULL). */
 const char *ctd_last_error(ctd_ctx *ctx);
 

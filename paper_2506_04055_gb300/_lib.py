@@ -45,7 +45,7 @@ EXPORTS = [
     "ctd_serve_create", "ctd_serve_submit", "ctd_serve_step", "ctd_serve_poll", "ctd_serve_stats",
     "ctd_serve_last_error", "ctd_serve_destroy", "ctd_domains_create", "ctd_domains_compute",
     "ctd_domains_info", "ctd_domains_context", "ctd_domains_last_error", "ctd_domains_destroy",
-    "ctd_neighbors_noalloc",
+    "ctd_neighbors_noalloc", "ctd_selftest_wait",
     "ctd_last_error",
     "ctd_destroy",
 ]
@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
         "ctd_domains_context": ([P], P),
         "ctd_domains_last_error": ([P], ctypes.c_char_p),
         "ctd_domains_destroy": ([P], None),
+        "ctd_selftest_wait": ([P, D, P], ctypes.c_int),
         "ctd_last_error": ([P], ctypes.c_char_p),
         "ctd_destroy": ([P], None),
     }
@@ -336,6 +337,13 @@ def ctd_domains_context(dom):
 
 def ctd_domains_destroy(dom):
     load().ctd_domains_destroy(dom)
+
+
+def ctd_selftest_wait(ctx, limit_ms):
+    """Returns (status code, milliseconds waited); CTD_ERR_TIMEOUT is the expected code."""
+    waited = ctypes.c_double()
+    code = load().ctd_selftest_wait(ctx, float(limit_ms), ctypes.byref(waited))
+    return code, waited.value
 
 
 def ctd_last_error(ctx) -> str:

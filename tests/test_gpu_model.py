@@ -184,3 +184,25 @@ def test_autograd_function_matches_forces_and_differences():
         fd = (ep - em) / (2 * h)
         an = float((x.grad * d).sum())
         assert fd == pytest.approx(an, rel=2e-3, abs=2e-4)
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    """Failure detection without a fault: a device wait on an mbarrier that nothing arrives on
+    gives up after its limit, frees its tensor memory and reports CTD_ERR_TIMEOUT; the same
+    context then computes exactly what it computed before."""
+    from paper_2506_04055_gb300 import _lib
+    eng = engine()
+    sy = syn.fcc(4, 4, 4, seed=1)
+    _, blob = model(128, 2, 1, seed=1)
+    with eng.Potential(128, T=2, n_species=1, precision="bf16", params=blob) as pot:
+        before = pot.compute(sy.species, sy.positions, sy.cell)
+        code, waited = _lib.ctd_selftest_wait(pot.ctx, 50.0)
+        assert code == _lib.CTD_ERR_TIMEOUT
+        assert "wait gave up" in _lib.ctd_last_error(pot.ctx)
+        assert 50.0 <= waited < 1000.0
+        code, _ = _lib.ctd_selftest_wait(pot.ctx, 5.0)      # repeatable
+        assert code == _lib.CTD_ERR_TIMEOUT
+        after = pot.compute(sy.species, sy.positions, sy.cell)
+        assert after["energy"] == before["energy"]
+        np.testing.assert_array_equal(after["forces"], before["forces"])
+        assert _lib.ctd_selftest_wait(pot.ctx, 0.0)[0] == _lib.CTD_ERR_INVALID_ARG
