@@ -220,6 +220,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself without a process group): every rank's
+    timed region ends at the slowest rank, so whole-job throughput uses the maximum time."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, steps, max_ms):
+    """Aggregate throughput of `world` ranks that each processed units_per_rank units per step
+    for `steps` steps, over the slowest rank's time (ms): units/s for the whole job."""
+    return units_per_rank * world * steps / (max_ms / 1e3)
+
+
 def run_ours(args):
     import torch
 
@@ -324,11 +341,7 @@ def run_ours(args):
                          "epot": [float(ep[0])], "ekin": [float(ek[0])]}
 
     def maxall(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, dist, "cuda")
 
     head = "bf16" if "bf16" in results and "error" not in results["bf16"] else "fp32"
     summary = {}
@@ -338,10 +351,10 @@ def run_ours(args):
             continue
         tot = maxall(r["total_ms"])
         e2e = maxall(r["e2e_s"])
-        summary[prec] = {"value": sy.n * world * args.steps / (tot / 1e3), "ms_per_step": tot / args.steps,
+        summary[prec] = {"value": whole_job_value(sy.n, world, args.steps, tot), "ms_per_step": tot / args.steps,
                          "p50_ms": r["step_ms"][len(r["step_ms"]) // 2],
                          "p99_ms": r["step_ms"][min(len(r["step_ms"]) - 1, int(0.99 * len(r["step_ms"])))],
-                         "e2e": sy.n * world * r["e2e_steps"] / e2e, "rebuilds": r["rebuilds"]}
+                         "e2e": whole_job_value(sy.n, world, r["e2e_steps"], 1e3 * e2e), "rebuilds": r["rebuilds"]}
     if dist:
         dist.destroy_process_group()
     if rank != 0:
