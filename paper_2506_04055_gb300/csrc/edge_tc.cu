@@ -1119,7 +1119,10 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tcg(const __g
 // Thread f accumulates the row's phi gradients and overwrites its own feature of the gathered
 // row with its partials of (dU/dd, dU/du); after a stream barrier the partials are reduced over
 // the F features from shared memory and turned into hedge[e].
-template <int NE, int NS, bool FOLD, bool SPLIT, int NBUF = 2, int KC = 0, bool G4L = false, bool L0 = false>
+// PIPE: the epilogue reads the accumulator in 4-edge halves, each half's TMEM loads in flight
+// while the previous half is computed (only a tile's first load is waited on at once)
+template <int NE, int NS, bool FOLD, bool SPLIT, int NBUF = 2, int KC = 0, bool G4L = false, bool L0 = false,
+          bool PIPE = false>
 __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   static_assert(NS <= 2, "one producer warp per stream");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -1409,6 +1412,103 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         const int hslot = f >> 3;
         float4 hold = make_float4(0.f, 0.f, 0.f, 0.f);
         if (p.accumulate && (lane & 7) == 0 && hslot < nlive) hold = p.hedge[tb + hslot];
+        // this thread's gathered values of edge `slot`
+        auto gat = [&](int slot) -> float4 {
+          if (G4L) return *reinterpret_cast<const float4*>(sG + ((size_t)(so + slot) * kF + f) * 4);
+          const float* gg = tG + (size_t)slot * 4 * kF;
+          return make_float4(gg[0], gg[kF], gg[2 * kF], gg[3 * kF]);
+        };
+        // per edge (accumulator columns w0..w5 = W_s, dW_s, W_vv, dW_vv, W_vs, dW_vs): accumulate
+        // the row's phi gradients; overwrite this thread's gathered gradients in place with its
+        // partials of (dU/dd, dU/du)
+        auto edge = [&](float w0, float w1, float w2, float w3, float w4, float w5, int slot, float gs, float gv0,
+                        float gv1, float gv2) {
+          float* gg = tG + (size_t)slot * 4 * kF;
+          const float4 geo = tg[slot];
+          float Ws, Wvv, Wvs, dWs, dWvv, dWvs;   // filter and its distance derivative, f_c included
+          if (FOLD) {
+            Ws = w0; Wvv = w2; Wvs = w4;
+            dWs = w1; dWvv = w3; dWvs = w5;
+          } else {
+            const float2 fcv = tc[slot];
+            const float ws = w0 + bs, wvv = w2 + bvv, wvs = w4 + bvs;
+            Ws = ws * fcv.x; Wvv = wvv * fcv.x; Wvs = wvs * fcv.x;
+            dWs = fcv.x * w1 + fcv.y * ws;
+            dWvv = fcv.x * w3 + fcv.y * wvv;
+            dWvs = fcv.x * w5 + fcv.y * wvs;
+          }
+          // L0 (first layer): v = 0 so psi = 0, and no phi gradients are written, so only the
+          // per-edge partials are formed
+          if (!L0) {
+            gps = fmaf(gs, Ws, gps);
+            gy0 = fmaf(gv0, Wvv, gy0);
+            gy1 = fmaf(gv1, Wvv, gy1);
+            gy2 = fmaf(gv2, Wvv, gy2);
+          }
+          const float qv = -(gv0 * geo.x + gv1 * geo.y + gv2 * geo.z);
+          if (!L0) gpvs = fmaf(qv, Wvs, gpvs);
+          const float gWs = gs * cur[0], gWvs = qv * cur[4];
+          const float gWvv = L0 ? 0.0f : gv0 * cur[1] + gv1 * cur[2] + gv2 * cur[3];
+          const float tv = cur[4] * Wvs;
+          const float pd = gWs * dWs + gWvv * dWvv + gWvs * dWvs;
+          if (G4L) {
+            *reinterpret_cast<float4*>(sG + ((size_t)(so + slot) * kF + f) * 4) = make_float4(pd, gv0 * tv, gv1 * tv, gv2 * tv);
+          } else {
+            gg[0] = pd;
+            gg[kF] = gv0 * tv;
+            gg[2 * kF] = gv1 * tv;
+            gg[3 * kF] = gv2 * tv;
+          }
+        };
+        if (PIPE) {
+          const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((s * 2 + a) * 6 * NE);
+          uint32_t RA[6][4], RB[6][4];
+          // four edges b .. b + 3 with their accumulator columns in R
+          auto half = [&](const uint32_t (&R)[6][4], int b4) {
+            const int4 fl = *reinterpret_cast<const int4*>(tf + b4);
+            if ((fl.x | fl.y | fl.z | fl.w) == 0 && b4 + 4 <= nlive) {
+              // no row ends in these four edges: their gathered values are read first
+              float4 G[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) G[u] = gat(b4 + u);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                edge(__uint_as_float(R[0][u]), __uint_as_float(R[1][u]), __uint_as_float(R[2][u]),
+                     __uint_as_float(R[3][u]), __uint_as_float(R[4][u]), __uint_as_float(R[5][u]), b4 + u, G[u].x,
+                     G[u].y, G[u].z, G[u].w);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int slot = b4 + u;
+                if (slot < nlive) {
+                  const float4 gq = gat(slot);
+                  edge(__uint_as_float(R[0][u]), __uint_as_float(R[1][u]), __uint_as_float(R[2][u]),
+                       __uint_as_float(R[3][u]), __uint_as_float(R[4][u]), __uint_as_float(R[5][u]), slot, gq.x, gq.y,
+                       gq.z, gq.w);
+                  for (int nf = tf[slot]; nf > 0 && r < C.r1; --nf) flush();
+                }
+              }
+            }
+          };
+          umma::tmem_ld4x6_issue(tbase, NE, RA);
+          umma::tmem_wait4x6(RA);
+#pragma unroll 1
+          for (int c = 0; c < NE / 8; ++c) {
+            umma::tmem_ld4x6_issue(tbase + c * 8 + 4, NE, RB);   // in flight during the first half
+            half(RA, c * 8);
+            umma::tmem_wait4x6(RB);
+            if (c + 1 < NE / 8) {
+              umma::tmem_ld4x6_issue(tbase + (c + 1) * 8, NE, RA);   // in flight during the second half
+            } else {
+              // every accumulator column of the tile has been read: the MMA may reuse the buffer
+              umma::fence_before();
+              __syncwarp();
+              if (lane == 0) umma::mbar_arrive(&b[10 + a]);
+            }
+            half(RB, c * 8 + 4);
+            if (c + 1 < NE / 8) umma::tmem_wait4x6(RA);
+          }
+        } else {
 #pragma unroll 1
         for (int c = 0; c < NE / 8; ++c) {
           // column groups at stride NE: W_s, dW_s, W_vv, dW_vv, W_vs, dW_vs
@@ -1419,52 +1519,6 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&b[10 + a]);
           }
-          // per edge: accumulate the row's phi gradients; overwrite this thread's gathered
-          // gradients in place with its partials of (dU/dd, dU/du)
-          // this thread's gathered values of edge `slot` and where its partials go back
-          auto gat = [&](int slot) -> float4 {
-            if (G4L) return *reinterpret_cast<const float4*>(sG + ((size_t)(so + slot) * kF + f) * 4);
-            const float* gg = tG + (size_t)slot * 4 * kF;
-            return make_float4(gg[0], gg[kF], gg[2 * kF], gg[3 * kF]);
-          };
-          auto edge = [&](int u, int slot, float gs, float gv0, float gv1, float gv2) {
-            float* gg = tG + (size_t)slot * 4 * kF;
-            const float4 geo = tg[slot];
-            float Ws, Wvv, Wvs, dWs, dWvv, dWvs;   // filter and its distance derivative, f_c included
-            if (FOLD) {
-              Ws = W[0][u]; Wvv = W[2][u]; Wvs = W[4][u];
-              dWs = W[1][u]; dWvv = W[3][u]; dWvs = W[5][u];
-            } else {
-              const float2 fcv = tc[slot];
-              const float ws = W[0][u] + bs, wvv = W[2][u] + bvv, wvs = W[4][u] + bvs;
-              Ws = ws * fcv.x; Wvv = wvv * fcv.x; Wvs = wvs * fcv.x;
-              dWs = fcv.x * W[1][u] + fcv.y * ws;
-              dWvv = fcv.x * W[3][u] + fcv.y * wvv;
-              dWvs = fcv.x * W[5][u] + fcv.y * wvs;
-            }
-            // L0 (first layer): v = 0 so psi = 0, and no phi gradients are written, so only the
-            // per-edge partials are formed
-            if (!L0) {
-              gps = fmaf(gs, Ws, gps);
-              gy0 = fmaf(gv0, Wvv, gy0);
-              gy1 = fmaf(gv1, Wvv, gy1);
-              gy2 = fmaf(gv2, Wvv, gy2);
-            }
-            const float qv = -(gv0 * geo.x + gv1 * geo.y + gv2 * geo.z);
-            if (!L0) gpvs = fmaf(qv, Wvs, gpvs);
-            const float gWs = gs * cur[0], gWvs = qv * cur[4];
-            const float gWvv = L0 ? 0.0f : gv0 * cur[1] + gv1 * cur[2] + gv2 * cur[3];
-            const float tv = cur[4] * Wvs;
-            const float pd = gWs * dWs + gWvv * dWvv + gWvs * dWvs;
-            if (G4L) {
-              *reinterpret_cast<float4*>(sG + ((size_t)(so + slot) * kF + f) * 4) = make_float4(pd, gv0 * tv, gv1 * tv, gv2 * tv);
-            } else {
-              gg[0] = pd;
-              gg[kF] = gv0 * tv;
-              gg[2 * kF] = gv1 * tv;
-              gg[3 * kF] = gv2 * tv;
-            }
-          };
           const int4 fa = *reinterpret_cast<const int4*>(tf + c * 8), fb = *reinterpret_cast<const int4*>(tf + c * 8 + 4);
           if ((fa.x | fa.y | fa.z | fa.w | fb.x | fb.y | fb.z | fb.w) == 0 && c * 8 + 8 <= nlive) {
             // no row ends in these eight edges: all their gathered values are read first, so
@@ -1473,18 +1527,20 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
 #pragma unroll
             for (int u = 0; u < 8; ++u) G[u] = gat(c * 8 + u);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) edge(u, c * 8 + u, G[u].x, G[u].y, G[u].z, G[u].w);
+            for (int u = 0; u < 8; ++u)
+              edge(W[0][u], W[1][u], W[2][u], W[3][u], W[4][u], W[5][u], c * 8 + u, G[u].x, G[u].y, G[u].z, G[u].w);
           } else {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int slot = c * 8 + u;
               if (slot < nlive) {
                 const float4 gq = gat(slot);
-                edge(u, slot, gq.x, gq.y, gq.z, gq.w);
+                edge(W[0][u], W[1][u], W[2][u], W[3][u], W[4][u], W[5][u], slot, gq.x, gq.y, gq.z, gq.w);
                 for (int nf = tf[slot]; nf > 0 && r < C.r1; --nf) flush();
               }
             }
           }
+        }
         }
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&b[12]);
@@ -1693,9 +1749,9 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, true, kBwgSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(true));
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
-    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
-    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     attr = true;
   }
   a.chunk_rows = chunk_rows_for(m, n, kBwgNS);
@@ -1709,10 +1765,11 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
     else if (m.tc_adjoint_variant == 4)
       k_edge_bwd_tcg<kBwgNE, kBwgNS, false, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(true), st>>>(tm, a);
     // the usual basis size (K = 20) with a compile-time loop bound; G4: gradients interleaved
+    // (with the accumulator read in pipelined 4-edge halves)
     else if (m.K == 20 && G4 && t == 0 && !GPHI)   // first layer: v = 0, no phi gradients
-      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
+      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true, true, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
     else if (m.K == 20 && G4)
-      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
+      k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 20, true, false, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
     else if (G4)
       k_edge_bwd_tcg<kBwgNE, kBwgNS, false, kBwgSplit, 2, 0, true><<<sms, 32 * (3 + 4 * kBwgNS), bwg_smem(), st>>>(tm, a);
     else if (m.K == 20)
