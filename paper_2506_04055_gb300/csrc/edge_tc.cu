@@ -467,16 +467,8 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
       const float4* tg = sgeo + so;
 #pragma unroll 1
       for (int c = 0; c < NE / 8; ++c) {
-        float ds[8], dv[8], dw[8];
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((s * TB + a) * 3 * NE + c * 8);
-        umma::tmem_ld8(ta, ds);
-        umma::tmem_ld8(ta + NE, dv);
-        umma::tmem_ld8(ta + 2 * NE, dw);
-        if (c == NE / 8 - 1) {
-          umma::fence_before();
-          __syncwarp();
-          if (lane == 0) umma::mbar_arrive(&b[6 + a]);
-        }
+        // the senders' message rows first (they do not depend on the accumulator), so their
+        // latency overlaps the TMEM loads below
         // V0 (first layer, v = 0): the psi channels v_a phi_vv are zero and not gathered
         float g[8][5];
 #pragma unroll
@@ -485,6 +477,14 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_fwd_tc(const __gr
           const float* pj = p.PHI + (int64_t)(live ? tj[c * 8 + u] : 0) * 6 * kF + f;
 #pragma unroll
           for (int k = 0; k < 5; ++k) g[u][k] = live && (!V0 || k == 0 || k == 4) ? __ldg(pj + k * kF) : 0.f;
+        }
+        float ds[8], dv[8], dw[8];
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((s * TB + a) * 3 * NE + c * 8);
+        umma::tmem_ld8x3(ta, NE, ds, dv, dw);
+        if (c == NE / 8 - 1) {
+          umma::fence_before();
+          __syncwarp();
+          if (lane == 0) umma::mbar_arrive(&b[6 + a]);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {

@@ -101,6 +101,27 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Three 8-column loads at column offsets 0, stride, 2 stride, with one wait for all of them.
+__device__ __forceinline__ void tmem_ld8x3(uint32_t taddr, uint32_t stride, float (&a)[8], float (&b)[8],
+                                           float (&c)[8]) {
+  uint32_t r[3][8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]), "=r"(r[0][7]),
+        "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]), "=r"(r[1][6]), "=r"(r[1][7]),
+        "=r"(r[2][0]), "=r"(r[2][1]), "=r"(r[2][2]), "=r"(r[2][3]), "=r"(r[2][4]), "=r"(r[2][5]), "=r"(r[2][6]), "=r"(r[2][7])
+      : "r"(taddr), "r"(taddr + stride), "r"(taddr + 2 * stride));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a[i] = __uint_as_float(r[0][i]);
+    b[i] = __uint_as_float(r[1][i]);
+    c[i] = __uint_as_float(r[2][i]);
+  }
+}
+
 // Six 4-column loads at column offsets 0, stride, ..., 5 stride, issued without waiting: the
 // registers hold the values only after tmem_wait4x6 on the same array.
 __device__ __forceinline__ void tmem_ld4x6_issue(uint32_t taddr, uint32_t stride, uint32_t (&r)[6][4]) {
