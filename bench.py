@@ -29,7 +29,7 @@ FCC_CELLS = 63
 F, K, T, S = 128, 20, 3, 1
 RC, SKIN, DT, TEMP = 5.0, 1.0, 1.0, 300.0
 
-# algorithmic FLOPs per (active edge, feature channel) of the two edge kernels (see DESIGN.md):
+# algorithmic FLOPs per (active edge, feature channel) of the two edge kernels:
 # message: filter 3K FMA + f_c scaling + s / v message terms; adjoint: filter and its radial
 # derivative (2 x 3K FMA) + message adjoint terms + per-edge gradient partials.
 EDGE_FWD_FLOP_PER_EF = 6 * K + 18
