@@ -174,3 +174,21 @@ def test_empty_system():
         assert out["energy"] == 0.0
         assert out["forces"].shape == (0, 3)
         assert np.all(out["virial"] == 0.0)
+
+
+def test_slab_with_empty_domains(orc):
+    """An fcc slab in a box four times its thickness (vacuum along x), 8 domains along x: the
+    domains in the vacuum hold neither owned atoms nor copies, and the result still matches."""
+    eng = engine()
+    F, T, S = 32, 2, 1
+    sy = syn.fcc(4, 4, 4, seed=9)
+    cell = sy.cell.copy()
+    cell[0, 0] *= 4.0
+    sy = syn.System(sy.positions, sy.species, sy.masses, cell, "slab")
+    vals, blob = model(F, T, S, seed=17, bias=0.2)
+    ref = orc.painn(vals, F, 20, T, S, sy.species, sy.positions, sy.cell)
+    out = decomposed(eng, blob, sy, F, T, S, (8, 1, 1))
+    compare(out, ref)
+    empty = [d for d in out["info"] if d["n_owned"] == 0 and d["n_copies"] == 0]
+    assert len(empty) >= 2
+    assert sum(d["n_owned"] for d in out["info"]) == len(sy.species)
