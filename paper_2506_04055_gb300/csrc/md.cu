@@ -104,19 +104,35 @@ __global__ void k_kinetic(int64_t n, const double* __restrict__ mass, const doub
   }
 }
 
-// Sum `count` groups of `width` partials in a fixed order with Neumaier compensation:
-// out[c] = sum_b partials[b * width + c].  One warp, lane c handles column c (width <= 32).
-__global__ void k_sum_partials(int nb, int width, const double* __restrict__ partials, double* __restrict__ out,
-                               double scale) {
-  int c = threadIdx.x;
-  if (c >= width) return;
+// out[c] = scale * sum_b partials[b * width + c], compensated (Neumaier) and in a fixed order:
+// one block per column; thread t sums partials t, t + 256, ... then a pairwise tree over the
+// threads carries the sums and their compensation terms.  The order depends only on nb, so the
+// result is deterministic.  (A single warp walking the partials one by one spent ~170 us on
+// GB300's FP64 latency chain for 608 partials.)
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) k_sum_partials(int nb, int width, const double* __restrict__ partials,
+                                                              double* __restrict__ out, double scale) {
+  __shared__ double ss[kSumThreads], sc[kSumThreads];
+  const int c = blockIdx.x, tid = threadIdx.x;
   double s = 0.0, comp = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    double x = partials[(int64_t)b * width + c], t = s + x;
+  for (int b = tid; b < nb; b += kSumThreads) {
+    const double x = partials[(int64_t)b * width + c], t = s + x;
     comp += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
     s = t;
   }
-  out[c] = (s + comp) * scale;
+  ss[tid] = s;
+  sc[tid] = comp;
+  __syncthreads();
+  for (int h = kSumThreads / 2; h > 0; h >>= 1) {
+    if (tid < h) {
+      const double a = ss[tid], b = ss[tid + h], t = a + b;
+      const double e = fabs(a) >= fabs(b) ? (a - t) + b : (b - t) + a;
+      ss[tid] = t;
+      sc[tid] = sc[tid] + sc[tid + h] + e;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) out[c] = (ss[0] + sc[0]) * scale;
 }
 
 // out[perm[k]] = (double) in[k]  for [n][w] rows
@@ -186,7 +202,8 @@ void launch_kinetic(cudaStream_t st, int64_t n, const double* m, const double* v
   { LaunchScope ls_(st); k_kinetic<<<nb, kThreads, 0, st>>>(n, m, v, partials); }
 }
 void launch_sum_partials(cudaStream_t st, int nb, int width, const double* partials, double* out, double scale) {
-  { LaunchScope ls_(st); k_sum_partials<<<1, 32, 0, st>>>(nb, width, partials, out, scale); }
+  if (width < 1) return;
+  { LaunchScope ls_(st); k_sum_partials<<<width, kSumThreads, 0, st>>>(nb, width, partials, out, scale); }
 }
 void launch_scatter_rows(cudaStream_t st, int64_t n, int w, const int32_t* perm, const float* in, double* out) {
   if (n) { LaunchScope ls_(st); k_scatter_rows<<<nblk(n * w), kThreads, 0, st>>>(n, w, perm, in, out); }
