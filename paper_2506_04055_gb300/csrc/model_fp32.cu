@@ -113,11 +113,40 @@ __global__ __launch_bounds__(256) void k_gemm(int64_t M, int N, int K, const flo
   }
 }
 
+// Small problems (fewer output tiles than one wave of the GPU): one thread per output element,
+// the same fmaf chain over k in increasing order and the same epilogue as k_gemm, so results
+// are bit for bit those of the tiled kernel, with more warps in flight than its few CTAs.
+template <int EPI>
+__global__ void k_gemm_small(int64_t M, int N, int K, const float* __restrict__ A, int lda,
+                             const float* __restrict__ B, const float* __restrict__ bias,
+                             const float* __restrict__ aux, int ldaux, float* __restrict__ out, int ldo,
+                             float* __restrict__ out2, int ldo2) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  const int64_t m = idx / N;
+  const int n = (int)(idx % N);
+  const float* a = A + m * lda;
+  float x = 0.0f;
+  for (int k = 0; k < K; ++k) x = fmaf(__ldg(a + k), __ldg(B + (int64_t)k * N + n), x);
+  if (EPI == EPI_BIAS || EPI == EPI_BIAS_SILU) x += bias ? bias[n] : 0.0f;
+  if (EPI == EPI_ADD) x += aux[m * ldaux + n];
+  if (EPI == EPI_DSILU) x *= dsilu_f(aux[m * ldaux + n]);
+  out[m * ldo + n] = x;
+  if (EPI == EPI_BIAS_SILU) out2[m * ldo2 + n] = silu_f(x);
+}
+
 template <int EPI>
 static void gemm(cudaStream_t st, int64_t M, int N, int K, const float* A, int lda, const float* B,
                  const float* bias, const float* aux, int ldaux, float* out, int ldo, float* out2 = nullptr,
                  int ldo2 = 0) {
   if (M == 0) return;
+  const int64_t tiles = (int64_t)((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
+  if (tiles < 152) {
+    LaunchScope ls_(st);
+    k_gemm_small<EPI><<<(unsigned)((M * N + 255) / 256), 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out,
+                                                                     ldo, out2, ldo2);
+    return;
+  }
   const int64_t blocks = (int64_t)((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
   { LaunchScope ls_(st); k_gemm<EPI><<<(unsigned)blocks, 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); }
 }
