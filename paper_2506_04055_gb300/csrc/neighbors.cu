@@ -19,6 +19,8 @@
 //                 |r_e| < rc (warp ballot, count then fill); rev of the active list via the
 //                 Verlet -> active map.  r_rev = -r_e exactly, so both directions survive
 //                 together.
+#include <cmath>
+
 #include "ctd_internal.cuh"
 
 namespace ctd {
@@ -127,15 +129,28 @@ __device__ __forceinline__ uint32_t pack_img(int a, int b, int c) {
 
 // One warp per (sorted) atom i.  Neighbour slabs are visited in a fixed order; within a cell
 // candidates are in sorted order, so the fill is deterministic.
+//
+// Every candidate first takes an FP32 distance test against R2f, a threshold above R^2 by a
+// bound on the FP32 rounding of the positions, the image shift and the squared distance
+// (computed on the host from the cell and the search range): it only drops pairs whose exact
+// distance is beyond the cutoff.  The survivors (about one candidate in seven) queue up per
+// warp in the order they were found and take the canonical FP64 test in batches of 32, so the
+// FP64 latency chain is paid once per batch instead of once per neighbour cell.  The pairs
+// kept, and their order, are those of the FP64 test alone.
+constexpr int kPsQueue = 64;   // per-warp survivor queue (a batch of 32 plus one chunk)
+
 template <bool FILL>
 __global__ void k_pair_search(int64_t n, const double* __restrict__ xs, const int32_t* __restrict__ cstart,
-                              CellGeom g, int32_t* __restrict__ count, const int32_t* __restrict__ row_ptr,
+                              CellGeom g, float r2f, int32_t* __restrict__ count, const int32_t* __restrict__ row_ptr,
                               int32_t* __restrict__ col, uint32_t* __restrict__ img,
                               float4* __restrict__ base) {
+  __shared__ int32_t qj[kThreads / 32][kPsQueue];
+  __shared__ uint32_t qi[kThreads / 32][kPsQueue];
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   if (i >= n) return;
   const double xi0 = xs[3 * i], xi1 = xs[3 * i + 1], xi2 = xs[3 * i + 2];
+  const float fi0 = (float)xi0, fi1 = (float)xi1, fi2 = (float)xi2;
   // Slab of atom i, recomputed from its wrapped position.  It may differ from the slab used for
   // binning only for atoms within rounding of a slab face; the search range keeps a relative
   // margin of 1e-6, so every pair within the cutoff is still visited.
@@ -145,8 +160,39 @@ __global__ void k_pair_search(int64_t n, const double* __restrict__ xs, const in
     int c = (int)floor(s * (double)g.nc[a]);
     ci[a] = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
   }
+  const float hf[9] = {(float)g.H[0], (float)g.H[1], (float)g.H[2], (float)g.H[3], (float)g.H[4],
+                       (float)g.H[5], (float)g.H[6], (float)g.H[7], (float)g.H[8]};
   int out = FILL ? row_ptr[i] : 0;
-  int cnt = 0;
+  int cnt = 0, qn = 0;
+  // canonical FP64 test of the first nb queued survivors (in queue order)
+  auto batch = [&](int nb) {
+    bool keep = false;
+    double dv0 = 0, dv1 = 0, dv2 = 0;
+    int j = 0;
+    uint32_t pim = 0;
+    if (lane < nb) {
+      j = qj[wq][lane];
+      pim = qi[wq][lane];
+      const int im0 = (int8_t)(pim & 0xff), im1 = (int8_t)((pim >> 8) & 0xff), im2 = (int8_t)((pim >> 16) & 0xff);
+      double sh[3];
+      for (int c = 0; c < 3; ++c)
+        sh[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)im0, g.H[c]), __dmul_rn((double)im1, g.H[3 + c])),
+                          __dmul_rn((double)im2, g.H[6 + c]));
+      dv0 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j], xi0), sh[0]);
+      dv1 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j + 1], xi1), sh[1]);
+      dv2 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j + 2], xi2), sh[2]);
+      const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dv0, dv0), __dmul_rn(dv1, dv1)), __dmul_rn(dv2, dv2));
+      keep = d2 < g.R2;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (FILL && keep) {
+      const int pos = out + cnt + __popc(m & ((1u << lane) - 1u));
+      col[pos] = j;
+      img[pos] = pim;
+      base[pos] = make_float4((float)dv0, (float)dv1, (float)dv2, 0.0f);
+    }
+    cnt += __popc(m);
+  };
   for (int d0 = -g.M[0]; d0 <= g.M[0]; ++d0)
     for (int d1 = -g.M[1]; d1 <= g.M[1]; ++d1)
       for (int d2 = -g.M[2]; d2 <= g.M[2]; ++d2) {
@@ -157,35 +203,62 @@ __global__ void k_pair_search(int64_t n, const double* __restrict__ xs, const in
           im[a] = q;
           w[a] = cc[a] - q * g.nc[a];
         }
-        double sh[3];
+        float shf[3];
         for (int c = 0; c < 3; ++c)
-          sh[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)im[0], g.H[c]), __dmul_rn((double)im[1], g.H[3 + c])),
-                            __dmul_rn((double)im[2], g.H[6 + c]));
-        bool zero_img = (im[0] == 0) && (im[1] == 0) && (im[2] == 0);
-        int lin = cell_linear(g, w[0], w[1], w[2]);
-        int b = cstart[lin], e = cstart[lin + 1];
+          shf[c] = fmaf((float)im[0], hf[c], fmaf((float)im[1], hf[3 + c], (float)im[2] * hf[6 + c]));
+        const bool zero_img = (im[0] == 0) && (im[1] == 0) && (im[2] == 0);
+        const uint32_t pim = pack_img(im[0], im[1], im[2]);
+        const int lin = cell_linear(g, w[0], w[1], w[2]);
+        const int b = cstart[lin], e = cstart[lin + 1];
         for (int j0 = b; j0 < e; j0 += 32) {
-          int j = j0 + lane;
-          bool keep = false;
-          double dv0 = 0, dv1 = 0, dv2 = 0;
+          const int j = j0 + lane;
+          bool pass = false;
           if (j < e) {
-            dv0 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j], xi0), sh[0]);
-            dv1 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j + 1], xi1), sh[1]);
-            dv2 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j + 2], xi2), sh[2]);
-            double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dv0, dv0), __dmul_rn(dv1, dv1)), __dmul_rn(dv2, dv2));
-            keep = (d2 < g.R2) && !(zero_img && j == (int)i);
+            const float a0 = ((float)xs[3 * (int64_t)j] - fi0) + shf[0];
+            const float a1 = ((float)xs[3 * (int64_t)j + 1] - fi1) + shf[1];
+            const float a2 = ((float)xs[3 * (int64_t)j + 2] - fi2) + shf[2];
+            pass = fmaf(a2, a2, fmaf(a1, a1, a0 * a0)) < r2f && !(zero_img && j == (int)i);
           }
-          unsigned m = __ballot_sync(0xffffffffu, keep);
-          if (FILL && keep) {
-            int pos = out + cnt + __popc(m & ((1u << lane) - 1u));
-            col[pos] = j;
-            img[pos] = pack_img(im[0], im[1], im[2]);
-            base[pos] = make_float4((float)dv0, (float)dv1, (float)dv2, 0.0f);
+          const unsigned m = __ballot_sync(0xffffffffu, pass);
+          if (pass) {
+            const int slot = qn + __popc(m & ((1u << lane) - 1u));
+            qj[wq][slot] = j;
+            qi[wq][slot] = pim;
           }
-          cnt += __popc(m);
+          qn += __popc(m);
+          __syncwarp();
+          if (qn >= 32) {
+            batch(32);
+            __syncwarp();
+            // move the overflow (at most 31 entries) to the front of the queue
+            int32_t mj = 0;
+            uint32_t mi = 0;
+            if (lane + 32 < qn) { mj = qj[wq][lane + 32]; mi = qi[wq][lane + 32]; }
+            __syncwarp();
+            if (lane + 32 < qn) { qj[wq][lane] = mj; qi[wq][lane] = mi; }
+            qn -= 32;
+            __syncwarp();
+          }
         }
       }
+  if (qn > 0) batch(qn);
   if (!FILL && lane == 0) count[i] = cnt;
+}
+
+// FP32 threshold of the prefilter: R^2 plus a bound on the FP32 error of the squared distance.
+// The wrapped positions lie in the cell and the image shifts span at most M cells per direction,
+// so every coordinate entering a difference is bounded by A = sum_a (M_a + 2) |h_a|_1; each of
+// the position and shift conversions, the difference and the sum adds at most 2^-24 A per
+// component (16 2^-24 A is taken), and the squared distance near R adds 2 sqrt(3) R e + 3 e^2
+// plus its own rounding (8 2^-24 R^2 taken).  The result is rounded up to a float.
+static float prefilter_r2(const CellGeom& g) {
+  double A = 0.0;
+  for (int a = 0; a < 3; ++a)
+    A += (g.M[a] + 2) * (std::fabs(g.H[3 * a]) + std::fabs(g.H[3 * a + 1]) + std::fabs(g.H[3 * a + 2]));
+  const double u = 5.9604644775390625e-08;   // 2^-24
+  const double e = 16.0 * u * A, R = std::sqrt(g.R2);
+  const double t = g.R2 + 2.0 * std::sqrt(3.0) * R * e + 3.0 * e * e + 8.0 * u * g.R2;
+  return std::nextafter((float)t, INFINITY);
 }
 
 void launch_pair_search(cudaStream_t st, bool fill, int64_t n, const double* xw_s,
@@ -194,10 +267,11 @@ void launch_pair_search(cudaStream_t st, bool fill, int64_t n, const double* xw_
   if (n == 0) return;
   int64_t threads = n * 32;
   unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
+  const float r2f = prefilter_r2(g);
   if (fill)
-    { LaunchScope ls_(st); k_pair_search<true><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, count, row_ptr, col, img, base); }
+    { LaunchScope ls_(st); k_pair_search<true><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, r2f, count, row_ptr, col, img, base); }
   else
-    { LaunchScope ls_(st); k_pair_search<false><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, count, row_ptr, col, img, base); }
+    { LaunchScope ls_(st); k_pair_search<false><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, r2f, count, row_ptr, col, img, base); }
 }
 
 // ------------------------------------------------------------------------------- reverse edges
