@@ -127,122 +127,154 @@ __device__ __forceinline__ uint32_t pack_img(int a, int b, int c) {
          ((uint32_t)(uint8_t)(int8_t)c << 16);
 }
 
-// One warp per (sorted) atom i.  Neighbour slabs are visited in a fixed order; within a cell
-// candidates are in sorted order, so the fill is deterministic.
+// One warp per cell of the grid: the cell's atoms (in groups of up to 32, the "home" atoms)
+// against the atoms of every neighbour cell, visited in a fixed order of slab offsets; within a
+// neighbour cell the candidates are in sorted order.  Each neighbour cell is staged in shared
+// memory (in pieces of up to kPsPiece atoms, image shift applied) and the lanes run over the
+// (home atom, candidate) pairs, so all 32 lanes work whatever the cell occupancy.
 //
-// Every candidate first takes an FP32 distance test against R2f, a threshold above R^2 by a
-// bound on the FP32 rounding of the positions, the image shift and the squared distance
-// (computed on the host from the cell and the search range): it only drops pairs whose exact
-// distance is beyond the cutoff.  The survivors (about one candidate in seven) queue up per
-// warp in the order they were found and take the canonical FP64 test in batches of 32, so the
-// FP64 latency chain is paid once per batch instead of once per neighbour cell.  The pairs
-// kept, and their order, are those of the FP64 test alone.
+// Every pair first takes an FP32 distance test against R2f, a threshold above R^2 by a bound on
+// the FP32 rounding of the positions, the image shift and the squared distance (computed on the
+// host from the cell and the search range): it only drops pairs whose exact distance is beyond
+// the cutoff.  The survivors (about one in seven) queue up per warp in the order they were found
+// and take the canonical FP64 test in batches of 32.  The pairs kept are those of the FP64 test
+// alone; each home atom's row lists them by neighbour cell, then candidate, and is written
+// through a per-atom cursor, so the fill is deterministic.
 constexpr int kPsQueue = 64;   // per-warp survivor queue (a batch of 32 plus one chunk)
+constexpr int kPsPiece = 64;   // neighbour atoms staged at a time
+constexpr int kPsWarps = kThreads / 32;
 
 template <bool FILL>
-__global__ void k_pair_search(int64_t n, const double* __restrict__ xs, const int32_t* __restrict__ cstart,
+__global__ void k_pair_search(int64_t ncells, const double* __restrict__ xs, const int32_t* __restrict__ cstart,
                               CellGeom g, float r2f, int32_t* __restrict__ count, const int32_t* __restrict__ row_ptr,
                               int32_t* __restrict__ col, uint32_t* __restrict__ img,
                               float4* __restrict__ base) {
-  __shared__ int32_t qj[kThreads / 32][kPsQueue];
-  __shared__ uint32_t qi[kThreads / 32][kPsQueue];
-  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  __shared__ float4 hx[kPsWarps][32];          // home atoms (FP32)
+  __shared__ float4 nx[kPsWarps][kPsPiece];    // neighbour piece (FP32, image shift applied)
+  __shared__ int32_t cur[kPsWarps][32];        // per home atom: pairs kept so far
+  __shared__ int32_t qj[kPsWarps][kPsQueue];
+  __shared__ uint32_t qi[kPsWarps][kPsQueue];
+  __shared__ int32_t qa[kPsWarps][kPsQueue];
+  const int64_t cw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  if (i >= n) return;
-  const double xi0 = xs[3 * i], xi1 = xs[3 * i + 1], xi2 = xs[3 * i + 2];
-  const float fi0 = (float)xi0, fi1 = (float)xi1, fi2 = (float)xi2;
-  // Slab of atom i, recomputed from its wrapped position.  It may differ from the slab used for
-  // binning only for atoms within rounding of a slab face; the search range keeps a relative
-  // margin of 1e-6, so every pair within the cutoff is still visited.
-  int ci[3];
-  for (int a = 0; a < 3; ++a) {
-    double s = (g.G[3 * a] * xi0 + g.G[3 * a + 1] * xi1) + g.G[3 * a + 2] * xi2;
-    int c = (int)floor(s * (double)g.nc[a]);
-    ci[a] = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
-  }
+  if (cw >= ncells) return;
+  const unsigned lt = (1u << lane) - 1u;
+  const int c0 = (int)(cw / ((int64_t)g.nc[1] * g.nc[2])), c1 = (int)((cw / g.nc[2]) % g.nc[1]),
+            c2 = (int)(cw % g.nc[2]);
+  const int hlin = cell_linear(g, c0, c1, c2);
+  const int hs = cstart[hlin], he = cstart[hlin + 1];
   const float hf[9] = {(float)g.H[0], (float)g.H[1], (float)g.H[2], (float)g.H[3], (float)g.H[4],
                        (float)g.H[5], (float)g.H[6], (float)g.H[7], (float)g.H[8]};
-  int out = FILL ? row_ptr[i] : 0;
-  int cnt = 0, qn = 0;
-  // canonical FP64 test of the first nb queued survivors (in queue order)
-  auto batch = [&](int nb) {
-    bool keep = false;
-    double dv0 = 0, dv1 = 0, dv2 = 0;
-    int j = 0;
-    uint32_t pim = 0;
-    if (lane < nb) {
-      j = qj[wq][lane];
-      pim = qi[wq][lane];
-      const int im0 = (int8_t)(pim & 0xff), im1 = (int8_t)((pim >> 8) & 0xff), im2 = (int8_t)((pim >> 16) & 0xff);
-      double sh[3];
-      for (int c = 0; c < 3; ++c)
-        sh[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)im0, g.H[c]), __dmul_rn((double)im1, g.H[3 + c])),
-                          __dmul_rn((double)im2, g.H[6 + c]));
-      dv0 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j], xi0), sh[0]);
-      dv1 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j + 1], xi1), sh[1]);
-      dv2 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j + 2], xi2), sh[2]);
-      const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dv0, dv0), __dmul_rn(dv1, dv1)), __dmul_rn(dv2, dv2));
-      keep = d2 < g.R2;
+  for (int h0 = hs; h0 < he; h0 += 32) {
+    const int ga = he - h0 < 32 ? he - h0 : 32;
+    if (lane < ga) {
+      const int64_t i = h0 + lane;
+      hx[wq][lane] = make_float4((float)xs[3 * i], (float)xs[3 * i + 1], (float)xs[3 * i + 2], 0.f);
+      cur[wq][lane] = 0;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (FILL && keep) {
-      const int pos = out + cnt + __popc(m & ((1u << lane) - 1u));
-      col[pos] = j;
-      img[pos] = pim;
-      base[pos] = make_float4((float)dv0, (float)dv1, (float)dv2, 0.0f);
-    }
-    cnt += __popc(m);
-  };
-  for (int d0 = -g.M[0]; d0 <= g.M[0]; ++d0)
-    for (int d1 = -g.M[1]; d1 <= g.M[1]; ++d1)
-      for (int d2 = -g.M[2]; d2 <= g.M[2]; ++d2) {
-        int cc[3] = {ci[0] + d0, ci[1] + d1, ci[2] + d2};
-        int im[3], w[3];
-        for (int a = 0; a < 3; ++a) {
-          int q = cc[a] >= 0 ? cc[a] / g.nc[a] : -((-cc[a] + g.nc[a] - 1) / g.nc[a]);
-          im[a] = q;
-          w[a] = cc[a] - q * g.nc[a];
-        }
-        float shf[3];
+    __syncwarp();
+    int qn = 0;
+    // canonical FP64 test of the first nb queued survivors (in queue order); kept pairs go to
+    // their home atom's row at its cursor, ranked among this batch's lanes of the same atom
+    auto batch = [&](int nb) {
+      bool keep = false;
+      double dv0 = 0, dv1 = 0, dv2 = 0;
+      int j = 0, a = 32 + lane;   // lanes without an entry get keys no home atom has
+      uint32_t pim = 0;
+      if (lane < nb) {
+        j = qj[wq][lane];
+        pim = qi[wq][lane];
+        a = qa[wq][lane];
+        const int64_t i = h0 + a;
+        const int im0 = (int8_t)(pim & 0xff), im1 = (int8_t)((pim >> 8) & 0xff), im2 = (int8_t)((pim >> 16) & 0xff);
+        double sh[3];
         for (int c = 0; c < 3; ++c)
-          shf[c] = fmaf((float)im[0], hf[c], fmaf((float)im[1], hf[3 + c], (float)im[2] * hf[6 + c]));
-        const bool zero_img = (im[0] == 0) && (im[1] == 0) && (im[2] == 0);
-        const uint32_t pim = pack_img(im[0], im[1], im[2]);
-        const int lin = cell_linear(g, w[0], w[1], w[2]);
-        const int b = cstart[lin], e = cstart[lin + 1];
-        for (int j0 = b; j0 < e; j0 += 32) {
-          const int j = j0 + lane;
-          bool pass = false;
-          if (j < e) {
-            const float a0 = ((float)xs[3 * (int64_t)j] - fi0) + shf[0];
-            const float a1 = ((float)xs[3 * (int64_t)j + 1] - fi1) + shf[1];
-            const float a2 = ((float)xs[3 * (int64_t)j + 2] - fi2) + shf[2];
-            pass = fmaf(a2, a2, fmaf(a1, a1, a0 * a0)) < r2f && !(zero_img && j == (int)i);
+          sh[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)im0, g.H[c]), __dmul_rn((double)im1, g.H[3 + c])),
+                            __dmul_rn((double)im2, g.H[6 + c]));
+        dv0 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j], xs[3 * i]), sh[0]);
+        dv1 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j + 1], xs[3 * i + 1]), sh[1]);
+        dv2 = __dadd_rn(__dsub_rn(xs[3 * (int64_t)j + 2], xs[3 * i + 2]), sh[2]);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dv0, dv0), __dmul_rn(dv1, dv1)), __dmul_rn(dv2, dv2));
+        keep = d2 < g.R2;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      const unsigned peers = __match_any_sync(0xffffffffu, a);
+      const int before = __popc(m & peers & lt);
+      if (FILL && keep) {
+        const int pos = row_ptr[h0 + a] + cur[wq][a] + before;
+        col[pos] = j;
+        img[pos] = pim;
+        base[pos] = make_float4((float)dv0, (float)dv1, (float)dv2, 0.0f);
+      }
+      __syncwarp();
+      if (lane < nb && (peers & lt) == 0) cur[wq][a] += __popc(m & peers);   // one lane per home atom
+      __syncwarp();
+    };
+    for (int d0 = -g.M[0]; d0 <= g.M[0]; ++d0)
+      for (int d1 = -g.M[1]; d1 <= g.M[1]; ++d1)
+        for (int d2 = -g.M[2]; d2 <= g.M[2]; ++d2) {
+          int cc[3] = {c0 + d0, c1 + d1, c2 + d2};
+          int im[3], w[3];
+          for (int a = 0; a < 3; ++a) {
+            int q = cc[a] >= 0 ? cc[a] / g.nc[a] : -((-cc[a] + g.nc[a] - 1) / g.nc[a]);
+            im[a] = q;
+            w[a] = cc[a] - q * g.nc[a];
           }
-          const unsigned m = __ballot_sync(0xffffffffu, pass);
-          if (pass) {
-            const int slot = qn + __popc(m & ((1u << lane) - 1u));
-            qj[wq][slot] = j;
-            qi[wq][slot] = pim;
-          }
-          qn += __popc(m);
-          __syncwarp();
-          if (qn >= 32) {
-            batch(32);
+          float shf[3];
+          for (int c = 0; c < 3; ++c)
+            shf[c] = fmaf((float)im[0], hf[c], fmaf((float)im[1], hf[3 + c], (float)im[2] * hf[6 + c]));
+          const bool zero_img = (im[0] == 0) && (im[1] == 0) && (im[2] == 0);
+          const uint32_t pim = pack_img(im[0], im[1], im[2]);
+          const int nlin = cell_linear(g, w[0], w[1], w[2]);
+          const int bs = cstart[nlin], be = cstart[nlin + 1];
+          for (int b0 = bs; b0 < be; b0 += kPsPiece) {
+            const int nb = be - b0 < kPsPiece ? be - b0 : kPsPiece;
+            for (int t = lane; t < nb; t += 32) {
+              const int64_t jj = b0 + t;
+              nx[wq][t] = make_float4((float)xs[3 * jj] + shf[0], (float)xs[3 * jj + 1] + shf[1],
+                                      (float)xs[3 * jj + 2] + shf[2], 0.f);
+            }
             __syncwarp();
-            // move the overflow (at most 31 entries) to the front of the queue
-            int32_t mj = 0;
-            uint32_t mi = 0;
-            if (lane + 32 < qn) { mj = qj[wq][lane + 32]; mi = qi[wq][lane + 32]; }
-            __syncwarp();
-            if (lane + 32 < qn) { qj[wq][lane] = mj; qi[wq][lane] = mi; }
-            qn -= 32;
-            __syncwarp();
+            const int total = ga * nb;
+            for (int p0 = 0; p0 < total; p0 += 32) {
+              const int p = p0 + lane;
+              bool pass = false;
+              int a = 0, bb = 0;
+              if (p < total) {
+                a = p / nb;
+                bb = p - a * nb;
+                const float4 y = nx[wq][bb], x = hx[wq][a];
+                const float e0 = y.x - x.x, e1 = y.y - x.y, e2 = y.z - x.z;
+                pass = fmaf(e2, e2, fmaf(e1, e1, e0 * e0)) < r2f && !(zero_img && b0 + bb == h0 + a);
+              }
+              const unsigned m = __ballot_sync(0xffffffffu, pass);
+              if (pass) {
+                const int slot = qn + __popc(m & lt);
+                qj[wq][slot] = b0 + bb;
+                qi[wq][slot] = pim;
+                qa[wq][slot] = a;
+              }
+              qn += __popc(m);
+              __syncwarp();
+              if (qn >= 32) {
+                batch(32);
+                // move the overflow (at most 31 entries) to the front of the queue
+                int32_t mj = 0, ma = 0;
+                uint32_t mi = 0;
+                if (lane + 32 < qn) { mj = qj[wq][lane + 32]; mi = qi[wq][lane + 32]; ma = qa[wq][lane + 32]; }
+                __syncwarp();
+                if (lane + 32 < qn) { qj[wq][lane] = mj; qi[wq][lane] = mi; qa[wq][lane] = ma; }
+                qn -= 32;
+                __syncwarp();
+              }
+            }
+            __syncwarp();   // the piece is read before the next one overwrites it
           }
         }
-      }
-  if (qn > 0) batch(qn);
-  if (!FILL && lane == 0) count[i] = cnt;
+    if (qn > 0) batch(qn);
+    if (!FILL && lane < ga) count[h0 + lane] = cur[wq][lane];
+    __syncwarp();
+  }
 }
 
 // FP32 threshold of the prefilter: R^2 plus a bound on the FP32 error of the squared distance.
@@ -265,13 +297,14 @@ void launch_pair_search(cudaStream_t st, bool fill, int64_t n, const double* xw_
                         const int32_t* cell_start, const CellGeom& g, int32_t* count,
                         const int32_t* row_ptr, int32_t* col, uint32_t* img, float4* base) {
   if (n == 0) return;
-  int64_t threads = n * 32;
-  unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
+  const int64_t ncells = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];   // one warp per grid cell
+  const int64_t threads = ncells * 32;
+  const unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
   const float r2f = prefilter_r2(g);
   if (fill)
-    { LaunchScope ls_(st); k_pair_search<true><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, r2f, count, row_ptr, col, img, base); }
+    { LaunchScope ls_(st); k_pair_search<true><<<blocks, kThreads, 0, st>>>(ncells, xw_s, cell_start, g, r2f, count, row_ptr, col, img, base); }
   else
-    { LaunchScope ls_(st); k_pair_search<false><<<blocks, kThreads, 0, st>>>(n, xw_s, cell_start, g, r2f, count, row_ptr, col, img, base); }
+    { LaunchScope ls_(st); k_pair_search<false><<<blocks, kThreads, 0, st>>>(ncells, xw_s, cell_start, g, r2f, count, row_ptr, col, img, base); }
 }
 
 // ------------------------------------------------------------------------------- reverse edges
