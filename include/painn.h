@@ -246,6 +246,21 @@ int ctd_serve_poll(ctd_server *s, int64_t request_id, int32_t *state, int32_t *s
  * CTD_ERR_STATE if the request is queued or finished (poll returns the final state). */
 int ctd_serve_snapshot(ctd_server *s, int64_t request_id, double *positions, double *velocities,
                        int32_t *steps_done);
+/* Nose-Hoover chain thermostat for one queued request (NVT; the chain and its parameters as in
+ * ctd_md_set_thermostat: chain = M thermostats 0..16, 0 = NVE; temperature (K) and tau (fs)
+ * positive and finite; n >= 2).  xi[M], vxi[M] (host, may both be NULL = zero) restore a chain
+ * state saved by ctd_serve_thermostat, to continue a checkpointed NVT replica.  Each step of the
+ * replica is then a chain half step, the velocity-Verlet step, and a chain half step, like
+ * ctd_md_run's NVT step; the kinetic energies recorded for it are those after the chain's
+ * velocity factor.  Replicas with and without thermostats share the batch, and a replica's
+ * trajectory still does not depend on the others.  CTD_ERR_STATE unless the request is queued. */
+int ctd_serve_set_thermostat(ctd_server *s, int64_t request_id, double temperature, double tau,
+                             int32_t chain, const double *xi, const double *vxi);
+/* Chain state of a request with a thermostat: xi[M], vxi[M] (host; the current state while
+ * resident, the final one when finished) and ethermo, the chain energy recorded with each
+ * energy of ctd_serve_poll (up to nsteps+1 values).  Any output may be NULL.  CTD_ERR_STATE
+ * without a thermostat. */
+int ctd_serve_thermostat(ctd_server *s, int64_t request_id, double *xi, double *vxi, double *ethermo);
 int ctd_serve_stats(ctd_server *s, int64_t *resident_atoms, int32_t *resident_replicas,
                     int32_t *queued, int64_t *bytes_held);
 const char *ctd_serve_last_error(ctd_server *s);

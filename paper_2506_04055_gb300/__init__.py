@@ -230,6 +230,7 @@ class Server:
         self.srv = _lib.ctd_serve_create(self.desc, params, hbm_budget_bytes, max_replicas, dt, stream)
         self._n = {}
         self._steps = {}
+        self._chain = {}
 
     def close(self):
         if getattr(self, "srv", None):
@@ -285,6 +286,29 @@ class Server:
         v = np.empty((n, 3))
         done = _lib.ctd_serve_snapshot(self.srv, rid, _ptr(x), _ptr(v))
         return {"positions": x, "velocities": v, "steps_done": done}
+
+    def set_thermostat(self, rid: int, temperature: float, tau: float, chain: int = 3, xi=None, vxi=None):
+        """Nose-Hoover chain for a queued request (chain 0: NVE); xi / vxi restore a saved chain."""
+        if (xi is None) != (vxi is None):
+            raise ValueError("give both xi and vxi, or neither")
+        a = b = None
+        if xi is not None:
+            a = _host(xi, np.float64)
+            b = _host(vxi, np.float64)
+            if a.shape != (chain,) or b.shape != (chain,):
+                raise ValueError("xi and vxi need one value per thermostat")
+        _lib.ctd_serve_set_thermostat(self.srv, rid, float(temperature), float(tau), int(chain),
+                                      _ptr(a) if a is not None else None, _ptr(b) if b is not None else None)
+        self._chain[rid] = int(chain)
+
+    def thermostat(self, rid: int):
+        """Chain state (xi, vxi) and the chain energy recorded with each step of a request."""
+        M, ns = self._chain.get(rid, 0), self._steps[rid]
+        xi = np.empty(max(M, 1))
+        vxi = np.empty(max(M, 1))
+        eth = np.full(ns + 1, np.nan)
+        _lib.ctd_serve_thermostat(self.srv, rid, _ptr(xi), _ptr(vxi), _ptr(eth))
+        return {"xi": xi[:M], "vxi": vxi[:M], "ethermo": eth}
 
     def stats(self):
         return _lib.ctd_serve_stats(self.srv)

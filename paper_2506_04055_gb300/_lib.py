@@ -41,6 +41,7 @@ EXPORTS = [
     "ctd_create", "ctd_load_params", "ctd_build_neighbors", "ctd_get_pairs", "ctd_compute",
     "ctd_set_energy_out", "ctd_md_set_state", "ctd_md_run", "ctd_md_get_state",
     "ctd_md_set_thermostat", "ctd_md_get_thermostat", "ctd_md_set_thermostat_state", "ctd_serve_snapshot",
+    "ctd_serve_set_thermostat", "ctd_serve_thermostat",
     "ctd_set_option", "ctd_profile_enable", "ctd_profile_read", "ctd_gemm_bf16",
     "ctd_serve_create", "ctd_serve_submit", "ctd_serve_step", "ctd_serve_poll", "ctd_serve_stats",
     "ctd_serve_last_error", "ctd_serve_destroy", "ctd_domains_create", "ctd_domains_compute",
@@ -107,6 +108,8 @@ def load(path: str = LIB_PATH):
         "ctd_md_get_thermostat": ([P, P, P, P], ctypes.c_int),
         "ctd_md_set_thermostat_state": ([P, P, P], ctypes.c_int),
         "ctd_serve_snapshot": ([P, I64, P, P, P], ctypes.c_int),
+        "ctd_serve_set_thermostat": ([P, I64, D, D, I32, P, P], ctypes.c_int),
+        "ctd_serve_thermostat": ([P, I64, P, P, P], ctypes.c_int),
         "ctd_set_option": ([P, I32, I64], ctypes.c_int),
         "ctd_profile_enable": ([P, I32], ctypes.c_int),
         "ctd_profile_read": ([P, P, P, I32], ctypes.c_int),
@@ -284,6 +287,14 @@ def ctd_serve_snapshot(srv, rid, positions_ptr, velocities_ptr):
     done = ctypes.c_int32()
     serve_check(srv, load().ctd_serve_snapshot(srv, rid, positions_ptr, velocities_ptr, ctypes.byref(done)))
     return done.value
+
+
+def ctd_serve_set_thermostat(srv, rid, temperature, tau, chain, xi_ptr=None, vxi_ptr=None):
+    serve_check(srv, load().ctd_serve_set_thermostat(srv, rid, temperature, tau, chain, xi_ptr, vxi_ptr))
+
+
+def ctd_serve_thermostat(srv, rid, xi_ptr=None, vxi_ptr=None, eth_ptr=None):
+    serve_check(srv, load().ctd_serve_thermostat(srv, rid, xi_ptr, vxi_ptr, eth_ptr))
 
 
 def ctd_serve_stats(srv):

@@ -165,6 +165,10 @@ struct NhcParams {
 void launch_nhc_half(cudaStream_t st, const NhcParams& p, double h, const double* ke, double* state);
 void launch_nhc_energy(cudaStream_t st, const NhcParams& p, const double* state, double* out);
 void launch_scale_v(cudaStream_t st, int64_t n, const double* g, double* v);
+void launch_rep_nhc_half(cudaStream_t st, int R, const NhcParams* params, double h, const double* ke, int ke_stride,
+                         const int32_t* flags, double* states, int state_stride, double* g, double* ke_after,
+                         double* eth);
+void launch_scale_v_rep(cudaStream_t st, int64_t n, const int32_t* rep, const double* g, double* v);
 void launch_kick(cudaStream_t st, int64_t n, double dt, const float* f, const double* m, double* v);
 void launch_kinetic(cudaStream_t st, int64_t n, const double* m, const double* v, double* partials, int nb);
 void launch_sum_partials(cudaStream_t st, int nb, int width, const double* partials, double* out, double scale);

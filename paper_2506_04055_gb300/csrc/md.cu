@@ -38,12 +38,12 @@ __device__ double nhc_force(int j, double ke, const NhcParams& p, const double* 
   return (p.Q[j - 1] * vxi[j - 1] * vxi[j - 1] - p.kT) / p.Q[j];
 }
 
-__global__ void k_nhc_half(NhcParams p, double h, const double* __restrict__ ke_in, double* __restrict__ state) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// One chain half step of length h from the kinetic energy ke; returns the velocity factor and
+// stores it in state[2M].
+__device__ double nhc_half_step(const NhcParams& p, double h, double ke, double* state) {
   const int M = p.M;
   double* xi = state;
   double* vxi = state + M;
-  double ke = *ke_in;
   vxi[M - 1] += 0.5 * h * nhc_force(M - 1, ke, p, vxi);
   for (int j = M - 2; j >= 0; --j) {
     const double e = exp(-0.25 * h * vxi[j + 1]);
@@ -62,15 +62,55 @@ __global__ void k_nhc_half(NhcParams p, double h, const double* __restrict__ ke_
   }
   vxi[M - 1] += 0.5 * h * nhc_force(M - 1, ke, p, vxi);
   state[2 * M] = g;
+  return g;
+}
+
+__global__ void k_nhc_half(NhcParams p, double h, const double* __restrict__ ke_in, double* __restrict__ state) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  nhc_half_step(p, h, *ke_in, state);
+}
+
+// Chain energy of one replica's state.
+__device__ double nhc_chain_energy(const NhcParams& p, const double* state) {
+  double e = 0.0;
+  for (int j = 0; j < p.M; ++j)
+    e += 0.5 * p.Q[j] * state[p.M + j] * state[p.M + j] + (j == 0 ? p.Nf * p.kT : p.kT) * state[j];
+  return e;
+}
+
+// Served replicas, one thread each: replicas with a thermostat (M > 0) that integrate this step
+// (flags bit 0) advance their chain from their kinetic energy ke[r * ke_stride]; the velocity
+// factor goes to g[r] (1 for the others).  ke_after[r] receives the kinetic energy after the
+// factor and eth[r] the chain energy (both may be null).
+__global__ void k_rep_nhc_half(int R, const NhcParams* __restrict__ params, double h, const double* __restrict__ ke,
+                               int ke_stride, const int32_t* __restrict__ flags, double* __restrict__ states,
+                               int state_stride, double* __restrict__ g, double* __restrict__ ke_after,
+                               double* __restrict__ eth) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const NhcParams p = params[r];
+  const double k = ke[(int64_t)r * ke_stride];
+  double* st = states + (int64_t)r * state_stride;
+  double gr = 1.0;
+  if (p.M > 0 && (flags[r] & 1)) gr = nhc_half_step(p, h, k, st);
+  g[r] = gr;
+  if (ke_after) ke_after[r] = k * gr * gr;
+  if (eth) eth[r] = p.M > 0 ? nhc_chain_energy(p, st) : 0.0;
+}
+
+// v *= g[replica of the atom]
+__global__ void k_scale_v_rep(int64_t n, const int32_t* __restrict__ rep, const double* __restrict__ g,
+                              double* __restrict__ v) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double gk = g[rep[k]];
+  for (int c = 0; c < 3; ++c) v[3 * k + c] *= gk;
 }
 
 // Energy of the chain: sum_j Q_j vxi_j^2 / 2 + Nf kT xi_1 + kT sum_{j>1} xi_j.
 __global__ void k_nhc_energy(NhcParams p, const double* __restrict__ state, double* __restrict__ out) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double e = 0.0;
-  for (int j = 0; j < p.M; ++j)
-    e += 0.5 * p.Q[j] * state[p.M + j] * state[p.M + j] + (j == 0 ? p.Nf * p.kT : p.kT) * state[j];
-  *out = e;
+  *out = nhc_chain_energy(p, state);
 }
 
 __global__ void k_scale_v(int64_t n3, const double* __restrict__ g, double* __restrict__ v) {
@@ -191,6 +231,18 @@ void launch_nhc_half(cudaStream_t st, const NhcParams& p, double h, const double
 void launch_nhc_energy(cudaStream_t st, const NhcParams& p, const double* state, double* out) {
   LaunchScope ls_(st);
   k_nhc_energy<<<1, 32, 0, st>>>(p, state, out);
+}
+void launch_rep_nhc_half(cudaStream_t st, int R, const NhcParams* params, double h, const double* ke, int ke_stride,
+                         const int32_t* flags, double* states, int state_stride, double* g, double* ke_after,
+                         double* eth) {
+  if (R > 0) {
+    LaunchScope ls_(st);
+    k_rep_nhc_half<<<(R + 127) / 128, 128, 0, st>>>(R, params, h, ke, ke_stride, flags, states, state_stride, g,
+                                                   ke_after, eth);
+  }
+}
+void launch_scale_v_rep(cudaStream_t st, int64_t n, const int32_t* rep, const double* g, double* v) {
+  if (n) { LaunchScope ls_(st); k_scale_v_rep<<<nblk(n), kThreads, 0, st>>>(n, rep, g, v); }
 }
 void launch_scale_v(cudaStream_t st, int64_t n, const double* g, double* v) {
   if (n) { LaunchScope ls_(st); k_scale_v<<<nblk(3 * n), kThreads, 0, st>>>(3 * n, g, v); }

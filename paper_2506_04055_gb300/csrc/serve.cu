@@ -94,15 +94,17 @@ __global__ void k_rep_reduce(const int64_t* __restrict__ aoff, const int32_t* __
 }
 
 // Velocity-Verlet halves for replicas whose flag says "integrating" (a replica's first step
-// only evaluates its forces).
+// only evaluates its forces).  g (may be null): per-replica factor of the thermostat's half step,
+// applied to the velocities before the kick (1 for replicas without a thermostat).
 __global__ void k_kick_drift_masked(int64_t n, double dt, const float* __restrict__ force, const double* __restrict__ mass,
                                     const int32_t* __restrict__ rep, const int32_t* __restrict__ flags,
-                                    double* __restrict__ x, double* __restrict__ v) {
+                                    const double* __restrict__ g, double* __restrict__ x, double* __restrict__ v) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n || !(flags[rep[k]] & 1)) return;
+  const double gk = g ? g[rep[k]] : 1.0;
   const double s = 0.5 * dt * 9.648533212331002e-3 / mass[k];
   for (int c = 0; c < 3; ++c) {
-    const double vc = v[3 * k + c] + s * (double)force[3 * k + c];
+    const double vc = gk * v[3 * k + c] + s * (double)force[3 * k + c];
     v[3 * k + c] = vc;
     x[3 * k + c] += dt * vc;
   }
@@ -124,6 +126,8 @@ __global__ void k_iota(int64_t n, int32_t* __restrict__ out) {
 }
 
 static inline unsigned blk(int64_t w) { return (unsigned)((w + kThreads - 1) / kThreads); }
+
+constexpr int kChainStride = 40;   // doubles per replica: xi [M], vxi [M], last factor (M <= 16)
 
 }  // namespace ctd
 
@@ -150,6 +154,11 @@ struct Replica {
   size_t est_bytes = 0;
   int32_t rebuilds = 0;
   std::vector<double> out_x, out_v;
+  // Nose-Hoover chain (chain length 0: NVE); the chain state lives on the device while the
+  // replica is resident and in `chain` otherwise
+  int nhc_M = 0;
+  double nhc_T = 0.0, nhc_tau = 0.0;
+  std::vector<double> chain, eth;
 };
 
 }  // namespace
@@ -165,6 +174,10 @@ struct ctd_server {
   size_t resident_est = 0;
   // batch bookkeeping (device)
   DBuf rep_table, rep_off, rep_of_atom, rep_flags, rep_out;
+  // thermostats of the resident replicas (when any has one): parameters, chain states,
+  // kinetic energy after the last step, velocity factors, chain energies
+  DBuf rep_np, rep_chain, rep_ke, rep_g, rep_eth;
+  bool any_nvt = false;
   // staging for repacking the batch arrays
   DBuf st_x, st_xref, st_v, st_m, st_z, st_f;
   // build scratch (largest replica)
@@ -173,7 +186,7 @@ struct ctd_server {
   bool lists_dirty = true;
   std::string err;
   std::vector<DBuf*> bufs() {
-    return {&rep_table, &rep_off, &rep_of_atom, &rep_flags, &rep_out, &st_x, &st_xref, &st_v, &st_m, &st_z, &st_f,
+    return {&rep_table, &rep_off, &rep_of_atom, &rep_flags, &rep_out, &rep_np, &rep_chain, &rep_ke, &rep_g, &rep_eth, &st_x, &st_xref, &st_v, &st_m, &st_z, &st_f,
             &b_xw, &b_wrap, &b_cell, &b_ccount, &b_cstart, &b_cursor, &b_tmp, &b_perm, &b_inv, &b_xws, &b_xnew,
             &b_count, &b_img, &b_scan, &b_i32, &b_d3};
   }
@@ -305,6 +318,15 @@ int collect(ctd_server* s, Replica& R) {
 int repack(ctd_server* s, const std::vector<Replica*>& next) {
   ctd_ctx* c = s->c;
   cudaStream_t st = c->st;
+  if (s->any_nvt && !s->resident.empty()) {   // chain states of the outgoing set back to the host
+    const size_t R0 = s->resident.size();
+    std::vector<double> h(kChainStride * R0);
+    CUDA_OK(c, cudaMemcpyAsync(h.data(), s->rep_chain.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+    CUDA_OK(c, cudaStreamSynchronize(st));
+    for (size_t k = 0; k < R0; ++k)
+      if (s->resident[k]->nhc_M > 0)
+        s->resident[k]->chain.assign(h.begin() + kChainStride * k, h.begin() + kChainStride * (k + 1));
+  }
   int64_t N = 0;
   for (Replica* R : next) N += R->n;
   const int64_t N1 = N > 0 ? N : 1;
@@ -356,6 +378,35 @@ int repack(ctd_server* s, const std::vector<Replica*>& next) {
       LaunchScope ls_(st);
       k_fill_i32<<<blk(next[k]->n), kThreads, 0, st>>>(next[k]->n, (int32_t)k, P<int32_t>(s->rep_of_atom) + offs[k]);
     }
+  // thermostat tables in the new order
+  s->any_nvt = false;
+  for (Replica* Rp : next) s->any_nvt = s->any_nvt || Rp->nhc_M > 0;
+  if (s->any_nvt) {
+    const int64_t R1 = R > 0 ? R : 1;
+    ENSURE(c, s->rep_np, sizeof(NhcParams) * R1);
+    ENSURE(c, s->rep_chain, sizeof(double) * kChainStride * R1);
+    ENSURE(c, s->rep_ke, sizeof(double) * R1);
+    ENSURE(c, s->rep_g, sizeof(double) * R1);
+    ENSURE(c, s->rep_eth, sizeof(double) * R1);
+    std::vector<NhcParams> np(R);
+    std::vector<double> ch(kChainStride * R, 0.0), ke(R, 0.0);
+    for (int64_t k = 0; k < R; ++k) {
+      const Replica& Q = *next[k];
+      NhcParams& p = np[k];
+      memset(&p, 0, sizeof(p));
+      p.M = Q.nhc_M;
+      if (Q.nhc_M > 0) {   // Nf = 3n - 3: the centre of mass is at rest
+        p.kT = 8.617333262e-5 * Q.nhc_T;
+        p.Nf = 3.0 * (double)Q.n - 3.0;
+        for (int j = 0; j < p.M; ++j) p.Q[j] = (j == 0 ? p.Nf : 1.0) * p.kT * Q.nhc_tau * Q.nhc_tau;
+        std::copy(Q.chain.begin(), Q.chain.end(), ch.begin() + kChainStride * k);
+      }
+      if (!Q.ekin.empty()) ke[k] = Q.ekin.back();
+    }
+    CUDA_OK(c, cudaMemcpyAsync(s->rep_np.p, np.data(), sizeof(NhcParams) * R, cudaMemcpyHostToDevice, st));
+    CUDA_OK(c, cudaMemcpyAsync(s->rep_chain.p, ch.data(), sizeof(double) * ch.size(), cudaMemcpyHostToDevice, st));
+    CUDA_OK(c, cudaMemcpyAsync(s->rep_ke.p, ke.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  }
   CUDA_OK(c, cudaStreamSynchronize(st));
   s->resident = next;
   s->lists_dirty = true;
@@ -547,13 +598,18 @@ int ctd_serve_step(ctd_server* s, int32_t* n_resident, int32_t* n_admitted, int3
   ENSURE(c, c->force_s, sizeof(float) * 3 * (N > 0 ? N : 1));
   ENSURE(c, c->delta, sizeof(float4) * (N > 0 ? N : 1));
   ENSURE(c, c->maxd, sizeof(unsigned int) * 4);
-  // 3. first half kick + drift
+  // 3. thermostat half step (replicas with one), first half kick + drift
   {
     StageGuard sg(STG_MD);
+    if (s->any_nvt)
+      launch_rep_nhc_half(st, (int)nres, P<NhcParams>(s->rep_np), 0.5 * s->dt, P<double>(s->rep_ke), 1,
+                          P<int32_t>(s->rep_flags), P<double>(s->rep_chain), kChainStride, P<double>(s->rep_g),
+                          nullptr, nullptr);
     LaunchScope ls_(st);
     k_kick_drift_masked<<<blk(N), kThreads, 0, st>>>(N, s->dt, P<float>(c->force_s), P<double>(c->md_m),
                                                      P<int32_t>(s->rep_of_atom), P<int32_t>(s->rep_flags),
-                                                     P<double>(c->x_s), P<double>(c->md_v));
+                                                     s->any_nvt ? P<double>(s->rep_g) : nullptr, P<double>(c->x_s),
+                                                     P<double>(c->md_v));
   }
   // 4. per-replica displacement since its last build; rebuild the replicas past skin/2
   {
@@ -587,7 +643,8 @@ int ctd_serve_step(ctd_server* s, int32_t* n_resident, int32_t* n_admitted, int3
   if (r) return r;
   r = evaluate(c, true);
   if (r) return r;
-  // 6. second half kick; per-replica energies and virial
+  // 6. second half kick; per-replica energies and virial; thermostat half step from the kinetic
+  // energy after the kick and the velocity factor it gives (kinetic energy recorded after it)
   {
     StageGuard sg(STG_MD);
     {
@@ -596,18 +653,33 @@ int ctd_serve_step(ctd_server* s, int32_t* n_resident, int32_t* n_admitted, int3
                                                  P<int32_t>(s->rep_of_atom), P<int32_t>(s->rep_flags),
                                                  P<double>(c->md_v));
     }
-    LaunchScope ls_(st);
-    k_rep_reduce<<<(unsigned)nres, kThreads, 0, st>>>(P<int64_t>(s->rep_off), P<int32_t>(c->arow), P<float>(c->eatom),
-                                                     P<double>(c->md_m), P<double>(c->md_v), P<float4>(c->delta),
-                                                     P<float4>(c->ar), P<float4>(c->hedge), 1, P<double>(s->rep_out));
+    {
+      LaunchScope ls_(st);
+      k_rep_reduce<<<(unsigned)nres, kThreads, 0, st>>>(P<int64_t>(s->rep_off), P<int32_t>(c->arow),
+                                                       P<float>(c->eatom), P<double>(c->md_m), P<double>(c->md_v),
+                                                       P<float4>(c->delta), P<float4>(c->ar), P<float4>(c->hedge), 1,
+                                                       P<double>(s->rep_out));
+    }
+    if (s->any_nvt) {
+      launch_rep_nhc_half(st, (int)nres, P<NhcParams>(s->rep_np), 0.5 * s->dt, P<double>(s->rep_out) + 1, 12,
+                          P<int32_t>(s->rep_flags), P<double>(s->rep_chain), kChainStride, P<double>(s->rep_g),
+                          P<double>(s->rep_ke), P<double>(s->rep_eth));
+      launch_scale_v_rep(st, N, P<int32_t>(s->rep_of_atom), P<double>(s->rep_g), P<double>(c->md_v));
+    }
   }
   CUDA_OK(c, cudaMemcpyAsync(ro.data(), s->rep_out.p, sizeof(double) * 12 * nres, cudaMemcpyDeviceToHost, st));
+  std::vector<double> ke(s->any_nvt ? nres : 0), eth(s->any_nvt ? nres : 0);
+  if (s->any_nvt) {
+    CUDA_OK(c, cudaMemcpyAsync(ke.data(), s->rep_ke.p, sizeof(double) * nres, cudaMemcpyDeviceToHost, st));
+    CUDA_OK(c, cudaMemcpyAsync(eth.data(), s->rep_eth.p, sizeof(double) * nres, cudaMemcpyDeviceToHost, st));
+  }
   r = check_status(c);
   if (r) return r;
   for (int64_t k = 0; k < nres; ++k) {
     Replica* R = s->resident[k];
     R->epot.push_back(ro[12 * k + 0]);
-    R->ekin.push_back(ro[12 * k + 1]);
+    R->ekin.push_back(s->any_nvt ? ke[k] : ro[12 * k + 1]);
+    if (R->nhc_M > 0) R->eth.push_back(eth[k]);
     for (int q = 0; q < 9; ++q) R->virial[q] = ro[12 * k + 3 + q];
     if (R->integrating) ++R->done;
     R->integrating = true;
@@ -646,6 +718,61 @@ int ctd_serve_snapshot(ctd_server* s, int64_t request_id, double* positions, dou
   if (positions) memcpy(positions, R->out_x.data(), sizeof(double) * R->out_x.size());
   if (velocities) memcpy(velocities, R->out_v.data(), sizeof(double) * R->out_v.size());
   if (steps_done) *steps_done = R->done;
+  return CTD_OK;
+}
+
+int ctd_serve_set_thermostat(ctd_server* s, int64_t request_id, double temperature, double tau, int32_t chain,
+                             const double* xi, const double* vxi) {
+  if (!s) return CTD_ERR_INVALID_ARG;
+  auto it = s->reps.find(request_id);
+  if (it == s->reps.end()) return sfail(s, CTD_ERR_INVALID_ARG, "unknown request");
+  Replica* R = it->second;
+  if (R->state != 0) return sfail(s, CTD_ERR_STATE, "the thermostat is set while the request is queued");
+  if (chain < 0 || chain > 16) return sfail(s, CTD_ERR_INVALID_ARG, "chain length must be 0..16");
+  if (chain > 0) {
+    if (!(temperature > 0.0 && std::isfinite(temperature) && tau > 0.0 && std::isfinite(tau)))
+      return sfail(s, CTD_ERR_INVALID_ARG, "temperature and tau must be positive and finite");
+    if (R->n < 2) return sfail(s, CTD_ERR_INVALID_ARG, "a thermostat needs at least two atoms");
+    if (!xi != !vxi) return sfail(s, CTD_ERR_INVALID_ARG, "give both xi and vxi, or neither");
+    if (xi)
+      for (int j = 0; j < chain; ++j)
+        if (!std::isfinite(xi[j]) || !std::isfinite(vxi[j]))
+          return sfail(s, CTD_ERR_INVALID_ARG, "non-finite chain state");
+  }
+  R->nhc_M = chain;
+  R->nhc_T = chain > 0 ? temperature : 0.0;
+  R->nhc_tau = chain > 0 ? tau : 0.0;
+  R->chain.assign(kChainStride, 0.0);
+  if (chain > 0 && xi)
+    for (int j = 0; j < chain; ++j) {
+      R->chain[j] = xi[j];
+      R->chain[chain + j] = vxi[j];
+    }
+  R->eth.clear();
+  return CTD_OK;
+}
+
+int ctd_serve_thermostat(ctd_server* s, int64_t request_id, double* xi, double* vxi, double* ethermo) {
+  if (!s) return CTD_ERR_INVALID_ARG;
+  Bind bind_(s->c);
+  auto it = s->reps.find(request_id);
+  if (it == s->reps.end()) return sfail(s, CTD_ERR_INVALID_ARG, "unknown request");
+  Replica* R = it->second;
+  if (R->nhc_M == 0) return sfail(s, CTD_ERR_STATE, "request has no thermostat");
+  const int M = R->nhc_M;
+  std::vector<double> ch = R->chain;
+  if (R->state == 1) {   // resident: the chain state is on the device
+    const auto pos = std::find(s->resident.begin(), s->resident.end(), R);
+    const size_t k = (size_t)(pos - s->resident.begin());
+    ch.assign(kChainStride, 0.0);
+    ctd_ctx* c = s->c;
+    CUDA_OK(c, cudaMemcpyAsync(ch.data(), P<double>(s->rep_chain) + kChainStride * k, sizeof(double) * kChainStride,
+                               cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(c, cudaStreamSynchronize(c->st));
+  }
+  if (xi) memcpy(xi, ch.data(), sizeof(double) * M);
+  if (vxi) memcpy(vxi, ch.data() + M, sizeof(double) * M);
+  if (ethermo && !R->eth.empty()) memcpy(ethermo, R->eth.data(), sizeof(double) * R->eth.size());
   return CTD_OK;
 }
 

@@ -165,3 +165,142 @@ def test_snapshot_restart_continues_trajectory():
     np.testing.assert_allclose(out["positions"], ref["positions"], rtol=0, atol=1e-6)
     np.testing.assert_allclose(out["velocities"], ref["velocities"], rtol=0, atol=1e-7)
     np.testing.assert_allclose(out["epot"][: N - K + 1], ref["epot"][K : N + 1], rtol=0, atol=1e-5)
+
+
+# ---- Nose-Hoover chain thermostat on served replicas (NVT) ----------------------------------
+
+NVT = (500.0, 25.0, 3)   # target temperature (K), tau (fs), chain length
+
+
+def _run_nvt_server(eng, blob, items, thermos, nsteps, late=0):
+    """Serve items (the last `late` of them submitted after three steps), each with its
+    thermostat (None: NVE); returns poll() and thermostat() results in submission order."""
+    srv = eng.Server(F, blob, T=T, n_species=S, precision="fp32", dt=DT)
+    ids = []
+
+    def submit(k):
+        sy, v = items[k]
+        rid = srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, nsteps, skin=1.0)
+        if thermos[k] is not None:
+            srv.set_thermostat(rid, *thermos[k])
+        ids.append(rid)
+
+    for k in range(len(items) - late):
+        submit(k)
+    for step in range(10 * nsteps + 50):
+        if late and step == 3:
+            for k in range(len(items) - late, len(items)):
+                submit(k)
+        srv.step()
+        if all(srv.poll(i)["state"] == 2 for i in ids) and (not late or step >= 3):
+            break
+    out = []
+    for k, i in enumerate(ids):
+        r = srv.poll(i)
+        if thermos[k] is not None:
+            r.update(srv.thermostat(i))
+        out.append(r)
+    srv.close()
+    return out
+
+
+def test_nvt_replica_matches_single_system_md():
+    """A served replica with a Nose-Hoover chain follows ctd_md_run's NVT trajectory (the two
+    reduce the kinetic energy in different orders: agreement to rounding)."""
+    eng = engine()
+    _, blob = model(F, T, S, seed=9, bias=0.1)
+    sy, v = _replicas()[0]
+    r = _run_nvt_server(eng, blob, [(sy, v)], [NVT], 30)[0]
+    with eng.Potential(F, T=T, n_species=S, params=blob) as pot:
+        pot.md_set_state(sy.species, sy.masses, sy.positions, v, sy.cell, skin=1.0)
+        pot.md_set_thermostat(*NVT)
+        ep, ek, _ = pot.md_run(30, DT)
+        xi, vxi, eth = pot.md_get_thermostat(30)
+        x, vv = pot.md_get_state()
+    assert r["state"] == 2 and r["steps_done"] == 30
+    assert np.abs(vxi).max() > 1e-4          # the chain moved
+    np.testing.assert_allclose(r["positions"], x, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(r["velocities"], vv, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(r["epot"], ep, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(r["ekin"], ek, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(r["ethermo"], eth, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(r["xi"], xi, rtol=1e-9, atol=1e-15)
+    np.testing.assert_allclose(r["vxi"], vxi, rtol=1e-9, atol=1e-15)
+
+
+def test_nvt_alone_equals_mixed():
+    """Thermostatted and plain replicas share the batch: each one's trajectory (and chain) is
+    bit-identical to its run alone, whatever the mix and admission time."""
+    eng = engine()
+    _, blob = model(F, T, S, seed=10, bias=0.1)
+    items = _replicas()
+    hot = (800.0, 15.0, 2)
+    alone_nvt = _run_nvt_server(eng, blob, [items[0]], [NVT], 12)[0]
+    alone_nve = _run_nvt_server(eng, blob, [items[1]], [None], 12)[0]
+    mixed = _run_nvt_server(eng, blob, [items[1], items[2], items[3], items[0]], [None, hot, None, NVT], 12, late=1)
+    for a, b in ((alone_nvt, mixed[3]), (alone_nve, mixed[0])):
+        for key in ("epot", "ekin", "positions", "velocities"):
+            np.testing.assert_array_equal(a[key], b[key])
+    for key in ("ethermo", "xi", "vxi"):
+        np.testing.assert_array_equal(alone_nvt[key], mixed[3][key])
+    assert np.isfinite(mixed[1]["ethermo"]).all() and np.abs(mixed[1]["vxi"]).max() > 0.0
+
+
+def test_nvt_checkpoint_restart():
+    """Snapshot and chain state of a resident NVT replica, resubmitted with the remaining steps
+    and the saved chain, continue its trajectory (new neighbour list: agreement to FP32
+    summation order)."""
+    eng = engine()
+    _, blob = model(F, T, S, seed=11, bias=0.1)
+    sy, v = _replicas()[0]
+    N, K = 20, 8
+    ref = _run_nvt_server(eng, blob, [(sy, v)], [NVT], N)[0]
+    srv = eng.Server(F, blob, T=T, n_species=S, precision="fp32", dt=DT)
+    rid = srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, N, skin=1.0)
+    srv.set_thermostat(rid, *NVT)
+    for _ in range(K + 1):
+        srv.step()
+    snap = srv.snapshot(rid)
+    chain = srv.thermostat(rid)
+    with pytest.raises(eng.CtdError):
+        srv.set_thermostat(rid, *NVT)   # resident: the thermostat is fixed
+    srv.close()
+    assert snap["steps_done"] == K and np.abs(chain["vxi"]).max() > 1e-5
+    srv2 = eng.Server(F, blob, T=T, n_species=S, precision="fp32", dt=DT)
+    rid2 = srv2.submit(sy.species, sy.masses, snap["positions"], snap["velocities"], sy.cell, N - K, skin=1.0)
+    srv2.set_thermostat(rid2, *NVT, xi=chain["xi"], vxi=chain["vxi"])
+    for _ in range(N - K + 5):
+        if srv2.poll(rid2)["state"] == 2:
+            break
+        srv2.step()
+    out = srv2.poll(rid2)
+    out.update(srv2.thermostat(rid2))
+    srv2.close()
+    assert out["state"] == 2
+    np.testing.assert_allclose(out["positions"], ref["positions"], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(out["velocities"], ref["velocities"], rtol=0, atol=1e-7)
+    np.testing.assert_allclose(out["xi"], ref["xi"], rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(out["vxi"], ref["vxi"], rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(out["ethermo"][: N - K + 1], ref["ethermo"][K : N + 1], rtol=0, atol=1e-6)
+
+
+def test_serve_thermostat_arguments_are_checked():
+    eng = engine()
+    _, blob = model(F, T, S, seed=12)
+    sy, v = _replicas()[2]
+    with eng.Server(F, blob, T=T, n_species=S, dt=DT) as srv:
+        rid = srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, 2, skin=1.0)
+        for bad in ((300.0, 100.0, 17), (0.0, 100.0, 3), (300.0, -1.0, 3), (float("nan"), 100.0, 3)):
+            with pytest.raises(eng.CtdError):
+                srv.set_thermostat(rid, *bad)
+        with pytest.raises(eng.CtdError):
+            srv.set_thermostat(rid, 300.0, 100.0, 2, xi=[0.0, float("inf")], vxi=[0.0, 0.0])
+        with pytest.raises(eng.CtdError):
+            srv.thermostat(rid)             # no thermostat
+        one = srv.submit(sy.species[:1], sy.masses[:1], sy.positions[:1], v[:1], sy.cell, 2, skin=1.0)
+        with pytest.raises(eng.CtdError):
+            srv.set_thermostat(one, 300.0, 100.0, 3)   # a single atom has no thermal degrees of freedom
+        srv.set_thermostat(rid, 300.0, 100.0, 3)
+        srv.set_thermostat(rid, 300.0, 100.0, 0)       # back to NVE while queued
+        with pytest.raises(eng.CtdError):
+            srv.thermostat(rid)
