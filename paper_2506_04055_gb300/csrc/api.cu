@@ -19,8 +19,8 @@
 using namespace ctd;
 
 namespace ctd {
+
 // The library always carries the tensor-core kernels (sm_103a), so the BF16 path is available.
-// The tensor-core path is compiled in only when its kernels exist in this build.
 bool bf16_available() { return true; }
 
 // Host float -> bf16, round to nearest even (NaN kept quiet).
