@@ -291,3 +291,60 @@ def unpack_params(values: np.ndarray, F: int, K: int, T: int, S: int) -> dict:
         out[name] = values[off:off + n].reshape(shape)
         off += n
     return out
+
+
+# ---- parameters of the strictly local edge model ---------------------------------------------
+LOCAL_MAGIC = b"CTDLOCAL"
+
+
+def local_param_shapes(F: int, K: int, L: int, S: int, C: int):
+    """(name, shape) of every parameter of the strictly local edge model in blob order: the
+    two-body MLP A0 [K+2S][F] and c0, the initial-feature map P0 [F][2C]; per layer l the
+    environment weights Q_l [F][2C], the latent update M_l [F+2C][F] and m_l, and for l < L the
+    channel mixings Gs_l, Gv_l [2C][C]; the readout R1 [F][F/2], d1, R2 [F/2], d2."""
+    shapes = [("A0", (K + 2 * S, F)), ("c0", (F,)), ("P0", (F, 2 * C))]
+    for layer in range(1, L + 1):
+        shapes += [(f"Q{layer}", (F, 2 * C)), (f"M{layer}", (F + 2 * C, F)), (f"m{layer}", (F,))]
+        if layer < L:
+            shapes += [(f"Gs{layer}", (2 * C, C)), (f"Gv{layer}", (2 * C, C))]
+    Fh = F // 2
+    return shapes + [("R1", (F, Fh)), ("d1", (Fh,)), ("R2", (Fh,)), ("d2", (1,))]
+
+
+def local_xavier_params(F: int, K: int, L: int, S: int, C: int, seed: int = 0, bias_scale: float = 0.0):
+    """Flat float64 parameters of the local model: matrices Xavier-uniform, R2 with fan_out 1,
+    biases zero or U(-bias_scale, bias_scale)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for name, shape in local_param_shapes(F, K, L, S, C):
+        if name == "R2":
+            bound = math.sqrt(6.0 / (shape[0] + 1))
+            out.append(rng.uniform(-bound, bound, size=shape).ravel())
+        elif len(shape) == 2:
+            bound = math.sqrt(6.0 / (shape[0] + shape[1]))
+            out.append(rng.uniform(-bound, bound, size=shape).ravel())
+        elif bias_scale > 0:
+            out.append(rng.uniform(-bias_scale, bias_scale, size=shape).ravel())
+        else:
+            out.append(np.zeros(shape).ravel())
+    return np.concatenate(out).astype(np.float64)
+
+
+def local_params_blob(F: int, K: int = 20, L: int = 2, S: int = 2, C: int = 16, rc: float = 5.0,
+                      e_scale: float = 1.0, seed: int = 0, bias_scale: float = 0.0,
+                      values: np.ndarray | None = None) -> bytes:
+    """Serialised local-model parameters: 64-byte header followed by float64 values.
+
+    header: magic[8]="CTDLOCAL", int32 version, F, K, L, S, C,
+            float64 rc, 0.0 (unused), e_scale, int64 n_values   (little endian)
+    """
+    if values is None:
+        values = local_xavier_params(F, K, L, S, C, seed, bias_scale)
+    values = np.ascontiguousarray(values, np.float64)
+    expect = sum(int(np.prod(s)) for _, s in local_param_shapes(F, K, L, S, C))
+    if values.size != expect:
+        raise ValueError(f"expected {expect} values, got {values.size}")
+    head = LOCAL_MAGIC + struct.pack("<iiiiii", PARAM_VERSION, F, K, L, S, C)
+    head += struct.pack("<dddq", rc, 0.0, e_scale, values.size)
+    assert len(head) == PARAM_HEADER_BYTES
+    return head + values.tobytes()
