@@ -57,13 +57,26 @@ extern "C" {
 #define CTD_REBUILD 4          /* rebuild the neighbour list even if the skin still holds     */
 #define CTD_DEVICE_PTRS 8      /* I/O pointers are device pointers on the context's stream    */
 
+/* ---- model families ------------------------------------------------------------------------ */
+#define CTD_FAMILY_PAINN 0  /* semi-local message passing (PaiNN form; Methods, "Chosen
+                               Architectures"): T layers reach T cutoffs                        */
+#define CTD_FAMILY_LOCAL 1  /* strictly local equivariant edge model (Allegro form, rotation
+                               orders <= 1): messages only between edges leaving the same atom,
+                               so an atom's energy depends on its own cutoff sphere alone        */
+
 /* Model description.  F: feature width (even, multiple of 32, <= 256); K: radial basis size
  * (<= 32); T: interaction layers (<= 8); n_species: embedding rows; rc: cutoff (A);
- * precision: CTD_PREC_*.  Must equal the header of the parameter blob. */
+ * precision: CTD_PREC_*.  Must equal the header of the parameter blob.
+ * family: CTD_FAMILY_*.  For CTD_FAMILY_LOCAL: F = latent width (multiple of 8, 8..256),
+ * channels = equivariant channels C (multiple of 4, 4..64), T = layers (1..8), precision
+ * CTD_PREC_FP32; ctd_load_params then takes the "CTDLOCAL" blob.  channels is ignored for
+ * CTD_FAMILY_PAINN (zero-initialise both fields for the PaiNN form). */
 typedef struct {
   int32_t F, K, T, n_species;
   double rc;
   int32_t precision;
+  int32_t family;
+  int32_t channels;
 } ctd_model_desc;
 
 /* Per-call statistics (the library "returns statistics of the computation"). */
@@ -93,6 +106,16 @@ int ctd_create(ctd_ctx **out, const ctd_model_desc *desc, size_t hbm_budget_byte
  * float64 weights in this order (matrices [out][in]): emb[S][F]; per layer W1[F][F] b1[F]
  * W2[3F][F] b2[3F] Wf[3F][K] bf[3F] U[F][F] V[F][F] A1[F][2F] c1[F] A2[3F][F] c2[3F];
  * R1[F/2][F] d1[F/2] R2[F/2] d2[1].  The caller keeps the blob. */
+/* CTD_FAMILY_LOCAL: magic "CTDLOCAL", int32 version=1, F, K, T (= layers L), S, C; float64
+ * rc, unused, e_scale; int64 n_values; then the float64 weights, matrices [in][out]:
+ * A0[K+2S][F] c0[F] P0[F][2C]; per layer l = 1..L: Q[F][2C] M[F+2C][F] m[F], and for l < L
+ * Gs[2C][C] Gv[2C][C]; R1[F][F/2] d1[F/2] R2[F/2] d2[1].  The model, per directed edge
+ * e = (i -> j) with r_e = x_j - x_i (+ image), d = |r_e|, u = r_e / d, cosine cutoff f_c and
+ * the Gaussian basis b_k of the PaiNN form: x = silu([b f_c | onehot(Z_i) | onehot(Z_j)] A0 + c0);
+ * s = (x P0)[0:C], v = (x P0)[C:2C] u; per layer: om = x Q, atom sums over i's edges
+ * Gs_i = sum f_c om[0:C], Gv_i = sum f_c om[C:2C] u; ts = [s Gs_i | v . Gv_i],
+ * tv = [s Gv_i | v Gs_i]; x = silu([x | ts] M + m); (l < L) s = ts Gs, v = tv Gv; energy
+ * E_i = e_scale sum_{e from i} f_c (silu(x R1 + d1) . R2 + d2). */
 int ctd_load_params(ctd_ctx *ctx, const void *blob, size_t nbytes);
 
 /* Build the Verlet neighbour list of n atoms: every (i, j, n) with

@@ -13,8 +13,11 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (CTD_DEVICE_PTRS, CTD_NEED_FORCES, CTD_NEED_VIRIAL, CTD_PREC_BF16,  # noqa: F401
-                   CTD_PREC_FP32, CTD_REBUILD, CtdError, ctd_model_desc, ctd_stats)
+from ._lib import (CTD_DEVICE_PTRS, CTD_FAMILY_LOCAL, CTD_FAMILY_PAINN, CTD_NEED_FORCES,  # noqa: F401
+                   CTD_NEED_VIRIAL, CTD_PREC_BF16, CTD_PREC_FP32, CTD_REBUILD, CtdError, ctd_model_desc,
+                   ctd_stats)
+
+_FAMILIES = {"painn": CTD_FAMILY_PAINN, "local": CTD_FAMILY_LOCAL}
 
 __all__ = ["Potential", "Server", "Domains", "PaiNNEnergy", "CtdError", "build", "load"]
 
@@ -98,14 +101,16 @@ class Potential:
 
     precision: "fp32" (all products in FP32) or "bf16" (tensor-core MLPs, FP32 accumulation).
     params: the blob of ``synthetic.params_blob`` (64-byte header + float64 weights).
+    family: "painn" (message passing, T layers) or "local" (strictly local equivariant edge
+    model, T layers, ``channels`` equivariant channels, FP32; blob of ``synthetic.local_params_blob``).
     stream: a CUDA stream handle (int) or None for a stream owned by the context.
     """
 
     def __init__(self, F: int, K: int = 20, T: int = 3, n_species: int = 2, rc: float = 5.0,
                  precision: str = "fp32", params: bytes | None = None, hbm_budget_bytes: int = 0,
-                 stream: int | None = None):
+                 stream: int | None = None, family: str = "painn", channels: int = 0):
         prec = {"fp32": CTD_PREC_FP32, "bf16": CTD_PREC_BF16}[precision]
-        self.desc = ctd_model_desc(F, K, T, n_species, rc, prec)
+        self.desc = ctd_model_desc(F, K, T, n_species, rc, prec, _FAMILIES[family], channels)
         self.F, self.K, self.T, self.S, self.rc, self.precision = F, K, T, n_species, rc, precision
         self.ctx = _lib.ctd_create(self.desc, hbm_budget_bytes, stream)
         if params is not None:
@@ -224,9 +229,9 @@ class Server:
 
     def __init__(self, F: int, params: bytes, K: int = 20, T: int = 3, n_species: int = 2, rc: float = 5.0,
                  precision: str = "fp32", hbm_budget_bytes: int = 0, max_replicas: int = 1024, dt: float = 1.0,
-                 stream: int | None = None):
+                 stream: int | None = None, family: str = "painn", channels: int = 0):
         prec = {"fp32": CTD_PREC_FP32, "bf16": CTD_PREC_BF16}[precision]
-        self.desc = ctd_model_desc(F, K, T, n_species, rc, prec)
+        self.desc = ctd_model_desc(F, K, T, n_species, rc, prec, _FAMILIES[family], channels)
         self.srv = _lib.ctd_serve_create(self.desc, params, hbm_budget_bytes, max_replicas, dt, stream)
         self._n = {}
         self._steps = {}
@@ -323,9 +328,9 @@ class Domains:
 
     def __init__(self, F: int, params: bytes, grid=(2, 2, 2), K: int = 20, T: int = 3, n_species: int = 2,
                  rc: float = 5.0, precision: str = "fp32", hop_prune: bool = True, skin: float = 1.0,
-                 hbm_budget_bytes: int = 0, stream: int | None = None):
+                 hbm_budget_bytes: int = 0, stream: int | None = None, family: str = "painn", channels: int = 0):
         prec = {"fp32": CTD_PREC_FP32, "bf16": CTD_PREC_BF16}[precision]
-        self.desc = ctd_model_desc(F, K, T, n_species, rc, prec)
+        self.desc = ctd_model_desc(F, K, T, n_species, rc, prec, _FAMILIES[family], channels)
         self.grid = tuple(int(g) for g in grid)
         self.dom = _lib.ctd_domains_create(self.desc, params, self.grid, hop_prune, skin, hbm_budget_bytes, stream)
         self.ctx = _lib.ctd_domains_context(self.dom)

@@ -24,6 +24,8 @@ CTD_ERR_NONFINITE = -7
 CTD_ERR_STATE = -8
 CTD_PREC_FP32 = 0
 CTD_PREC_BF16 = 1
+CTD_FAMILY_PAINN = 0
+CTD_FAMILY_LOCAL = 1
 CTD_NEED_FORCES = 1
 CTD_NEED_VIRIAL = 2
 CTD_REBUILD = 4
@@ -58,7 +60,8 @@ STAGES = ["build", "prune", "node", "edge_fwd", "edge_bwd", "forces", "md", "oth
 
 class ctd_model_desc(ctypes.Structure):
     _fields_ = [("F", ctypes.c_int32), ("K", ctypes.c_int32), ("T", ctypes.c_int32),
-                ("n_species", ctypes.c_int32), ("rc", ctypes.c_double), ("precision", ctypes.c_int32)]
+                ("n_species", ctypes.c_int32), ("rc", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("family", ctypes.c_int32), ("channels", ctypes.c_int32)]
 
 
 class ctd_stats(ctypes.Structure):

@@ -264,6 +264,12 @@ int prune(ctd_ctx* c, double* maxdisp_out) {
 // BF16 operand copies), as evaluate() allocates them.
 size_t model_bytes_per_atom(const ctd_ctx* c) {
   const int F = c->desc.F, T = c->desc.T;
+  if (c->local()) {   // per-edge arrays at 64 active edges per atom (water and fcc at rc = 5 A: ~50)
+    LocalW w = c->lw;
+    w.F = F; w.L = T; w.C = c->desc.channels; w.S = c->desc.n_species;
+    w.KA = (c->desc.K + 2 * w.S + 3) / 4 * 4;
+    return sizeof(float) * (size_t)local_buffer_floats(w, 1, 64);
+  }
   const bool g4 = model_uses_g4(c->mw, c->desc.precision);
   size_t bytes = 0;
   for (int b = 0; b < model_buffer_count(); ++b) bytes += sizeof(float) * (size_t)model_buffer_floats_per_atom(b, F, T, g4);
@@ -275,7 +281,43 @@ size_t model_bytes_per_atom(const ctd_ctx* c) {
 
 // Model evaluation on the current active list; forces (sorted, FP32) in c->force_s,
 // energy in c->out_e[0], virial in c->out_w[0..8], per-atom energies (sorted) in c->eatom.
+// The strictly local model: edge arrays sized by this step's active edge count.
+int evaluate_local(ctd_ctx* c, bool need_grad) {
+  cudaStream_t st = c->st;
+  const int64_t n = c->n, n1 = n > 0 ? n : 1, e1 = c->n_verlet > 0 ? c->n_verlet : 1;
+  int32_t act = 0;
+  if (n > 0) {
+    CUDA_OK(c, cudaMemcpyAsync(&act, P<int32_t>(c->arow) + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_OK(c, cudaStreamSynchronize(st));
+  }
+  const int64_t E = act;
+  ENSURE(c, c->lbuf, sizeof(float) * (size_t)local_buffer_floats(c->lw, n1, E > 0 ? E : 1));
+  ENSURE(c, c->hedge, sizeof(float4) * e1);
+  ENSURE(c, c->force_s, sizeof(float) * 3 * n1);
+  ENSURE(c, c->eatom, sizeof(float) * n1);
+  ENSURE(c, c->epart, sizeof(double) * kPartials);
+  ENSURE(c, c->vpart, sizeof(double) * 9 * kPartials);
+  ENSURE(c, c->out_e, sizeof(double) * 4);
+  ENSURE(c, c->out_w, sizeof(double) * 9);
+  const float* ew = c->use_ew ? P<float>(c->ew) : nullptr;
+  c->last_stored = false;
+  local_forward_backward(st, c->lw, n, E, P<int32_t>(c->z_s), P<int32_t>(c->arow), P<int32_t>(c->acol),
+                         P<float4>(c->ar), P<float>(c->lbuf), need_grad, ew, P<double>(c->epart), kPartials,
+                         P<float>(c->eatom), P<float4>(c->hedge));
+  StageGuard sg(STG_FORCES);
+  if (need_grad) {
+    if (E == 0) CUDA_OK(c, cudaMemsetAsync(c->hedge.p, 0, sizeof(float4), st));
+    launch_forces(st, n, P<int32_t>(c->arow), P<float4>(c->ar), P<int32_t>(c->arev), P<float4>(c->hedge),
+                  P<float>(c->force_s), P<double>(c->vpart), kPartials, P<int>(c->status));
+  }
+  launch_sum_partials(st, kPartials, 1, P<double>(c->epart), P<double>(c->out_e), 1.0);
+  if (need_grad) launch_sum_partials(st, kPartials, 9, P<double>(c->vpart), P<double>(c->out_w), 1.0);
+  CUDA_OK(c, cudaGetLastError());
+  return CTD_OK;
+}
+
 int evaluate(ctd_ctx* c, bool need_grad) {
+  if (c->local()) return evaluate_local(c, need_grad);
   cudaStream_t st = c->st;
   const int64_t n = c->n, n1 = n > 0 ? n : 1, e1 = c->n_verlet > 0 ? c->n_verlet : 1;
   const int F = c->desc.F, T = c->desc.T;
@@ -373,9 +415,91 @@ int prepare_step(ctd_ctx* c, int64_t n, const double H[9], bool force_rebuild, i
   return CTD_OK;
 }
 
+// Parameters of the strictly local edge model ("CTDLOCAL" blob, matrices [in][out]).
+int load_local_params(ctd_ctx* c, const char* b, size_t nbytes) {
+  if (memcmp(b, "CTDLOCAL", 8) != 0) return fail(c, CTD_ERR_INVALID_ARG, "bad parameter blob magic");
+  int32_t hdr[6];
+  memcpy(hdr, b + 8, sizeof(hdr));
+  double rc, unused, esc;
+  int64_t nval;
+  memcpy(&rc, b + 32, 8);
+  memcpy(&unused, b + 40, 8);
+  memcpy(&esc, b + 48, 8);
+  memcpy(&nval, b + 56, 8);
+  const int F = hdr[1], K = hdr[2], L = hdr[3], S = hdr[4], C = hdr[5];
+  const ctd_model_desc& d = c->desc;
+  if (hdr[0] != 1 || F != d.F || K != d.K || L != d.T || S != d.n_species || C != d.channels || rc != d.rc)
+    return fail(c, CTD_ERR_INVALID_ARG, "parameter blob header does not match the model description");
+  const int C2 = 2 * C, FX = F + C2, Fh = F / 2, KA0 = K + 2 * S, KA = (KA0 + 3) / 4 * 4;
+  int64_t expect = (int64_t)KA0 * F + F + (int64_t)F * C2 + (int64_t)F * Fh + Fh + Fh + 1;
+  for (int l = 1; l <= L; ++l) expect += (int64_t)F * C2 + (int64_t)FX * F + F + (l < L ? 2 * C2 * C : 0);
+  if (nval != expect || nbytes < 64 + (size_t)nval * 8)
+    return fail(c, CTD_ERR_INVALID_ARG, "parameter blob has the wrong number of values");
+  std::vector<double> v((size_t)nval);
+  memcpy(v.data(), b + 64, (size_t)nval * 8);
+  for (double x : v)
+    if (!std::isfinite(x)) return fail(c, CTD_ERR_INVALID_ARG, "non-finite parameter");
+  std::vector<float> h;
+  auto alloc = [&](size_t cnt) {
+    size_t off = (h.size() + 7) / 8 * 8;   // 32-byte aligned arrays (GEMM operands are read as float4)
+    h.resize(off + cnt, 0.0f);
+    return off;
+  };
+  const double* p = v.data();
+  // a [rows][cols] matrix, stored as is (padded to prow rows) and transposed ([cols][prow])
+  auto mat = [&](int rows, int cols, int prow, size_t* t_off) {
+    const double* src = p;
+    p += (size_t)rows * cols;
+    size_t off = alloc((size_t)prow * cols);
+    for (int r = 0; r < rows; ++r)
+      for (int k = 0; k < cols; ++k) h[off + (size_t)r * cols + k] = (float)src[(size_t)r * cols + k];
+    if (t_off) {
+      *t_off = alloc((size_t)cols * prow);
+      for (int r = 0; r < rows; ++r)
+        for (int k = 0; k < cols; ++k) h[*t_off + (size_t)k * prow + r] = (float)src[(size_t)r * cols + k];
+    }
+    return off;
+  };
+  auto vec = [&](int cnt) { return mat(1, cnt, 1, nullptr); };
+  size_t oA0t, oP0t, oR1t;
+  const size_t oA0 = mat(KA0, F, KA, &oA0t), oc0 = vec(F), oP0 = mat(F, C2, F, &oP0t);
+  struct LOff { size_t Q, Qt, M, Mt, m, Gs, Gst, Gv, Gvt; } lo[kMaxT] = {};
+  for (int l = 1; l <= L; ++l) {
+    LOff& o = lo[l - 1];
+    o.Q = mat(F, C2, F, &o.Qt);
+    o.M = mat(FX, F, FX, &o.Mt);
+    o.m = vec(F);
+    if (l < L) {
+      o.Gs = mat(C2, C, C2, &o.Gst);
+      o.Gv = mat(C2, C, C2, &o.Gvt);
+    }
+  }
+  const size_t oR1 = mat(F, Fh, F, &oR1t), od1 = vec(Fh), oR2 = vec(Fh), od2 = vec(1);
+  ENSURE(c, c->params, h.size() * sizeof(float));
+  CUDA_OK(c, cudaMemcpyAsync(c->params.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  const float* base = P<float>(c->params);
+  LocalW& w = c->lw;
+  w.F = F; w.K = K; w.KA = KA; w.L = L; w.S = S; w.C = C;
+  w.rc = (float)rc; w.e_scale = (float)esc;
+  w.A0 = base + oA0; w.A0t = base + oA0t; w.c0 = base + oc0; w.P0 = base + oP0; w.P0t = base + oP0t;
+  for (int l = 1; l <= L; ++l) {
+    const LOff& o = lo[l - 1];
+    LocalLayerW& q = w.Lw[l - 1];
+    q.Q = base + o.Q; q.Qt = base + o.Qt; q.M = base + o.M; q.Mt = base + o.Mt; q.m = base + o.m;
+    q.Gs = l < L ? base + o.Gs : nullptr; q.Gst = l < L ? base + o.Gst : nullptr;
+    q.Gv = l < L ? base + o.Gv : nullptr; q.Gvt = l < L ? base + o.Gvt : nullptr;
+  }
+  w.R1 = base + oR1; w.R1t = base + oR1t; w.d1 = base + od1; w.R2 = base + oR2; w.d2 = base + od2;
+  c->e_scale = esc;
+  c->have_params = true;
+  return CTD_OK;
+}
+
 int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
   if (!blob || nbytes < 64) return fail(c, CTD_ERR_INVALID_ARG, "parameter blob too short");
   const char* b = static_cast<const char*>(blob);
+  if (c->local()) return load_local_params(c, b, nbytes);
   if (memcmp(b, "CTDPAINN", 8) != 0) return fail(c, CTD_ERR_INVALID_ARG, "bad parameter blob magic");
   int32_t hdr[6];
   memcpy(hdr, b + 8, sizeof(hdr));
@@ -523,10 +647,19 @@ int ctd_create(ctd_ctx** out, const ctd_model_desc* desc, size_t hbm_budget_byte
   if (!out || !desc) return CTD_ERR_INVALID_ARG;
   *out = nullptr;
   const int F = desc->F;
-  if (!(F == 32 || F == 64 || F == 128 || F == 256) || desc->K < 2 || desc->K > kMaxKP || desc->T < 0 ||
-      desc->T > kMaxT || desc->n_species < 1 || !(desc->rc > 0.0) ||
-      (desc->precision != CTD_PREC_FP32 && desc->precision != CTD_PREC_BF16))
+  if (desc->family == CTD_FAMILY_LOCAL) {
+    // edge rows of width F, F/2, 2C, K + 2S (rounded up to 4) feed the SIMT GEMM
+    const int C = desc->channels;
+    if (F < 8 || F > 256 || F % 8 != 0 || C < 4 || C > 64 || C % 4 != 0 || desc->K < 2 || desc->K > kMaxKP ||
+        desc->T < 1 || desc->T > kMaxT || desc->n_species < 1 || desc->n_species > 64 || !(desc->rc > 0.0) ||
+        desc->precision != CTD_PREC_FP32)
+      return CTD_ERR_INVALID_ARG;
+  } else if (desc->family != CTD_FAMILY_PAINN ||
+             !(F == 32 || F == 64 || F == 128 || F == 256) || desc->K < 2 || desc->K > kMaxKP || desc->T < 0 ||
+             desc->T > kMaxT || desc->n_species < 1 || !(desc->rc > 0.0) ||
+             (desc->precision != CTD_PREC_FP32 && desc->precision != CTD_PREC_BF16)) {
     return CTD_ERR_INVALID_ARG;
+  }
   if (desc->precision == CTD_PREC_BF16 && (!bf16_available() || !(F == 64 || F == 128)))
     return CTD_ERR_INVALID_ARG;
   int dev_count = 0;

@@ -108,6 +108,35 @@ struct ModelW {
   int64_t edge_chunk_rows;         // bulk-gathered kernels: rows per chunk (0: one range per stream)
 };
 
+// Strictly local equivariant edge model (model_local.cu): FP32 weights on the device, matrices
+// [in][out] as the GEMMs' B operand and their transposes for the adjoint; A0 zero-padded to KA
+// rows (K + 2S rounded up to a multiple of 4).
+struct LocalLayerW {
+  const float *Q, *Qt, *M, *Mt, *m;      // [F][2C], [2C][F], [F+2C][F], [F][F+2C], [F]
+  const float *Gs, *Gst, *Gv, *Gvt;      // [2C][C], [C][2C] (layers l < L)
+};
+struct LocalW {
+  int F, K, KA, L, S, C;
+  float rc, e_scale;
+  const float *A0, *A0t, *c0, *P0, *P0t;  // [KA][F], [F][KA], [F], [F][2C], [2C][F]
+  LocalLayerW Lw[kMaxT];
+  const float *R1, *R1t, *d1, *R2, *d2;   // [F][F/2], [F/2][F], [F/2], [F/2], [1]
+};
+// Device floats the local model needs for n atoms and E active edges.
+int64_t local_buffer_floats(const LocalW& w, int64_t n, int64_t E);
+// Energy partials, per-atom energies, and (need_grad) hedge = -dE/dr_e per active edge.
+void local_forward_backward(cudaStream_t st, const LocalW& w, int64_t n, int64_t E, const int32_t* species_s,
+                            const int32_t* arow, const int32_t* acol, const float4* ar, float* buf,
+                            bool need_grad, const float* ew, double* energy_partials, int n_energy_partials,
+                            float* e_atom, float4* hedge);
+// Forces F_i = sum_{e in row i} (hedge[rev e] - hedge[e]) and virial partials sum_e r_e (x) hedge[e].
+void launch_forces(cudaStream_t st, int64_t n, const int32_t* arow, const float4* ar, const int32_t* arev,
+                   const float4* hedge, float* force, double* vpart, int n_vpart, int* status);
+// out = A B (+ epilogue) with the FP32 SIMT GEMM: epi 0 bias (may be null), 1 bias + silu into
+// out2, 2 out = A B + aux (aux and out must not overlap), 3 out = (A B) * silu'(aux).
+void gemm_f32(cudaStream_t st, int epi, int64_t M, int N, int K, const float* A, int lda, const float* B,
+              const float* bias, const float* aux, int ldaux, float* out, int ldo, float* out2, int ldo2);
+
 // ---------------------------------------------------------------- small device helpers
 __device__ __forceinline__ float silu_f(float x) { return x / (1.0f + __expf(-x)); }
 __device__ __forceinline__ float dsilu_f(float x) {

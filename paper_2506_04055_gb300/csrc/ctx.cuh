@@ -39,6 +39,10 @@ struct ctd_ctx {
   double eps = 1e-8, e_scale = 1.0;
   DBuf params, params_bf;
   ModelW mw{};
+  // strictly local edge model (desc.family == CTD_FAMILY_LOCAL): weights and edge buffers
+  ctd::LocalW lw{};
+  DBuf lbuf;
+  bool local() const { return desc.family == CTD_FAMILY_LOCAL; }
 
   // neighbour state
   bool have_list = false;
@@ -78,7 +82,7 @@ struct ctd_ctx {
                     &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev, &aend,
                     &hedge, &force_s, &eatom, &epart, &vpart, &kpart, &scan_tmp, &out_e, &out_f, &out_w,
                     &out_eatom, &wstore, &ew, &near, &md_v, &md_m, &md_x_user, &md_v_user, &md_ep, &md_ek, &md_tmp,
-                    &nhc_state, &nhc_ke, &md_eth};
+                    &nhc_state, &nhc_ke, &md_eth, &lbuf};
     for (DBuf* b : list) all.push_back(b);
   }
 };

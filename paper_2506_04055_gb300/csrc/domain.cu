@@ -729,6 +729,7 @@ int ctd_domains_create(ctd_domains** out, const ctd_model_desc* desc, const void
   for (int a = 0; a < 3; ++a)
     if (grid[a] < 1 || grid[a] > 64) return CTD_ERR_INVALID_ARG;
   if ((int64_t)grid[0] * grid[1] * grid[2] > 4096) return CTD_ERR_INVALID_ARG;
+  if (desc->family != CTD_FAMILY_PAINN) return CTD_ERR_INVALID_ARG;   // the decomposition serves the message-passing form
   ctd_ctx* c = nullptr;
   int r = ctd_create(&c, desc, hbm_budget_bytes, cuda_stream);
   if (r) return r;

@@ -151,6 +151,16 @@ static void gemm(cudaStream_t st, int64_t M, int N, int K, const float* A, int l
   { LaunchScope ls_(st); k_gemm<EPI><<<(unsigned)blocks, 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); }
 }
 
+void gemm_f32(cudaStream_t st, int epi, int64_t M, int N, int K, const float* A, int lda, const float* B,
+              const float* bias, const float* aux, int ldaux, float* out, int ldo, float* out2, int ldo2) {
+  switch (epi) {
+    case EPI_BIAS: gemm<EPI_BIAS>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
+    case EPI_BIAS_SILU: gemm<EPI_BIAS_SILU>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
+    case EPI_ADD: gemm<EPI_ADD>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
+    default: gemm<EPI_DSILU>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
+  }
+}
+
 // ================================================================================ node kernels
 __global__ void k_embed(int64_t n, int F, const int32_t* __restrict__ Z, const float* __restrict__ emb,
                         float* __restrict__ S, float* __restrict__ V, __nv_bfloat16* __restrict__ Sb) {
@@ -943,6 +953,12 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
   { LaunchScope ls_(st); k_forces<<<n_virial_partials, kThreads, 0, st>>>(n, arow, ar, arev, hedge, force_s, virial_partials, status); }
 }
 
+
+void launch_forces(cudaStream_t st, int64_t n, const int32_t* arow, const float4* ar, const int32_t* arev,
+                   const float4* hedge, float* force, double* vpart, int n_vpart, int* status) {
+  LaunchScope ls_(st);
+  k_forces<<<n_vpart, kThreads, 0, st>>>(n, arow, ar, arev, hedge, force, vpart, status);
+}
 
 // ================================================================================ BF16 driver
 // Same layer as above; every node MLP contraction runs on tcgen05 with BF16 operands and FP32
