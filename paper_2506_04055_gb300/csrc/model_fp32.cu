@@ -29,25 +29,30 @@
 namespace ctd {
 
 // ================================================================================ SIMT GEMM
-// out[m][n] = sum_k A[m][k] B[k][n], A [M][K] (lda), B [K][N] row-major; 64x128 tile,
-// 256 threads, each 8 rows x 4 columns, K staged 32 at a time (A transposed in smem).
+// out[m][n] = sum_k A[m][k] B[k][n], A [M][K] (lda), B [K][N] row-major; BM x BN tile
+// (64 x 128, or 128 x 64 / 256 x 32 for narrow outputs), 256 threads, each 8 rows x 4 columns,
+// K staged 32 at a time (A transposed in smem).  Every output is the same fmaf chain over k in
+// increasing order whatever the tile, so the tile shapes give bit-identical results.
 enum Epi { EPI_BIAS = 0, EPI_BIAS_SILU = 1, EPI_ADD = 2, EPI_DSILU = 3 };
 constexpr int GBM = 64, GBN = 128, GBK = 32;
 
-template <int EPI>
+template <int EPI, int BN = GBN>
 __global__ __launch_bounds__(256) void k_gemm(int64_t M, int N, int K, const float* __restrict__ A, int lda,
                                               const float* __restrict__ B, const float* __restrict__ bias,
                                               const float* aux, int ldaux, float* out, int ldo,
                                               float* __restrict__ out2, int ldo2) {
-  __shared__ __align__(16) float AsT[GBK][GBM + 4];
-  __shared__ __align__(16) float Bs[GBK][GBN];
-  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
+  constexpr int TX = BN / 4;          // column groups of 4
+  constexpr int BM = 8 * (256 / TX);  // row groups of 8
+  static_assert(BN == 32 || BN == 64 || BN == 128, "tile width");
+  __shared__ __align__(16) float AsT[GBK][BM + 4];
+  __shared__ __align__(16) float Bs[GBK][BN];
+  const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX;
   // 1-D grid, column tile fastest: consecutive blocks share their A rows (L2 reuse), and the row
   // tile count is not limited to the 65,535 of a grid's y dimension (M = 3n rows exceed it
   // beyond 1.4M atoms)
-  const int ncol = (N + GBN - 1) / GBN;
-  const int64_t m0 = (int64_t)(blockIdx.x / ncol) * GBM;
-  const int n0 = (int)(blockIdx.x % ncol) * GBN;
+  const int ncol = (N + BN - 1) / BN;
+  const int64_t m0 = (int64_t)(blockIdx.x / ncol) * BM;
+  const int n0 = (int)(blockIdx.x % ncol) * BN;
   float acc[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -55,9 +60,9 @@ __global__ __launch_bounds__(256) void k_gemm(int64_t M, int N, int K, const flo
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
 
   for (int k0 = 0; k0 < K; k0 += GBK) {
-    // A tile: 64 rows x 32 k, two float4 per thread, stored transposed
+    // A tile: BM rows x 32 k, BM/32 float4 per thread, stored transposed
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < BM / 32; ++q) {
       int idx = tid + q * 256;
       int r = idx >> 3, c4 = (idx & 7) * 4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -67,11 +72,11 @@ __global__ __launch_bounds__(256) void k_gemm(int64_t M, int N, int K, const flo
       AsT[c4 + 2][r] = v.z;
       AsT[c4 + 3][r] = v.w;
     }
-    // B tile: 32 k x 128 n, four float4 per thread
+    // B tile: 32 k x BN n, BN/32 float4 per thread
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < BN / 32; ++q) {
       int idx = tid + q * 256;
-      int r = idx >> 5, c4 = (idx & 31) * 4;
+      int r = idx / TX, c4 = (idx % TX) * 4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (k0 + r < K && n0 + c4 < N) v = *reinterpret_cast<const float4*>(&B[(int64_t)(k0 + r) * N + n0 + c4]);
       *reinterpret_cast<float4*>(&Bs[r][c4]) = v;
@@ -135,30 +140,39 @@ __global__ void k_gemm_small(int64_t M, int N, int K, const float* __restrict__ 
   if (EPI == EPI_BIAS_SILU) out2[m * ldo2 + n] = silu_f(x);
 }
 
-template <int EPI>
+template <int EPI, int BN = GBN>
 static void gemm(cudaStream_t st, int64_t M, int N, int K, const float* A, int lda, const float* B,
                  const float* bias, const float* aux, int ldaux, float* out, int ldo, float* out2 = nullptr,
                  int ldo2 = 0) {
   if (M == 0) return;
-  const int64_t tiles = (int64_t)((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
+  constexpr int BM = 8 * (256 / (BN / 4));
+  const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
   if (tiles < 152) {
     LaunchScope ls_(st);
     k_gemm_small<EPI><<<(unsigned)((M * N + 255) / 256), 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out,
                                                                      ldo, out2, ldo2);
     return;
   }
-  const int64_t blocks = (int64_t)((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
-  { LaunchScope ls_(st); k_gemm<EPI><<<(unsigned)blocks, 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); }
+  { LaunchScope ls_(st); k_gemm<EPI, BN><<<(unsigned)tiles, 256, 0, st>>>(M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); }
 }
 
+// The tile width follows N (32, 64 or 128 columns), so narrow outputs do not compute idle
+// columns; the results are those of the 128-column tile, bit for bit.
+template <int BN>
+static void gemm_epi(cudaStream_t st, int epi, int64_t M, int N, int K, const float* A, int lda, const float* B,
+                     const float* bias, const float* aux, int ldaux, float* out, int ldo, float* out2, int ldo2) {
+  switch (epi) {
+    case EPI_BIAS: gemm<EPI_BIAS, BN>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
+    case EPI_BIAS_SILU: gemm<EPI_BIAS_SILU, BN>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
+    case EPI_ADD: gemm<EPI_ADD, BN>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
+    default: gemm<EPI_DSILU, BN>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
+  }
+}
 void gemm_f32(cudaStream_t st, int epi, int64_t M, int N, int K, const float* A, int lda, const float* B,
               const float* bias, const float* aux, int ldaux, float* out, int ldo, float* out2, int ldo2) {
-  switch (epi) {
-    case EPI_BIAS: gemm<EPI_BIAS>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
-    case EPI_BIAS_SILU: gemm<EPI_BIAS_SILU>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
-    case EPI_ADD: gemm<EPI_ADD>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
-    default: gemm<EPI_DSILU>(st, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2); break;
-  }
+  if (N <= 32) gemm_epi<32>(st, epi, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2);
+  else if (N <= 64) gemm_epi<64>(st, epi, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2);
+  else gemm_epi<128>(st, epi, M, N, K, A, lda, B, bias, aux, ldaux, out, ldo, out2, ldo2);
 }
 
 // ================================================================================ node kernels
