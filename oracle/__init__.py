@@ -14,6 +14,9 @@ What pins each function (tests/test_oracle_*.py):
   * nve                       -- pinned (time reversibility, dt^2 energy-error scaling)
   * nvt                       -- pinned (NVE limit, conserved extended energy and its dt^2
                                  scaling, time reversibility, mean temperature of free particles)
+  * local.local_model         -- the strictly local edge model in PyTorch CPU float64 (module
+                                 local.py); pinned (scalar dimer and trimer evaluations, finite
+                                 differences, invariances, strict locality, cutoff continuity)
 """
 from __future__ import annotations
 
