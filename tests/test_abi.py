@@ -78,3 +78,36 @@ def test_param_blob_layout():
     bound = np.sqrt(6.0 / (F + F))
     assert np.abs(P["W1_0"]).max() <= bound and np.abs(P["W1_0"]).max() > 0.9 * bound
     assert np.all(P["b1_0"] == 0)
+
+
+def test_struct_layouts_match_the_header():
+    """ctypes mirrors of ctd_model_desc, ctd_stats and ctd_domain_info have the C compiler's sizes and offsets
+    (a program built from include/painn.h with gcc prints them)."""
+    import ctypes
+
+    from paper_2506_04055_gb300 import _lib
+    out_dir = os.path.join(ROOT, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, "layout.c")
+    exe = os.path.join(out_dir, "layout")
+    fields = {"ctd_model_desc": [f for f, _ in _lib.ctd_model_desc._fields_],
+              "ctd_stats": [f for f, _ in _lib.ctd_stats._fields_],
+              "ctd_domain_info": [f for f, _ in _lib.ctd_domain_info._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "painn.h"', "int main(void) {"]
+    for st, names in fields.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in names:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+    got = {}
+    for line in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.splitlines():
+        st, key, val = line.split()
+        got[(st, key)] = int(val)
+    for st in fields:
+        cls = getattr(_lib, st)
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
