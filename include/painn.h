@@ -306,7 +306,9 @@ void ctd_serve_destroy(ctd_server *s);
  * before the model, copy forces after it) as kernels.  ctd_domains_info reports the work the
  * copies add.  desc / params / nbytes / hbm_budget_bytes / cuda_stream: as ctd_create and
  * ctd_load_params.  grid[a] in 1..64 with at most 4096 domains; skin >= 0 (A).  Options
- * (ctd_set_option) and profiling go through the context ctd_domains_context returns. */
+ * (ctd_set_option) and profiling go through the context ctd_domains_context returns.  T is the
+ * model's reach in hops: desc->T for CTD_FAMILY_PAINN, 1 for CTD_FAMILY_LOCAL (strictly local:
+ * R_comm = rc + skin and copies one hop deep, whatever the layer count). */
 typedef struct ctd_domains ctd_domains;
 typedef struct {
   int64_t n_owned;         /* atoms the domain owns                                           */

@@ -454,6 +454,10 @@ int layout_batch(ctd_domains* D, const std::vector<int64_t>& counts) {
   return CTD_OK;
 }
 
+// Hops of the model's receptive field: T layers of message passing reach T cutoffs; the strictly
+// local family reaches one, whatever its layer count.
+static int receptive_hops(const ctd_ctx* c) { return c->local() ? 1 : c->desc.T; }
+
 // Build every domain on the candidates (src, shift, own) laid out domain-major per layout_batch,
 // with hop levels; keep (optional, candidate order) receives level <= T.
 int build_all(ctd_domains* D, const int32_t* src, const double* shift, const uint8_t* own, int32_t* keep) {
@@ -466,11 +470,11 @@ int build_all(ctd_domains* D, const int32_t* src, const double* shift, const uin
   for (Dom& M : D->doms) {
     int r = build_domain(D, M, P<double>(D->xc) + 3 * M.atom_off, src, shift, own);
     if (r) return r;
-    hop_levels(D, M, c->desc.T);
+    hop_levels(D, M, receptive_hops(c));
     if (keep && M.n > 0) {   // the domain's sort permutation is still in b_perm here
       LaunchScope ls_(st);
       k_hop_keep<<<dblk(M.n), kThreads, 0, st>>>(M.n, P<int32_t>(D->b_perm), P<int32_t>(D->lev) + M.atom_off,
-                                                 c->desc.T, keep + M.atom_off);
+                                                 receptive_hops(c), keep + M.atom_off);
     }
   }
   return CTD_OK;
@@ -554,7 +558,7 @@ int decompose(ctd_domains* D) {
   StageGuard sg(STG_BUILD);
   D->decomposed = false;   // until every buffer below is consistent again
   const int64_t N = D->N, N1 = N > 0 ? N : 1;
-  const int nd = D->nd, T = c->desc.T;
+  const int nd = D->nd, T = receptive_hops(c);
   const double rcomm = T * c->desc.rc + D->skin;
   const double R = c->desc.rc + D->skin;
   CellGeom g{};
@@ -729,7 +733,6 @@ int ctd_domains_create(ctd_domains** out, const ctd_model_desc* desc, const void
   for (int a = 0; a < 3; ++a)
     if (grid[a] < 1 || grid[a] > 64) return CTD_ERR_INVALID_ARG;
   if ((int64_t)grid[0] * grid[1] * grid[2] > 4096) return CTD_ERR_INVALID_ARG;
-  if (desc->family != CTD_FAMILY_PAINN) return CTD_ERR_INVALID_ARG;   // the decomposition serves the message-passing form
   ctd_ctx* c = nullptr;
   int r = ctd_create(&c, desc, hbm_budget_bytes, cuda_stream);
   if (r) return r;

@@ -5,7 +5,8 @@ passes messages only between edges leaving the same atom.  Parity with oracle/lo
 FP32 tolerances (force RMSE 1e-5 relative, |dE|/N 1e-6 of the per-atom energy scale) on water,
 a crystal and a triclinic four-species mixture; per-atom energies; strict locality holds bit
 for bit; the resident MD loop follows the oracle's velocity-Verlet trajectory; served replicas
-are bit-identical alone and mixed; degenerate systems and invalid descriptions."""
+are bit-identical alone and mixed; the spatial decomposition with one-hop copies; degenerate
+systems and invalid descriptions."""
 import numpy as np
 import pytest
 
@@ -170,5 +171,23 @@ def test_invalid_descriptions_rejected():
     _, blob32 = _model(32, 2, 2, 4, seed=9)
     with pytest.raises(eng.CtdError):
         eng.Potential(32, K=K, T=2, n_species=2, params=blob32)
-    with pytest.raises(eng.CtdError):
-        eng.Domains(16, blob, grid=(2, 1, 1), K=K, T=2, n_species=2, family="local", channels=4)
+
+
+@pytest.mark.parametrize("grid", [(2, 1, 1), (2, 2, 1)])
+def test_spatial_decomposition_one_hop(loc, orc, grid):
+    """The decomposition of a strictly local model: copies within rc + skin of each domain (one
+    hop, whatever the layer count), owned energies summed over domains, copy forces summed onto
+    their atoms: the oracle's periodic result at the FP32 tolerances."""
+    from test_gpu_domains import expected_counts
+    F, L, S, C = 16, 3, 1, 4
+    sy = syn.fcc(5, 5, 5, seed=10)
+    eng = engine()
+    vals, blob = _model(F, L, S, C, seed=10)
+    ref = loc.local_model(vals, F, K, L, S, C, sy.species, sy.positions, sy.cell)
+    with eng.Domains(F, blob, grid=grid, K=K, T=L, n_species=S, family="local", channels=C, skin=1.0) as dom:
+        out = dom.compute(sy.species, sy.positions, sy.cell, energies=True)
+        info = dom.info()
+    compare(out, ref)
+    owned, cands = expected_counts(orc, sy.positions, sy.cell, grid, 5.0 + 1.0)
+    assert [d["n_owned"] for d in info] == owned
+    assert [d["n_candidates"] for d in info] == cands
