@@ -80,6 +80,25 @@ def test_param_blob_layout():
     assert np.all(P["b1_0"] == 0)
 
 
+def test_local_param_blob_layout():
+    """The strictly local model's blob: the header the library checks and the value count of
+    the documented order (A0, c0, P0; per layer Q, M, m and, before the last, Gs, Gv; R1, d1,
+    R2, d2)."""
+    F, K, L, S, C = 64, 20, 3, 2, 16
+    blob = syn.local_params_blob(F, K, L, S, C, rc=5.0, e_scale=0.5, seed=0)
+    assert blob[:8] == b"CTDLOCAL"
+    ver, f, k, layers, s, c = struct.unpack("<iiiiii", blob[8:32])
+    rc, _, esc, nval = struct.unpack("<dddq", blob[32:64])
+    assert (ver, f, k, layers, s, c, rc, esc) == (1, F, K, L, S, C, 5.0, 0.5)
+    C2, Fh = 2 * C, F // 2
+    count = (K + 2 * S) * F + F + F * C2 + L * (F * C2 + (F + C2) * F + F) + (L - 1) * 2 * C2 * C
+    count += F * Fh + Fh + Fh + 1
+    assert nval == count == (len(blob) - 64) // 8
+    names = [n for n, _ in syn.local_param_shapes(F, K, L, S, C)]
+    assert names[:3] == ["A0", "c0", "P0"] and names[-4:] == ["R1", "d1", "R2", "d2"]
+    assert "Gs3" not in names and "Gs2" in names
+
+
 def test_struct_layouts_match_the_header():
     """ctypes mirrors of ctd_model_desc, ctd_stats and ctd_domain_info have the C compiler's sizes and offsets
     (a program built from include/painn.h with gcc prints them)."""
