@@ -5,7 +5,8 @@ exchanges information only between edges leaving the same atom, so an atom's ene
 function of its own cutoff sphere alone.  Pins: a dimer and a trimer evaluated with scalar
 arithmetic along the bond (all vectors of a dimer are parallel to it), central differences of
 the energy in positions and in strain, invariance under rotations, reflections, translations
-and permutations, strict locality through three layers, and continuity at the cutoff.
+and permutations, strict locality through three layers, continuity at the cutoff, energy
+weights and supercell extensivity.
 """
 import math
 
@@ -268,3 +269,23 @@ def test_energy_weights_scale_per_atom_energies(loc):
             x = sy.positions.copy(); x[7, comp] += sgn * h
             e.append(loc.local_model(vals, F, K, L, S, C, sy.species, x, sy.cell, need_grad=False)["energies"][4])
         assert c["forces"][7, comp] == pytest.approx(-(e[0] - e[1]) / (2 * h), rel=1e-6, abs=1e-9)
+
+
+def test_supercell_extensivity(loc):
+    """A 2x1x2 replica of a periodic cell has 4x the energy and virial, and each copy of an atom
+    carries its forces and energy (periodic images are handled like any other neighbour)."""
+    F, L, S, C = 8, 2, 2, 4
+    vals = _vals(F, L, S, C, seed=11)
+    sy = _water(8, seed=6)
+    a = loc.local_model(vals, F, K, L, S, C, sy.species, sy.positions, sy.cell)
+    reps = [(i, 0, k) for i in range(2) for k in range(2)]
+    x = np.concatenate([sy.positions + np.array(r) @ sy.cell for r in reps])
+    z = np.concatenate([sy.species] * len(reps))
+    H = sy.cell * np.array([[2.0], [1.0], [2.0]])
+    b = loc.local_model(vals, F, K, L, S, C, z, x, H)
+    assert b["energy"] == pytest.approx(4 * a["energy"], rel=1e-12)
+    np.testing.assert_allclose(b["virial"], 4 * a["virial"], rtol=1e-11, atol=1e-11)
+    n = len(sy.species)
+    for q in range(len(reps)):
+        np.testing.assert_allclose(b["forces"][q * n:(q + 1) * n], a["forces"], atol=1e-11)
+        np.testing.assert_allclose(b["energies"][q * n:(q + 1) * n], a["energies"], atol=1e-12)
