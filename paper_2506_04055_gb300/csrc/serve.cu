@@ -11,6 +11,11 @@
 // virials and displacements come from segmented reductions whose order depends only on the
 // replica itself, so a replica's trajectory is the same alone and in any mix.
 //
+// A queued request may carry a Nose-Hoover chain (Methods, "MD simulations": NVT).  Its chain
+// state is one row of the batch's chain table; one thread per replica takes the chain half
+// steps, and the velocity factors enter the masked kick and one scaling pass (factor 1 for
+// replicas without a thermostat, so they are unaffected by the others).
+//
 // The paper's buffering rules (Results, "Runtime optimizations and buffering": capacities that
 // only grow, repeat with larger buffers) apply to the batch arrays as to a single system.
 #include <algorithm>
