@@ -153,6 +153,8 @@ int check_status(ctd_ctx* c) {
 int build_from_device_positions(ctd_ctx* c, int64_t n, const double H[9], double cutoff, double skin) {
   if (!finite_cell(H)) return fail(c, CTD_ERR_INVALID_ARG, "cell is singular or not finite");
   if (!(cutoff > 0.0) || !(skin >= 0.0)) return fail(c, CTD_ERR_INVALID_ARG, "cutoff must be > 0, skin >= 0");
+  // a build that fails below leaves no list behind, so the next call builds again
+  c->have_list = false;
   int r = setup_geometry(c, H, cutoff + skin);
   if (r) return r;
   StageGuard sg(STG_BUILD);
@@ -176,6 +178,9 @@ int build_from_device_positions(ctd_ctx* c, int64_t n, const double H[9], double
   ENSURE(c, c->status, sizeof(int32_t) * 4);
   ENSURE(c, c->scan_tmp, scan_temp_bytes(std::max<int64_t>(n1, c->ncell)) + 64);
   CUDA_OK(c, cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), st));
+  // non-finite positions are reported (CTD_ERR_NONFINITE) instead of being binned: the binning
+  // clamps their cell index, so they would silently find no neighbours
+  launch_check_finite(st, 3 * n, P<double>(c->x_user), P<int>(c->status));
   CUDA_OK(c, cudaMemsetAsync(c->cell_count.p, 0, sizeof(int32_t) * c->ncell, st));
   CUDA_OK(c, cudaMemsetAsync(c->cursor.p, 0, sizeof(int32_t) * c->ncell, st));
   launch_wrap_bin(st, n, P<double>(c->x_user), c->geom, P<double>(c->xw), P<int32_t>(c->wrapm),
@@ -275,7 +280,7 @@ size_t model_bytes_per_atom(const ctd_ctx* c) {
   for (int b = 0; b < model_buffer_count(); ++b) bytes += sizeof(float) * (size_t)model_buffer_floats_per_atom(b, F, T, g4);
   if (c->desc.precision == CTD_PREC_BF16)
     for (int b = 0; b < model_bf16_buffer_count(); ++b)
-      bytes += sizeof(__nv_bfloat16) * (size_t)model_bf16_buffer_elems_per_atom(b, F, T);
+      bytes += sizeof(__nv_bfloat16) * (size_t)model_bf16_buffer_elems_per_atom(b, F, T, model_uses_msg_mma(c->mw));
   return bytes;
 }
 
@@ -363,7 +368,7 @@ int evaluate(ctd_ctx* c, bool need_grad) {
     if ((int)c->mbufb.size() < nbb) c->mbufb.resize(nbb);
     std::vector<__nv_bfloat16*> bptrs(nbb, nullptr);
     for (int b = 0; b < nbb; ++b) {
-      int64_t per = model_bf16_buffer_elems_per_atom(b, F, T);
+      int64_t per = model_bf16_buffer_elems_per_atom(b, F, T, model_uses_msg_mma(c->mw));
       if (per == 0) continue;
       ENSURE(c, c->mbufb[b], sizeof(__nv_bfloat16) * (size_t)per * (size_t)n1);
       bptrs[b] = P<__nv_bfloat16>(c->mbufb[b]);
@@ -781,7 +786,7 @@ int ctd_set_option(ctd_ctx* c, int32_t option, int64_t value) {
       c->mw.edge_chunk_rows = value;
       return CTD_OK;
     case CTD_OPT_TC_MESSAGE:
-      if (value < 1 || value > 4) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_MESSAGE takes 1 .. 4");
+      if (value < 1 || value > 5) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_MESSAGE takes 1 .. 5");
       c->mw.tc_message_variant = (int)value;
       return CTD_OK;
     case CTD_OPT_EDGE_STORE:
