@@ -304,3 +304,41 @@ def test_serve_thermostat_arguments_are_checked():
         srv.set_thermostat(rid, 300.0, 100.0, 0)       # back to NVE while queued
         with pytest.raises(eng.CtdError):
             srv.thermostat(rid)
+
+
+def test_buffer_regrowth_mid_run_leaves_trajectories_unchanged():
+    """Grow-only buffers shared by the batch (Results, "Runtime optimizations and buffering":
+    nearly full buffers grow together).  A 6,000-atom replica admitted after three steps makes
+    every batch buffer of the server grow; the two small replicas resident before and after the
+    growth keep trajectories bit-identical to a server that never grew."""
+    eng = engine()
+    _, blob = model(F, T, S, seed=13, bias=0.1)
+    items = _replicas()
+    small = [items[2], items[1]]
+    big = syn.water_box(2000, seed=14)
+    vbig = syn.maxwell_boltzmann(big.masses, 300.0, seed=15)
+
+    def run(with_big):
+        srv = eng.Server(F, blob, T=T, n_species=S, precision="fp32", dt=DT)
+        ids = [srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, 12, skin=1.0) for sy, v in small]
+        held = []
+        for step in range(40):
+            if with_big and step == 3:
+                held.append(srv.stats()["bytes_held"])
+                srv.submit(big.species, big.masses, big.positions, vbig, big.cell, 4, skin=1.0)
+            srv.step()
+            if with_big and step == 3:
+                held.append(srv.stats()["bytes_held"])
+            if all(srv.poll(i)["state"] == 2 for i in ids) and step > 4:
+                break
+        out = [srv.poll(i) for i in ids]
+        srv.close()
+        return out, held
+
+    grown, held = run(True)
+    plain, _ = run(False)
+    assert held[1] > 2 * held[0], held          # the admission regrew the batch buffers
+    for a, b in zip(grown, plain):
+        assert a["state"] == 2 and a["steps_done"] == 12
+        for key in ("epot", "ekin", "positions", "velocities", "virial"):
+            np.testing.assert_array_equal(a[key], b[key])
