@@ -357,15 +357,20 @@ void ctd_domains_destroy(ctd_domains *d);
  * positions: device doubles [n][3] (any atom order, need not be wrapped); cell: host
  * double[9] (rows = lattice vectors).  pair_i, pair_j: device int32 [cap]; pair_shift: device
  * int8 [cap][3].  They receive the pairs in the caller's atom indices (grouped by atom, not
- * sorted) with the image shift relative to the wrapped positions.  *n_pairs (host) receives
- * the number of pairs; if it exceeds cap nothing is written and CTD_ERR_CAPACITY is returned.
- * cuda_stream: the cudaStream_t to run on (NULL = default stream); the call synchronises it.
+ * sorted) with the image shift relative to the positions passed in: the pair's vector is
+ * x_j - x_i + shift[0] a + shift[1] b + shift[2] c for those positions, wrapped or not.  If a
+ * shift does not fit int8 (positions more than ~127 cells outside the cell) the call returns
+ * CTD_ERR_INVALID_ARG.  *n_pairs (host) receives the number of pairs; if it exceeds cap (or
+ * INT32_MAX) nothing is written and CTD_ERR_CAPACITY is returned, so the caller can size its
+ * arrays and call again.  Non-finite positions: CTD_ERR_NONFINITE.
+ * cuda_stream: the cudaStream_t to run on (NULL = default stream); the call synchronises it and
+ * copies counts to host memory, so it must not be called on a stream that is being captured
+ * into a CUDA graph (it returns CTD_ERR_INVALID_ARG there).
  *
  * The first call on each device looks up the device address of the static array (with that
- * device current), so make a first call before capturing any stream on that device.  All
- * calls share the one array, and each starts by clearing the parts that must start at zero;
- * calls that overlap on the GPU (different streams or threads at once) race on it and must be
- * serialised by the caller. */
+ * device current).  All calls share the one array, and each starts by clearing the parts that
+ * must start at zero; calls that overlap on the GPU (different streams or threads at once)
+ * race on it and must be serialised by the caller. */
 #define CTD_NOALLOC_MAX_ATOMS 32768
 #define CTD_NOALLOC_MAX_CELLS 32768
 int ctd_neighbors_noalloc(int64_t n, const double *positions, const double cell[9], double cutoff,

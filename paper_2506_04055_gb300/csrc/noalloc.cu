@@ -10,7 +10,9 @@
 //
 // The pairs are the same set ctd_build_neighbors finds (same wrap, same cell search, same
 // FP64 pair test); they are written in the caller's atom indices, grouped by atom in cell
-// order, not sorted.
+// order, not sorted, with each image shift taken relative to the caller's own positions (the
+// wrap counts of both atoms folded in), so that r_ij = x_j - x_i + shift . H holds for the
+// positions the caller passed, wrapped or not.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -51,6 +53,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 unsigned char* g_addr[kMaxDevices] = {};
+int32_t g_host_counts[kNAMaxAtoms];   // per-atom pair counts, for the int64 total (guarded by g_mu)
 
 int scratch_address(unsigned char** out) {
   int dev = 0;
@@ -71,24 +74,25 @@ int scratch_address(unsigned char** out) {
   return CTD_OK;
 }
 
-// Fill pass writing caller indices.  Same enumeration and FP64 pair test as the count pass;
-// writes are bounded by the row's counted slots and by cap (overruns raise status bit 1).
+// Fill pass writing caller indices.  Same enumeration and FP64 pair test as the count pass,
+// from the home cell the binning assigned (cell[perm[i]]), so both passes visit the same
+// neighbour cells.  Writes are bounded by the row's counted slots and by cap.  Status bits:
+// 2 a pair beyond its row or cap, 4 a row with fewer pairs than counted (its tail would be
+// stale), 8 a shift relative to the caller's positions outside the int8 range.
 __global__ void k_na_fill(int64_t n, const double* __restrict__ xs, const int32_t* __restrict__ cstart, CellGeom g,
-                          const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ perm, int64_t cap,
+                          const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ perm,
+                          const int32_t* __restrict__ cell, const int32_t* __restrict__ wrapm, int64_t cap,
                           int32_t* __restrict__ pi, int32_t* __restrict__ pj, int8_t* __restrict__ shift,
                           int* status) {
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (i >= n) return;
   const double xi0 = xs[3 * i], xi1 = xs[3 * i + 1], xi2 = xs[3 * i + 2];
-  int ci[3];
-  for (int a = 0; a < 3; ++a) {
-    double s = (g.G[3 * a] * xi0 + g.G[3 * a + 1] * xi1) + g.G[3 * a + 2] * xi2;
-    int c = (int)floor(s * (double)g.nc[a]);
-    ci[a] = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
-  }
-  const int out = row_ptr[i], end = row_ptr[i + 1];
   const int self = perm[i];
+  const int hl = cell[self];   // lexicographic: (c0 nc1 + c1) nc2 + c2
+  const int ci[3] = {hl / (g.nc[1] * g.nc[2]), (hl / g.nc[2]) % g.nc[1], hl % g.nc[2]};
+  const int wi[3] = {wrapm[3 * self], wrapm[3 * self + 1], wrapm[3 * self + 2]};
+  const int out = row_ptr[i], end = row_ptr[i + 1];
   int cnt = 0;
   for (int d0 = -g.M[0]; d0 <= g.M[0]; ++d0)
     for (int d1 = -g.M[1]; d1 <= g.M[1]; ++d1)
@@ -120,12 +124,21 @@ __global__ void k_na_fill(int64_t n, const double* __restrict__ xs, const int32_
           unsigned m = __ballot_sync(0xffffffffu, keep);
           if (keep) {
             int pos = out + cnt + __popc(m & ((1u << lane) - 1u));
+            const int other = perm[j];
+            // x~ = x - wrap . H for both atoms, so the caller's shift is im - wrap_j + wrap_i
+            int sc[3];
+            bool fits = true;
+            for (int a = 0; a < 3; ++a) {
+              sc[a] = im[a] - wrapm[3 * other + a] + wi[a];
+              fits = fits && sc[a] >= -128 && sc[a] <= 127;
+            }
+            if (!fits) atomicOr(status, 8);
             if (pos < end && pos < cap) {
               pi[pos] = self;
-              pj[pos] = perm[j];
-              shift[3 * (int64_t)pos] = (int8_t)im[0];
-              shift[3 * (int64_t)pos + 1] = (int8_t)im[1];
-              shift[3 * (int64_t)pos + 2] = (int8_t)im[2];
+              pj[pos] = other;
+              shift[3 * (int64_t)pos] = (int8_t)sc[0];
+              shift[3 * (int64_t)pos + 1] = (int8_t)sc[1];
+              shift[3 * (int64_t)pos + 2] = (int8_t)sc[2];
             } else {
               atomicOr(status, 2);
             }
@@ -133,6 +146,7 @@ __global__ void k_na_fill(int64_t n, const double* __restrict__ xs, const int32_
           cnt += __popc(m);
         }
       }
+  if (lane == 0 && cnt != end - out) atomicOr(status, 4);
 }
 
 }  // namespace
@@ -183,11 +197,27 @@ extern "C" int ctd_neighbors_noalloc(int64_t n, const double* positions, const d
   }
   if (ncell > kNAMaxCells) return CTD_ERR_INVALID_ARG;
   g.R2 = R * R;
+  // Bounds on the int32 counts: a home atom's search visits each cell at most
+  // visits = prod_a ceil((2 M_a + 1) / nc_a) times (once per image), so it counts at most
+  // n * visits pairs, and all atoms together at most n^2 * visits.
+  int64_t visits = 1;
+  for (int a = 0; a < 3; ++a) visits *= (2 * (int64_t)g.M[a] + 1 + g.nc[a] - 1) / g.nc[a];
+  if (n * visits > (int64_t)INT32_MAX) return CTD_ERR_INVALID_ARG;   // one atom's count could overflow
+  const bool total_may_overflow = n * n * visits > (int64_t)INT32_MAX;
 
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  {
+    // the call synchronises its stream and reads results into host memory: not capturable
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return CTD_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return CTD_ERR_INVALID_ARG;
+  }
   unsigned char* base = nullptr;
   int r = scratch_address(&base);
   if (r) return r;
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   double* xw = reinterpret_cast<double*>(base + kOffXw);
   double* xw_s = reinterpret_cast<double*>(base + kOffXwS);
   double* xref = reinterpret_cast<double*>(base + kOffXref);
@@ -211,34 +241,54 @@ extern "C" int ctd_neighbors_noalloc(int64_t n, const double* positions, const d
     cudaGetLastError();
     return CTD_ERR_CUDA;
   }
+  launch_check_finite(st, 3 * n, positions, status + 1);
   launch_wrap_bin(st, n, positions, g, xw, wrapm, cellid, ccount);
   launch_exclusive_scan(st, ncell, ccount, cstart, sums);
   launch_place(st, n, cellid, cstart, cursor, tmp);
   launch_sort_cells(st, ncell, cstart, tmp, perm);
   launch_gather_sorted(st, n, perm, xw, positions, nullptr, xw_s, xref, nullptr, inv);
   launch_pair_search(st, false, n, xw_s, cstart, g, count, nullptr, nullptr, nullptr, nullptr);
+  int stv[2] = {0, 0};
+  if (total_may_overflow) {
+    // the row offsets are an int32 scan: total the per-atom counts in int64 first
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (cudaMemcpyAsync(g_host_counts, count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(stv, status, sizeof(stv), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return CTD_ERR_CUDA;
+    }
+    if (stv[1]) return CTD_ERR_NONFINITE;
+    int64_t total64 = 0;
+    for (int64_t k = 0; k < n; ++k) total64 += g_host_counts[k];
+    if (total64 > (int64_t)INT32_MAX) {
+      *n_pairs = total64;
+      return CTD_ERR_CAPACITY;
+    }
+  }
   launch_exclusive_scan(st, n, count, row, sums);
   int32_t total = 0;
   if (cudaMemcpyAsync(&total, row + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(stv, status, sizeof(stv), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return CTD_ERR_CUDA;
   }
-  if (total < 0) return CTD_ERR_CAPACITY;
+  if (stv[1]) return CTD_ERR_NONFINITE;
   *n_pairs = total;
   if (total > cap) return CTD_ERR_CAPACITY;
   if (n > 0) {
     int64_t threads = n * 32;
     LaunchScope ls_(st);
     k_na_fill<<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-        n, xw_s, cstart, g, row, perm, cap, pair_i, pair_j, pair_shift, status);
+        n, xw_s, cstart, g, row, perm, cellid, wrapm, cap, pair_i, pair_j, pair_shift, status);
   }
-  int stv = 0;
-  if (cudaMemcpyAsync(&stv, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  if (cudaMemcpyAsync(stv, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return CTD_ERR_CUDA;
   }
   if (cudaGetLastError() != cudaSuccess) return CTD_ERR_CUDA;
-  return stv ? CTD_ERR_CAPACITY : CTD_OK;
+  if (stv[0] & 8) return CTD_ERR_INVALID_ARG;   // a shift does not fit int8: positions too far out
+  return stv[0] ? CTD_ERR_CAPACITY : CTD_OK;
 }
