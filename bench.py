@@ -29,15 +29,30 @@ FCC_CELLS = 63
 F, K, T, S = 128, 20, 3, 1
 RC, SKIN, DT, TEMP = 5.0, 1.0, 1.0, 300.0
 
-# algorithmic FLOPs per (active edge, feature channel) of the two edge kernels:
-# message: filter 3K FMA + f_c scaling + s / v message terms; adjoint: filter and its radial
-# derivative (2 x 3K FMA) + message adjoint terms + per-edge gradient partials.
+# Algorithmic work (the per-unit figures of the roofline):
+#   per active edge and layer, the message step is (6K + 22) F FLOP: the filter contraction
+#   2 x 3F x K (the K x 3F filter times the basis), bias and cutoff, and the s / v message terms
+#   (22 F); its adjoint is counted as the same again (input gradients only);
+#   per atom and step, 2 T (30 F^2 + n_e (6K + 22) F) + F^2 FLOP (node MLPs 30 F^2 per layer,
+#   forward and adjoint, plus the readout) and 42 F T stored values (read and written node
+#   features and saved activations) plus 2 T n_e 8 B of edge indices.
+def edge_flop_per_edge():
+    return (6 * K + 22) * F
+
+
+def step_flop_per_atom(n_e):
+    return 2 * T * (30 * F * F + n_e * (6 * K + 22) * F) + F * F
+
+
+def step_bytes_per_atom(n_e, value_bytes):
+    return 42 * F * T * value_bytes + 2 * T * n_e * 8
+
+
+# FMA-pipe FLOPs per (active edge, feature channel) the edge kernels execute on CUDA cores
+# (reported beside the roofline): FP32 message 6K + 18, FP32 adjoint 12K + 45; with the filter
+# on the tensor pipe (BF16, F = 128) message 21, adjoint 50.
 EDGE_FWD_FLOP_PER_EF = 6 * K + 18
 EDGE_BWD_FLOP_PER_EF = 12 * K + 45
-# On the BF16 path (F = 128) the filter contractions run on the tensor pipe; the FMA pipes keep
-# the elementwise part: message 21 FLOP (bias, f_c, four message terms), adjoint 50 FLOP (bias,
-# f_c and f_c' terms, phi-gradient sums, u-projection, dU/dd and dU/du partials and their
-# reduction over the features).
 EDGE_FWD_TC_ALU_FLOP_PER_EF = 21
 EDGE_BWD_TC_ALU_FLOP_PER_EF = 50
 FP32_LANES_PER_SM, N_SM = 128, 152
@@ -368,40 +383,54 @@ def run_ours(args):
     dom_ms, dom_launches = prof[dom]
     active_edges_per_launch = r.get("active_edges")
     roofline = None
+    # active edges per launch and n_e from the stats of one compute call on the same system
+    import paper_2506_04055_gb300 as eng2
+    with eng2.Potential(F, K=K, T=T, n_species=S, rc=RC, params=blob) as p2:
+        st = p2.compute(sy.species, sy.positions, sy.cell, stats=True)["stats"]
+    ea = st["n_active_edges"]
+    n_e = ea / sy.n
     if dom in ("edge_bwd", "edge_fwd") and dom_launches:
-        # active edges: n_e from the stats of one compute call on the same system
-        import paper_2506_04055_gb300 as eng2
-        with eng2.Potential(F, K=K, T=T, n_species=S, rc=RC, params=blob) as p2:
-            st = p2.compute(sy.species, sy.positions, sy.cell, stats=True)["stats"]
-        ea = st["n_active_edges"]
         launch_s = dom_ms / dom_launches / 1e3
-        peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         tc = head == "bf16" and F == 128 and (dom == "edge_fwd" or args.tc_adjoint != 0)
-        if tc:
-            # FMA-pipe FLOPs of the tensor-core kernel; the filter contractions (2K FLOP per
-            # edge, feature and channel, and as many again for the derivative in the adjoint)
-            # are on the tensor pipe and reported beside it against the BF16 peak
-            alu_ef = EDGE_BWD_TC_ALU_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_TC_ALU_FLOP_PER_EF
-            tensor = ea * 3 * F * 2 * K * (2 if dom == "edge_bwd" else 1)
-            kname = ("k_edge_bwd_tc" if args.tc_adjoint == 1 else "k_edge_bwd_tcg") if dom == "edge_bwd" else "k_edge_fwd_tc"
-        else:
-            alu_ef = EDGE_BWD_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_FLOP_PER_EF
-            tensor = 0
-            kname = f"k_{dom}"
-        flop = ea * F * alu_ef
+        kname = ("k_edge_bwd_tcg" if dom == "edge_bwd" else "k_edge_fwd_tc") if tc else f"k_{dom}"
+        flop = ea * edge_flop_per_edge()
         achieved = flop / launch_s / 1e12
-        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": kernel_traffic(kname),
-                    "peak_source": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                                   f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
-                    "algorithmic_flop_per_launch": flop, "launch_ms": dom_ms / dom_launches,
-                    "active_edges": ea}
-        if tensor:
-            tpk = peaks.get("bf16_tflops_sustained", 1700.0)
-            roofline["tensor_flop_per_launch"] = tensor
-            roofline["tensor_tflops"] = tensor / launch_s / 1e12
-            roofline["tensor_frac_of_bf16_sustained"] = tensor / launch_s / 1e12 / tpk
+        if tc:
+            # the contraction runs on tcgen05 in BF16: the sustained BF16 peak (timed in a long step)
+            peak, bound = peaks.get("bf16_tflops_sustained", 1700.0), "tensor"
+            peak_source = f"bf16_tflops_sustained ({peak_kind})"
+        else:
+            peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            bound = "alu"
+            peak_source = (f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                           f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)")
+        traffic = kernel_traffic(kname)
+        roofline = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic, "peak_source": peak_source,
+                    "algorithmic_flop_per_launch": flop, "flop_per_active_edge": edge_flop_per_edge(),
+                    "launch_ms": dom_ms / dom_launches, "active_edges": ea}
+        if traffic:
+            roofline["hbm_gbs"] = traffic / launch_s / 1e9
+            roofline["hbm_frac"] = traffic / launch_s / 1e9 / peaks.get("hbm_gbs", 6800.0)
+        alu_ef = ((EDGE_BWD_TC_ALU_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_TC_ALU_FLOP_PER_EF) if tc else
+                  (EDGE_BWD_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_FLOP_PER_EF))
+        fma_peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roofline["fma_pipe"] = {"flop_per_edge_channel": alu_ef, "tflops": ea * F * alu_ef / launch_s / 1e12,
+                                "frac_of_fp32_fma_peak": ea * F * alu_ef / launch_s / 1e12 / fma_peak}
+    # the whole step against both roofs (algorithmic FLOPs and bytes per atom-step)
+    step_s = s["ms_per_step"] / 1e3
+    vb = 2 if head == "bf16" else 4
+    step_flop = sy.n * step_flop_per_atom(n_e)
+    step_bytes = sy.n * step_bytes_per_atom(n_e, vb)
+    tpk = peaks.get("bf16_tflops_sustained", 1700.0) if head == "bf16" else \
+        N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    step_roof = {"flop": step_flop, "bytes": step_bytes, "tflops": step_flop / step_s / 1e12,
+                 "flop_frac": step_flop / step_s / 1e12 / tpk,
+                 "gbs": step_bytes / step_s / 1e9, "bytes_frac": step_bytes / step_s / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                 "bound_ms": 1e3 * max(step_flop / (tpk * 1e12), step_bytes / (peaks.get("hbm_gbs", 6800.0) * 1e9)),
+                 "n_e": n_e}
+    if roofline is not None:
+        roofline["step"] = step_roof
     launches = int(sum(v[1] for v in prof.values()))
     line = {
         "metric": METRIC, "value": s["value"], "unit": "atom-steps/s", "n_gpus": world,

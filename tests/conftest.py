@@ -12,12 +12,6 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
 
 
-def pytest_collection_modifyitems(config, items):
-    # GPU tests fail loudly (not skip) when they are selected on a machine without a GPU:
-    # they are only selected with -m gpu, which is run on the GPU machine.
-    pass
-
-
 @pytest.fixture(scope="session")
 def orc():
     import oracle

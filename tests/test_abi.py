@@ -39,10 +39,17 @@ def test_every_declared_symbol_is_exported(lib):
         getattr(lib, name)
 
 
-def test_library_targets_sm103a():
-    so = os.path.join(ROOT, "paper_2506_04055_gb300", "libctd_painn.so")
-    out = subprocess.run(["cuobjdump", "--list-elf", so], capture_output=True, text=True).stdout
-    assert "sm_103a" in out
+def test_library_targets_sm103a(lib):
+    """Every translation unit is compiled for compute_103a/sm_103a only, and the assembler's own
+    report of each build names sm_103a for every kernel it compiled."""
+    from paper_2506_04055_gb300 import buildlib
+    assert buildlib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    for src in buildlib.SOURCES:
+        log = open(os.path.join(buildlib.BUILD, src + ".ptxas.txt")).read()
+        targets = set(re.findall(r"for '(sm_[0-9a-z]+)'", log))
+        assert targets <= {"sm_103a"}, (src, targets)
+        if "__global__" in open(os.path.join(buildlib.SRC, src)).read():
+            assert targets == {"sm_103a"}, src
 
 
 def test_invalid_model_description_rejected(lib):
