@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libctd_painn.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "neighbors.cu", "scan.cu", "model_fp32.cu", "md.cu", "prof.cu", "noalloc.cu", "gemm_bf16.cu", "edge_tc.cu", "serve.cu", "domain.cu", "selftest.cu", "model_local.cu"]
+SOURCES = ["api.cu", "neighbors.cu", "scan.cu", "model_fp32.cu", "md.cu", "prof.cu", "noalloc.cu", "gemm_bf16.cu", "edge_tc.cu", "edge_mma.cu", "serve.cu", "domain.cu", "selftest.cu", "model_local.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
               "--expt-relaxed-constexpr", "-Xptxas", "-v"]

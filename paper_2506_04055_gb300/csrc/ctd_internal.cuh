@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <cstddef>
 #include <vector>
@@ -104,7 +105,8 @@ struct ModelW {
   bool tc_adjoint;                 // BF16 path: edge adjoint with the tensor-core filter
   int tc_adjoint_variant;          // 1 register gathers, 2 bulk-copy gathers, 3 + folded basis, 4 + split basis
   bool edge_store;                 // store per-edge filters in the forward pass for the adjoint
-  int tc_message_variant;          // BF16 message kernel: 1 register gathers, 2 bulk-copy gathers, 3 = 1 + split basis
+  int tc_message_variant;          // BF16 message kernel: 1 register gathers, 2 bulk-copy gathers, 3 = 1 + split basis,
+                                   // 5 contraction over each receiver's edges on tcgen05 (edge_mma.cu)
   int64_t edge_chunk_rows;         // bulk-gathered kernels: rows per chunk (0: one range per stream)
 };
 
@@ -219,16 +221,23 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
                 const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm, const float* Gvm,
                 float* GPHI, float4* hedge, int* status,
                 const int32_t* aend, const float* G4);
+// edge_mma.cu: the message step as a tensor-core contraction over each receiver's edges
+// (F = 128, K < 32): gathered FP16 message rows x per-edge basis, FP32 filter weights after it.
+bool edge_mma_supported(int F, int K);
+int edge_fwd_mma(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow, const int32_t* acol,
+                 const float4* ar, const __half* PHIh, const float* S, const float* V, float* SM, float* VM,
+                 __nv_bfloat16* VMb, int* status);
 template <int EPI>
 int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, int64_t lda,
               const __nv_bfloat16* W, const float* bias, const float* aux, int ldaux, float* out, int ldo,
-              __nv_bfloat16* outb, int ldob, int* status);
+              __nv_bfloat16* outb, int ldob, int* status, __half* outh = nullptr);
 // model_fp32.cu
 int model_buffer_count();
 bool model_uses_g4(const ModelW& m, int precision);
 int64_t model_buffer_floats_per_atom(int b, int F, int T, bool g4);
 int model_bf16_buffer_count();
-int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T);
+bool model_uses_msg_mma(const ModelW& m);
+int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T, bool msg_mma);
 int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
                                 const int32_t* arow, const int32_t* acol, const float4* ar, const int32_t* arev,
                                 float* const* bufs, __nv_bfloat16* const* bbufs, bool need_grad,

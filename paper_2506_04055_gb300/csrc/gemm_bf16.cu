@@ -13,6 +13,8 @@
 // winds down.
 #include <cstdio>
 
+#include <cuda_fp16.h>
+
 #include "ctd_internal.cuh"
 #include "umma.cuh"
 
@@ -30,6 +32,7 @@ struct GemmBf16Args {
   int ldo;
   bf16* outb;
   int ldob;
+  __half* outh;   // EPI 4: FP16 message table [M][5F] = [phi_s | psi_0 | psi_1 | psi_2 | phi_vs] (optional)
   int* status;
   int a_stages, n_acc, b_box_rows, n_chunk;   // a_stages: k-block stages of the A ring
   uint32_t tmem_cols;
@@ -204,15 +207,27 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __gr
             if (EPI == 0 || EPI == 1 || EPI == 4) { x.x += bq.x; x.y += bq.y; x.z += bq.z; x.w += bq.w; }
             if (EPI == 4) {
               float* o = p.out + m * p.ldo;
+              __half* oh = p.outh ? p.outh + m * 5 * Fb : nullptr;
+              auto put_h = [&](int col, float4 y) {
+                if (oh) {
+                  const __half2 a = __floats2half2_rn(y.x, y.y), b = __floats2half2_rn(y.z, y.w);
+                  *reinterpret_cast<uint2*>(oh + col) =
+                      make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+                }
+              };
               if (blk == 0) {
                 *reinterpret_cast<float4*>(o + f0) = x;
+                put_h(f0, x);
               } else if (blk == 2) {
                 *reinterpret_cast<float4*>(o + 4 * Fb + f0) = x;
+                put_h(4 * Fb + f0, x);
               } else {
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                  *reinterpret_cast<float4*>(o + (1 + c) * Fb + f0) =
-                      make_float4(gv[j][c].x * x.x, gv[j][c].y * x.y, gv[j][c].z * x.z, gv[j][c].w * x.w);
+                for (int c = 0; c < 3; ++c) {
+                  const float4 y = make_float4(gv[j][c].x * x.x, gv[j][c].y * x.y, gv[j][c].z * x.z, gv[j][c].w * x.w);
+                  *reinterpret_cast<float4*>(o + (1 + c) * Fb + f0) = y;
+                  put_h((1 + c) * Fb + f0, y);
+                }
                 *reinterpret_cast<float4*>(o + 5 * Fb + f0) = x;
               }
               continue;
@@ -288,7 +303,7 @@ bool gemm_bf16_supported(int N, int K) { return K % 64 == 0 && K > 0 && N % 32 =
 template <int EPI>
 int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t lda, const bf16* W,
               const float* bias, const float* aux, int ldaux, float* out, int ldo, bf16* outb, int ldob,
-              int* status) {
+              int* status, __half* outh) {
   if (M == 0) return 0;
   // the epilogue moves 16-byte quads of FP32 (8-byte quads of BF16) per row
   if (!gemm_bf16_supported(N, K) || (lda * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) ||
@@ -298,7 +313,8 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
     return -1;
   GemmBf16Args p{};
   p.M = M; p.N = N; p.K = K; p.bias = bias; p.aux = aux; p.ldaux = ldaux; p.out = out; p.ldo = ldo;
-  p.outb = outb; p.ldob = ldob; p.status = status;
+  p.outb = outb; p.ldob = ldob; p.status = status; p.outh = EPI == 4 ? outh : nullptr;
+  if (p.outh && (reinterpret_cast<uintptr_t>(outh) & 7)) return -1;
   p.b_box_rows = N % 64 == 0 ? 64 : 32;
   p.n_chunk = N <= 256 ? N : N / 2;
   if (p.n_chunk > 256 || p.n_chunk % 16) return -1;
@@ -333,14 +349,14 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
 }
 
 template int gemm_bf16<0>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*);
 template int gemm_bf16<1>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*);
 template int gemm_bf16<2>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*);
 template int gemm_bf16<3>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*);
 template int gemm_bf16<4>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*);
 
 }  // namespace ctd

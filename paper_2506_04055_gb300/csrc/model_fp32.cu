@@ -721,18 +721,39 @@ __global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restr
   }
 }
 
+// Error-free transformations in FP32 (Knuth's TwoSum; the exact product split by one FMA):
+// a + b = s + e and a * b = p + e exactly, with s, p the rounded results.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// Add the pair (x, xe) to the float-float accumulator (s, c): c collects every rounding error.
+__device__ __forceinline__ void ff_add(float& s, float& c, float x, float xe) {
+  float t, e;
+  two_sum_f(s, x, t, e);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(e, xe));
+}
+
 // F_i = sum_{e in row i} (hedge[rev e] - hedge[e]);  virial partials = sum_e r_e (x) hedge[e]
-// (= -sum_e r_e (x) dU/dr_e over all edges).  One warp per row, FP64 per-warp accumulation.
+// (= -sum_e r_e (x) dU/dr_e over all edges).  One warp per row for the forces.  The virial is a
+// compensated sum: every product r_p h_q is split exactly into a float pair (FMA) and added with
+// TwoSum into float-float accumulators that each lane keeps over all its edges of all its rows
+// (about 44 significant bits); the warp combines its lanes once at the end with TwoSum, and the
+// warps of a block in FP64 Neumaier order, so the only roundings left are those of the
+// float-float sums and of the final FP64 sums.
 __global__ void k_forces(int64_t n, const int32_t* __restrict__ arow, const float4* __restrict__ ar,
                          const int32_t* __restrict__ arev, const float4* __restrict__ hedge,
                          float* __restrict__ force, double* __restrict__ vpart, int* status) {
-  __shared__ double sv[kThreads / 32][9];
+  __shared__ double sv[kThreads / 32][18];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double vacc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  float v[9], ve[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) v[p] = ve[p] = 0.f;
   const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
   for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + w; i < n; i += nw) {
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    float v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int a = arow[i] + lane; a < arow[i + 1]; a += 32) {
       const int ra = arev[a];
       const float4 h = hedge[a], r = ar[a];
@@ -744,28 +765,41 @@ __global__ void k_forces(int64_t n, const int32_t* __restrict__ arow, const floa
 #pragma unroll
       for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) v[3 * p + q] = fmaf(rr[p], hh[q], v[3 * p + q]);
+        for (int q = 0; q < 3; ++q) {
+          const float pr = __fmul_rn(rr[p], hh[q]);
+          ff_add(v[3 * p + q], ve[3 * p + q], pr, __fmaf_rn(rr[p], hh[q], -pr));
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
       fx += __shfl_xor_sync(0xffffffffu, fx, o);
       fy += __shfl_xor_sync(0xffffffffu, fy, o);
       fz += __shfl_xor_sync(0xffffffffu, fz, o);
-#pragma unroll
-      for (int p = 0; p < 9; ++p) v[p] += __shfl_xor_sync(0xffffffffu, v[p], o);
     }
     if (lane == 0) {
       force[3 * i] = fx; force[3 * i + 1] = fy; force[3 * i + 2] = fz;
-#pragma unroll
-      for (int p = 0; p < 9; ++p) vacc[p] += (double)v[p];
     }
   }
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      const float os = __shfl_xor_sync(0xffffffffu, v[p], o), oe = __shfl_xor_sync(0xffffffffu, ve[p], o);
+      ff_add(v[p], ve[p], os, oe);
+    }
   if (lane == 0)
-    for (int p = 0; p < 9; ++p) sv[w][p] = vacc[p];
+    for (int p = 0; p < 9; ++p) {
+      sv[w][p] = (double)v[p];
+      sv[w][9 + p] = (double)ve[p];
+    }
   __syncthreads();
   if (threadIdx.x < 9) {
-    double s = 0.0;
-    for (int q = 0; q < kThreads / 32; ++q) s += sv[q][threadIdx.x];
-    vpart[(int64_t)blockIdx.x * 9 + threadIdx.x] = s;
+    double s = 0.0, c = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q)
+      for (int h = 0; h < 2; ++h) {
+        const double x = sv[q][9 * h + threadIdx.x], t = s + x;
+        c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+      }
+    vpart[(int64_t)blockIdx.x * 9 + threadIdx.x] = s + c;
   }
 }
 
@@ -989,18 +1023,22 @@ enum BufB {
   BB_GUV,                    // [gUv | gVv]            [3n][2F]
   BB_GP3,                    // g_phi                  [n][3F]
   BB_GH1,                    // g_h1                   [n][F]
+  BB_PHIH,                   // FP16 message table [phi_s | psi_0..2 | phi_vs] [n][5F] (contracted message kernel)
   BB_COUNT
 };
 
 int model_bf16_buffer_count() { return BB_COUNT; }
 
-int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T) {
+bool model_uses_msg_mma(const ModelW& m) { return edge_mma_supported(m.F, m.K) && m.tc_message_variant == 5; }
+
+int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T, bool msg_mma) {
   if (b >= BB_S0 && b < BB_S0 + T + 1) return F;
   switch (b) {
     case BB_A1: case BB_A2: case BB_GH2: case BB_GH1: return F;
     case BB_VM: case BB_GA: case BB_GP3: return 3 * F;
     case BB_Z: return 2 * F;
     case BB_GUV: return 6 * F;
+    case BB_PHIH: return msg_mma ? 5 * F : 0;
     default: return 0;
   }
 }
@@ -1023,6 +1061,8 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   // applies to the CUDA-core edge kernels only.
   const bool use_tc = edge_tc_supported(F, m.K);
   const bool use_tc_bwd = use_tc && m.tc_adjoint;
+  const bool msg_mma = model_uses_msg_mma(m);
+  __half* PHIh = msg_mma ? reinterpret_cast<__half*>(Bb[BB_PHIH]) : nullptr;
   const bool g4 = model_uses_g4(m, CTD_PREC_BF16);
   if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], Bb[BB_S0]); }
   for (int t = 0; t < T; ++t) {
@@ -1032,12 +1072,14 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     float *T1 = B[B_T1], *T2 = B[B_T2];
     bad |= gemm_bf16<1>(st, n, F, F, Bb[BB_S0 + t], F, L.W1b, L.b1, nullptr, 0, H1, F, Bb[BB_A1], F, status);
     // phi = W2 silu(.) + b2, packed into PHI by the GEMM epilogue
-    bad |= gemm_bf16<4>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, V, 3 * F, PHI, 6 * F, nullptr, 0, status);
+    bad |= gemm_bf16<4>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, V, 3 * F, PHI, 6 * F, nullptr, 0, status, PHIh);
     float* wst = (wstore && need_grad && !use_tc) ? wstore + t * wstore_layer_floats : nullptr;
 #define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_FWD);
-      if (use_tc) {
+      if (msg_mma) {
+        bad |= edge_fwd_mma(st, m, t, n, arow, acol, ar, PHIh, S, V, SM, VM, Bb[BB_VM], status);
+      } else if (use_tc) {
         bad |= edge_fwd_tc(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], status, aend);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_FWD)

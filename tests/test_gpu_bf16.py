@@ -84,14 +84,26 @@ def test_bf16_rejects_unsupported_width():
         eng.Potential(32, T=1, n_species=1, precision="bf16")
 
 
-@pytest.mark.parametrize("message", [1, 2, 3, 4])
+def _sparse_system():
+    """A 30 A cubic cell with a dense water cluster (rows of 40-70 edges: several 16-edge steps)
+    and three isolated atoms (rows without edges)."""
+    w = syn.water_box(40, seed=6)
+    x = np.concatenate([w.positions, [[25.0, 25.0, 25.0], [25.0, 12.0, 25.0], [12.0, 25.0, 25.0]]])
+    z = np.concatenate([w.species, [0, 1, 0]]).astype(np.int32)
+    m = np.concatenate([w.masses, [16.0, 1.0, 16.0]])
+    return syn.System(x, z, m, np.eye(3) * 30.0, name="sparse")
+
+
+@pytest.mark.parametrize("message", [1, 2, 3, 4, 5])
 def test_bf16_message_variants(orc, message):
-    """Message kernel with register gathers (1) or bulk-copy gathers and the folded basis (2),
-    on the fcc sub-cell, a small water cell and a 4-species mixture with filter biases."""
+    """Message kernel with register gathers (1), bulk-copy gathers and the folded basis (2), the
+    split basis (3), chunked rows (4), or the contraction over each receiver's edges on the
+    tensor cores (5), on the fcc sub-cell, a small water cell, a 4-species mixture with filter
+    biases, and a sparse cell with isolated atoms."""
     from paper_2506_04055_gb300 import _lib
     eng = engine()
     cases = ((syn.fcc(10, 10, 10, jitter=0.05, seed=0), 1, 0.1), (syn.water_box(21, seed=2), 2, 0.1),
-             (syn.mixture(n_chain=30, n_water=150, seed=1), 4, 0.2))
+             (syn.mixture(n_chain=30, n_water=150, seed=1), 4, 0.2), (_sparse_system(), 2, 0.1))
     for sy, S, bias in cases:
         vals, blob = model(128, 2, S, seed=5, bias=bias)
         with eng.Potential(128, T=2, n_species=S, precision="bf16", params=blob) as pot:
