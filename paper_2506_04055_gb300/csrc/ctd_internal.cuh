@@ -140,9 +140,12 @@ void gemm_f32(cudaStream_t st, int epi, int64_t M, int N, int K, const float* A,
               const float* bias, const float* aux, int ldaux, float* out, int ldo, float* out2, int ldo2);
 
 // ---------------------------------------------------------------- small device helpers
-__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + __expf(-x)); }
+// SiLU and its derivative for FP32 results.  expf (not __expf): the fast exponential's error
+// grows with |x| and is the same for the same input, so in a crystal, where every atom sees the
+// same activations, it would add up coherently over the atoms' energies.
+__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + expf(-x)); }
 __device__ __forceinline__ float dsilu_f(float x) {
-  float s = 1.0f / (1.0f + __expf(-x));
+  float s = 1.0f / (1.0f + expf(-x));
   return s * (1.0f + x * (1.0f - s));
 }
 // Approximate-division forms for epilogues whose result is rounded to BF16 (relative error of

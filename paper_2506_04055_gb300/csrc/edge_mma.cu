@@ -11,16 +11,17 @@
 //   s_i[c] += sum_k Wf'_s[c][k] D_s[c][k],  v_i,a[c] += sum_k Wf'_vv[c][k] D_psi_a[c][k]
 //                                                     + sum_k Wf'_vs[c][k] D_vs,a[c][k].
 // The first line is a dense contraction over the row's edges, run on the tensor cores: A is the
-// senders' message rows (FP16, gathered by TMA tile::gather4 straight into a 128B-swizzled
-// MN-major tile: M = 128 channels, K = 16 edges per step), B the per-edge basis (FP16, MN-major,
-// N = 32 or 96), D accumulates in TMEM over the row's K-steps.  The second line runs per
+// senders' message rows (FP16, gathered by per-lane 16-byte asynchronous copies straight into a
+// 128B-swizzled MN-major tile: M = 128 channels, K = 16 edges per step), B the per-edge basis
+// (FP16, MN-major, N = 32 or 96), D accumulates in TMEM over the row's K-steps.  The second line runs per
 // receiver on CUDA cores with the FP32 filter weights.  Both are exact rearrangements of the
 // sum; the rounding is that of the FP16 operands (phi to 2^-11 relative, the basis likewise)
 // with FP32 accumulation, and the filter weights stay FP32.
 //
 // CTA (one per SM, persistent over block-cyclic chunks of receiver rows):
 //   warps 0..2  producers: per 16-edge unit of a row, the basis tiles and the gathers (ring of
-//               kUnits units in shared memory)
+//               kUnits units in shared memory); a unit is full once lane 0 has arrived after the
+//               basis stores and every lane's copies have landed (cp.async.mbarrier.arrive)
 //   warp 3      TMEM owner and single-thread MMA issue; per unit 5 MMAs (2 in the first layer,
 //               whose psi channels are zero), accumulated into the row's TMEM buffer
 //   warps 4..11 two epilogue warpgroups (thread = channel = TMEM lane), taking alternate rows
@@ -42,10 +43,18 @@ constexpr int kBPlainOff = kNBlk * kABlockBytes;     // basis b_k: 16 edges x 32
 constexpr int kBUOff = kBPlainOff + kKS * 32 * 2;    // u_a b_k: 16 edges x 96 columns FP16
 constexpr int kUnitBytes = kBUOff + kKS * 96 * 2;    // 24576
 constexpr int kUnits = 9;
-constexpr int kNProd = 3;
-constexpr int kMmaWarp = 3;
-constexpr int kEpiWarp0 = 4;
-constexpr int kThreads_ = 32 * 12;
+constexpr int kNProd = 6;                            // producer warps
+constexpr int kEpiWG = 1;                            // epilogue warpgroups (rows alternate between them)
+constexpr int kNMma = 2;                             // MMA-issuing warps (rows alternate between them)
+constexpr bool kTmaGather = true;                    // gathers by TMA tile::gather4 (else per-lane cp.async)
+constexpr int kMmaWarp = kNProd;
+constexpr int kEpiWarp0 = kNProd + kNMma;
+constexpr int kThreads_ = 32 * (kNProd + kNMma + 4 * kEpiWG);
+// A producer takes every kNProd-th unit and waits for the ring slot's previous unit (kUnits
+// back) to be consumed.  Its own previous unit (kNProd back) was admitted only after the unit
+// kUnits before that one was consumed, and the MMA consumes in order, so with kNProd <= kUnits
+// no producer can run a whole ring ahead, which would alias the slot barriers' phase parity.
+static_assert(kNProd <= kUnits, "more producer warps than ring units breaks the slot barrier protocol");
 constexpr int kBufCols = 256;                        // TMEM columns per row buffer (224 used)
 constexpr uint32_t kColS = 0, kColPsi = 32, kColVs = 128;
 
@@ -73,6 +82,15 @@ __device__ __forceinline__ uint32_t b_off(int n, int k, int N) {
   return (uint32_t)((n >> 3) * 128 + (k & 7) * 16 + (k >> 3) * 128 * (N / 8));
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only), and the arrival on an mbarrier once all
+// of this thread's earlier copies have landed (counted in the barrier's expected arrivals).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(umma::smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void gather4(uint32_t dst, const CUtensorMap* map, int col, int r0, int r1, int r2, int r3,
                                         uint32_t bar) {
   asm volatile(
@@ -93,6 +111,7 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
 }
 
 struct MsgArgs {
+  const __half* __restrict__ PHIh;   // [n][5F] FP16 message rows
   int64_t n;
   int64_t chunk_rows;
   int K;
@@ -111,22 +130,58 @@ struct MsgArgs {
   int* status;
 };
 
-// The rows of this CTA, in order: block-cyclic chunks of chunk_rows rows.
-struct RowIter {
-  int64_t chunk, r, r1, n, cr;
-  __device__ void begin(const MsgArgs& a) {
-    n = a.n;
-    cr = a.chunk_rows;
-    chunk = blockIdx.x;
-    r = chunk * cr;
-    r1 = r + cr < n ? r + cr : n;
+// The rows of this CTA, in order: block-cyclic chunks of chunk_rows (<= 31) rows.  A warp walks
+// them together: lane l holds the row offset arow[r0 + l] of the current chunk (one load per
+// chunk), and a row's edge range comes from two shuffles.
+struct RowGen {
+  int32_t chunk, r0, nrows, off, k, e0, e1, n, cr;
+  bool valid;
+  __device__ void load(const int32_t* __restrict__ arow, int lane) {
+    r0 = chunk * cr;
+    nrows = n - r0 < cr ? n - r0 : cr;
+    off = lane <= nrows ? arow[r0 + lane] : 0;
+    k = 0;
+    e0 = __shfl_sync(0xffffffffu, off, 0);
+    e1 = __shfl_sync(0xffffffffu, off, 1);
   }
-  __device__ bool valid() const { return r < n; }
-  __device__ void next() {
-    if (++r >= r1) {
+  __device__ void begin(const MsgArgs& a, int lane) {
+    n = (int32_t)a.n;
+    cr = (int32_t)a.chunk_rows;
+    chunk = blockIdx.x;
+    valid = chunk * cr < n;
+    if (valid) load(a.arow, lane);
+  }
+  __device__ void next(const int32_t* __restrict__ arow, int lane) {
+    if (++k >= nrows) {
       chunk += gridDim.x;
-      r = chunk * cr;
-      r1 = r + cr < n ? r + cr : n;
+      valid = chunk * cr < n;
+      if (valid) load(arow, lane);
+    } else {
+      e0 = __shfl_sync(0xffffffffu, off, k);
+      e1 = __shfl_sync(0xffffffffu, off, k + 1);
+    }
+  }
+  __device__ int32_t row() const { return r0 + k; }
+};
+
+// The 16-edge units of this CTA in order (rows without edges have none).
+struct UnitCursor {
+  RowGen rg;
+  int32_t ub;
+  __device__ void skip_empty(const int32_t* __restrict__ arow, int lane) {
+    while (rg.valid && rg.e0 == rg.e1) rg.next(arow, lane);
+    ub = rg.e0;
+  }
+  __device__ void begin(const MsgArgs& a, int lane) {
+    rg.begin(a, lane);
+    skip_empty(a.arow, lane);
+  }
+  __device__ bool valid() const { return rg.valid; }
+  __device__ void advance(const int32_t* __restrict__ arow, int lane) {
+    ub += kKS;
+    if (ub >= rg.e1) {
+      rg.next(arow, lane);
+      skip_empty(arow, lane);
     }
   }
 };
@@ -148,7 +203,8 @@ __global__ void __launch_bounds__(kThreads_, 1) k_edge_msg_mma(const __grid_cons
     reinterpret_cast<uint4*>(ring)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (threadIdx.x == 0) {
     for (int u = 0; u < kUnits; ++u) {
-      umma::mbar_init(&full[u], 1);
+      // TMA: lane 0's arrival with the byte count; copies: lane 0 after the basis, every lane's copies
+      umma::mbar_init(&full[u], kTmaGather ? 1 : 1 + 32);
       umma::mbar_init(&freeb[u], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -167,155 +223,229 @@ __global__ void __launch_bounds__(kThreads_, 1) k_edge_msg_mma(const __grid_cons
 
   if (warp < kNProd) {
     // ---------------------------------------------------------------- producers
+    // Warp w takes units w, w + kNProd, ...; the next unit's edge data is loaded while the
+    // current one is processed.
     const float sig = p.rc / (float)(p.K - 1), inv2s2 = 1.0f / (2.0f * sig * sig), inv_rc = 1.0f / p.rc;
-    const int slot = lane & 15, h = lane >> 4;   // h = 0: basis columns 0..15, h = 1: 16..31 and the gathers
-    int64_t g = 0;                               // units of this CTA so far (all producers)
-    int64_t last_g = -1;                         // this warp's last unit
-    RowIter it;
-    for (it.begin(p); ok && it.valid(); it.next()) {
-      const int e0 = p.arow[it.r], e1 = p.arow[it.r + 1];
-      for (int ub = e0; ub < e1; ub += kKS, ++g) {
-        if ((int)(g % kNProd) != warp) continue;
-        const int u = (int)(g % kUnits);
-        // warp-uniform bounded wait (a lane timing out alone would leave the warp divergent)
-        if (g >= kUnits && !__all_sync(0xffffffffu, umma::mbar_wait(&freeb[u], (uint32_t)(((g / kUnits) - 1) & 1)))) {
-          ok = false;
-          break;
-        }
-        unsigned char* unit = ring + (size_t)u * kUnitBytes;
-        const int e = ub + slot;
-        const bool live = e < e1;
-        float4 r = make_float4(1.f, 0.f, 0.f, 1.f);
-        int j = p.acol[ub];   // padded slots gather a live sender's row (finite, times a zero basis)
-        if (live) {
-          r = p.ar[e];
-          j = p.acol[e];
-        }
-        const float d = r.w, id = 1.0f / d;
-        const float fc = live ? 0.5f * (cospif(d * inv_rc) + 1.0f) : 0.0f;
-        const float ux = r.x * id, uy = r.y * id, uz = r.z * id;
-        float b[16];
+    const int slot = lane & 15, h = lane >> 4;   // h = 0: basis columns 0..15, h = 1: 16..31
+    UnitCursor cur;
+    cur.begin(p, lane);
+    for (int s = 0; s < warp && cur.valid(); ++s) cur.advance(p.arow, lane);
+    int64_t g = warp;        // this unit's index in the CTA's sequence
+    int64_t last_g = -1;     // this warp's last unit
+    auto fetch = [&](const UnitCursor& c, float4& r, int& j) {
+      const int e = c.ub + slot;
+      r = make_float4(1.f, 0.f, 0.f, 1.f);
+      j = p.acol[c.ub];   // padded slots gather a live sender's row (finite, times a zero basis)
+      if (e < c.rg.e1) {
+        r = p.ar[e];
+        j = p.acol[e];
+      }
+    };
+    float4 r_cur;
+    int j_cur = 0;
+    if (cur.valid()) fetch(cur, r_cur, j_cur);
+    while (ok && cur.valid()) {
+      UnitCursor nxt = cur;
+      for (int s = 0; s < kNProd && nxt.valid(); ++s) nxt.advance(p.arow, lane);
+      float4 r_nxt;
+      int j_nxt = 0;
+      if (nxt.valid()) fetch(nxt, r_nxt, j_nxt);
+      const int u = (int)(g % kUnits);
+      // warp-uniform bounded wait (a lane timing out alone would leave the warp divergent)
+      if (g >= kUnits && !__all_sync(0xffffffffu, umma::mbar_wait(&freeb[u], (uint32_t)(((g / kUnits) - 1) & 1)))) {
+        ok = false;
+        break;
+      }
+      unsigned char* unit = ring + (size_t)u * kUnitBytes;
+      const bool live = cur.ub + slot < cur.rg.e1;
+      const float4 r = r_cur;
+      const int j = j_cur;
+      const float d = r.w, id = 1.0f / d;
+      const float fc = live ? 0.5f * (cospif(d * inv_rc) + 1.0f) : 0.0f;
+      const float ux = r.x * id, uy = r.y * id, uz = r.z * id;
+      // Basis columns k = 0 .. 23 of the edge (k < K Gaussians, k = K the cutoff alone, zero above;
+      // columns 24 .. 31 stay zero from the ring's initialisation).  The lane pair splits them:
+      // h = 0 evaluates k = 0 .. 11 and h = 1 k = 12 .. 23, so each evaluates at most 12
+      // exponentials; 8-column chunk 1 (k = 8 .. 15) is assembled by h = 0 from both halves.
+      float b[12];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int k = 16 * h + q;
-          const float tq = d - (float)k * sig;
-          b[q] = k < K ? fc * __expf(-tq * tq * inv2s2) : (k == K ? fc : 0.0f);
+      for (int q = 0; q < 12; ++q) {
+        const int k = 12 * h + q;
+        const float tq = d - (float)k * sig;
+        b[q] = k < K ? fc * __expf(-tq * tq * inv2s2) : (k == K ? fc : 0.0f);
+      }
+      float o[4];   // the partner's k = 12 .. 15 (h = 0 needs them for chunk 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) o[q] = __shfl_xor_sync(0xffffffffu, b[q], 16);
+      float ch[2][8];   // this lane's chunks: h = 0: k 0..7 and 8..15; h = 1: k 16..23
+      const int nch = h == 0 ? 2 : 1;
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        ch[0][x] = h == 0 ? b[x] : b[4 + x];
+        ch[1][x] = x < 4 ? b[8 + x] : o[x - 4];
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (c >= nch) break;
+        const int col = h == 0 ? 8 * c : 16;
+        *reinterpret_cast<uint4*>(unit + kBPlainOff + b_off(col, slot, 32)) = pack8(ch[c]);
+        float w[8];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float ua = a == 0 ? ux : (a == 1 ? uy : uz);
+#pragma unroll
+          for (int x = 0; x < 8; ++x) w[x] = ua * ch[c][x];
+          *reinterpret_cast<uint4*>(unit + kBUOff + b_off(32 * a + col, slot, 96)) = pack8(w);
         }
-        // this lane's two 8-column chunks of the plain basis and of each u_a-weighted copy
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          *reinterpret_cast<uint4*>(unit + kBPlainOff + b_off(16 * h + 8 * c, slot, 32)) = pack8(b + 8 * c);
-          float w[8];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const float ua = a == 0 ? ux : (a == 1 ? uy : uz);
-#pragma unroll
-            for (int x = 0; x < 8; ++x) w[x] = ua * b[8 * c + x];
-            *reinterpret_cast<uint4*>(unit + kBUOff + b_off(32 * a + 16 * h + 8 * c, slot, 96)) = pack8(w);
-          }
-        }
-        const int nlive = e1 - ub < kKS ? e1 - ub : kKS;
+      }
+      const int nlive = cur.rg.e1 - cur.ub < kKS ? cur.rg.e1 - cur.ub : kKS;
+      umma::fence_proxy_async_smem();
+      __syncwarp();
+      if (kTmaGather) {
+        // four rows x 128 B per gather4 (channel half hh of block blk of an edge group), spread
+        // over the lanes; the barrier completes when lane 0 has arrived and the bytes landed
+        constexpr int nbh = (V0 ? 2 : kNBlk) * 2;
         const int ngroups = (nlive + 3) >> 2;
-        constexpr int nblk = V0 ? 2 : kNBlk;
-        umma::fence_proxy_async_smem();
+        if (lane == 0) umma::mbar_expect_tx(&full[u], (uint32_t)(ngroups * nbh * 4 * 128));
         __syncwarp();
-        if (lane == 0) umma::mbar_expect_tx(&full[u], (uint32_t)(ngroups * nblk * 2 * 4 * 128));
-        __syncwarp();
-        // gathers: lane 16 + q serves edge group q (slots 4q .. 4q + 3)
-        const int jq0 = __shfl_sync(0xffffffffu, j, (4 * (lane & 3)) & 15);
-        const int jq1 = __shfl_sync(0xffffffffu, j, (4 * (lane & 3) + 1) & 15);
-        const int jq2 = __shfl_sync(0xffffffffu, j, (4 * (lane & 3) + 2) & 15);
-        const int jq3 = __shfl_sync(0xffffffffu, j, (4 * (lane & 3) + 3) & 15);
-        if (h == 1 && slot < ngroups) {
-          const int q = slot;
-          const uint32_t dst0 = umma::smem_u32(unit) + (uint32_t)((q >> 1) * 2048 + (q & 1) * 512);
 #pragma unroll
-          for (int bi = 0; bi < nblk; ++bi) {
+        for (int rep = 0; rep < 2; ++rep) {
+          const int ci = lane + 32 * rep;
+          const int q = ci % ngroups, bh = ci / ngroups;
+          const int j0 = __shfl_sync(0xffffffffu, j, 4 * q), j1 = __shfl_sync(0xffffffffu, j, 4 * q + 1);
+          const int j2 = __shfl_sync(0xffffffffu, j, 4 * q + 2), j3 = __shfl_sync(0xffffffffu, j, 4 * q + 3);
+          if (bh < nbh) {
+            const int bi = bh >> 1, hh = bh & 1;
             const int blk = V0 ? (bi == 0 ? 0 : 4) : bi;
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh)
-              gather4(dst0 + (uint32_t)(blk * kABlockBytes + hh * 1024), &tmPhi, blk * kF + hh * 64, jq0, jq1, jq2, jq3,
-                      umma::smem_u32(&full[u]));
+            const uint32_t dst = umma::smem_u32(unit) +
+                                 (uint32_t)(blk * kABlockBytes + (q >> 1) * 2048 + hh * 1024 + (q & 1) * 512);
+            gather4(dst, &tmPhi, blk * kF + hh * 64, j0, j1, j2, j3, umma::smem_u32(&full[u]));
           }
         }
         last_g = g;
+        g += kNProd;
+        cur = nxt;
+        r_cur = r_nxt;
+        j_cur = j_nxt;
+        continue;
       }
-    }
-    // every gather this warp issued has landed before the CTA may exit (normally the MMA thread
-    // has waited for all of them; after a timeout it may not have): units whose ring slot no
-    // later unit reused, the others completed before their slot was refilled
-    if (lane == 0)
-      for (int64_t q = last_g; q >= 0 && q >= g - kUnits; q -= kNProd)
-        umma::mbar_wait(&full[q % kUnits], (uint32_t)((q / kUnits) & 1), 200000000ull);
-  } else if (warp == kMmaWarp) {
-    // ---------------------------------------------------------------- MMA issue
-    if (lane == 0) {
-      const uint32_t id32 = idesc_f16_mn(32), id96 = idesc_f16_mn(96);
-      int64_t g = 0, rows = 0;
-      uint64_t* last_bar = nullptr;   // the barrier of the last commit, and its phase parity
-      uint32_t last_par = 0;
-      RowIter it;
-      for (it.begin(p); ok && it.valid(); it.next()) {
-        const int e0 = p.arow[it.r], e1 = p.arow[it.r + 1];
-        if (e1 == e0) continue;
-        const int b = (int)(rows & 1);
-        if (rows >= 2 && !umma::mbar_wait(&tempty[b], (uint32_t)(((rows >> 1) - 1) & 1))) { ok = false; break; }
-        const uint32_t d0 = tmem + (uint32_t)(b * kBufCols);
-        for (int ub = e0; ub < e1; ub += kKS, ++g) {
-          const int u = (int)(g % kUnits);
-          if (!umma::mbar_wait(&full[u], (uint32_t)((g / kUnits) & 1))) { ok = false; break; }
-          umma::fence_after();
-          const uint32_t base = umma::smem_u32(ring + (size_t)u * kUnitBytes);
-          const uint64_t bp = b_desc(base + kBPlainOff, 32), bu = b_desc(base + kBUOff, 96);
-          const uint32_t acc = ub > e0 ? 1u : 0u;
-          umma::mma_bf16(d0 + kColS, a_desc(base), bp, id32, acc);
-          if (!V0)
-            for (int a = 0; a < 3; ++a)
-              umma::mma_bf16(d0 + kColPsi + 32 * a, a_desc(base + (uint32_t)((1 + a) * kABlockBytes)), bp, id32, acc);
-          umma::mma_bf16(d0 + kColVs, a_desc(base + 4 * kABlockBytes), bu, id96, acc);
-          umma::mma_commit(&freeb[u]);
-          last_bar = &freeb[u];
-          last_par = (uint32_t)((g / kUnits) & 1);
+      if (lane == 0) umma::mbar_arrive(&full[u]);
+      // gathers: the live slots' message rows, 16 bytes per copy; item = (slot, block, 16-byte
+      // chunk of the 256-byte block), lanes take consecutive chunks of a row (coalesced reads),
+      // each written to its 128B-swizzled place (chunk c of edge row k0 sits at chunk c ^ k0)
+      constexpr int nbk = V0 ? 2 : kNBlk;   // gathered blocks (the first layer's psi are zero)
+      const uint32_t ubase = umma::smem_u32(unit);
+      const int items = nlive * nbk * 16;
+      for (int base = 0; base < items; base += 32) {   // warp-uniform trip count (shuffles below)
+        const int it = base + lane;
+        const int sl = it / (nbk * 16), rem = it - sl * (nbk * 16), bi = rem >> 4, q = rem & 15;
+        const int js = __shfl_sync(0xffffffffu, j, sl & 15);
+        if (it < items) {
+          const int blk = V0 ? (bi == 0 ? 0 : 4) : bi;
+          const int k0 = sl & 7, hh = q >> 3, cc = q & 7;
+          const uint32_t dst = ubase + (uint32_t)(blk * kABlockBytes + (sl >> 3) * 2048 + hh * 1024 + k0 * 128 +
+                                                  ((cc ^ k0) << 4));
+          cp_async16(dst, p.PHIh + (size_t)js * (kNBlk * kF) + blk * kF + q * 8);
         }
-        if (!ok) break;
-        umma::mma_commit(&tfull[b]);
-        last_bar = &tfull[b];
-        last_par = (uint32_t)((rows >> 1) & 1);
-        ++rows;
       }
-      // every MMA issued has completed before TMEM is released (commits complete in order)
-      if (last_bar) umma::mbar_wait(last_bar, last_par, 200000000ull);
+      cp_async_arrive(&full[u]);
+      last_g = g;
+      g += kNProd;
+      cur = nxt;
+      r_cur = r_nxt;
+      j_cur = j_nxt;
     }
+    // the gathers of this warp's last unit have landed before the CTA may exit (normally the MMA
+    // thread has waited for all of them; after a timeout it may not have).  No later unit reuses
+    // that ring slot (the CTA's last unit is at most kNProd - 1 further); earlier units were
+    // issued at least one full unit earlier.
+    if (lane == 0 && last_g >= 0)
+      umma::mbar_wait(&full[last_g % kUnits], (uint32_t)((last_g / kUnits) & 1), 200000000ull);
+  } else if (warp < kMmaWarp + kNMma) {
+    // ---------------------------------------------------------------- MMA issue
+    // the warp walks the units together (row offsets by chunk); lane 0 issues.  With two MMA
+    // warps, warp m issues the rows whose TMEM buffer is m (every other row with edges).
+    const int mw = warp - kMmaWarp;
+    const uint32_t id32 = idesc_f16_mn(32), id96 = idesc_f16_mn(96);
+    int64_t g = 0, rows = 0;
+    uint64_t* last_bar = nullptr;   // the barrier of the last commit, and its phase parity
+    uint32_t last_par = 0;
+    UnitCursor cur;
+    for (cur.begin(p, lane); ok && cur.valid(); cur.advance(p.arow, lane), ++g) {
+      const bool first = cur.ub == cur.rg.e0, last = cur.ub + kKS >= cur.rg.e1;
+      const int b = (int)(rows & 1);
+      if (kNMma == 2 && b != mw) {   // the other MMA warp's row
+        if (last) ++rows;
+        continue;
+      }
+      if (first && rows >= 2 &&
+          !__all_sync(0xffffffffu, umma::mbar_wait(&tempty[b], (uint32_t)(((rows >> 1) - 1) & 1)))) {
+        ok = false;
+        break;
+      }
+      const int u = (int)(g % kUnits);
+      if (!__all_sync(0xffffffffu, umma::mbar_wait(&full[u], (uint32_t)((g / kUnits) & 1)))) {
+        ok = false;
+        break;
+      }
+      // the unit's copies and basis stores (generic proxy) before the MMAs read it (async proxy)
+      umma::fence_proxy_async_smem();
+      umma::fence_after();
+      if (lane == 0) {
+        const uint32_t d0 = tmem + (uint32_t)(b * kBufCols);
+        const uint32_t base = umma::smem_u32(ring + (size_t)u * kUnitBytes);
+        const uint64_t bp = b_desc(base + kBPlainOff, 32), bu = b_desc(base + kBUOff, 96);
+        const uint32_t acc = first ? 0u : 1u;
+        umma::mma_bf16(d0 + kColS, a_desc(base), bp, id32, acc);
+        if (!V0)
+          for (int a = 0; a < 3; ++a)
+            umma::mma_bf16(d0 + kColPsi + 32 * a, a_desc(base + (uint32_t)((1 + a) * kABlockBytes)), bp, id32, acc);
+        umma::mma_bf16(d0 + kColVs, a_desc(base + 4 * kABlockBytes), bu, id96, acc);
+        umma::mma_commit(&freeb[u]);
+        if (last) umma::mma_commit(&tfull[b]);
+      }
+      __syncwarp();
+      last_bar = last ? &tfull[b] : &freeb[u];
+      last_par = last ? (uint32_t)((rows >> 1) & 1) : (uint32_t)((g / kUnits) & 1);
+      if (last) ++rows;
+    }
+    // every MMA issued has completed before TMEM is released (commits complete in order)
+    if (lane == 0 && last_bar) umma::mbar_wait(last_bar, last_par, 200000000ull);
   } else {
     // ---------------------------------------------------------------- epilogue
     const int wg = (warp - kEpiWarp0) >> 2, q4 = warp & 3, c = q4 * 32 + lane;
-    // filter weights of channel c with the bias in column K: in registers for the usual basis
-    // size (KC = 20), read through L1 per row otherwise
+    // filter weights of channel c with the bias in column K.  For the usual basis size (KC = 20)
+    // the vs row stays in registers and the s and vv rows are reloaded (L1) before each use, so
+    // that two rows of weights are live at a time; for other sizes every weight is read through
+    // L1 where it is used.
     constexpr int NW = KC > 0 ? KC + 1 : 32;
     constexpr int NR = KC > 0 ? NW : 1;
     float ws[NR], wvv[NR], wvs[NR];
     auto wf = [&](int blk, int k) -> float {
       return k < K ? __ldg(p.Wf + (size_t)(blk * kF + c) * p.KP + k) : (k == K ? __ldg(p.bf + blk * kF + c) : 0.0f);
     };
+    // a load the compiler does not hoist out of the row loop
+    auto wf_row = [&](int blk, int k) -> float {
+      const float* q = k < K ? p.Wf + (size_t)(blk * kF + c) * p.KP + k : p.bf + blk * kF + c;
+      float v;
+      asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(q));
+      return k <= K ? v : 0.0f;
+    };
     if (KC > 0) {
 #pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        ws[k] = wf(0, k);
-        wvv[k] = wf(1, k);
-        wvs[k] = wf(2, k);
-      }
+      for (int k = 0; k < NR; ++k) wvs[k] = wf(2, k);
     }
     auto W = [&](const float (&w)[NR], int blk, int k) -> float { return KC > 0 ? w[k < NR ? k : 0] : wf(blk, k); };
     const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16);
     int64_t rows = 0;
-    RowIter it;
-    for (it.begin(p); it.valid(); it.next()) {
-      const int64_t i = it.r;
-      const int e0 = p.arow[i], e1 = p.arow[i + 1];
+    RowGen it;
+    for (it.begin(p, lane); it.valid; it.next(p.arow, lane)) {
+      const int64_t i = it.row();
+      const int e0 = it.e0, e1 = it.e1;
       if (e1 > e0) {
         const int b = (int)(rows & 1);
         const int64_t q = rows++;
-        if (b != wg) continue;
+        if (kEpiWG == 2 && b != wg) continue;
         if (!ok) continue;
         const float s_in = p.S[i * kF + c];
         const float v_in0 = p.V[i * 3 * kF + c], v_in1 = p.V[i * 3 * kF + kF + c], v_in2 = p.V[i * 3 * kF + 2 * kF + c];
@@ -328,25 +458,42 @@ __global__ void __launch_bounds__(kThreads_, 1) k_edge_msg_mma(const __grid_cons
         float D[32];
         float ds = 0.f, dv[3];
         // each sum is finished before the next TMEM load (the empty asm consumes it), so that one
-        // 32-column tile is live at a time
-        umma::tmem_ld32(t0 + kColS, D);
+        // group of accumulator columns is live at a time; with KC = 20 the 21 used columns of a
+        // group are read as 16 + 8
+        auto group = [&](uint32_t col, const float (&w)[NR], int blk, float acc) -> float {
+          if (KC > 0 && NW <= 24) {
+            float lo[16], hi[8];
+            umma::tmem_ld16(col, lo);
 #pragma unroll
-        for (int k = 0; k < NW; ++k) ds = fmaf(W(ws, 0, k), D[k], ds);
-        asm volatile("" ::"f"(ds));
+            for (int k = 0; k < 16; ++k) acc = fmaf(W(w, blk, k), lo[k], acc);
+            asm volatile("" ::"f"(acc));
+            umma::tmem_ld8(col + 16, hi);
+#pragma unroll
+            for (int k = 16; k < NW; ++k) acc = fmaf(W(w, blk, k), hi[k - 16], acc);
+          } else {
+            umma::tmem_ld32(col, D);
+#pragma unroll
+            for (int k = 0; k < NW; ++k) acc = fmaf(W(w, blk, k), D[k], acc);
+          }
+          asm volatile("" ::"f"(acc));
+          return acc;
+        };
+        if (KC > 0) {
+#pragma unroll
+          for (int k = 0; k < NR; ++k) ws[k] = wf_row(0, k);
+        }
+        ds = group(t0 + kColS, ws, 0, 0.f);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           float acc = 0.f;
           if (!V0) {
-            umma::tmem_ld32(t0 + kColPsi + 32 * a, D);
+            if (KC > 0) {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) acc = fmaf(W(wvv, 1, k), D[k], acc);
-            asm volatile("" ::"f"(acc));
+              for (int k = 0; k < NR; ++k) wvv[k] = wf_row(1, k);
+            }
+            acc = group(t0 + kColPsi + 32 * a, wvv, 1, acc);
           }
-          umma::tmem_ld32(t0 + kColVs + 32 * a, D);
-#pragma unroll
-          for (int k = 0; k < NW; ++k) acc = fmaf(W(wvs, 2, k), D[k], acc);
-          asm volatile("" ::"f"(acc));
-          dv[a] = acc;
+          dv[a] = group(t0 + kColVs + 32 * a, wvs, 2, acc);
         }
         umma::fence_before();
         __syncwarp();
@@ -423,12 +570,14 @@ int edge_fwd_mma(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32
                  __nv_bfloat16* VMb, int* status) {
   if (n == 0) return 0;
   if (!edge_mma_supported(m.F, m.K) || (reinterpret_cast<uintptr_t>(PHIh) & 15)) return -1;
-  CUtensorMap tm;
-  if (!make_tmap_rows_f16(&tm, PHIh, n, 5 * kF)) return -2;
+  CUtensorMap tm{};
+  if (kTmaGather && !make_tmap_rows_f16(&tm, PHIh, n, 5 * kF)) return -2;
   MsgArgs a{};
+  a.PHIh = PHIh;
   a.n = n; a.K = m.K; a.rc = m.rc; a.arow = arow; a.acol = acol; a.ar = ar; a.S = S; a.V = V;
   a.Wf = m.L[t].Wf; a.bf = m.L[t].bf; a.KP = m.KP; a.SM = SM; a.VM = VM; a.VMb = VMb; a.status = status;
-  a.chunk_rows = m.edge_chunk_rows > 0 ? m.edge_chunk_rows : 32;
+  // rows per block-cyclic chunk: at most 31 (a warp holds a chunk's row offsets, one per lane)
+  a.chunk_rows = m.edge_chunk_rows > 0 && m.edge_chunk_rows < 31 ? m.edge_chunk_rows : 16;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

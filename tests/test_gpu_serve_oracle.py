@@ -9,11 +9,7 @@ virial with the oracle's virial at the replica's final positions.
 Tolerances follow from the FP32 force and energy bars (relative force RMSE 1e-5, |dE|/N 1e-6 of
 the RMS per-atom energy): with |F| ~ 1 eV/A and hydrogen masses, a 1e-5 relative force error
 moves a velocity by < 1e-6 A/fs and a position by < 1e-5 A over 15 steps of 0.5 fs; the
-potential energy along the trajectory is held to the energy bar.  The oracle evaluates the
-weights the FP32 engine holds (the blob's FP64 values rounded to FP32): the test measures the
-serving path's arithmetic, not the representation of the weights, whose FP32 rounding alone moves
-the energy of a near-perfect crystal coherently by about 1e-6 of its per-atom energy.  The BF16
-replicas (tensor-core path, F = 128) are held to the BF16 force bar through their displacements."""
+potential energy along the trajectory is held to the energy bar.  The BF16 replicas (tensor-core path, F = 128) are held to the BF16 force bar through their displacements."""
 import numpy as np
 import pytest
 
@@ -64,8 +60,7 @@ def _serve(eng, blob, F, items, thermos, precision, late):
 def test_served_fp32_replicas_follow_the_oracle(orc):
     eng = engine()
     F = 64
-    vals64, blob = model(F, T, S, seed=31, bias=0.1)
-    vals = vals64.astype(np.float32).astype(np.float64)   # the weights the FP32 engine evaluates
+    vals, blob = model(F, T, S, seed=31, bias=0.1)
     items = _systems()
     nvt = (500.0, 25.0, 3)
     thermos = [None, nvt, None]
