@@ -50,10 +50,10 @@ def step_bytes_per_atom(n_e, value_bytes):
 
 # FMA-pipe FLOPs per (active edge, feature channel) the edge kernels execute on CUDA cores
 # (reported beside the roofline): FP32 message 6K + 18, FP32 adjoint 12K + 45; with the filter
-# on the tensor pipe (BF16, F = 128) message 21, adjoint 50.
+# on the tensor pipe (BF16, F = 128) the adjoint keeps 50 (the tensor-core message kernel's
+# CUDA-core work is per receiver, counted where it is reported).
 EDGE_FWD_FLOP_PER_EF = 6 * K + 18
 EDGE_BWD_FLOP_PER_EF = 12 * K + 45
-EDGE_FWD_TC_ALU_FLOP_PER_EF = 21
 EDGE_BWD_TC_ALU_FLOP_PER_EF = 50
 FP32_LANES_PER_SM, N_SM = 128, 152
 
@@ -391,8 +391,9 @@ def run_ours(args):
     n_e = ea / sy.n
     if dom in ("edge_bwd", "edge_fwd") and dom_launches:
         launch_s = dom_ms / dom_launches / 1e3
-        tc = head == "bf16" and F == 128 and (dom == "edge_fwd" or args.tc_adjoint != 0)
-        kname = ("k_edge_bwd_tcg" if dom == "edge_bwd" else "k_edge_fwd_tc") if tc else f"k_{dom}"
+        tc = head == "bf16" and F == 128 and ((dom == "edge_fwd" and args.tc_message != 0) or
+                                              (dom == "edge_bwd" and args.tc_adjoint != 0))
+        kname = ("k_edge_bwd_tcg" if dom == "edge_bwd" else "k_edge_msg_mma") if tc else f"k_{dom}"
         flop = ea * edge_flop_per_edge()
         achieved = flop / launch_s / 1e12
         if tc:
@@ -412,11 +413,16 @@ def run_ours(args):
         if traffic:
             roofline["hbm_gbs"] = traffic / launch_s / 1e9
             roofline["hbm_frac"] = traffic / launch_s / 1e9 / peaks.get("hbm_gbs", 6800.0)
-        alu_ef = ((EDGE_BWD_TC_ALU_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_TC_ALU_FLOP_PER_EF) if tc else
-                  (EDGE_BWD_FLOP_PER_EF if dom == "edge_bwd" else EDGE_FWD_FLOP_PER_EF))
+        if tc and dom == "edge_fwd":
+            # the contraction kernel's CUDA-core work is per receiver: the FP32 filter weights
+            # applied to 7 accumulator groups of K + 1 columns, 2 x 7 (K + 1) FLOP per channel
+            alu_flop = sy.n * F * 2 * 7 * (K + 1)
+        else:
+            alu_flop = ea * F * ((EDGE_BWD_TC_ALU_FLOP_PER_EF if tc else EDGE_BWD_FLOP_PER_EF) if dom == "edge_bwd"
+                                 else EDGE_FWD_FLOP_PER_EF)
         fma_peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roofline["fma_pipe"] = {"flop_per_edge_channel": alu_ef, "tflops": ea * F * alu_ef / launch_s / 1e12,
-                                "frac_of_fp32_fma_peak": ea * F * alu_ef / launch_s / 1e12 / fma_peak}
+        roofline["fma_pipe"] = {"flop_per_launch": alu_flop, "tflops": alu_flop / launch_s / 1e12,
+                                "frac_of_fp32_fma_peak": alu_flop / launch_s / 1e12 / fma_peak}
     # the whole step against both roofs (algorithmic FLOPs and bytes per atom-step)
     step_s = s["ms_per_step"] / 1e3
     vb = 2 if head == "bf16" else 4
@@ -935,13 +941,12 @@ def main():
     ap.add_argument("--cells", type=int, default=FCC_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tc-adjoint", type=int, default=None,
-                    help="BF16 edge adjoint: 0 CUDA cores, 1 tcgen05 filter with register gathers, "
-                         "2 tcgen05 filter with bulk-copy gathers (the library's default), 3 as 2 with "
-                         "the folded basis")
+                    help="BF16 edge adjoint: 0 CUDA cores, 1 tcgen05 filter (the library's default), "
+                         "2 tcgen05 filter with the basis as a BF16 hi + lo pair")
     ap.add_argument("--tc-message", type=int, default=None,
-                    help="BF16 message kernel: 1 register gathers (the library's default), 2 bulk-copy gathers")
+                    help="BF16 message step: 0 CUDA cores, 1 tensor-core contraction (the library's default)")
     ap.add_argument("--chunk-rows", type=int, default=None,
-                    help="rows per block-cyclic chunk of the bulk-gathered edge kernels (0: contiguous)")
+                    help="rows per block-cyclic chunk of the tensor-core adjoint (0: contiguous)")
     ap.add_argument("--workload", default="fcc1m",
                     choices=["fcc1m", "water192", "water96k", "mixture90k", "serve", "domains", "nvt_al",
                              "local96k"])

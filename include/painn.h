@@ -48,8 +48,9 @@ extern "C" {
 
 /* ---- precision of the dense contractions ----------------------------------------------- */
 #define CTD_PREC_FP32 0   /* every product in FP32 on CUDA cores                              */
-#define CTD_PREC_BF16 1   /* filter / message / update MLPs in BF16 on tcgen05, FP32 accum;
-                             F must be 64 or 128                                             */
+#define CTD_PREC_BF16 1   /* node MLPs in BF16 on tcgen05 with FP32 accumulation; at F = 128
+                             also the edge message (FP16 rows x basis, FP32 filter weights)
+                             and the adjoint's radial filter; F must be 64 or 128           */
 
 /* ---- flags for ctd_compute ---------------------------------------------------------------- */
 #define CTD_NEED_FORCES 1      /* write forces[n][3]                                          */
@@ -184,26 +185,27 @@ int ctd_md_get_thermostat(ctd_ctx *ctx, double *xi, double *vxi, double *ethermo
 int ctd_md_set_thermostat_state(ctd_ctx *ctx, const double *xi, const double *vxi);
 
 /* ---- options -------------------------------------------------------------------------- */
-/* CTD_OPT_TC_ADJOINT (value 0..4; default 2): on the BF16 path with F = 128, run the edge
- * adjoint with the radial filter on tcgen05 as well (the message kernel always does):
- * 1 = neighbour gradients gathered into registers, 2 = gathered into shared memory by bulk
- * asynchronous copies, 3 = as 2 with the cutoff and bias folded into the tensor-core basis,
- * 4 = as 2 with each basis value entered as a BF16 pair (hi + lo, two MMAs).  0 selects the
- * CUDA-core adjoint. */
+/* CTD_OPT_TC_ADJOINT (value 0..2; default 1): on the BF16 path with F = 128, run the edge
+ * adjoint with the radial filter and its distance derivative on tcgen05 (1), the same with each
+ * basis value entered as a BF16 pair (hi + lo, two MMAs; closer to FP32 at twice the tensor
+ * work) (2), or on CUDA cores (0). */
 #define CTD_OPT_TC_ADJOINT 1
 /* CTD_OPT_EDGE_STORE (value 0 or 1; default 0): the forward message kernel stores, per active
  * edge and layer, the cutoff-scaled radial filter and its distance derivative (6F floats), and
  * the adjoint reads them instead of recomputing basis and filter (the default).  Storage costs
  * T x E x 6F x 4 bytes; it is used only when that fits the HBM budget (if one is set) and 80 %
  * of the device's free memory, and otherwise the call recomputes (ctd_stats.edges_stored says
- * which).  It applies to the CUDA-core edge kernels: the FP32 path and BF16 with F != 128. */
+ * which).  It applies to the CUDA-core edge kernels: the FP32 path, and BF16 with F != 128 or
+ * with both tensor-core edge kernels switched off (CTD_OPT_TC_MESSAGE 0, CTD_OPT_TC_ADJOINT 0). */
 #define CTD_OPT_EDGE_STORE 2
-/* CTD_OPT_TC_MESSAGE (value 1..3; default 1): BF16 path with F = 128, message kernel with the
- * senders' rows gathered into registers (1), into shared memory by bulk asynchronous copies
- * with the filter's cutoff and bias folded into the tensor-core basis (2), or as 1 with each
- * basis value entered as a BF16 pair (hi + lo, two MMAs) (3). */
+/* CTD_OPT_TC_MESSAGE (value 0 or 1; default 1): on the BF16 path with F = 128, compute the
+ * message step as a tensor-core contraction over each receiver's edges (1): the senders' message
+ * rows [phi_s | v_a phi_vv | phi_vs] in FP16 times the per-edge basis f_c rbf_k (with u_a for
+ * the vector term), accumulated in FP32, and the FP32 filter weights applied per receiver
+ * (Wf rbf + bf = sum_k Wf'[c][k] b_k with the bias as column K); or on CUDA cores with the FP32
+ * filter (0). */
 #define CTD_OPT_TC_MESSAGE 3
-/* CTD_OPT_EDGE_CHUNK_ROWS (value >= 0; default 32): the bulk-gathered edge kernels hand out the
+/* CTD_OPT_EDGE_CHUNK_ROWS (value >= 0; default 32): the tensor-core adjoint hands out the
  * sorted rows in chunks of this many rows, block-cyclically over all row streams of the GPU;
  * 0 gives each stream one contiguous range. */
 #define CTD_OPT_EDGE_CHUNK_ROWS 4

@@ -351,7 +351,7 @@ int evaluate(ctd_ctx* c, bool need_grad) {
   float* wst = nullptr;
   const int64_t wlayer = e1 * 6 * (int64_t)F;
   c->last_stored = false;
-  if (c->mw.edge_store && need_grad && T > 0) {
+  if (model_stores_edges(c->mw, c->desc.precision) && need_grad && T > 0) {
     const size_t want = sizeof(float) * (size_t)wlayer * (size_t)T;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
@@ -675,9 +675,9 @@ int ctd_create(ctd_ctx** out, const ctd_model_desc* desc, size_t hbm_budget_byte
   ctd_ctx* c = new ctd_ctx();
   c->desc = *desc;
   c->budget = hbm_budget_bytes;
-  c->mw.tc_adjoint = true;   // BF16 path, F = 128: bulk-gathered tensor-core adjoint
-  c->mw.tc_adjoint_variant = 2;
-  c->mw.tc_message_variant = 1;
+  c->mw.tc_adjoint = true;   // BF16 path, F = 128: tensor-core adjoint and message contraction
+  c->mw.tc_adjoint_split = false;
+  c->mw.tc_message = true;
   c->mw.edge_chunk_rows = 32;
   cudaGetDevice(&c->device);
   if (cuda_stream) {
@@ -786,17 +786,17 @@ int ctd_set_option(ctd_ctx* c, int32_t option, int64_t value) {
       c->mw.edge_chunk_rows = value;
       return CTD_OK;
     case CTD_OPT_TC_MESSAGE:
-      if (value < 1 || value > 5) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_MESSAGE takes 1 .. 5");
-      c->mw.tc_message_variant = (int)value;
+      if (value < 0 || value > 1) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_MESSAGE takes 0 or 1");
+      c->mw.tc_message = value != 0;
       return CTD_OK;
     case CTD_OPT_EDGE_STORE:
       if (value < 0 || value > 1) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_EDGE_STORE takes 0 or 1");
       c->mw.edge_store = value != 0;
       return CTD_OK;
     case CTD_OPT_TC_ADJOINT:
-      if (value < 0 || value > 4) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0 .. 4");
+      if (value < 0 || value > 2) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0 .. 2");
       c->mw.tc_adjoint = value != 0;
-      c->mw.tc_adjoint_variant = (int)value;
+      c->mw.tc_adjoint_split = value == 2;
       return CTD_OK;
     default:
       return fail(c, CTD_ERR_INVALID_ARG, "unknown option");

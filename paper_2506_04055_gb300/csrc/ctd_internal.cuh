@@ -102,12 +102,11 @@ struct ModelW {
   LayerW L[kMaxT];
   const float *R1, *R1t, *d1, *R2, *d2;   // [F/2][F], [F][F/2]
   const __nv_bfloat16 *R1b, *R1tb;
-  bool tc_adjoint;                 // BF16 path: edge adjoint with the tensor-core filter
-  int tc_adjoint_variant;          // 1 register gathers, 2 bulk-copy gathers, 3 + folded basis, 4 + split basis
+  bool tc_adjoint;                 // BF16 path, F = 128: edge adjoint with the tensor-core filter
+  bool tc_adjoint_split;           // ... with each basis value entered as a BF16 hi + lo pair
   bool edge_store;                 // store per-edge filters in the forward pass for the adjoint
-  int tc_message_variant;          // BF16 message kernel: 1 register gathers, 2 bulk-copy gathers, 3 = 1 + split basis,
-                                   // 5 contraction over each receiver's edges on tcgen05 (edge_mma.cu)
-  int64_t edge_chunk_rows;         // bulk-gathered kernels: rows per chunk (0: one range per stream)
+  bool tc_message;                 // BF16 path, F = 128: message step as the tensor-core contraction (edge_mma.cu)
+  int64_t edge_chunk_rows;         // tensor-core adjoint: rows per chunk (0: one range per stream)
 };
 
 // Strictly local equivariant edge model (model_local.cu): FP32 weights on the device, matrices
@@ -215,14 +214,11 @@ void launch_check_finite(cudaStream_t st, int64_t n, const double* a, int* statu
 // EPI 0 bias, 1 bias + SiLU (bf16 copy gets the SiLU), 2 + aux, 3 * SiLU'(aux).
 bool gemm_bf16_supported(int N, int K);
 bool make_tmap_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
-// edge_tc.cu: tensor-core edge message / adjoint (F = 128, K <= 32)
+// edge_tc.cu: tensor-core edge adjoint (F = 128, K <= 31); G4 = the receivers' (gsm, gvm)
+// interleaved per feature
 bool edge_tc_supported(int F, int K);
-int edge_fwd_tc(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32_t* arow, const int32_t* acol,
-                const float4* ar, const float* PHI, const float* S, const float* V, float* SM, float* VM,
-                __nv_bfloat16* VMb, int* status, const int32_t* aend);
 int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
-                const int32_t* acol, const float4* ar, const float* PHI, const float* Gsm, const float* Gvm,
-                float* GPHI, float4* hedge, int* status,
+                const int32_t* acol, const float4* ar, const float* PHI, float* GPHI, float4* hedge, int* status,
                 const int32_t* aend, const float* G4);
 // edge_mma.cu: the message step as a tensor-core contraction over each receiver's edges
 // (F = 128, K < 32): gathered FP16 message rows x per-edge basis, FP32 filter weights after it.
@@ -240,6 +236,7 @@ bool model_uses_g4(const ModelW& m, int precision);
 int64_t model_buffer_floats_per_atom(int b, int F, int T, bool g4);
 int model_bf16_buffer_count();
 bool model_uses_msg_mma(const ModelW& m);
+bool model_stores_edges(const ModelW& m, int precision);
 int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T, bool msg_mma);
 int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, const int32_t* species_s,
                                 const int32_t* arow, const int32_t* acol, const float4* ar, const int32_t* arev,

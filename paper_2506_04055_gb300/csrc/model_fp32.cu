@@ -693,20 +693,22 @@ __global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restr
   double acc = 0.0, comp = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float wi = ew ? ew[i] : 1.0f;
-    float e = d2[0];
+    // the readout's terms largely cancel (U_i is small next to them), so they are summed in
+    // FP64: in a crystal every atom would otherwise carry the same FP32 rounding of that sum
+    double e = (double)d2[0];
     for (int k = 0; k < Fh; ++k) {
       float h = H3[i * Fh + k];
-      e = fmaf(R2[k], silu_f(h), e);
+      e = fma((double)R2[k], (double)silu_f(h), e);
       if (G3) {
         const float gk = wi * (e_scale * R2[k] * dsilu_f(h));
         G3[i * Fh + k] = gk;
         if (G3b) G3b[i * Fh + k] = __float2bfloat16_rn(gk);
       }
     }
-    e *= e_scale;
-    e *= wi;
-    if (e_atom) e_atom[i] = e;
-    double x = (double)e, t = acc + x;   // Neumaier
+    e *= (double)e_scale;
+    e *= (double)wi;
+    if (e_atom) e_atom[i] = (float)e;
+    double x = e, t = acc + x;   // Neumaier
     comp += fabs(acc) >= fabs(x) ? (acc - t) + x : (x - t) + acc;
     acc = t;
   }
@@ -898,7 +900,7 @@ int model_buffer_count() { return B_COUNT; }
 // The interleaved receiver gradients (G4) are read only by the bulk-gathered tensor-core
 // adjoint of the BF16 path; no other path allocates them.
 bool model_uses_g4(const ModelW& m, int precision) {
-  return precision == CTD_PREC_BF16 && edge_tc_supported(m.F, m.K) && m.tc_adjoint && m.tc_adjoint_variant == 2;
+  return precision == CTD_PREC_BF16 && edge_tc_supported(m.F, m.K) && m.tc_adjoint;
 }
 
 int64_t model_buffer_floats_per_atom(int b, int F, int T, bool g4) {
@@ -1029,7 +1031,15 @@ enum BufB {
 
 int model_bf16_buffer_count() { return BB_COUNT; }
 
-bool model_uses_msg_mma(const ModelW& m) { return edge_mma_supported(m.F, m.K) && m.tc_message_variant == 5; }
+bool model_uses_msg_mma(const ModelW& m) { return edge_mma_supported(m.F, m.K) && m.tc_message; }
+
+// Stored edge filters are written by the CUDA-core message kernel and read by the CUDA-core
+// adjoint, so they apply only when both run.
+bool model_stores_edges(const ModelW& m, int precision) {
+  if (!m.edge_store) return false;
+  if (precision != CTD_PREC_BF16) return true;
+  return !model_uses_msg_mma(m) && !(edge_tc_supported(m.F, m.K) && m.tc_adjoint);
+}
 
 int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T, bool msg_mma) {
   if (b >= BB_S0 && b < BB_S0 + T + 1) return F;
@@ -1055,10 +1065,11 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   const int F = m.F, T = m.T, Fh = F / 2;
   const unsigned nb = blocks_for(n * F);
   int bad = 0;
-  // Radial filter on tcgen05 inside the message kernel (F = 128); other widths keep the FP32
-  // filter.  The adjoint takes the tcgen05 filter too unless the CUDA-core kernel is selected
-  // (m.tc_adjoint).  The tensor-core kernels recompute the filter, so storing edge filters
-  // applies to the CUDA-core edge kernels only.
+  // F = 128: the message step as the tensor-core contraction over each receiver's edges
+  // (edge_mma.cu) and the adjoint with the radial filter on tcgen05 (edge_tc.cu), unless the
+  // CUDA-core kernels are selected; other widths keep the CUDA-core edge kernels (FP32 filter).
+  // The tensor-core kernels recompute the filter, so storing edge filters applies to the
+  // CUDA-core kernels only.
   const bool use_tc = edge_tc_supported(F, m.K);
   const bool use_tc_bwd = use_tc && m.tc_adjoint;
   const bool msg_mma = model_uses_msg_mma(m);
@@ -1073,14 +1084,12 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     bad |= gemm_bf16<1>(st, n, F, F, Bb[BB_S0 + t], F, L.W1b, L.b1, nullptr, 0, H1, F, Bb[BB_A1], F, status);
     // phi = W2 silu(.) + b2, packed into PHI by the GEMM epilogue
     bad |= gemm_bf16<4>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, V, 3 * F, PHI, 6 * F, nullptr, 0, status, PHIh);
-    float* wst = (wstore && need_grad && !use_tc) ? wstore + t * wstore_layer_floats : nullptr;
+    float* wst = (wstore && need_grad && !use_tc_bwd && !msg_mma) ? wstore + t * wstore_layer_floats : nullptr;
 #define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_FWD);
       if (msg_mma) {
         bad |= edge_fwd_mma(st, m, t, n, arow, acol, ar, PHIh, S, V, SM, VM, Bb[BB_VM], status);
-      } else if (use_tc) {
-        bad |= edge_fwd_tc(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], status, aend);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_FWD)
       }
@@ -1121,14 +1130,14 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid_bf16<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, AV, GSM, Bb[BB_GUV]); }
     bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
     if (G4 && n > 0) { LaunchScope ls_(st); k_interleave_g4<<<nb, kThreads, 0, st>>>(n, F, GSM, GVM, reinterpret_cast<float4*>(G4)); }
-    const float* wst = (wstore && !use_tc) ? wstore + t * wstore_layer_floats : nullptr;
+    const float* wst = (wstore && !use_tc_bwd && !msg_mma) ? wstore + t * wstore_layer_floats : nullptr;
     // first layer: no phi gradients, no phi backward (its inputs do not depend on positions)
     float* gphi = t > 0 ? GPHI : nullptr;
 #define CTD_BWD(KPV) edge_bwd_kp<KPV>(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, gphi, hedge, wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
       if (use_tc_bwd) {
-        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, GSM, GVM, gphi, hedge, status, aend, G4);
+        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, gphi, hedge, status, aend, G4);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_BWD)
       }

@@ -37,10 +37,10 @@ def test_bf16_fcc4000_F128(orc):
     print(f"bf16 fcc4000: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_bf16_tensor_core_adjoint(orc, variant):
-    """Each edge-adjoint variant (CUDA cores; tcgen05 filter with register or bulk-copy gathers)
-    on the fcc sub-cell and a small cell."""
+    """Each edge-adjoint variant (CUDA cores; tcgen05 filter; tcgen05 filter with the basis as a
+    BF16 hi + lo pair) on the fcc sub-cell and a small cell."""
     eng = engine()
     for sy in (syn.fcc(10, 10, 10, jitter=0.05, seed=0), syn.water_box(21, seed=2)):
         out, ref = _run(eng, orc, sy, 128, 3, 2, bias=0.1, tc_adjoint=variant)
@@ -94,12 +94,12 @@ def _sparse_system():
     return syn.System(x, z, m, np.eye(3) * 30.0, name="sparse")
 
 
-@pytest.mark.parametrize("message", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("message", [0, 1])
 def test_bf16_message_variants(orc, message):
-    """Message kernel with register gathers (1), bulk-copy gathers and the folded basis (2), the
-    split basis (3), chunked rows (4), or the contraction over each receiver's edges on the
-    tensor cores (5), on the fcc sub-cell, a small water cell, a 4-species mixture with filter
-    biases, and a sparse cell with isolated atoms."""
+    """Message step on CUDA cores with the FP32 filter (0) or as the tensor-core contraction over
+    each receiver's edges (1: FP16 message rows x basis, FP32 filter weights per receiver), on
+    the fcc sub-cell, a small water cell, a 4-species mixture with filter biases, and a sparse
+    cell with isolated atoms and rows spanning several 16-edge steps."""
     from paper_2506_04055_gb300 import _lib
     eng = engine()
     cases = ((syn.fcc(10, 10, 10, jitter=0.05, seed=0), 1, 0.1), (syn.water_box(21, seed=2), 2, 0.1),
