@@ -349,8 +349,11 @@ def run_ours(args):
         e2e_s = time.perf_counter() - t0
         if dist:
             dist.barrier()
+        # device memory the context holds for this system (all buffers, after the runs above)
+        held = pot.compute(sy.species, sy.positions, sy.cell, stats=True)["stats"]["bytes_allocated"]
         pot.close()
         results[prec] = {"total_ms": total_ms, "step_ms": step_ms, "prof": prof, "rebuilds": rebuilds,
+                         "device_bytes_per_atom": held / sy.n,
                          "clocks": clk.summary(), "e2e_s": e2e_s, "e2e_steps": e2e_steps,
                          "h2d": n * 3 * 8 + n * 4 + 72, "d2h": n * 3 * 8 + 8 + 72,
                          "epot": [float(ep[0])], "ekin": [float(ek[0])]}
@@ -369,7 +372,8 @@ def run_ours(args):
         summary[prec] = {"value": whole_job_value(sy.n, world, args.steps, tot), "ms_per_step": tot / args.steps,
                          "p50_ms": r["step_ms"][len(r["step_ms"]) // 2],
                          "p99_ms": r["step_ms"][min(len(r["step_ms"]) - 1, int(0.99 * len(r["step_ms"])))],
-                         "e2e": whole_job_value(sy.n, world, r["e2e_steps"], 1e3 * e2e), "rebuilds": r["rebuilds"]}
+                         "e2e": whole_job_value(sy.n, world, r["e2e_steps"], 1e3 * e2e), "rebuilds": r["rebuilds"],
+                         "device_bytes_per_atom": round(r["device_bytes_per_atom"])}
     if dist:
         dist.destroy_process_group()
     if rank != 0:
@@ -744,6 +748,7 @@ def run_serve(args):
                 fin_t.append(b - t0)
             nfin += nf
         wall = time.perf_counter() - t0
+        gstats = srv.graph_stats()
         srv.close()
         req = np.array(fin_t) - np.array(sub_t)
         busy = sum(lat) / 1e3
@@ -751,7 +756,10 @@ def run_serve(args):
                 "atom_steps_per_busy_s": float(natoms.sum()) * S_ / busy,
                 "step_ms_p50": _pct(lat, 0.5), "step_ms_p99": _pct(lat, 0.99), "server_steps": len(lat),
                 "request_s_p50": float(np.percentile(req, 50)), "request_s_p99": float(np.percentile(req, 99)),
-                "mean_resident_atoms": float(np.mean(res_atoms))}
+                "mean_resident_atoms": float(np.mean(res_atoms)),
+                # steps whose device work after the rebuild decisions ran as one CUDA-graph launch
+                "graph_steps": gstats["graph_steps"], "eager_steps": gstats["eager_steps"],
+                "kernels_per_graph_launch": gstats["kernels_per_replay"]}
 
     # warm-up session (kernels, allocations)
     session(None, args.serve_precision)

@@ -288,6 +288,21 @@ int ctd_serve_set_thermostat(ctd_server *s, int64_t request_id, double temperatu
 int ctd_serve_thermostat(ctd_server *s, int64_t request_id, double *xi, double *vxi, double *ethermo);
 int ctd_serve_stats(ctd_server *s, int64_t *resident_atoms, int32_t *resident_replicas,
                     int32_t *queued, int64_t *bytes_held);
+
+/* A served step's device work after the per-replica rebuild decisions -- the prune, the model
+ * (energy, forces, virial) over the whole batch, the second half kick, the per-replica sums and
+ * thermostat half step -- is recorded once as a CUDA graph when the batch layout (resident
+ * replicas, atom count, device buffers, options) has not changed over the previous step, and
+ * replayed as one graph launch while it stays unchanged; a change (admission, retirement, a
+ * buffer that grows) runs that step eagerly and records again on the next.  Replay and eager
+ * steps launch the same kernels on the same data, so trajectories are identical either way.
+ * Not used for the strictly local family, with stored edge filters, or while per-launch
+ * profiling is on.  ctd_serve_use_graph(s, 0) turns it off (default on). */
+int ctd_serve_use_graph(ctd_server *s, int32_t enable);
+/* Steps run by graph replay and eagerly, kernel launches in one replay, graphs recorded.
+ * Any output may be NULL. */
+int ctd_serve_graph_stats(ctd_server *s, int64_t *graph_steps, int64_t *eager_steps,
+                          int64_t *kernels_per_replay, int64_t *captures);
 const char *ctd_serve_last_error(ctd_server *s);
 void ctd_serve_destroy(ctd_server *s);
 

@@ -318,6 +318,14 @@ class Server:
     def stats(self):
         return _lib.ctd_serve_stats(self.srv)
 
+    def use_graph(self, enable: bool = True):
+        """Record and replay each step's device work as a CUDA graph (default on)."""
+        _lib.serve_check(self.srv, _lib.load().ctd_serve_use_graph(self.srv, 1 if enable else 0))
+
+    def graph_stats(self):
+        """Steps run by graph replay and eagerly, kernels per replay, graphs recorded."""
+        return _lib.ctd_serve_graph_stats(self.srv)
+
 
 class Domains:
     """Spatial domain decomposition of one periodic system (see ctd_domains_* in

@@ -46,6 +46,7 @@ EXPORTS = [
     "ctd_serve_set_thermostat", "ctd_serve_thermostat",
     "ctd_set_option", "ctd_profile_enable", "ctd_profile_read", "ctd_gemm_bf16",
     "ctd_serve_create", "ctd_serve_submit", "ctd_serve_step", "ctd_serve_poll", "ctd_serve_stats",
+    "ctd_serve_use_graph", "ctd_serve_graph_stats",
     "ctd_serve_last_error", "ctd_serve_destroy", "ctd_domains_create", "ctd_domains_compute",
     "ctd_domains_info", "ctd_domains_context", "ctd_domains_last_error", "ctd_domains_destroy",
     "ctd_neighbors_noalloc", "ctd_selftest_wait",
@@ -123,6 +124,8 @@ def load(path: str = LIB_PATH):
         "ctd_serve_step": ([P, P, P, P], ctypes.c_int),
         "ctd_serve_poll": ([P, I64, P, P, P, P, P, P, P], ctypes.c_int),
         "ctd_serve_stats": ([P, P, P, P, P], ctypes.c_int),
+        "ctd_serve_use_graph": ([P, I32], ctypes.c_int),
+        "ctd_serve_graph_stats": ([P, P, P, P, P], ctypes.c_int),
         "ctd_serve_last_error": ([P], ctypes.c_char_p),
         "ctd_serve_destroy": ([P], None),
         "ctd_domains_create": ([P, P, P, ctypes.c_size_t, ctypes.c_size_t, P, I32, D, P], ctypes.c_int),
@@ -298,6 +301,13 @@ def ctd_serve_set_thermostat(srv, rid, temperature, tau, chain, xi_ptr=None, vxi
 
 def ctd_serve_thermostat(srv, rid, xi_ptr=None, vxi_ptr=None, eth_ptr=None):
     serve_check(srv, load().ctd_serve_thermostat(srv, rid, xi_ptr, vxi_ptr, eth_ptr))
+
+
+def ctd_serve_graph_stats(srv):
+    g, e, k, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    serve_check(srv, load().ctd_serve_graph_stats(srv, ctypes.byref(g), ctypes.byref(e), ctypes.byref(k),
+                                                  ctypes.byref(c)))
+    return {"graph_steps": g.value, "eager_steps": e.value, "kernels_per_replay": k.value, "captures": c.value}
 
 
 def ctd_serve_stats(srv):

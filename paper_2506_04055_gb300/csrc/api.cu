@@ -46,6 +46,8 @@ int fail(ctd_ctx* c, int code, const std::string& msg) {
 // Grow-only allocation with 25 % headroom, charged against the budget.
 int ensure(ctd_ctx* c, DBuf& b, size_t bytes) {
   if (bytes <= b.bytes) return CTD_OK;
+  if (c->capturing) return fail(c, CTD_ERR_STATE, "a buffer would grow during graph capture");
+  ++c->alloc_gen;
   size_t want = bytes + bytes / 4 + 256;
   want = (want + 255) & ~(size_t)255;
   if (c->budget && c->held - b.bytes + want > c->budget) {
@@ -143,6 +145,10 @@ int check_status(ctd_ctx* c) {
   CUDA_OK(c, cudaMemcpyAsync(&st, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
   if (st & ST_REV_MISSING) return fail(c, CTD_ERR_CAPACITY, "reverse edge missing in the neighbour list");
+  if (st & ST_FP16_RANGE)
+    return fail(c, CTD_ERR_NONFINITE,
+                "an activation stored in FP16 (message table, U/V products or update coefficients) is outside "
+                "the FP16 range; the FP32 path keeps them in FP32");
   if (st & ST_NONFINITE) return fail(c, CTD_ERR_NONFINITE, "non-finite value in positions or results");
   if (st & ST_TIMEOUT) return fail(c, CTD_ERR_TIMEOUT, "a bounded device wait gave up");
   if (st & ST_OWNERSHIP) return fail(c, CTD_ERR_STATE, "domain decomposition: an atom is not owned exactly once");
@@ -275,9 +281,9 @@ size_t model_bytes_per_atom(const ctd_ctx* c) {
     w.KA = (c->desc.K + 2 * w.S + 3) / 4 * 4;
     return sizeof(float) * (size_t)local_buffer_floats(w, 1, 64);
   }
-  const bool g4 = model_uses_g4(c->mw, c->desc.precision);
   size_t bytes = 0;
-  for (int b = 0; b < model_buffer_count(); ++b) bytes += sizeof(float) * (size_t)model_buffer_floats_per_atom(b, F, T, g4);
+  for (int b = 0; b < model_buffer_count(); ++b)
+    bytes += sizeof(float) * (size_t)model_buffer_floats_per_atom(b, c->mw, F, T, c->desc.precision);
   if (c->desc.precision == CTD_PREC_BF16)
     for (int b = 0; b < model_bf16_buffer_count(); ++b)
       bytes += sizeof(__nv_bfloat16) * (size_t)model_bf16_buffer_elems_per_atom(b, F, T, model_uses_msg_mma(c->mw));
@@ -329,9 +335,8 @@ int evaluate(ctd_ctx* c, bool need_grad) {
   const int nb = model_buffer_count();
   if ((int)c->mbuf.size() < nb) c->mbuf.resize(nb);
   std::vector<float*> ptrs(nb, nullptr);
-  const bool g4 = model_uses_g4(c->mw, c->desc.precision);
   for (int b = 0; b < nb; ++b) {
-    int64_t per = model_buffer_floats_per_atom(b, F, T, g4);
+    int64_t per = model_buffer_floats_per_atom(b, c->mw, F, T, c->desc.precision);
     if (per == 0) continue;
     size_t bytes = sizeof(float) * (size_t)per * (size_t)n1;
     ENSURE(c, c->mbuf[b], bytes);

@@ -30,6 +30,8 @@ struct ProfState {
 void prof_bind(ProfState* p);   // bind the calling thread to a context's profiler (or null)
 int prof_stage();
 void prof_set_stage(int s);
+bool prof_recording();                 // CUDA-event timing is on for the bound profiler
+void prof_count_launches(int64_t k);   // add k launches (a graph replay) to the current stage
 struct StageGuard {
   int prev;
   explicit StageGuard(int s) : prev(prof_stage()) { prof_set_stage(s); }
@@ -80,6 +82,7 @@ enum Status : int {
   ST_NONFINITE = 4,
   ST_TIMEOUT = 8,         // a bounded device wait gave up
   ST_OWNERSHIP = 16,      // a spatial decomposition left an atom without exactly one owned copy
+  ST_FP16_RANGE = 32,     // a value stored in FP16 (BF16 path) was outside the FP16 range
 };
 
 // FP32 weights of one interaction layer (device pointers).  "t" = transposed ([in][out]).
@@ -219,7 +222,7 @@ bool make_tmap_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols
 bool edge_tc_supported(int F, int K);
 int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
                 const int32_t* acol, const float4* ar, const float* PHI, float* GPHI, float4* hedge, int* status,
-                const int32_t* aend, const float* G4);
+                const int32_t* aend, const float* G4, const __half* PHIh = nullptr);
 // edge_mma.cu: the message step as a tensor-core contraction over each receiver's edges
 // (F = 128, K < 32): gathered FP16 message rows x per-edge basis, FP32 filter weights after it.
 bool edge_mma_supported(int F, int K);
@@ -233,7 +236,8 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, 
 // model_fp32.cu
 int model_buffer_count();
 bool model_uses_g4(const ModelW& m, int precision);
-int64_t model_buffer_floats_per_atom(int b, int F, int T, bool g4);
+bool model_phi_fp16_only(const ModelW& m, int precision);
+int64_t model_buffer_floats_per_atom(int b, const ModelW& m, int F, int T, int precision);
 int model_bf16_buffer_count();
 bool model_uses_msg_mma(const ModelW& m);
 bool model_stores_edges(const ModelW& m, int precision);

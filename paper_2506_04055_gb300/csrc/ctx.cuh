@@ -32,6 +32,11 @@ struct ctd_ctx {
   bool own_stream = false;
   size_t budget = 0, held = 0;
   std::string err;
+  // While a served step is being captured into a CUDA graph, a buffer that would have to grow
+  // fails instead of reallocating (the capture is then abandoned); alloc_gen counts every
+  // (re)allocation and free, so that a graph is replayed only over the buffers it captured.
+  bool capturing = false;
+  uint64_t alloc_gen = 0;
   std::vector<DBuf*> all;
 
   // parameters

@@ -111,7 +111,7 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
 }
 
 struct MsgArgs {
-  const __half* __restrict__ PHIh;   // [n][5F] FP16 message rows
+  const __half* __restrict__ PHIh;   // [n][6F] FP16 message table; columns 0..5F-1 are gathered
   int64_t n;
   int64_t chunk_rows;
   int K;
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads_, 1) k_edge_msg_mma(const __grid_cons
           const int k0 = sl & 7, hh = q >> 3, cc = q & 7;
           const uint32_t dst = ubase + (uint32_t)(blk * kABlockBytes + (sl >> 3) * 2048 + hh * 1024 + k0 * 128 +
                                                   ((cc ^ k0) << 4));
-          cp_async16(dst, p.PHIh + (size_t)js * (kNBlk * kF) + blk * kF + q * 8);
+          cp_async16(dst, p.PHIh + (size_t)js * (6 * kF) + blk * kF + q * 8);
         }
       }
       cp_async_arrive(&full[u]);
@@ -546,12 +546,13 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// Rows of the FP16 message table [n][5F] as gather4 sources: boxes of 64 columns x 1 row, 128B swizzle.
-bool make_tmap_rows_f16(CUtensorMap* m, const __half* base, int64_t rows, int cols) {
+// The first `cols` columns of the rows of an FP16 table with `ld` columns per row as gather4
+// sources: boxes of 64 columns x 1 row, 128B swizzle.
+bool make_tmap_rows_f16(CUtensorMap* m, const __half* base, int64_t rows, int cols, int ld) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   cuuint32_t box[2] = {64, 1};
   cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), dims, strides, box, es,
@@ -571,7 +572,7 @@ int edge_fwd_mma(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32
   if (n == 0) return 0;
   if (!edge_mma_supported(m.F, m.K) || (reinterpret_cast<uintptr_t>(PHIh) & 15)) return -1;
   CUtensorMap tm{};
-  if (kTmaGather && !make_tmap_rows_f16(&tm, PHIh, n, 5 * kF)) return -2;
+  if (kTmaGather && !make_tmap_rows_f16(&tm, PHIh, n, 5 * kF, 6 * kF)) return -2;
   MsgArgs a{};
   a.PHIh = PHIh;
   a.n = n; a.K = m.K; a.rc = m.rc; a.arow = arow; a.acol = acol; a.ar = ar; a.S = S; a.V = V;

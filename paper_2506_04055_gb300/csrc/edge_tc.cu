@@ -73,7 +73,8 @@ struct EdgeTcArgs {
   const int32_t* __restrict__ acol;
   const int32_t* __restrict__ aend;  // rows completed at each edge (1 + following empty rows; 0 inside a row)
   const float4* __restrict__ ar;
-  const float* __restrict__ PHI;   // [n][6F]
+  const float* __restrict__ PHI;   // [n][6F] FP32 message table, or
+  const __half* __restrict__ PHIh; // [n][6F] its FP16 copy (the one the contracted message step used)
   const float* __restrict__ bf;    // [3F]
   float* __restrict__ GPHI;        // [n][5F]
   float4* __restrict__ hedge;      // [E]
@@ -352,10 +353,20 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
       float cur[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, nxt[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       auto fetch = [&](int64_t row, float (&o)[5]) {
         if (row < C.r1) {
-          const float* pj = p.PHI + row * 6 * kF + f;
+          if (p.PHIh) {
+            const __half* pj = p.PHIh + row * 6 * kF + f;
 #pragma unroll
-          for (int kk = 0; kk < 5; ++kk)
-            if (!L0 || kk == 0 || kk == 4) o[kk] = __ldg(pj + kk * kF);
+            for (int kk = 0; kk < 5; ++kk)
+              if (!L0 || kk == 0 || kk == 4) {
+                o[kk] = __half2float(__ldg(pj + kk * kF));
+                asm volatile("" : "+f"(o[kk]));   // converted once here, not again at every use
+              }
+          } else {
+            const float* pj = p.PHI + row * 6 * kF + f;
+#pragma unroll
+            for (int kk = 0; kk < 5; ++kk)
+              if (!L0 || kk == 0 || kk == 4) o[kk] = __ldg(pj + kk * kF);
+          }
         }
       };
       float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
@@ -555,14 +566,14 @@ static int64_t chunk_rows_for(const ModelW& m, int64_t n, int ns) {
 
 int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
                 const int32_t* acol, const float4* ar, const float* PHI, float* GPHI, float4* hedge, int* status,
-                const int32_t* aend, const float* G4) {
+                const int32_t* aend, const float* G4, const __half* PHIh) {
   if (n == 0) return 0;
-  if (!G4) return -1;
+  if (!G4 || (!PHI && !PHIh)) return -1;
   CUtensorMap tm;
   if (!make_tmap_bf16(&tm, m.L[t].Wfb, 3 * kF, 64, 64, 128)) return -2;
   EdgeTcArgs a{};
   a.n = n; a.K = m.K; a.rc = m.rc; a.accumulate = accumulate; a.arow = arow; a.acol = acol; a.ar = ar;
-  a.PHI = PHI; a.bf = m.L[t].bf; a.GPHI = GPHI; a.hedge = hedge; a.status = status; a.aend = aend; a.G4 = G4;
+  a.PHI = PHI; a.PHIh = PHIh; a.bf = m.L[t].bf; a.GPHI = GPHI; a.hedge = hedge; a.status = status; a.aend = aend; a.G4 = G4;
   a.chunk_rows = chunk_rows_for(m, n, kBwgNS);
   static bool attr = false;
   if (!attr) {

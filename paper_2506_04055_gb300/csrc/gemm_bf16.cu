@@ -32,7 +32,7 @@ struct GemmBf16Args {
   int ldo;
   bf16* outb;
   int ldob;
-  __half* outh;   // EPI 4: FP16 message table [M][5F] = [phi_s | psi_0 | psi_1 | psi_2 | phi_vs] (optional)
+  __half* outh;   // EPI 0 and 4: FP16 copy of out, same element stride ldo (optional; EPI 4: the message table)
   int* status;
   int a_stages, n_acc, b_box_rows, n_chunk;   // a_stages: k-block stages of the A ring
   uint32_t tmem_cols;
@@ -206,29 +206,38 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __gr
           if (m < p.M) {
             if (EPI == 0 || EPI == 1 || EPI == 4) { x.x += bq.x; x.y += bq.y; x.z += bq.z; x.w += bq.w; }
             if (EPI == 4) {
-              float* o = p.out + m * p.ldo;
-              __half* oh = p.outh ? p.outh + m * 5 * Fb : nullptr;
+              // FP32 table (if out) and FP16 copy (if outh), both [phi_s | psi_0..2 | phi_vs | phi_vv]
+              float* o = p.out ? p.out + m * p.ldo : nullptr;
+              __half* oh = p.outh ? p.outh + m * p.ldo : nullptr;
+              auto put = [&](int col, float4 y) {
+                if (o) *reinterpret_cast<float4*>(o + col) = y;
+              };
               auto put_h = [&](int col, float4 y) {
                 if (oh) {
+                  // FP16's largest finite value is 65504: a larger value is reported (it would round
+                  // to Inf and reach the results as a non-finite value without its cause)
+                  const float ym = fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(y.z), fabsf(y.w)));
+                  if (ym > 65504.f) atomicOr(p.status, (int)ST_FP16_RANGE);
                   const __half2 a = __floats2half2_rn(y.x, y.y), b = __floats2half2_rn(y.z, y.w);
                   *reinterpret_cast<uint2*>(oh + col) =
                       make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
                 }
               };
               if (blk == 0) {
-                *reinterpret_cast<float4*>(o + f0) = x;
+                put(f0, x);
                 put_h(f0, x);
               } else if (blk == 2) {
-                *reinterpret_cast<float4*>(o + 4 * Fb + f0) = x;
+                put(4 * Fb + f0, x);
                 put_h(4 * Fb + f0, x);
               } else {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                   const float4 y = make_float4(gv[j][c].x * x.x, gv[j][c].y * x.y, gv[j][c].z * x.z, gv[j][c].w * x.w);
-                  *reinterpret_cast<float4*>(o + (1 + c) * Fb + f0) = y;
+                  put((1 + c) * Fb + f0, y);
                   put_h((1 + c) * Fb + f0, y);
                 }
-                *reinterpret_cast<float4*>(o + 5 * Fb + f0) = x;
+                put(5 * Fb + f0, x);
+                put_h(5 * Fb + f0, x);
               }
               continue;
             }
@@ -237,6 +246,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __gr
               x.x *= dsilu_fast(g[j].x); x.y *= dsilu_fast(g[j].y); x.z *= dsilu_fast(g[j].z); x.w *= dsilu_fast(g[j].w);
             }
             if (p.out) *reinterpret_cast<float4*>(p.out + m * p.ldo + c0 + cc) = x;
+            if (EPI == 0 && p.outh) {
+              const float ym = fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w)));
+              if (ym > 65504.f) atomicOr(p.status, (int)ST_FP16_RANGE);
+              const __half2 h01 = __floats2half2_rn(x.x, x.y), h23 = __floats2half2_rn(x.z, x.w);
+              *reinterpret_cast<uint2*>(p.outh + m * p.ldo + c0 + cc) =
+                  make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+            }
             if (p.outb) {
               float y0 = x.x, y1 = x.y, y2 = x.z, y3 = x.w;
               if (EPI == 1) { y0 = silu_fast(y0); y1 = silu_fast(y1); y2 = silu_fast(y2); y3 = silu_fast(y3); }
@@ -308,12 +324,13 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
   // the epilogue moves 16-byte quads of FP32 (8-byte quads of BF16) per row
   if (!gemm_bf16_supported(N, K) || (lda * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) ||
       (reinterpret_cast<uintptr_t>(W) & 15) || (out && (ldo % 4 || (reinterpret_cast<uintptr_t>(out) & 15))) ||
+      (outh && ldo % 4) ||
       (outb && (ldob % 4 || (reinterpret_cast<uintptr_t>(outb) & 7))) ||
       (aux && (ldaux % 4 || (reinterpret_cast<uintptr_t>(aux) & 15))) || (bias && (reinterpret_cast<uintptr_t>(bias) & 15)))
     return -1;
   GemmBf16Args p{};
   p.M = M; p.N = N; p.K = K; p.bias = bias; p.aux = aux; p.ldaux = ldaux; p.out = out; p.ldo = ldo;
-  p.outb = outb; p.ldob = ldob; p.status = status; p.outh = EPI == 4 ? outh : nullptr;
+  p.outb = outb; p.ldob = ldob; p.status = status; p.outh = (EPI == 0 || EPI == 4) ? outh : nullptr;
   if (p.outh && (reinterpret_cast<uintptr_t>(outh) & 7)) return -1;
   p.b_box_rows = N % 64 == 0 ? 64 : 32;
   p.n_chunk = N <= 256 ? N : N / 2;

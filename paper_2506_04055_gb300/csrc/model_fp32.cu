@@ -208,15 +208,21 @@ __global__ void k_phi_pack(int64_t n, int F, const float* __restrict__ P3, const
   o[5 * F + f] = pvv;
 }
 
+// U/V products and update coefficients are read as FP32 (FP32 path) or from their FP16 copies
+// (BF16 path)
+__device__ __forceinline__ float ldx(const float* p) { return *p; }
+__device__ __forceinline__ float ldx(const __half* p) { return __half2float(*p); }
+
 // Z = [s^m ; sqrt(sum_a Vv_a^2 + eps)], UV rows (i, a) = [Uv_a | Vv_a]
+template <typename TX>
 __global__ void k_update_pre(int64_t n, int F, float eps, const float* __restrict__ SM,
-                             const float* __restrict__ UV, float* __restrict__ Z, __nv_bfloat16* __restrict__ Zb) {
+                             const TX* __restrict__ UV, float* __restrict__ Z, __nv_bfloat16* __restrict__ Zb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
   int f = (int)(idx % F);
-  const float* uv = UV + i * 3 * 2 * F;
-  float v0 = uv[F + f], v1 = uv[2 * F + F + f], v2 = uv[4 * F + F + f];
+  const TX* uv = UV + i * 3 * 2 * F;
+  float v0 = ldx(uv + F + f), v1 = ldx(uv + 2 * F + F + f), v2 = ldx(uv + 4 * F + F + f);
   const float nv = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
   if (Z) {
     Z[i * 2 * F + f] = SM[idx];
@@ -229,23 +235,25 @@ __global__ void k_update_pre(int64_t n, int F, float eps, const float* __restric
 }
 
 // s' = s^m + a_ss + a_sv <Uv, Vv>,  v'_a = v^m_a + a_vv Uv_a
+template <typename TX>
 __global__ void k_update_post(int64_t n, int F, const float* __restrict__ SM, const float* __restrict__ VM,
-                              const float* __restrict__ UV, const float* __restrict__ AV,
+                              const TX* __restrict__ UV, const TX* __restrict__ AV,
                               float* __restrict__ Sn, float* __restrict__ Vn, __nv_bfloat16* __restrict__ Snb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
   int f = (int)(idx % F);
-  const float* uv = UV + i * 6 * F;
-  const float* a = AV + i * 3 * F;
+  const TX* uv = UV + i * 6 * F;
+  const TX* a = AV + i * 3 * F;
+  const float avv = ldx(a + f);
   float sp = 0.0f;
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
-    float u = uv[al * 2 * F + f], v = uv[al * 2 * F + F + f];
+    float u = ldx(uv + al * 2 * F + f), v = ldx(uv + al * 2 * F + F + f);
     sp += u * v;
-    Vn[i * 3 * F + al * F + f] = VM[i * 3 * F + al * F + f] + a[f] * u;
+    Vn[i * 3 * F + al * F + f] = VM[i * 3 * F + al * F + f] + avv * u;
   }
-  const float snew = SM[idx] + a[2 * F + f] + a[F + f] * sp;
+  const float snew = SM[idx] + ldx(a + 2 * F + f) + ldx(a + F + f) * sp;
   Sn[idx] = snew;
   if (Snb) Snb[idx] = __float2bfloat16_rn(snew);
 }
@@ -311,20 +319,20 @@ __global__ void k_update_bwd_mid(int64_t n, int F, float eps, const float* __res
 //   pre: g_a (BF16) and the Uv half of each GUV row, gUv_a = gv'_a a_vv + gs' a_sv Vv_a;
 //   mid: gsm = gs' + gz_s and the Vv half, gVv_a = gs' a_sv Uv_a + gz_n Vv_a / |Vv|.
 __global__ void k_update_bwd_pre_bf16(int64_t n, int F, const float* __restrict__ GS, const float* __restrict__ GV,
-                                      const float* __restrict__ UV, const float* __restrict__ AV,
+                                      const __half* __restrict__ UV, const __half* __restrict__ AV,
                                       __nv_bfloat16* __restrict__ GAb, __nv_bfloat16* __restrict__ GUVb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
   int f = (int)(idx % F);
-  const float* uv = UV + i * 6 * F;
-  const float* a = AV + i * 3 * F;
-  const float gs = GS[idx], asv = a[F + f], avv = a[f];
+  const __half* uv = UV + i * 6 * F;
+  const __half* a = AV + i * 3 * F;
+  const float gs = GS[idx], asv = ldx(a + F + f), avv = ldx(a + f);
   const float gsp = gs * asv;
   float sp = 0.0f, gavv = 0.0f;
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
-    const float u = uv[al * 2 * F + f], v = uv[al * 2 * F + F + f];
+    const float u = ldx(uv + al * 2 * F + f), v = ldx(uv + al * 2 * F + F + f);
     const float gv = GV[i * 3 * F + al * F + f];
     sp += u * v;
     gavv += gv * u;
@@ -336,23 +344,23 @@ __global__ void k_update_bwd_pre_bf16(int64_t n, int F, const float* __restrict_
 }
 
 __global__ void k_update_bwd_mid_bf16(int64_t n, int F, float eps, const float* __restrict__ GS,
-                                      const float* __restrict__ GZ, const float* __restrict__ UV,
-                                      const float* __restrict__ AV, float* __restrict__ Gsm,
+                                      const float* __restrict__ GZ, const __half* __restrict__ UV,
+                                      const __half* __restrict__ AV, float* __restrict__ Gsm,
                                       __nv_bfloat16* __restrict__ GUVb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
   int f = (int)(idx % F);
-  const float* uv = UV + i * 6 * F;
-  const float v0 = uv[F + f], v1 = uv[3 * F + f], v2 = uv[5 * F + f];
+  const __half* uv = UV + i * 6 * F;
+  const float v0 = ldx(uv + F + f), v1 = ldx(uv + 3 * F + f), v2 = ldx(uv + 5 * F + f);
   const float nv = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
   const float g = GZ[i * 2 * F + F + f] / nv;
   const float gs = GS[idx];
-  const float gsp = gs * AV[i * 3 * F + F + f];
+  const float gsp = gs * ldx(AV + i * 3 * F + F + f);
   Gsm[idx] = gs + GZ[i * 2 * F + f];
-  GUVb[i * 6 * F + F + f] = __float2bfloat16_rn(gsp * uv[f] + g * v0);
-  GUVb[i * 6 * F + 3 * F + f] = __float2bfloat16_rn(gsp * uv[2 * F + f] + g * v1);
-  GUVb[i * 6 * F + 5 * F + f] = __float2bfloat16_rn(gsp * uv[4 * F + f] + g * v2);
+  GUVb[i * 6 * F + F + f] = __float2bfloat16_rn(gsp * ldx(uv + f) + g * v0);
+  GUVb[i * 6 * F + 3 * F + f] = __float2bfloat16_rn(gsp * ldx(uv + 2 * F + f) + g * v1);
+  GUVb[i * 6 * F + 5 * F + f] = __float2bfloat16_rn(gsp * ldx(uv + 4 * F + f) + g * v2);
 }
 
 // G4[i][f] = (gsm_i,f, gvm_i,0,f, gvm_i,1,f, gvm_i,2,f): the receivers' gradients interleaved per
@@ -369,15 +377,17 @@ __global__ void k_interleave_g4(int64_t n, int F, const float* __restrict__ Gsm,
 
 // Backward of PHI packing: gphi_vv = sum_a gpsi_a v_a, gv_a = gvm_a + gpsi_a phi_vv;
 // GP3 = [gphi_s | gphi_vv | gphi_vs]
+// (phi_vv from the FP32 table PHI, or from its FP16 copy PHIh when PHI is null)
 __global__ void k_phi_bwd_pre(int64_t n, int F, const float* __restrict__ GPHI, const float* __restrict__ PHI,
-                              const float* __restrict__ V, const float* __restrict__ Gvm,
-                              float* __restrict__ GP3, float* __restrict__ GVn, __nv_bfloat16* __restrict__ GP3b) {
+                              const __half* __restrict__ PHIh, const float* __restrict__ V,
+                              const float* __restrict__ Gvm, float* __restrict__ GP3, float* __restrict__ GVn,
+                              __nv_bfloat16* __restrict__ GP3b) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n * F) return;
   int64_t i = idx / F;
   int f = (int)(idx % F);
   const float* g = GPHI + i * 5 * F;
-  float pvv = PHI[i * 6 * F + 5 * F + f];
+  const float pvv = PHI ? PHI[i * 6 * F + 5 * F + f] : __half2float(PHIh[i * 6 * F + 5 * F + f]);
   float gpvv = 0.0f;
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
@@ -693,8 +703,9 @@ __global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restr
   double acc = 0.0, comp = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float wi = ew ? ew[i] : 1.0f;
-    // the readout's terms largely cancel (U_i is small next to them), so they are summed in
-    // FP64: in a crystal every atom would otherwise carry the same FP32 rounding of that sum
+    // the readout's terms can largely cancel (U_i small next to them): they are summed in FP64
+    // and rounded once to the FP32 per-atom energy; the total is the compensated sum of those
+    // per-atom values, so that any grouping of atoms (a served replica) sums to the same total
     double e = (double)d2[0];
     for (int k = 0; k < Fh; ++k) {
       float h = H3[i * Fh + k];
@@ -707,8 +718,9 @@ __global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restr
     }
     e *= (double)e_scale;
     e *= (double)wi;
-    if (e_atom) e_atom[i] = (float)e;
-    double x = e, t = acc + x;   // Neumaier
+    const float ef = (float)e;
+    if (e_atom) e_atom[i] = ef;
+    double x = (double)ef, t = acc + x;   // Neumaier
     comp += fabs(acc) >= fabs(x) ? (acc - t) + x : (x - t) + acc;
     acc = t;
   }
@@ -879,8 +891,8 @@ enum BufId {
   B_V0 = B_S0 + kMaxT + 1,         // V[t] for t = 0..T
   B_PHI0 = B_V0 + kMaxT + 1,       // [n][6F] per layer
   B_H10 = B_PHI0 + kMaxT,          // [n][F]
-  B_SM0 = B_H10 + kMaxT,           // [n][F]
-  B_VM0 = B_SM0 + kMaxT,           // [n][3F]
+  B_SM0 = B_H10 + kMaxT,           // [n][F]  s^m, v^m: read only within their layer's forward pass,
+  B_VM0 = B_SM0 + kMaxT,           // [n][3F] so one buffer each (id + 0) serves every layer
   B_UV0 = B_VM0 + kMaxT,           // [3n][2F]
   B_H20 = B_UV0 + kMaxT,           // [n][F]
   B_AV0 = B_H20 + kMaxT,           // [n][3F]
@@ -903,20 +915,28 @@ bool model_uses_g4(const ModelW& m, int precision) {
   return precision == CTD_PREC_BF16 && edge_tc_supported(m.F, m.K) && m.tc_adjoint;
 }
 
-int64_t model_buffer_floats_per_atom(int b, int F, int T, bool g4) {
+// The BF16 path keeps the message table of each layer only as its FP16 copy when the contracted
+// message step and the tensor-core adjoint both run: nothing else reads the FP32 table then.
+bool model_phi_fp16_only(const ModelW& m, int precision) {
+  return model_uses_g4(m, precision) && model_uses_msg_mma(m);
+}
+
+int64_t model_buffer_floats_per_atom(int b, const ModelW& m, int F, int T, int precision) {
+  const bool g4 = model_uses_g4(m, precision), bf16 = precision == CTD_PREC_BF16;
   auto layer = [&](int base, int cnt) { return b >= base && b < base + cnt; };
   if (layer(B_S0, T + 1)) return F;
   if (layer(B_V0, T + 1)) return 3 * F;
-  if (layer(B_PHI0, T)) return 6 * F;
+  if (layer(B_PHI0, T)) return model_phi_fp16_only(m, precision) ? 0 : 6 * F;
   if (layer(B_H10, T)) return F;
-  if (layer(B_SM0, T)) return F;
-  if (layer(B_VM0, T)) return 3 * F;
-  if (layer(B_UV0, T)) return 6 * F;
+  if (b == B_SM0 && T > 0) return F;
+  if (b == B_VM0 && T > 0) return 3 * F;
+  if (layer(B_UV0, T)) return bf16 ? 0 : 6 * F;   // the BF16 path keeps U/V products and
   if (layer(B_H20, T)) return F;
-  if (layer(B_AV0, T)) return 3 * F;
+  if (layer(B_AV0, T)) return bf16 ? 0 : 3 * F;   // update coefficients in FP16 (BB_UVH0, BB_AVH0)
   switch (b) {
-    case B_T1: case B_T2: return 3 * F;
-    case B_T3: return 6 * F;
+    case B_T1: return bf16 ? 2 * F : 3 * F;   // the BF16 path uses only T1, as [n][2F]
+    case B_T2: return bf16 ? 0 : 3 * F;
+    case B_T3: return bf16 ? 0 : 6 * F;
     case B_GS: case B_GSM: return F;
     case B_GV: case B_GVM: return 3 * F;
     case B_GPHI: return 5 * F;
@@ -941,7 +961,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
     float *S = B[B_S0 + t], *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
-    float *SM = B[B_SM0 + t], *VM = B[B_VM0 + t], *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
+    float *SM = B[B_SM0], *VM = B[B_VM0], *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
     float *T1 = B[B_T1], *T2 = B[B_T2];
     // phi = W2 silu(W1 s + b1) + b2
     gemm<EPI_BIAS_SILU>(st, n, F, F, S, F, L.W1t, L.b1, nullptr, 0, H1, F, T1, F);
@@ -957,10 +977,10 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
 #undef CTD_FWD
     // update
     gemm<EPI_BIAS>(st, 3 * n, 2 * F, F, VM, F, L.UVt, nullptr, nullptr, 0, UV, 2 * F);
-    if (n > 0) { LaunchScope ls_(st); k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1, nullptr); }
+    if (n > 0) { LaunchScope ls_(st); k_update_pre<float><<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1, nullptr); }
     gemm<EPI_BIAS_SILU>(st, n, F, 2 * F, T1, 2 * F, L.A1t, L.c1, nullptr, 0, H2, F, T2, F);
     gemm<EPI_BIAS>(st, n, 3 * F, F, T2, F, L.A2t, L.c2, nullptr, 0, AV, 3 * F);
-    if (n > 0) { LaunchScope ls_(st); k_update_post<<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1], nullptr); }
+    if (n > 0) { LaunchScope ls_(st); k_update_post<float><<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1], nullptr); }
   }
   // readout
   gemm<EPI_BIAS>(st, n, Fh, F, B[B_S0 + T], F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
@@ -995,7 +1015,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
 #undef CTD_BWD
     if (t == 0) break;
     // phi backward -> gradients w.r.t. the layer input (s_t, v_t)
-    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, T2, GV, nullptr); }
+    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, nullptr, V, GVM, T2, GV, nullptr); }
     gemm<EPI_DSILU>(st, n, F, 3 * F, T2, 3 * F, L.W2, nullptr, H1, F, T1, F);          // gh1
     gemm<EPI_ADD>(st, n, F, F, T1, F, L.W1, nullptr, GSM, F, GS, F);                    // gs
   }
@@ -1025,8 +1045,11 @@ enum BufB {
   BB_GUV,                    // [gUv | gVv]            [3n][2F]
   BB_GP3,                    // g_phi                  [n][3F]
   BB_GH1,                    // g_h1                   [n][F]
-  BB_PHIH,                   // FP16 message table [phi_s | psi_0..2 | phi_vs] [n][5F] (contracted message kernel)
-  BB_COUNT
+  BB_PHIH0,                  // FP16 message table of layer t, [n][6F] = [phi_s | psi_0..2 | phi_vs | phi_vv]
+                             // (contracted message step; ids BB_PHIH0 + t)
+  BB_UVH0 = BB_PHIH0 + kMaxT, // FP16 U/V products of layer t, rows (i, a) = [Uv_a | Vv_a]  [3n][2F]
+  BB_AVH0 = BB_UVH0 + kMaxT,  // FP16 update coefficients of layer t, [a_vv | a_sv | a_ss]  [n][3F]
+  BB_COUNT = BB_AVH0 + kMaxT
 };
 
 int model_bf16_buffer_count() { return BB_COUNT; }
@@ -1043,12 +1066,14 @@ bool model_stores_edges(const ModelW& m, int precision) {
 
 int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T, bool msg_mma) {
   if (b >= BB_S0 && b < BB_S0 + T + 1) return F;
+  if (b >= BB_PHIH0 && b < BB_PHIH0 + kMaxT) return msg_mma && b < BB_PHIH0 + T ? 6 * F : 0;
+  if (b >= BB_UVH0 && b < BB_UVH0 + kMaxT) return b < BB_UVH0 + T ? 6 * F : 0;
+  if (b >= BB_AVH0 && b < BB_AVH0 + kMaxT) return b < BB_AVH0 + T ? 3 * F : 0;
   switch (b) {
     case BB_A1: case BB_A2: case BB_GH2: case BB_GH1: return F;
     case BB_VM: case BB_GA: case BB_GP3: return 3 * F;
     case BB_Z: return 2 * F;
     case BB_GUV: return 6 * F;
-    case BB_PHIH: return msg_mma ? 5 * F : 0;
     default: return 0;
   }
 }
@@ -1073,16 +1098,21 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   const bool use_tc = edge_tc_supported(F, m.K);
   const bool use_tc_bwd = use_tc && m.tc_adjoint;
   const bool msg_mma = model_uses_msg_mma(m);
-  __half* PHIh = msg_mma ? reinterpret_cast<__half*>(Bb[BB_PHIH]) : nullptr;
   const bool g4 = model_uses_g4(m, CTD_PREC_BF16);
+  // with the contracted message step each layer's table is kept in FP16 ([n][6F]); the FP32
+  // table is written only for the CUDA-core adjoint, which reads it
+  const bool phi32 = !model_phi_fp16_only(m, CTD_PREC_BF16);
+  auto phih = [&](int t) { return msg_mma ? reinterpret_cast<__half*>(Bb[BB_PHIH0 + t]) : nullptr; };
   if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], Bb[BB_S0]); }
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
-    float *S = B[B_S0 + t], *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
-    float *SM = B[B_SM0 + t], *VM = B[B_VM0 + t], *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
-    float *T1 = B[B_T1], *T2 = B[B_T2];
+    float *S = B[B_S0 + t], *V = B[B_V0 + t], *PHI = phi32 ? B[B_PHI0 + t] : nullptr, *H1 = B[B_H10 + t];
+    float *SM = B[B_SM0], *VM = B[B_VM0], *H2 = B[B_H20 + t];
+    __half* PHIh = phih(t);
+    __half* UV = reinterpret_cast<__half*>(Bb[BB_UVH0 + t]);   // FP16 copies (range checked by the GEMMs)
+    __half* AV = reinterpret_cast<__half*>(Bb[BB_AVH0 + t]);
     bad |= gemm_bf16<1>(st, n, F, F, Bb[BB_S0 + t], F, L.W1b, L.b1, nullptr, 0, H1, F, Bb[BB_A1], F, status);
-    // phi = W2 silu(.) + b2, packed into PHI by the GEMM epilogue
+    // phi = W2 silu(.) + b2, packed into PHI (and its FP16 copy) by the GEMM epilogue
     bad |= gemm_bf16<4>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, V, 3 * F, PHI, 6 * F, nullptr, 0, status, PHIh);
     float* wst = (wstore && need_grad && !use_tc_bwd && !msg_mma) ? wstore + t * wstore_layer_floats : nullptr;
 #define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], wst)
@@ -1095,13 +1125,15 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
       }
     }
 #undef CTD_FWD
-    bad |= gemm_bf16<0>(st, 3 * n, 2 * F, F, Bb[BB_VM], F, L.UVb, nullptr, nullptr, 0, UV, 2 * F, nullptr, 0, status);
-    if (n > 0) { LaunchScope ls_(st); k_update_pre<<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, nullptr, Bb[BB_Z]); }
+    bad |= gemm_bf16<0>(st, 3 * n, 2 * F, F, Bb[BB_VM], F, L.UVb, nullptr, nullptr, 0, nullptr, 2 * F, nullptr, 0,
+                        status, UV);
+    if (n > 0) { LaunchScope ls_(st); k_update_pre<__half><<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, nullptr, Bb[BB_Z]); }
     bad |= gemm_bf16<1>(st, n, F, 2 * F, Bb[BB_Z], 2 * F, L.A1b, L.c1, nullptr, 0, H2, F, Bb[BB_A2], F, status);
-    bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A2], F, L.A2b, L.c2, nullptr, 0, AV, 3 * F, nullptr, 0, status);
+    bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A2], F, L.A2b, L.c2, nullptr, 0, nullptr, 3 * F, nullptr, 0, status, AV);
     if (n > 0) {
       LaunchScope ls_(st);
-      k_update_post<<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1], Bb[BB_S0 + t + 1]);
+      k_update_post<__half><<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1],
+                                                     Bb[BB_S0 + t + 1]);
     }
   }
   // The readout MLP (F -> F/2 -> 1, ~1 % of the node FLOPs) stays in FP32: its output is the
@@ -1118,10 +1150,13 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   if (n > 0) cudaMemsetAsync(B[B_GV], 0, sizeof(float) * (size_t)n * 3 * F, st);
   for (int t = T - 1; t >= 0; --t) {
     const LayerW& L = m.L[t];
-    float *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
-    float *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
-    float *T1 = B[B_T1], *T2 = B[B_T2], *T3 = B[B_T3];
+    float *V = B[B_V0 + t], *PHI = phi32 ? B[B_PHI0 + t] : nullptr, *H1 = B[B_H10 + t];
+    float* H2 = B[B_H20 + t];
+    const __half* UV = reinterpret_cast<const __half*>(Bb[BB_UVH0 + t]);
+    const __half* AV = reinterpret_cast<const __half*>(Bb[BB_AVH0 + t]);
+    float* T1 = B[B_T1];
     float *GS = B[B_GS], *GV = B[B_GV], *GSM = B[B_GSM], *GVM = B[B_GVM], *GPHI = B[B_GPHI];
+    const __half* PHIh = phih(t);
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_pre_bf16<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, Bb[BB_GA], Bb[BB_GUV]); }
     bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GA], 3 * F, L.A2tb, nullptr, H2, F, nullptr, 0, Bb[BB_GH2], F, status);
     bad |= gemm_bf16<0>(st, n, 2 * F, F, Bb[BB_GH2], F, L.A1tb, nullptr, nullptr, 0, T1, 2 * F, nullptr, 0, status);
@@ -1137,14 +1172,15 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
       if (use_tc_bwd) {
-        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, gphi, hedge, status, aend, G4);
+        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, gphi, hedge, status, aend, G4,
+                           phi32 ? nullptr : PHIh);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_BWD)
       }
     }
 #undef CTD_BWD
     if (t == 0) break;
-    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, V, GVM, nullptr, GV, Bb[BB_GP3]); }
+    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, PHIh, V, GVM, nullptr, GV, Bb[BB_GP3]); }
     bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GP3], 3 * F, L.W2tb, nullptr, H1, F, nullptr, 0, Bb[BB_GH1], F, status);
     bad |= gemm_bf16<2>(st, n, F, F, Bb[BB_GH1], F, L.W1tb, nullptr, GSM, F, GS, F, nullptr, 0, status);
   }

@@ -10,6 +10,11 @@ int prof_stage() { return g_prof ? g_prof->stage : STG_MISC; }
 void prof_set_stage(int s) {
   if (g_prof) g_prof->stage = s;
 }
+bool prof_recording() { return g_prof && g_prof->on; }
+// kernels launched by a CUDA graph replay, counted like individual launches (current stage)
+void prof_count_launches(int64_t k) {
+  if (g_prof) g_prof->launches[g_prof->stage] += k;
+}
 
 static cudaEvent_t take_event(ProfState* p) {
   if (!p->pool.empty()) {

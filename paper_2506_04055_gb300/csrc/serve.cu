@@ -190,6 +190,13 @@ struct ctd_server {
       b_scan, b_i32, b_d3;
   bool lists_dirty = true;
   std::string err;
+  // The step's device work after the rebuild decisions (prune, model, second kick, per-replica
+  // sums) as a CUDA graph: captured once the batch layout has stayed the same over one eager
+  // step, replayed while it stays the same (one graph launch instead of ~65 kernel launches).
+  bool use_graph = true;
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t gkey = 0, last_key = 0;
+  int64_t graph_kernels = 0, steps_graph = 0, steps_eager = 0, captures = 0;
   std::vector<DBuf*> bufs() {
     return {&rep_table, &rep_off, &rep_of_atom, &rep_flags, &rep_out, &rep_np, &rep_chain, &rep_ke, &rep_g, &rep_eth, &st_x, &st_xref, &st_v, &st_m, &st_z, &st_f,
             &b_xw, &b_wrap, &b_cell, &b_ccount, &b_cstart, &b_cursor, &b_tmp, &b_perm, &b_inv, &b_xws, &b_xnew,
@@ -206,6 +213,7 @@ int sfail(ctd_server* s, int code, const std::string& msg) {
 
 void free_buf(ctd_ctx* c, DBuf& b) {
   if (b.p) {
+    ++c->alloc_gen;
     cudaFree(b.p);
     c->held -= b.bytes;
     b.p = nullptr;
@@ -473,6 +481,98 @@ void release(ctd_server* s, Replica* R) {
 
 extern "C" {
 
+namespace {
+
+void drop_graph(ctd_server* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  s->gkey = 0;
+  s->graph_kernels = 0;
+}
+
+// Everything a captured step depends on besides device memory contents: the buffers (by their
+// allocation generation), the batch size and layout, the thermostat mode and the model options.
+uint64_t layout_key(const ctd_server* s, int64_t nres) {
+  const ctd_ctx* c = s->c;
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  mix(c->alloc_gen); mix((uint64_t)c->n); mix((uint64_t)nres); mix(s->any_nvt ? 1 : 0);
+  mix(c->mw.tc_adjoint); mix(c->mw.tc_adjoint_split); mix(c->mw.tc_message); mix((uint64_t)c->mw.edge_chunk_rows);
+  mix((uint64_t)c->desc.precision); mix(c->use_ew); mix(c->use_near);
+  return h == 0 ? 1 : h;
+}
+
+// Step part 5-6: prune, forces of the whole batch, second half kick, per-replica energies and
+// virial, thermostat half step.  No host synchronisation, so that it can be captured.
+int step_device(ctd_server* s, int64_t nres) {
+  ctd_ctx* c = s->c;
+  cudaStream_t st = c->st;
+  const int64_t N = c->n;
+  int r = prune(c, nullptr);
+  if (r) return r;
+  r = evaluate(c, true);
+  if (r) return r;
+  StageGuard sg(STG_MD);
+  {
+    LaunchScope ls_(st);
+    k_kick_masked<<<blk(N), kThreads, 0, st>>>(N, s->dt, P<float>(c->force_s), P<double>(c->md_m),
+                                               P<int32_t>(s->rep_of_atom), P<int32_t>(s->rep_flags),
+                                               P<double>(c->md_v));
+  }
+  {
+    LaunchScope ls_(st);
+    k_rep_reduce<<<(unsigned)nres, kThreads, 0, st>>>(P<int64_t>(s->rep_off), P<int32_t>(c->arow),
+                                                     P<float>(c->eatom), P<double>(c->md_m), P<double>(c->md_v),
+                                                     P<float4>(c->delta), P<float4>(c->ar), P<float4>(c->hedge), 1,
+                                                     P<double>(s->rep_out));
+  }
+  if (s->any_nvt) {
+    launch_rep_nhc_half(st, (int)nres, P<NhcParams>(s->rep_np), 0.5 * s->dt, P<double>(s->rep_out) + 1, 12,
+                        P<int32_t>(s->rep_flags), P<double>(s->rep_chain), kChainStride, P<double>(s->rep_g),
+                        P<double>(s->rep_ke), P<double>(s->rep_eth));
+    launch_scale_v_rep(st, N, P<int32_t>(s->rep_of_atom), P<double>(s->rep_g), P<double>(c->md_v));
+  }
+  return CTD_OK;
+}
+
+// Captures step_device into s->gexec; false (nothing launched, capture state cleared) if the
+// capture does not complete (a buffer would have had to grow, or a call is not capturable).
+bool capture_step(ctd_server* s, int64_t nres, uint64_t key) {
+  ctd_ctx* c = s->c;
+  drop_graph(s);
+  cudaGraph_t g = nullptr;
+  c->capturing = true;
+  int r = CTD_ERR_CUDA;
+  if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    r = step_device(s, nres);
+    if (cudaStreamEndCapture(c->st, &g) != cudaSuccess) r = CTD_ERR_CUDA;
+  }
+  c->capturing = false;
+  bool ok = r == CTD_OK && g && layout_key(s, nres) == key && cudaGraphInstantiate(&s->gexec, g, 0) == cudaSuccess;
+  if (ok) {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    int64_t kern = 0;
+    for (size_t k = 0; k < nn; ++k) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
+    }
+    s->graph_kernels = kern;
+    s->gkey = key;
+    ++s->captures;
+  } else {
+    s->gexec = nullptr;
+    cudaGetLastError();
+    c->err.clear();
+  }
+  if (g) cudaGraphDestroy(g);
+  return ok;
+}
+
+}  // namespace
+
 int ctd_serve_create(ctd_server** out, const ctd_model_desc* desc, const void* params, size_t nbytes,
                      size_t hbm_budget_bytes, int32_t max_replicas, double dt, void* cuda_stream) {
   // replicas index the y dimension of the list concatenation grid (at most 65,535)
@@ -497,6 +597,7 @@ int ctd_serve_create(ctd_server** out, const ctd_model_desc* desc, const void* p
 void ctd_serve_destroy(ctd_server* s) {
   if (!s) return;
   if (s->c) cudaStreamSynchronize(s->c->st);
+  drop_graph(s);
   for (auto& kv : s->reps) {
     release(s, kv.second);
     delete kv.second;
@@ -641,44 +742,38 @@ int ctd_serve_step(ctd_server* s, int32_t* n_resident, int32_t* n_admitted, int3
     int r = concat_lists(s);
     if (r) return r;
   }
-  // 5. forces of the whole batch
+  // 5. forces of the whole batch; 6. second half kick, per-replica energies and virial,
+  // thermostat half step from the kinetic energy after the kick and the velocity factor it
+  // gives (kinetic energy recorded after it).  Replayed as a CUDA graph while the layout holds.
   ENSURE(c, c->status, sizeof(int32_t) * 4);
   CUDA_OK(c, cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), st));
-  int r = prune(c, nullptr);
-  if (r) return r;
-  r = evaluate(c, true);
-  if (r) return r;
-  // 6. second half kick; per-replica energies and virial; thermostat half step from the kinetic
-  // energy after the kick and the velocity factor it gives (kinetic energy recorded after it)
-  {
-    StageGuard sg(STG_MD);
-    {
-      LaunchScope ls_(st);
-      k_kick_masked<<<blk(N), kThreads, 0, st>>>(N, s->dt, P<float>(c->force_s), P<double>(c->md_m),
-                                                 P<int32_t>(s->rep_of_atom), P<int32_t>(s->rep_flags),
-                                                 P<double>(c->md_v));
-    }
-    {
-      LaunchScope ls_(st);
-      k_rep_reduce<<<(unsigned)nres, kThreads, 0, st>>>(P<int64_t>(s->rep_off), P<int32_t>(c->arow),
-                                                       P<float>(c->eatom), P<double>(c->md_m), P<double>(c->md_v),
-                                                       P<float4>(c->delta), P<float4>(c->ar), P<float4>(c->hedge), 1,
-                                                       P<double>(s->rep_out));
-    }
-    if (s->any_nvt) {
-      launch_rep_nhc_half(st, (int)nres, P<NhcParams>(s->rep_np), 0.5 * s->dt, P<double>(s->rep_out) + 1, 12,
-                          P<int32_t>(s->rep_flags), P<double>(s->rep_chain), kChainStride, P<double>(s->rep_g),
-                          P<double>(s->rep_ke), P<double>(s->rep_eth));
-      launch_scale_v_rep(st, N, P<int32_t>(s->rep_of_atom), P<double>(s->rep_g), P<double>(c->md_v));
-    }
+  const bool graphable = s->use_graph && !c->local() && !prof_recording() &&
+                         !model_stores_edges(c->mw, c->desc.precision);
+  const uint64_t key = layout_key(s, nres);
+  bool launched = false;
+  if (graphable && s->gexec && s->gkey == key) {
+    CUDA_OK(c, cudaGraphLaunch(s->gexec, st));
+    launched = true;
+  } else if (graphable && key == s->last_key && capture_step(s, nres, key)) {
+    CUDA_OK(c, cudaGraphLaunch(s->gexec, st));
+    launched = true;
   }
+  if (launched) {
+    ++s->steps_graph;
+    prof_count_launches(s->graph_kernels);
+  } else {
+    int r = step_device(s, nres);
+    if (r) return r;
+    ++s->steps_eager;
+  }
+  s->last_key = layout_key(s, nres);
   CUDA_OK(c, cudaMemcpyAsync(ro.data(), s->rep_out.p, sizeof(double) * 12 * nres, cudaMemcpyDeviceToHost, st));
   std::vector<double> ke(s->any_nvt ? nres : 0), eth(s->any_nvt ? nres : 0);
   if (s->any_nvt) {
     CUDA_OK(c, cudaMemcpyAsync(ke.data(), s->rep_ke.p, sizeof(double) * nres, cudaMemcpyDeviceToHost, st));
     CUDA_OK(c, cudaMemcpyAsync(eth.data(), s->rep_eth.p, sizeof(double) * nres, cudaMemcpyDeviceToHost, st));
   }
-  r = check_status(c);
+  int r = check_status(c);
   if (r) return r;
   for (int64_t k = 0; k < nres; ++k) {
     Replica* R = s->resident[k];
@@ -788,6 +883,26 @@ int ctd_serve_stats(ctd_server* s, int64_t* resident_atoms, int32_t* resident_re
   if (resident_replicas) *resident_replicas = (int32_t)s->resident.size();
   if (queued) *queued = (int32_t)s->queue.size();
   if (bytes_held) *bytes_held = (int64_t)s->c->held;
+  return CTD_OK;
+}
+
+int ctd_serve_use_graph(ctd_server* s, int32_t enable) {
+  if (!s) return CTD_ERR_INVALID_ARG;
+  Bind bind_(s->c);
+  cudaStreamSynchronize(s->c->st);
+  s->use_graph = enable != 0;
+  drop_graph(s);
+  s->last_key = 0;
+  return CTD_OK;
+}
+
+int ctd_serve_graph_stats(ctd_server* s, int64_t* graph_steps, int64_t* eager_steps, int64_t* kernels_per_replay,
+                          int64_t* captures) {
+  if (!s) return CTD_ERR_INVALID_ARG;
+  if (graph_steps) *graph_steps = s->steps_graph;
+  if (eager_steps) *eager_steps = s->steps_eager;
+  if (kernels_per_replay) *kernels_per_replay = s->graph_kernels;
+  if (captures) *captures = s->captures;
   return CTD_OK;
 }
 

@@ -152,3 +152,46 @@ def test_small_large_small_equals_fresh_contexts(precision, width):
         assert c["stats"]["bytes_allocated"] == b["stats"]["bytes_allocated"]   # and never shrink
     for got, ref in ((a, ref_small), (b, ref_large), (c, ref_small)):
         _same(got, ref)
+
+
+def _offset(name, F, K, S):
+    off = 0
+    for nm, shape in syn.param_shapes(F, K, 1, S):
+        if nm == name:
+            return off
+        off += int(np.prod(shape))
+    raise KeyError(name)
+
+
+def test_fp16_storage_beyond_range_is_reported():
+    """The BF16 path stores the message table (F = 128 contraction), the U/V products and the
+    update coefficients in FP16; a value beyond FP16's largest finite value (65504) is reported
+    instead of turning into an Inf.  A message table beyond the range is reported only where it
+    is stored in FP16 (the CUDA-core message step keeps the FP32 table); update coefficients
+    beyond it are reported on either message step; the FP32 path computes both systems."""
+    eng = engine()
+    from paper_2506_04055_gb300 import _lib
+    Fb, Tb, Sb, K = 128, 1, 1, 20
+    sy = syn.fcc(3, 3, 3, jitter=0.05, seed=2)
+    base = syn.xavier_params(Fb, K, Tb, Sb, seed=5, bias_scale=0.1)
+    phi = base.copy()
+    o = _offset("b2_0", Fb, K, Sb)
+    phi[o:o + 3 * Fb] = 7.0e4                        # every phi channel beyond the FP16 range
+    coef = base.copy()
+    o = _offset("c2_0", Fb, K, Sb)
+    coef[o:o + 3 * Fb] = 7.0e4                       # every update coefficient beyond it
+    for vals, raises in ((phi, {1: True, 0: False}), (coef, {1: True, 0: True})):
+        blob = syn.params_blob(Fb, K, Tb, Sb, values=vals)
+        for msg in (1, 0):
+            with eng.Potential(Fb, K=K, T=Tb, n_species=Sb, precision="bf16", params=blob) as pot:
+                pot.set_option(_lib.CTD_OPT_TC_MESSAGE, msg)
+                if raises[msg]:
+                    with pytest.raises(eng.CtdError) as err:
+                        pot.compute(sy.species, sy.positions, sy.cell)
+                    assert err.value.code == _lib.CTD_ERR_NONFINITE and "FP16" in str(err.value)
+                else:
+                    out = pot.compute(sy.species, sy.positions, sy.cell)
+                    assert np.isfinite(out["energy"]) and np.isfinite(out["forces"]).all()
+        with eng.Potential(Fb, K=K, T=Tb, n_species=Sb, precision="fp32", params=blob) as pot:
+            out = pot.compute(sy.species, sy.positions, sy.cell)
+            assert np.isfinite(out["energy"]) and np.isfinite(out["forces"]).all()

@@ -342,3 +342,41 @@ def test_buffer_regrowth_mid_run_leaves_trajectories_unchanged():
         assert a["state"] == 2 and a["steps_done"] == 12
         for key in ("epot", "ekin", "positions", "velocities", "virial"):
             np.testing.assert_array_equal(a[key], b[key])
+
+
+@pytest.mark.parametrize("precision,Fw", [("fp32", 64), ("bf16", 128)])
+def test_graph_replay_equals_eager(precision, Fw):
+    """A step's device work replayed as a CUDA graph gives the trajectories of eager steps bit
+    for bit, across an admission, retirements and a Nose-Hoover replica; replays happen (the
+    layout holds between those events) and launch the whole model per replay."""
+    eng = engine()
+    vals = syn.xavier_params(Fw, 20, T, S, seed=9, bias_scale=0.1)
+    blob = syn.params_blob(Fw, 20, T, S, values=vals)
+    items = _replicas()
+
+    def run(graph):
+        srv = eng.Server(Fw, blob, T=T, n_species=S, precision=precision, dt=DT)
+        srv.use_graph(graph)
+        ids = [srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, 20 if k != 1 else 12, skin=1.0)
+               for k, (sy, v) in enumerate(items[:3])]
+        srv.set_thermostat(ids[1], 400.0, 20.0, 2)
+        for step in range(80):
+            if step == 6:
+                sy, v = items[3]
+                ids.append(srv.submit(sy.species, sy.masses, sy.positions, v, sy.cell, 10, skin=1.0))
+            srv.step()
+            if len(ids) == 4 and all(srv.poll(i)["state"] == 2 for i in ids):
+                break
+        res = [srv.poll(i) for i in ids]
+        gs = srv.graph_stats()
+        srv.close()
+        return res, gs
+
+    ra, ga = run(True)
+    rb, gb = run(False)
+    assert gb["graph_steps"] == 0 and ga["graph_steps"] >= 10 and ga["kernels_per_replay"] > 20, ga
+    for a, b in zip(ra, rb):
+        assert a["state"] == 2 and b["state"] == 2
+        np.testing.assert_array_equal(a["epot"], b["epot"])
+        np.testing.assert_array_equal(a["positions"], b["positions"])
+        np.testing.assert_array_equal(a["velocities"], b["velocities"])
