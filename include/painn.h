@@ -231,7 +231,7 @@ int ctd_profile_read(ctd_ctx *ctx, double *ms, int64_t *launches, int32_t reset)
  * tensor cores, operand tiles staged by TMA -- the contraction every MLP of the BF16 path
  * runs on.  Device pointers on the context's stream: A bf16 row-major with leading dimension
  * lda (elements, lda*2 a multiple of 16 bytes), B bf16 [N][K] row-major, C float row-major
- * with leading dimension ldc.  K: multiple of 64; N: multiple of 32, <= 512.  Synchronises
+ * with leading dimension ldc.  K: multiple of 32, >= 64; N: multiple of 32, <= 512.  Synchronises
  * the stream; CTD_ERR_TIMEOUT if a bounded device wait gave up. */
 int ctd_gemm_bf16(ctd_ctx *ctx, int64_t M, int32_t N, int32_t K, const void *A, int64_t lda,
                   const void *B, float *C, int64_t ldc);

@@ -834,7 +834,7 @@ int ctd_gemm_bf16(ctd_ctx* c, int64_t M, int32_t N, int32_t K, const void* A, in
   if (!c) return CTD_ERR_INVALID_ARG;
   Bind bind_(c);
   if (M < 0 || !gemm_bf16_supported(N, K) || (M > 0 && (!A || !B || !C)) || lda < K || ldc < N || ldc % 4)
-    return fail(c, CTD_ERR_INVALID_ARG, "gemm: K must be a multiple of 64, N of 32 (<= 512)");
+    return fail(c, CTD_ERR_INVALID_ARG, "gemm: K must be a multiple of 32 and at least 64, N a multiple of 32 (<= 512)");
   ENSURE(c, c->status, sizeof(int32_t) * 4);
   CUDA_OK(c, cudaMemsetAsync(c->status.p, 0, sizeof(int32_t), c->st));
   int r = gemm_bf16<0>(c->st, M, N, K, static_cast<const __nv_bfloat16*>(A), lda,

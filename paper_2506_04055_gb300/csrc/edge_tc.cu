@@ -350,24 +350,30 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
     Chunk C;
     for (int64_t k = (int64_t)blockIdx.x * NS + s; ok && chunk_at<NE>(p, k, C); k += nstreams) {
       int64_t r = C.r0;
-      float cur[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, nxt[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      auto fetch = [&](int64_t row, float (&o)[5]) {
+      // the row's table values (cur) and the next row's, prefetched as raw bits (nxt: FP32, or
+      // FP16 in the low half) and converted only when that row begins, one row after the load
+      const bool th = p.PHIh != nullptr;
+      float cur[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      uint32_t nxt[5] = {0u, 0u, 0u, 0u, 0u};
+      auto fetch = [&](int64_t row, uint32_t (&o)[5]) {
         if (row < C.r1) {
-          if (p.PHIh) {
+          if (th) {
             const __half* pj = p.PHIh + row * 6 * kF + f;
 #pragma unroll
             for (int kk = 0; kk < 5; ++kk)
-              if (!L0 || kk == 0 || kk == 4) {
-                o[kk] = __half2float(__ldg(pj + kk * kF));
-                asm volatile("" : "+f"(o[kk]));   // converted once here, not again at every use
-              }
+              if (!L0 || kk == 0 || kk == 4) o[kk] = __half_as_ushort(__ldg(pj + kk * kF));
           } else {
             const float* pj = p.PHI + row * 6 * kF + f;
 #pragma unroll
             for (int kk = 0; kk < 5; ++kk)
-              if (!L0 || kk == 0 || kk == 4) o[kk] = __ldg(pj + kk * kF);
+              if (!L0 || kk == 0 || kk == 4) o[kk] = __float_as_uint(__ldg(pj + kk * kF));
           }
         }
+      };
+      auto take = [&]() {
+#pragma unroll
+        for (int kk = 0; kk < 5; ++kk)
+          cur[kk] = th ? __half2float(__ushort_as_half((unsigned short)nxt[kk])) : __uint_as_float(nxt[kk]);
       };
       float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
       auto flush = [&]() {
@@ -377,11 +383,11 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         }
         gps = gy0 = gy1 = gy2 = gpvs = 0.f;
         ++r;
-#pragma unroll
-        for (int kk = 0; kk < 5; ++kk) cur[kk] = nxt[kk];
+        take();
         fetch(r + 1, nxt);
       };
-      fetch(r, cur);
+      fetch(r, nxt);
+      take();
       fetch(r + 1, nxt);
       while (r < C.r1 && p.arow[r + 1] == C.e0) flush();
       for (int t = 0; t < C.ntiles; ++t, ++it) {

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __gr
                                                       const __grid_constant__ CUtensorMap tmB, GemmBf16Args p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const int KB = p.K / kBlockK;
+  const int KB = (p.K + kBlockK - 1) / kBlockK;   // a ragged last block is zero-filled by the TMA
   const int N = p.N;
   unsigned char* sB = smem;                                        // KB x N x 128 B
   unsigned char* sA = sB + (size_t)KB * N * 128;                   // a_stages x 16 KB
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __gr
 
   if (warp == 0) {
     if (lane == 0) {
-      umma::mbar_expect_tx(bbar, (uint32_t)(N * p.K * 2));
+      umma::mbar_expect_tx(bbar, (uint32_t)(N * KB * kBlockK * 2));   // whole boxes, fill included
       for (int kb = 0; kb < KB; ++kb)
         for (int r0 = 0; r0 < N; r0 += p.b_box_rows)
           umma::tma_load_2d(sB + (size_t)kb * N * 128 + (size_t)r0 * 128, &tmB, kb * kBlockK, r0, bbar);
@@ -314,7 +314,9 @@ static int num_sms() {
   return n;
 }
 
-bool gemm_bf16_supported(int N, int K) { return K % 64 == 0 && K > 0 && N % 32 == 0 && N > 0 && N <= 512; }
+// K: a multiple of 32, at least one 64-column block (the tensor map's box is never wider than the
+// tensor); a last half block reads zeros past column K, which add nothing to the product.
+bool gemm_bf16_supported(int N, int K) { return K % 32 == 0 && K >= 64 && N % 32 == 0 && N > 0 && N <= 512; }
 
 template <int EPI>
 int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t lda, const bf16* W,
@@ -335,7 +337,7 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
   p.b_box_rows = N % 64 == 0 ? 64 : 32;
   p.n_chunk = N <= 256 ? N : N / 2;
   if (p.n_chunk > 256 || p.n_chunk % 16) return -1;
-  const int KB = K / kBlockK;
+  const int KB = (K + kBlockK - 1) / kBlockK;
   const size_t b_bytes = (size_t)KB * N * 128;
   const size_t t_bytes = (size_t)kEpiWarps * 32 * kTP * sizeof(float);
   const size_t limit = 227 * 1024 - 1024 - 256 - t_bytes;

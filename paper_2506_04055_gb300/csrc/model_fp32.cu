@@ -213,24 +213,44 @@ __global__ void k_phi_pack(int64_t n, int F, const float* __restrict__ P3, const
 __device__ __forceinline__ float ldx(const float* p) { return *p; }
 __device__ __forceinline__ float ldx(const __half* p) { return __half2float(*p); }
 
-// Z = [s^m ; sqrt(sum_a Vv_a^2 + eps)], UV rows (i, a) = [Uv_a | Vv_a]
+// Four consecutive features per thread (F is a multiple of 4): 16-byte FP32 and 8-byte FP16 or
+// BF16 accesses instead of one scalar per thread.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld4(const __half* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+
+// Z = [s^m ; sqrt(sum_a Vv_a^2 + eps)], UV rows (i, a) = [Uv_a | Vv_a]; thread = 4 features
 template <typename TX>
 __global__ void k_update_pre(int64_t n, int F, float eps, const float* __restrict__ SM,
                              const TX* __restrict__ UV, float* __restrict__ Z, __nv_bfloat16* __restrict__ Zb) {
+  const int F4 = F >> 2;
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= n * F) return;
-  int64_t i = idx / F;
-  int f = (int)(idx % F);
+  if (idx >= n * F4) return;
+  const int64_t i = idx / F4;
+  const int f = 4 * (int)(idx % F4);
   const TX* uv = UV + i * 3 * 2 * F;
-  float v0 = ldx(uv + F + f), v1 = ldx(uv + 2 * F + F + f), v2 = ldx(uv + 4 * F + F + f);
-  const float nv = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
+  const float4 v0 = ld4(uv + F + f), v1 = ld4(uv + 3 * F + f), v2 = ld4(uv + 5 * F + f);
+  const float4 sm = ld4(SM + i * F + f);
+  const float4 nv = make_float4(sqrtf(v0.x * v0.x + v1.x * v1.x + v2.x * v2.x + eps),
+                                sqrtf(v0.y * v0.y + v1.y * v1.y + v2.y * v2.y + eps),
+                                sqrtf(v0.z * v0.z + v1.z * v1.z + v2.z * v2.z + eps),
+                                sqrtf(v0.w * v0.w + v1.w * v1.w + v2.w * v2.w + eps));
   if (Z) {
-    Z[i * 2 * F + f] = SM[idx];
-    Z[i * 2 * F + F + f] = nv;
+    st4(Z + i * 2 * F + f, sm);
+    st4(Z + i * 2 * F + F + f, nv);
   }
   if (Zb) {
-    Zb[i * 2 * F + f] = __float2bfloat16_rn(SM[idx]);
-    Zb[i * 2 * F + F + f] = __float2bfloat16_rn(nv);
+    st4(Zb + i * 2 * F + f, sm);
+    st4(Zb + i * 2 * F + F + f, nv);
   }
 }
 
@@ -347,20 +367,33 @@ __global__ void k_update_bwd_mid_bf16(int64_t n, int F, float eps, const float* 
                                       const float* __restrict__ GZ, const __half* __restrict__ UV,
                                       const __half* __restrict__ AV, float* __restrict__ Gsm,
                                       __nv_bfloat16* __restrict__ GUVb) {
+  const int F4 = F >> 2;   // thread = 4 features
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= n * F) return;
-  int64_t i = idx / F;
-  int f = (int)(idx % F);
+  if (idx >= n * F4) return;
+  const int64_t i = idx / F4;
+  const int f = 4 * (int)(idx % F4);
   const __half* uv = UV + i * 6 * F;
-  const float v0 = ldx(uv + F + f), v1 = ldx(uv + 3 * F + f), v2 = ldx(uv + 5 * F + f);
-  const float nv = sqrtf(v0 * v0 + v1 * v1 + v2 * v2 + eps);
-  const float g = GZ[i * 2 * F + F + f] / nv;
-  const float gs = GS[idx];
-  const float gsp = gs * ldx(AV + i * 3 * F + F + f);
-  Gsm[idx] = gs + GZ[i * 2 * F + f];
-  GUVb[i * 6 * F + F + f] = __float2bfloat16_rn(gsp * ldx(uv + f) + g * v0);
-  GUVb[i * 6 * F + 3 * F + f] = __float2bfloat16_rn(gsp * ldx(uv + 2 * F + f) + g * v1);
-  GUVb[i * 6 * F + 5 * F + f] = __float2bfloat16_rn(gsp * ldx(uv + 4 * F + f) + g * v2);
+  const float4 v0 = ld4(uv + F + f), v1 = ld4(uv + 3 * F + f), v2 = ld4(uv + 5 * F + f);
+  const float4 u0 = ld4(uv + f), u1 = ld4(uv + 2 * F + f), u2 = ld4(uv + 4 * F + f);
+  const float4 gzs = ld4(GZ + i * 2 * F + f), gzn = ld4(GZ + i * 2 * F + F + f);
+  const float4 gs = ld4(GS + i * F + f), asv = ld4(AV + i * 3 * F + F + f);
+  float4 o0, o1, o2;
+  auto one = [&](float x0, float x1, float x2, float y0, float y1, float y2, float gn, float g_s, float a_sv,
+                 float& r0, float& r1, float& r2) {
+    const float nv = sqrtf(x0 * x0 + x1 * x1 + x2 * x2 + eps);
+    const float g = gn / nv, gsp = g_s * a_sv;
+    r0 = gsp * y0 + g * x0;
+    r1 = gsp * y1 + g * x1;
+    r2 = gsp * y2 + g * x2;
+  };
+  one(v0.x, v1.x, v2.x, u0.x, u1.x, u2.x, gzn.x, gs.x, asv.x, o0.x, o1.x, o2.x);
+  one(v0.y, v1.y, v2.y, u0.y, u1.y, u2.y, gzn.y, gs.y, asv.y, o0.y, o1.y, o2.y);
+  one(v0.z, v1.z, v2.z, u0.z, u1.z, u2.z, gzn.z, gs.z, asv.z, o0.z, o1.z, o2.z);
+  one(v0.w, v1.w, v2.w, u0.w, u1.w, u2.w, gzn.w, gs.w, asv.w, o0.w, o1.w, o2.w);
+  st4(Gsm + i * F + f, make_float4(gs.x + gzs.x, gs.y + gzs.y, gs.z + gzs.z, gs.w + gzs.w));
+  st4(GUVb + i * 6 * F + F + f, o0);
+  st4(GUVb + i * 6 * F + 3 * F + f, o1);
+  st4(GUVb + i * 6 * F + 5 * F + f, o2);
 }
 
 // G4[i][f] = (gsm_i,f, gvm_i,0,f, gvm_i,1,f, gvm_i,2,f): the receivers' gradients interleaved per
@@ -956,7 +989,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
   edge_smem_setup();
   StageGuard node_stage(STG_NODE);
   const int F = m.F, T = m.T, Fh = F / 2;
-  const unsigned nb = blocks_for(n * F);
+  const unsigned nb = blocks_for(n * F), nb4 = blocks_for(n * F / 4);   // nb4: four features per thread
   if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], nullptr); }
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
@@ -977,7 +1010,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
 #undef CTD_FWD
     // update
     gemm<EPI_BIAS>(st, 3 * n, 2 * F, F, VM, F, L.UVt, nullptr, nullptr, 0, UV, 2 * F);
-    if (n > 0) { LaunchScope ls_(st); k_update_pre<float><<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1, nullptr); }
+    if (n > 0) { LaunchScope ls_(st); k_update_pre<float><<<nb4, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1, nullptr); }
     gemm<EPI_BIAS_SILU>(st, n, F, 2 * F, T1, 2 * F, L.A1t, L.c1, nullptr, 0, H2, F, T2, F);
     gemm<EPI_BIAS>(st, n, 3 * F, F, T2, F, L.A2t, L.c2, nullptr, 0, AV, 3 * F);
     if (n > 0) { LaunchScope ls_(st); k_update_post<float><<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1], nullptr); }
@@ -1088,7 +1121,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   edge_smem_setup();
   StageGuard node_stage(STG_NODE);
   const int F = m.F, T = m.T, Fh = F / 2;
-  const unsigned nb = blocks_for(n * F);
+  const unsigned nb = blocks_for(n * F), nb4 = blocks_for(n * F / 4);   // nb4: four features per thread
   int bad = 0;
   // F = 128: the message step as the tensor-core contraction over each receiver's edges
   // (edge_mma.cu) and the adjoint with the radial filter on tcgen05 (edge_tc.cu), unless the
@@ -1127,7 +1160,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
 #undef CTD_FWD
     bad |= gemm_bf16<0>(st, 3 * n, 2 * F, F, Bb[BB_VM], F, L.UVb, nullptr, nullptr, 0, nullptr, 2 * F, nullptr, 0,
                         status, UV);
-    if (n > 0) { LaunchScope ls_(st); k_update_pre<__half><<<nb, kThreads, 0, st>>>(n, F, m.eps, SM, UV, nullptr, Bb[BB_Z]); }
+    if (n > 0) { LaunchScope ls_(st); k_update_pre<__half><<<nb4, kThreads, 0, st>>>(n, F, m.eps, SM, UV, nullptr, Bb[BB_Z]); }
     bad |= gemm_bf16<1>(st, n, F, 2 * F, Bb[BB_Z], 2 * F, L.A1b, L.c1, nullptr, 0, H2, F, Bb[BB_A2], F, status);
     bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A2], F, L.A2b, L.c2, nullptr, 0, nullptr, 3 * F, nullptr, 0, status, AV);
     if (n > 0) {
@@ -1162,7 +1195,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     bad |= gemm_bf16<0>(st, n, 2 * F, F, Bb[BB_GH2], F, L.A1tb, nullptr, nullptr, 0, T1, 2 * F, nullptr, 0, status);
     // the bulk-gathered tensor-core adjoint reads gsm and gvm interleaved per feature (G4)
     float* G4 = g4 ? B[B_G4] : nullptr;
-    if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid_bf16<<<nb, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, AV, GSM, Bb[BB_GUV]); }
+    if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid_bf16<<<nb4, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, AV, GSM, Bb[BB_GUV]); }
     bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
     if (G4 && n > 0) { LaunchScope ls_(st); k_interleave_g4<<<nb, kThreads, 0, st>>>(n, F, GSM, GVM, reinterpret_cast<float4*>(G4)); }
     const float* wst = (wstore && !use_tc_bwd && !msg_mma) ? wstore + t * wstore_layer_floats : nullptr;

@@ -1,7 +1,8 @@
 """The tcgen05 BF16 GEMM building block (ctd_gemm_bf16) against a float64 product of the same
 BF16 operands.  BF16 x BF16 products are exact in FP32; only the FP32 accumulation rounds, so
 the relative error bound is ~K * 2^-24 of the sum of |products|.  Shapes cover every (N, K) the
-node MLPs use for F = 64 and F = 128, ragged M tails, and multiple persistent tiles per CTA."""
+node MLPs use for F = 64 and F = 128, K that ends in half a 64-column block (zero-filled by the
+TMA), ragged M tails, and multiple persistent tiles per CTA."""
 import ctypes
 
 import numpy as np
@@ -12,7 +13,7 @@ from gpu_common import engine
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(64, 64), (128, 128), (256, 128), (384, 128), (128, 256), (128, 384), (192, 64), (32, 128),
-          (64, 128), (128, 64), (256, 64), (64, 192)]
+          (64, 128), (128, 64), (256, 64), (64, 192), (64, 96), (32, 96), (96, 160)]
 
 
 @pytest.mark.parametrize("N,K", SHAPES)
