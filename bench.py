@@ -640,25 +640,46 @@ def _local_cpu_baseline():
 
 def run_local96k(args):
     """96,000-atom water (32,000 H2O) with the strictly local equivariant edge model (Allegro
-    form, l <= 1): F=64 latent, C=16 channels, L=2 layers, FP32; NVE dt 0.5 fs from 300 K."""
+    form, l <= 1): F=64 latent, C=16 channels, L=2 layers; NVE dt 0.5 fs from 300 K.  The BF16
+    path (dense edge GEMMs on tcgen05) is the headline, the FP32 path beside it, with the BF16
+    forces' relative RMSE against the FP32 path's on the first frame."""
     import synthetic as syn
     eng, torch = _init_engine()
     Fl, Ll, Sl, Cl = 64, 2, 2, 16
     steps = args.steps if args.steps_given else 50
-    sy = syn.water_box(32000, seed=0)
+    sy = syn.water_box(args.local_waters, seed=0)
     v0 = syn.maxwell_boltzmann(sy.masses, 300.0, seed=0)
     blob = syn.local_params_blob(Fl, K, Ll, Sl, Cl, rc=RC, seed=0)
-    with eng.Potential(Fl, K=K, T=Ll, n_species=Sl, rc=RC, params=blob, family="local", channels=Cl,
-                       stream=torch.cuda.current_stream().cuda_stream) as pot:
-        st = pot.compute(sy.species, sy.positions, sy.cell, stats=True)["stats"]
-        pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=1.0)
-        res = _timed_md(pot, torch, steps, max(3, args.warmup), 0.5)
-    cfg = {"workload": f"water 32,000 H2O ({sy.n:,} atoms), L={sy.cell[0, 0]:.2f} A; strictly local edge model "
+    res, st, frames = {}, {}, {}
+    precs = ("fp32", "bf16") if args.local_precision == "both" else (args.local_precision,)
+    for prec in precs:
+        with eng.Potential(Fl, K=K, T=Ll, n_species=Sl, rc=RC, params=blob, family="local", channels=Cl,
+                           precision=prec, stream=torch.cuda.current_stream().cuda_stream) as pot:
+            out = pot.compute(sy.species, sy.positions, sy.cell, stats=True)
+            st[prec], frames[prec] = out["stats"], out["forces"]
+            pot.md_set_state(sy.species, sy.masses, sy.positions, v0, sy.cell, skin=1.0)
+            res[prec] = _timed_md(pot, torch, steps, max(3, args.warmup), 0.5)
+    if len(precs) == 1:   # one precision only (profiling runs): its own line
+        r = res[precs[0]]
+        cfg = {"workload": f"water {args.local_waters:,} H2O ({sy.n:,} atoms); strictly local edge model F=64, C=16, L=2",
+               "precision": precs[0], "active_edges": st[precs[0]]["n_active_edges"]}
+        print(json.dumps(_md_line("atom-steps/s, 96k-atom water NVE, strictly local model", sy.n, steps,
+                                  max(3, args.warmup), r, "bf16" if precs[0] == "bf16" else "f32", cfg, {})),
+              flush=True)
+        return
+    d = frames["bf16"] - frames["fp32"]
+    f_rmse = float(np.sqrt((d ** 2).sum() / (frames["fp32"] ** 2).sum()))
+    cfg = {"workload": f"water {args.local_waters:,} H2O ({sy.n:,} atoms), L={sy.cell[0, 0]:.2f} A; strictly local edge model "
                        f"F=64, C=16, L=2, K=20, rc=5 A, skin=1 A; NVE dt=0.5 fs, 300 K",
-           "precision": "fp32", "l2": "inputs larger than L2", "active_edges": st["n_active_edges"],
-           "bytes_held": st["bytes_allocated"]}
-    line = _md_line("atom-steps/s, 96k-atom water NVE, strictly local model (FP32), p50/p99", sy.n, steps,
-                    max(3, args.warmup), res, "f32", cfg, {})
+           "precision": "bf16", "l2": "inputs larger than L2", "active_edges": st["bf16"]["n_active_edges"],
+           "bytes_held": st["bf16"]["bytes_allocated"]}
+    line = _md_line("atom-steps/s, 96k-atom water NVE, strictly local model (BF16 tensor-core GEMMs vs FP32), p50/p99",
+                    sy.n, steps, max(3, args.warmup), res["bf16"], "bf16", cfg, {})
+    r = res["fp32"]
+    line["fp32"] = {"value": sy.n * steps / (r["total_ms"] / 1e3), "ms_per_step": r["total_ms"] / steps,
+                    "p50_ms": _pct(r["step_ms"], 0.5), "p99_ms": _pct(r["step_ms"], 0.99),
+                    "stage_ms_per_step": r["stage_ms_per_step"], "bytes_held": st["fp32"]["bytes_allocated"]}
+    line["bf16_vs_fp32_force_rmse"] = f_rmse
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _local_cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -961,6 +982,10 @@ def main():
     ap.add_argument("--replicas", type=int, default=512)
     ap.add_argument("--serve-steps", type=int, default=20)
     ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--local-precision", default="both", choices=["both", "fp32", "bf16"],
+                    help="local96k: both precisions (BF16 headline) or one of them")
+    ap.add_argument("--local-waters", type=int, default=32000,
+                    help="local96k: water molecules in the box (32,000 = 96,000 atoms; fewer for profiling)")
     ap.add_argument("--serve-budget-gib", type=float, default=16.0)
     ap.add_argument("--serial-replicas", type=int, default=64)
     args = ap.parse_args()

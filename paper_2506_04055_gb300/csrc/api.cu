@@ -278,7 +278,10 @@ size_t model_bytes_per_atom(const ctd_ctx* c) {
   if (c->local()) {   // per-edge arrays at 64 active edges per atom (water and fcc at rc = 5 A: ~50)
     LocalW w = c->lw;
     w.F = F; w.L = T; w.C = c->desc.channels; w.S = c->desc.n_species;
-    w.KA = (c->desc.K + 2 * w.S + 3) / 4 * 4;
+    w.bf16 = c->desc.precision == CTD_PREC_BF16;
+    w.KA = local_ka(c->desc.K, w.S, w.bf16);
+    w.KAb = w.KA < 64 ? 64 : w.KA;
+    w.Kh = F / 2 < 64 ? 64 : F / 2;
     return sizeof(float) * (size_t)local_buffer_floats(w, 1, 64);
   }
   size_t bytes = 0;
@@ -312,9 +315,12 @@ int evaluate_local(ctd_ctx* c, bool need_grad) {
   ENSURE(c, c->out_w, sizeof(double) * 9);
   const float* ew = c->use_ew ? P<float>(c->ew) : nullptr;
   c->last_stored = false;
-  local_forward_backward(st, c->lw, n, E, P<int32_t>(c->z_s), P<int32_t>(c->arow), P<int32_t>(c->acol),
-                         P<float4>(c->ar), P<float>(c->lbuf), need_grad, ew, P<double>(c->epart), kPartials,
-                         P<float>(c->eatom), P<float4>(c->hedge));
+  ENSURE(c, c->status, sizeof(int32_t) * 4);
+  const int bad = local_forward_backward(st, c->lw, n, E, P<int32_t>(c->z_s), P<int32_t>(c->arow),
+                                         P<int32_t>(c->acol), P<float4>(c->ar), P<float>(c->lbuf), need_grad, ew,
+                                         P<double>(c->epart), kPartials, P<float>(c->eatom), P<float4>(c->hedge),
+                                         P<int>(c->status));
+  if (bad) return fail(c, CTD_ERR_INVALID_ARG, "local model, BF16 path: unsupported GEMM shape");
   StageGuard sg(STG_FORCES);
   if (need_grad) {
     if (E == 0) CUDA_OK(c, cudaMemsetAsync(c->hedge.p, 0, sizeof(float4), st));
@@ -440,7 +446,8 @@ int load_local_params(ctd_ctx* c, const char* b, size_t nbytes) {
   const ctd_model_desc& d = c->desc;
   if (hdr[0] != 1 || F != d.F || K != d.K || L != d.T || S != d.n_species || C != d.channels || rc != d.rc)
     return fail(c, CTD_ERR_INVALID_ARG, "parameter blob header does not match the model description");
-  const int C2 = 2 * C, FX = F + C2, Fh = F / 2, KA0 = K + 2 * S, KA = (KA0 + 3) / 4 * 4;
+  const bool bf16 = d.precision == CTD_PREC_BF16;
+  const int C2 = 2 * C, FX = F + C2, Fh = F / 2, KA0 = K + 2 * S, KA = local_ka(K, S, bf16);
   int64_t expect = (int64_t)KA0 * F + F + (int64_t)F * C2 + (int64_t)F * Fh + Fh + Fh + 1;
   for (int l = 1; l <= L; ++l) expect += (int64_t)F * C2 + (int64_t)FX * F + F + (l < L ? 2 * C2 * C : 0);
   if (nval != expect || nbytes < 64 + (size_t)nval * 8)
@@ -501,6 +508,44 @@ int load_local_params(ctd_ctx* c, const char* b, size_t nbytes) {
     q.Gv = l < L ? base + o.Gv : nullptr; q.Gvt = l < L ? base + o.Gvt : nullptr;
   }
   w.R1 = base + oR1; w.R1t = base + oR1t; w.d1 = base + od1; w.R2 = base + oR2; w.d2 = base + od2;
+  w.bf16 = bf16;
+  if (bf16) {
+    // BF16 GEMM operands W [N][K]: forward the [out][in] arrays, adjoint the [in][out] ones, each
+    // row zero-padded to at least 64 columns
+    w.KAb = KA < 64 ? 64 : KA;
+    w.Kh = Fh < 64 ? 64 : Fh;
+    std::vector<uint16_t> hb;
+    auto put = [&](size_t off, int rows, int cols, int kpad) {
+      size_t o = (hb.size() + 7) / 8 * 8;   // 16-byte aligned rows
+      hb.resize(o + (size_t)rows * kpad, 0);
+      for (int r = 0; r < rows; ++r)
+        for (int k = 0; k < cols; ++k) hb[o + (size_t)r * kpad + k] = to_bf16_bits(h[off + (size_t)r * cols + k]);
+      return o;
+    };
+    // the transposed arrays are stored [cols][prow]: A0t [F][KA], P0t [2C][F], Qt [2C][F],
+    // Mt [F][FX], R1t [F/2][F]; the plain ones [rows][cols]: A0 [KA][F], P0 [F][2C], Q [F][2C],
+    // M [FX][F], R1 [F][F/2]
+    const size_t bA0t = put(oA0t, F, KA, w.KAb), bP0t = put(oP0t, C2, F, F), bR1t = put(oR1t, Fh, F, F);
+    const size_t bA0 = put(oA0, KA, F, F), bP0 = put(oP0, F, C2, 64 > C2 ? 64 : C2), bR1 = put(oR1, F, Fh, w.Kh);
+    size_t bQt[kMaxT], bMt[kMaxT], bQ[kMaxT], bM[kMaxT];
+    for (int l = 1; l <= L; ++l) {
+      const LOff& o = lo[l - 1];
+      bQt[l - 1] = put(o.Qt, C2, F, F);
+      bMt[l - 1] = put(o.Mt, F, FX, FX);
+      bQ[l - 1] = put(o.Q, F, C2, 64 > C2 ? 64 : C2);
+      bM[l - 1] = put(o.M, FX, F, F);
+    }
+    ENSURE(c, c->params_bf, hb.size() * sizeof(uint16_t));
+    CUDA_OK(c, cudaMemcpyAsync(c->params_bf.p, hb.data(), hb.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, c->st));
+    CUDA_OK(c, cudaStreamSynchronize(c->st));
+    const __nv_bfloat16* bb = P<__nv_bfloat16>(c->params_bf);
+    w.wb.A0t = bb + bA0t; w.wb.P0t = bb + bP0t; w.wb.R1t = bb + bR1t;
+    w.wb.A0 = bb + bA0; w.wb.P0 = bb + bP0; w.wb.R1 = bb + bR1;
+    for (int l = 1; l <= L; ++l) {
+      w.wb.Qt[l - 1] = bb + bQt[l - 1]; w.wb.Mt[l - 1] = bb + bMt[l - 1];
+      w.wb.Q[l - 1] = bb + bQ[l - 1]; w.wb.M[l - 1] = bb + bM[l - 1];
+    }
+  }
   c->e_scale = esc;
   c->have_params = true;
   return CTD_OK;
@@ -662,7 +707,11 @@ int ctd_create(ctd_ctx** out, const ctd_model_desc* desc, size_t hbm_budget_byte
     const int C = desc->channels;
     if (F < 8 || F > 256 || F % 8 != 0 || C < 4 || C > 64 || C % 4 != 0 || desc->K < 2 || desc->K > kMaxKP ||
         desc->T < 1 || desc->T > kMaxT || desc->n_species < 1 || desc->n_species > 64 || !(desc->rc > 0.0) ||
-        desc->precision != CTD_PREC_FP32)
+        (desc->precision != CTD_PREC_FP32 && desc->precision != CTD_PREC_BF16))
+      return CTD_ERR_INVALID_ARG;
+    // BF16: every tensor-core GEMM width (F, F/2, 2C, F + 2C, the padded two-body input) a
+    // multiple of 32
+    if (desc->precision == CTD_PREC_BF16 && (!bf16_available() || !(F == 64 || F == 128) || C % 16 != 0))
       return CTD_ERR_INVALID_ARG;
   } else if (desc->family != CTD_FAMILY_PAINN ||
              !(F == 32 || F == 64 || F == 128 || F == 256) || desc->K < 2 || desc->K > kMaxKP || desc->T < 0 ||

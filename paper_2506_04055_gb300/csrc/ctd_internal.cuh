@@ -119,20 +119,34 @@ struct LocalLayerW {
   const float *Q, *Qt, *M, *Mt, *m;      // [F][2C], [2C][F], [F+2C][F], [F][F+2C], [F]
   const float *Gs, *Gst, *Gv, *Gvt;      // [2C][C], [C][2C] (layers l < L)
 };
+// BF16 copies of the local model's weights for the tensor-core GEMM (C = A W^T, W [N][K]):
+// forward W = the [out][in] matrices, backward W = the [in][out] ones; K below 64 is zero-padded
+// to 64 columns (KAb for the two-body input, 64 for the 2C- and F/2-wide gradients).
+struct LocalWb {
+  const __nv_bfloat16 *A0t, *P0t, *R1t, *A0, *P0, *R1;   // [F][KAb], [2C][F], [F/2][F], [KA][F], [F][64], [F][Kh]
+  const __nv_bfloat16 *Qt[kMaxT], *Mt[kMaxT], *Q[kMaxT], *M[kMaxT];   // [2C][F], [F][F+2C], [F][64], [F+2C][F]
+};
 struct LocalW {
   int F, K, KA, L, S, C;
   float rc, e_scale;
   const float *A0, *A0t, *c0, *P0, *P0t;  // [KA][F], [F][KA], [F], [F][2C], [2C][F]
   LocalLayerW Lw[kMaxT];
   const float *R1, *R1t, *d1, *R2, *d2;   // [F][F/2], [F/2][F], [F/2], [F/2], [1]
+  bool bf16 = false;                      // BF16 path: the edge GEMMs on tcgen05 (weights wb)
+  int KAb = 0, Kh = 0;                    // padded K of the two-body input and of the F/2 gradient
+  LocalWb wb{};
 };
+// Width of the two-body input rows: K + 2S rounded up to 4 (FP32) or to 32 (BF16, where it is a
+// GEMM output width in the adjoint).
+inline int local_ka(int K, int S, bool bf16) { return bf16 ? (K + 2 * S + 31) / 32 * 32 : (K + 2 * S + 3) / 4 * 4; }
 // Device floats the local model needs for n atoms and E active edges.
 int64_t local_buffer_floats(const LocalW& w, int64_t n, int64_t E);
-// Energy partials, per-atom energies, and (need_grad) hedge = -dE/dr_e per active edge.
-void local_forward_backward(cudaStream_t st, const LocalW& w, int64_t n, int64_t E, const int32_t* species_s,
-                            const int32_t* arow, const int32_t* acol, const float4* ar, float* buf,
-                            bool need_grad, const float* ew, double* energy_partials, int n_energy_partials,
-                            float* e_atom, float4* hedge);
+// Energy partials, per-atom energies, and (need_grad) hedge = -dE/dr_e per active edge.  Nonzero
+// if the BF16 path's GEMM rejected a shape (nothing is computed wrongly: the call fails).
+int local_forward_backward(cudaStream_t st, const LocalW& w, int64_t n, int64_t E, const int32_t* species_s,
+                           const int32_t* arow, const int32_t* acol, const float4* ar, float* buf,
+                           bool need_grad, const float* ew, double* energy_partials, int n_energy_partials,
+                           float* e_atom, float4* hedge, int* status);
 // Forces F_i = sum_{e in row i} (hedge[rev e] - hedge[e]) and virial partials sum_e r_e (x) hedge[e].
 void launch_forces(cudaStream_t st, int64_t n, const int32_t* arow, const float4* ar, const int32_t* arev,
                    const float4* hedge, float* force, double* vpart, int n_vpart, int* status);

@@ -23,6 +23,18 @@ namespace {
 
 constexpr float kPiF = 3.14159265358979323846f;
 
+// Eight FP32 values as one 16-byte store of BF16 (a thread writing its own edge's row: one
+// store per 8 columns instead of one per column)
+__device__ __forceinline__ void st8_bf16(__nv_bfloat16* p, const float (&v)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    w[j] = *reinterpret_cast<const uint32_t*>(&b);
+  }
+  *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 inline unsigned nblocks(int64_t w) { return (unsigned)((w + kThreads - 1) / kThreads); }
 
 // Per-edge and per-atom arrays, carved from one allocation (128-byte aligned pieces).
@@ -37,7 +49,11 @@ struct LocalBufs {
   // adjoint
   float *gzh, *gx, *gxc, *gts, *gtv, *gs[2], *gv[2], *gom, *gw0, *gin, *ggamS, *ggamV;
   float4* gg;                         // [E]: (dE/df_c, dE/du)
+  // BF16 path: the tensor-core GEMMs' A operands, rows zero-padded to >= 64 columns
+  __nv_bfloat16 *inb, *Xb[kMaxT + 1], *gzhb, *gomb, *gw0b, *gxb;   // [E][KAb], [E][F+2C], [E][Kh], [E][Kc] x2, [E][F]
 };
+
+inline int local_kc(const LocalW& w) { return 2 * w.C < 64 ? 64 : 2 * w.C; }   // padded K of 2C-wide gradients
 
 struct Carver {
   float* base;
@@ -87,6 +103,19 @@ int64_t carve(const LocalW& w, int64_t n, int64_t E, float* base, LocalBufs* b) 
   b->gg = reinterpret_cast<float4*>(cv.take(E * 4));
   b->ggamS = cv.take(n * C);
   b->ggamV = cv.take(n * 3 * C);
+  auto tb = [&](int64_t cnt) { return reinterpret_cast<__nv_bfloat16*>(cv.take((cnt + 1) / 2)); };
+  if (w.bf16) {
+    const int64_t Kc = local_kc(w);
+    b->inb = tb(E * w.KAb);
+    for (int l = 0; l <= w.L; ++l) b->Xb[l] = tb(E * FX);
+    b->gzhb = tb(E * w.Kh);
+    b->gomb = tb(E * Kc);
+    b->gw0b = tb(E * Kc);
+    b->gxb = tb(E * F);
+  } else {
+    b->inb = b->gzhb = b->gomb = b->gw0b = b->gxb = nullptr;
+    for (int l = 0; l <= w.L; ++l) b->Xb[l] = nullptr;
+  }
   return cv.off;
 }
 
@@ -99,9 +128,11 @@ __global__ void k_loc_erow(int64_t n, const int32_t* __restrict__ arow, int32_t*
 
 // geo[e] = (d, f_c, f_c', u_x, u_y, u_z, 0, 0); in[e] = [b_k(d) f_c (K) | onehot Z_i | onehot Z_j | 0].
 // b_k = exp(-(d - k sigma)^2 / (2 sigma^2)), sigma = rc / (K - 1); f_c = (cos(pi d / rc) + 1) / 2.
+// (inb: the same row in BF16, KAb >= KA columns (a multiple of 32), zeros after KA; may be null)
 __global__ void k_loc_geom(int64_t E, int K, int S, int KA, float rc, const float4* __restrict__ ar,
                            const int32_t* __restrict__ acol, const int32_t* __restrict__ erow,
-                           const int32_t* __restrict__ Z, float* __restrict__ geo, float* __restrict__ in) {
+                           const int32_t* __restrict__ Z, float* __restrict__ geo, float* __restrict__ in,
+                           __nv_bfloat16* __restrict__ inb, int KAb) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
   const float4 r = ar[e];
@@ -123,8 +154,27 @@ __global__ void k_loc_geom(int64_t E, int K, int S, int KA, float rc, const floa
   }
   for (int k = K; k < KA; ++k) row[k] = 0.0f;
   const int zi = Z[erow[e]], zj = Z[acol[e]];
-  if (zi >= 0 && zi < S) row[K + zi] = 1.0f;
-  if (zj >= 0 && zj < S) row[K + S + zj] = 1.0f;
+  const bool zi_ok = zi >= 0 && zi < S, zj_ok = zj >= 0 && zj < S;
+  if (zi_ok) row[K + zi] = 1.0f;
+  if (zj_ok) row[K + S + zj] = 1.0f;
+  if (inb) {
+    for (int k0 = 0; k0 < KAb; k0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k = k0 + j;
+        const float t = d - (float)k * sig;
+        v[j] = k < K ? expf(-t * t * c) * fc : (((zi_ok && k == K + zi) || (zj_ok && k == K + S + zj)) ? 1.0f : 0.0f);
+      }
+      st8_bf16(inb + e * KAb + k0, v);
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // s[e][c] = w0[e][c], v[e][a][c] = w0[e][C+c] u_a
@@ -166,7 +216,7 @@ __global__ void k_loc_env(int64_t n, int C, const int32_t* __restrict__ arow, co
 // ts[e] = [s Gs_i | v . Gv_i] (row stride ld), tv[e][a] = [s Gv_i[a] | v[a] Gs_i] (may be null)
 __global__ void k_loc_tp(int64_t E, int C, const int32_t* __restrict__ erow, const float* __restrict__ S,
                          const float* __restrict__ V, const float* __restrict__ gamS, const float* __restrict__ gamV,
-                         float* __restrict__ ts, int ld, float* __restrict__ tv) {
+                         float* __restrict__ ts, int ld, float* __restrict__ tv, __nv_bfloat16* __restrict__ tsb) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= E * C) return;
   const int64_t e = idx / C;
@@ -176,8 +226,13 @@ __global__ void k_loc_tp(int64_t E, int C, const int32_t* __restrict__ erow, con
   const float v0 = V[(e * 3 + 0) * C + c], v1 = V[(e * 3 + 1) * C + c], v2 = V[(e * 3 + 2) * C + c];
   const float gs = gamS[i * C + c];
   const float g0 = gamV[(i * 3 + 0) * C + c], g1 = gamV[(i * 3 + 1) * C + c], g2 = gamV[(i * 3 + 2) * C + c];
-  ts[e * ld + c] = s * gs;
-  ts[e * ld + C + c] = fmaf(v2, g2, fmaf(v1, g1, v0 * g0));
+  const float t0 = s * gs, t1 = fmaf(v2, g2, fmaf(v1, g1, v0 * g0));
+  ts[e * ld + c] = t0;
+  ts[e * ld + C + c] = t1;
+  if (tsb) {   // BF16 copy, same row stride
+    tsb[e * ld + c] = __float2bfloat16_rn(t0);
+    tsb[e * ld + C + c] = __float2bfloat16_rn(t1);
+  }
   if (tv) {
     float* t = tv + e * 6 * C;
     t[0 * 2 * C + c] = s * g0;
@@ -190,8 +245,10 @@ __global__ void k_loc_tp(int64_t E, int C, const int32_t* __restrict__ erow, con
 }
 
 // E_i = e_scale w_i sum_{e in row i} f_c (h_e . R2 + d2); FP64 Neumaier sums per block.
+// (H = silu(ZH) as stored, or computed here from ZH when H is null)
 __global__ void k_loc_readout(int64_t n, int Fh, float e_scale, const int32_t* __restrict__ arow,
-                              const float* __restrict__ geo, const float* __restrict__ H, const float* __restrict__ R2,
+                              const float* __restrict__ geo, const float* __restrict__ H,
+                              const float* __restrict__ ZH, const float* __restrict__ R2,
                               const float* __restrict__ d2, const float* __restrict__ ew, float* __restrict__ e_atom,
                               double* __restrict__ partials) {
   __shared__ double sbuf[kThreads / 32];
@@ -200,7 +257,7 @@ __global__ void k_loc_readout(int64_t n, int Fh, float e_scale, const int32_t* _
     float e = 0.0f;
     for (int64_t q = arow[i]; q < arow[i + 1]; ++q) {
       float y = d2[0];
-      for (int k = 0; k < Fh; ++k) y = fmaf(R2[k], H[q * Fh + k], y);
+      for (int k = 0; k < Fh; ++k) y = fmaf(R2[k], H ? H[q * Fh + k] : silu_f(ZH[q * Fh + k]), y);
       e = fmaf(geo[q * 8 + 1], y, e);
     }
     e *= e_scale;
@@ -223,29 +280,48 @@ __global__ void k_loc_readout(int64_t n, int Fh, float e_scale, const int32_t* _
 
 // ---------------------------------------------------------------------------- adjoint kernels
 // Seed g = e_scale w_i per edge: dE/df_c = g (h . R2 + d2) starts gg; g_zh = g f_c R2 silu'(zh).
+// One warp per edge (lanes over the F/2 columns; h . R2 summed by a shuffle tree).
 __global__ void k_loc_readout_bwd(int64_t E, int Fh, float e_scale, const int32_t* __restrict__ erow,
                                   const float* __restrict__ geo, const float* __restrict__ H,
                                   const float* __restrict__ ZH, const float* __restrict__ R2,
                                   const float* __restrict__ d2, const float* __restrict__ ew, float* __restrict__ gzh,
-                                  float4* __restrict__ gg) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                                  float4* __restrict__ gg, __nv_bfloat16* __restrict__ gzhb, int Kh) {
+  const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (e >= E) return;
   const float g = ew ? e_scale * ew[erow[e]] : e_scale;
   const float fc = geo[e * 8 + 1];
-  float y = d2[0];
-  for (int k = 0; k < Fh; ++k) y = fmaf(R2[k], H[e * Fh + k], y);
-  gg[e] = make_float4(g * y, 0.0f, 0.0f, 0.0f);
+  float y = 0.0f;
+  for (int k = lane; k < Fh; k += 32) y = fmaf(R2[k], H ? H[e * Fh + k] : silu_f(ZH[e * Fh + k]), y);
+  y = warp_sum(y) + d2[0];
+  if (lane == 0) gg[e] = make_float4(g * y, 0.0f, 0.0f, 0.0f);
   const float a = g * fc;
-  for (int k = 0; k < Fh; ++k) gzh[e * Fh + k] = a * R2[k] * dsilu_f(ZH[e * Fh + k]);
+  const int kend = gzhb ? Kh : Fh;
+  for (int k = lane; k < kend; k += 32) {
+    const float v = k < Fh ? a * R2[k] * dsilu_f(ZH[e * Fh + k]) : 0.0f;
+    if (k < Fh) gzh[e * Fh + k] = v;
+    if (gzhb) gzhb[e * Kh + k] = __float2bfloat16_rn(v);
+  }
 }
 
-// dst[e][f] = src[e][f] (row stride lds) * silu'(Z[e][f]); dst may equal src when lds == F.
-__global__ void k_loc_mul_dsilu(int64_t E, int F, const float* src, int lds, const float* __restrict__ Z, float* dst) {
+// dst[e][f] = src[e][f] (row stride lds) * silu'(Z[e][f]); dst may equal src when lds == F;
+// dstb (may be null) receives a BF16 copy.  Four features per thread (F and lds multiples of 4).
+__global__ void k_loc_mul_dsilu(int64_t E, int F, const float* src, int lds, const float* __restrict__ Z, float* dst,
+                                __nv_bfloat16* __restrict__ dstb) {
+  const int F4 = F >> 2;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= E * F) return;
-  const int64_t e = idx / F;
-  const int f = (int)(idx % F);
-  dst[e * F + f] = src[e * lds + f] * dsilu_f(Z[e * F + f]);
+  if (idx >= E * F4) return;
+  const int64_t e = idx / F4;
+  const int f = 4 * (int)(idx % F4);
+  const float4 x = *reinterpret_cast<const float4*>(src + e * lds + f);
+  const float4 z = *reinterpret_cast<const float4*>(Z + e * F + f);
+  const float4 v = make_float4(x.x * dsilu_f(z.x), x.y * dsilu_f(z.y), x.z * dsilu_f(z.z), x.w * dsilu_f(z.w));
+  *reinterpret_cast<float4*>(dst + e * F + f) = v;
+  if (dstb) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    *reinterpret_cast<uint2*>(dstb + e * F + f) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+  }
 }
 
 // Edge side of the tensor-product adjoint: g_s = g_ts0 Gs + g_tv0 . Gv, g_v[a] = g_ts1 Gv[a] + g_tv1[a] Gs.
@@ -311,27 +387,46 @@ __global__ void k_loc_tp_bwd_atom(int64_t n, int C, const int32_t* __restrict__ 
 
 // Environment sums, reversed: g_om[c] = f_c g_Gs[c], g_om[C+c] = f_c (g_Gv[c] . u);
 // dE/df_c += om[c] g_Gs[c] + om[C+c] (g_Gv[c] . u);  dE/du += f_c om[C+c] g_Gv[c].
+// One thread per edge, 8 channels at a time (C: a multiple of 4; of 16 when gomb is written).
 __global__ void k_loc_env_bwd(int64_t E, int C, const int32_t* __restrict__ erow, const float* __restrict__ geo,
                               const float* __restrict__ om, const float* __restrict__ ggamS,
-                              const float* __restrict__ ggamV, float* __restrict__ gom, float4* __restrict__ gg) {
+                              const float* __restrict__ ggamV, float* __restrict__ gom, float4* __restrict__ gg,
+                              __nv_bfloat16* __restrict__ gomb, int Kc) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int64_t i = erow[e];
   const float* g = geo + e * 8;
   const float fc = g[1], u0 = g[3], u1 = g[4], u2 = g[5];
   float gfc = 0.0f, gu0 = 0.0f, gu1 = 0.0f, gu2 = 0.0f;
-  for (int c = 0; c < C; ++c) {
-    const float gs = ggamS[i * C + c];
-    const float q0 = ggamV[(i * 3 + 0) * C + c], q1 = ggamV[(i * 3 + 1) * C + c], q2 = ggamV[(i * 3 + 2) * C + c];
-    const float o0 = om[e * 2 * C + c], o1 = om[e * 2 * C + C + c];
-    const float gd = fmaf(q2, u2, fmaf(q1, u1, q0 * u0));
-    gom[e * 2 * C + c] = fc * gs;
-    gom[e * 2 * C + C + c] = fc * gd;
-    gfc = fmaf(o0, gs, fmaf(o1, gd, gfc));
-    const float t = fc * o1;
-    gu0 = fmaf(t, q0, gu0);
-    gu1 = fmaf(t, q1, gu1);
-    gu2 = fmaf(t, q2, gu2);
+  for (int c0 = 0; c0 < C; c0 += 8) {
+    float va[8], vb[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + j;
+      va[j] = vb[j] = 0.0f;
+      if (c >= C) continue;
+      const float gs = ggamS[i * C + c];
+      const float q0 = ggamV[(i * 3 + 0) * C + c], q1 = ggamV[(i * 3 + 1) * C + c], q2 = ggamV[(i * 3 + 2) * C + c];
+      const float o0 = om[e * 2 * C + c], o1 = om[e * 2 * C + C + c];
+      const float gd = fmaf(q2, u2, fmaf(q1, u1, q0 * u0));
+      va[j] = fc * gs;
+      vb[j] = fc * gd;
+      gom[e * 2 * C + c] = va[j];
+      gom[e * 2 * C + C + c] = vb[j];
+      gfc = fmaf(o0, gs, fmaf(o1, gd, gfc));
+      const float t = fc * o1;
+      gu0 = fmaf(t, q0, gu0);
+      gu1 = fmaf(t, q1, gu1);
+      gu2 = fmaf(t, q2, gu2);
+    }
+    if (gomb) {
+      st8_bf16(gomb + e * Kc + c0, va);
+      st8_bf16(gomb + e * Kc + C + c0, vb);
+    }
+  }
+  if (gomb) {
+    const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 2 * C; k0 < Kc; k0 += 8) st8_bf16(gomb + e * Kc + k0, z);
   }
   float4 a = gg[e];
   a.x += gfc; a.y += gu0; a.z += gu1; a.w += gu2;
@@ -339,22 +434,40 @@ __global__ void k_loc_env_bwd(int64_t E, int C, const int32_t* __restrict__ erow
 }
 
 // Initial features, reversed: g_w0[c] = g_s[c], g_w0[C+c] = g_v[c] . u;  dE/du += w0[C+c] g_v[c].
+// One thread per edge, 8 channels at a time (C: a multiple of 4; of 16 when gw0b is written).
 __global__ void k_loc_init_bwd(int64_t E, int C, const float* __restrict__ w0, const float* __restrict__ geo,
                                const float* __restrict__ GS, const float* __restrict__ GV, float* __restrict__ gw0,
-                               float4* __restrict__ gg) {
+                               float4* __restrict__ gg, __nv_bfloat16* __restrict__ gw0b, int Kc) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
   const float* g = geo + e * 8;
   const float u0 = g[3], u1 = g[4], u2 = g[5];
   float gu0 = 0.0f, gu1 = 0.0f, gu2 = 0.0f;
-  for (int c = 0; c < C; ++c) {
-    const float q0 = GV[(e * 3 + 0) * C + c], q1 = GV[(e * 3 + 1) * C + c], q2 = GV[(e * 3 + 2) * C + c];
-    gw0[e * 2 * C + c] = GS[e * C + c];
-    gw0[e * 2 * C + C + c] = fmaf(q2, u2, fmaf(q1, u1, q0 * u0));
-    const float wv = w0[e * 2 * C + C + c];
-    gu0 = fmaf(wv, q0, gu0);
-    gu1 = fmaf(wv, q1, gu1);
-    gu2 = fmaf(wv, q2, gu2);
+  for (int c0 = 0; c0 < C; c0 += 8) {
+    float va[8], vb[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + j;
+      va[j] = vb[j] = 0.0f;
+      if (c >= C) continue;
+      const float q0 = GV[(e * 3 + 0) * C + c], q1 = GV[(e * 3 + 1) * C + c], q2 = GV[(e * 3 + 2) * C + c];
+      va[j] = GS[e * C + c];
+      vb[j] = fmaf(q2, u2, fmaf(q1, u1, q0 * u0));
+      gw0[e * 2 * C + c] = va[j];
+      gw0[e * 2 * C + C + c] = vb[j];
+      const float wv = w0[e * 2 * C + C + c];
+      gu0 = fmaf(wv, q0, gu0);
+      gu1 = fmaf(wv, q1, gu1);
+      gu2 = fmaf(wv, q2, gu2);
+    }
+    if (gw0b) {
+      st8_bf16(gw0b + e * Kc + c0, va);
+      st8_bf16(gw0b + e * Kc + C + c0, vb);
+    }
+  }
+  if (gw0b) {
+    const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 2 * C; k0 < Kc; k0 += 8) st8_bf16(gw0b + e * Kc + k0, z);
   }
   float4 a = gg[e];
   a.y += gu0; a.z += gu1; a.w += gu2;
@@ -393,51 +506,85 @@ int64_t local_buffer_floats(const LocalW& w, int64_t n, int64_t E) {
   return carve(w, n, E, nullptr, &b) + 32;
 }
 
-void local_forward_backward(cudaStream_t st, const LocalW& w, int64_t n, int64_t E, const int32_t* species_s,
+int local_forward_backward(cudaStream_t st, const LocalW& w, int64_t n, int64_t E, const int32_t* species_s,
                             const int32_t* arow, const int32_t* acol, const float4* ar, float* buf,
                             bool need_grad, const float* ew, double* energy_partials, int n_energy_partials,
-                            float* e_atom, float4* hedge) {
+                            float* e_atom, float4* hedge, int* status) {
   const int F = w.F, C = w.C, C2 = 2 * w.C, FX = w.F + 2 * w.C, Fh = w.F / 2, L = w.L, KA = w.KA;
+  const bool bf = w.bf16;   // BF16 path: the dense edge GEMMs on tcgen05 (BF16 operands, FP32 accumulation)
+  const int Kc = local_kc(w), Kh = w.Kh, KAb = w.KAb;
+  int bad = 0;   // a GEMM shape the tensor-core GEMM rejects (checked on the host)
   LocalBufs b;
   carve(w, n, E, buf, &b);
   StageGuard fwd_stage(STG_EDGE_FWD);   // the whole forward is edge work
   if (E > 0) {
     { LaunchScope ls_(st); k_loc_erow<<<nblocks(n), kThreads, 0, st>>>(n, arow, b.erow); }
-    { LaunchScope ls_(st); k_loc_geom<<<nblocks(E), kThreads, 0, st>>>(E, w.K, w.S, KA, w.rc, ar, acol, b.erow, species_s, b.geo, b.in); }
-    gemm_f32(st, 1, E, F, KA, b.in, KA, w.A0, w.c0, nullptr, 0, b.z0, F, b.X[0], FX);
-    gemm_f32(st, 0, E, C2, F, b.X[0], FX, w.P0, nullptr, nullptr, 0, b.w0, C2, nullptr, 0);
+    {
+      LaunchScope ls_(st);
+      k_loc_geom<<<nblocks(E), kThreads, 0, st>>>(E, w.K, w.S, KA, w.rc, ar, acol, b.erow, species_s, b.geo, b.in,
+                                                  b.inb, KAb);
+    }
+    if (bf) {
+      bad |= gemm_bf16<1>(st, E, F, KAb, b.inb, KAb, w.wb.A0t, w.c0, nullptr, 0, b.z0, F, b.Xb[0], FX, status);
+      bad |= gemm_bf16<0>(st, E, C2, F, b.Xb[0], FX, w.wb.P0t, nullptr, nullptr, 0, b.w0, C2, nullptr, 0, status);
+    } else {
+      gemm_f32(st, 1, E, F, KA, b.in, KA, w.A0, w.c0, nullptr, 0, b.z0, F, b.X[0], FX);
+      gemm_f32(st, 0, E, C2, F, b.X[0], FX, w.P0, nullptr, nullptr, 0, b.w0, C2, nullptr, 0);
+    }
     { LaunchScope ls_(st); k_loc_init<<<nblocks(E * C), kThreads, 0, st>>>(E, C, b.w0, b.geo, b.S[0], b.V[0]); }
     for (int l = 1; l <= L; ++l) {
       const LocalLayerW& lw = w.Lw[l - 1];
-      gemm_f32(st, 0, E, C2, F, b.X[l - 1], FX, lw.Q, nullptr, nullptr, 0, b.OM[l], C2, nullptr, 0);
+      if (bf)
+        bad |= gemm_bf16<0>(st, E, C2, F, b.Xb[l - 1], FX, w.wb.Qt[l - 1], nullptr, nullptr, 0, b.OM[l], C2, nullptr, 0, status);
+      else
+        gemm_f32(st, 0, E, C2, F, b.X[l - 1], FX, lw.Q, nullptr, nullptr, 0, b.OM[l], C2, nullptr, 0);
       { LaunchScope ls_(st); k_loc_env<<<nblocks(n * C), kThreads, 0, st>>>(n, C, arow, b.geo, b.OM[l], b.gamS[l], b.gamV[l]); }
       {
         LaunchScope ls_(st);
         k_loc_tp<<<nblocks(E * C), kThreads, 0, st>>>(E, C, b.erow, b.S[l - 1], b.V[l - 1], b.gamS[l], b.gamV[l],
-                                                      b.X[l - 1] + F, FX, l < L ? b.TV[l] : nullptr);
+                                                      b.X[l - 1] + F, FX, l < L ? b.TV[l] : nullptr,
+                                                      bf ? b.Xb[l - 1] + F : nullptr);
       }
-      gemm_f32(st, 1, E, F, FX, b.X[l - 1], FX, lw.M, lw.m, nullptr, 0, b.Z[l], F, b.X[l], FX);
-      if (l < L) {
+      if (bf)
+        bad |= gemm_bf16<1>(st, E, F, FX, b.Xb[l - 1], FX, w.wb.Mt[l - 1], lw.m, nullptr, 0, b.Z[l], F, b.Xb[l], FX, status);
+      else
+        gemm_f32(st, 1, E, F, FX, b.X[l - 1], FX, lw.M, lw.m, nullptr, 0, b.Z[l], F, b.X[l], FX);
+      if (l < L) {   // the 2C -> C channel mixings stay on the SIMT GEMM (N = C below a tensor-core tile)
         gemm_f32(st, 0, E, C, C2, b.X[l - 1] + F, FX, lw.Gs, nullptr, nullptr, 0, b.S[l], C, nullptr, 0);
         gemm_f32(st, 0, 3 * E, C, C2, b.TV[l], C2, lw.Gv, nullptr, nullptr, 0, b.V[l], C, nullptr, 0);
       }
     }
-    gemm_f32(st, 1, E, Fh, F, b.X[L], FX, w.R1, w.d1, nullptr, 0, b.zh, Fh, b.h, Fh);
+    if (bf)   // zh only; the readout applies silu itself
+      bad |= gemm_bf16<0>(st, E, Fh, F, b.Xb[L], FX, w.wb.R1t, w.d1, nullptr, 0, b.zh, Fh, nullptr, 0, status);
+    else
+      gemm_f32(st, 1, E, Fh, F, b.X[L], FX, w.R1, w.d1, nullptr, 0, b.zh, Fh, b.h, Fh);
   }
+  const float* H = bf ? nullptr : b.h;
   {
     LaunchScope ls_(st);
-    k_loc_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, w.e_scale, arow, b.geo, b.h, w.R2, w.d2, ew, e_atom,
-                                                          energy_partials);
+    k_loc_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, w.e_scale, arow, b.geo, H, b.zh, w.R2, w.d2, ew,
+                                                          e_atom, energy_partials);
   }
-  if (!need_grad || E == 0) return;
+  if (!need_grad || E == 0) return bad;
   StageGuard bwd_stage(STG_EDGE_BWD);
-  { LaunchScope ls_(st); k_loc_readout_bwd<<<nblocks(E), kThreads, 0, st>>>(E, Fh, w.e_scale, b.erow, b.geo, b.h, b.zh, w.R2, w.d2, ew, b.gzh, b.gg); }
-  gemm_f32(st, 3, E, F, Fh, b.gzh, Fh, w.R1t, nullptr, b.Z[L], F, b.gx, F, nullptr, 0);   // g_z of layer L
+  {
+    LaunchScope ls_(st);
+    k_loc_readout_bwd<<<nblocks(E * 32), kThreads, 0, st>>>(E, Fh, w.e_scale, b.erow, b.geo, H, b.zh, w.R2, w.d2, ew,
+                                                       b.gzh, b.gg, b.gzhb, Kh);
+  }
+  // g_z of layer L
+  if (bf)
+    bad |= gemm_bf16<3>(st, E, F, Kh, b.gzhb, Kh, w.wb.R1, nullptr, b.Z[L], F, b.gx, F, b.gxb, F, status);
+  else
+    gemm_f32(st, 3, E, F, Fh, b.gzh, Fh, w.R1t, nullptr, b.Z[L], F, b.gx, F, nullptr, 0);
   float *gs_in = b.gs[0], *gv_in = b.gv[0], *gs_out = b.gs[1], *gv_out = b.gv[1];
   for (int l = L; l >= 1; --l) {
     const LocalLayerW& lw = w.Lw[l - 1];
     // [g_x^{l-1} | g_ts] = g_z M_l^T
-    gemm_f32(st, 0, E, FX, F, b.gx, F, lw.Mt, nullptr, nullptr, 0, b.gxc, FX, nullptr, 0);
+    if (bf)
+      bad |= gemm_bf16<0>(st, E, FX, F, b.gxb, F, w.wb.M[l - 1], nullptr, nullptr, 0, b.gxc, FX, nullptr, 0, status);
+    else
+      gemm_f32(st, 0, E, FX, F, b.gx, F, lw.Mt, nullptr, nullptr, 0, b.gxc, FX, nullptr, 0);
     const float* gts = b.gxc + F;
     int ldg = FX;
     const float* gtv = nullptr;
@@ -458,19 +605,36 @@ void local_forward_backward(cudaStream_t st, const LocalW& w, int64_t n, int64_t
       k_loc_tp_bwd_atom<<<nblocks(n * C), kThreads, 0, st>>>(n, C, arow, b.S[l - 1], b.V[l - 1], gts, ldg, gtv, b.ggamS,
                                                              b.ggamV);
     }
-    { LaunchScope ls_(st); k_loc_env_bwd<<<nblocks(E), kThreads, 0, st>>>(E, C, b.erow, b.geo, b.OM[l], b.ggamS, b.ggamV, b.gom, b.gg); }
+    {
+      LaunchScope ls_(st);
+      k_loc_env_bwd<<<nblocks(E), kThreads, 0, st>>>(E, C, b.erow, b.geo, b.OM[l], b.ggamS, b.ggamV, b.gom, b.gg,
+                                                     b.gomb, Kc);
+    }
     // g_x^{l-1} = g_xc[:, 0:F] + g_om Q_l^T
-    gemm_f32(st, 2, E, F, C2, b.gom, C2, lw.Qt, nullptr, b.gxc, FX, b.gx, F, nullptr, 0);
-    if (l > 1) { LaunchScope ls_(st); k_loc_mul_dsilu<<<nblocks(E * F), kThreads, 0, st>>>(E, F, b.gx, F, b.Z[l - 1], b.gx); }
+    if (bf)
+      bad |= gemm_bf16<2>(st, E, F, Kc, b.gomb, Kc, w.wb.Q[l - 1], nullptr, b.gxc, FX, b.gx, F, nullptr, 0, status);
+    else
+      gemm_f32(st, 2, E, F, C2, b.gom, C2, lw.Qt, nullptr, b.gxc, FX, b.gx, F, nullptr, 0);
+    if (l > 1) {
+      LaunchScope ls_(st);
+      k_loc_mul_dsilu<<<nblocks(E * F / 4), kThreads, 0, st>>>(E, F, b.gx, F, b.Z[l - 1], b.gx, b.gxb);
+    }
     std::swap(gs_in, gs_out);
     std::swap(gv_in, gv_out);
   }
   // gs_in, gv_in: gradients of the initial edge features
-  { LaunchScope ls_(st); k_loc_init_bwd<<<nblocks(E), kThreads, 0, st>>>(E, C, b.w0, b.geo, gs_in, gv_in, b.gw0, b.gg); }
-  gemm_f32(st, 2, E, F, C2, b.gw0, C2, w.P0t, nullptr, b.gx, F, b.gxc, FX, nullptr, 0);   // g_x0
-  { LaunchScope ls_(st); k_loc_mul_dsilu<<<nblocks(E * F), kThreads, 0, st>>>(E, F, b.gxc, FX, b.z0, b.gx); }
-  gemm_f32(st, 0, E, KA, F, b.gx, F, w.A0t, nullptr, nullptr, 0, b.gin, KA, nullptr, 0);
+  { LaunchScope ls_(st); k_loc_init_bwd<<<nblocks(E), kThreads, 0, st>>>(E, C, b.w0, b.geo, gs_in, gv_in, b.gw0, b.gg, b.gw0b, Kc); }
+  if (bf)   // g_x0
+    bad |= gemm_bf16<2>(st, E, F, Kc, b.gw0b, Kc, w.wb.P0, nullptr, b.gx, F, b.gxc, FX, nullptr, 0, status);
+  else
+    gemm_f32(st, 2, E, F, C2, b.gw0, C2, w.P0t, nullptr, b.gx, F, b.gxc, FX, nullptr, 0);
+  { LaunchScope ls_(st); k_loc_mul_dsilu<<<nblocks(E * F / 4), kThreads, 0, st>>>(E, F, b.gxc, FX, b.z0, b.gx, b.gxb); }
+  if (bf)
+    bad |= gemm_bf16<0>(st, E, KA, F, b.gxb, F, w.wb.A0, nullptr, nullptr, 0, b.gin, KA, nullptr, 0, status);
+  else
+    gemm_f32(st, 0, E, KA, F, b.gx, F, w.A0t, nullptr, nullptr, 0, b.gin, KA, nullptr, 0);
   { LaunchScope ls_(st); k_loc_geom_bwd<<<nblocks(E), kThreads, 0, st>>>(E, w.K, w.rc, b.geo, b.gin, KA, b.gg, hedge); }
+  return bad;
 }
 
 }  // namespace ctd

@@ -191,3 +191,32 @@ def test_spatial_decomposition_one_hop(loc, orc, grid):
     owned, cands = expected_counts(orc, sy.positions, sy.cell, grid, 5.0 + 1.0)
     assert [d["n_owned"] for d in info] == owned
     assert [d["n_candidates"] for d in info] == cands
+
+
+@pytest.mark.parametrize("case", ["water192_F64", "fcc256_F128"])
+def test_bf16_tensor_core_path_matches_oracle(loc, case):
+    """BF16 path: the dense edge GEMMs (two-body MLP, latent update, channel projections, readout
+    and their adjoints) on the tcgen05 GEMM with BF16 operands and FP32 accumulation, the rest
+    FP32.  Against the FP64 oracle at the BF16 force bar (relative force RMSE <= 1e-2)."""
+    from gpu_common import rel_force_rmse, virial_rel
+    if case == "water192_F64":
+        sy, F, L, S, C = syn.water_box(64, seed=0), 64, 2, 2, 16
+    else:
+        sy, F, L, S, C = syn.fcc(4, 4, 4, jitter=0.05, seed=1), 128, 2, 1, 32
+    eng = engine()
+    vals, blob = _model(F, L, S, C, seed=11, bias=0.1)
+    ref = loc.local_model(vals, F, K, L, S, C, sy.species, sy.positions, sy.cell)
+    with eng.Potential(F, K=K, T=L, n_species=S, params=blob, family="local", channels=C, precision="bf16") as pot:
+        out = pot.compute(sy.species, sy.positions, sy.cell, energies=True)
+    fr = rel_force_rmse(out["forces"], ref["forces"])
+    scale = float(np.sqrt(np.mean(ref["energies"] ** 2)))
+    er = abs(out["energy"] - ref["energy"]) / sy.n / scale
+    wr = virial_rel(out["virial"], ref["virial"])
+    print(f"local bf16 {case}: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
+    assert fr <= 1e-2 and er <= 1e-2 and wr <= 2e-2, (fr, er, wr)
+
+
+def test_bf16_rejects_channel_counts_off_the_tensor_core_tiles():
+    eng = engine()
+    with pytest.raises(eng.CtdError):
+        eng.Potential(64, K=K, T=2, n_species=2, family="local", channels=8, precision="bf16")
