@@ -34,6 +34,11 @@ __device__ __forceinline__ void st8_bf16(__nv_bfloat16* p, const float (&v)[8]) 
   }
   *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
 }
+__device__ __forceinline__ float4 ld4f(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4_bf16(__nv_bfloat16* p, float4 v) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
 
 inline unsigned nblocks(int64_t w) { return (unsigned)((w + kThreads - 1) / kThreads); }
 
@@ -387,91 +392,107 @@ __global__ void k_loc_tp_bwd_atom(int64_t n, int C, const int32_t* __restrict__ 
 
 // Environment sums, reversed: g_om[c] = f_c g_Gs[c], g_om[C+c] = f_c (g_Gv[c] . u);
 // dE/df_c += om[c] g_Gs[c] + om[C+c] (g_Gv[c] . u);  dE/du += f_c om[C+c] g_Gv[c].
-// One thread per edge, 8 channels at a time (C: a multiple of 4; of 16 when gomb is written).
+// Four lanes per edge, each over channel quads j, j + 4, ... (16-byte accesses; C a multiple of 4,
+// of 16 when gomb is written), the sums over channels by two shuffle steps in a fixed order.
 __global__ void k_loc_env_bwd(int64_t E, int C, const int32_t* __restrict__ erow, const float* __restrict__ geo,
                               const float* __restrict__ om, const float* __restrict__ ggamS,
                               const float* __restrict__ ggamV, float* __restrict__ gom, float4* __restrict__ gg,
                               __nv_bfloat16* __restrict__ gomb, int Kc) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= E) return;
-  const int64_t i = erow[e];
-  const float* g = geo + e * 8;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t e = t >> 2;
+  const int j = (int)(t & 3);
+  const bool live = e < E;
+  const int64_t es = live ? e : 0;
+  const int64_t i = erow[es];
+  const float* g = geo + es * 8;
   const float fc = g[1], u0 = g[3], u1 = g[4], u2 = g[5];
   float gfc = 0.0f, gu0 = 0.0f, gu1 = 0.0f, gu2 = 0.0f;
-  for (int c0 = 0; c0 < C; c0 += 8) {
-    float va[8], vb[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = c0 + j;
-      va[j] = vb[j] = 0.0f;
-      if (c >= C) continue;
-      const float gs = ggamS[i * C + c];
-      const float q0 = ggamV[(i * 3 + 0) * C + c], q1 = ggamV[(i * 3 + 1) * C + c], q2 = ggamV[(i * 3 + 2) * C + c];
-      const float o0 = om[e * 2 * C + c], o1 = om[e * 2 * C + C + c];
-      const float gd = fmaf(q2, u2, fmaf(q1, u1, q0 * u0));
-      va[j] = fc * gs;
-      vb[j] = fc * gd;
-      gom[e * 2 * C + c] = va[j];
-      gom[e * 2 * C + C + c] = vb[j];
-      gfc = fmaf(o0, gs, fmaf(o1, gd, gfc));
-      const float t = fc * o1;
-      gu0 = fmaf(t, q0, gu0);
-      gu1 = fmaf(t, q1, gu1);
-      gu2 = fmaf(t, q2, gu2);
-    }
+  for (int c = 4 * j; live && c < C; c += 16) {
+    const float4 gs = ld4f(ggamS + i * C + c);
+    const float4 q0 = ld4f(ggamV + (i * 3 + 0) * C + c), q1 = ld4f(ggamV + (i * 3 + 1) * C + c),
+                 q2 = ld4f(ggamV + (i * 3 + 2) * C + c);
+    const float4 o0 = ld4f(om + es * 2 * C + c), o1 = ld4f(om + es * 2 * C + C + c);
+    float4 va, vb;
+    auto one = [&](float s_, float a0, float a1, float a2, float p0, float p1, float& ra, float& rb) {
+      const float gd = fmaf(a2, u2, fmaf(a1, u1, a0 * u0));
+      ra = fc * s_;
+      rb = fc * gd;
+      gfc = fmaf(p0, s_, fmaf(p1, gd, gfc));
+      const float tt = fc * p1;
+      gu0 = fmaf(tt, a0, gu0);
+      gu1 = fmaf(tt, a1, gu1);
+      gu2 = fmaf(tt, a2, gu2);
+    };
+    one(gs.x, q0.x, q1.x, q2.x, o0.x, o1.x, va.x, vb.x);
+    one(gs.y, q0.y, q1.y, q2.y, o0.y, o1.y, va.y, vb.y);
+    one(gs.z, q0.z, q1.z, q2.z, o0.z, o1.z, va.z, vb.z);
+    one(gs.w, q0.w, q1.w, q2.w, o0.w, o1.w, va.w, vb.w);
+    *reinterpret_cast<float4*>(gom + es * 2 * C + c) = va;
+    *reinterpret_cast<float4*>(gom + es * 2 * C + C + c) = vb;
     if (gomb) {
-      st8_bf16(gomb + e * Kc + c0, va);
-      st8_bf16(gomb + e * Kc + C + c0, vb);
+      st4_bf16(gomb + es * Kc + c, va);
+      st4_bf16(gomb + es * Kc + C + c, vb);
     }
   }
-  if (gomb) {
-    const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int k0 = 2 * C; k0 < Kc; k0 += 8) st8_bf16(gomb + e * Kc + k0, z);
+  if (live && gomb)
+    for (int k = 2 * C + 4 * j; k < Kc; k += 16) st4_bf16(gomb + es * Kc + k, make_float4(0.f, 0.f, 0.f, 0.f));
+  // the four lanes of an edge are consecutive lanes of one warp (t & 3)
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    gfc += __shfl_xor_sync(0xffffffffu, gfc, o);
+    gu0 += __shfl_xor_sync(0xffffffffu, gu0, o);
+    gu1 += __shfl_xor_sync(0xffffffffu, gu1, o);
+    gu2 += __shfl_xor_sync(0xffffffffu, gu2, o);
   }
-  float4 a = gg[e];
-  a.x += gfc; a.y += gu0; a.z += gu1; a.w += gu2;
-  gg[e] = a;
+  if (live && j == 0) {
+    float4 a = gg[e];
+    a.x += gfc; a.y += gu0; a.z += gu1; a.w += gu2;
+    gg[e] = a;
+  }
 }
 
 // Initial features, reversed: g_w0[c] = g_s[c], g_w0[C+c] = g_v[c] . u;  dE/du += w0[C+c] g_v[c].
-// One thread per edge, 8 channels at a time (C: a multiple of 4; of 16 when gw0b is written).
+// Four lanes per edge over channel quads, as k_loc_env_bwd.
 __global__ void k_loc_init_bwd(int64_t E, int C, const float* __restrict__ w0, const float* __restrict__ geo,
                                const float* __restrict__ GS, const float* __restrict__ GV, float* __restrict__ gw0,
                                float4* __restrict__ gg, __nv_bfloat16* __restrict__ gw0b, int Kc) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= E) return;
-  const float* g = geo + e * 8;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t e = t >> 2;
+  const int j = (int)(t & 3);
+  const bool live = e < E;
+  const int64_t es = live ? e : 0;
+  const float* g = geo + es * 8;
   const float u0 = g[3], u1 = g[4], u2 = g[5];
   float gu0 = 0.0f, gu1 = 0.0f, gu2 = 0.0f;
-  for (int c0 = 0; c0 < C; c0 += 8) {
-    float va[8], vb[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = c0 + j;
-      va[j] = vb[j] = 0.0f;
-      if (c >= C) continue;
-      const float q0 = GV[(e * 3 + 0) * C + c], q1 = GV[(e * 3 + 1) * C + c], q2 = GV[(e * 3 + 2) * C + c];
-      va[j] = GS[e * C + c];
-      vb[j] = fmaf(q2, u2, fmaf(q1, u1, q0 * u0));
-      gw0[e * 2 * C + c] = va[j];
-      gw0[e * 2 * C + C + c] = vb[j];
-      const float wv = w0[e * 2 * C + C + c];
-      gu0 = fmaf(wv, q0, gu0);
-      gu1 = fmaf(wv, q1, gu1);
-      gu2 = fmaf(wv, q2, gu2);
-    }
+  for (int c = 4 * j; live && c < C; c += 16) {
+    const float4 q0 = ld4f(GV + (es * 3 + 0) * C + c), q1 = ld4f(GV + (es * 3 + 1) * C + c),
+                 q2 = ld4f(GV + (es * 3 + 2) * C + c);
+    const float4 va = ld4f(GS + es * C + c), wv = ld4f(w0 + es * 2 * C + C + c);
+    const float4 vb = make_float4(fmaf(q2.x, u2, fmaf(q1.x, u1, q0.x * u0)), fmaf(q2.y, u2, fmaf(q1.y, u1, q0.y * u0)),
+                                  fmaf(q2.z, u2, fmaf(q1.z, u1, q0.z * u0)), fmaf(q2.w, u2, fmaf(q1.w, u1, q0.w * u0)));
+    *reinterpret_cast<float4*>(gw0 + es * 2 * C + c) = va;
+    *reinterpret_cast<float4*>(gw0 + es * 2 * C + C + c) = vb;
     if (gw0b) {
-      st8_bf16(gw0b + e * Kc + c0, va);
-      st8_bf16(gw0b + e * Kc + C + c0, vb);
+      st4_bf16(gw0b + es * Kc + c, va);
+      st4_bf16(gw0b + es * Kc + C + c, vb);
     }
+    gu0 = fmaf(wv.w, q0.w, fmaf(wv.z, q0.z, fmaf(wv.y, q0.y, fmaf(wv.x, q0.x, gu0))));
+    gu1 = fmaf(wv.w, q1.w, fmaf(wv.z, q1.z, fmaf(wv.y, q1.y, fmaf(wv.x, q1.x, gu1))));
+    gu2 = fmaf(wv.w, q2.w, fmaf(wv.z, q2.z, fmaf(wv.y, q2.y, fmaf(wv.x, q2.x, gu2))));
   }
-  if (gw0b) {
-    const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int k0 = 2 * C; k0 < Kc; k0 += 8) st8_bf16(gw0b + e * Kc + k0, z);
+  if (live && gw0b)
+    for (int k = 2 * C + 4 * j; k < Kc; k += 16) st4_bf16(gw0b + es * Kc + k, make_float4(0.f, 0.f, 0.f, 0.f));
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    gu0 += __shfl_xor_sync(0xffffffffu, gu0, o);
+    gu1 += __shfl_xor_sync(0xffffffffu, gu1, o);
+    gu2 += __shfl_xor_sync(0xffffffffu, gu2, o);
   }
-  float4 a = gg[e];
-  a.y += gu0; a.z += gu1; a.w += gu2;
-  gg[e] = a;
+  if (live && j == 0) {
+    float4 a = gg[e];
+    a.y += gu0; a.z += gu1; a.w += gu2;
+    gg[e] = a;
+  }
 }
 
 // Geometry, reversed: dE/dd = sum_k g_in[k] (b_k' f_c + b_k f_c') + (dE/df_c) f_c';
@@ -607,7 +628,7 @@ int local_forward_backward(cudaStream_t st, const LocalW& w, int64_t n, int64_t 
     }
     {
       LaunchScope ls_(st);
-      k_loc_env_bwd<<<nblocks(E), kThreads, 0, st>>>(E, C, b.erow, b.geo, b.OM[l], b.ggamS, b.ggamV, b.gom, b.gg,
+      k_loc_env_bwd<<<nblocks(E * 4), kThreads, 0, st>>>(E, C, b.erow, b.geo, b.OM[l], b.ggamS, b.ggamV, b.gom, b.gg,
                                                      b.gomb, Kc);
     }
     // g_x^{l-1} = g_xc[:, 0:F] + g_om Q_l^T
@@ -623,7 +644,7 @@ int local_forward_backward(cudaStream_t st, const LocalW& w, int64_t n, int64_t 
     std::swap(gv_in, gv_out);
   }
   // gs_in, gv_in: gradients of the initial edge features
-  { LaunchScope ls_(st); k_loc_init_bwd<<<nblocks(E), kThreads, 0, st>>>(E, C, b.w0, b.geo, gs_in, gv_in, b.gw0, b.gg, b.gw0b, Kc); }
+  { LaunchScope ls_(st); k_loc_init_bwd<<<nblocks(E * 4), kThreads, 0, st>>>(E, C, b.w0, b.geo, gs_in, gv_in, b.gw0, b.gg, b.gw0b, Kc); }
   if (bf)   // g_x0
     bad |= gemm_bf16<2>(st, E, F, Kc, b.gw0b, Kc, w.wb.P0, nullptr, b.gx, F, b.gxc, FX, nullptr, 0, status);
   else
