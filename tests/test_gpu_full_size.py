@@ -31,20 +31,31 @@ def cluster(sy, i, radius):
     return idx, pos, box, r[idx]
 
 
-def oracle_energy_of(orc, vals, F, T, S, sy, i):
-    idx, pos, box, _ = cluster(sy, i, T * RC + 1.0)
-    w = (idx == i).astype(float)
-    return orc.painn(vals, F, 20, T, S, sy.species[idx], pos, box, weights=w, forces=False, virial=False)["energy"]
+def _energy_job(args):
+    vals, F, T, S, species, pos, box, w = args
+    import oracle
+    return oracle.painn(vals, F, 20, T, S, species, pos, box, weights=w, forces=False, virial=False)["energy"]
 
 
-def oracle_force_on(orc, vals, F, T, S, sy, i):
-    idx, pos, box, r = cluster(sy, i, 2 * T * RC + 1.0)
-    w = (r < T * RC + 0.5).astype(float)
-    out = orc.painn(vals, F, 20, T, S, sy.species[idx], pos, box, weights=w, virial=False)
-    return out["forces"][np.nonzero(idx == i)[0][0]]
+def _force_job(args):
+    vals, F, T, S, species, pos, box, w, k = args
+    import oracle
+    return oracle.painn(vals, F, 20, T, S, species, pos, box, weights=w, virial=False)["forces"][k]
 
 
-def _check(orc, sy, F, T, precision, e_tol, f_tol, samples):
+def _pool_map(fn, jobs):
+    """The oracle's open clusters in a spawned process pool (one per host core)."""
+    import multiprocessing
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    n = max(1, min(len(jobs), os.cpu_count() or 1))
+    with ProcessPoolExecutor(max_workers=n, mp_context=multiprocessing.get_context("spawn")) as ex:
+        return list(ex.map(fn, jobs))
+
+
+def _check(orc, sy, F, T, precision, e_rms, e_max, f_rms, f_max, e_samples, f_samples):
+    """Per-atom energies of e_samples and forces on f_samples against the oracle's open clusters:
+    RMS and largest error over the samples, relative to the RMS per-atom energy and force."""
     eng = engine()
     vals, blob = model(F, T, 1, seed=0)
     with eng.Potential(F, T=T, n_species=1, precision=precision, params=blob) as pot:
@@ -53,27 +64,43 @@ def _check(orc, sy, F, T, precision, e_tol, f_tol, samples):
     assert np.isfinite(f).all() and np.isfinite(e).all()
     e_scale = float(np.sqrt(np.mean(e ** 2)))
     f_scale = float(np.sqrt(np.mean(f ** 2)))
-    for i in samples:
-        ue = oracle_energy_of(orc, vals, F, T, 1, sy, i)
-        assert abs(e[i] - ue) <= e_tol * e_scale, (i, e[i], ue)
-    fo = oracle_force_on(orc, vals, F, T, 1, sy, samples[0])
-    assert np.abs(f[samples[0]] - fo).max() <= f_tol * f_scale, (f[samples[0]], fo)
+    ejobs, fjobs = [], []
+    for i in e_samples:
+        idx, pos, box, _ = cluster(sy, i, T * RC + 1.0)
+        ejobs.append((vals, F, T, 1, sy.species[idx], pos, box, (idx == i).astype(float)))
+    for i in f_samples:
+        idx, pos, box, r = cluster(sy, i, 2 * T * RC + 1.0)
+        fjobs.append((vals, F, T, 1, sy.species[idx], pos, box, (r < T * RC + 0.5).astype(float),
+                      int(np.nonzero(idx == i)[0][0])))
+    ue = np.array(_pool_map(_energy_job, ejobs))
+    fo = np.array(_pool_map(_force_job, fjobs))
+    de = (e[e_samples] - ue) / e_scale
+    df = (f[f_samples] - fo) / f_scale
+    print(f"{precision}: energy error RMS {np.sqrt(np.mean(de ** 2)):.2e} max {np.abs(de).max():.2e} "
+          f"({len(e_samples)} atoms); force error RMS {np.sqrt(np.mean(df ** 2)):.2e} max {np.abs(df).max():.2e} "
+          f"({len(f_samples)} atoms)")
+    assert np.sqrt(np.mean(de ** 2)) <= e_rms and np.abs(de).max() <= e_max, de
+    assert np.sqrt(np.mean(df ** 2)) <= f_rms and np.abs(df).max() <= f_max, df
     return out
 
 
 def test_bf16_1M_sampled_atoms(orc):
-    """The benchmarked configuration: 1,000,188 atoms, F = 128, T = 3, BF16 (tensor-core kernels)."""
+    """The benchmarked configuration: 1,000,188 atoms, F = 128, T = 3, BF16 (tensor-core kernels):
+    32 per-atom energies and 8 forces.  BF16 operands: the sub-run's relative force RMSE is 9.1e-3;
+    estimated from 24 force components its RMS can read up to ~1.3x that, so the sample's RMS is
+    held to 1.5e-2 of the RMS force and single components to 5e-2."""
     sy = syn.fcc(63, 63, 63, jitter=0.05, seed=0)
     rng = np.random.default_rng(1)
-    samples = [int(k) for k in rng.integers(0, sy.n, 3)]
-    # BF16 operands: per-atom errors of a few 1e-2 of the scales (RMS force error 9.5e-3)
-    _check(orc, sy, 128, 3, "bf16", e_tol=5e-2, f_tol=6e-2, samples=samples)
+    samples = [int(k) for k in rng.choice(sy.n, 32, replace=False)]
+    _check(orc, sy, 128, 3, "bf16", e_rms=2e-2, e_max=6e-2, f_rms=1.5e-2, f_max=5e-2,
+           e_samples=samples, f_samples=samples[:8])
 
 
 def test_fp32_1p49M_sampled_atoms(orc):
-    """1,492,992 atoms on the FP32 path (3n = 4.48M rows in the U/V GEMM)."""
+    """1,492,992 atoms on the FP32 path (3n = 4.48M rows in the U/V GEMM): 16 energies, 4 forces."""
     sy = syn.fcc(72, 72, 72, jitter=0.05, seed=2)
     rng = np.random.default_rng(2)
-    samples = [int(k) for k in rng.integers(0, sy.n, 3)]
-    out = _check(orc, sy, 128, 3, "fp32", e_tol=2e-5, f_tol=2e-5, samples=samples)
+    samples = [int(k) for k in rng.choice(sy.n, 16, replace=False)]
+    out = _check(orc, sy, 128, 3, "fp32", e_rms=1e-5, e_max=2e-5, f_rms=1e-5, f_max=2e-5,
+                 e_samples=samples, f_samples=samples[:4])
     assert np.abs(out["forces"].sum(0)).max() < 1e-5 * np.abs(out["forces"]).sum(0).max()
