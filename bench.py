@@ -970,8 +970,7 @@ def main():
     ap.add_argument("--cells", type=int, default=FCC_CELLS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tc-adjoint", type=int, default=None,
-                    help="BF16 edge adjoint: 0 CUDA cores, 1 tcgen05 filter (the library's default), "
-                         "2 tcgen05 filter with the basis as a BF16 hi + lo pair")
+                    help="BF16 edge adjoint: 0 CUDA cores, 1 tcgen05 filter with FP16 operands (the library's default)")
     ap.add_argument("--tc-message", type=int, default=None,
                     help="BF16 message step: 0 CUDA cores, 1 tensor-core contraction (the library's default)")
     ap.add_argument("--chunk-rows", type=int, default=None,

@@ -185,10 +185,10 @@ int ctd_md_get_thermostat(ctd_ctx *ctx, double *xi, double *vxi, double *ethermo
 int ctd_md_set_thermostat_state(ctd_ctx *ctx, const double *xi, const double *vxi);
 
 /* ---- options -------------------------------------------------------------------------- */
-/* CTD_OPT_TC_ADJOINT (value 0..2; default 1): on the BF16 path with F = 128, run the edge
- * adjoint with the radial filter and its distance derivative on tcgen05 (1), the same with each
- * basis value entered as a BF16 pair (hi + lo, two MMAs; closer to FP32 at twice the tensor
- * work) (2), or on CUDA cores (0). */
+/* CTD_OPT_TC_ADJOINT (value 0 or 1; default 1): on the BF16 path with F = 128, run the edge
+ * adjoint with the radial filter and its distance derivative on tcgen05 with FP16 weights and
+ * basis (1), or on CUDA cores with FP32 weights (0).  A model whose filter weights exceed the
+ * FP16 range is loaded with 0. */
 #define CTD_OPT_TC_ADJOINT 1
 /* CTD_OPT_EDGE_STORE (value 0 or 1; default 0): the forward message kernel stores, per active
  * edge and layer, the cutoff-scaled radial filter and its distance derivative (6F floats), and

@@ -666,6 +666,21 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
   CUDA_OK(c, cudaMemcpyAsync(c->params_bf.p, hb.data(), hb.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
   const __nv_bfloat16* bbase = P<__nv_bfloat16>(c->params_bf);
+  // FP16 copies of the zero-padded radial filters [3F][64] for the tensor-core adjoint; a filter
+  // weight beyond FP16's range keeps that model on the CUDA-core adjoint (FP32 weights)
+  std::vector<__half> hh((size_t)T * 3 * F * 64);
+  bool f16_ok = true;
+  for (int t = 0; t < T; ++t)
+    for (size_t k = 0; k < (size_t)3 * F * 64; ++k) {
+      const float x = h[lo[t].Wf64 + k];
+      if (!(std::fabs(x) <= 65504.0f)) f16_ok = false;
+      hh[(size_t)t * 3 * F * 64 + k] = __float2half_rn(x);
+    }
+  if (T > 0) {
+    ENSURE(c, c->params_h, hh.size() * sizeof(__half));
+    CUDA_OK(c, cudaMemcpyAsync(c->params_h.p, hh.data(), hh.size() * sizeof(__half), cudaMemcpyHostToDevice, c->st));
+    CUDA_OK(c, cudaStreamSynchronize(c->st));
+  }
   const float* base = P<float>(c->params);
   ModelW& m = c->mw;
   m.F = F; m.K = K; m.KP = KP; m.T = T; m.S = S;
@@ -684,7 +699,9 @@ int load_params_impl(ctd_ctx* c, const void* blob, size_t nbytes) {
     L.UVb = bbase + o.UV; L.UVtb = bbase + o.UVt; L.A1b = bbase + o.A1; L.A1tb = bbase + o.A1t;
     L.A2b = bbase + o.A2; L.A2tb = bbase + o.A2t;
     L.Wfb = bbase + o.Wf64;
+    L.Wfh = f16_ok ? P<__half>(c->params_h) + (size_t)t * 3 * F * 64 : nullptr;
   }
+  if (!f16_ok) m.tc_adjoint = false;
   m.R1 = base + o_R1; m.R1t = base + o_R1t; m.d1 = base + o_d1; m.R2 = base + o_R2; m.d2 = base + o_d2;
   m.R1b = bbase + o_R1; m.R1tb = bbase + o_R1t;
   c->eps = eps;
@@ -730,7 +747,6 @@ int ctd_create(ctd_ctx** out, const ctd_model_desc* desc, size_t hbm_budget_byte
   c->desc = *desc;
   c->budget = hbm_budget_bytes;
   c->mw.tc_adjoint = true;   // BF16 path, F = 128: tensor-core adjoint and message contraction
-  c->mw.tc_adjoint_split = false;
   c->mw.tc_message = true;
   c->mw.edge_chunk_rows = 32;
   cudaGetDevice(&c->device);
@@ -848,9 +864,8 @@ int ctd_set_option(ctd_ctx* c, int32_t option, int64_t value) {
       c->mw.edge_store = value != 0;
       return CTD_OK;
     case CTD_OPT_TC_ADJOINT:
-      if (value < 0 || value > 2) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0 .. 2");
+      if (value < 0 || value > 1) return fail(c, CTD_ERR_INVALID_ARG, "CTD_OPT_TC_ADJOINT takes 0 or 1");
       c->mw.tc_adjoint = value != 0;
-      c->mw.tc_adjoint_split = value == 2;
       return CTD_OK;
     default:
       return fail(c, CTD_ERR_INVALID_ARG, "unknown option");

@@ -96,6 +96,7 @@ struct LayerW {
   // BF16 copies for the tensor-core path (same shapes as the FP32 arrays above)
   const __nv_bfloat16 *W1b, *W1tb, *W2b, *W2tb, *UVb, *UVtb, *A1b, *A1tb, *A2b, *A2tb;
   const __nv_bfloat16* Wfb;        // [3F][64] radial filter, zero padded (tensor-core edge kernels)
+  const __half* Wfh;               // the same in FP16 (the tensor-core adjoint's filter operand)
 };
 
 struct ModelW {
@@ -106,7 +107,6 @@ struct ModelW {
   const float *R1, *R1t, *d1, *R2, *d2;   // [F/2][F], [F][F/2]
   const __nv_bfloat16 *R1b, *R1tb;
   bool tc_adjoint;                 // BF16 path, F = 128: edge adjoint with the tensor-core filter
-  bool tc_adjoint_split;           // ... with each basis value entered as a BF16 hi + lo pair
   bool edge_store;                 // store per-edge filters in the forward pass for the adjoint
   bool tc_message;                 // BF16 path, F = 128: message step as the tensor-core contraction (edge_mma.cu)
   int64_t edge_chunk_rows;         // tensor-core adjoint: rows per chunk (0: one range per stream)

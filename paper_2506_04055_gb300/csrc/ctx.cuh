@@ -42,7 +42,7 @@ struct ctd_ctx {
   // parameters
   bool have_params = false;
   double eps = 1e-8, e_scale = 1.0;
-  DBuf params, params_bf;
+  DBuf params, params_bf, params_h;   // FP32 weights, their BF16 twin, FP16 copies of the filters
   ModelW mw{};
   // strictly local edge model (desc.family == CTD_FAMILY_LOCAL): weights and edge buffers
   ctd::LocalW lw{};
@@ -82,7 +82,7 @@ struct ctd_ctx {
   DBuf nhc_state, nhc_ke, md_eth;
 
   ctd_ctx() {
-    DBuf* list[] = {&params, &params_bf, &x_user, &z_user, &xw, &wrapm, &cellid, &cell_count, &cell_start, &cursor,
+    DBuf* list[] = {&params, &params_bf, &params_h, &x_user, &z_user, &xw, &wrapm, &cellid, &cell_count, &cell_start, &cursor,
                     &tmp_idx, &perm, &inv_perm, &xw_s, &xref_s, &z_s, &x_s, &count, &vrow, &vcol, &vimg,
                     &vbase, &vrev, &v2a, &status, &delta, &maxd, &acount, &arow, &acol, &ar, &vidx, &arev, &aend,
                     &hedge, &force_s, &eatom, &epart, &vpart, &kpart, &scan_tmp, &out_e, &out_f, &out_w,

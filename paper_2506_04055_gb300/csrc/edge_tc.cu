@@ -6,14 +6,15 @@
 // [3F x K] x [K x edges] contractions per tile of edges: D[c][e] = sum_k Wf[c][k] rbf_k(d_e)
 // and the same with rbf'_k.  They run as UMMA with M = 128 filter channels (three M tiles: the
 // s, vv and vs blocks), N = 2 x 16 edges (basis and derivative basis of a 16-edge tile),
-// K = 32 (the basis zero-padded), BF16 operands and FP32 accumulation in TMEM.  Everything
+// K = 32 (the basis zero-padded), FP16 operands (11 significant bits; the weights, the basis
+// and its derivative lie far inside FP16's range) and FP32 accumulation in TMEM.  Everything
 // after the contraction (bias, cutoff, the adjoint terms, the reductions over the features)
 // stays FP32 on CUDA cores.
 //
 // CTA layout (one CTA per SM, 2 row streams):
 //   warps 0..1 producers, one per stream: per edge of the next tile, geometry, f_c, f_c' and
 //              the basis and its derivative (a lane pair per edge), written as a 128B-swizzled
-//              BF16 tile; bulk copies of the receivers' interleaved gradient rows; Wf arrives
+//              FP16 tile; bulk copies of the receivers' interleaved gradient rows; Wf arrives
 //              once per CTA by TMA
 //   warp 2     TMEM owner and single-thread MMA issue
 //   warps 3..  epilogue, four warps per stream: thread = feature channel f (TMEM lane); a
@@ -38,29 +39,18 @@ __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
   return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
 }
 
-// Columns 16h .. 16h+15 of row r of a 128B-swizzled BF16 tile (two 16-byte chunks).
+// Columns 16h .. 16h+15 of row r of a 128B-swizzled FP16 tile (two 16-byte chunks).
 __device__ __forceinline__ void store_basis_half(unsigned char* tile, int r, int h, const float (&v)[16]) {
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     uint32_t w[4];
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
-      __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * c + 2 * x], v[8 * c + 2 * x + 1]);
+      __half2 b2 = __floats2half2_rn(v[8 * c + 2 * x], v[8 * c + 2 * x + 1]);
       w[x] = *reinterpret_cast<uint32_t*>(&b2);
     }
     *reinterpret_cast<uint4*>(tile + umma::sw128_offset(r, 16 * h + 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
-}
-__device__ __forceinline__ void store_basis_half_split(unsigned char* hi, unsigned char* lo, int r, int h,
-                                                       const float (&v)[16]) {
-  float a[16], b[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    a[k] = __bfloat162float(__float2bfloat16_rn(v[k]));
-    b[k] = v[k] - a[k];
-  }
-  store_basis_half(hi, r, h, a);
-  store_basis_half(lo, r, h, b);
 }
 
 struct EdgeTcArgs {
@@ -111,23 +101,22 @@ __device__ __forceinline__ bool chunk_at(const EdgeTcArgs& p, int64_t k, Chunk& 
 // own feature of the gathered row with its partials of (dU/dd, dU/du); after a stream barrier
 // the partials are reduced over the F features from shared memory and turned into hedge[e].
 // The epilogue reads the accumulator in 4-edge halves, each half's TMEM loads in flight while
-// the previous half is computed.  SPLIT: each basis value enters as a BF16 pair (hi + lo, two
-// MMAs).  KC: compile-time basis size (0: runtime).  L0: first layer (v = 0, no phi gradients).
-template <int NE, int NS, bool SPLIT, int KC = 0, bool L0 = false>
+// the previous half is computed.  KC: compile-time basis size (0: runtime).  L0: first layer
+// (v = 0, no phi gradients).
+template <int NE, int NS, int KC = 0, bool L0 = false>
 __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __grid_constant__ CUtensorMap tmWf, EdgeTcArgs p) {
   static_assert(NS <= 2, "one producer warp per stream");
   constexpr int NBUF = 2;   // tile buffers per stream
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = align1024(smem_raw);
   unsigned char* sA = smem;                                          // Wf tiles (bias in column K)
-  // per buffer one (or, SPLIT, a hi and a lo) operand of 2 NE rows: the basis of the tile's
+  // per buffer one operand of 2 NE rows: the basis of the tile's
   // edges in rows 0..NE-1 and their derivative basis in rows NE..2NE-1, so that one MMA per
   // channel block yields [W | dW/dd] as 2 NE columns
-  constexpr int NB = SPLIT ? 2 : 1;
   static_assert(NS * 2 * 6 * NE <= 512, "TMEM columns");
   static_assert(NE == 16, "tile shape: one lane pair per edge");
   unsigned char* sB = sA + kWfBytes;                                 // [NS][NBUF][NB][2 NE x 128 B]
-  float* sG = reinterpret_cast<float*>(sB + NS * NBUF * NB * 2 * NE * 128);   // [NS][NBUF][NE][4F]
+  float* sG = reinterpret_cast<float*>(sB + NS * NBUF * 2 * NE * 128);   // [NS][NBUF][NE][4F]
   int* sfl = reinterpret_cast<int*>(sG + (size_t)NS * NBUF * NE * 4 * kF);   // [NS][NBUF][NE]
   float4* sgeo = reinterpret_cast<float4*>(sfl + NS * NBUF * NE);    // [NS][NBUF][NE] (u, d)
   float2* sfc = reinterpret_cast<float2*>(sgeo + NS * NBUF * NE);    // [NS][NBUF][NE] (f_c, f_c')
@@ -259,17 +248,12 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         float* g = sG + (size_t)so * 4 * kF;
         if (lane == 0) umma::mbar_expect_tx_only(&b[bb], (uint32_t)(nlive * 4 * kF * 4));
         __syncwarp();
-        unsigned char* tile = sB + (s * NBUF + bb) * NB * 2 * NE * 128;
+        unsigned char* tile = sB + (s * NBUF + bb) * 2 * NE * 128;
         // the receiver's (gsm, gvm) interleaved per feature, one 2 KB row
         if (live && h == 0)
           umma::bulk_copy_g2s(g + (size_t)slot * 4 * kF, p.G4 + (int64_t)jj * 4 * kF, 4 * kF * 4, &b[bb]);
-        if (SPLIT) {
-          store_basis_half_split(tile, tile + 2 * NE * 128, slot, h, bs);
-          store_basis_half_split(tile, tile + 2 * NE * 128, NE + slot, h, ds);
-        } else {
-          store_basis_half(tile, slot, h, bs);
-          store_basis_half(tile, NE + slot, h, ds);
-        }
+        store_basis_half(tile, slot, h, bs);
+        store_basis_half(tile, NE + slot, h, ds);
         if (h == 0) {
           sgeo[so + slot] = geo;
           sfc[so + slot] = fcv;
@@ -284,7 +268,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
   } else if (warp == 2) {
     if (lane == 0) {
       if (!umma::mbar_wait(wbar, 0)) ok = false;
-      const uint32_t idesc = umma::idesc_bf16_m128(2 * NE);
+      const uint32_t idesc = umma::idesc_f16_m128(2 * NE);   // FP16 weights and basis
       int64_t k[NS];
       int t[NS], it[NS];
       bool have[NS];
@@ -320,11 +304,11 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
           if (it[s] >= 2 && !umma::mbar_test(&b[10 + a], ((it[s] >> 1) - 1) & 1)) continue;
           progressed = true;
           umma::fence_after();
-          const uint32_t bbase = umma::smem_u32(sB + (s * NBUF + bb) * NB * 2 * NE * 128);
+          const uint32_t bbase = umma::smem_u32(sB + (s * NBUF + bb) * 2 * NE * 128);
 #pragma unroll
           for (int m = 0; m < 3; ++m)
 #pragma unroll
-            for (int kk = 0; kk < 2 * NB; ++kk)   // k-halves of the hi operand[, then of the lo one]
+            for (int kk = 0; kk < 2; ++kk)   // the two 16-column k-halves of the basis
               umma::mma_bf16(tmem + (uint32_t)((s * 2 + a) * 6 * NE + m * 2 * NE),
                              umma::desc_sw128(umma::smem_u32(sA + m * kWfTileBytes) + 32u * (kk & 1)),
                              umma::desc_sw128(bbase + (uint32_t)(kk >> 1) * 2 * NE * 128 + 32u * (kk & 1)), idesc, kk > 0);
@@ -551,8 +535,8 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
 // ------------------------------------------------------------------------------ host side
 constexpr int kBwgNE = 16, kBwgNS = 2;   // bulk-gathered adjoint: 2 streams, double-buffered tiles
 
-static size_t bwg_smem(bool split) {
-  return 1024 + kWfBytes + (size_t)kBwgNS * 2 * (split ? 2 : 1) * 2 * kBwgNE * 128 + (size_t)kBwgNS * 2 * kBwgNE * 4 * kF * 4 +
+static size_t bwg_smem() {
+  return 1024 + kWfBytes + (size_t)kBwgNS * 2 * 2 * kBwgNE * 128 + (size_t)kBwgNS * 2 * kBwgNE * 4 * kF * 4 +
          (size_t)kBwgNS * 2 * kBwgNE * (4 + 16 + 8) + 8 * (1 + 13 * kBwgNS) + 64;
 }
 
@@ -576,17 +560,17 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
   if (n == 0) return 0;
   if (!G4 || (!PHI && !PHIh)) return -1;
   CUtensorMap tm;
-  if (!make_tmap_bf16(&tm, m.L[t].Wfb, 3 * kF, 64, 64, 128)) return -2;
+  // the FP16 weights: 2-byte elements like BF16, which is all the TMA copy depends on
+  if (!m.L[t].Wfh || !make_tmap_bf16(&tm, m.L[t].Wfh, 3 * kF, 64, 64, 128)) return -2;
   EdgeTcArgs a{};
   a.n = n; a.K = m.K; a.rc = m.rc; a.accumulate = accumulate; a.arow = arow; a.acol = acol; a.ar = ar;
   a.PHI = PHI; a.PHIh = PHIh; a.bf = m.L[t].bf; a.GPHI = GPHI; a.hedge = hedge; a.status = status; a.aend = aend; a.G4 = G4;
   a.chunk_rows = chunk_rows_for(m, n, kBwgNS);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(false));
-    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(false));
-    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, false, 20, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(false));
-    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem(true));
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
+    cudaFuncSetAttribute(k_edge_bwd_tcg<kBwgNE, kBwgNS, 20, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwg_smem());
     attr = true;
   }
   int sms = 0, dev = 0;
@@ -594,14 +578,12 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int threads = 32 * (3 + 4 * kBwgNS);
   LaunchScope ls_(st);
-  if (m.tc_adjoint_split)   // each basis value entered as a BF16 hi + lo pair (two MMAs)
-    k_edge_bwd_tcg<kBwgNE, kBwgNS, true><<<sms, threads, bwg_smem(true), st>>>(tm, a);
-  else if (m.K == 20 && t == 0 && !GPHI)   // the usual basis size; first layer: v = 0, no phi gradients
-    k_edge_bwd_tcg<kBwgNE, kBwgNS, false, 20, true><<<sms, threads, bwg_smem(false), st>>>(tm, a);
+  if (m.K == 20 && t == 0 && !GPHI)   // the usual basis size; first layer: v = 0, no phi gradients
+    k_edge_bwd_tcg<kBwgNE, kBwgNS, 20, true><<<sms, threads, bwg_smem(), st>>>(tm, a);
   else if (m.K == 20)
-    k_edge_bwd_tcg<kBwgNE, kBwgNS, false, 20><<<sms, threads, bwg_smem(false), st>>>(tm, a);
+    k_edge_bwd_tcg<kBwgNE, kBwgNS, 20><<<sms, threads, bwg_smem(), st>>>(tm, a);
   else
-    k_edge_bwd_tcg<kBwgNE, kBwgNS, false><<<sms, threads, bwg_smem(false), st>>>(tm, a);
+    k_edge_bwd_tcg<kBwgNE, kBwgNS><<<sms, threads, bwg_smem(), st>>>(tm, a);
   return 0;
 }
 

@@ -497,7 +497,7 @@ uint64_t layout_key(const ctd_server* s, int64_t nres) {
   uint64_t h = 1469598103934665603ull;
   auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
   mix(c->alloc_gen); mix((uint64_t)c->n); mix((uint64_t)nres); mix(s->any_nvt ? 1 : 0);
-  mix(c->mw.tc_adjoint); mix(c->mw.tc_adjoint_split); mix(c->mw.tc_message); mix((uint64_t)c->mw.edge_chunk_rows);
+  mix(c->mw.tc_adjoint); mix(c->mw.tc_message); mix((uint64_t)c->mw.edge_chunk_rows);
   mix((uint64_t)c->desc.precision); mix(c->use_ew); mix(c->use_near);
   return h == 0 ? 1 : h;
 }

@@ -35,6 +35,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16_m128(int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
+// The same with A = B = F16 (formats 0): FP16 operands, FP32 accumulation.
+__host__ __device__ constexpr uint32_t idesc_f16_m128(int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(

@@ -37,15 +37,19 @@ def test_bf16_fcc4000_F128(orc):
     print(f"bf16 fcc4000: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1])
 def test_bf16_tensor_core_adjoint(orc, variant):
-    """Each edge-adjoint variant (CUDA cores; tcgen05 filter; tcgen05 filter with the basis as a
-    BF16 hi + lo pair) on the fcc sub-cell and a small cell."""
+    """Each edge-adjoint variant (CUDA cores with FP32 weights; tcgen05 filter with FP16 weights and
+    basis) on the fcc sub-cell and a small cell; the removed option value 2 is rejected."""
     eng = engine()
     for sy in (syn.fcc(10, 10, 10, jitter=0.05, seed=0), syn.water_box(21, seed=2)):
         out, ref = _run(eng, orc, sy, 128, 3, 2, bias=0.1, tc_adjoint=variant)
         fr, er, wr = compare(out, ref, force_tol=BF16_FORCE_RMSE, e_tol=1e-2, w_tol=2e-2)
         print(f"bf16 tc-adjoint{variant} {sy.name}: force rmse {fr:.2e}, energy {er:.2e}, virial {wr:.2e}")
+    from paper_2506_04055_gb300 import _lib
+    with eng.Potential(128, T=1, n_species=1, precision="bf16") as pot:
+        with pytest.raises(eng.CtdError):
+            pot.set_option(_lib.CTD_OPT_TC_ADJOINT, 2)
 
 
 def test_bf16_mixture_biases(orc):
