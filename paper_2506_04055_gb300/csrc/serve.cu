@@ -499,6 +499,8 @@ uint64_t layout_key(const ctd_server* s, int64_t nres) {
   mix(c->alloc_gen); mix((uint64_t)c->n); mix((uint64_t)nres); mix(s->any_nvt ? 1 : 0);
   mix(c->mw.tc_adjoint); mix(c->mw.tc_message); mix((uint64_t)c->mw.edge_chunk_rows);
   mix((uint64_t)c->desc.precision); mix(c->use_ew); mix(c->use_near);
+  // a model without layers clears the per-edge gradients with a memset sized by the Verlet list
+  if (c->desc.T == 0) mix((uint64_t)c->n_verlet);
   return h == 0 ? 1 : h;
 }
 
