@@ -50,11 +50,12 @@ def step_bytes_per_atom(n_e, value_bytes):
 
 # FMA-pipe FLOPs per (active edge, feature channel) the edge kernels execute on CUDA cores
 # (reported beside the roofline): FP32 message 6K + 18, FP32 adjoint 12K + 45; with the filter
-# on the tensor pipe (BF16, F = 128) the adjoint keeps 50 (the tensor-core message kernel's
-# CUDA-core work is per receiver, counted where it is reported).
+# on the tensor pipe (BF16, F = 128, the cutoff and bias folded into the basis so the MMA yields
+# the filter and its derivative) the adjoint keeps 35 (the tensor-core message kernel's CUDA-core
+# work is per receiver, counted where it is reported).
 EDGE_FWD_FLOP_PER_EF = 6 * K + 18
 EDGE_BWD_FLOP_PER_EF = 12 * K + 45
-EDGE_BWD_TC_ALU_FLOP_PER_EF = 50
+EDGE_BWD_TC_ALU_FLOP_PER_EF = 35
 FP32_LANES_PER_SM, N_SM = 128, 152
 
 

@@ -3,13 +3,14 @@
 //
 // The filter W_e = (Wf rbf(d_e) + bf) f_c(d_e) (PaiNN message function, arXiv 2506.04055
 // Methods "Graph Neural Networks" / "Chosen Architectures") and its distance derivative are
-// [3F x K] x [K x edges] contractions per tile of edges: D[c][e] = sum_k Wf[c][k] rbf_k(d_e)
-// and the same with rbf'_k.  They run as UMMA with M = 128 filter channels (three M tiles: the
+// [3F x (K+1)] x [(K+1) x edges] contractions per tile of edges: with the weights [Wf | bf] and
+// the basis columns (rbf_k f_c, f_c), D[c][e] = W_e[c], and with (rbf_k' f_c + rbf_k f_c', f_c')
+// its distance derivative.  They run as UMMA with M = 128 filter channels (three M tiles: the
 // s, vv and vs blocks), N = 2 x 16 edges (basis and derivative basis of a 16-edge tile),
 // K = 32 (the basis zero-padded), FP16 operands (11 significant bits; the weights, the basis
 // and its derivative lie far inside FP16's range) and FP32 accumulation in TMEM.  Everything
-// after the contraction (bias, cutoff, the adjoint terms, the reductions over the features)
-// stays FP32 on CUDA cores.
+// after the contraction (the adjoint terms, the reductions over the features) stays FP32 on
+// CUDA cores.
 //
 // CTA layout (one CTA per SM, 2 row streams):
 //   warps 0..1 producers, one per stream: per edge of the next tile, geometry, f_c, f_c' and
@@ -65,7 +66,6 @@ struct EdgeTcArgs {
   const float4* __restrict__ ar;
   const float* __restrict__ PHI;   // [n][6F] FP32 message table, or
   const __half* __restrict__ PHIh; // [n][6F] its FP16 copy (the one the contracted message step used)
-  const float* __restrict__ bf;    // [3F]
   float* __restrict__ GPHI;        // [n][5F]
   float4* __restrict__ hedge;      // [E]
   const float* __restrict__ G4;    // [n][F][4] = (gsm, gvm_0..2) per feature, interleaved
@@ -95,8 +95,8 @@ __device__ __forceinline__ bool chunk_at(const EdgeTcArgs& p, int64_t k, Chunk& 
   return true;
 }
 
-// Adjoint: the MMA yields Wf rbf and Wf rbf' per edge (the bias and f_c applied in FP32 by the
-// epilogue); the receivers' gradient rows, (gsm_i, gvm_i) interleaved per feature (G4, 2 KB),
+// Adjoint: the MMA yields the filter W = (Wf rbf + bf) f_c and its distance derivative per edge
+// (f_c, f_c' and the bias folded into the basis tile); the receivers' gradient rows, (gsm_i, gvm_i) interleaved per feature (G4, 2 KB),
 // are gathered by bulk copies.  Thread f accumulates the row's phi gradients and overwrites its
 // own feature of the gathered row with its partials of (dU/dd, dU/du); after a stream barrier
 // the partials are reduced over the F features from shared memory and turned into hedge[e].
@@ -119,8 +119,7 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
   float* sG = reinterpret_cast<float*>(sB + NS * NBUF * 2 * NE * 128);   // [NS][NBUF][NE][4F]
   int* sfl = reinterpret_cast<int*>(sG + (size_t)NS * NBUF * NE * 4 * kF);   // [NS][NBUF][NE]
   float4* sgeo = reinterpret_cast<float4*>(sfl + NS * NBUF * NE);    // [NS][NBUF][NE] (u, d)
-  float2* sfc = reinterpret_cast<float2*>(sgeo + NS * NBUF * NE);    // [NS][NBUF][NE] (f_c, f_c')
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sfc + NS * NBUF * NE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sgeo + NS * NBUF * NE);
   uint64_t* wbar = bars;
   // per stream: bready[4], bfree[4] (NBUF used), tfull[2], tempty[2], esync
   constexpr int kBars = 13;
@@ -211,22 +210,24 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         const int bb = it % NBUF;
         float bq[16], dq[16];
         float4 geo = make_float4(0.f, 0.f, 0.f, 1.f);
-        float2 fcv = make_float2(0.f, 0.f);
         const bool live = slot < nlive;
         if (live) {
           const float d = r.w, id = 1.0f / d;
           geo = make_float4(r.x * id, r.y * id, r.z * id, d);
           const float fc = 0.5f * (cospif(d * inv_rc) + 1.0f);
           const float dfc = -0.5f * 3.14159265358979f * inv_rc * sinpif(d * inv_rc);
-          fcv = make_float2(fc, dfc);
+          // the cutoff and the filter bias folded in: columns k < K hold b_k f_c and its distance
+          // derivative b_k' f_c + b_k f_c', column K holds f_c and f_c' (it meets the bias bf in
+          // the weights' column K), so the MMA yields W and dW/dd themselves
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int kk = 2 * q + h;
             const float tq = d - (float)kk * sig;
             const bool in = kk < KK;
             const float v = in ? expf(-tq * tq * inv2s2) : 0.0f;
-            bq[q] = v;
-            dq[q] = -v * tq * inv_s2;
+            const float dv = -v * tq * inv_s2;
+            bq[q] = in ? v * fc : (kk == KK ? fc : 0.0f);
+            dq[q] = in ? fmaf(dv, fc, v * dfc) : (kk == KK ? dfc : 0.0f);
           }
         } else {
 #pragma unroll
@@ -256,7 +257,6 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         store_basis_half(tile, NE + slot, h, ds);
         if (h == 0) {
           sgeo[so + slot] = geo;
-          sfc[so + slot] = fcv;
           sfl[so + slot] = live ? ecnt : 0;
         }
         gathered = it + 1;
@@ -329,7 +329,6 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
     const int s = (warp - 3) >> 2;
     const int q = warp & 3, f = q * 32 + lane;
     uint64_t* b = sbar + kBars * s;
-    const float bs = p.bf[f], bvv = p.bf[kF + f], bvs = p.bf[2 * kF + f];
     int it = 0;
     Chunk C;
     for (int64_t k = (int64_t)blockIdx.x * NS + s; ok && chunk_at<NE>(p, k, C); k += nstreams) {
@@ -384,7 +383,6 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         const int so = (s * NBUF + bb) * NE;
         const int* tf = sfl + so;
         const float4* tg = sgeo + so;
-        const float2* tc = sfc + so;
         // lane 8k of warp q writes edge 4q + k of the tile; its previous value is read now
         const int hslot = f >> 3;
         float4 hold = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -400,12 +398,8 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
                         float gv1, float gv2) {
           const float4 geo = tg[slot];
           // filter and its distance derivative, f_c included
-          const float2 fcv = tc[slot];
-          const float ws = w0 + bs, wvv = w2 + bvv, wvs = w4 + bvs;
-          const float Ws = ws * fcv.x, Wvv = wvv * fcv.x, Wvs = wvs * fcv.x;
-          const float dWs = fcv.x * w1 + fcv.y * ws;
-          const float dWvv = fcv.x * w3 + fcv.y * wvv;
-          const float dWvs = fcv.x * w5 + fcv.y * wvs;
+          // the accumulator holds the filter and its distance derivative, cutoff and bias included
+          const float Ws = w0, dWs = w1, Wvv = w2, dWvv = w3, Wvs = w4, dWvs = w5;
           // L0 (first layer): v = 0 so psi = 0, and no phi gradients are written, so only the
           // per-edge partials are formed
           if (!L0) {
@@ -537,7 +531,7 @@ constexpr int kBwgNE = 16, kBwgNS = 2;   // bulk-gathered adjoint: 2 streams, do
 
 static size_t bwg_smem() {
   return 1024 + kWfBytes + (size_t)kBwgNS * 2 * 2 * kBwgNE * 128 + (size_t)kBwgNS * 2 * kBwgNE * 4 * kF * 4 +
-         (size_t)kBwgNS * 2 * kBwgNE * (4 + 16 + 8) + 8 * (1 + 13 * kBwgNS) + 64;
+         (size_t)kBwgNS * 2 * kBwgNE * (4 + 16) + 8 * (1 + 13 * kBwgNS) + 64;
 }
 
 // K < kKPad leaves basis column K zero
@@ -564,7 +558,7 @@ int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t
   if (!m.L[t].Wfh || !make_tmap_bf16(&tm, m.L[t].Wfh, 3 * kF, 64, 64, 128)) return -2;
   EdgeTcArgs a{};
   a.n = n; a.K = m.K; a.rc = m.rc; a.accumulate = accumulate; a.arow = arow; a.acol = acol; a.ar = ar;
-  a.PHI = PHI; a.PHIh = PHIh; a.bf = m.L[t].bf; a.GPHI = GPHI; a.hedge = hedge; a.status = status; a.aend = aend; a.G4 = G4;
+  a.PHI = PHI; a.PHIh = PHIh; a.GPHI = GPHI; a.hedge = hedge; a.status = status; a.aend = aend; a.G4 = G4;
   a.chunk_rows = chunk_rows_for(m, n, kBwgNS);
   static bool attr = false;
   if (!attr) {
