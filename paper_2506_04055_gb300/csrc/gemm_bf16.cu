@@ -8,7 +8,8 @@
 // loaded once per CTA and stays in shared memory; A streams through a ring of 64-column
 // k-blocks, 16 KB each, as many stages as shared memory holds).  Warp 1: TMEM allocation and
 // the single-thread MMA issue (M = 128, N up to 256 per instruction, K = 16 per instruction).
-// Warps 2-9: epilogue, two warps per TMEM lane quarter taking alternate 32-column chunks.
+// Warps 2 and up: epilogue, epi_warps / 4 warps per TMEM lane quarter taking the quarter's
+// 32-column chunks in turn.
 // Every wait is bounded; on a timeout the kernel records ST_TIMEOUT in the status word and
 // winds down.
 #include <cstdio>
@@ -42,14 +43,20 @@ constexpr int kTileM = 128;
 constexpr int kBlockK = 64;
 constexpr int kATileBytes = kTileM * kBlockK * 2;   // 16 KB per 64-column block
 constexpr int kTP = 36;                              // row pitch (floats) of an epilogue transpose tile
-constexpr int kEpiWarps = 8;
+// Epilogue warps, a multiple of 4 (epi_warps / 4 warps per TMEM lane quarter).  Sixteen hide the
+// TMEM -> shared -> global latency of a chunk better than eight (U/V GEMM with FP16 output, 3M x
+// 256 x 128: 0.47 against 0.69 ms); the PHI-packing epilogue holds three V quads per row in
+// registers and stays at eight, the register budget of sixteen warps would spill it.
+template <int EPI>
+constexpr int epi_warps() { return EPI == 4 ? 8 : 16; }
 constexpr int kMaxAStages = 8;
 
 template <int EPI>
-__global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, GemmBf16Args p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int kEpiWarps = epi_warps<EPI>(), kEpiGroups = kEpiWarps / 4;
   const int KB = (p.K + kBlockK - 1) / kBlockK;   // a ragged last block is zero-filled by the TMA
   const int N = p.N;
   unsigned char* sB = smem;                                        // KB x N x 128 B
@@ -139,10 +146,11 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __gr
       }
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4.  Each 32-row x 32-column chunk goes
+    // epilogue warps: TMEM lane quarter = warp % 4, group grp takes the quarter's chunks grp,
+    // grp + kEpiGroups, ...  Each 32-row x 32-column chunk goes
     // TMEM -> registers (thread = row) -> padded shared tile -> registers (8 lanes per row,
     // 16 bytes each), so that global loads and stores move whole 128-byte row segments.
-    const int q = warp & 3, half = (warp - 2) >> 2;
+    const int q = warp & 3, grp = (warp - 2) >> 2;
     float* T = sT + (warp - 2) * 32 * kTP;
     const int cr = lane >> 3, cc = 4 * (lane & 7);   // row within a group of 4, column quad
     const int nchunks = N / 32;
@@ -152,16 +160,16 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) k_gemm_bf16(const __gr
       if (!umma::mbar_wait(&tfull[a], (it / p.n_acc) & 1)) { ok = false; break; }
       umma::fence_after();
       const int64_t m0 = tile * kTileM + q * 32;   // first row of this warp's quarter
-      if (half >= nchunks) {
+      if (grp >= nchunks) {
         umma::fence_before();
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&tempty[a]);
       }
-      for (int ch = half; ch < nchunks; ch += 2) {
+      for (int ch = grp; ch < nchunks; ch += kEpiGroups) {
         const int c0 = 32 * ch;
         float v[32];
         umma::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * N + c0), v);
-        if (ch + 2 >= nchunks) {
+        if (ch + kEpiGroups >= nchunks) {
           // the accumulator has been read: the MMA of a later tile may reuse it
           umma::fence_before();
           __syncwarp();
@@ -339,6 +347,7 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
   if (p.n_chunk > 256 || p.n_chunk % 16) return -1;
   const int KB = (K + kBlockK - 1) / kBlockK;
   const size_t b_bytes = (size_t)KB * N * 128;
+  constexpr int kEpiWarps = epi_warps<EPI>();
   const size_t t_bytes = (size_t)kEpiWarps * 32 * kTP * sizeof(float);
   const size_t limit = 227 * 1024 - 1024 - 256 - t_bytes;
   if (b_bytes + 2 * (size_t)kATileBytes > limit) return -1;
