@@ -66,7 +66,9 @@ struct EdgeTcArgs {
   const float4* __restrict__ ar;
   const float* __restrict__ PHI;   // [n][6F] FP32 message table, or
   const __half* __restrict__ PHIh; // [n][6F] its FP16 copy (the one the contracted message step used)
-  float* __restrict__ GPHI;        // [n][5F]
+  float* __restrict__ GPHI;        // [n][3F]: the row's psi gradients (gpsi_0..2), or null (first layer)
+  __nv_bfloat16* __restrict__ GP3b;  // [n][3F]: BF16 operand of the phi-MLP backward; blocks 0 and 2
+                                     // (gphi_s, gphi_vs) written here, block 1 by the pass after
   float4* __restrict__ hedge;      // [E]
   const float* __restrict__ G4;    // [n][F][4] = (gsm, gvm_0..2) per feature, interleaved
   int* status;
@@ -361,8 +363,12 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
       float gps = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f, gpvs = 0.f;
       auto flush = [&]() {
         if (p.GPHI) {
-          float* o = p.GPHI + r * 5 * kF;
-          o[f] = gps; o[kF + f] = gy0; o[2 * kF + f] = gy1; o[3 * kF + f] = gy2; o[4 * kF + f] = gpvs;
+          float* o = p.GPHI + r * 3 * kF;
+          o[f] = gy0; o[kF + f] = gy1; o[2 * kF + f] = gy2;
+          // the phi-MLP backward reads gphi_s and gphi_vs only as BF16 operands
+          __nv_bfloat16* ob = p.GP3b + r * 3 * kF;
+          ob[f] = __float2bfloat16_rn(gps);
+          ob[2 * kF + f] = __float2bfloat16_rn(gpvs);
         }
         gps = gy0 = gy1 = gy2 = gpvs = 0.f;
         ++r;
@@ -397,7 +403,6 @@ __global__ void __launch_bounds__(32 * (3 + 4 * NS), 1) k_edge_bwd_tcg(const __g
         auto edge = [&](float w0, float w1, float w2, float w3, float w4, float w5, int slot, float gs, float gv0,
                         float gv1, float gv2) {
           const float4 geo = tg[slot];
-          // filter and its distance derivative, f_c included
           // the accumulator holds the filter and its distance derivative, cutoff and bias included
           const float Ws = w0, dWs = w1, Wvv = w2, dWvv = w3, Wvs = w4, dWvs = w5;
           // L0 (first layer): v = 0 so psi = 0, and no phi gradients are written, so only the
@@ -549,16 +554,16 @@ static int64_t chunk_rows_for(const ModelW& m, int64_t n, int ns) {
 }
 
 int edge_bwd_tc(cudaStream_t st, const ModelW& m, int t, int accumulate, int64_t n, const int32_t* arow,
-                const int32_t* acol, const float4* ar, const float* PHI, float* GPHI, float4* hedge, int* status,
-                const int32_t* aend, const float* G4, const __half* PHIh) {
+                const int32_t* acol, const float4* ar, const float* PHI, float* GPHI, __nv_bfloat16* GP3b,
+                float4* hedge, int* status, const int32_t* aend, const float* G4, const __half* PHIh) {
   if (n == 0) return 0;
-  if (!G4 || (!PHI && !PHIh)) return -1;
+  if (!G4 || (!PHI && !PHIh) || (GPHI && !GP3b)) return -1;
   CUtensorMap tm;
   // the FP16 weights: 2-byte elements like BF16, which is all the TMA copy depends on
   if (!m.L[t].Wfh || !make_tmap_bf16(&tm, m.L[t].Wfh, 3 * kF, 64, 64, 128)) return -2;
   EdgeTcArgs a{};
   a.n = n; a.K = m.K; a.rc = m.rc; a.accumulate = accumulate; a.arow = arow; a.acol = acol; a.ar = ar;
-  a.PHI = PHI; a.PHIh = PHIh; a.GPHI = GPHI; a.hedge = hedge; a.status = status; a.aend = aend; a.G4 = G4;
+  a.PHI = PHI; a.PHIh = PHIh; a.GPHI = GPHI; a.GP3b = GP3b; a.hedge = hedge; a.status = status; a.aend = aend; a.G4 = G4;
   a.chunk_rows = chunk_rows_for(m, n, kBwgNS);
   static bool attr = false;
   if (!attr) {

@@ -29,6 +29,7 @@ struct GemmBf16Args {
   const float* bias;
   const float* aux;
   int ldaux;
+  const float* aux2;   // EPI 5: gsm [M/3][N], the first component of each interleaved quad
   float* out;
   int ldo;
   bf16* outb;
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
         }
         // the chunk's aux values, all loads in flight before any store
         float4 g[8];
-        if (EPI == 2 || EPI == 3) {
+        if (EPI == 2 || EPI == 3 || EPI == 5) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int64_t m = m0 + cr + 4 * j;
@@ -249,7 +250,21 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
               }
               continue;
             }
-            if (EPI == 2) { x.x += g[j].x; x.y += g[j].y; x.z += g[j].z; x.w += g[j].w; }
+            if (EPI == 2 || EPI == 5) { x.x += g[j].x; x.y += g[j].y; x.z += g[j].z; x.w += g[j].w; }
+            if (EPI == 5) {
+              // rows are (atom, spatial component), m = 3 i + a: out[i][c] = (gsm, gvm_0, gvm_1,
+              // gvm_2), the receivers' gradients interleaved per feature for the bulk-gathered
+              // adjoint; the three rows of an atom are written by the same or a neighbouring
+              // chunk, so whole sectors reach DRAM
+              const uint32_t mi = (uint32_t)m / 3u, ca = (uint32_t)m - 3u * mi;
+              float* o = p.out + ((int64_t)mi * N + c0 + cc) * 4;
+              o[1 + ca] = x.x; o[5 + ca] = x.y; o[9 + ca] = x.z; o[13 + ca] = x.w;
+              if (ca == 0) {
+                const float4 gs = __ldg(reinterpret_cast<const float4*>(p.aux2 + (int64_t)mi * N + c0 + cc));
+                o[0] = gs.x; o[4] = gs.y; o[8] = gs.z; o[12] = gs.w;
+              }
+              continue;
+            }
             if (EPI == 3) {
               x.x *= dsilu_fast(g[j].x); x.y *= dsilu_fast(g[j].y); x.z *= dsilu_fast(g[j].z); x.w *= dsilu_fast(g[j].w);
             }
@@ -329,8 +344,12 @@ bool gemm_bf16_supported(int N, int K) { return K % 32 == 0 && K >= 64 && N % 32
 template <int EPI>
 int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t lda, const bf16* W,
               const float* bias, const float* aux, int ldaux, float* out, int ldo, bf16* outb, int ldob,
-              int* status, __half* outh) {
+              int* status, __half* outh, const float* aux2) {
   if (M == 0) return 0;
+  // EPI 5: rows (atom, component) of whole atoms, 32-bit row arithmetic in the epilogue
+  if (EPI == 5 && (M % 3 != 0 || M >= ((int64_t)1 << 31) || !out || !aux || !aux2 ||
+                   (reinterpret_cast<uintptr_t>(aux2) & 15)))
+    return -1;
   // the epilogue moves 16-byte quads of FP32 (8-byte quads of BF16) per row
   if (!gemm_bf16_supported(N, K) || (lda * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) ||
       (reinterpret_cast<uintptr_t>(W) & 15) || (out && (ldo % 4 || (reinterpret_cast<uintptr_t>(out) & 15))) ||
@@ -339,7 +358,7 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
       (aux && (ldaux % 4 || (reinterpret_cast<uintptr_t>(aux) & 15))) || (bias && (reinterpret_cast<uintptr_t>(bias) & 15)))
     return -1;
   GemmBf16Args p{};
-  p.M = M; p.N = N; p.K = K; p.bias = bias; p.aux = aux; p.ldaux = ldaux; p.out = out; p.ldo = ldo;
+  p.M = M; p.N = N; p.K = K; p.bias = bias; p.aux = aux; p.ldaux = ldaux; p.aux2 = aux2; p.out = out; p.ldo = ldo;
   p.outb = outb; p.ldob = ldob; p.status = status; p.outh = (EPI == 0 || EPI == 4) ? outh : nullptr;
   if (p.outh && (reinterpret_cast<uintptr_t>(outh) & 7)) return -1;
   p.b_box_rows = N % 64 == 0 ? 64 : 32;
@@ -362,7 +381,7 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
   size_t smem = 1024 + b_bytes + (size_t)p.a_stages * kATileBytes + t_bytes + 256;
   // a CTA holding more than half of TMEM runs alone on its SM, so allocation never waits
   if (p.tmem_cols > 256 && smem < 120 * 1024) smem = 120 * 1024;
-  static bool attr_set[5] = {false, false, false, false, false};
+  static bool attr_set[6] = {false, false, false, false, false, false};
   if (!attr_set[EPI]) {
     cudaFuncSetAttribute(k_gemm_bf16<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set[EPI] = true;
@@ -377,14 +396,16 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
 }
 
 template int gemm_bf16<0>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
 template int gemm_bf16<1>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
 template int gemm_bf16<2>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
 template int gemm_bf16<3>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
 template int gemm_bf16<4>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
+template int gemm_bf16<5>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
 
 }  // namespace ctd

@@ -396,18 +396,6 @@ __global__ void k_update_bwd_mid_bf16(int64_t n, int F, float eps, const float* 
   st4(GUVb + i * 6 * F + 5 * F + f, o2);
 }
 
-// G4[i][f] = (gsm_i,f, gvm_i,0,f, gvm_i,1,f, gvm_i,2,f): the receivers' gradients interleaved per
-// feature for the bulk-gathered tensor-core adjoint (one 2 KB row per gathered receiver).
-__global__ void k_interleave_g4(int64_t n, int F, const float* __restrict__ Gsm, const float* __restrict__ Gvm,
-                                float4* __restrict__ G4) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= n * F) return;
-  int64_t i = idx / F;
-  int f = (int)(idx % F);
-  const float* gv = Gvm + i * 3 * F + f;
-  G4[idx] = make_float4(Gsm[idx], gv[0], gv[F], gv[2 * F]);
-}
-
 // Backward of PHI packing: gphi_vv = sum_a gpsi_a v_a, gv_a = gvm_a + gpsi_a phi_vv;
 // GP3 = [gphi_s | gphi_vv | gphi_vs]
 // (phi_vv from the FP32 table PHI, or from its FP16 copy PHIh when PHI is null)
@@ -438,6 +426,35 @@ __global__ void k_phi_bwd_pre(int64_t n, int F, const float* __restrict__ GPHI, 
     GP3b[i * 3 * F + F + f] = __float2bfloat16_rn(gpvv);
     GP3b[i * 3 * F + 2 * F + f] = __float2bfloat16_rn(g[4 * F + f]);
   }
+}
+
+// The same backward after the tensor-core adjoint, which wrote the psi gradients GPSI ([n][3F],
+// FP32) and blocks 0 and 2 of GP3b itself: block 1 gets gphi_vv = sum_a gpsi_a v_a, and
+// gv_a = gvm_a + gpsi_a phi_vv, gvm read from the interleaved G4 = (gsm, gvm_0..2) per feature.
+// Thread = 4 features.
+__global__ void k_phi_bwd_psi(int64_t n, int F, const float* __restrict__ GPSI, const float* __restrict__ PHI,
+                              const __half* __restrict__ PHIh, const float* __restrict__ V,
+                              const float4* __restrict__ G4, float* __restrict__ GVn,
+                              __nv_bfloat16* __restrict__ GP3b) {
+  const int F4 = F >> 2;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F4) return;
+  const int64_t i = idx / F4;
+  const int f = 4 * (int)(idx % F4);
+  const float4 pvv = PHI ? ld4(PHI + i * 6 * F + 5 * F + f) : ld4(PHIh + i * 6 * F + 5 * F + f);
+  const float4* q = G4 + i * F + f;
+  const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+  float4 gpvv = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    const int64_t o = i * 3 * F + al * F + f;
+    const float4 g = ld4(GPSI + o), v = ld4(V + o);
+    const float4 gm = al == 0 ? make_float4(q0.y, q1.y, q2.y, q3.y)
+                    : al == 1 ? make_float4(q0.z, q1.z, q2.z, q3.z) : make_float4(q0.w, q1.w, q2.w, q3.w);
+    gpvv.x += g.x * v.x; gpvv.y += g.y * v.y; gpvv.z += g.z * v.z; gpvv.w += g.w * v.w;
+    st4(GVn + o, make_float4(gm.x + g.x * pvv.x, gm.y + g.y * pvv.y, gm.z + g.z * pvv.z, gm.w + g.w * pvv.w));
+  }
+  st4(GP3b + i * 3 * F + F + f, gpvv);
 }
 
 // ================================================================================ edge kernels
@@ -971,8 +988,9 @@ int64_t model_buffer_floats_per_atom(int b, const ModelW& m, int F, int T, int p
     case B_T2: return bf16 ? 0 : 3 * F;
     case B_T3: return bf16 ? 0 : 6 * F;
     case B_GS: case B_GSM: return F;
-    case B_GV: case B_GVM: return 3 * F;
-    case B_GPHI: return 5 * F;
+    case B_GV: return 3 * F;
+    case B_GVM: return g4 ? 0 : 3 * F;   // with the tensor-core adjoint gvm lives only in G4
+    case B_GPHI: return g4 ? 3 * F : 5 * F;   // the tensor-core adjoint writes only the psi gradients
     case B_G4: return g4 ? 4 * F : 0;
     case B_H3: case B_G3: return F / 2;
     default: return 0;
@@ -1196,8 +1214,11 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     // the bulk-gathered tensor-core adjoint reads gsm and gvm interleaved per feature (G4)
     float* G4 = g4 ? B[B_G4] : nullptr;
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_mid_bf16<<<nb4, kThreads, 0, st>>>(n, F, m.eps, GS, T1, UV, AV, GSM, Bb[BB_GUV]); }
-    bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
-    if (G4 && n > 0) { LaunchScope ls_(st); k_interleave_g4<<<nb, kThreads, 0, st>>>(n, F, GSM, GVM, reinterpret_cast<float4*>(G4)); }
+    if (G4)   // gvm = gv + the U/V backward, written straight into G4 beside gsm
+      bad |= gemm_bf16<5>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, G4, F, nullptr, 0, status,
+                          nullptr, GSM);
+    else
+      bad |= gemm_bf16<2>(st, 3 * n, F, 2 * F, Bb[BB_GUV], 2 * F, L.UVtb, nullptr, GV, F, GVM, F, nullptr, 0, status);
     const float* wst = (wstore && !use_tc_bwd && !msg_mma) ? wstore + t * wstore_layer_floats : nullptr;
     // first layer: no phi gradients, no phi backward (its inputs do not depend on positions)
     float* gphi = t > 0 ? GPHI : nullptr;
@@ -1205,15 +1226,22 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     if (n > 0) {
       StageGuard sg(STG_EDGE_BWD);
       if (use_tc_bwd) {
-        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, gphi, hedge, status, aend, G4,
-                           phi32 ? nullptr : PHIh);
+        bad |= edge_bwd_tc(st, m, t, t != T - 1, n, arow, acol, ar, PHI, gphi, gphi ? Bb[BB_GP3] : nullptr, hedge,
+                           status, aend, G4, phi32 ? nullptr : PHIh);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_BWD)
       }
     }
 #undef CTD_BWD
     if (t == 0) break;
-    if (n > 0) { LaunchScope ls_(st); k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, PHIh, V, GVM, nullptr, GV, Bb[BB_GP3]); }
+    if (n > 0) {
+      LaunchScope ls_(st);
+      if (use_tc_bwd)
+        k_phi_bwd_psi<<<nb4, kThreads, 0, st>>>(n, F, GPHI, PHI, PHIh, V, reinterpret_cast<const float4*>(G4), GV,
+                                                Bb[BB_GP3]);
+      else
+        k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, PHIh, V, GVM, nullptr, GV, Bb[BB_GP3]);
+    }
     bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GP3], 3 * F, L.W2tb, nullptr, H1, F, nullptr, 0, Bb[BB_GH1], F, status);
     bad |= gemm_bf16<2>(st, n, F, F, Bb[BB_GH1], F, L.W1tb, nullptr, GSM, F, GS, F, nullptr, 0, status);
   }
