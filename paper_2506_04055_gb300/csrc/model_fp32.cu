@@ -254,7 +254,8 @@ __global__ void k_update_pre(int64_t n, int F, float eps, const float* __restric
   }
 }
 
-// s' = s^m + a_ss + a_sv <Uv, Vv>,  v'_a = v^m_a + a_vv Uv_a
+// s' = s^m + a_ss + a_sv <Uv, Vv>,  v'_a = v^m_a + a_vv Uv_a  (v' skipped when Vn is null: the
+// last layer's vector features reach neither the readout nor the backward)
 template <typename TX>
 __global__ void k_update_post(int64_t n, int F, const float* __restrict__ SM, const float* __restrict__ VM,
                               const TX* __restrict__ UV, const TX* __restrict__ AV,
@@ -265,13 +266,13 @@ __global__ void k_update_post(int64_t n, int F, const float* __restrict__ SM, co
   int f = (int)(idx % F);
   const TX* uv = UV + i * 6 * F;
   const TX* a = AV + i * 3 * F;
-  const float avv = ldx(a + f);
+  const float avv = Vn ? ldx(a + f) : 0.0f;
   float sp = 0.0f;
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
     float u = ldx(uv + al * 2 * F + f), v = ldx(uv + al * 2 * F + F + f);
     sp += u * v;
-    Vn[i * 3 * F + al * F + f] = VM[i * 3 * F + al * F + f] + avv * u;
+    if (Vn) Vn[i * 3 * F + al * F + f] = VM[i * 3 * F + al * F + f] + avv * u;
   }
   const float snew = SM[idx] + ldx(a + 2 * F + f) + ldx(a + F + f) * sp;
   Sn[idx] = snew;
@@ -785,6 +786,142 @@ __global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restr
   }
 }
 
+// The readout MLP and its backward in one pass: per atom h = R1 s + d1 (F/2 units),
+// E_i = e_scale w_i (R2 . silu(h) + d2) and, with gradients, g = w_i e_scale R2 * silu'(h) and
+// gs = R1^T g.  The arithmetic and its order are those of the GEMM, readout and GEMM launches it
+// replaces (FP32 fmaf chains over the inputs and over the hidden units, the energy terms in FP64
+// from d2 up), so the results are the same bit for bit.  Block b takes the 256-atom ranges
+// starting at 256 (b + G k) (G = blocks), as 64-atom tiles, and its thread t then adds the energy
+// of atom 256 (b + G k) + t: the same atoms in the same order as the grid-stride energy sum.
+static bool readout_is_fused(int F) { return F == 64 || F == 128; }
+
+template <int F>
+__global__ __launch_bounds__(256) void k_readout_fused(int64_t n, float e_scale, const float* __restrict__ S,
+                                                       const float* __restrict__ R1, const float* __restrict__ d1,
+                                                       const float* __restrict__ R2, const float* __restrict__ d2,
+                                                       const float* __restrict__ ew, float* __restrict__ GS,
+                                                       float* __restrict__ e_atom, double* __restrict__ partials) {
+  constexpr int FH = F / 2, TA = 64, SP = F + 4, HP = FH + 1, F4 = F / 4;
+  extern __shared__ float4 rd_smem4[];
+  float* sR1 = reinterpret_cast<float*>(rd_smem4);   // [FH][SP]  R1 rows (unit, input)
+  float* sS = sR1 + FH * SP;                         // [TA][SP]  the tile's s rows
+  float* sH = sS + TA * SP;                          // [TA][HP]  h, then g
+  float* sE = sH + TA * HP;                          // [256]     per-atom energies of the range
+  float* sR2 = sE + 256;                             // [FH]
+  __shared__ double sbuf[kThreads / 32];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < FH * F4; idx += 256)
+    *reinterpret_cast<float4*>(sR1 + (idx / F4) * SP + 4 * (idx % F4)) = reinterpret_cast<const float4*>(R1)[idx];
+  for (int k = tid; k < FH; k += 256) sR2[k] = R2[k];
+  __syncthreads();
+  double acc = 0.0, comp = 0.0;
+  const int64_t G = (int64_t)gridDim.x * 256;
+  for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += G) {
+    for (int t4 = 0; t4 < 4; ++t4) {
+      const int64_t a0 = base + t4 * TA;
+      for (int idx = tid; idx < TA * F4; idx += 256) {
+        const int a = idx / F4, k4 = idx % F4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a0 + a < n) v = reinterpret_cast<const float4*>(S + (a0 + a) * F)[k4];
+        *reinterpret_cast<float4*>(sS + a * SP + 4 * k4) = v;
+      }
+      __syncthreads();
+      {
+        // h: thread -> atoms aa, aa + 32 and units oo + 8 j
+        constexpr int OPT = FH / 8;
+        const int aa = tid >> 3, oo = tid & 7;
+        float h0[OPT], h1[OPT];
+#pragma unroll
+        for (int j = 0; j < OPT; ++j) h0[j] = h1[j] = 0.0f;
+#pragma unroll 4
+        for (int k = 0; k < F; k += 4) {
+          const float4 s0 = *reinterpret_cast<const float4*>(sS + aa * SP + k);
+          const float4 s1 = *reinterpret_cast<const float4*>(sS + (aa + 32) * SP + k);
+#pragma unroll
+          for (int j = 0; j < OPT; ++j) {
+            const float4 r = *reinterpret_cast<const float4*>(sR1 + (oo + 8 * j) * SP + k);
+            h0[j] = fmaf(s0.x, r.x, h0[j]); h0[j] = fmaf(s0.y, r.y, h0[j]);
+            h0[j] = fmaf(s0.z, r.z, h0[j]); h0[j] = fmaf(s0.w, r.w, h0[j]);
+            h1[j] = fmaf(s1.x, r.x, h1[j]); h1[j] = fmaf(s1.y, r.y, h1[j]);
+            h1[j] = fmaf(s1.z, r.z, h1[j]); h1[j] = fmaf(s1.w, r.w, h1[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < OPT; ++j) {
+          const int o = oo + 8 * j;
+          const float b = d1 ? d1[o] : 0.0f;
+          sH[aa * HP + o] = h0[j] + b;
+          sH[(aa + 32) * HP + o] = h1[j] + b;
+        }
+      }
+      __syncthreads();
+      if (tid < TA) {
+        // the atom's energy: terms in FP64 from d2 up over the units in order; g in place of h
+        const int64_t i = a0 + tid;
+        float ef = 0.0f;
+        if (i < n) {
+          const float wi = ew ? ew[i] : 1.0f;
+          double e = (double)d2[0];
+          for (int k = 0; k < FH; ++k) {
+            const float h = sH[tid * HP + k];
+            e = fma((double)sR2[k], (double)silu_f(h), e);
+            if (GS) sH[tid * HP + k] = wi * (e_scale * sR2[k] * dsilu_f(h));
+          }
+          e *= (double)e_scale;
+          e *= (double)wi;
+          ef = (float)e;
+          if (e_atom) e_atom[i] = ef;
+        }
+        sE[t4 * TA + tid] = ef;
+      }
+      __syncthreads();
+      if (GS) {
+        // gs = R1^T g: thread -> inputs 4 k4 .. 4 k4 + 3 of atoms ab + AT m
+        constexpr int AT = 256 / F4, APT = TA / AT;
+        const int k4 = tid % F4, ab = tid / F4;
+        float4 gq[APT];
+#pragma unroll
+        for (int mm = 0; mm < APT; ++mm) gq[mm] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+        for (int o = 0; o < FH; ++o) {
+          const float4 r = *reinterpret_cast<const float4*>(sR1 + o * SP + 4 * k4);
+#pragma unroll
+          for (int mm = 0; mm < APT; ++mm) {
+            const float g = sH[(ab + AT * mm) * HP + o];
+            gq[mm].x = fmaf(g, r.x, gq[mm].x); gq[mm].y = fmaf(g, r.y, gq[mm].y);
+            gq[mm].z = fmaf(g, r.z, gq[mm].z); gq[mm].w = fmaf(g, r.w, gq[mm].w);
+          }
+        }
+#pragma unroll
+        for (int mm = 0; mm < APT; ++mm) {
+          const int64_t i = a0 + ab + AT * mm;
+          if (i < n) *reinterpret_cast<float4*>(GS + i * F + 4 * k4) = gq[mm];
+        }
+      }
+      __syncthreads();   // the next tile overwrites sS and sH
+    }
+    if (base + tid < n) {
+      const double x = (double)sE[tid], t = acc + x;   // Neumaier
+      comp += fabs(acc) >= fabs(x) ? (acc - t) + x : (x - t) + acc;
+      acc = t;
+    }
+  }
+  double v = acc + comp;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) sbuf[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) sum += sbuf[w];
+    partials[blockIdx.x] = sum;
+  }
+}
+
+template <int F>
+static size_t readout_fused_smem() {
+  return sizeof(float) * ((size_t)(F / 2) * (F + 4) + (size_t)64 * (F + 4) + (size_t)64 * (F / 2 + 1) + 256 + F / 2);
+}
+
 // Error-free transformations in FP32 (Knuth's TwoSum; the exact product split by one FMA):
 // a + b = s + e and a * b = p + e exactly, with s, p the rounded results.
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
@@ -958,6 +1095,37 @@ enum BufId {
 
 int model_buffer_count() { return B_COUNT; }
 
+// The readout and, with gradients, gs = dE/ds_T: one fused launch for F = 64 and 128, else the
+// FP32 GEMM, readout and GEMM launches (H3 and G3 buffers).
+static void readout_fwd_bwd(cudaStream_t st, const ModelW& m, int64_t n, const float* S_T, const float* ew,
+                            bool need_grad, float* const* B, float* e_atom, double* partials, int n_partials) {
+  const int F = m.F, Fh = F / 2;
+  if (readout_is_fused(F)) {
+    LaunchScope ls_(st);
+    float* gs = need_grad ? B[B_GS] : nullptr;
+    if (F == 128) {
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_readout_fused<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)readout_fused_smem<128>());
+        attr = true;
+      }
+      k_readout_fused<128><<<n_partials, kThreads, readout_fused_smem<128>(), st>>>(n, m.e_scale, S_T, m.R1, m.d1, m.R2,
+                                                                                    m.d2, ew, gs, e_atom, partials);
+    } else {
+      k_readout_fused<64><<<n_partials, kThreads, readout_fused_smem<64>(), st>>>(n, m.e_scale, S_T, m.R1, m.d1, m.R2,
+                                                                                  m.d2, ew, gs, e_atom, partials);
+    }
+    return;
+  }
+  gemm<EPI_BIAS>(st, n, Fh, F, S_T, F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
+  {
+    LaunchScope ls_(st);
+    k_readout<<<n_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2, ew,
+                                               need_grad ? B[B_G3] : nullptr, nullptr, e_atom, partials);
+  }
+  if (need_grad) gemm<EPI_BIAS>(st, n, F, Fh, B[B_G3], Fh, m.R1, nullptr, nullptr, 0, B[B_GS], F);
+}
+
 // floats per atom of buffer id b (0 if unused for this T)
 // The interleaved receiver gradients (G4) are read only by the bulk-gathered tensor-core
 // adjoint of the BF16 path; no other path allocates them.
@@ -975,7 +1143,7 @@ int64_t model_buffer_floats_per_atom(int b, const ModelW& m, int F, int T, int p
   const bool g4 = model_uses_g4(m, precision), bf16 = precision == CTD_PREC_BF16;
   auto layer = [&](int base, int cnt) { return b >= base && b < base + cnt; };
   if (layer(B_S0, T + 1)) return F;
-  if (layer(B_V0, T + 1)) return 3 * F;
+  if (layer(B_V0, T + 1)) return T > 0 && b == B_V0 + T ? 0 : 3 * F;   // v[T] is never formed
   if (layer(B_PHI0, T)) return model_phi_fp16_only(m, precision) ? 0 : 6 * F;
   if (layer(B_H10, T)) return F;
   if (b == B_SM0 && T > 0) return F;
@@ -992,7 +1160,7 @@ int64_t model_buffer_floats_per_atom(int b, const ModelW& m, int F, int T, int p
     case B_GVM: return g4 ? 0 : 3 * F;   // with the tensor-core adjoint gvm lives only in G4
     case B_GPHI: return g4 ? 3 * F : 5 * F;   // the tensor-core adjoint writes only the psi gradients
     case B_G4: return g4 ? 4 * F : 0;
-    case B_H3: case B_G3: return F / 2;
+    case B_H3: case B_G3: return readout_is_fused(F) ? 0 : F / 2;   // the fused readout keeps h and g on chip
     default: return 0;
   }
 }
@@ -1006,7 +1174,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
                                  const float* ew) {
   edge_smem_setup();
   StageGuard node_stage(STG_NODE);
-  const int F = m.F, T = m.T, Fh = F / 2;
+  const int F = m.F, T = m.T;
   const unsigned nb = blocks_for(n * F), nb4 = blocks_for(n * F / 4);   // nb4: four features per thread
   if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], nullptr); }
   for (int t = 0; t < T; ++t) {
@@ -1031,15 +1199,16 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     if (n > 0) { LaunchScope ls_(st); k_update_pre<float><<<nb4, kThreads, 0, st>>>(n, F, m.eps, SM, UV, T1, nullptr); }
     gemm<EPI_BIAS_SILU>(st, n, F, 2 * F, T1, 2 * F, L.A1t, L.c1, nullptr, 0, H2, F, T2, F);
     gemm<EPI_BIAS>(st, n, 3 * F, F, T2, F, L.A2t, L.c2, nullptr, 0, AV, 3 * F);
-    if (n > 0) { LaunchScope ls_(st); k_update_post<float><<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1], nullptr); }
+    if (n > 0) {
+      LaunchScope ls_(st);
+      k_update_post<float><<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1],
+                                                    t + 1 < T ? B[B_V0 + t + 1] : nullptr, nullptr);
+    }
   }
   // readout
-  gemm<EPI_BIAS>(st, n, Fh, F, B[B_S0 + T], F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
-  { LaunchScope ls_(st); k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2, ew,
-                                                    need_grad ? B[B_G3] : nullptr, nullptr, e_atom, energy_partials); }
+  // readout, and dU/ds^T = G3 R1
+  readout_fwd_bwd(st, m, n, B[B_S0 + T], ew, need_grad, B, e_atom, energy_partials, n_energy_partials);
   if (!need_grad) return;
-  // dU/ds^T = G3 R1
-  gemm<EPI_BIAS>(st, n, F, Fh, B[B_G3], Fh, m.R1, nullptr, nullptr, 0, B[B_GS], F);
   if (n > 0) cudaMemsetAsync(B[B_GV], 0, sizeof(float) * (size_t)n * 3 * F, st);
   for (int t = T - 1; t >= 0; --t) {
     const LayerW& L = m.L[t];
@@ -1116,7 +1285,7 @@ bool model_stores_edges(const ModelW& m, int precision) {
 }
 
 int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T, bool msg_mma) {
-  if (b >= BB_S0 && b < BB_S0 + T + 1) return F;
+  if (b >= BB_S0 && b < BB_S0 + T + 1) return T > 0 && b == BB_S0 + T ? 0 : F;   // no BF16 s[T]
   if (b >= BB_PHIH0 && b < BB_PHIH0 + kMaxT) return msg_mma && b < BB_PHIH0 + T ? 6 * F : 0;
   if (b >= BB_UVH0 && b < BB_UVH0 + kMaxT) return b < BB_UVH0 + T ? 6 * F : 0;
   if (b >= BB_AVH0 && b < BB_AVH0 + kMaxT) return b < BB_AVH0 + T ? 3 * F : 0;
@@ -1138,7 +1307,7 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
                                 const float* ew) {
   edge_smem_setup();
   StageGuard node_stage(STG_NODE);
-  const int F = m.F, T = m.T, Fh = F / 2;
+  const int F = m.F, T = m.T;
   const unsigned nb = blocks_for(n * F), nb4 = blocks_for(n * F / 4);   // nb4: four features per thread
   int bad = 0;
   // F = 128: the message step as the tensor-core contraction over each receiver's edges
@@ -1183,21 +1352,16 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A2], F, L.A2b, L.c2, nullptr, 0, nullptr, 3 * F, nullptr, 0, status, AV);
     if (n > 0) {
       LaunchScope ls_(st);
-      k_update_post<__half><<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1],
-                                                     Bb[BB_S0 + t + 1]);
+      // the last layer's v and BF16 s feed nothing: only its FP32 s reaches the readout
+      k_update_post<__half><<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1],
+                                                     t + 1 < T ? B[B_V0 + t + 1] : nullptr,
+                                                     t + 1 < T ? Bb[BB_S0 + t + 1] : nullptr);
     }
   }
   // The readout MLP (F -> F/2 -> 1, ~1 % of the node FLOPs) stays in FP32: its output is the
   // per-atom energy itself, which BF16 operands would perturb by ~2^-9 of the readout terms.
-  gemm<EPI_BIAS>(st, n, Fh, F, B[B_S0 + T], F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
-  {
-    LaunchScope ls_(st);
-    k_readout<<<n_energy_partials, kThreads, 0, st>>>(n, Fh, m.e_scale, B[B_H3], m.R2, m.d2, ew,
-                                                      need_grad ? B[B_G3] : nullptr, nullptr, e_atom,
-                                                      energy_partials);
-  }
+  readout_fwd_bwd(st, m, n, B[B_S0 + T], ew, need_grad, B, e_atom, energy_partials, n_energy_partials);
   if (!need_grad) return bad;
-  gemm<EPI_BIAS>(st, n, F, Fh, B[B_G3], Fh, m.R1, nullptr, nullptr, 0, B[B_GS], F);
   if (n > 0) cudaMemsetAsync(B[B_GV], 0, sizeof(float) * (size_t)n * 3 * F, st);
   for (int t = T - 1; t >= 0; --t) {
     const LayerW& L = m.L[t];
