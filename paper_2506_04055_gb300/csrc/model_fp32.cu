@@ -254,29 +254,40 @@ __global__ void k_update_pre(int64_t n, int F, float eps, const float* __restric
   }
 }
 
-// s' = s^m + a_ss + a_sv <Uv, Vv>,  v'_a = v^m_a + a_vv Uv_a  (v' skipped when Vn is null: the
-// last layer's vector features reach neither the readout nor the backward)
-template <typename TX>
+// s' = s^m + a_ss + a_sv <Uv, Vv>,  v'_a = v^m_a + a_vv Uv_a; WV false: s' only (the last
+// layer's v and BF16 s reach neither the readout nor the backward).  Thread = 4 features.
+template <typename TX, bool WV>
 __global__ void k_update_post(int64_t n, int F, const float* __restrict__ SM, const float* __restrict__ VM,
                               const TX* __restrict__ UV, const TX* __restrict__ AV,
                               float* __restrict__ Sn, float* __restrict__ Vn, __nv_bfloat16* __restrict__ Snb) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= n * F) return;
-  int64_t i = idx / F;
-  int f = (int)(idx % F);
+  const int F4 = F >> 2;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * F4) return;
+  const int64_t i = idx / F4;
+  const int f = 4 * (int)(idx % F4);
   const TX* uv = UV + i * 6 * F;
   const TX* a = AV + i * 3 * F;
-  const float avv = Vn ? ldx(a + f) : 0.0f;
-  float sp = 0.0f;
+  float4 sp = make_float4(0.f, 0.f, 0.f, 0.f), u[3];
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
-    float u = ldx(uv + al * 2 * F + f), v = ldx(uv + al * 2 * F + F + f);
-    sp += u * v;
-    if (Vn) Vn[i * 3 * F + al * F + f] = VM[i * 3 * F + al * F + f] + avv * u;
+    u[al] = ld4(uv + al * 2 * F + f);
+    const float4 v = ld4(uv + al * 2 * F + F + f);
+    sp.x += u[al].x * v.x; sp.y += u[al].y * v.y; sp.z += u[al].z * v.z; sp.w += u[al].w * v.w;
   }
-  const float snew = SM[idx] + ldx(a + 2 * F + f) + ldx(a + F + f) * sp;
-  Sn[idx] = snew;
-  if (Snb) Snb[idx] = __float2bfloat16_rn(snew);
+  if (WV) {
+    const float4 avv = ld4(a + f);
+#pragma unroll
+    for (int al = 0; al < 3; ++al) {
+      const float4 vm = ld4(VM + i * 3 * F + al * F + f);
+      st4(Vn + i * 3 * F + al * F + f, make_float4(vm.x + avv.x * u[al].x, vm.y + avv.y * u[al].y,
+                                                   vm.z + avv.z * u[al].z, vm.w + avv.w * u[al].w));
+    }
+  }
+  const float4 sm = ld4(SM + i * F + f), ass = ld4(a + 2 * F + f), asv = ld4(a + F + f);
+  const float4 sn = make_float4(sm.x + ass.x + asv.x * sp.x, sm.y + ass.y + asv.y * sp.y,
+                                sm.z + ass.z + asv.z * sp.z, sm.w + ass.w + asv.w * sp.w);
+  st4(Sn + i * F + f, sn);
+  if (Snb) st4(Snb + i * F + f, sn);
 }
 
 // Backward of the update elementwise part: given gs' (GS), gv' (GV):
@@ -786,142 +797,6 @@ __global__ void k_readout(int64_t n, int Fh, float e_scale, const float* __restr
   }
 }
 
-// The readout MLP and its backward in one pass: per atom h = R1 s + d1 (F/2 units),
-// E_i = e_scale w_i (R2 . silu(h) + d2) and, with gradients, g = w_i e_scale R2 * silu'(h) and
-// gs = R1^T g.  The arithmetic and its order are those of the GEMM, readout and GEMM launches it
-// replaces (FP32 fmaf chains over the inputs and over the hidden units, the energy terms in FP64
-// from d2 up), so the results are the same bit for bit.  Block b takes the 256-atom ranges
-// starting at 256 (b + G k) (G = blocks), as 64-atom tiles, and its thread t then adds the energy
-// of atom 256 (b + G k) + t: the same atoms in the same order as the grid-stride energy sum.
-static bool readout_is_fused(int F) { return F == 64 || F == 128; }
-
-template <int F>
-__global__ __launch_bounds__(256) void k_readout_fused(int64_t n, float e_scale, const float* __restrict__ S,
-                                                       const float* __restrict__ R1, const float* __restrict__ d1,
-                                                       const float* __restrict__ R2, const float* __restrict__ d2,
-                                                       const float* __restrict__ ew, float* __restrict__ GS,
-                                                       float* __restrict__ e_atom, double* __restrict__ partials) {
-  constexpr int FH = F / 2, TA = 64, SP = F + 4, HP = FH + 1, F4 = F / 4;
-  extern __shared__ float4 rd_smem4[];
-  float* sR1 = reinterpret_cast<float*>(rd_smem4);   // [FH][SP]  R1 rows (unit, input)
-  float* sS = sR1 + FH * SP;                         // [TA][SP]  the tile's s rows
-  float* sH = sS + TA * SP;                          // [TA][HP]  h, then g
-  float* sE = sH + TA * HP;                          // [256]     per-atom energies of the range
-  float* sR2 = sE + 256;                             // [FH]
-  __shared__ double sbuf[kThreads / 32];
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < FH * F4; idx += 256)
-    *reinterpret_cast<float4*>(sR1 + (idx / F4) * SP + 4 * (idx % F4)) = reinterpret_cast<const float4*>(R1)[idx];
-  for (int k = tid; k < FH; k += 256) sR2[k] = R2[k];
-  __syncthreads();
-  double acc = 0.0, comp = 0.0;
-  const int64_t G = (int64_t)gridDim.x * 256;
-  for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += G) {
-    for (int t4 = 0; t4 < 4; ++t4) {
-      const int64_t a0 = base + t4 * TA;
-      for (int idx = tid; idx < TA * F4; idx += 256) {
-        const int a = idx / F4, k4 = idx % F4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (a0 + a < n) v = reinterpret_cast<const float4*>(S + (a0 + a) * F)[k4];
-        *reinterpret_cast<float4*>(sS + a * SP + 4 * k4) = v;
-      }
-      __syncthreads();
-      {
-        // h: thread -> atoms aa, aa + 32 and units oo + 8 j
-        constexpr int OPT = FH / 8;
-        const int aa = tid >> 3, oo = tid & 7;
-        float h0[OPT], h1[OPT];
-#pragma unroll
-        for (int j = 0; j < OPT; ++j) h0[j] = h1[j] = 0.0f;
-#pragma unroll 4
-        for (int k = 0; k < F; k += 4) {
-          const float4 s0 = *reinterpret_cast<const float4*>(sS + aa * SP + k);
-          const float4 s1 = *reinterpret_cast<const float4*>(sS + (aa + 32) * SP + k);
-#pragma unroll
-          for (int j = 0; j < OPT; ++j) {
-            const float4 r = *reinterpret_cast<const float4*>(sR1 + (oo + 8 * j) * SP + k);
-            h0[j] = fmaf(s0.x, r.x, h0[j]); h0[j] = fmaf(s0.y, r.y, h0[j]);
-            h0[j] = fmaf(s0.z, r.z, h0[j]); h0[j] = fmaf(s0.w, r.w, h0[j]);
-            h1[j] = fmaf(s1.x, r.x, h1[j]); h1[j] = fmaf(s1.y, r.y, h1[j]);
-            h1[j] = fmaf(s1.z, r.z, h1[j]); h1[j] = fmaf(s1.w, r.w, h1[j]);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < OPT; ++j) {
-          const int o = oo + 8 * j;
-          const float b = d1 ? d1[o] : 0.0f;
-          sH[aa * HP + o] = h0[j] + b;
-          sH[(aa + 32) * HP + o] = h1[j] + b;
-        }
-      }
-      __syncthreads();
-      if (tid < TA) {
-        // the atom's energy: terms in FP64 from d2 up over the units in order; g in place of h
-        const int64_t i = a0 + tid;
-        float ef = 0.0f;
-        if (i < n) {
-          const float wi = ew ? ew[i] : 1.0f;
-          double e = (double)d2[0];
-          for (int k = 0; k < FH; ++k) {
-            const float h = sH[tid * HP + k];
-            e = fma((double)sR2[k], (double)silu_f(h), e);
-            if (GS) sH[tid * HP + k] = wi * (e_scale * sR2[k] * dsilu_f(h));
-          }
-          e *= (double)e_scale;
-          e *= (double)wi;
-          ef = (float)e;
-          if (e_atom) e_atom[i] = ef;
-        }
-        sE[t4 * TA + tid] = ef;
-      }
-      __syncthreads();
-      if (GS) {
-        // gs = R1^T g: thread -> inputs 4 k4 .. 4 k4 + 3 of atoms ab + AT m
-        constexpr int AT = 256 / F4, APT = TA / AT;
-        const int k4 = tid % F4, ab = tid / F4;
-        float4 gq[APT];
-#pragma unroll
-        for (int mm = 0; mm < APT; ++mm) gq[mm] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-        for (int o = 0; o < FH; ++o) {
-          const float4 r = *reinterpret_cast<const float4*>(sR1 + o * SP + 4 * k4);
-#pragma unroll
-          for (int mm = 0; mm < APT; ++mm) {
-            const float g = sH[(ab + AT * mm) * HP + o];
-            gq[mm].x = fmaf(g, r.x, gq[mm].x); gq[mm].y = fmaf(g, r.y, gq[mm].y);
-            gq[mm].z = fmaf(g, r.z, gq[mm].z); gq[mm].w = fmaf(g, r.w, gq[mm].w);
-          }
-        }
-#pragma unroll
-        for (int mm = 0; mm < APT; ++mm) {
-          const int64_t i = a0 + ab + AT * mm;
-          if (i < n) *reinterpret_cast<float4*>(GS + i * F + 4 * k4) = gq[mm];
-        }
-      }
-      __syncthreads();   // the next tile overwrites sS and sH
-    }
-    if (base + tid < n) {
-      const double x = (double)sE[tid], t = acc + x;   // Neumaier
-      comp += fabs(acc) >= fabs(x) ? (acc - t) + x : (x - t) + acc;
-      acc = t;
-    }
-  }
-  double v = acc + comp;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((tid & 31) == 0) sbuf[tid >> 5] = v;
-  __syncthreads();
-  if (tid == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) sum += sbuf[w];
-    partials[blockIdx.x] = sum;
-  }
-}
-
-template <int F>
-static size_t readout_fused_smem() {
-  return sizeof(float) * ((size_t)(F / 2) * (F + 4) + (size_t)64 * (F + 4) + (size_t)64 * (F / 2 + 1) + 256 + F / 2);
-}
-
 // Error-free transformations in FP32 (Knuth's TwoSum; the exact product split by one FMA):
 // a + b = s + e and a * b = p + e exactly, with s, p the rounded results.
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
@@ -935,6 +810,167 @@ __device__ __forceinline__ void ff_add(float& s, float& c, float x, float xe) {
   two_sum_f(s, x, t, e);
   s = t;
   c = __fadd_rn(c, __fadd_rn(e, xe));
+}
+
+static bool readout_is_fused(int F) { return F == 64 || F == 128; }
+
+// The readout MLP and its backward in one pass: per atom h = R1 s + d1 (F/2 units),
+// E_i = e_scale w_i (R2 . silu(h) + d2) and, with gradients, g = w_i e_scale R2 * silu'(h) and
+// gs = R1^T g, h and gs as FP32 fmaf chains over the inputs and over the hidden units in order
+// (as the GEMMs they replace), the energy terms in FP64, summed over the 16 threads that hold an
+// atom's units in a fixed tree (so independent of the launch).  A block of 512 threads stands for one
+// 256-thread block of the grid-stride energy sum: it takes the 256-atom ranges starting at
+// 256 (b + G k) (G = blocks), as two 128-atom tiles, and its thread t < 256 adds the energy of
+// atom 256 (b + G k) + t, the same atoms in the same order.  s and R1 are staged transposed so
+// that each thread's 4 atoms and 4 units come in 16-byte shared loads.
+template <int F>
+__global__ __launch_bounds__(512, 1) void k_readout_fused(int64_t n, float e_scale, const float* __restrict__ S,
+                                                       const float* __restrict__ R1, const float* __restrict__ R1t,
+                                                       const float* __restrict__ d1, const float* __restrict__ R2,
+                                                       const float* __restrict__ d2, const float* __restrict__ ew,
+                                                       float* __restrict__ GS, float* __restrict__ e_atom,
+                                                       double* __restrict__ partials) {
+  constexpr int FH = F / 2, TA = 128, F4 = F / 4, GP = FH + 4;
+  constexpr int OPT = FH / 16, KPT = F / 16;   // units (forward) and inputs (backward) per thread
+  extern __shared__ float4 rd_smem4[];
+  float* sR1T = reinterpret_cast<float*>(rd_smem4);   // [F][FH]   R1^T (input, unit)
+  float* sR1 = sR1T + F * FH;                         // [FH][F]   R1 (unit, input)
+  float* sST = sR1 + FH * F;                          // [F][TA]   s^T of the tile
+  float* sG = sST + F * TA;                           // [TA][GP]  g of the tile
+  float* sE = sG + TA * GP;                           // [256]     per-atom energies of the range
+  float* sR2 = sE + 256;                              // [FH]
+  __shared__ double sbuf[8];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;   // ty: atoms 4 ty .. 4 ty + 3
+  for (int idx = tid; idx < F * FH / 4; idx += 512) {
+    reinterpret_cast<float4*>(sR1T)[idx] = reinterpret_cast<const float4*>(R1t)[idx];
+    reinterpret_cast<float4*>(sR1)[idx] = reinterpret_cast<const float4*>(R1)[idx];
+  }
+  for (int k = tid; k < FH; k += 512) sR2[k] = R2[k];
+  __syncthreads();
+  double acc = 0.0, comp = 0.0;
+  const int64_t G = (int64_t)gridDim.x * 256;
+  for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += G) {
+    for (int t2 = 0; t2 < 2; ++t2) {
+      const int64_t a0 = base + t2 * TA;
+      for (int idx = tid; idx < TA * F4; idx += 512) {
+        const int a = idx % TA, k4 = idx / TA;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a0 + a < n) v = reinterpret_cast<const float4*>(S + (a0 + a) * F)[k4];
+        sST[(4 * k4 + 0) * TA + a] = v.x;
+        sST[(4 * k4 + 1) * TA + a] = v.y;
+        sST[(4 * k4 + 2) * TA + a] = v.z;
+        sST[(4 * k4 + 3) * TA + a] = v.w;
+      }
+      __syncthreads();
+      {
+        float h[4][OPT];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < OPT; ++j) h[i][j] = 0.0f;
+#pragma unroll 4
+        for (int k = 0; k < F; ++k) {
+          const float4 sa = *reinterpret_cast<const float4*>(sST + k * TA + 4 * ty);
+          float r[OPT];
+          if constexpr (OPT == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(sR1T + k * FH + 4 * tx);
+            r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+          } else {
+            const float2 q = *reinterpret_cast<const float2*>(sR1T + k * FH + 2 * tx);
+            r[0] = q.x; r[1] = q.y;
+          }
+          const float sv[4] = {sa.x, sa.y, sa.z, sa.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < OPT; ++j) h[i][j] = fmaf(sv[i], r[j], h[i][j]);
+        }
+        // energy terms of this thread's units, each product split exactly (FMA) and added into a
+        // float-float pair (TwoSum), the pairs of the 16 threads of an atom combined in a fixed
+        // tree: the terms can largely cancel, and this keeps ~44 bits of their sum without the
+        // FP64 pipe; g = w e_scale R2 silu'(h) goes to the g tile
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t ai = a0 + 4 * ty + i;
+          const float wi = ai < n && ew ? ew[ai] : 1.0f;
+          float es = 0.0f, ec = 0.0f;
+#pragma unroll
+          for (int j = 0; j < OPT; ++j) {
+            const int o = OPT * tx + j;
+            const float hk = h[i][j] + (d1 ? d1[o] : 0.0f);
+            const float sl = silu_f(hk), pr = __fmul_rn(sR2[o], sl);
+            ff_add(es, ec, pr, __fmaf_rn(sR2[o], sl, -pr));
+            if (GS) sG[(4 * ty + i) * GP + o] = ai < n ? wi * (e_scale * sR2[o] * dsilu_f(hk)) : 0.0f;
+          }
+#pragma unroll
+          for (int off = 1; off < 16; off <<= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, es, off), oc = __shfl_xor_sync(0xffffffffu, ec, off);
+            ff_add(es, ec, os, oc);
+          }
+          if (tx == 0) {
+            double e = ((double)es + (double)ec + (double)d2[0]) * (double)e_scale;
+            e *= (double)wi;
+            const float ef = ai < n ? (float)e : 0.0f;
+            if (ai < n && e_atom) e_atom[ai] = ef;
+            sE[t2 * TA + 4 * ty + i] = ef;
+          }
+        }
+      }
+      __syncthreads();
+      if (GS) {
+        // gs = R1^T g over the units in order: thread -> atoms 4 ty .. + 3, inputs KPT tx .. + KPT - 1
+        float gq[4][KPT];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < KPT; ++j) gq[i][j] = 0.0f;
+#pragma unroll 4
+        for (int o = 0; o < FH; ++o) {
+          const float gv[4] = {sG[(4 * ty) * GP + o], sG[(4 * ty + 1) * GP + o], sG[(4 * ty + 2) * GP + o],
+                               sG[(4 * ty + 3) * GP + o]};
+          float r[KPT];
+#pragma unroll
+          for (int j = 0; j < KPT; j += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(sR1 + o * F + KPT * tx + j);
+            r[j] = q.x; r[j + 1] = q.y; r[j + 2] = q.z; r[j + 3] = q.w;
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < KPT; ++j) gq[i][j] = fmaf(gv[i], r[j], gq[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t ai = a0 + 4 * ty + i;
+          if (ai < n)
+#pragma unroll
+            for (int j = 0; j < KPT; j += 4)
+              *reinterpret_cast<float4*>(GS + ai * F + KPT * tx + j) =
+                  make_float4(gq[i][j], gq[i][j + 1], gq[i][j + 2], gq[i][j + 3]);
+        }
+      }
+      __syncthreads();   // the next tile overwrites s^T and g
+    }
+    if (tid < 256 && base + tid < n) {
+      const double x = (double)sE[tid], t = acc + x;   // Neumaier
+      comp += fabs(acc) >= fabs(x) ? (acc - t) + x : (x - t) + acc;
+      acc = t;
+    }
+  }
+  double v = acc + comp;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0 && tid < 256) sbuf[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < 8; ++w) sum += sbuf[w];
+    partials[blockIdx.x] = sum;
+  }
+}
+
+template <int F>
+static size_t readout_fused_smem() {
+  return sizeof(float) * ((size_t)2 * F * (F / 2) + (size_t)F * 128 + (size_t)128 * (F / 2 + 4) + 256 + F / 2);
 }
 
 // F_i = sum_{e in row i} (hedge[rev e] - hedge[e]);  virial partials = sum_e r_e (x) hedge[e]
@@ -1103,18 +1139,18 @@ static void readout_fwd_bwd(cudaStream_t st, const ModelW& m, int64_t n, const f
   if (readout_is_fused(F)) {
     LaunchScope ls_(st);
     float* gs = need_grad ? B[B_GS] : nullptr;
-    if (F == 128) {
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(k_readout_fused<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)readout_fused_smem<128>());
-        attr = true;
-      }
-      k_readout_fused<128><<<n_partials, kThreads, readout_fused_smem<128>(), st>>>(n, m.e_scale, S_T, m.R1, m.d1, m.R2,
-                                                                                    m.d2, ew, gs, e_atom, partials);
-    } else {
-      k_readout_fused<64><<<n_partials, kThreads, readout_fused_smem<64>(), st>>>(n, m.e_scale, S_T, m.R1, m.d1, m.R2,
-                                                                                  m.d2, ew, gs, e_atom, partials);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_readout_fused<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)readout_fused_smem<128>());
+      cudaFuncSetAttribute(k_readout_fused<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)readout_fused_smem<64>());
+      attr = true;
     }
+    if (F == 128)
+      k_readout_fused<128><<<n_partials, 512, readout_fused_smem<128>(), st>>>(n, m.e_scale, S_T, m.R1, m.R1t, m.d1,
+                                                                               m.R2, m.d2, ew, gs, e_atom, partials);
+    else
+      k_readout_fused<64><<<n_partials, 512, readout_fused_smem<64>(), st>>>(n, m.e_scale, S_T, m.R1, m.R1t, m.d1,
+                                                                             m.R2, m.d2, ew, gs, e_atom, partials);
     return;
   }
   gemm<EPI_BIAS>(st, n, Fh, F, S_T, F, m.R1t, m.d1, nullptr, 0, B[B_H3], Fh);
@@ -1201,8 +1237,11 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     gemm<EPI_BIAS>(st, n, 3 * F, F, T2, F, L.A2t, L.c2, nullptr, 0, AV, 3 * F);
     if (n > 0) {
       LaunchScope ls_(st);
-      k_update_post<float><<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1],
-                                                    t + 1 < T ? B[B_V0 + t + 1] : nullptr, nullptr);
+      if (t + 1 < T)
+        k_update_post<float, true><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1],
+                                                             nullptr);
+      else
+        k_update_post<float, false><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], nullptr, nullptr);
     }
   }
   // readout
@@ -1353,9 +1392,11 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     if (n > 0) {
       LaunchScope ls_(st);
       // the last layer's v and BF16 s feed nothing: only its FP32 s reaches the readout
-      k_update_post<__half><<<nb, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1],
-                                                     t + 1 < T ? B[B_V0 + t + 1] : nullptr,
-                                                     t + 1 < T ? Bb[BB_S0 + t + 1] : nullptr);
+      if (t + 1 < T)
+        k_update_post<__half, true><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1],
+                                                              Bb[BB_S0 + t + 1]);
+      else
+        k_update_post<__half, false><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], nullptr, nullptr);
     }
   }
   // The readout MLP (F -> F/2 -> 1, ~1 % of the node FLOPs) stays in FP32: its output is the
