@@ -147,7 +147,8 @@ int check_status(ctd_ctx* c) {
   if (st & ST_REV_MISSING) return fail(c, CTD_ERR_CAPACITY, "reverse edge missing in the neighbour list");
   if (st & ST_FP16_RANGE)
     return fail(c, CTD_ERR_NONFINITE,
-                "an activation stored in FP16 (message table, U/V products or update coefficients) is outside "
+                "an activation stored in FP16 (message table, U/V products, update coefficients or SiLU arguments) "
+                "is outside "
                 "the FP16 range; the FP32 path keeps them in FP32");
   if (st & ST_NONFINITE) return fail(c, CTD_ERR_NONFINITE, "non-finite value in positions or results");
   if (st & ST_TIMEOUT) return fail(c, CTD_ERR_TIMEOUT, "a bounded device wait gave up");

@@ -228,8 +228,10 @@ void launch_gather_rows_d(cudaStream_t st, int64_t n, int w, const int32_t* perm
 void launch_gather_i32(cudaStream_t st, int64_t n, const int32_t* perm, const int32_t* in, int32_t* out);
 void launch_check_finite(cudaStream_t st, int64_t n, const double* a, int* status);
 // gemm_bf16.cu: C[M][N] = A[M][K] . W[N][K]^T on tcgen05 (BF16 in, FP32 accumulate), epilogue
-// EPI 0 bias, 1 bias + SiLU (bf16 copy gets the SiLU), 2 + aux, 3 * SiLU'(aux), 4 PHI packing,
-// 5 + aux written as the interleaved (aux2, rows 3i..3i+2) quads of the adjoint's G4.
+// EPI 0 bias, 1 bias + SiLU (bf16 copy gets the SiLU; outh: FP16 copy of the argument), 2 + aux,
+// 3 * SiLU'(aux), 4 PHI packing,
+// 5 + aux written as the interleaved (aux2, rows 3i..3i+2) quads of the adjoint's G4,
+// 6 * SiLU'(auxh), the argument stored in FP16.
 bool gemm_bf16_supported(int N, int K);
 bool make_tmap_bf16(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
 // edge_tc.cu: tensor-core edge adjoint (F = 128, K <= 31); G4 = the receivers' (gsm, gvm)
@@ -248,7 +250,8 @@ int edge_fwd_mma(cudaStream_t st, const ModelW& m, int t, int64_t n, const int32
 template <int EPI>
 int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, int64_t lda,
               const __nv_bfloat16* W, const float* bias, const float* aux, int ldaux, float* out, int ldo,
-              __nv_bfloat16* outb, int ldob, int* status, __half* outh = nullptr, const float* aux2 = nullptr);
+              __nv_bfloat16* outb, int ldob, int* status, __half* outh = nullptr, const float* aux2 = nullptr,
+              const __half* auxh = nullptr);
 // model_fp32.cu
 int model_buffer_count();
 bool model_uses_g4(const ModelW& m, int precision);

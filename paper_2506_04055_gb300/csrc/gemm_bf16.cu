@@ -30,11 +30,13 @@ struct GemmBf16Args {
   const float* aux;
   int ldaux;
   const float* aux2;   // EPI 5: gsm [M/3][N], the first component of each interleaved quad
+  const __half* auxh;  // EPI 6: the SiLU' argument in FP16 (stride ldaux)
   float* out;
   int ldo;
   bf16* outb;
   int ldob;
-  __half* outh;   // EPI 0 and 4: FP16 copy of out, same element stride ldo (optional; EPI 4: the message table)
+  __half* outh;   // EPI 0, 1 and 4: FP16 copy of out, same element stride ldo (optional; EPI 1: the
+                  // SiLU argument; EPI 4: the message table)
   int* status;
   int a_stages, n_acc, b_box_rows, n_chunk;   // a_stages: k-block stages of the A ring
   uint32_t tmem_cols;
@@ -207,6 +209,14 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
                            : make_float4(0.f, 0.f, 0.f, 0.f);
           }
         }
+        uint2 gh[EPI == 6 ? 8 : 1];   // EPI 6: four FP16 SiLU' arguments per row
+        if (EPI == 6) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int64_t m = m0 + cr + 4 * j;
+            gh[j] = m < p.M ? __ldg(reinterpret_cast<const uint2*>(p.auxh + m * p.ldaux + c0 + cc)) : make_uint2(0u, 0u);
+          }
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int r = cr + 4 * j;
@@ -268,8 +278,13 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
             if (EPI == 3) {
               x.x *= dsilu_fast(g[j].x); x.y *= dsilu_fast(g[j].y); x.z *= dsilu_fast(g[j].z); x.w *= dsilu_fast(g[j].w);
             }
+            if (EPI == 6) {
+              const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&gh[j].x));
+              const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&gh[j].y));
+              x.x *= dsilu_fast(a.x); x.y *= dsilu_fast(a.y); x.z *= dsilu_fast(b.x); x.w *= dsilu_fast(b.y);
+            }
             if (p.out) *reinterpret_cast<float4*>(p.out + m * p.ldo + c0 + cc) = x;
-            if (EPI == 0 && p.outh) {
+            if ((EPI == 0 || EPI == 1) && p.outh) {
               const float ym = fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w)));
               if (ym > 65504.f) atomicOr(p.status, (int)ST_FP16_RANGE);
               const __half2 h01 = __floats2half2_rn(x.x, x.y), h23 = __floats2half2_rn(x.z, x.w);
@@ -344,7 +359,7 @@ bool gemm_bf16_supported(int N, int K) { return K % 32 == 0 && K >= 64 && N % 32
 template <int EPI>
 int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t lda, const bf16* W,
               const float* bias, const float* aux, int ldaux, float* out, int ldo, bf16* outb, int ldob,
-              int* status, __half* outh, const float* aux2) {
+              int* status, __half* outh, const float* aux2, const __half* auxh) {
   if (M == 0) return 0;
   // EPI 5: rows (atom, component) of whole atoms, 32-bit row arithmetic in the epilogue
   if (EPI == 5 && (M % 3 != 0 || M >= ((int64_t)1 << 31) || !out || !aux || !aux2 ||
@@ -359,8 +374,11 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
     return -1;
   GemmBf16Args p{};
   p.M = M; p.N = N; p.K = K; p.bias = bias; p.aux = aux; p.ldaux = ldaux; p.aux2 = aux2; p.out = out; p.ldo = ldo;
-  p.outb = outb; p.ldob = ldob; p.status = status; p.outh = (EPI == 0 || EPI == 4) ? outh : nullptr;
+  p.outb = outb; p.ldob = ldob; p.status = status; p.outh = (EPI == 0 || EPI == 1 || EPI == 4) ? outh : nullptr;
   if (p.outh && (reinterpret_cast<uintptr_t>(outh) & 7)) return -1;
+  p.auxh = EPI == 6 ? auxh : nullptr;
+  if (EPI == 6 && (!auxh || ldaux % 4 || (reinterpret_cast<uintptr_t>(auxh) & 7))) return -1;
+  if ((EPI == 2 || EPI == 3) && !aux) return -1;
   p.b_box_rows = N % 64 == 0 ? 64 : 32;
   p.n_chunk = N <= 256 ? N : N / 2;
   if (p.n_chunk > 256 || p.n_chunk % 16) return -1;
@@ -381,7 +399,7 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
   size_t smem = 1024 + b_bytes + (size_t)p.a_stages * kATileBytes + t_bytes + 256;
   // a CTA holding more than half of TMEM runs alone on its SM, so allocation never waits
   if (p.tmem_cols > 256 && smem < 120 * 1024) smem = 120 * 1024;
-  static bool attr_set[6] = {false, false, false, false, false, false};
+  static bool attr_set[7] = {false, false, false, false, false, false, false};
   if (!attr_set[EPI]) {
     cudaFuncSetAttribute(k_gemm_bf16<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set[EPI] = true;
@@ -396,16 +414,25 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
 }
 
 template int gemm_bf16<0>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*,
+                          const __half*);
 template int gemm_bf16<1>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*,
+                          const __half*);
 template int gemm_bf16<2>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*,
+                          const __half*);
 template int gemm_bf16<3>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*,
+                          const __half*);
 template int gemm_bf16<4>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*,
+                          const __half*);
 template int gemm_bf16<5>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
-                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*);
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*,
+                          const __half*);
+template int gemm_bf16<6>(cudaStream_t, int64_t, int, int, const bf16*, int64_t, const bf16*, const float*,
+                          const float*, int, float*, int, bf16*, int, int*, __half*, const float*,
+                          const __half*);
 
 }  // namespace ctd

@@ -1110,7 +1110,7 @@ void edge_smem_setup() {
 
 // Buffers (all float, sized by the caller; see api.cu for the list and shapes).
 enum BufId {
-  B_S0 = 0,                        // S[t] for t = 0..T  -> ids B_S0 + t
+  B_S0 = 0,                        // s, one buffer for every layer (ids B_S0 + t unused)
   B_V0 = B_S0 + kMaxT + 1,         // V[t] for t = 0..T
   B_PHI0 = B_V0 + kMaxT + 1,       // [n][6F] per layer
   B_H10 = B_PHI0 + kMaxT,          // [n][F]
@@ -1178,14 +1178,16 @@ bool model_phi_fp16_only(const ModelW& m, int precision) {
 int64_t model_buffer_floats_per_atom(int b, const ModelW& m, int F, int T, int precision) {
   const bool g4 = model_uses_g4(m, precision), bf16 = precision == CTD_PREC_BF16;
   auto layer = [&](int base, int cnt) { return b >= base && b < base + cnt; };
-  if (layer(B_S0, T + 1)) return F;
+  // s[t] is read only by layer t's forward (message residual; the backward never reads it), so
+  // every layer's s lives in one buffer, overwritten by the next layer's update
+  if (layer(B_S0, T + 1)) return b == B_S0 ? F : 0;
   if (layer(B_V0, T + 1)) return T > 0 && b == B_V0 + T ? 0 : 3 * F;   // v[T] is never formed
   if (layer(B_PHI0, T)) return model_phi_fp16_only(m, precision) ? 0 : 6 * F;
-  if (layer(B_H10, T)) return F;
+  if (layer(B_H10, T)) return bf16 ? 0 : F;   // the BF16 path keeps h1, h2 in FP16 (BB_H1H0, BB_H2H0)
   if (b == B_SM0 && T > 0) return F;
   if (b == B_VM0 && T > 0) return 3 * F;
   if (layer(B_UV0, T)) return bf16 ? 0 : 6 * F;   // the BF16 path keeps U/V products and
-  if (layer(B_H20, T)) return F;
+  if (layer(B_H20, T)) return bf16 ? 0 : F;
   if (layer(B_AV0, T)) return bf16 ? 0 : 3 * F;   // update coefficients in FP16 (BB_UVH0, BB_AVH0)
   switch (b) {
     case B_T1: return bf16 ? 2 * F : 3 * F;   // the BF16 path uses only T1, as [n][2F]
@@ -1215,7 +1217,7 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
   if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], nullptr); }
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
-    float *S = B[B_S0 + t], *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
+    float *S = B[B_S0], *V = B[B_V0 + t], *PHI = B[B_PHI0 + t], *H1 = B[B_H10 + t];
     float *SM = B[B_SM0], *VM = B[B_VM0], *UV = B[B_UV0 + t], *H2 = B[B_H20 + t], *AV = B[B_AV0 + t];
     float *T1 = B[B_T1], *T2 = B[B_T2];
     // phi = W2 silu(W1 s + b1) + b2
@@ -1238,15 +1240,15 @@ void model_forward_backward_fp32(cudaStream_t st, const ModelW& m, int64_t n, co
     if (n > 0) {
       LaunchScope ls_(st);
       if (t + 1 < T)
-        k_update_post<float, true><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1],
+        k_update_post<float, true><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, S, B[B_V0 + t + 1],
                                                              nullptr);
       else
-        k_update_post<float, false><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], nullptr, nullptr);
+        k_update_post<float, false><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, S, nullptr, nullptr);
     }
   }
   // readout
   // readout, and dU/ds^T = G3 R1
-  readout_fwd_bwd(st, m, n, B[B_S0 + T], ew, need_grad, B, e_atom, energy_partials, n_energy_partials);
+  readout_fwd_bwd(st, m, n, B[B_S0], ew, need_grad, B, e_atom, energy_partials, n_energy_partials);
   if (!need_grad) return;
   if (n > 0) cudaMemsetAsync(B[B_GV], 0, sizeof(float) * (size_t)n * 3 * F, st);
   for (int t = T - 1; t >= 0; --t) {
@@ -1291,10 +1293,12 @@ void launch_forces(cudaStream_t st, int64_t n, const int32_t* arow, const float4
 
 // ================================================================================ BF16 driver
 // Same layer as above; every node MLP contraction runs on tcgen05 with BF16 operands and FP32
-// accumulation (gemm_bf16.cu).  Producers write a BF16 shadow of each GEMM A operand; all
-// elementwise work, the edge kernels, the reductions and the stored activations stay FP32.
+// accumulation (gemm_bf16.cu).  Producers write a BF16 shadow of each GEMM A operand; the
+// elementwise work, the reductions and the residual streams s, v and their gradients stay FP32;
+// the stored activations the backward reads as operands (message tables, U/V products, update
+// coefficients, SiLU arguments) are kept in FP16, each write range-checked.
 enum BufB {
-  BB_S0 = 0,                 // bf16 S[t], t = 0..T    [n][F]
+  BB_S0 = 0,                 // bf16 s, one buffer     [n][F]
   BB_A1 = BB_S0 + kMaxT + 1, // silu(h1)               [n][F]
   BB_VM,                     // v^m                    [n][3F]
   BB_Z,                      // [s^m ; |Vv|]           [n][2F]
@@ -1308,7 +1312,9 @@ enum BufB {
                              // (contracted message step; ids BB_PHIH0 + t)
   BB_UVH0 = BB_PHIH0 + kMaxT, // FP16 U/V products of layer t, rows (i, a) = [Uv_a | Vv_a]  [3n][2F]
   BB_AVH0 = BB_UVH0 + kMaxT,  // FP16 update coefficients of layer t, [a_vv | a_sv | a_ss]  [n][3F]
-  BB_COUNT = BB_AVH0 + kMaxT
+  BB_H1H0 = BB_AVH0 + kMaxT,  // FP16 SiLU arguments h1, h2 of layer t (read back only as SiLU'
+  BB_H2H0 = BB_H1H0 + kMaxT,  // arguments of the BF16 backward GEMMs)  [n][F]
+  BB_COUNT = BB_H2H0 + kMaxT
 };
 
 int model_bf16_buffer_count() { return BB_COUNT; }
@@ -1324,10 +1330,12 @@ bool model_stores_edges(const ModelW& m, int precision) {
 }
 
 int64_t model_bf16_buffer_elems_per_atom(int b, int F, int T, bool msg_mma) {
-  if (b >= BB_S0 && b < BB_S0 + T + 1) return T > 0 && b == BB_S0 + T ? 0 : F;   // no BF16 s[T]
+  if (b >= BB_S0 && b < BB_S0 + T + 1) return b == BB_S0 ? F : 0;   // read by the next W1 GEMM only
   if (b >= BB_PHIH0 && b < BB_PHIH0 + kMaxT) return msg_mma && b < BB_PHIH0 + T ? 6 * F : 0;
   if (b >= BB_UVH0 && b < BB_UVH0 + kMaxT) return b < BB_UVH0 + T ? 6 * F : 0;
   if (b >= BB_AVH0 && b < BB_AVH0 + kMaxT) return b < BB_AVH0 + T ? 3 * F : 0;
+  if (b >= BB_H1H0 && b < BB_H1H0 + kMaxT) return b < BB_H1H0 + T ? F : 0;
+  if (b >= BB_H2H0 && b < BB_H2H0 + kMaxT) return b < BB_H2H0 + T ? F : 0;
   switch (b) {
     case BB_A1: case BB_A2: case BB_GH2: case BB_GH1: return F;
     case BB_VM: case BB_GA: case BB_GP3: return 3 * F;
@@ -1365,12 +1373,14 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], Bb[BB_S0]); }
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
-    float *S = B[B_S0 + t], *V = B[B_V0 + t], *PHI = phi32 ? B[B_PHI0 + t] : nullptr, *H1 = B[B_H10 + t];
-    float *SM = B[B_SM0], *VM = B[B_VM0], *H2 = B[B_H20 + t];
+    float *S = B[B_S0], *V = B[B_V0 + t], *PHI = phi32 ? B[B_PHI0 + t] : nullptr;
+    float *SM = B[B_SM0], *VM = B[B_VM0];
+    __half* H1 = reinterpret_cast<__half*>(Bb[BB_H1H0 + t]);   // SiLU arguments in FP16
+    __half* H2 = reinterpret_cast<__half*>(Bb[BB_H2H0 + t]);
     __half* PHIh = phih(t);
     __half* UV = reinterpret_cast<__half*>(Bb[BB_UVH0 + t]);   // FP16 copies (range checked by the GEMMs)
     __half* AV = reinterpret_cast<__half*>(Bb[BB_AVH0 + t]);
-    bad |= gemm_bf16<1>(st, n, F, F, Bb[BB_S0 + t], F, L.W1b, L.b1, nullptr, 0, H1, F, Bb[BB_A1], F, status);
+    bad |= gemm_bf16<1>(st, n, F, F, Bb[BB_S0], F, L.W1b, L.b1, nullptr, 0, nullptr, F, Bb[BB_A1], F, status, H1);
     // phi = W2 silu(.) + b2, packed into PHI (and its FP16 copy) by the GEMM epilogue
     bad |= gemm_bf16<4>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, V, 3 * F, PHI, 6 * F, nullptr, 0, status, PHIh);
     float* wst = (wstore && need_grad && !use_tc_bwd && !msg_mma) ? wstore + t * wstore_layer_floats : nullptr;
@@ -1387,34 +1397,36 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     bad |= gemm_bf16<0>(st, 3 * n, 2 * F, F, Bb[BB_VM], F, L.UVb, nullptr, nullptr, 0, nullptr, 2 * F, nullptr, 0,
                         status, UV);
     if (n > 0) { LaunchScope ls_(st); k_update_pre<__half><<<nb4, kThreads, 0, st>>>(n, F, m.eps, SM, UV, nullptr, Bb[BB_Z]); }
-    bad |= gemm_bf16<1>(st, n, F, 2 * F, Bb[BB_Z], 2 * F, L.A1b, L.c1, nullptr, 0, H2, F, Bb[BB_A2], F, status);
+    bad |= gemm_bf16<1>(st, n, F, 2 * F, Bb[BB_Z], 2 * F, L.A1b, L.c1, nullptr, 0, nullptr, F, Bb[BB_A2], F, status,
+                        H2);
     bad |= gemm_bf16<0>(st, n, 3 * F, F, Bb[BB_A2], F, L.A2b, L.c2, nullptr, 0, nullptr, 3 * F, nullptr, 0, status, AV);
     if (n > 0) {
       LaunchScope ls_(st);
       // the last layer's v and BF16 s feed nothing: only its FP32 s reaches the readout
       if (t + 1 < T)
-        k_update_post<__half, true><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], B[B_V0 + t + 1],
-                                                              Bb[BB_S0 + t + 1]);
+        k_update_post<__half, true><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, S, B[B_V0 + t + 1], Bb[BB_S0]);
       else
-        k_update_post<__half, false><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, B[B_S0 + t + 1], nullptr, nullptr);
+        k_update_post<__half, false><<<nb4, kThreads, 0, st>>>(n, F, SM, VM, UV, AV, S, nullptr, nullptr);
     }
   }
   // The readout MLP (F -> F/2 -> 1, ~1 % of the node FLOPs) stays in FP32: its output is the
   // per-atom energy itself, which BF16 operands would perturb by ~2^-9 of the readout terms.
-  readout_fwd_bwd(st, m, n, B[B_S0 + T], ew, need_grad, B, e_atom, energy_partials, n_energy_partials);
+  readout_fwd_bwd(st, m, n, B[B_S0], ew, need_grad, B, e_atom, energy_partials, n_energy_partials);
   if (!need_grad) return bad;
   if (n > 0) cudaMemsetAsync(B[B_GV], 0, sizeof(float) * (size_t)n * 3 * F, st);
   for (int t = T - 1; t >= 0; --t) {
     const LayerW& L = m.L[t];
-    float *V = B[B_V0 + t], *PHI = phi32 ? B[B_PHI0 + t] : nullptr, *H1 = B[B_H10 + t];
-    float* H2 = B[B_H20 + t];
+    float *V = B[B_V0 + t], *PHI = phi32 ? B[B_PHI0 + t] : nullptr;
+    const __half* H1 = reinterpret_cast<const __half*>(Bb[BB_H1H0 + t]);
+    const __half* H2 = reinterpret_cast<const __half*>(Bb[BB_H2H0 + t]);
     const __half* UV = reinterpret_cast<const __half*>(Bb[BB_UVH0 + t]);
     const __half* AV = reinterpret_cast<const __half*>(Bb[BB_AVH0 + t]);
     float* T1 = B[B_T1];
     float *GS = B[B_GS], *GV = B[B_GV], *GSM = B[B_GSM], *GVM = B[B_GVM], *GPHI = B[B_GPHI];
     const __half* PHIh = phih(t);
     if (n > 0) { LaunchScope ls_(st); k_update_bwd_pre_bf16<<<nb, kThreads, 0, st>>>(n, F, GS, GV, UV, AV, Bb[BB_GA], Bb[BB_GUV]); }
-    bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GA], 3 * F, L.A2tb, nullptr, H2, F, nullptr, 0, Bb[BB_GH2], F, status);
+    bad |= gemm_bf16<6>(st, n, F, 3 * F, Bb[BB_GA], 3 * F, L.A2tb, nullptr, nullptr, F, nullptr, 0, Bb[BB_GH2], F, status,
+                        nullptr, nullptr, H2);
     bad |= gemm_bf16<0>(st, n, 2 * F, F, Bb[BB_GH2], F, L.A1tb, nullptr, nullptr, 0, T1, 2 * F, nullptr, 0, status);
     // the bulk-gathered tensor-core adjoint reads gsm and gvm interleaved per feature (G4)
     float* G4 = g4 ? B[B_G4] : nullptr;
@@ -1447,7 +1459,8 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
       else
         k_phi_bwd_pre<<<nb, kThreads, 0, st>>>(n, F, GPHI, PHI, PHIh, V, GVM, nullptr, GV, Bb[BB_GP3]);
     }
-    bad |= gemm_bf16<3>(st, n, F, 3 * F, Bb[BB_GP3], 3 * F, L.W2tb, nullptr, H1, F, nullptr, 0, Bb[BB_GH1], F, status);
+    bad |= gemm_bf16<6>(st, n, F, 3 * F, Bb[BB_GP3], 3 * F, L.W2tb, nullptr, nullptr, F, nullptr, 0, Bb[BB_GH1], F,
+                        status, nullptr, nullptr, H1);
     bad |= gemm_bf16<2>(st, n, F, F, Bb[BB_GH1], F, L.W1tb, nullptr, GSM, F, GS, F, nullptr, 0, status);
   }
   StageGuard fstage(STG_FORCES);

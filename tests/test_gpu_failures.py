@@ -164,11 +164,12 @@ def _offset(name, F, K, S):
 
 
 def test_fp16_storage_beyond_range_is_reported():
-    """The BF16 path stores the message table (F = 128 contraction), the U/V products and the
-    update coefficients in FP16; a value beyond FP16's largest finite value (65504) is reported
-    instead of turning into an Inf.  A message table beyond the range is reported only where it
-    is stored in FP16 (the CUDA-core message step keeps the FP32 table); update coefficients
-    beyond it are reported on either message step; the FP32 path computes both systems."""
+    """The BF16 path stores the message table (F = 128 contraction), the U/V products, the
+    update coefficients and the SiLU arguments in FP16; a value beyond FP16's largest finite value
+    (65504) is reported instead of turning into an Inf.  Update coefficients beyond it are reported
+    on either message step; so is a message table beyond it, through the table itself where the
+    contraction stores it in FP16 and through the update's SiLU argument h2 (fed by the message)
+    where the CUDA-core message step keeps the FP32 table; the FP32 path computes both systems."""
     eng = engine()
     from paper_2506_04055_gb300 import _lib
     Fb, Tb, Sb, K = 128, 1, 1, 20
@@ -180,7 +181,7 @@ def test_fp16_storage_beyond_range_is_reported():
     coef = base.copy()
     o = _offset("c2_0", Fb, K, Sb)
     coef[o:o + 3 * Fb] = 7.0e4                       # every update coefficient beyond it
-    for vals, raises in ((phi, {1: True, 0: False}), (coef, {1: True, 0: True})):
+    for vals, raises in ((phi, {1: True, 0: True}), (coef, {1: True, 0: True})):
         blob = syn.params_blob(Fb, K, Tb, Sb, values=vals)
         for msg in (1, 0):
             with eng.Potential(Fb, K=K, T=Tb, n_species=Sb, precision="bf16", params=blob) as pot:
