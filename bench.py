@@ -351,10 +351,11 @@ def run_ours(args):
         if dist:
             dist.barrier()
         # device memory the context holds for this system (all buffers, after the runs above)
-        held = pot.compute(sy.species, sy.positions, sy.cell, stats=True)["stats"]["bytes_allocated"]
+        mst = pot.compute(sy.species, sy.positions, sy.cell, stats=True)["stats"]
+        held, in_use = mst["bytes_allocated"], mst["bytes_in_use"]
         pot.close()
         results[prec] = {"total_ms": total_ms, "step_ms": step_ms, "prof": prof, "rebuilds": rebuilds,
-                         "device_bytes_per_atom": held / sy.n,
+                         "device_bytes_per_atom": held / sy.n, "device_bytes_in_use_per_atom": in_use / sy.n,
                          "clocks": clk.summary(), "e2e_s": e2e_s, "e2e_steps": e2e_steps,
                          "h2d": n * 3 * 8 + n * 4 + 72, "d2h": n * 3 * 8 + 8 + 72,
                          "epot": [float(ep[0])], "ekin": [float(ek[0])]}
@@ -374,7 +375,8 @@ def run_ours(args):
                          "p50_ms": r["step_ms"][len(r["step_ms"]) // 2],
                          "p99_ms": r["step_ms"][min(len(r["step_ms"]) - 1, int(0.99 * len(r["step_ms"])))],
                          "e2e": whole_job_value(sy.n, world, r["e2e_steps"], 1e3 * e2e), "rebuilds": r["rebuilds"],
-                         "device_bytes_per_atom": round(r["device_bytes_per_atom"])}
+                         "device_bytes_per_atom": round(r["device_bytes_per_atom"]),
+                         "device_bytes_in_use_per_atom": round(r["device_bytes_in_use_per_atom"])}
     if dist:
         dist.destroy_process_group()
     if rank != 0:

@@ -92,6 +92,8 @@ typedef struct {
   float ms_neighbors, ms_model;   /* device time of the neighbour and model stages (ms)      */
   int32_t edges_stored;     /* 1 if the adjoint read per-edge filters stored by the forward   */
   int32_t reserved;
+  int64_t bytes_in_use;     /* device bytes the current shapes need: bytes_allocated less the  */
+                            /* growth headroom (25 % of each buffer grown)                     */
 } ctd_stats;
 
 typedef struct ctd_ctx ctd_ctx;

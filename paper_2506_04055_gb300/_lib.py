@@ -71,7 +71,7 @@ class ctd_stats(ctypes.Structure):
                 ("retries", ctypes.c_int32), ("max_displacement", ctypes.c_double),
                 ("bytes_allocated", ctypes.c_int64), ("ms_neighbors", ctypes.c_float),
                 ("ms_model", ctypes.c_float), ("edges_stored", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("bytes_in_use", ctypes.c_int64)]
 
 
 class ctd_domain_info(ctypes.Structure):

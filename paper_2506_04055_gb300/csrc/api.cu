@@ -43,9 +43,17 @@ int fail(ctd_ctx* c, int code, const std::string& msg) {
 
 
 
+static void note_need(ctd_ctx* c, DBuf& b, size_t bytes) {
+  c->used = c->used - b.need + bytes;
+  b.need = bytes;
+}
+
 // Grow-only allocation with 25 % headroom, charged against the budget.
 int ensure(ctd_ctx* c, DBuf& b, size_t bytes) {
-  if (bytes <= b.bytes) return CTD_OK;
+  if (bytes <= b.bytes) {
+    note_need(c, b, bytes);
+    return CTD_OK;
+  }
   if (c->capturing) return fail(c, CTD_ERR_STATE, "a buffer would grow during graph capture");
   ++c->alloc_gen;
   size_t want = bytes + bytes / 4 + 256;
@@ -61,8 +69,10 @@ int ensure(ctd_ctx* c, DBuf& b, size_t bytes) {
     cudaStreamSynchronize(c->st);
     cudaFree(b.p);
     c->held -= b.bytes;
+    c->used -= b.need;
     b.p = nullptr;
     b.bytes = 0;
+    b.need = 0;
   }
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, want);
@@ -74,6 +84,7 @@ int ensure(ctd_ctx* c, DBuf& b, size_t bytes) {
   b.p = p;
   b.bytes = want;
   c->held += want;
+  note_need(c, b, bytes);
   return CTD_OK;
 }
 
@@ -989,6 +1000,7 @@ int ctd_compute(ctd_ctx* c, int64_t n, const int32_t* species, const double* pos
     stats->retries = 0;
     stats->max_displacement = md;
     stats->bytes_allocated = (int64_t)c->held;
+    stats->bytes_in_use = (int64_t)c->used;
     stats->edges_stored = c->last_stored ? 1 : 0;
     cudaEventElapsedTime(&stats->ms_neighbors, ev[0], ev[1]);
     cudaEventElapsedTime(&stats->ms_model, ev[1], ev[2]);

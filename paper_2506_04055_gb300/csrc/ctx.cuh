@@ -12,6 +12,7 @@ namespace ctd {
 struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  size_t need = 0;   // bytes the last request asked for (the rest of `bytes` is growth headroom)
 };
 
 constexpr int kPartials = 152 * 4;   // fixed block count of the reductions (deterministic)
@@ -30,7 +31,7 @@ struct ctd_ctx {
   int device = 0;
   cudaStream_t st = nullptr;
   bool own_stream = false;
-  size_t budget = 0, held = 0;
+  size_t budget = 0, held = 0, used = 0;   // used: the buffers' last requests
   std::string err;
   // While a served step is being captured into a CUDA graph, a buffer that would have to grow
   // fails instead of reallocating (the capture is then abandoned); alloc_gen counts every

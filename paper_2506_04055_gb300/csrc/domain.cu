@@ -354,8 +354,10 @@ void dfree(ctd_ctx* c, DBuf& b) {
   if (b.p) {
     cudaFree(b.p);
     c->held -= b.bytes;
+    c->used -= b.need;
     b.p = nullptr;
     b.bytes = 0;
+    b.need = 0;
   }
 }
 

@@ -43,6 +43,10 @@ struct GemmBf16Args {
 };
 
 constexpr int kTileM = 128;
+// Output rows per tile: EPI 5 takes 126 (42 whole atoms of three component rows; the MMA still
+// covers 128 rows, the last two of which belong to the next tile and are ignored).
+template <int EPI>
+constexpr int tile_rows() { return EPI == 5 ? 126 : kTileM; }
 constexpr int kBlockK = 64;
 constexpr int kATileBytes = kTileM * kBlockK * 2;   // 16 KB per 64-column block
 constexpr int kTP = 36;                              // row pitch (floats) of an epilogue transpose tile
@@ -71,10 +75,12 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
   uint64_t* tfull = bars + 2 * kMaxAStages; // [2]
   uint64_t* tempty = tfull + 2;             // [2]
   uint64_t* bbar = tempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bbar + 1);
+  uint64_t* gbar = bbar + 1;                // [4] EPI 5: one per epilogue group (its four quarter warps)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ntiles = (p.M + kTileM - 1) / kTileM;
+  constexpr int kRT = tile_rows<EPI>();
+  const int64_t ntiles = (p.M + kRT - 1) / kRT;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < p.a_stages; ++i) {
@@ -86,6 +92,7 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
       umma::mbar_init(&tempty[i], kEpiWarps);
     }
     umma::mbar_init(bbar, 1);
+    for (int i = 0; i < 4; ++i) umma::mbar_init(&gbar[i], 4);
     umma::mbar_fence_init();
   }
   if (warp == 1) umma::tmem_alloc(tmem_slot, p.tmem_cols);
@@ -109,7 +116,7 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
           const int64_t u = g / p.a_stages;
           if (g >= p.a_stages && !umma::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) { ok = false; break; }
           umma::mbar_expect_tx(&full[s], (uint32_t)kATileBytes);
-          umma::tma_load_2d(sA + (size_t)s * kATileBytes, &tmA, kb * kBlockK, (int)(tile * kTileM), &full[s]);
+          umma::tma_load_2d(sA + (size_t)s * kATileBytes, &tmA, kb * kBlockK, (int)(tile * kRT), &full[s]);
         }
       }
     }
@@ -157,12 +164,18 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
     float* T = sT + (warp - 2) * 32 * kTP;
     const int cr = lane >> 3, cc = 4 * (lane & 7);   // row within a group of 4, column quad
     const int nchunks = N / 32;
+    uint32_t gph = 0;   // EPI 5: phases of this group's barrier passed
+    auto gsync = [&]() -> bool {
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&gbar[grp]);
+      return umma::mbar_wait(&gbar[grp], (gph++) & 1);
+    };
     int it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++it) {
       const int a = it % p.n_acc;
       if (!umma::mbar_wait(&tfull[a], (it / p.n_acc) & 1)) { ok = false; break; }
       umma::fence_after();
-      const int64_t m0 = tile * kTileM + q * 32;   // first row of this warp's quarter
+      const int64_t m0 = tile * kRT + q * 32;   // first row of this warp's quarter
       if (grp >= nchunks) {
         umma::fence_before();
         __syncwarp();
@@ -201,7 +214,37 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
         }
         // the chunk's aux values, all loads in flight before any store
         float4 g[8];
-        if (EPI == 2 || EPI == 3 || EPI == 5) {
+        if (EPI == 5) {
+          // the group's four warps hold the four row quarters of this chunk in their shared tiles:
+          // once all are written, the group's 128 threads assemble G4 quads of whole atoms,
+          // 8 threads per atom (32 features, 512 contiguous bytes)
+          if (!gsync()) { ok = false; break; }
+          const int tg = ((warp - 2) & 3) * 32 + lane;
+          const int64_t a0 = tile * (kRT / 3);
+          for (int item = tg; item < (kRT / 3) * 8; item += 128) {
+            const int al = item >> 3, fq = 4 * (item & 7);
+            const int64_t ai = a0 + al;
+            if (3 * ai >= p.M) break;
+            float4 x[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const int r = 3 * al + k, qq = r >> 5;
+              const float* Tq = sT + (4 * grp + ((qq + 2) & 3)) * 32 * kTP;
+              const float4 t = *reinterpret_cast<const float4*>(Tq + (r & 31) * kTP + fq);
+              const float4 gk = __ldg(reinterpret_cast<const float4*>(p.aux + (3 * ai + k) * p.ldaux + c0 + fq));
+              x[k] = make_float4(t.x + gk.x, t.y + gk.y, t.z + gk.z, t.w + gk.w);
+            }
+            const float4 gs = __ldg(reinterpret_cast<const float4*>(p.aux2 + ai * N + c0 + fq));
+            float4* o = reinterpret_cast<float4*>(p.out + (ai * N + c0 + fq) * 4);
+            o[0] = make_float4(gs.x, x[0].x, x[1].x, x[2].x);
+            o[1] = make_float4(gs.y, x[0].y, x[1].y, x[2].y);
+            o[2] = make_float4(gs.z, x[0].z, x[1].z, x[2].z);
+            o[3] = make_float4(gs.w, x[0].w, x[1].w, x[2].w);
+          }
+          if (!gsync()) { ok = false; break; }   // the tiles are free for the next chunk
+          continue;
+        }
+        if (EPI == 2 || EPI == 3) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int64_t m = m0 + cr + 4 * j;
@@ -260,21 +303,7 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
               }
               continue;
             }
-            if (EPI == 2 || EPI == 5) { x.x += g[j].x; x.y += g[j].y; x.z += g[j].z; x.w += g[j].w; }
-            if (EPI == 5) {
-              // rows are (atom, spatial component), m = 3 i + a: out[i][c] = (gsm, gvm_0, gvm_1,
-              // gvm_2), the receivers' gradients interleaved per feature for the bulk-gathered
-              // adjoint; the three rows of an atom are written by the same or a neighbouring
-              // chunk, so whole sectors reach DRAM
-              const uint32_t mi = (uint32_t)m / 3u, ca = (uint32_t)m - 3u * mi;
-              float* o = p.out + ((int64_t)mi * N + c0 + cc) * 4;
-              o[1 + ca] = x.x; o[5 + ca] = x.y; o[9 + ca] = x.z; o[13 + ca] = x.w;
-              if (ca == 0) {
-                const float4 gs = __ldg(reinterpret_cast<const float4*>(p.aux2 + (int64_t)mi * N + c0 + cc));
-                o[0] = gs.x; o[4] = gs.y; o[8] = gs.z; o[12] = gs.w;
-              }
-              continue;
-            }
+            if (EPI == 2) { x.x += g[j].x; x.y += g[j].y; x.z += g[j].z; x.w += g[j].w; }
             if (EPI == 3) {
               x.x *= dsilu_fast(g[j].x); x.y *= dsilu_fast(g[j].y); x.z *= dsilu_fast(g[j].z); x.w *= dsilu_fast(g[j].w);
             }
@@ -404,7 +433,7 @@ int gemm_bf16(cudaStream_t st, int64_t M, int N, int K, const bf16* A, int64_t l
     cudaFuncSetAttribute(k_gemm_bf16<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set[EPI] = true;
   }
-  const int64_t ntiles = (M + kTileM - 1) / kTileM;
+  const int64_t ntiles = (M + tile_rows<EPI>() - 1) / tile_rows<EPI>();
   const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
   {
     LaunchScope ls_(st);

@@ -216,8 +216,10 @@ void free_buf(ctd_ctx* c, DBuf& b) {
     ++c->alloc_gen;
     cudaFree(b.p);
     c->held -= b.bytes;
+    c->used -= b.need;
     b.p = nullptr;
     b.bytes = 0;
+    b.need = 0;
   }
 }
 
