@@ -448,7 +448,9 @@ __global__ void __launch_bounds__(kThreads_, 1) k_edge_msg_mma(const __grid_cons
         if (kEpiWG == 2 && b != wg) continue;
         if (!ok) continue;
         const float s_in = p.S[i * kF + c];
-        const float v_in0 = p.V[i * 3 * kF + c], v_in1 = p.V[i * 3 * kF + kF + c], v_in2 = p.V[i * 3 * kF + 2 * kF + c];
+        // V null: the first layer, whose input vector features are zero
+        const float v_in0 = p.V ? p.V[i * 3 * kF + c] : 0.f, v_in1 = p.V ? p.V[i * 3 * kF + kF + c] : 0.f,
+                    v_in2 = p.V ? p.V[i * 3 * kF + 2 * kF + c] : 0.f;
         if (!__all_sync(0xffffffffu, umma::mbar_wait(&tfull[b], (uint32_t)((q >> 1) & 1)))) {
           ok = false;
           continue;
@@ -511,7 +513,8 @@ __global__ void __launch_bounds__(kThreads_, 1) k_edge_msg_mma(const __grid_cons
       } else if (wg == 0) {
         // a row without edges: the residual alone
         const float sm = p.S[i * kF + c];
-        const float vm0 = p.V[i * 3 * kF + c], vm1 = p.V[i * 3 * kF + kF + c], vm2 = p.V[i * 3 * kF + 2 * kF + c];
+        const float vm0 = p.V ? p.V[i * 3 * kF + c] : 0.f, vm1 = p.V ? p.V[i * 3 * kF + kF + c] : 0.f,
+                    vm2 = p.V ? p.V[i * 3 * kF + 2 * kF + c] : 0.f;
         p.SM[i * kF + c] = sm;
         p.VM[i * 3 * kF + c] = vm0;
         p.VM[i * 3 * kF + kF + c] = vm1;

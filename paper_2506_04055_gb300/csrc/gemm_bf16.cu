@@ -203,13 +203,14 @@ __global__ void __launch_bounds__(64 + 32 * epi_warps<EPI>(), 1) k_gemm_bf16(con
         const int Fb = N / 3, blk = EPI == 4 ? c0 / Fb : 0, f0 = c0 - blk * Fb + cc;
         float4 gv[EPI == 4 ? 8 : 1][3];
         if (EPI == 4 && blk == 1) {
+          // aux null: v = 0 (first layer), psi = 0
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int64_t m = m0 + cr + 4 * j;
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-              gv[j][c] = m < p.M ? __ldg(reinterpret_cast<const float4*>(p.aux + m * p.ldaux + c * Fb + f0))
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+              gv[j][c] = m < p.M && p.aux ? __ldg(reinterpret_cast<const float4*>(p.aux + m * p.ldaux + c * Fb + f0))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
           }
         }
         // the chunk's aux values, all loads in flight before any store

@@ -184,9 +184,11 @@ __global__ void k_embed(int64_t n, int F, const int32_t* __restrict__ Z, const f
   int f = (int)(idx % F);
   S[idx] = emb[(int64_t)Z[i] * F + f];
   if (Sb) Sb[idx] = __float2bfloat16_rn(S[idx]);
-  V[i * 3 * F + f] = 0.0f;
-  V[i * 3 * F + F + f] = 0.0f;
-  V[i * 3 * F + 2 * F + f] = 0.0f;
+  if (V) {   // null where the first layer's kernels take v = 0 without reading it
+    V[i * 3 * F + f] = 0.0f;
+    V[i * 3 * F + F + f] = 0.0f;
+    V[i * 3 * F + 2 * F + f] = 0.0f;
+  }
 }
 
 // PHI[i] = [phi_s | v_0 phi_vv | v_1 phi_vv | v_2 phi_vv | phi_vs | phi_vv]
@@ -1181,7 +1183,12 @@ int64_t model_buffer_floats_per_atom(int b, const ModelW& m, int F, int T, int p
   // s[t] is read only by layer t's forward (message residual; the backward never reads it), so
   // every layer's s lives in one buffer, overwritten by the next layer's update
   if (layer(B_S0, T + 1)) return b == B_S0 ? F : 0;
-  if (layer(B_V0, T + 1)) return T > 0 && b == B_V0 + T ? 0 : 3 * F;   // v[T] is never formed
+  if (layer(B_V0, T + 1)) {
+    if (T > 0 && b == B_V0 + T) return 0;   // v[T] is never formed
+    // v[0] = 0: the BF16 path with the contracted message step never stores it
+    if (b == B_V0 && bf16 && model_uses_msg_mma(m)) return 0;
+    return 3 * F;
+  }
   if (layer(B_PHI0, T)) return model_phi_fp16_only(m, precision) ? 0 : 6 * F;
   if (layer(B_H10, T)) return bf16 ? 0 : F;   // the BF16 path keeps h1, h2 in FP16 (BB_H1H0, BB_H2H0)
   if (b == B_SM0 && T > 0) return F;
@@ -1370,7 +1377,11 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
   // table is written only for the CUDA-core adjoint, which reads it
   const bool phi32 = !model_phi_fp16_only(m, CTD_PREC_BF16);
   auto phih = [&](int t) { return msg_mma ? reinterpret_cast<__half*>(Bb[BB_PHIH0 + t]) : nullptr; };
-  if (n > 0) { LaunchScope ls_(st); k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], B[B_V0], Bb[BB_S0]); }
+  // with the contracted message step the first layer takes v = 0 without a stored v[0]
+  if (n > 0) {
+    LaunchScope ls_(st);
+    k_embed<<<nb, kThreads, 0, st>>>(n, F, species_s, m.emb, B[B_S0], msg_mma ? nullptr : B[B_V0], Bb[BB_S0]);
+  }
   for (int t = 0; t < T; ++t) {
     const LayerW& L = m.L[t];
     float *S = B[B_S0], *V = B[B_V0 + t], *PHI = phi32 ? B[B_PHI0 + t] : nullptr;
@@ -1382,13 +1393,14 @@ int model_forward_backward_bf16(cudaStream_t st, const ModelW& m, int64_t n, con
     __half* AV = reinterpret_cast<__half*>(Bb[BB_AVH0 + t]);
     bad |= gemm_bf16<1>(st, n, F, F, Bb[BB_S0], F, L.W1b, L.b1, nullptr, 0, nullptr, F, Bb[BB_A1], F, status, H1);
     // phi = W2 silu(.) + b2, packed into PHI (and its FP16 copy) by the GEMM epilogue
-    bad |= gemm_bf16<4>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, V, 3 * F, PHI, 6 * F, nullptr, 0, status, PHIh);
+    const float* Vin = (t == 0 && msg_mma) ? nullptr : V;   // null: v = 0, psi = 0
+    bad |= gemm_bf16<4>(st, n, 3 * F, F, Bb[BB_A1], F, L.W2b, L.b2, Vin, 3 * F, PHI, 6 * F, nullptr, 0, status, PHIh);
     float* wst = (wstore && need_grad && !use_tc_bwd && !msg_mma) ? wstore + t * wstore_layer_floats : nullptr;
 #define CTD_FWD(KPV) edge_fwd_kp<KPV>(st, m, t, n, arow, acol, ar, PHI, S, V, SM, VM, Bb[BB_VM], wst)
     if (n > 0) {
       StageGuard sg(STG_EDGE_FWD);
       if (msg_mma) {
-        bad |= edge_fwd_mma(st, m, t, n, arow, acol, ar, PHIh, S, V, SM, VM, Bb[BB_VM], status);
+        bad |= edge_fwd_mma(st, m, t, n, arow, acol, ar, PHIh, S, Vin, SM, VM, Bb[BB_VM], status);
       } else {
         CTD_KP_DISPATCH(m.KP, CTD_FWD)
       }
