@@ -131,7 +131,8 @@ def test_cell_too_thin_for_the_image_search():
 @pytest.mark.parametrize("precision,width", [("fp32", 64), ("bf16", 128)])
 def test_small_large_small_equals_fresh_contexts(precision, width):
     """Grow-only buffers: a context that computed a much larger system gives the small system's
-    results bit for bit as a fresh context does (F = 128 BF16 runs the tensor-core kernels)."""
+    results bit for bit as a fresh context does (F = 128 BF16 runs the tensor-core kernels), and
+    its statistics separate the bytes the current shapes need from the bytes held."""
     eng = engine()
     vals = syn.xavier_params(width, 20, T, S, seed=5, bias_scale=0.1)
     blob = syn.params_blob(width, 20, T, S, values=vals)
@@ -150,6 +151,13 @@ def test_small_large_small_equals_fresh_contexts(precision, width):
         assert b["stats"]["bytes_allocated"] > 4 * held_small     # the buffers grew
         c = pot.compute(small.species, small.positions, small.cell, stats=True)
         assert c["stats"]["bytes_allocated"] == b["stats"]["bytes_allocated"]   # and never shrink
+    # bytes in use follow the current shapes; what is held above them is the growth headroom
+    # (a quarter of each buffer grown, plus 256-byte rounding) and, after the large system, the
+    # capacity the small one leaves unused
+    for r in (a, b):
+        use, held = r["stats"]["bytes_in_use"], r["stats"]["bytes_allocated"]
+        assert 0 < use <= held <= 1.25 * use + (1 << 17)
+    assert 0 < c["stats"]["bytes_in_use"] * 4 < b["stats"]["bytes_in_use"]
     for got, ref in ((a, ref_small), (b, ref_large), (c, ref_small)):
         _same(got, ref)
 
